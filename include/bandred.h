@@ -1,0 +1,148 @@
+/*
+ * bandred: reduction of dense FP64 matrices to compact band form on NVIDIA GB300 (sm_103a).
+ *
+ * The operations follow Rodriguez-Sanchez, Catalan, Herrero, Quintana-Orti, Tomas,
+ * "Look-Ahead in the Two-Sided Reduction to Compact Band Forms for Symmetric Eigenvalue
+ * Problems and the SVD" (arXiv:1709.00302):
+ *
+ *   sy2sb  Section 2.1 (Eqs. updateA0, updateA1, updateA2, updateA2symm .. updateA2syr2k)
+ *          with the look-ahead of Section 2.2 (Variants V1, 2b <= w, and V2, 2b > w):
+ *          symmetric A = Q B Q^T, B symmetric with bandwidth w.
+ *   ge2gb  Section 3.1 (Eqs. updateB, updateCD, updateC, updateD) with the look-ahead
+ *          rules of Section 3.2 (w >= 3b for both overlaps):
+ *          general A (m x n, m >= n) = U B V^T, B upper triangular with upper bandwidth w.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Matrices are FP64, column-major: A(i, j) = A[i + j * lda], 0-based.
+ *  - Every pointer to matrix data, tau, workspace or status is DEVICE memory owned by the
+ *    caller; nothing is freed by the library.  Sizes and option structs are host values.
+ *  - Calls are stream-ordered on `stream` and, unless stated otherwise, return on the host
+ *    before the device finishes.  The "_ex" and batched forms never allocate memory and
+ *    never synchronise; they are safe to capture in a CUDA graph once the first call for
+ *    that shape has been made (the first call on a device configures kernel attributes).
+ *  - Reflectors follow the Householder convention of Golub & Van Loan as used by LAPACK:
+ *    for x = [alpha; x2], beta = -sign(alpha) ||x||_2 with sign(0) = +1,
+ *    tau = (beta - alpha) / beta, v = [1; x2 / (alpha - beta)], H = I - tau v v^T;
+ *    when x2 = 0 (or x has length 1) tau = 0 and H = I.
+ *  - Return value (LAPACK-style info): 0 on success; -i when the i-th argument is invalid;
+ *    BANDRED_ERR_* (< -1000) for a CUDA error or an unusable workspace.  Device-side
+ *    failures (a bounded wait that timed out) are written to the caller's `dev_status`
+ *    (an int in device memory; 0 = OK, see BANDRED_DEV_*), readable after the stream has
+ *    been synchronised.  NaN and Inf entries are not checked; they propagate.
+ */
+#ifndef BANDRED_H
+#define BANDRED_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Arithmetic of the trailing updates (panels, reflectors, T factors and the band
+ * write-back are always FP64). */
+enum bandred_precision {
+    BANDRED_FP64 = 0,      /* FP64 FMA on the CUDA cores */
+    BANDRED_BF16X3 = 1,    /* each FP64 operand split into bf16 slices; tensor-core
+                              products hi*hi + hi*lo + lo*hi, FP32 accumulation in TMEM,
+                              FP64 recombination (FP32-class accuracy) */
+    BANDRED_BF16X6 = 2,    /* three bf16 slices, the six products of order <= 2 */
+    BANDRED_OZAKI = 3      /* `slices` bf16 slices with exponent alignment per row/column,
+                              exact chunked FP32 accumulation, FP64 recombination */
+};
+
+/* Look-ahead variant (Section 2.2): 0 = none (the basic right-looking loop), 1 = V1
+ * (requires 2b <= w), 2 = V2 (requires 2b > w), -1 = choose from b and w. */
+typedef struct bandred_opts {
+    int b;                 /* panel width (algorithmic block size), 1 <= b <= w; 0 = default */
+    int lookahead;         /* -1 auto, 0 none, 1 V1, 2 V2 */
+    int precision;         /* enum bandred_precision */
+    int slices;            /* slices for BANDRED_OZAKI (2..8); ignored otherwise */
+    int panel_ctas;        /* CTAs of the panel factorisation (0 = all SMs when no
+                              look-ahead, a tuned share otherwise) */
+    int timeout_ms;        /* limit of every device-side wait (0 = 2000 ms) */
+    int debug;             /* 0.  Tests only: 1 makes the first device-side wait
+                              unsatisfiable, so the call ends through its bounded-wait
+                              path and reports BANDRED_DEV_TIMEOUT in dev_status */
+    int reserved[9];       /* must be zero */
+} bandred_opts;
+
+/* Device-side status codes written to dev_status. */
+#define BANDRED_DEV_OK 0
+#define BANDRED_DEV_TIMEOUT 1      /* a bounded wait ran out; the results are invalid */
+#define BANDRED_DEV_INVARIANT 2    /* an internal consistency check failed */
+
+/* Host-side error codes. */
+#define BANDRED_ERR_CUDA (-1001)       /* a CUDA runtime call failed */
+#define BANDRED_ERR_WORKSPACE (-1002)  /* workspace NULL, misaligned or too small */
+#define BANDRED_ERR_UNSUPPORTED (-1003)/* a size beyond what the kernels support */
+#define BANDRED_ERR_ALLOC (-1004)      /* the allocating short form could not allocate */
+
+/* Fill *opts with the defaults (b = min(w, 64), auto look-ahead, FP64). */
+void bandred_default_opts(bandred_opts* opts);
+
+/* Text for a return value or a device status code. */
+const char* bandred_status_string(int code);
+
+/* Description of the last CUDA runtime failure seen by this host thread (the call and
+ * the CUDA error), or "" if none.  The string is owned by the library. */
+const char* bandred_last_error(void);
+
+/* ---------------------------------------------------------------- sy2sb -------------
+ * Symmetric band reduction, Section 2.1: A = Q B Q^T.
+ *   n     order of A (n >= 0)
+ *   w     bandwidth of B (w >= 1)
+ *   A     device, n x n, lda >= max(1, n).  Only the lower triangle is read and written;
+ *         the strictly upper triangle is never accessed.  On exit the lower band
+ *         0 <= i - j <= w holds B; for reflector c (c = 0 .. n-w-1), A(c+w, c) holds its
+ *         beta (the band entry) and A(c+w+1 : n, c) holds v below its implicit unit entry.
+ *   tau   device, max(n - w, 0) entries: tau[c] of reflector c (tau[n-w-1] = 0, a length-1
+ *         reflector).  Q = H_0 H_1 ... H_{n-w-1}, H_c acting on rows c+w .. n-1.
+ * Panels of width b_k = min(b, n - w - 1 - k) start at k = 0, b, 2b, ... while k <= n-w-2.
+ */
+size_t bandred_sy2sb_workspace(int64_t n, int64_t w, const bandred_opts* opts);
+
+/* Allocating short form: allocates its workspace on `stream` (stream-ordered allocator),
+ * runs, synchronises `stream` and returns the device status as a positive code, if any.
+ * Not capturable in a CUDA graph.  opts == NULL uses the defaults. */
+int bandred_sy2sb(int64_t n, int64_t w, double* A, int64_t lda, double* tau,
+                  const bandred_opts* opts, cudaStream_t stream);
+
+/* Non-allocating form.  work: device, 256-byte aligned, at least
+ * bandred_sy2sb_workspace(n, w, opts) bytes, not shared with a concurrent call.
+ * dev_status: device int (may be NULL) set to 0 at the start and to a BANDRED_DEV_* code
+ * on a device-side failure. */
+int bandred_sy2sb_ex(int64_t n, int64_t w, double* A, int64_t lda, double* tau,
+                     const bandred_opts* opts, void* work, size_t work_bytes, int* dev_status,
+                     cudaStream_t stream);
+
+/* ---------------------------------------------------------------- ge2gb -------------
+ * Reduction to upper triangular band form, Section 3.1: A = U B V^T, m >= n.
+ *   A     device, m x n, lda >= max(1, m).  On exit the band 0 <= j - i <= w holds B;
+ *         left reflector c (c = 0 .. n-1): beta on A(c, c), v below the diagonal in
+ *         A(c+1 : m, c); right reflector c (c = 0 .. n-w-1): beta on A(c, c+w), v in row c,
+ *         A(c, c+w+1 : n).  Entries below the diagonal and right of superdiagonal w are
+ *         reflector storage.
+ *   tauq  device, n entries (left reflectors; U = Hq_0 Hq_1 ... Hq_{n-1}, Hq_c acting on
+ *         rows c .. m-1).
+ *   taup  device, max(n - w, 0) entries (right reflectors; V = Hp_0 Hp_1 ..., Hp_c acting
+ *         on columns c+w .. n-1).
+ * Returns -2 when n > m (the transposed problem is not handled).
+ */
+size_t bandred_ge2gb_workspace(int64_t m, int64_t n, int64_t w, const bandred_opts* opts);
+
+int bandred_ge2gb(int64_t m, int64_t n, int64_t w, double* A, int64_t lda, double* tauq,
+                  double* taup, const bandred_opts* opts, cudaStream_t stream);
+
+int bandred_ge2gb_ex(int64_t m, int64_t n, int64_t w, double* A, int64_t lda, double* tauq,
+                     double* taup, const bandred_opts* opts, void* work, size_t work_bytes,
+                     int* dev_status, cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BANDRED_H */

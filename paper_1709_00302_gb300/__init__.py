@@ -1,0 +1,210 @@
+"""GB300-native reduction of dense FP64 matrices to compact band form.
+
+Python binding of ``libbandred.so`` (the C ABI of ``include/bandred.h``): argument
+marshalling only.  Every step of the reduction runs in the library's CUDA kernels;
+PyTorch supplies device memory and streams.  There is no CPU fallback: when the library
+is missing or no GPU is present, the calls raise.
+
+Matrices are column-major FP64 CUDA tensors: ``A.stride(0) == 1`` and ``lda =
+A.stride(1)`` (e.g. ``torch.from_numpy(np.asfortranarray(a)).cuda()`` or ``X.t()`` of a
+contiguous ``X``).
+
+Method: Rodriguez-Sanchez et al., "Look-Ahead in the Two-Sided Reduction to Compact
+Band Forms for Symmetric Eigenvalue Problems and the SVD" (arXiv:1709.00302), Sections
+2 (sy2sb) and 3 (ge2gb).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from ._build import LIB, build  # noqa: F401
+
+__all__ = [
+    "bandred_opts", "make_opts", "lib", "PRECISIONS",
+    "bandred_sy2sb_workspace", "bandred_sy2sb_ex", "bandred_sy2sb",
+    "bandred_ge2gb_workspace", "bandred_ge2gb_ex", "bandred_ge2gb",
+    "bandred_status_string", "bandred_last_error", "sy2sb", "ge2gb", "BandredError",
+]
+
+PRECISIONS = {"fp64": 0, "bf16x3": 1, "bf16x6": 2, "ozaki": 3}
+
+
+class bandred_opts(ctypes.Structure):
+    _fields_ = [
+        ("b", ctypes.c_int),
+        ("lookahead", ctypes.c_int),
+        ("precision", ctypes.c_int),
+        ("slices", ctypes.c_int),
+        ("panel_ctas", ctypes.c_int),
+        ("timeout_ms", ctypes.c_int),
+        ("debug", ctypes.c_int),
+        ("reserved", ctypes.c_int * 9),
+    ]
+
+
+class BandredError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = f"{where}: {code} ({bandred_status_string(code)})"
+        if code == -1001 or code == -1004:
+            msg += f": {bandred_last_error()}"
+        super().__init__(msg)
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libbandred.so (raises when it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError(f"{LIB} is missing: build it with paper_1709_00302_gb300.build()")
+        L = ctypes.CDLL(LIB)
+        i64, vp, sz, ci = ctypes.c_int64, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int
+        op = ctypes.POINTER(bandred_opts)
+        L.bandred_default_opts.argtypes = [op]
+        L.bandred_default_opts.restype = None
+        L.bandred_status_string.argtypes = [ci]
+        L.bandred_status_string.restype = ctypes.c_char_p
+        L.bandred_last_error.argtypes = []
+        L.bandred_last_error.restype = ctypes.c_char_p
+        L.bandred_sy2sb_workspace.argtypes = [i64, i64, op]
+        L.bandred_sy2sb_workspace.restype = sz
+        L.bandred_sy2sb_ex.argtypes = [i64, i64, vp, i64, vp, op, vp, sz, vp, vp]
+        L.bandred_sy2sb_ex.restype = ci
+        L.bandred_sy2sb.argtypes = [i64, i64, vp, i64, vp, op, vp]
+        L.bandred_sy2sb.restype = ci
+        L.bandred_ge2gb_workspace.argtypes = [i64, i64, i64, op]
+        L.bandred_ge2gb_workspace.restype = sz
+        L.bandred_ge2gb_ex.argtypes = [i64, i64, i64, vp, i64, vp, vp, op, vp, sz, vp, vp]
+        L.bandred_ge2gb_ex.restype = ci
+        L.bandred_ge2gb.argtypes = [i64, i64, i64, vp, i64, vp, vp, op, vp]
+        L.bandred_ge2gb.restype = ci
+        _lib = L
+    return _lib
+
+
+def make_opts(b: int = 0, lookahead: int = -1, precision="fp64", slices: int = 0, panel_ctas: int = 0,
+              timeout_ms: int = 0, debug: int = 0) -> bandred_opts:
+    o = bandred_opts()
+    lib().bandred_default_opts(ctypes.byref(o))
+    o.b = b
+    o.lookahead = lookahead
+    o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    o.slices = slices
+    o.panel_ctas = panel_ctas
+    o.timeout_ms = timeout_ms
+    o.debug = debug
+    return o
+
+
+def bandred_status_string(code: int) -> str:
+    return lib().bandred_status_string(int(code)).decode()
+
+
+def bandred_last_error() -> str:
+    return lib().bandred_last_error().decode()
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _lda(A) -> int:
+    import torch
+
+    if A.dtype != torch.float64 or not A.is_cuda or A.dim() != 2:
+        raise TypeError("A must be a 2-D float64 CUDA tensor")
+    if A.shape[0] > 1 and A.stride(0) != 1:
+        raise ValueError("A must be column-major (A.stride(0) == 1)")
+    return max(A.stride(1), A.shape[0], 1)
+
+
+def _opts_ref(opts):
+    return None if opts is None else ctypes.byref(opts)
+
+
+# ------------------------------------------------------------------ raw C-ABI calls
+def bandred_sy2sb_workspace(n: int, w: int, opts: bandred_opts | None = None) -> int:
+    return lib().bandred_sy2sb_workspace(n, w, _opts_ref(opts))
+
+
+def bandred_sy2sb_ex(A, w: int, tau, opts, work, dev_status=None, stream=None) -> int:
+    n = A.shape[0]
+    return lib().bandred_sy2sb_ex(n, w, _ptr(A), _lda(A), _ptr(tau), _opts_ref(opts), _ptr(work),
+                                  work.numel() * work.element_size() if work is not None else 0,
+                                  _ptr(dev_status), _stream(stream))
+
+
+def bandred_sy2sb(A, w: int, tau, opts=None, stream=None) -> int:
+    return lib().bandred_sy2sb(A.shape[0], w, _ptr(A), _lda(A), _ptr(tau), _opts_ref(opts), _stream(stream))
+
+
+def bandred_ge2gb_workspace(m: int, n: int, w: int, opts: bandred_opts | None = None) -> int:
+    return lib().bandred_ge2gb_workspace(m, n, w, _opts_ref(opts))
+
+
+def bandred_ge2gb_ex(A, w: int, tauq, taup, opts, work, dev_status=None, stream=None) -> int:
+    m, n = A.shape
+    return lib().bandred_ge2gb_ex(m, n, w, _ptr(A), _lda(A), _ptr(tauq), _ptr(taup), _opts_ref(opts), _ptr(work),
+                                  work.numel() * work.element_size() if work is not None else 0,
+                                  _ptr(dev_status), _stream(stream))
+
+
+def bandred_ge2gb(A, w: int, tauq, taup, opts=None, stream=None) -> int:
+    m, n = A.shape
+    return lib().bandred_ge2gb(m, n, w, _ptr(A), _lda(A), _ptr(tauq), _ptr(taup), _opts_ref(opts), _stream(stream))
+
+
+# ------------------------------------------------------------------ conveniences
+def sy2sb(A, w: int, opts: bandred_opts | None = None, stream=None, check: bool = True):
+    """In-place symmetric band reduction of the column-major CUDA tensor A.
+
+    Returns (A, tau, dev_status) with tau on the device; raises BandredError on a
+    negative return code, and (when ``check``) synchronises to raise on a device status.
+    """
+    import torch
+
+    n = A.shape[0]
+    opts = make_opts() if opts is None else opts
+    tau = torch.zeros(max(n - w, 0), dtype=torch.float64, device=A.device)
+    work = torch.empty(max(bandred_sy2sb_workspace(n, w, opts), 256), dtype=torch.uint8, device=A.device)
+    status = torch.zeros(1, dtype=torch.int32, device=A.device)
+    rc = bandred_sy2sb_ex(A, w, tau, opts, work, status, stream)
+    if rc != 0:
+        raise BandredError(rc, "bandred_sy2sb_ex")
+    if check:
+        st = int(status.item())
+        if st != 0:
+            raise BandredError(st, "bandred_sy2sb_ex (device)")
+    return A, tau, status
+
+
+def ge2gb(A, w: int, opts: bandred_opts | None = None, stream=None, check: bool = True):
+    """In-place reduction of the column-major CUDA tensor A (m x n, m >= n) to upper
+    triangular band form.  Returns (A, tauq, taup, dev_status)."""
+    import torch
+
+    m, n = A.shape
+    opts = make_opts() if opts is None else opts
+    tauq = torch.zeros(n, dtype=torch.float64, device=A.device)
+    taup = torch.zeros(max(n - w, 0), dtype=torch.float64, device=A.device)
+    work = torch.empty(max(bandred_ge2gb_workspace(m, n, w, opts), 256), dtype=torch.uint8, device=A.device)
+    status = torch.zeros(1, dtype=torch.int32, device=A.device)
+    rc = bandred_ge2gb_ex(A, w, tauq, taup, opts, work, status, stream)
+    if rc != 0:
+        raise BandredError(rc, "bandred_ge2gb_ex")
+    if check:
+        st = int(status.item())
+        if st != 0:
+            raise BandredError(st, "bandred_ge2gb_ex (device)")
+    return A, tauq, taup, status

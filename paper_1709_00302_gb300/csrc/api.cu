@@ -1,0 +1,171 @@
+// The extern "C" entry points declared in include/bandred.h: argument validation
+// (LAPACK-style negative codes), workspace checks, device selection, and the allocating
+// short forms.  The computation itself is in driver.cu and the kernels.
+#include <cstdint>
+#include <cstring>
+
+#include "driver.h"
+
+using bandred::Options;
+
+namespace {
+
+// Makes the device that owns `ptr` current (the library may run beside other CUDA
+// runtimes in the same process, e.g. PyTorch's, which keep their own current device).
+bool select_device_of(const void* ptr) {
+  if (!ptr) return true;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return false;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != at.device && cudaSetDevice(at.device) != cudaSuccess) return false;
+  return true;
+}
+
+bool aligned(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 255u) == 0; }
+
+int sy2sb_check(int64_t n, int64_t w, const double* A, int64_t lda, const double* tau, const bandred_opts* opts,
+                Options* o) {
+  if (n < 0) return -1;
+  if (w < 1) return -2;
+  if (n > 0 && !A) return -3;
+  if (lda < (n > 1 ? n : 1)) return -4;
+  if (n - w > 0 && !tau) return -5;
+  if (n > INT32_MAX / 2) return BANDRED_ERR_UNSUPPORTED;
+  if (bandred::resolve_options(opts, w, o) != 0) return -6;
+  return 0;
+}
+
+int ge2gb_check(int64_t m, int64_t n, int64_t w, const double* A, int64_t lda, const double* tauq,
+                const double* taup, const bandred_opts* opts, Options* o) {
+  if (m < 0) return -1;
+  if (n < 0 || n > m) return -2;
+  if (w < 1) return -3;
+  if (n > 0 && !A) return -4;
+  if (lda < (m > 1 ? m : 1)) return -5;
+  if (n > 0 && !tauq) return -6;
+  if (n - w > 0 && !taup) return -7;
+  if (m > INT32_MAX / 2) return BANDRED_ERR_UNSUPPORTED;
+  if (bandred::resolve_options(opts, w, o) != 0) return -8;
+  return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+void bandred_default_opts(bandred_opts* opts) {
+  if (!opts) return;
+  std::memset(opts, 0, sizeof(*opts));
+  opts->b = 0;
+  opts->lookahead = -1;
+  opts->precision = BANDRED_FP64;
+  opts->slices = 0;
+}
+
+const char* bandred_status_string(int code) {
+  switch (code) {
+    case 0: return "success";
+    case BANDRED_DEV_TIMEOUT: return "device: a bounded wait timed out (results invalid)";
+    case BANDRED_DEV_INVARIANT: return "device: internal consistency check failed";
+    case BANDRED_ERR_CUDA: return "a CUDA runtime call failed";
+    case BANDRED_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    case BANDRED_ERR_UNSUPPORTED: return "size not supported by the kernels";
+    case BANDRED_ERR_ALLOC: return "workspace allocation failed";
+    default: break;
+  }
+  if (code < 0 && code > -100) return "invalid argument (-i = i-th argument)";
+  return "unknown status";
+}
+
+const char* bandred_last_error(void) { return bandred::last_cuda_error(); }
+
+size_t bandred_sy2sb_workspace(int64_t n, int64_t w, const bandred_opts* opts) {
+  Options o;
+  if (n < 0 || w < 1 || bandred::resolve_options(opts, w, &o) != 0) return 0;
+  return bandred::sy2sb_workspace_bytes(n, w, o);
+}
+
+int bandred_sy2sb_ex(int64_t n, int64_t w, double* A, int64_t lda, double* tau, const bandred_opts* opts,
+                     void* work, size_t work_bytes, int* dev_status, cudaStream_t stream) {
+  Options o;
+  int rc = sy2sb_check(n, w, A, lda, tau, opts, &o);
+  if (rc) return rc;
+  if (!select_device_of(A)) return -3;
+  if (!work || !aligned(work)) return -7;
+  if (work_bytes < bandred::sy2sb_workspace_bytes(n, w, o)) return -8;
+  return bandred::sy2sb_run(n, w, A, lda, tau, o, work, dev_status, stream);
+}
+
+int bandred_sy2sb(int64_t n, int64_t w, double* A, int64_t lda, double* tau, const bandred_opts* opts,
+                  cudaStream_t stream) {
+  Options o;
+  int rc = sy2sb_check(n, w, A, lda, tau, opts, &o);
+  if (rc) return rc;
+  if (!select_device_of(A)) return -3;
+  const size_t bytes = bandred::sy2sb_workspace_bytes(n, w, o);
+  void* work = nullptr;
+  if (cudaError_t e = cudaMallocAsync(&work, bytes, stream); e != cudaSuccess) {
+    bandred::record_cuda_error(e, "cudaMallocAsync");
+    return BANDRED_ERR_ALLOC;
+  }
+  rc = bandred::sy2sb_run(n, w, A, lda, tau, o, work, nullptr, stream);
+  int status = 0;
+  // The run wrote its status into the workspace (dev_status == nullptr).
+  if (rc == 0) {
+    // The status word is the last piece of the workspace.
+    const int* st = reinterpret_cast<const int*>(static_cast<char*>(work) + bytes - 256);
+    if (cudaMemcpyAsync(&status, st, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess)
+      rc = BANDRED_ERR_CUDA;
+  }
+  cudaFreeAsync(work, stream);
+  if (cudaStreamSynchronize(stream) != cudaSuccess) return BANDRED_ERR_CUDA;
+  return rc ? rc : status;
+}
+
+size_t bandred_ge2gb_workspace(int64_t m, int64_t n, int64_t w, const bandred_opts* opts) {
+  Options o;
+  if (m < 0 || n < 0 || n > m || w < 1 || bandred::resolve_options(opts, w, &o) != 0) return 0;
+  return bandred::ge2gb_workspace_bytes(m, n, w, o);
+}
+
+int bandred_ge2gb_ex(int64_t m, int64_t n, int64_t w, double* A, int64_t lda, double* tauq, double* taup,
+                     const bandred_opts* opts, void* work, size_t work_bytes, int* dev_status, cudaStream_t stream) {
+  Options o;
+  int rc = ge2gb_check(m, n, w, A, lda, tauq, taup, opts, &o);
+  if (rc) return rc;
+  if (!select_device_of(A)) return -4;
+  if (!work || !aligned(work)) return -9;
+  if (work_bytes < bandred::ge2gb_workspace_bytes(m, n, w, o)) return -10;
+  return bandred::ge2gb_run(m, n, w, A, lda, tauq, taup, o, work, dev_status, stream);
+}
+
+int bandred_ge2gb(int64_t m, int64_t n, int64_t w, double* A, int64_t lda, double* tauq, double* taup,
+                  const bandred_opts* opts, cudaStream_t stream) {
+  Options o;
+  int rc = ge2gb_check(m, n, w, A, lda, tauq, taup, opts, &o);
+  if (rc) return rc;
+  if (!select_device_of(A)) return -4;
+  const size_t bytes = bandred::ge2gb_workspace_bytes(m, n, w, o);
+  void* work = nullptr;
+  if (cudaError_t e = cudaMallocAsync(&work, bytes, stream); e != cudaSuccess) {
+    bandred::record_cuda_error(e, "cudaMallocAsync");
+    return BANDRED_ERR_ALLOC;
+  }
+  rc = bandred::ge2gb_run(m, n, w, A, lda, tauq, taup, o, work, nullptr, stream);
+  int status = 0;
+  if (rc == 0) {
+    const int* st = reinterpret_cast<const int*>(static_cast<char*>(work) + bytes - 256);
+    if (cudaMemcpyAsync(&status, st, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess)
+      rc = BANDRED_ERR_CUDA;
+  }
+  cudaFreeAsync(work, stream);
+  if (cudaStreamSynchronize(stream) != cudaSuccess) return BANDRED_ERR_CUDA;
+  return rc ? rc : status;
+}
+
+}  // extern "C"

@@ -1,0 +1,84 @@
+// Device helpers shared by the band-reduction kernels: bounded waits, reductions,
+// cache-bypassing loads and the workspace/status conventions.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/bandred.h"
+
+namespace bandred {
+
+// Counters used by the grid-wide barrier of a cooperative launch.  Zeroed by the host
+// (cudaMemsetAsync) before every launch that uses them.
+struct GridSync {
+  unsigned int count;   // arrivals, monotonically increasing within one launch
+  unsigned int abort;   // set by the first CTA whose wait timed out
+  unsigned int pad[30];
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void red_release_add(unsigned int* p, unsigned int v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid-wide barrier with a time limit.  Every CTA of the (co-resident, cooperative)
+// grid calls it with the same `generation` (1, 2, 3, ...).  `extra` extra arrivals are
+// awaited (0 in normal use; a positive value makes the wait unsatisfiable, which is how
+// the tests exercise the timeout path).  Returns false when the wait timed out or
+// another CTA aborted; the caller must then return without touching shared results.
+__device__ __forceinline__ bool grid_barrier(GridSync* gs, unsigned int generation, unsigned int extra,
+                                             int* status, unsigned long long limit_ns) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    __threadfence();
+    red_release_add(&gs->count, 1u);
+    const unsigned int target = generation * (gridDim.x + extra);
+    const unsigned long long t0 = global_ns();
+    unsigned int spins = 0;
+    while (true) {
+      if (ld_acquire_gpu(&gs->count) >= target) break;
+      if (ld_acquire_gpu(&gs->abort) != 0u) { ok = 0; break; }
+      if ((++spins & 63u) == 0u && global_ns() - t0 > limit_ns) {
+        atomicExch(&gs->abort, 1u);
+        if (status) atomicCAS(status, 0, BANDRED_DEV_TIMEOUT);
+        ok = 0;
+        break;
+      }
+      __nanosleep(20);
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Loads of data written by other CTAs during the same launch: skip L1.
+__device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
+
+}  // namespace bandred

@@ -1,0 +1,37 @@
+// Internal interface between the C ABI (api.cu) and the host-side loops (driver.cu).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/bandred.h"
+
+namespace bandred {
+
+struct Options {
+  int b;
+  int lookahead;
+  int precision;
+  int slices;
+  int panel_ctas;
+  unsigned long long limit_ns;
+  int debug;
+};
+
+// Records a failed CUDA call (readable through bandred_last_error) and returns
+// BANDRED_ERR_CUDA.
+int record_cuda_error(cudaError_t e, const char* what);
+const char* last_cuda_error();
+
+// Validates and completes the caller's options for bandwidth w; returns 0 or -1.
+int resolve_options(const bandred_opts* in, int64_t w, Options* o);
+
+size_t sy2sb_workspace_bytes(int64_t n, int64_t w, const Options& o);
+int sy2sb_run(int64_t n, int64_t w, double* A, int64_t lda, double* tau, const Options& o, void* work,
+              int* dev_status, cudaStream_t s);
+
+size_t ge2gb_workspace_bytes(int64_t m, int64_t n, int64_t w, const Options& o);
+int ge2gb_run(int64_t m, int64_t n, int64_t w, double* A, int64_t lda, double* tauq, double* taup,
+              const Options& o, void* work, int* dev_status, cudaStream_t s);
+
+}  // namespace bandred

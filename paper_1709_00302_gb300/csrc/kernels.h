@@ -1,0 +1,59 @@
+// Internal launch interface of the band-reduction kernels (not part of the C ABI).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace bandred {
+
+struct GridSync;
+
+// ---------------------------------------------------------------- panel (panel.cu)
+struct PanelParams {
+  double* A;             // panel element (r, c) at A[r * rs + c * cs]
+  int64_t rs, cs;
+  int j, bk;             // rows (length of reflector 0) and number of reflectors
+  int R, Rp;             // rows per CTA and the shared-memory stride (odd, >= R)
+  double* tau;           // bk outputs
+  double* Y;             // j x bk, column-major, ld = ldy (unit lower trapezoidal copy of V)
+  double* W;             // j x bk, column-major, ld = ldy (W = -Y T)
+  int64_t ldy;
+  double* part;          // 2 * G * (bk + 1) doubles
+  double* rowbuf;        // 2 * bk doubles
+  double* part2;         // G doubles
+  GridSync* gs;
+  int* status;
+  unsigned long long limit_ns;
+  unsigned int extra;    // extra awaited arrivals (tests of the timeout path)
+};
+
+size_t panel_smem_bytes(int bk, int Rp);
+int panel_geometry(int j, int bk, int max_ctas, int min_rows, int* G, int* R, int* Rp);
+cudaError_t launch_panel(const PanelParams& p, int G, cudaStream_t s);
+
+// ---------------------------------------------------------------- FP64 kernels (gemm_f64.cu)
+// A strided matrix view: element (i, k) at p[i * rs + k * cs].
+struct MatView {
+  const double* p;
+  int64_t rs, cs;
+};
+
+// C (M x N, column-major, ldc) = alpha * op(A) op(B) + beta * C, where op(A) is the M x K
+// view `a` and op(B) the K x N view `b`.  When splits > 1 the K range is cut into
+// `splits` pieces whose partial products go to `partial` (splits * M * N doubles) and
+// are summed in a fixed order by a second kernel.
+cudaError_t gemm_f64(int M, int N, int K, double alpha, MatView a, MatView b, double beta, double* C,
+                     int64_t ldc, int splits, double* partial, cudaStream_t s);
+
+// X (n x nb) = S W for symmetric S (n x n) of which only the lower triangle (column-major,
+// lds) is read, and W (n x nb, column-major, ldw).
+cudaError_t symm_lower_f64(int n, int nb, const double* S, int64_t lds, const double* W, int64_t ldw, double* X,
+                           int64_t ldx, cudaStream_t s);
+
+// Lower triangle of S (n x n) += X Y^T + Y X^T for X, Y (n x nb, column-major).  The
+// column range [col0, col1) of S is updated (used to split the update around the next
+// panel for look-ahead); rows run over the whole lower part of those columns.
+cudaError_t syr2k_lower_f64(int n, int nb, double* S, int64_t lds, const double* X, int64_t ldx, const double* Y,
+                            int64_t ldy, int col0, int col1, cudaStream_t s);
+
+}  // namespace bandred

@@ -1,0 +1,256 @@
+// Panel factorisation in FP64: Householder QR of a tall j x bk panel (Eq. updateA0 of
+// Section 2.1; Eq. updateB of Section 3.1) or, through transposed addressing, the LQ
+// factorisation of a wide bk x j row panel (Eq. updateC).  Produces, in one cooperative
+// launch:
+//   - the reflectors in the packed LAPACK layout (beta on the diagonal, v below it,
+//     tau[0..bk)),
+//   - Y: a contiguous copy of V with its unit diagonal and zeros above (j x bk),
+//   - W = -Y T (j x bk), so that the panel's orthogonal factor is Q = I + W Y^T with the
+//     compact-WY triangular factor T of the paper's reference implementation (Section 4.1).
+//
+// Design (one GPU, FP64 on the CUDA cores):
+//   Each CTA keeps a contiguous slab of the panel's rows in shared memory.  For reflector
+//   i the CTAs compute, over their rows below row i, the dot products of column i with
+//   every panel column (column i itself gives ||x2||^2; earlier columns give the entries
+//   Y^T y_i needed for T; later columns give v^T a_c for the in-panel update), publish
+//   them together with row i, and meet at one grid-wide barrier.  After it every CTA
+//   sums the published partials in the same fixed order, so all of them derive the same
+//   beta, tau and coefficients and update their own rows without further communication.
+//   W's column i follows from the recurrence W(:, i) = -tau_i (y_i + W(:, 0:i) Y(:, 0:i)^T y_i),
+//   which equals -Y T with T built column by column as in the compact-WY definition.
+#include <cmath>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace bandred {
+
+namespace {
+
+constexpr int kPanelThreads = 256;
+
+__global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams p) {
+  extern __shared__ double smem[];
+  constexpr int NT = kPanelThreads;
+  constexpr int NW = NT / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int G = gridDim.x, g = blockIdx.x;
+  const int bk = p.bk, Rp = p.Rp;
+  const int rb = g * p.R;
+  const int nr = max(0, min(p.R, p.j - rb));
+  double* slab = smem;                        // bk columns x Rp rows
+  double* dsum = slab + (size_t)bk * Rp;      // bk + 1 combined sums
+  double* rowi = dsum + bk + 1;               // row i of the panel
+  double* coef = rowi + bk;                   // z_c (c > i) and Y^T y_i (p < i)
+  __shared__ double s_beta, s_tau, s_scal, s_xnorm;
+  __shared__ double s_red[NW];
+  __shared__ int s_rescale;
+
+  if (p.rs == 1) {
+    for (int idx = tid; idx < nr * bk; idx += NT) {
+      const int r = idx % nr, c = idx / nr;
+      slab[(size_t)c * Rp + r] = p.A[(int64_t)(rb + r) + (int64_t)c * p.cs];
+    }
+  } else {
+    for (int idx = tid; idx < nr * bk; idx += NT) {
+      const int c = idx % bk, r = idx / bk;
+      slab[(size_t)c * Rp + r] = p.A[(int64_t)(rb + r) * p.rs + (int64_t)c * p.cs];
+    }
+  }
+  __syncthreads();
+
+  unsigned int gen = 0;
+  const size_t pstride = (size_t)bk + 1;
+  for (int i = 0; i < bk; ++i) {
+    const int buf = i & 1;
+    double* part = p.part + (size_t)buf * G * pstride;
+    double* rowg = p.rowbuf + (size_t)buf * bk;
+    const int lo = min(max(i + 1 - rb, 0), nr);
+    const double* xi = slab + (size_t)i * Rp;
+    const bool own_row = (i >= rb) && (i < rb + nr);
+
+    // Partial dot products of x2 = column i below row i with every panel column.
+    for (int c = warp; c < bk; c += NW) {
+      const double* ac = slab + (size_t)c * Rp;
+      double s = 0.0, m = 0.0;
+      for (int r = lo + lane; r < nr; r += 32) {
+        const double x = xi[r];
+        s = fma(x, ac[r], s);
+        m = fmax(m, fabs(x));
+      }
+      s = warp_sum(s);
+      if (lane == 0) __stcg(&part[(size_t)g * pstride + c], s);
+      if (c == i) {
+        m = warp_max(m);
+        if (lane == 0) __stcg(&part[(size_t)g * pstride + bk], m);
+      }
+    }
+    if (own_row)
+      for (int c = tid; c < bk; c += NT) __stcg(&rowg[c], slab[(size_t)c * Rp + (i - rb)]);
+
+    if (!grid_barrier(p.gs, ++gen, p.extra, p.status, p.limit_ns)) return;
+
+    // Combine in a fixed order: every CTA obtains bit-identical sums.
+    for (int v = warp; v <= bk; v += NW) {
+      double s = 0.0;
+      if (v < bk) {
+        for (int q = lane; q < G; q += 32) s += ldcg(&part[(size_t)q * pstride + v]);
+        s = warp_sum(s);
+      } else {
+        for (int q = lane; q < G; q += 32) s = fmax(s, ldcg(&part[(size_t)q * pstride + v]));
+        s = warp_max(s);
+      }
+      if (lane == 0) dsum[v] = s;
+    }
+    for (int c = tid; c < bk; c += NT) rowi[c] = ldcg(&rowg[c]);
+    __syncthreads();
+
+    // ||x2||: plain sum of squares unless it over/underflows; then a scaled second pass.
+    if (tid == 0) {
+      const double ssq = dsum[i], amax = dsum[bk];
+      s_rescale = (p.j - i > 1) && (amax > 0.0) && !(ssq < 0x1p1000 && amax > 0x1p-450);
+      s_xnorm = sqrt(ssq);
+    }
+    __syncthreads();
+    if (s_rescale) {  // same decision in every CTA: the inputs of the test are identical
+      const double inv = 1.0 / dsum[bk];
+      double s = 0.0;
+      for (int r = lo + tid; r < nr; r += NT) {
+        const double t = xi[r] * inv;
+        s = fma(t, t, s);
+      }
+      s = warp_sum(s);
+      if (lane == 0) s_red[warp] = s;
+      __syncthreads();
+      if (tid == 0) {
+        double t = 0.0;
+        for (int q = 0; q < NW; ++q) t += s_red[q];
+        __stcg(&p.part2[g], t);
+      }
+      if (!grid_barrier(p.gs, ++gen, p.extra, p.status, p.limit_ns)) return;
+      if (warp == 0) {
+        double t = 0.0;
+        for (int q = lane; q < G; q += 32) t += ldcg(&p.part2[q]);
+        t = warp_sum(t);
+        if (lane == 0) s_xnorm = dsum[bk] * sqrt(t);
+      }
+      __syncthreads();
+    }
+
+    // Reflector (larfg convention).
+    if (tid == 0) {
+      const double alpha = rowi[i];
+      const double xnorm = s_xnorm;
+      double tau = 0.0, beta = alpha, scal = 1.0;
+      if (p.j - i > 1 && xnorm != 0.0) {
+        const double h = hypot(alpha, xnorm);
+        beta = (alpha >= 0.0) ? -h : h;
+        tau = (beta - alpha) / beta;
+        scal = 1.0 / (alpha - beta);
+      }
+      s_beta = beta;
+      s_tau = tau;
+      s_scal = scal;
+      if (g == 0) p.tau[i] = tau;
+    }
+    __syncthreads();
+    const double tau = s_tau, scal = s_scal;
+    for (int c = tid; c < bk; c += NT) {
+      if (c > i) coef[c] = tau * (rowi[c] + scal * dsum[c]);  // tau * v^T a_c
+      else if (c < i) coef[c] = rowi[c] + scal * dsum[c];     // (Y^T y_i)_c
+    }
+    __syncthreads();
+
+    // In-panel update of the columns right of i, then scale x2 into v.
+    if (tau != 0.0) {
+      const int nrow = nr - lo, ncol = bk - i - 1;
+      for (int idx = tid; idx < nrow * ncol; idx += NT) {
+        const int r = lo + idx % nrow, c = i + 1 + idx / nrow;
+        slab[(size_t)c * Rp + r] = fma(-coef[c] * scal, xi[r], slab[(size_t)c * Rp + r]);
+      }
+      if (own_row)
+        for (int c = i + 1 + tid; c < bk; c += NT) slab[(size_t)c * Rp + (i - rb)] -= coef[c];
+      __syncthreads();
+      for (int r = lo + tid; r < nr; r += NT) slab[(size_t)i * Rp + r] *= scal;
+    }
+    if (own_row && tid == 0) slab[(size_t)i * Rp + (i - rb)] = s_beta;
+    __syncthreads();
+
+    // W(:, i) = -tau (y_i + W(:, 0:i) (Y^T y_i)) for this CTA's rows.
+    for (int r = tid; r < nr; r += NT) {
+      const int gr = rb + r;
+      double s = gr > i ? slab[(size_t)i * Rp + r] : (gr == i ? 1.0 : 0.0);
+      for (int q = 0; q < i; ++q) s = fma(p.W[gr + (int64_t)q * p.ldy], coef[q], s);
+      p.W[gr + (int64_t)i * p.ldy] = -tau * s;
+    }
+    __syncthreads();
+  }
+
+  // Write back: packed reflectors/R into the matrix, Y into the workspace.
+  if (p.rs == 1) {
+    for (int idx = tid; idx < nr * bk; idx += NT) {
+      const int r = idx % nr, c = idx / nr;
+      const double v = slab[(size_t)c * Rp + r];
+      p.A[(int64_t)(rb + r) + (int64_t)c * p.cs] = v;
+      const int gr = rb + r;
+      p.Y[gr + (int64_t)c * p.ldy] = gr > c ? v : (gr == c ? 1.0 : 0.0);
+    }
+  } else {
+    for (int idx = tid; idx < nr * bk; idx += NT) {
+      const int c = idx % bk, r = idx / bk;
+      p.A[(int64_t)(rb + r) * p.rs + (int64_t)c * p.cs] = slab[(size_t)c * Rp + r];
+    }
+    for (int idx = tid; idx < nr * bk; idx += NT) {
+      const int r = idx % nr, c = idx / nr;
+      const int gr = rb + r;
+      p.Y[gr + (int64_t)c * p.ldy] = gr > c ? slab[(size_t)c * Rp + r] : (gr == c ? 1.0 : 0.0);
+    }
+  }
+}
+
+}  // namespace
+
+size_t panel_smem_bytes(int bk, int Rp) { return ((size_t)bk * Rp + 3 * (size_t)bk + 1) * sizeof(double); }
+
+int panel_geometry(int j, int bk, int max_ctas, int min_rows, int* G, int* R, int* Rp) {
+  if (j <= 0 || bk <= 0) return -1;
+  int g = (j + min_rows - 1) / min_rows;
+  if (g > max_ctas) g = max_ctas;
+  if (g < 1) g = 1;
+  int r = (j + g - 1) / g;
+  g = (j + r - 1) / r;  // every CTA owns at least one row
+  int rp = r | 1;       // odd stride: conflict-free strided shared-memory access
+  if (panel_smem_bytes(bk, rp) > 227 * 1024) return -2;
+  *G = g;
+  *R = r;
+  *Rp = rp;
+  return 0;
+}
+
+cudaError_t launch_panel(const PanelParams& prm, int G, cudaStream_t s) {
+  static int configured_device = -1;
+  static size_t max_dynamic = 0;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (configured_device != dev) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, panel_qr_kernel);
+    if (e != cudaSuccess) return e;
+    int optin = 0;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    max_dynamic = (size_t)optin - fa.sharedSizeBytes;
+    e = cudaFuncSetAttribute(panel_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_dynamic);
+    if (e != cudaSuccess) return e;
+    configured_device = dev;
+  }
+  const size_t smem = panel_smem_bytes(prm.bk, prm.Rp);
+  if (smem > max_dynamic) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(prm.gs, 0, sizeof(GridSync), s);
+  if (e != cudaSuccess) return e;
+  PanelParams p = prm;
+  void* args[] = {&p};
+  return cudaLaunchCooperativeKernel((const void*)panel_qr_kernel, dim3(G), dim3(kPanelThreads), args, smem, s);
+}
+
+}  // namespace bandred

@@ -1,0 +1,78 @@
+"""The C-ABI library builds, loads and exports every entry point of include/bandred.h
+(CPU only: no call here launches device work)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    hdr = open(os.path.join(ROOT, "include", "bandred.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    return sorted(set(re.findall(r"\b(bandred_[a-z0-9_]+)\s*\(", hdr)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    import paper_1709_00302_gb300 as br
+
+    br.build()
+    return br.lib()
+
+
+def test_every_declared_symbol_is_exported(L):
+    syms = declared_symbols()
+    assert len(syms) >= 9
+    for s in syms:
+        assert hasattr(L, s), s
+
+
+def test_default_opts_and_status_strings(L):
+    import paper_1709_00302_gb300 as br
+
+    o = br.bandred_opts()
+    L.bandred_default_opts(ctypes.byref(o))
+    assert o.b == 0 and o.lookahead == -1 and o.precision == 0 and o.debug == 0
+    assert all(r == 0 for r in o.reserved)
+    assert br.bandred_status_string(0) == "success"
+    assert "timed out" in br.bandred_status_string(1)
+    assert "argument" in br.bandred_status_string(-3)
+
+
+def test_invalid_arguments_are_rejected_before_any_device_work(L):
+    i64 = ctypes.c_int64
+    null = ctypes.c_void_p(0)
+    # sy2sb: n < 0, w < 1, A missing, lda < n, tau missing
+    assert L.bandred_sy2sb_ex(-1, 4, null, 1, null, None, null, 0, null, null) == -1
+    assert L.bandred_sy2sb_ex(10, 0, null, 10, null, None, null, 0, null, null) == -2
+    assert L.bandred_sy2sb_ex(10, 4, null, 10, null, None, null, 0, null, null) == -3
+    fake = ctypes.c_void_p(4096)
+    assert L.bandred_sy2sb_ex(10, 4, fake, 9, fake, None, null, 0, null, null) == -4
+    assert L.bandred_sy2sb_ex(10, 4, fake, 10, null, None, null, 0, null, null) == -5
+    import paper_1709_00302_gb300 as br
+
+    bad = br.bandred_opts()
+    L.bandred_default_opts(ctypes.byref(bad))
+    bad.b = 5  # b > w
+    assert L.bandred_sy2sb_ex(10, 4, fake, 10, fake, ctypes.byref(bad), null, 0, null, null) == -6
+    bad.b = 2
+    bad.reserved[3] = 1
+    assert L.bandred_sy2sb_ex(10, 4, fake, 10, fake, ctypes.byref(bad), null, 0, null, null) == -6
+    # ge2gb: n > m, w < 1, lda < m
+    assert L.bandred_ge2gb_ex(4, 5, 1, fake, 4, fake, fake, None, null, 0, null, null) == -2
+    assert L.bandred_ge2gb_ex(6, 5, 0, fake, 6, fake, fake, None, null, 0, null, null) == -3
+    assert L.bandred_ge2gb_ex(6, 5, 1, fake, 5, fake, fake, None, null, 0, null, null) == -5
+    assert L.bandred_ge2gb_ex(6, 5, 1, fake, 6, null, fake, None, null, 0, null, null) == -6
+    assert L.bandred_ge2gb_ex(6, 5, 1, fake, 6, fake, null, None, null, 0, null, null) == -7
+
+
+def test_product_path_does_not_import_the_oracle():
+    import subprocess
+    import sys
+
+    code = ("import sys; import paper_1709_00302_gb300 as br; br.lib(); "
+            "assert 'oracle' not in sys.modules, 'oracle imported by the product path'")
+    subprocess.run([sys.executable, "-c", code], check=True, cwd=ROOT)
