@@ -141,6 +141,29 @@ int bandred_ge2gb_ex(int64_t m, int64_t n, int64_t w, double* A, int64_t lda, do
                      double* taup, const bandred_opts* opts, void* work, size_t work_bytes,
                      int* dev_status, cudaStream_t stream);
 
+/* ---------------------------------------------------------------- tracing -----------
+ * Per-kernel-class timing.  Between bandred_profile_begin() and bandred_profile_end()
+ * every kernel group the library launches is bracketed by a pair of CUDA events on its
+ * stream.  bandred_profile_end synchronises those events and writes one entry per kernel
+ * class that ran (at most max_entries): launches, summed event time, and the algorithmic
+ * flops and HBM bytes of those launches (the counts of the method, not of the hardware).
+ * Returns the number of entries written or a negative code.  Host-side, not thread-safe
+ * with concurrent calls on other threads.
+ */
+typedef struct bandred_kernel_stat {
+    char name[32];
+    long long launches;
+    double ms;
+    double flops;
+    double bytes;
+} bandred_kernel_stat;
+
+int bandred_profile_begin(void);
+int bandred_profile_end(bandred_kernel_stat* out, int max_entries);
+
+/* Number of kernel launches the library has issued since it was loaded. */
+long long bandred_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

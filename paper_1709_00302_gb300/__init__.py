@@ -24,7 +24,8 @@ __all__ = [
     "bandred_opts", "make_opts", "lib", "PRECISIONS",
     "bandred_sy2sb_workspace", "bandred_sy2sb_ex", "bandred_sy2sb",
     "bandred_ge2gb_workspace", "bandred_ge2gb_ex", "bandred_ge2gb",
-    "bandred_status_string", "bandred_last_error", "sy2sb", "ge2gb", "BandredError",
+    "bandred_status_string", "bandred_last_error", "bandred_profile_begin", "bandred_profile_end",
+    "bandred_launch_count", "bandred_kernel_stat", "sy2sb", "ge2gb", "BandredError",
 ]
 
 PRECISIONS = {"fp64": 0, "bf16x3": 1, "bf16x6": 2, "ozaki": 3}
@@ -40,6 +41,16 @@ class bandred_opts(ctypes.Structure):
         ("timeout_ms", ctypes.c_int),
         ("debug", ctypes.c_int),
         ("reserved", ctypes.c_int * 9),
+    ]
+
+
+class bandred_kernel_stat(ctypes.Structure):
+    _fields_ = [
+        ("name", ctypes.c_char * 32),
+        ("launches", ctypes.c_longlong),
+        ("ms", ctypes.c_double),
+        ("flops", ctypes.c_double),
+        ("bytes", ctypes.c_double),
     ]
 
 
@@ -82,6 +93,12 @@ def lib():
         L.bandred_ge2gb_ex.restype = ci
         L.bandred_ge2gb.argtypes = [i64, i64, i64, vp, i64, vp, vp, op, vp]
         L.bandred_ge2gb.restype = ci
+        L.bandred_profile_begin.argtypes = []
+        L.bandred_profile_begin.restype = ci
+        L.bandred_profile_end.argtypes = [ctypes.POINTER(bandred_kernel_stat), ci]
+        L.bandred_profile_end.restype = ci
+        L.bandred_launch_count.argtypes = []
+        L.bandred_launch_count.restype = ctypes.c_longlong
         _lib = L
     return _lib
 
@@ -163,6 +180,24 @@ def bandred_ge2gb_ex(A, w: int, tauq, taup, opts, work, dev_status=None, stream=
 def bandred_ge2gb(A, w: int, tauq, taup, opts=None, stream=None) -> int:
     m, n = A.shape
     return lib().bandred_ge2gb(m, n, w, _ptr(A), _lda(A), _ptr(tauq), _ptr(taup), _opts_ref(opts), _stream(stream))
+
+
+def bandred_profile_begin() -> int:
+    return lib().bandred_profile_begin()
+
+
+def bandred_profile_end(max_entries: int = 16) -> list:
+    """Per-kernel-class stats since bandred_profile_begin(): list of dicts."""
+    arr = (bandred_kernel_stat * max_entries)()
+    n = lib().bandred_profile_end(arr, max_entries)
+    if n < 0:
+        raise BandredError(n, "bandred_profile_end")
+    return [{"name": arr[i].name.decode(), "launches": arr[i].launches, "ms": arr[i].ms,
+             "flops": arr[i].flops, "bytes": arr[i].bytes} for i in range(n)]
+
+
+def bandred_launch_count() -> int:
+    return lib().bandred_launch_count()
 
 
 # ------------------------------------------------------------------ conveniences

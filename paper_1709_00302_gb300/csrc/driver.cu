@@ -11,6 +11,7 @@
 #include "common.cuh"
 #include "driver.h"
 #include "kernels.h"
+#include "prof.h"
 
 namespace bandred {
 
@@ -61,6 +62,21 @@ int choose_splits(int M, int N, int K, size_t capacity_doubles, int sms) {
   s = std::min(s, std::max(1, K / 256));
   while (s > 1 && (size_t)s * M * N > capacity_doubles) --s;
   return s;
+}
+
+// Algorithmic flop and HBM-byte counts attributed to each kernel class by the profiler.
+// Householder QR of a j x bk panel (2 j bk^2) plus the W = -Y T build (j bk^2); the panel
+// is read and written once and Y, W are written once.
+double panel_flops(double j, double bk) { return 3.0 * j * bk * bk; }
+double panel_bytes(double j, double bk) { return 8.0 * 4.0 * j * bk; }
+// X1 = A2 W over the lower triangle of A2 (read once) with W read and X1 written once.
+double symm_flops(double j, double bk) { return 2.0 * j * j * bk; }
+double symm_bytes(double j, double bk) { return 8.0 * (j * (j + 1) / 2 + 2.0 * j * bk); }
+// A2 += X3 Y^T + Y X3^T on the lower triangle of columns [c0, c1) (read and written once).
+double lower_entries(double j, double c0, double c1) { return (c1 - c0) * j - (c1 * (c1 - 1) - c0 * (c0 - 1)) / 2; }
+double syr2k_flops(double j, double c0, double c1, double bk) { return 4.0 * bk * lower_entries(j, c0, c1); }
+double syr2k_bytes(double j, double c0, double c1, double bk) {
+  return 8.0 * (2.0 * lower_entries(j, c0, c1) + 2.0 * j * bk);
 }
 
 }  // namespace
@@ -225,23 +241,37 @@ int sy2sb_run(int64_t n, int64_t w, double* A, int64_t lda, double* tau, const O
     const int bk = (int)std::min<int64_t>(b, n - w - 1 - k);
     const int64_t r0 = k + w;
     const int j = (int)(n - r0);
-    int rc = run_panel(A + r0 + k * lda, 1, lda, j, bk, tau + k, ws.Y, ws.W, ld, ws.part, ws.rowbuf, ws.part2,
-                       ws.gs, status, o, pmax, extra, s);
+    int rc;
+    {
+      prof::Scope sc(prof::kPanel, s, panel_flops(j, bk), panel_bytes(j, bk));
+      rc = run_panel(A + r0 + k * lda, 1, lda, j, bk, tau + k, ws.Y, ws.W, ld, ws.part, ws.rowbuf, ws.part2, ws.gs,
+                     status, o, pmax, extra, s);
+    }
     if (rc) return rc;
     extra = 0;
     const int na1 = (int)(w - bk);
     if (na1 > 0) {
       double* A1 = A + r0 + (k + bk) * lda;
       const int sp = choose_splits(bk, na1, j, ws.splitk_cap, sms);
+      prof::Scope sc(prof::kGemm, s, 4.0 * j * na1 * bk, 8.0 * (2.0 * j * na1 + 2.0 * j * bk));
       CK(gemm_f64(bk, na1, j, 1.0, MatView{ws.W, ld, 1}, MatView{A1, 1, lda}, 0.0, ws.Z, bk, sp, ws.splitk, s));
       CK(gemm_f64(j, na1, bk, 1.0, MatView{ws.Y, 1, ld}, MatView{ws.Z, 1, bk}, 1.0, A1, lda, 1, nullptr, s));
     }
     double* A2 = A + r0 + r0 * lda;
-    CK(symm_lower_f64(j, bk, A2, lda, ws.W, ld, ws.X, ld, s));
-    const int sp = choose_splits(bk, bk, j, ws.splitk_cap, sms);
-    CK(gemm_f64(bk, bk, j, 0.5, MatView{ws.X, ld, 1}, MatView{ws.W, 1, ld}, 0.0, ws.X2, bk, sp, ws.splitk, s));
-    CK(gemm_f64(j, bk, bk, 1.0, MatView{ws.Y, 1, ld}, MatView{ws.X2, 1, bk}, 1.0, ws.X, ld, 1, nullptr, s));
-    CK(syr2k_lower_f64(j, bk, A2, lda, ws.X, ld, ws.Y, ld, 0, j, s));
+    {
+      prof::Scope sc(prof::kSymm, s, symm_flops(j, bk), symm_bytes(j, bk));
+      CK(symm_lower_f64(j, bk, A2, lda, ws.W, ld, ws.X, ld, s));
+    }
+    {
+      prof::Scope sc(prof::kGemm, s, 4.0 * j * bk * bk, 8.0 * 4.0 * j * bk);
+      const int sp = choose_splits(bk, bk, j, ws.splitk_cap, sms);
+      CK(gemm_f64(bk, bk, j, 0.5, MatView{ws.X, ld, 1}, MatView{ws.W, 1, ld}, 0.0, ws.X2, bk, sp, ws.splitk, s));
+      CK(gemm_f64(j, bk, bk, 1.0, MatView{ws.Y, 1, ld}, MatView{ws.X2, 1, bk}, 1.0, ws.X, ld, 1, nullptr, s));
+    }
+    {
+      prof::Scope sc(prof::kSyr2k, s, syr2k_flops(j, 0, j, bk), syr2k_bytes(j, 0, j, bk));
+      CK(syr2k_lower_f64(j, bk, A2, lda, ws.X, ld, ws.Y, ld, 0, j, s));
+    }
   }
   return 0;
 }
@@ -269,14 +299,19 @@ int ge2gb_run(int64_t m, int64_t n, int64_t w, double* A, int64_t lda, double* t
   for (int64_t k = 0; k < n; k += b) {
     const int bk = (int)std::min<int64_t>(b, n - k);
     const int j = (int)(m - k);
-    int rc = run_panel(A + k + k * lda, 1, lda, j, bk, tauq + k, ws.Yu, ws.Wu, ws.ldu, ws.part, ws.rowbuf,
-                       ws.part2, ws.gs, status, o, pmax, extra, s);
+    int rc;
+    {
+      prof::Scope sc(prof::kPanel, s, panel_flops(j, bk), panel_bytes(j, bk));
+      rc = run_panel(A + k + k * lda, 1, lda, j, bk, tauq + k, ws.Yu, ws.Wu, ws.ldu, ws.part, ws.rowbuf, ws.part2,
+                     ws.gs, status, o, pmax, extra, s);
+    }
     if (rc) return rc;
     extra = 0;
     const int ncol = (int)(n - k - bk);
     if (ncol > 0) {
       double* E = A + k + (k + bk) * lda;
       const int sp = choose_splits(bk, ncol, j, ws.splitk_cap, sms);
+      prof::Scope sc(prof::kGemm, s, 4.0 * j * ncol * bk, 8.0 * (2.0 * j * ncol + 2.0 * j * bk));
       CK(gemm_f64(bk, ncol, j, 1.0, MatView{ws.Wu, ws.ldu, 1}, MatView{E, 1, lda}, 0.0, ws.Z, bk, sp, ws.splitk,
                   s));
       CK(gemm_f64(j, ncol, bk, 1.0, MatView{ws.Yu, 1, ws.ldu}, MatView{ws.Z, 1, bk}, 1.0, E, lda, 1, nullptr, s));
@@ -284,13 +319,17 @@ int ge2gb_run(int64_t m, int64_t n, int64_t w, double* A, int64_t lda, double* t
     const int64_t bkr = std::min<int64_t>(bk, n - w - 1 - k);
     if (bkr > 0) {
       const int jr = (int)(n - k - w);
-      rc = run_panel(A + k + (k + w) * lda, lda, 1, jr, (int)bkr, taup + k, ws.Yv, ws.Wv, ws.ldv, ws.part,
-                     ws.rowbuf, ws.part2, ws.gs, status, o, pmax, 0u, s);
+      {
+        prof::Scope sc(prof::kPanel, s, panel_flops(jr, (int)bkr), panel_bytes(jr, (int)bkr));
+        rc = run_panel(A + k + (k + w) * lda, lda, 1, jr, (int)bkr, taup + k, ws.Yv, ws.Wv, ws.ldv, ws.part,
+                       ws.rowbuf, ws.part2, ws.gs, status, o, pmax, 0u, s);
+      }
       if (rc) return rc;
       const int nrow = (int)(m - k - bkr);
       if (nrow > 0) {
         double* D = A + (k + bkr) + (k + w) * lda;
         const int sp = choose_splits(nrow, (int)bkr, jr, ws.splitk_cap, sms);
+        prof::Scope sc(prof::kGemm, s, 4.0 * nrow * jr * bkr, 8.0 * (2.0 * nrow * jr + 2.0 * nrow * bkr));
         CK(gemm_f64(nrow, (int)bkr, jr, 1.0, MatView{D, 1, lda}, MatView{ws.Wv, 1, ws.ldv}, 0.0, ws.P, ws.ldu, sp,
                     ws.splitk, s));
         CK(gemm_f64(nrow, jr, (int)bkr, 1.0, MatView{ws.P, 1, ws.ldu}, MatView{ws.Yv, ws.ldv, 1}, 1.0, D, lda, 1,

@@ -11,6 +11,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "prof.h"
 
 namespace bandred {
 
@@ -259,14 +260,17 @@ cudaError_t gemm_f64(int M, int N, int K, double alpha, MatView a, MatView b, do
   dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN, splits);
   if (splits == 1) {
     gemm_kernel<<<grid, NT, 0, s>>>(M, N, K, alpha, la, lb, beta, C, ldc, kchunk, nullptr);
+    prof::count_launch();
     return cudaGetLastError();
   }
   gemm_kernel<<<grid, NT, 0, s>>>(M, N, K, alpha, la, lb, beta, C, ldc, kchunk, partial);
+  prof::count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int64_t total = (int64_t)M * N;
   const int blocks = (int)std::min<int64_t>((total + 255) / 256, 1184);
   splitk_reduce_kernel<<<blocks, 256, 0, s>>>(M, N, splits, alpha, partial, beta, C, ldc);
+  prof::count_launch();
   return cudaGetLastError();
 }
 
@@ -277,6 +281,7 @@ cudaError_t symm_lower_f64(int n, int nb, const double* S, int64_t lds, const do
   ViewB lb{W, 1, ldw, n, nb};
   dim3 grid((n + BM - 1) / BM, (nb + BN - 1) / BN);
   symm_kernel<<<grid, NT, 0, s>>>(n, nb, la, lb, X, ldx);
+  prof::count_launch();
   return cudaGetLastError();
 }
 
@@ -290,6 +295,7 @@ cudaError_t syr2k_lower_f64(int n, int nb, double* S, int64_t lds, const double*
   const int tj0 = col0 / BN, tj1 = (col1 - 1) / BN;
   dim3 grid(T, tj1 - tj0 + 1);
   syr2k_kernel<<<grid, NT, 0, s>>>(n, nb, S, lds, la, lb, tj0, col0, col1);
+  prof::count_launch();
   return cudaGetLastError();
 }
 

@@ -22,6 +22,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "prof.h"
 
 namespace bandred {
 
@@ -250,6 +251,7 @@ cudaError_t launch_panel(const PanelParams& prm, int G, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   PanelParams p = prm;
   void* args[] = {&p};
+  prof::count_launch();
   return cudaLaunchCooperativeKernel((const void*)panel_qr_kernel, dim3(G), dim3(kPanelThreads), args, smem, s);
 }
 

@@ -1,0 +1,30 @@
+// Per-kernel-class timing with CUDA events (enabled between bandred_profile_begin and
+// bandred_profile_end) and a count of every kernel launch the library issues.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace bandred {
+namespace prof {
+
+enum Kind { kPanel = 0, kSymm, kSyr2k, kGemm, kSplitReduce, kConvert, kOther, kNumKinds };
+
+const char* kind_name(int k);
+void count_launch(int n = 1);
+long long launches();
+
+// Records an event pair around the launches issued while it lives (when profiling is on)
+// and attributes the given algorithmic flops and HBM bytes to `kind`.
+class Scope {
+ public:
+  Scope(Kind kind, cudaStream_t s, double flops, double bytes);
+  ~Scope();
+  Scope(const Scope&) = delete;
+  Scope& operator=(const Scope&) = delete;
+
+ private:
+  int slot_ = -1;
+  cudaStream_t s_;
+};
+
+}  // namespace prof
+}  // namespace bandred
