@@ -80,6 +80,8 @@ typedef struct bandred_opts {
 #define BANDRED_ERR_WORKSPACE (-1002)  /* workspace NULL, misaligned or too small */
 #define BANDRED_ERR_UNSUPPORTED (-1003)/* a size beyond what the kernels support */
 #define BANDRED_ERR_ALLOC (-1004)      /* the allocating short form could not allocate */
+#define BANDRED_ERR_SCRATCH (-1005)    /* bandred_sy2sb_noalloc: the problem needs more than
+                                          the fixed scratch (BANDRED_NOALLOC_SCRATCH_BYTES) */
 
 /* Fill *opts with the defaults (b = min(w, 64), auto look-ahead, FP64). */
 void bandred_default_opts(bandred_opts* opts);
@@ -118,6 +120,29 @@ int bandred_sy2sb(int64_t n, int64_t w, double* A, int64_t lda, double* tau,
 int bandred_sy2sb_ex(int64_t n, int64_t w, double* A, int64_t lda, double* tau,
                      const bandred_opts* opts, void* work, size_t work_bytes, int* dev_status,
                      cudaStream_t stream);
+
+/* Non-allocating variant for callers that may not allocate device memory when they
+ * call: code inside a stream capture, hosts with a fixed memory budget, plug-ins that
+ * do not own the process's allocator.  The paper has no counterpart; this is a
+ * deployment convenience.  It computes exactly what bandred_sy2sb_ex computes, with the
+ * same arguments minus the workspace: the workspace is a fixed device array of
+ * BANDRED_NOALLOC_SCRATCH_BYTES bytes that the library declares at file scope, reserved
+ * on every GPU that loads the library until the process exits.  No call allocates or
+ * frees memory.
+ *   - Limit: the problem must satisfy bandred_sy2sb_workspace(n, w, opts) <=
+ *     BANDRED_NOALLOC_SCRATCH_BYTES (about n <= 8000 at w = b = 64); larger problems
+ *     return BANDRED_ERR_SCRATCH before any device work.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call before any
+ *     stream capture that includes this entry point.
+ *   - All calls on a device share the one array, and it keeps the previous call's
+ *     contents.  Each call zeroes the counters and status word it relies on; everything
+ *     else is written before it is read.  Calls that can overlap on the GPU (different
+ *     streams without ordering, or different host threads) race on the array: order them.
+ * Arguments, layout and return codes are those of bandred_sy2sb_ex. */
+#define BANDRED_NOALLOC_SCRATCH_BYTES (16u << 20)
+int bandred_sy2sb_noalloc(int64_t n, int64_t w, double* A, int64_t lda, double* tau,
+                          const bandred_opts* opts, int* dev_status, cudaStream_t stream);
 
 /* ---------------------------------------------------------------- ge2gb -------------
  * Reduction to upper triangular band form, Section 3.1: A = U B V^T, m >= n.

@@ -22,7 +22,7 @@ from ._build import LIB, build  # noqa: F401
 
 __all__ = [
     "bandred_opts", "make_opts", "lib", "PRECISIONS",
-    "bandred_sy2sb_workspace", "bandred_sy2sb_ex", "bandred_sy2sb",
+    "bandred_sy2sb_workspace", "bandred_sy2sb_ex", "bandred_sy2sb", "bandred_sy2sb_noalloc",
     "bandred_ge2gb_workspace", "bandred_ge2gb_ex", "bandred_ge2gb",
     "bandred_status_string", "bandred_last_error", "bandred_profile_begin", "bandred_profile_end",
     "bandred_launch_count", "bandred_kernel_stat", "sy2sb", "ge2gb", "BandredError",
@@ -93,6 +93,8 @@ def lib():
         L.bandred_ge2gb_ex.restype = ci
         L.bandred_ge2gb.argtypes = [i64, i64, i64, vp, i64, vp, vp, op, vp]
         L.bandred_ge2gb.restype = ci
+        L.bandred_sy2sb_noalloc.argtypes = [i64, i64, vp, i64, vp, op, vp, vp]
+        L.bandred_sy2sb_noalloc.restype = ci
         L.bandred_profile_begin.argtypes = []
         L.bandred_profile_begin.restype = ci
         L.bandred_profile_end.argtypes = [ctypes.POINTER(bandred_kernel_stat), ci]
@@ -164,6 +166,16 @@ def bandred_sy2sb_ex(A, w: int, tau, opts, work, dev_status=None, stream=None) -
 
 def bandred_sy2sb(A, w: int, tau, opts=None, stream=None) -> int:
     return lib().bandred_sy2sb(A.shape[0], w, _ptr(A), _lda(A), _ptr(tau), _opts_ref(opts), _stream(stream))
+
+
+NOALLOC_SCRATCH_BYTES = 16 << 20
+
+
+def bandred_sy2sb_noalloc(A, w: int, tau, opts=None, dev_status=None, stream=None) -> int:
+    """bandred_sy2sb_ex without a workspace argument, for callers that cannot allocate:
+    the library's fixed device scratch array is used instead (see include/bandred.h)."""
+    return lib().bandred_sy2sb_noalloc(A.shape[0], w, _ptr(A), _lda(A), _ptr(tau), _opts_ref(opts),
+                                       _ptr(dev_status), _stream(stream))
 
 
 def bandred_ge2gb_workspace(m: int, n: int, w: int, opts: bandred_opts | None = None) -> int:

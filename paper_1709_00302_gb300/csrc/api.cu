@@ -76,6 +76,7 @@ const char* bandred_status_string(int code) {
     case BANDRED_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
     case BANDRED_ERR_UNSUPPORTED: return "size not supported by the kernels";
     case BANDRED_ERR_ALLOC: return "workspace allocation failed";
+    case BANDRED_ERR_SCRATCH: return "problem too large for the fixed scratch of bandred_sy2sb_noalloc";
     default: break;
   }
   if (code < 0 && code > -100) return "invalid argument (-i = i-th argument)";
