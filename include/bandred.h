@@ -74,6 +74,9 @@ typedef struct bandred_opts {
 #define BANDRED_DEV_OK 0
 #define BANDRED_DEV_TIMEOUT 1      /* a bounded wait ran out; the results are invalid */
 #define BANDRED_DEV_INVARIANT 2    /* an internal consistency check failed */
+#define BANDRED_DEV_RANGE 3        /* split precision only: an entry outside the range the bf16
+                                      slices represent exactly (|x| < 2^-95 or >= 2^127, or
+                                      subnormal); results are not valid, use BANDRED_FP64 */
 
 /* Host-side error codes. */
 #define BANDRED_ERR_CUDA (-1001)       /* a CUDA runtime call failed */
@@ -165,6 +168,33 @@ int bandred_ge2gb(int64_t m, int64_t n, int64_t w, double* A, int64_t lda, doubl
 int bandred_ge2gb_ex(int64_t m, int64_t n, int64_t w, double* A, int64_t lda, double* tauq,
                      double* taup, const bandred_opts* opts, void* work, size_t work_bytes,
                      int* dev_status, cudaStream_t stream);
+
+/* ---------------------------------------------------------------- split-precision engine
+ * The tensor-core products of the trailing updates, usable on their own.  FP64 operands
+ * are cut into bf16 slices (x ~ s0 + s1 [+ s2]; s0 keeps the leading 8 bits); the slice
+ * products of order < S (precision BANDRED_BF16X3: S = 2, three products; BANDRED_BF16X6:
+ * S = 3, six products) run as tcgen05.mma with FP32 accumulation in tensor memory and are
+ * recombined in FP64 every 256 reduction steps.  Accuracy is FP32-class (about 1e-5
+ * relative for BF16X3 and 1e-6 for BF16X6, relative to sum_k |a_ik||b_kj|).  Entries must
+ * be zero or lie in 2^-95 <= |x| < 2^127; otherwise dev_status reports BANDRED_DEV_RANGE.
+ * Arguments are device pointers (column-major FP64) except sizes; work is a device
+ * buffer (256-byte aligned) of at least the queried size.  No allocation, stream-ordered.
+ */
+
+/* C (m x n) = op(A) B with op(A) = A (m x k, lda >= m) or A^T (A is k x m, lda >= k when
+ * transA != 0); B is k x n (ldb >= k); 1 <= n <= 128.  Used for X1 = A2 W
+ * (Eq. updateA2symm) and the products with W of Eqs. updateA1, updateCD and updateD. */
+size_t bandred_gemm_split_workspace(int64_t m, int64_t n, int64_t k, int precision);
+int bandred_gemm_split(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, int transA,
+                       const double* B, int64_t ldb, double* C, int64_t ldc, int precision,
+                       void* work, size_t work_bytes, int* dev_status, cudaStream_t stream);
+
+/* Lower triangle of C (n x n) += X Y^T + Y X^T for X, Y (n x kb, 1 <= kb <= 128): the
+ * rank-2k update of Eq. updateA2syr2k.  The strictly upper triangle is not accessed. */
+size_t bandred_syr2k_split_workspace(int64_t n, int64_t kb, int precision);
+int bandred_syr2k_split(int64_t n, int64_t kb, const double* X, int64_t ldx, const double* Y,
+                        int64_t ldy, double* C, int64_t ldc, int precision, void* work,
+                        size_t work_bytes, int* dev_status, cudaStream_t stream);
 
 /* ---------------------------------------------------------------- tracing -----------
  * Per-kernel-class timing.  Between bandred_profile_begin() and bandred_profile_end()

@@ -25,7 +25,8 @@ __all__ = [
     "bandred_sy2sb_workspace", "bandred_sy2sb_ex", "bandred_sy2sb", "bandred_sy2sb_noalloc",
     "bandred_ge2gb_workspace", "bandred_ge2gb_ex", "bandred_ge2gb",
     "bandred_status_string", "bandred_last_error", "bandred_profile_begin", "bandred_profile_end",
-    "bandred_launch_count", "bandred_kernel_stat", "sy2sb", "ge2gb", "BandredError",
+    "bandred_launch_count", "bandred_kernel_stat", "bandred_gemm_split", "bandred_gemm_split_workspace",
+    "bandred_syr2k_split", "bandred_syr2k_split_workspace", "sy2sb", "ge2gb", "BandredError",
 ]
 
 PRECISIONS = {"fp64": 0, "bf16x3": 1, "bf16x6": 2, "ozaki": 3}
@@ -93,6 +94,14 @@ def lib():
         L.bandred_ge2gb_ex.restype = ci
         L.bandred_ge2gb.argtypes = [i64, i64, i64, vp, i64, vp, vp, op, vp]
         L.bandred_ge2gb.restype = ci
+        L.bandred_gemm_split_workspace.argtypes = [i64, i64, i64, ci]
+        L.bandred_gemm_split_workspace.restype = sz
+        L.bandred_gemm_split.argtypes = [i64, i64, i64, vp, i64, ci, vp, i64, vp, i64, ci, vp, sz, vp, vp]
+        L.bandred_gemm_split.restype = ci
+        L.bandred_syr2k_split_workspace.argtypes = [i64, i64, ci]
+        L.bandred_syr2k_split_workspace.restype = sz
+        L.bandred_syr2k_split.argtypes = [i64, i64, vp, i64, vp, i64, vp, i64, ci, vp, sz, vp, vp]
+        L.bandred_syr2k_split.restype = ci
         L.bandred_sy2sb_noalloc.argtypes = [i64, i64, vp, i64, vp, op, vp, vp]
         L.bandred_sy2sb_noalloc.restype = ci
         L.bandred_profile_begin.argtypes = []
@@ -192,6 +201,43 @@ def bandred_ge2gb_ex(A, w: int, tauq, taup, opts, work, dev_status=None, stream=
 def bandred_ge2gb(A, w: int, tauq, taup, opts=None, stream=None) -> int:
     m, n = A.shape
     return lib().bandred_ge2gb(m, n, w, _ptr(A), _lda(A), _ptr(tauq), _ptr(taup), _opts_ref(opts), _stream(stream))
+
+
+def _prec(p):
+    return PRECISIONS[p] if isinstance(p, str) else int(p)
+
+
+def bandred_gemm_split_workspace(m: int, n: int, k: int, precision="bf16x6") -> int:
+    return lib().bandred_gemm_split_workspace(m, n, k, _prec(precision))
+
+
+def bandred_gemm_split(A, B, C, precision="bf16x6", transA=False, work=None, dev_status=None, stream=None) -> int:
+    """C = op(A) B on the split-precision tensor-core engine (column-major CUDA tensors)."""
+    import torch
+
+    k, n = B.shape
+    m = C.shape[0]
+    if work is None:
+        work = torch.empty(max(bandred_gemm_split_workspace(m, n, k, precision), 256), dtype=torch.uint8,
+                           device=C.device)
+    return lib().bandred_gemm_split(m, n, k, _ptr(A), _lda(A), 1 if transA else 0, _ptr(B), _lda(B), _ptr(C), _lda(C),
+                                    _prec(precision), _ptr(work), work.numel(), _ptr(dev_status), _stream(stream))
+
+
+def bandred_syr2k_split_workspace(n: int, kb: int, precision="bf16x6") -> int:
+    return lib().bandred_syr2k_split_workspace(n, kb, _prec(precision))
+
+
+def bandred_syr2k_split(X, Y, C, precision="bf16x6", work=None, dev_status=None, stream=None) -> int:
+    """Lower triangle of C += X Y^T + Y X^T on the split-precision engine."""
+    import torch
+
+    n, kb = X.shape
+    if work is None:
+        work = torch.empty(max(bandred_syr2k_split_workspace(n, kb, precision), 256), dtype=torch.uint8,
+                           device=C.device)
+    return lib().bandred_syr2k_split(n, kb, _ptr(X), _lda(X), _ptr(Y), _lda(Y), _ptr(C), _lda(C), _prec(precision),
+                                     _ptr(work), work.numel(), _ptr(dev_status), _stream(stream))
 
 
 def bandred_profile_begin() -> int:

@@ -72,6 +72,7 @@ const char* bandred_status_string(int code) {
     case 0: return "success";
     case BANDRED_DEV_TIMEOUT: return "device: a bounded wait timed out (results invalid)";
     case BANDRED_DEV_INVARIANT: return "device: internal consistency check failed";
+    case BANDRED_DEV_RANGE: return "device: an entry is outside the range of the split-precision path";
     case BANDRED_ERR_CUDA: return "a CUDA runtime call failed";
     case BANDRED_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
     case BANDRED_ERR_UNSUPPORTED: return "size not supported by the kernels";

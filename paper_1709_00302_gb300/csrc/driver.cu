@@ -195,7 +195,8 @@ static int run_panel(double* A, int64_t rs, int64_t cs, int j, int bk, double* t
                      int64_t ldy, double* part, double* rowbuf, double* part2, GridSync* gs, int* status,
                      const Options& o, int max_ctas, unsigned int extra, cudaStream_t s) {
   int G, R, Rp;
-  if (panel_geometry(j, bk, max_ctas, kMinPanelRows, &G, &R, &Rp) != 0) return BANDRED_ERR_UNSUPPORTED;
+  bool w_smem = false;
+  if (panel_geometry(j, bk, max_ctas, kMinPanelRows, &G, &R, &Rp, &w_smem) != 0) return BANDRED_ERR_UNSUPPORTED;
   PanelParams p{};
   p.A = A;
   p.rs = rs;
@@ -215,6 +216,7 @@ static int run_panel(double* A, int64_t rs, int64_t cs, int j, int bk, double* t
   p.status = status;
   p.limit_ns = o.limit_ns;
   p.extra = extra;
+  p.w_in_smem = w_smem;
   CK(launch_panel(p, G, s));
   return 0;
 }

@@ -25,10 +25,11 @@ struct PanelParams {
   int* status;
   unsigned long long limit_ns;
   unsigned int extra;    // extra awaited arrivals (tests of the timeout path)
+  bool w_in_smem;        // this CTA's rows of W kept in shared memory during the panel
 };
 
-size_t panel_smem_bytes(int bk, int Rp);
-int panel_geometry(int j, int bk, int max_ctas, int min_rows, int* G, int* R, int* Rp);
+size_t panel_smem_bytes(int bk, int Rp, bool w_in_smem);
+int panel_geometry(int j, int bk, int max_ctas, int min_rows, int* G, int* R, int* Rp, bool* w_in_smem);
 cudaError_t launch_panel(const PanelParams& p, int G, cudaStream_t s);
 
 // ---------------------------------------------------------------- FP64 kernels (gemm_f64.cu)

@@ -43,6 +43,10 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
   double* dsum = slab + (size_t)bk * Rp;      // bk + 1 combined sums
   double* rowi = dsum + bk + 1;               // row i of the panel
   double* coef = rowi + bk;                   // z_c (c > i) and Y^T y_i (p < i)
+  double* red2 = coef + bk;                   // NT partial sums of the combine
+  // This CTA's rows of W: in shared memory when they fit, else in the W output itself.
+  double* wl = p.w_in_smem ? red2 + NT : p.W + rb;
+  const int64_t wld = p.w_in_smem ? Rp : p.ldy;
   __shared__ double s_beta, s_tau, s_scal, s_xnorm;
   __shared__ double s_red[NW];
   __shared__ int s_rescale;
@@ -91,17 +95,36 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
 
     if (!grid_barrier(p.gs, ++gen, p.extra, p.status, p.limit_ns)) return;
 
-    // Combine in a fixed order: every CTA obtains bit-identical sums.
-    for (int v = warp; v <= bk; v += NW) {
-      double s = 0.0;
-      if (v < bk) {
-        for (int q = lane; q < G; q += 32) s += ldcg(&part[(size_t)q * pstride + v]);
-        s = warp_sum(s);
-      } else {
-        for (int q = lane; q < G; q += 32) s = fmax(s, ldcg(&part[(size_t)q * pstride + v]));
-        s = warp_max(s);
+    // Combine in a fixed order: every CTA obtains bit-identical sums.  Thread t sums
+    // value t % (bk+1) over every ngrp-th CTA (coalesced, independent loads), then the
+    // ngrp partial sums of each value are added in order.
+    {
+      const int VP = bk + 1;
+      const int ngrp = NT / VP;
+      if (tid < ngrp * VP) {
+        const int v = tid % VP, grp = tid / VP;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int q = grp;
+        if (v < bk) {
+          for (; q + 3 * ngrp < G; q += 4 * ngrp) {
+            s0 += ldcg(&part[(size_t)q * pstride + v]);
+            s1 += ldcg(&part[(size_t)(q + ngrp) * pstride + v]);
+            s2 += ldcg(&part[(size_t)(q + 2 * ngrp) * pstride + v]);
+            s3 += ldcg(&part[(size_t)(q + 3 * ngrp) * pstride + v]);
+          }
+          for (; q < G; q += ngrp) s0 += ldcg(&part[(size_t)q * pstride + v]);
+          red2[tid] = (s0 + s1) + (s2 + s3);
+        } else {
+          for (; q < G; q += ngrp) s0 = fmax(s0, ldcg(&part[(size_t)q * pstride + v]));
+          red2[tid] = s0;
+        }
       }
-      if (lane == 0) dsum[v] = s;
+      __syncthreads();
+      if (tid < VP) {
+        double s = red2[tid];
+        for (int g2 = 1; g2 < ngrp; ++g2) s = (tid < bk) ? s + red2[g2 * VP + tid] : fmax(s, red2[g2 * VP + tid]);
+        dsum[tid] = s;
+      }
     }
     for (int c = tid; c < bk; c += NT) rowi[c] = ldcg(&rowg[c]);
     __syncthreads();
@@ -180,12 +203,26 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
     // W(:, i) = -tau (y_i + W(:, 0:i) (Y^T y_i)) for this CTA's rows.
     for (int r = tid; r < nr; r += NT) {
       const int gr = rb + r;
-      double s = gr > i ? slab[(size_t)i * Rp + r] : (gr == i ? 1.0 : 0.0);
-      for (int q = 0; q < i; ++q) s = fma(p.W[gr + (int64_t)q * p.ldy], coef[q], s);
-      p.W[gr + (int64_t)i * p.ldy] = -tau * s;
+      double s0 = gr > i ? slab[(size_t)i * Rp + r] : (gr == i ? 1.0 : 0.0);
+      double s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      int q = 0;
+      for (; q + 3 < i; q += 4) {
+        s0 = fma(wl[r + (int64_t)q * wld], coef[q], s0);
+        s1 = fma(wl[r + (int64_t)(q + 1) * wld], coef[q + 1], s1);
+        s2 = fma(wl[r + (int64_t)(q + 2) * wld], coef[q + 2], s2);
+        s3 = fma(wl[r + (int64_t)(q + 3) * wld], coef[q + 3], s3);
+      }
+      for (; q < i; ++q) s0 = fma(wl[r + (int64_t)q * wld], coef[q], s0);
+      wl[r + (int64_t)i * wld] = -tau * ((s0 + s1) + (s2 + s3));
     }
     __syncthreads();
   }
+
+  if (p.w_in_smem)
+    for (int idx = tid; idx < nr * bk; idx += NT) {
+      const int r = idx % nr, c = idx / nr;
+      p.W[rb + r + (int64_t)c * p.ldy] = wl[r + (int64_t)c * wld];
+    }
 
   // Write back: packed reflectors/R into the matrix, Y into the workspace.
   if (p.rs == 1) {
@@ -211,9 +248,11 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
 
 }  // namespace
 
-size_t panel_smem_bytes(int bk, int Rp) { return ((size_t)bk * Rp + 3 * (size_t)bk + 1) * sizeof(double); }
+size_t panel_smem_bytes(int bk, int Rp, bool w_in_smem) {
+  return ((size_t)bk * Rp * (w_in_smem ? 2 : 1) + 3 * (size_t)bk + 1 + kPanelThreads) * sizeof(double);
+}
 
-int panel_geometry(int j, int bk, int max_ctas, int min_rows, int* G, int* R, int* Rp) {
+int panel_geometry(int j, int bk, int max_ctas, int min_rows, int* G, int* R, int* Rp, bool* w_in_smem) {
   if (j <= 0 || bk <= 0) return -1;
   int g = (j + min_rows - 1) / min_rows;
   if (g > max_ctas) g = max_ctas;
@@ -221,10 +260,11 @@ int panel_geometry(int j, int bk, int max_ctas, int min_rows, int* G, int* R, in
   int r = (j + g - 1) / g;
   g = (j + r - 1) / r;  // every CTA owns at least one row
   int rp = r | 1;       // odd stride: conflict-free strided shared-memory access
-  if (panel_smem_bytes(bk, rp) > 227 * 1024) return -2;
+  if (panel_smem_bytes(bk, rp, false) > 227 * 1024) return -2;
   *G = g;
   *R = r;
   *Rp = rp;
+  *w_in_smem = panel_smem_bytes(bk, rp, true) <= 227 * 1024;
   return 0;
 }
 
@@ -245,7 +285,7 @@ cudaError_t launch_panel(const PanelParams& prm, int G, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     configured_device = dev;
   }
-  const size_t smem = panel_smem_bytes(prm.bk, prm.Rp);
+  const size_t smem = panel_smem_bytes(prm.bk, prm.Rp, prm.w_in_smem);
   if (smem > max_dynamic) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(prm.gs, 0, sizeof(GridSync), s);
   if (e != cudaSuccess) return e;

@@ -1,0 +1,538 @@
+// Split-precision tensor-core products for the trailing updates (tcgen05, sm_103a).
+//
+// Every FP64 operand x is cut into S bf16 slices (x ~ s0 + s1 [+ s2], see tc::split_bf16)
+// and a product A B is formed as the sum of the slice products A_s B_t with s + t < S
+// (S = 2: three products, "bf16x3"; S = 3: six products, "bf16x6"), accumulated in FP32 in
+// tensor memory.  Partial sums are recombined in FP64 every `kChunk` reduction steps, so
+// the FP32 accumulation never runs over more than kChunk terms.
+//
+// Kernels:
+//   pack_kernel         FP64 (R x K, optionally two matrices concatenated along K) ->
+//                       bf16 slices in the canonical K-major core-matrix layout of
+//                       tcgen05 operands, blocked into (TR x TK) tiles.
+//   stream_gemm_kernel  C_partial = A B for a large FP64 A streamed from HBM and sliced in
+//                       shared memory on the fly (plain, transposed, or symmetric with only
+//                       the lower triangle stored), and a pre-packed thin B (N <= 128).
+//                       Used for X1 = A2 W (Eq. updateA2symm), W^T E and D W_V.
+//   rank_update_kernel  C += alpha A B^T for pre-packed A, B with a short reduction
+//                       (Eq. updateA2syr2k on the lower triangle; Eqs. updateCD, updateD).
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "prof.h"
+#include "split.h"
+#include "tc.cuh"
+
+namespace bandred {
+namespace split {
+
+namespace {
+
+constexpr int NT = 256;
+constexpr int BM = 128;       // rows of a C tile (TMEM lanes)
+constexpr int BK = 32;        // reduction depth of one pipeline stage
+constexpr int kChunk = 256;   // FP32 accumulation length before FP64 recombination
+constexpr int CH = kChunk / BK;
+
+__device__ __forceinline__ void report(int* status, int code) {
+  if (status) atomicCAS(status, 0, code);
+}
+
+// ================================================================= pack
+__global__ void pack_kernel(PackParams p) {
+  const int groups_per_tile = p.TR * (p.TK / 8);
+  const int64_t total = (int64_t)p.nrb * p.nkb * groups_per_tile;
+  const int K = p.K1 + p.K2;
+  bool ok = true;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
+    const int within = (int)(g % groups_per_tile);
+    const int64_t tile = g / groups_per_tile;
+    const int kb = (int)(tile % p.nkb), rb = (int)(tile / p.nkb);
+    const int r = within % p.TR, kg = within / p.TR;
+    const int row = rb * p.TR + r;
+    uint32_t words[3][4];
+#pragma unroll
+    for (int kk = 0; kk < 8; kk += 2) {
+      __nv_bfloat16 sl0[3], sl1[3];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int k = kb * p.TK + kg * 8 + kk + h;
+        double x = 0.0;
+        if (row < p.R && k < K) {
+          if (k < p.K1)
+            x = p.t1 ? p.M1[k + (int64_t)row * p.ld1] : p.M1[row + (int64_t)k * p.ld1];
+          else
+            x = p.t2 ? p.M2[(k - p.K1) + (int64_t)row * p.ld2] : p.M2[row + (int64_t)(k - p.K1) * p.ld2];
+          x *= (k < p.K1) ? p.scale1 : p.scale2;
+        }
+        __nv_bfloat16 sl[3];
+        ok &= tc::split_bf16<3>(x, sl);
+#pragma unroll
+        for (int s = 0; s < 3; ++s) (h ? sl1 : sl0)[s] = sl[s];
+      }
+#pragma unroll
+      for (int s = 0; s < 3; ++s)
+        words[s][kk / 2] = (uint32_t)__bfloat16_as_ushort(sl0[s]) | ((uint32_t)__bfloat16_as_ushort(sl1[s]) << 16);
+    }
+    const size_t tile_elems = (size_t)p.TR * p.TK;
+    for (int s = 0; s < p.S; ++s) {
+      __nv_bfloat16* base = p.out + ((size_t)tile * p.S + s) * tile_elems;
+      uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<char*>(base) + tc::kmajor_offset(r, kg * 8, p.TR));
+      *dst = make_uint4(words[s][0], words[s][1], words[s][2], words[s][3]);
+    }
+  }
+  if (!ok) report(p.status, BANDRED_DEV_RANGE);
+}
+
+// ================================================================= stream GEMM
+template <int S>
+struct Products;
+template <>
+struct Products<2> {
+  static constexpr int n = 3;
+  __device__ static constexpr int s(int q) { return q == 2 ? 1 : 0; }
+  __device__ static constexpr int t(int q) { return q == 1 ? 1 : 0; }
+};
+template <>
+struct Products<3> {
+  static constexpr int n = 6;
+  // (0,0) (0,1) (1,0) (0,2) (1,1) (2,0)
+  __device__ static constexpr int s(int q) { return q == 2 ? 1 : (q == 4 ? 1 : (q == 5 ? 2 : 0)); }
+  __device__ static constexpr int t(int q) { return q == 1 ? 1 : (q == 3 ? 2 : (q == 4 ? 1 : 0)); }
+};
+
+template <int BN, int S, int NSTAGE>
+struct StreamSmem {
+  static constexpr int NB = NSTAGE + 1;
+  static constexpr size_t fp64_bytes = (size_t)NSTAGE * BK * BM * 8;
+  static constexpr size_t aslice_bytes = (size_t)BM * BK * 2;  // one slice, one stage
+  static constexpr size_t bslice_bytes = (size_t)BN * BK * 2;
+  static constexpr size_t off_a = fp64_bytes;
+  static constexpr size_t off_b = off_a + 2 * S * aslice_bytes;
+  static constexpr size_t off_bar = off_b + (size_t)NB * S * bslice_bytes;
+  static constexpr size_t total = off_bar + 64;
+};
+
+template <int BN, int S, int NSTAGE>
+__global__ void __launch_bounds__(NT, 1) stream_gemm_kernel(StreamParams p) {
+  using L = StreamSmem<BN, S, NSTAGE>;
+  using PR = Products<S>;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  double* ring = reinterpret_cast<double*>(smem);
+  unsigned char* aslices = smem + L::off_a;
+  unsigned char* bslices = smem + L::off_b;
+  uint64_t* bar_mma = reinterpret_cast<uint64_t*>(smem + L::off_bar);  // [2]
+  uint64_t* bar_acc = bar_mma + 2;                                       // [2]
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bar_acc + 2);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int i0 = blockIdx.x * BM;
+  const int z = blockIdx.y;
+  const int st_begin = z * p.stages_per_split;
+  const int st_end = min(p.nkb, st_begin + p.stages_per_split);
+  const int nst = st_end - st_begin;
+  constexpr uint32_t kTmemCols = 2 * BN;
+  const unsigned long long deadline = global_ns() + p.limit_ns;
+
+  if (tid == 0) {
+    tc::mbar_init(&bar_mma[0], 1);
+    tc::mbar_init(&bar_mma[1], 1);
+    tc::mbar_init(&bar_acc[0], 1);
+    tc::mbar_init(&bar_acc[1], 1);
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(tmem_holder, kTmemCols);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_holder;
+
+  // ---- loads of one stage: the FP64 A tile (BK x BM, [k][i]) and the B slices
+  auto issue_loads = [&](int ls) {
+    const int kst = st_begin + ls;
+    const int k0 = kst * BK;
+    double* dst = ring + (size_t)(ls % NSTAGE) * BK * BM;
+    const double* A = p.A;
+    const int64_t lda = p.lda;
+    bool lower_map = true;
+    if (p.mode == kModeTrans) lower_map = false;
+    if (p.mode == kModeSymLower && k0 >= i0 + BM - 1) lower_map = false;  // whole tile above the diagonal
+    const bool mixed = p.mode == kModeSymLower && !(k0 + BK - 1 <= i0) && lower_map;
+    if (lower_map) {
+#pragma unroll 4
+      for (int q = 0; q < (BK * BM) / NT; ++q) {
+        const int i = tid & (BM - 1), k = (tid >> 7) + 2 * q;
+        const int gi = i0 + i, gk = k0 + k;
+        const bool in = gi < p.M && gk < p.K;
+        const double* src = A;
+        if (in) {
+          if (mixed && gi < gk)
+            src = A + gk + (int64_t)gi * lda;
+          else
+            src = A + gi + (int64_t)gk * lda;
+        }
+        tc::cp_async8(dst + k * BM + i, src, in ? 8u : 0u);
+      }
+    } else {
+#pragma unroll 4
+      for (int q = 0; q < (BK * BM) / NT; ++q) {
+        const int k = tid & (BK - 1), i = (tid >> 5) + 8 * q;
+        const int gi = i0 + i, gk = k0 + k;
+        const bool in = gi < p.M && gk < p.K;
+        const double* src = in ? A + gk + (int64_t)gi * lda : A;
+        tc::cp_async8(dst + k * BM + i, src, in ? 8u : 0u);
+      }
+    }
+    // B slices of this stage: S * BN * BK bf16, contiguous in the packed blob.
+    const unsigned char* bsrc =
+        reinterpret_cast<const unsigned char*>(p.Bblob) + (size_t)kst * S * L::bslice_bytes;
+    unsigned char* bdst = bslices + (size_t)(ls % L::NB) * S * L::bslice_bytes;
+    for (int c = tid; c < (int)(S * L::bslice_bytes / 16); c += NT) tc::cp_async16(bdst + 16 * c, bsrc + 16 * c);
+  };
+
+  double acc[BN / 2];
+#pragma unroll
+  for (int c = 0; c < BN / 2; ++c) acc[c] = 0.0;
+  int timed_out = 0;
+  bool range_ok = true;
+
+  auto drain_chunk = [&](int c) {
+    // all threads: wait for the chunk's MMAs, then add its FP32 sums into FP64 registers
+    int to = tc::mbar_wait(&bar_acc[c & 1], (c >> 1) & 1, deadline) ? 0 : 1;
+    tc::fence_after_sync();
+    const uint32_t q = warp & 3, h = warp >> 2;
+    const uint32_t taddr = tmem + ((q * 32) << 16) + (uint32_t)((c & 1) * BN + h * (BN / 2));
+    if (!to) {
+      if constexpr (BN / 2 >= 32) {
+#pragma unroll
+        for (int part = 0; part < BN / 64; ++part) {
+          float v[32];
+          tc::tmem_ld32(taddr + part * 32, v);
+#pragma unroll
+          for (int cc = 0; cc < 32; ++cc) acc[part * 32 + cc] += (double)v[cc];
+        }
+      } else {
+        float v[16];
+        tc::tmem_ld16(taddr, v);
+#pragma unroll
+        for (int cc = 0; cc < 16; ++cc) acc[cc] += (double)v[cc];
+      }
+    }
+    tc::fence_before_sync();
+    return to;
+  };
+
+  for (int ls = 0; ls < NSTAGE - 1; ++ls) {
+    if (ls < nst) issue_loads(ls);
+    tc::cp_async_commit();
+  }
+
+  for (int st = 0; st < nst && !timed_out; ++st) {
+    const int sb = st & 1;
+    int to = 0;
+    if (st >= 2) to = tc::mbar_wait(&bar_mma[sb], ((st - 2) >> 1) & 1, deadline) ? 0 : 1;
+    if (__syncthreads_or(to)) {
+      timed_out = 1;
+      break;
+    }
+    const int ls = st + NSTAGE - 1;
+    if (ls < nst) issue_loads(ls);
+    tc::cp_async_commit();
+    tc::cp_async_wait<NSTAGE - 1>();
+    __syncthreads();
+
+    // ---- convert the FP64 stage into S bf16 slices (K-major core layout)
+    {
+      const double* src = ring + (size_t)(st % NSTAGE) * BK * BM;
+      unsigned char* adst = aslices + (size_t)sb * S * L::aslice_bytes;
+#pragma unroll
+      for (int q = 0; q < (BM * (BK / 8)) / NT; ++q) {
+        const int i = tid & (BM - 1), kg = (tid >> 7) + 2 * q;
+        uint32_t words[S][4];
+#pragma unroll
+        for (int kk = 0; kk < 8; kk += 2) {
+          __nv_bfloat16 a[S], b[S];
+          range_ok &= tc::split_bf16<S>(src[(kg * 8 + kk) * BM + i], a);
+          range_ok &= tc::split_bf16<S>(src[(kg * 8 + kk + 1) * BM + i], b);
+#pragma unroll
+          for (int s = 0; s < S; ++s)
+            words[s][kk / 2] = (uint32_t)__bfloat16_as_ushort(a[s]) | ((uint32_t)__bfloat16_as_ushort(b[s]) << 16);
+        }
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+          uint4* d = reinterpret_cast<uint4*>(adst + s * L::aslice_bytes + tc::kmajor_offset(i, kg * 8, BM));
+          *d = make_uint4(words[s][0], words[s][1], words[s][2], words[s][3]);
+        }
+      }
+    }
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+
+    // ---- one thread issues the slice-pair MMAs of this stage
+    const int chunk = st / CH;
+    if (tid == 0) {
+      tc::fence_after_sync();
+      const uint32_t d = tmem + (uint32_t)((chunk & 1) * BN);
+      constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
+      const uint32_t abase = tc::smem_u32(aslices + (size_t)sb * S * L::aslice_bytes);
+      const uint32_t bbase = tc::smem_u32(bslices + (size_t)(st % L::NB) * S * L::bslice_bytes);
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk) {
+#pragma unroll
+        for (int q = 0; q < PR::n; ++q) {
+          const uint64_t ad = tc::smem_desc(abase + PR::s(q) * L::aslice_bytes + kk * 2 * (BM / 8) * 128,
+                                            (BM / 8) * 128, 128);
+          const uint64_t bd = tc::smem_desc(bbase + PR::t(q) * L::bslice_bytes + kk * 2 * (BN / 8) * 128,
+                                            (BN / 8) * 128, 128);
+          const uint32_t accum = (st % CH == 0 && kk == 0 && q == 0) ? 0u : 1u;
+          tc::mma_bf16(d, ad, bd, idesc, accum);
+        }
+      }
+      tc::mma_commit(&bar_mma[sb]);
+      if (st % CH == CH - 1 || st == nst - 1) tc::mma_commit(&bar_acc[chunk & 1]);
+    }
+
+    // ---- FP64 recombination of the previous chunk, one stage into the next one
+    if (st % CH == 0 && st > 0) {
+      to = drain_chunk(chunk - 1);
+      if (__syncthreads_or(to)) timed_out = 1;
+    }
+  }
+  if (!timed_out && nst > 0) {
+    const int last = (nst - 1) / CH;
+    const int to = drain_chunk(last);
+    if (__syncthreads_or(to)) timed_out = 1;
+  }
+  tc::cp_async_wait_all();
+
+  if (timed_out) {
+    report(p.status, BANDRED_DEV_TIMEOUT);
+  } else {
+    const int q = warp & 3, h = warp >> 2;
+    const int row = i0 + q * 32 + lane;
+    double* P = p.P + (size_t)z * p.split_stride;
+    if (row < p.M) {
+#pragma unroll
+      for (int c = 0; c < BN / 2; ++c) {
+        const int col = h * (BN / 2) + c;
+        if (col < p.N) P[row + (int64_t)col * p.ldp] = acc[c];
+      }
+    }
+  }
+  if (!__syncthreads_and(range_ok ? 1 : 0) && tid == 0) report(p.status, BANDRED_DEV_RANGE);
+  // Let any MMA still in flight finish before TMEM is released (bounded).
+  if (timed_out && tid == 0) {
+    const unsigned long long dl = global_ns() + p.limit_ns;
+    for (int b = 0; b < 2; ++b) tc::mbar_wait(&bar_mma[b], 0, dl);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+// ================================================================= rank update
+constexpr int RK = 64;  // reduction depth per smem load
+
+template <int S>
+struct RankSmem {
+  static constexpr size_t slice_bytes = (size_t)BM * RK * 2;
+  static constexpr size_t off_b = (size_t)S * slice_bytes;
+  static constexpr size_t off_bar = off_b + (size_t)S * slice_bytes;
+  static constexpr size_t total = off_bar + 64;
+};
+
+template <int S>
+__global__ void __launch_bounds__(NT) rank_update_kernel(RankParams p) {
+  using L = RankSmem<S>;
+  using PR = Products<S>;
+  const int I = blockIdx.x, J = p.tj0 + blockIdx.y;
+  if (p.lower && I < J) return;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* as = smem;
+  unsigned char* bs = smem + L::off_b;
+  uint64_t* bar_ld = reinterpret_cast<uint64_t*>(smem + L::off_bar);
+  uint64_t* bar_mma = bar_ld + 1;
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bar_mma + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const unsigned long long deadline = global_ns() + p.limit_ns;
+  if (tid == 0) {
+    tc::mbar_init(bar_ld, 1);
+    tc::mbar_init(bar_mma, 1);
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(tmem_holder, BM);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_holder;
+  const int nkb = p.Kr / RK;
+  const size_t blk = (size_t)S * L::slice_bytes;  // one (row block, K block) of a blob
+  int to = 0;
+  for (int kb = 0; kb < nkb && !to; ++kb) {
+    if (tid == 0) {
+      tc::mbar_arrive_expect_tx(bar_ld, (uint32_t)(2 * blk));
+      tc::bulk_g2s(as, reinterpret_cast<const unsigned char*>(p.Ablob) + ((size_t)I * nkb + kb) * blk,
+                   (uint32_t)blk, bar_ld);
+      tc::bulk_g2s(bs, reinterpret_cast<const unsigned char*>(p.Bblob) + ((size_t)J * nkb + kb) * blk,
+                   (uint32_t)blk, bar_ld);
+      int t = tc::mbar_wait(bar_ld, kb & 1, deadline) ? 0 : 1;
+      if (!t) {
+        tc::fence_after_sync();
+        constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BM);
+        const uint32_t ab = tc::smem_u32(as), bb = tc::smem_u32(bs);
+#pragma unroll
+        for (int kk = 0; kk < RK / 16; ++kk)
+#pragma unroll
+          for (int q = 0; q < PR::n; ++q) {
+            const uint64_t ad = tc::smem_desc(ab + PR::s(q) * L::slice_bytes + kk * 2 * (BM / 8) * 128, (BM / 8) * 128, 128);
+            const uint64_t bd = tc::smem_desc(bb + PR::t(q) * L::slice_bytes + kk * 2 * (BM / 8) * 128, (BM / 8) * 128, 128);
+            tc::mma_bf16(tmem, ad, bd, idesc, (kb == 0 && kk == 0 && q == 0) ? 0u : 1u);
+          }
+        tc::mma_commit(bar_mma);
+        t = tc::mbar_wait(bar_mma, kb & 1, deadline) ? 0 : 1;
+      }
+      to = t;
+    }
+    to = __syncthreads_or(to);
+  }
+  if (!to) {
+    tc::fence_after_sync();
+    const int q = warp & 3, h = warp >> 2;
+    const int row = I * BM + q * 32 + lane;
+    const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * 64);
+#pragma unroll
+    for (int part = 0; part < 2; ++part) {
+      float v[32];
+      tc::tmem_ld32(taddr + part * 32, v);
+      if (row < p.M) {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          const int col = J * BM + h * 64 + part * 32 + c;
+          if (col < p.N && col >= p.col0 && col < p.col1 && (!p.lower || row >= col)) {
+            double* cp = p.C + row + (int64_t)col * p.ldc;
+            *cp = fma(p.alpha, (double)v[c], *cp);
+          }
+        }
+      }
+    }
+  } else if (tid == 0) {
+    report(p.status, BANDRED_DEV_TIMEOUT);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, BM);
+  }
+}
+
+// ================================================================= split-K reduce
+__global__ void reduce_kernel(int M, int N, int splits, const double* P, int64_t ldp, int64_t sstride, double alpha,
+                              double beta, double* C, int64_t ldc) {
+  const int64_t total = (int64_t)M * N;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % M), c = (int)(e / M);
+    double s = 0.0;
+    for (int z = 0; z < splits; ++z) s += P[(size_t)z * sstride + i + (int64_t)c * ldp];
+    double* cp = &C[i + (int64_t)c * ldc];
+    *cp = (beta == 0.0) ? alpha * s : fma(alpha, s, beta * *cp);
+  }
+}
+
+template <int BN, int S, int NSTAGE>
+cudaError_t launch_stream(const StreamParams& p, int splits, cudaStream_t s) {
+  using L = StreamSmem<BN, S, NSTAGE>;
+  static_assert(L::total <= 227 * 1024, "stream GEMM shared memory");
+  static int configured = -1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (configured != dev) {
+    cudaError_t e = cudaFuncSetAttribute(stream_gemm_kernel<BN, S, NSTAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)L::total);
+    if (e != cudaSuccess) return e;
+    configured = dev;
+  }
+  dim3 grid((p.M + BM - 1) / BM, splits);
+  stream_gemm_kernel<BN, S, NSTAGE><<<grid, NT, L::total, s>>>(p);
+  prof::count_launch();
+  return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t launch_rank(const RankParams& p, int tiles_i, int tiles_j, cudaStream_t s) {
+  using L = RankSmem<S>;
+  static int configured = -1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (configured != dev) {
+    cudaError_t e =
+        cudaFuncSetAttribute(rank_update_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::total);
+    if (e != cudaSuccess) return e;
+    configured = dev;
+  }
+  rank_update_kernel<S><<<dim3(tiles_i, tiles_j), NT, L::total, s>>>(p);
+  prof::count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// ================================================================= host API
+int slices_of(int precision) { return precision == BANDRED_BF16X3 ? 2 : 3; }
+
+size_t packed_bytes(int R, int K, int TR, int TK, int S) {
+  const size_t nrb = (R + TR - 1) / TR, nkb = (K + TK - 1) / TK;
+  return nrb * nkb * (size_t)S * TR * TK * 2;
+}
+
+cudaError_t pack(const PackParams& pp, cudaStream_t s) {
+  const int64_t total = (int64_t)pp.nrb * pp.nkb * pp.TR * (pp.TK / 8);
+  if (total <= 0) return cudaSuccess;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
+  pack_kernel<<<blocks, 256, 0, s>>>(pp);
+  prof::count_launch();
+  return cudaGetLastError();
+}
+
+int stream_bn(int N) { return N <= 32 ? 32 : (N <= 64 ? 64 : 128); }
+
+cudaError_t stream_gemm(const StreamParams& p, int S, int splits, cudaStream_t s) {
+  const int BN = stream_bn(p.N);
+  if (S == 2) {
+    if (BN == 32) return launch_stream<32, 2, 3>(p, splits, s);
+    if (BN == 64) return launch_stream<64, 2, 3>(p, splits, s);
+    return launch_stream<128, 2, 2>(p, splits, s);
+  }
+  if (BN == 32) return launch_stream<32, 3, 3>(p, splits, s);
+  if (BN == 64) return launch_stream<64, 3, 3>(p, splits, s);
+  return launch_stream<128, 3, 2>(p, splits, s);
+}
+
+cudaError_t reduce(int M, int N, int splits, const double* P, int64_t ldp, int64_t sstride, double alpha, double beta,
+                   double* C, int64_t ldc, cudaStream_t s) {
+  const int64_t total = (int64_t)M * N;
+  if (total <= 0) return cudaSuccess;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 2048);
+  reduce_kernel<<<blocks, 256, 0, s>>>(M, N, splits, P, ldp, sstride, alpha, beta, C, ldc);
+  prof::count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t rank_update(const RankParams& p, int S, int tiles_i, int tiles_j, cudaStream_t s) {
+  if (tiles_i <= 0 || tiles_j <= 0) return cudaSuccess;
+  return S == 2 ? launch_rank<2>(p, tiles_i, tiles_j, s) : launch_rank<3>(p, tiles_i, tiles_j, s);
+}
+
+}  // namespace split
+}  // namespace bandred
