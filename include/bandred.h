@@ -133,7 +133,7 @@ int bandred_sy2sb_ex(int64_t n, int64_t w, double* A, int64_t lda, double* tau,
  * on every GPU that loads the library until the process exits.  No call allocates or
  * frees memory.
  *   - Limit: the problem must satisfy bandred_sy2sb_workspace(n, w, opts) <=
- *     BANDRED_NOALLOC_SCRATCH_BYTES (about n <= 8000 at w = b = 64); larger problems
+ *     BANDRED_NOALLOC_SCRATCH_BYTES (about n <= 5500 at w = b = 64 with default options); larger problems
  *     return BANDRED_ERR_SCRATCH before any device work.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call before any

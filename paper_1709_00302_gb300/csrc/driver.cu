@@ -12,6 +12,7 @@
 #include "driver.h"
 #include "kernels.h"
 #include "prof.h"
+#include "split.h"
 
 namespace bandred {
 
@@ -20,6 +21,9 @@ namespace {
 constexpr size_t kAlign = 256;
 constexpr int kMinPanelRows = 32;
 constexpr int kMaxSplits = 128;
+constexpr int kSmallSplits = 32;       // split-K of the FP64 products with a b-wide output
+constexpr int kMaxStreamSplits = 8;    // split-K of the streamed X1 = A2 W product
+constexpr int kMaxSmallSplits = 256;   // split-K of the b x b product X1^T W
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -113,15 +117,24 @@ int resolve_options(const bandred_opts* in, int64_t w, Options* o) {
   return 0;
 }
 
-// Workspace of sy2sb (layout shared by sizing and carving).
+// Workspace of sy2sb (layout shared by sizing and carving).  Y and W are double-buffered:
+// with look-ahead the next panel writes one pair while the current update reads the other.
 struct Sy2sbWs {
-  double *Y, *W, *X, *X2, *Z, *splitk, *part, *rowbuf, *part2;
+  double *Y[2], *W[2], *X, *X2;
+  double *Z[2], *splitk[2];  // FP64 small products; [1] belongs to the panel stream
+  double *part, *rowbuf, *part2;
   GridSync* gs;
-  int* status;
+  // split-precision buffers
+  __nv_bfloat16 *wblob, *x2blob, *ablob, *bblob;
+  double* P;
+  size_t P_cap;
   int64_t ld;
   size_t splitk_cap;
+  int* status;
   size_t bytes;
 };
+
+static bool is_split(const Options& o) { return o.precision == BANDRED_BF16X3 || o.precision == BANDRED_BF16X6; }
 
 static Sy2sbWs carve_sy2sb(void* work, int64_t n, int64_t w, const Options& o, int sms) {
   Carver c{static_cast<char*>(work)};
@@ -129,17 +142,34 @@ static Sy2sbWs carve_sy2sb(void* work, int64_t n, int64_t w, const Options& o, i
   const int64_t jmax = std::max<int64_t>(n - w, 1);
   const int64_t b = o.b;
   ws.ld = jmax;
-  ws.Y = c.take<double>(jmax * b);
-  ws.W = c.take<double>(jmax * b);
+  // the second Y/W pair and the panel stream's product buffers exist only with look-ahead
+  const int nbuf = o.lookahead == 0 ? 1 : 2;
+  for (int q = 0; q < 2; ++q) {
+    ws.Y[q] = q < nbuf ? c.take<double>(jmax * b) : ws.Y[0];
+    ws.W[q] = q < nbuf ? c.take<double>(jmax * b) : ws.W[0];
+  }
   ws.X = c.take<double>(jmax * b);
   ws.X2 = c.take<double>(b * b);
-  ws.Z = c.take<double>(b * std::max<int64_t>(w, 1));
-  ws.splitk_cap = (size_t)kMaxSplits * b * std::max<int64_t>(w, b);
-  ws.splitk = c.take<double>(ws.splitk_cap);
-  ws.part = c.take<double>(2 * (size_t)sms * (b + 1));
+  ws.splitk_cap = (size_t)kSmallSplits * b * std::max<int64_t>(w, b);
+  for (int q = 0; q < 2; ++q) {
+    ws.Z[q] = q < nbuf ? c.take<double>(b * std::max<int64_t>(w, 1)) : ws.Z[0];
+    ws.splitk[q] = q < nbuf ? c.take<double>(ws.splitk_cap) : ws.splitk[0];
+  }
   ws.rowbuf = c.take<double>(2 * (size_t)b);
   ws.part2 = c.take<double>((size_t)sms);
-  ws.gs = c.take<GridSync>(1);
+  ws.gs = c.take<GridSync>(1);  // 256 bytes, immediately followed by the accumulators
+  ws.part = c.take<double>((panel_sync_bytes((int)b) - 256) / sizeof(double));
+  if (is_split(o)) {
+    const int S = split::slices_of(o.precision);
+    const int BN = split::stream_bn((int)b);
+    const int Kr = (int)((2 * b + 63) / 64 * 64);
+    ws.wblob = c.take<__nv_bfloat16>(split::packed_bytes(BN, (int)jmax, BN, 32, S) / 2);
+    ws.x2blob = c.take<__nv_bfloat16>(split::packed_bytes(BN, (int)b, BN, 32, S) / 2);
+    ws.ablob = c.take<__nv_bfloat16>(split::packed_bytes((int)jmax, Kr, 128, 64, S) / 2);
+    ws.bblob = c.take<__nv_bfloat16>(split::packed_bytes((int)jmax, Kr, 128, 64, S) / 2);
+    ws.P_cap = std::max<size_t>((size_t)kMaxStreamSplits * jmax * BN, (size_t)kMaxSmallSplits * BN * BN);
+    ws.P = c.take<double>(ws.P_cap);
+  }
   ws.status = c.take<int>(1);  // last piece: the short forms read it at bytes - 256
   ws.bytes = c.off;
   return ws;
@@ -168,10 +198,10 @@ static Ge2gbWs carve_ge2gb(void* work, int64_t m, int64_t n, const Options& o, i
   ws.P = c.take<double>(ws.ldu * b);
   ws.splitk_cap = (size_t)kMaxSplits * b * b * 4;
   ws.splitk = c.take<double>(ws.splitk_cap);
-  ws.part = c.take<double>(2 * (size_t)sms * (b + 1));
   ws.rowbuf = c.take<double>(2 * (size_t)b);
   ws.part2 = c.take<double>((size_t)sms);
-  ws.gs = c.take<GridSync>(1);
+  ws.gs = c.take<GridSync>(1);  // 256 bytes, immediately followed by the accumulators
+  ws.part = c.take<double>((panel_sync_bytes((int)b) - 256) / sizeof(double));
   ws.status = c.take<int>(1);  // last piece: the short forms read it at bytes - 256
   ws.bytes = c.off;
   return ws;
@@ -192,7 +222,7 @@ static int current_sms() {
 // One panel factorisation: QR of the j x bk panel at `A` (rs = 1, cs = lda) or LQ of the
 // bk x j row panel (rs = lda, cs = 1).
 static int run_panel(double* A, int64_t rs, int64_t cs, int j, int bk, double* tau, double* Y, double* W,
-                     int64_t ldy, double* part, double* rowbuf, double* part2, GridSync* gs, int* status,
+                     int64_t ldy, double* acc, double* rowbuf, double* part2, GridSync* gs, int* status,
                      const Options& o, int max_ctas, unsigned int extra, cudaStream_t s) {
   int G, R, Rp;
   bool w_smem = false;
@@ -209,7 +239,7 @@ static int run_panel(double* A, int64_t rs, int64_t cs, int j, int bk, double* t
   p.Y = Y;
   p.W = W;
   p.ldy = ldy;
-  p.part = part;
+  p.acc = acc;
   p.rowbuf = rowbuf;
   p.part2 = part2;
   p.gs = gs;
@@ -222,59 +252,374 @@ static int run_panel(double* A, int64_t rs, int64_t cs, int j, int bk, double* t
 }
 
 // ---------------------------------------------------------------------------------
+// Auxiliary stream (highest priority) and events used for look-ahead, one set per host
+// thread and device, created on first use.
+struct AuxStreams {
+  cudaStream_t panel = nullptr;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+
+static int aux_streams(AuxStreams** out) {
+  thread_local AuxStreams per_dev[16];
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  AuxStreams& a = per_dev[dev & 15];
+  if (!a.panel) {
+    int lo = 0, hi = 0;
+    CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    CK(cudaStreamCreateWithPriority(&a.panel, cudaStreamNonBlocking, hi));
+    for (auto& e : a.ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+  *out = &a;
+  return 0;
+}
+
+// Split of the streamed product over the reduction dimension: enough CTAs for whole
+// waves on `sms` SMs (one CTA per SM), at least two stages per split.
+static int stream_splits(int tiles, int nkb, int sms, int cap) {
+  int best = 1;
+  double best_eff = 0.0;
+  for (int sp = 1; sp <= cap; ++sp) {
+    if (sp > 1 && nkb / sp < 2) break;
+    const int ctas = tiles * sp;
+    const int waves = (ctas + sms - 1) / sms;
+    const double eff = (double)ctas / ((double)waves * sms);
+    if (eff > best_eff + 0.02) {
+      best_eff = eff;
+      best = sp;
+    }
+    if (eff >= 0.9) break;
+  }
+  return best;
+}
+
+namespace {
+
+// One sy2sb reduction: the state shared by the steps of an iteration.
+struct Sy2sb {
+  int64_t n, w, lda;
+  double* A;
+  double* tau;
+  Options o;
+  Sy2sbWs ws;
+  int* status;
+  int sms, pmax, S;
+  unsigned int extra;
+
+  int panel(int64_t k, int buf, cudaStream_t s) {
+    const int bk = (int)std::min<int64_t>(o.b, n - w - 1 - k);
+    const int64_t r0 = k + w;
+    const int j = (int)(n - r0);
+    prof::Scope sc(prof::kPanel, s, panel_flops(j, bk), panel_bytes(j, bk));
+    int rc = run_panel(A + r0 + k * lda, 1, lda, j, bk, tau + k, ws.Y[buf], ws.W[buf], ws.ld, ws.part, ws.rowbuf,
+                       ws.part2, ws.gs, status, o, pmax, extra, s);
+    extra = 0;
+    return rc;
+  }
+
+  // A1 = A(r0:n, k+bk : k+w) columns [c0, c1) (relative to A1) += Y (W^T A1).
+  int update_a1(int64_t k, int buf, int c0, int c1, int zi, cudaStream_t s) {
+    const int bk = (int)std::min<int64_t>(o.b, n - w - 1 - k);
+    const int64_t r0 = k + w;
+    const int j = (int)(n - r0);
+    if (c1 <= c0) return 0;
+    const int na = c1 - c0;
+    double* A1 = A + r0 + (k + bk + c0) * lda;
+    const int sp = choose_splits(bk, na, j, ws.splitk_cap, sms);
+    prof::Scope sc(prof::kGemm, s, 4.0 * j * na * bk, 8.0 * (2.0 * j * na + 2.0 * j * bk));
+    CK(gemm_f64(bk, na, j, 1.0, MatView{ws.W[buf], ws.ld, 1}, MatView{A1, 1, lda}, 0.0, ws.Z[zi], bk, sp,
+                ws.splitk[zi], s));
+    CK(gemm_f64(j, na, bk, 1.0, MatView{ws.Y[buf], 1, ws.ld}, MatView{ws.Z[zi], 1, bk}, 1.0, A1, lda, 1, nullptr, s));
+    return 0;
+  }
+
+  // X1 = A2 W, X2 = X1^T W / 2, X3 = X1 + Y X2 (into ws.X); for the split path also packs
+  // the operands of the rank-2k update.
+  int compute_x(int64_t k, int buf, cudaStream_t s) {
+    const int bk = (int)std::min<int64_t>(o.b, n - w - 1 - k);
+    const int64_t r0 = k + w;
+    const int j = (int)(n - r0);
+    const int64_t ld = ws.ld;
+    double* A2 = A + r0 + r0 * lda;
+    const double* Y = ws.Y[buf];
+    const double* W = ws.W[buf];
+    if (!is_split(o)) {
+      {
+        prof::Scope sc(prof::kSymm, s, symm_flops(j, bk), symm_bytes(j, bk));
+        CK(symm_lower_f64(j, bk, A2, lda, W, ld, ws.X, ld, s));
+      }
+      prof::Scope sc(prof::kGemm, s, 4.0 * j * bk * bk, 8.0 * 4.0 * j * bk);
+      const int sp = choose_splits(bk, bk, j, ws.splitk_cap, sms);
+      CK(gemm_f64(bk, bk, j, 0.5, MatView{ws.X, ld, 1}, MatView{W, 1, ld}, 0.0, ws.X2, bk, sp, ws.splitk[0], s));
+      CK(gemm_f64(j, bk, bk, 1.0, MatView{Y, 1, ld}, MatView{ws.X2, 1, bk}, 1.0, ws.X, ld, 1, nullptr, s));
+      return 0;
+    }
+    const int BN = split::stream_bn(bk);
+    const int nkb = (j + 31) / 32;
+    {
+      prof::Scope sc(prof::kConvert, s, 0.0, 8.0 * j * bk + 2.0 * S * j * BN);
+      split::PackParams pp{};
+      pp.M1 = W;
+      pp.ld1 = ld;
+      pp.K1 = j;
+      pp.t1 = 1;
+      pp.scale1 = pp.scale2 = 1.0;
+      pp.R = bk;
+      pp.TR = BN;
+      pp.TK = 32;
+      pp.nrb = 1;
+      pp.nkb = nkb;
+      pp.S = S;
+      pp.out = ws.wblob;
+      pp.status = status;
+      CK(split::pack(pp, s));
+    }
+    split::StreamParams sp{};
+    sp.Bblob = ws.wblob;
+    sp.nkb = nkb;
+    sp.N = bk;
+    sp.status = status;
+    sp.limit_ns = o.limit_ns;
+    {
+      // X1 = A2 W, A2 symmetric with its lower triangle stored
+      prof::Scope sc(prof::kSymm, s, symm_flops(j, bk), symm_bytes(j, bk));
+      const int tiles = (j + 127) / 128;
+      int splits = stream_splits(tiles, nkb, sms, kMaxStreamSplits);
+      sp.A = A2;
+      sp.lda = lda;
+      sp.mode = split::kModeSymLower;
+      sp.M = j;
+      sp.K = j;
+      sp.stages_per_split = (nkb + splits - 1) / splits;
+      splits = (nkb + sp.stages_per_split - 1) / sp.stages_per_split;
+      sp.P = ws.P;
+      sp.ldp = j;
+      sp.split_stride = (int64_t)j * bk;
+      CK(split::stream_gemm(sp, S, splits, s));
+      CK(split::reduce(j, bk, splits, ws.P, j, (int64_t)j * bk, 1.0, 0.0, ws.X, ld, s));
+    }
+    prof::Scope sc(prof::kGemm, s, 4.0 * j * bk * bk, 8.0 * 4.0 * j * bk);
+    {
+      // X2 = X1^T W / 2
+      int splits = std::min(kMaxSmallSplits, std::max(1, std::min(sms, nkb / 2)));
+      sp.A = ws.X;
+      sp.lda = ld;
+      sp.mode = split::kModeTrans;
+      sp.M = bk;
+      sp.K = j;
+      sp.stages_per_split = (nkb + splits - 1) / splits;
+      splits = (nkb + sp.stages_per_split - 1) / sp.stages_per_split;
+      sp.P = ws.P;
+      sp.ldp = bk;
+      sp.split_stride = (int64_t)bk * bk;
+      CK(split::stream_gemm(sp, S, splits, s));
+      CK(split::reduce(bk, bk, splits, ws.P, bk, (int64_t)bk * bk, 0.5, 0.0, ws.X2, bk, s));
+    }
+    {
+      // X3 = X1 + Y X2
+      split::PackParams pp{};
+      pp.M1 = ws.X2;
+      pp.ld1 = bk;
+      pp.K1 = bk;
+      pp.t1 = 1;
+      pp.scale1 = pp.scale2 = 1.0;
+      pp.R = bk;
+      pp.TR = BN;
+      pp.TK = 32;
+      pp.nrb = 1;
+      pp.nkb = (bk + 31) / 32;
+      pp.S = S;
+      pp.out = ws.x2blob;
+      pp.status = status;
+      CK(split::pack(pp, s));
+      split::StreamParams s3 = sp;
+      s3.A = Y;
+      s3.lda = ld;
+      s3.mode = split::kModePlain;
+      s3.M = j;
+      s3.K = bk;
+      s3.Bblob = ws.x2blob;
+      s3.nkb = pp.nkb;
+      s3.stages_per_split = pp.nkb;
+      s3.P = ws.P;
+      s3.ldp = j;
+      s3.split_stride = (int64_t)j * bk;
+      CK(split::stream_gemm(s3, S, 1, s));
+      CK(split::reduce(j, bk, 1, ws.P, j, (int64_t)j * bk, 1.0, 1.0, ws.X, ld, s));
+    }
+    {
+      // operands of A2 += X3 Y^T + Y X3^T: [X3 | Y] and [Y | X3]
+      const int Kr = (2 * bk + 63) / 64 * 64;
+      split::PackParams pp{};
+      pp.M1 = ws.X;
+      pp.ld1 = ld;
+      pp.K1 = bk;
+      pp.t1 = 0;
+      pp.M2 = Y;
+      pp.ld2 = ld;
+      pp.K2 = bk;
+      pp.t2 = 0;
+      pp.scale1 = pp.scale2 = 1.0;
+      pp.R = j;
+      pp.TR = 128;
+      pp.TK = 64;
+      pp.nrb = (j + 127) / 128;
+      pp.nkb = Kr / 64;
+      pp.S = S;
+      pp.out = ws.ablob;
+      pp.status = status;
+      CK(split::pack(pp, s));
+      pp.M1 = Y;
+      pp.M2 = ws.X;
+      pp.out = ws.bblob;
+      CK(split::pack(pp, s));
+    }
+    return 0;
+  }
+
+  // A2 += X3 Y^T + Y X3^T on the lower triangle of A2's columns [c0, c1).
+  int syr2k(int64_t k, int buf, int c0, int c1, cudaStream_t s) {
+    const int bk = (int)std::min<int64_t>(o.b, n - w - 1 - k);
+    const int64_t r0 = k + w;
+    const int j = (int)(n - r0);
+    c1 = std::min(c1, j);
+    if (c1 <= c0) return 0;
+    double* A2 = A + r0 + r0 * lda;
+    prof::Scope sc(prof::kSyr2k, s, syr2k_flops(j, c0, c1, bk), syr2k_bytes(j, c0, c1, bk));
+    if (!is_split(o)) {
+      CK(syr2k_lower_f64(j, bk, A2, lda, ws.X, ws.ld, ws.Y[buf], ws.ld, c0, c1, s));
+      return 0;
+    }
+    split::RankParams rp{};
+    rp.Ablob = ws.ablob;
+    rp.Bblob = ws.bblob;
+    rp.Kr = (2 * bk + 63) / 64 * 64;
+    rp.C = A2;
+    rp.ldc = lda;
+    rp.M = j;
+    rp.N = j;
+    rp.col0 = c0;
+    rp.col1 = c1;
+    rp.lower = 1;
+    rp.tj0 = c0 / 128;
+    rp.alpha = 1.0;
+    rp.status = status;
+    rp.limit_ns = o.limit_ns;
+    const int ti = (j + 127) / 128;
+    const int tj = (c1 - 1) / 128 - rp.tj0 + 1;
+    CK(split::rank_update(rp, S, ti, tj, s));
+    return 0;
+  }
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------
 // sy2sb: Section 2.1 loop.  Iteration k: panel A0 = A(k+w:n, k:k+bk) (Eq. updateA0),
 // A1 = A(k+w:n, k+bk:k+w) := A1 + Y (W^T A1) (Eq. updateA1), and the two-sided update of
 // A2 = A(k+w:n, k+w:n) through X1 = A2 W, X2 = X1^T W / 2, X3 = X1 + Y X2,
 // A2 += X3 Y^T + Y X3^T (Eqs. updateA2symm .. updateA2syr2k).
+//
+// Look-ahead (Section 2.2) with two streams: the caller's stream `s` and a highest-
+// priority panel stream.  V2 (2b > w): after X3, the panel stream updates the columns of
+// A2 that hold the next panel (A2^L) and factors it while `s` updates A2^R.  V1 (2b <= w):
+// the next panel lies in A1; the panel stream updates A1^L and factors it while `s`
+// updates A1^R and A2.
 int sy2sb_run(int64_t n, int64_t w, double* A, int64_t lda, double* tau, const Options& o, void* work,
               int* dev_status, cudaStream_t s) {
-  const int sms = current_sms();
-  Sy2sbWs ws = carve_sy2sb(work, n, w, o, sms);
-  int* status = dev_status ? dev_status : ws.status;
-  CK(cudaMemsetAsync(status, 0, sizeof(int), s));
+  Sy2sb R{};
+  R.n = n;
+  R.w = w;
+  R.A = A;
+  R.lda = lda;
+  R.tau = tau;
+  R.o = o;
+  R.sms = current_sms();
+  R.ws = carve_sy2sb(work, n, w, o, R.sms);
+  R.status = dev_status ? dev_status : R.ws.status;
+  R.pmax = panel_max_ctas(R.sms, o);
+  R.S = is_split(o) ? split::slices_of(o.precision) : 0;
+  R.extra = o.debug ? 1u : 0u;
+  if (o.precision == BANDRED_OZAKI) return BANDRED_ERR_UNSUPPORTED;
+  CK(cudaMemsetAsync(R.status, 0, sizeof(int), s));
   const int64_t nref = n - w;
   if (nref <= 0) return 0;
   CK(cudaMemsetAsync(tau, 0, sizeof(double) * nref, s));
   const int b = o.b;
-  const int64_t ld = ws.ld;
-  const int pmax = panel_max_ctas(sms, o);
-  unsigned int extra = o.debug ? 1u : 0u;
-  for (int64_t k = 0; k <= n - w - 2; k += b) {
+  int la = o.lookahead;
+  if (la < 0) la = (2 * b > w) ? 2 : 1;
+  if (la == 1 && 2 * b > w) la = 0;  // V1 needs 2b <= w
+  if (la == 2 && 2 * b <= w) la = 1;
+  const int64_t last = n - w - 2;  // panels start at k <= n-w-2
+
+  if (la == 0) {
+    int buf = 0;
+    for (int64_t k = 0; k <= last; k += b) {
+      const int bk = (int)std::min<int64_t>(b, n - w - 1 - k);
+      int rc = R.panel(k, buf, s);
+      if (rc) return rc;
+      if ((rc = R.update_a1(k, buf, 0, (int)(w - bk), 0, s))) return rc;
+      if ((rc = R.compute_x(k, buf, s))) return rc;
+      if ((rc = R.syr2k(k, buf, 0, (int)(n - k - w), s))) return rc;
+    }
+    return 0;
+  }
+
+  if (last < 0) return 0;  // no panel: every reflector has length <= 1
+  AuxStreams* ax = nullptr;
+  if (int rc = aux_streams(&ax)) return rc;
+  cudaStream_t sp = ax->panel;
+  cudaEvent_t ev_fork = ax->ev[0], ev_panel = ax->ev[1];
+  // The panel stream starts after everything already queued on s.
+  CK(cudaEventRecord(ev_fork, s));
+  CK(cudaStreamWaitEvent(sp, ev_fork, 0));
+  int rc = R.panel(0, 0, sp);
+  if (rc) return rc;
+  CK(cudaEventRecord(ev_panel, sp));
+  int buf = 0;
+  for (int64_t k = 0; k <= last; k += b, buf ^= 1) {
     const int bk = (int)std::min<int64_t>(b, n - w - 1 - k);
-    const int64_t r0 = k + w;
-    const int j = (int)(n - r0);
-    int rc;
-    {
-      prof::Scope sc(prof::kPanel, s, panel_flops(j, bk), panel_bytes(j, bk));
-      rc = run_panel(A + r0 + k * lda, 1, lda, j, bk, tau + k, ws.Y, ws.W, ld, ws.part, ws.rowbuf, ws.part2, ws.gs,
-                     status, o, pmax, extra, s);
-    }
-    if (rc) return rc;
-    extra = 0;
-    const int na1 = (int)(w - bk);
-    if (na1 > 0) {
-      double* A1 = A + r0 + (k + bk) * lda;
-      const int sp = choose_splits(bk, na1, j, ws.splitk_cap, sms);
-      prof::Scope sc(prof::kGemm, s, 4.0 * j * na1 * bk, 8.0 * (2.0 * j * na1 + 2.0 * j * bk));
-      CK(gemm_f64(bk, na1, j, 1.0, MatView{ws.W, ld, 1}, MatView{A1, 1, lda}, 0.0, ws.Z, bk, sp, ws.splitk, s));
-      CK(gemm_f64(j, na1, bk, 1.0, MatView{ws.Y, 1, ld}, MatView{ws.Z, 1, bk}, 1.0, A1, lda, 1, nullptr, s));
-    }
-    double* A2 = A + r0 + r0 * lda;
-    {
-      prof::Scope sc(prof::kSymm, s, symm_flops(j, bk), symm_bytes(j, bk));
-      CK(symm_lower_f64(j, bk, A2, lda, ws.W, ld, ws.X, ld, s));
-    }
-    {
-      prof::Scope sc(prof::kGemm, s, 4.0 * j * bk * bk, 8.0 * 4.0 * j * bk);
-      const int sp = choose_splits(bk, bk, j, ws.splitk_cap, sms);
-      CK(gemm_f64(bk, bk, j, 0.5, MatView{ws.X, ld, 1}, MatView{ws.W, 1, ld}, 0.0, ws.X2, bk, sp, ws.splitk, s));
-      CK(gemm_f64(j, bk, bk, 1.0, MatView{ws.Y, 1, ld}, MatView{ws.X2, 1, bk}, 1.0, ws.X, ld, 1, nullptr, s));
-    }
-    {
-      prof::Scope sc(prof::kSyr2k, s, syr2k_flops(j, 0, j, bk), syr2k_bytes(j, 0, j, bk));
-      CK(syr2k_lower_f64(j, bk, A2, lda, ws.X, ld, ws.Y, ld, 0, j, s));
+    const int64_t kn = k + b;  // next panel
+    const bool has_next = kn <= last;
+    const int bkn = has_next ? (int)std::min<int64_t>(b, n - w - 1 - kn) : 0;
+    CK(cudaStreamWaitEvent(s, ev_panel, 0));  // panel k done
+    const int j = (int)(n - k - w);
+    if (la == 2) {
+      // V2: A1 (if any), X1..X3 on s; then A2^L + next panel on sp, A2^R on s.
+      if ((rc = R.update_a1(k, buf, 0, (int)(w - bk), 0, s))) return rc;
+      if ((rc = R.compute_x(k, buf, s))) return rc;
+      const int cL = has_next ? (int)std::max<int64_t>(0, b - w + bkn) : 0;
+      if (has_next && cL > 0) {
+        CK(cudaEventRecord(ev_fork, s));
+        CK(cudaStreamWaitEvent(sp, ev_fork, 0));
+        if ((rc = R.syr2k(k, buf, 0, cL, sp))) return rc;
+        if ((rc = R.panel(kn, buf ^ 1, sp))) return rc;
+        CK(cudaEventRecord(ev_panel, sp));
+        if ((rc = R.syr2k(k, buf, cL, j, s))) return rc;
+      } else {
+        if ((rc = R.syr2k(k, buf, 0, j, s))) return rc;
+        if (has_next) {
+          if ((rc = R.panel(kn, buf ^ 1, s))) return rc;
+          CK(cudaEventRecord(ev_panel, s));
+        }
+      }
+    } else {
+      // V1: the next panel lies in A1 columns [0, bkn) (relative to A1).
+      if (has_next) {
+        CK(cudaEventRecord(ev_fork, s));  // iteration k-1's update is complete on s
+        CK(cudaStreamWaitEvent(sp, ev_fork, 0));
+        if ((rc = R.update_a1(k, buf, 0, bkn, 1, sp))) return rc;
+        if ((rc = R.panel(kn, buf ^ 1, sp))) return rc;
+        CK(cudaEventRecord(ev_panel, sp));
+      }
+      if ((rc = R.update_a1(k, buf, has_next ? bkn : 0, (int)(w - bk), 0, s))) return rc;
+      if ((rc = R.compute_x(k, buf, s))) return rc;
+      if ((rc = R.syr2k(k, buf, 0, j, s))) return rc;
     }
   }
+  // Join: everything issued on the panel stream is ordered before later work on s.
+  CK(cudaEventRecord(ev_fork, sp));
+  CK(cudaStreamWaitEvent(s, ev_fork, 0));
   return 0;
 }
 

@@ -18,7 +18,7 @@ struct PanelParams {
   double* Y;             // j x bk, column-major, ld = ldy (unit lower trapezoidal copy of V)
   double* W;             // j x bk, column-major, ld = ldy (W = -Y T)
   int64_t ldy;
-  double* part;          // 2 * G * (bk + 1) doubles
+  double* acc;           // 3 * (bk + 1) * 32 doubles, directly after *gs (zeroed with it)
   double* rowbuf;        // 2 * bk doubles
   double* part2;         // G doubles
   GridSync* gs;
@@ -29,6 +29,7 @@ struct PanelParams {
 };
 
 size_t panel_smem_bytes(int bk, int Rp, bool w_in_smem);
+size_t panel_sync_bytes(int bk);  // bytes from gs to the end of acc
 int panel_geometry(int j, int bk, int max_ctas, int min_rows, int* G, int* R, int* Rp, bool* w_in_smem);
 cudaError_t launch_panel(const PanelParams& p, int G, cudaStream_t s);
 

@@ -12,10 +12,12 @@
 //   Each CTA keeps a contiguous slab of the panel's rows in shared memory.  For reflector
 //   i the CTAs compute, over their rows below row i, the dot products of column i with
 //   every panel column (column i itself gives ||x2||^2; earlier columns give the entries
-//   Y^T y_i needed for T; later columns give v^T a_c for the in-panel update), publish
-//   them together with row i, and meet at one grid-wide barrier.  After it every CTA
-//   sums the published partials in the same fixed order, so all of them derive the same
-//   beta, tau and coefficients and update their own rows without further communication.
+//   Y^T y_i needed for T; later columns give v^T a_c for the in-panel update), add them
+//   into accumulators in L2, publish row i, and meet at one grid-wide barrier.  After it
+//   every CTA reads the same sums, derives the same beta, tau and coefficients, and
+//   updates its own rows without further communication.  GB300 issues FP64 at two
+//   operations per clock per SM, so the kernel keeps FP64 instructions to the FMAs the
+//   method needs (no per-CTA re-summation of partials, hoisted scalings).
 //   W's column i follows from the recurrence W(:, i) = -tau_i (y_i + W(:, 0:i) Y(:, 0:i)^T y_i),
 //   which equals -Y T with T built column by column as in the compact-WY definition.
 #include <cmath>
@@ -30,11 +32,18 @@ namespace {
 
 constexpr int kPanelThreads = 256;
 
+// The per-reflector reductions are accumulated with FP64 atomic adds in L2 (one value per
+// 256-byte line, three rotating buffers), so no CTA spends its FP64 pipe on summing the
+// partials of the others.  The order of those additions is not fixed: results agree
+// across runs to rounding, not bit for bit.
+constexpr int kAccStride = 32;  // doubles between accumulated values (one 256-byte line)
+
+__device__ __forceinline__ void red_add(double* p, double v) { atomicAdd(p, v); }
+
 __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams p) {
   extern __shared__ double smem[];
   constexpr int NT = kPanelThreads;
-  constexpr int NW = NT / 32;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x, lane = tid & 31;
   const int G = gridDim.x, g = blockIdx.x;
   const int bk = p.bk, Rp = p.Rp;
   const int rb = g * p.R;
@@ -43,12 +52,12 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
   double* dsum = slab + (size_t)bk * Rp;      // bk + 1 combined sums
   double* rowi = dsum + bk + 1;               // row i of the panel
   double* coef = rowi + bk;                   // z_c (c > i) and Y^T y_i (p < i)
-  double* red2 = coef + bk;                   // NT partial sums of the combine
+  double* coef2 = coef + bk;                  // -z_c * scal (c > i)
   // This CTA's rows of W: in shared memory when they fit, else in the W output itself.
-  double* wl = p.w_in_smem ? red2 + NT : p.W + rb;
+  double* wl = p.w_in_smem ? coef2 + bk : p.W + rb;
   const int64_t wld = p.w_in_smem ? Rp : p.ldy;
   __shared__ double s_beta, s_tau, s_scal, s_xnorm;
-  __shared__ double s_red[NW];
+  __shared__ double s_red[NT / 32];
   __shared__ int s_rescale;
 
   if (p.rs == 1) {
@@ -64,68 +73,49 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
   }
   __syncthreads();
 
+  // Threads per column in the dot products (a power of two dividing 32).
+  const int TPC = bk >= 128 ? 2 : (bk >= 64 ? 4 : 8);
+  const int CPP = NT / TPC;  // columns per pass
+  const int sub = tid % TPC;
+  const size_t accsz = (size_t)(bk + 1) * kAccStride;
   unsigned int gen = 0;
-  const size_t pstride = (size_t)bk + 1;
   for (int i = 0; i < bk; ++i) {
-    const int buf = i & 1;
-    double* part = p.part + (size_t)buf * G * pstride;
-    double* rowg = p.rowbuf + (size_t)buf * bk;
+    double* acc = p.acc + (size_t)(i % 3) * accsz;
+    double* rowg = p.rowbuf + (size_t)(i & 1) * bk;
     const int lo = min(max(i + 1 - rb, 0), nr);
     const double* xi = slab + (size_t)i * Rp;
     const bool own_row = (i >= rb) && (i < rb + nr);
+    if (g == 0) {  // clear the buffer of step i+1 (last read at step i-2, before barrier i-1)
+      double* nxt = p.acc + (size_t)((i + 1) % 3) * accsz;
+      for (int v = tid; v <= bk; v += NT) nxt[(size_t)v * kAccStride] = 0.0;
+    }
 
     // Partial dot products of x2 = column i below row i with every panel column.
-    for (int c = warp; c < bk; c += NW) {
-      const double* ac = slab + (size_t)c * Rp;
-      double s = 0.0, m = 0.0;
-      for (int r = lo + lane; r < nr; r += 32) {
-        const double x = xi[r];
-        s = fma(x, ac[r], s);
-        m = fmax(m, fabs(x));
+    for (int c0 = 0; c0 < bk; c0 += CPP) {
+      const int c = c0 + tid / TPC;
+      double s = 0.0;
+      if (c < bk) {
+        const double* ac = slab + (size_t)c * Rp;
+        for (int r = lo + sub; r < nr; r += TPC) s = fma(xi[r], ac[r], s);
       }
-      s = warp_sum(s);
-      if (lane == 0) __stcg(&part[(size_t)g * pstride + c], s);
-      if (c == i) {
-        m = warp_max(m);
-        if (lane == 0) __stcg(&part[(size_t)g * pstride + bk], m);
-      }
+      for (int o = TPC / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (sub == 0 && c < bk) red_add(&acc[(size_t)c * kAccStride], s);
+    }
+    // max |x2| (decides whether the plain sum of squares is safe): one warp
+    if (tid < 32) {
+      double m = 0.0;
+      for (int r = lo + lane; r < nr; r += 32) m = fmax(m, fabs(xi[r]));
+      m = warp_max(m);
+      if (lane == 0)
+        atomicMax(reinterpret_cast<unsigned long long*>(&acc[(size_t)bk * kAccStride]),
+                  (unsigned long long)__double_as_longlong(m));
     }
     if (own_row)
       for (int c = tid; c < bk; c += NT) __stcg(&rowg[c], slab[(size_t)c * Rp + (i - rb)]);
 
     if (!grid_barrier(p.gs, ++gen, p.extra, p.status, p.limit_ns)) return;
 
-    // Combine in a fixed order: every CTA obtains bit-identical sums.  Thread t sums
-    // value t % (bk+1) over every ngrp-th CTA (coalesced, independent loads), then the
-    // ngrp partial sums of each value are added in order.
-    {
-      const int VP = bk + 1;
-      const int ngrp = NT / VP;
-      if (tid < ngrp * VP) {
-        const int v = tid % VP, grp = tid / VP;
-        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-        int q = grp;
-        if (v < bk) {
-          for (; q + 3 * ngrp < G; q += 4 * ngrp) {
-            s0 += ldcg(&part[(size_t)q * pstride + v]);
-            s1 += ldcg(&part[(size_t)(q + ngrp) * pstride + v]);
-            s2 += ldcg(&part[(size_t)(q + 2 * ngrp) * pstride + v]);
-            s3 += ldcg(&part[(size_t)(q + 3 * ngrp) * pstride + v]);
-          }
-          for (; q < G; q += ngrp) s0 += ldcg(&part[(size_t)q * pstride + v]);
-          red2[tid] = (s0 + s1) + (s2 + s3);
-        } else {
-          for (; q < G; q += ngrp) s0 = fmax(s0, ldcg(&part[(size_t)q * pstride + v]));
-          red2[tid] = s0;
-        }
-      }
-      __syncthreads();
-      if (tid < VP) {
-        double s = red2[tid];
-        for (int g2 = 1; g2 < ngrp; ++g2) s = (tid < bk) ? s + red2[g2 * VP + tid] : fmax(s, red2[g2 * VP + tid]);
-        dsum[tid] = s;
-      }
-    }
+    for (int v = tid; v <= bk; v += NT) dsum[v] = ldcg(&acc[(size_t)v * kAccStride]);
     for (int c = tid; c < bk; c += NT) rowi[c] = ldcg(&rowg[c]);
     __syncthreads();
 
@@ -144,15 +134,15 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
         s = fma(t, t, s);
       }
       s = warp_sum(s);
-      if (lane == 0) s_red[warp] = s;
+      if (lane == 0) s_red[tid >> 5] = s;
       __syncthreads();
       if (tid == 0) {
         double t = 0.0;
-        for (int q = 0; q < NW; ++q) t += s_red[q];
+        for (int q = 0; q < NT / 32; ++q) t += s_red[q];
         __stcg(&p.part2[g], t);
       }
       if (!grid_barrier(p.gs, ++gen, p.extra, p.status, p.limit_ns)) return;
-      if (warp == 0) {
+      if (tid < 32) {
         double t = 0.0;
         for (int q = lane; q < G; q += 32) t += ldcg(&p.part2[q]);
         t = warp_sum(t);
@@ -180,8 +170,13 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
     __syncthreads();
     const double tau = s_tau, scal = s_scal;
     for (int c = tid; c < bk; c += NT) {
-      if (c > i) coef[c] = tau * (rowi[c] + scal * dsum[c]);  // tau * v^T a_c
-      else if (c < i) coef[c] = rowi[c] + scal * dsum[c];     // (Y^T y_i)_c
+      if (c > i) {
+        const double z = tau * (rowi[c] + scal * dsum[c]);  // tau * v^T a_c
+        coef[c] = z;
+        coef2[c] = -z * scal;
+      } else if (c < i) {
+        coef[c] = rowi[c] + scal * dsum[c];  // (Y^T y_i)_c
+      }
     }
     __syncthreads();
 
@@ -190,7 +185,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
       const int nrow = nr - lo, ncol = bk - i - 1;
       for (int idx = tid; idx < nrow * ncol; idx += NT) {
         const int r = lo + idx % nrow, c = i + 1 + idx / nrow;
-        slab[(size_t)c * Rp + r] = fma(-coef[c] * scal, xi[r], slab[(size_t)c * Rp + r]);
+        slab[(size_t)c * Rp + r] = fma(coef2[c], xi[r], slab[(size_t)c * Rp + r]);
       }
       if (own_row)
         for (int c = i + 1 + tid; c < bk; c += NT) slab[(size_t)c * Rp + (i - rb)] -= coef[c];
@@ -249,8 +244,10 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
 }  // namespace
 
 size_t panel_smem_bytes(int bk, int Rp, bool w_in_smem) {
-  return ((size_t)bk * Rp * (w_in_smem ? 2 : 1) + 3 * (size_t)bk + 1 + kPanelThreads) * sizeof(double);
+  return ((size_t)bk * Rp * (w_in_smem ? 2 : 1) + 4 * (size_t)bk + 1) * sizeof(double);
 }
+
+size_t panel_sync_bytes(int bk) { return 256 + 3 * (size_t)(bk + 1) * kAccStride * sizeof(double); }
 
 int panel_geometry(int j, int bk, int max_ctas, int min_rows, int* G, int* R, int* Rp, bool* w_in_smem) {
   if (j <= 0 || bk <= 0) return -1;
@@ -287,7 +284,8 @@ cudaError_t launch_panel(const PanelParams& prm, int G, cudaStream_t s) {
   }
   const size_t smem = panel_smem_bytes(prm.bk, prm.Rp, prm.w_in_smem);
   if (smem > max_dynamic) return cudaErrorInvalidValue;
-  cudaError_t e = cudaMemsetAsync(prm.gs, 0, sizeof(GridSync), s);
+  // barrier counters and the first accumulator buffer (contiguous, see PanelParams)
+  cudaError_t e = cudaMemsetAsync(prm.gs, 0, panel_sync_bytes(prm.bk), s);
   if (e != cudaSuccess) return e;
   PanelParams p = prm;
   void* args[] = {&p};

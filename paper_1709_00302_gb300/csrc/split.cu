@@ -33,6 +33,8 @@ constexpr int NT = 256;
 constexpr int BM = 128;       // rows of a C tile (TMEM lanes)
 constexpr int BK = 32;        // reduction depth of one pipeline stage
 constexpr int kChunk = 256;   // FP32 accumulation length before FP64 recombination
+constexpr int RS = BM + 1;    // k-stride (doubles) of a staged FP64 tile: conflict-free
+                              // for both the row-contiguous and the column-contiguous fill
 constexpr int CH = kChunk / BK;
 
 __device__ __forceinline__ void report(int* status, int code) {
@@ -105,7 +107,7 @@ struct Products<3> {
 template <int BN, int S, int NSTAGE>
 struct StreamSmem {
   static constexpr int NB = NSTAGE + 1;
-  static constexpr size_t fp64_bytes = (size_t)NSTAGE * BK * BM * 8;
+  static constexpr size_t fp64_bytes = ((size_t)NSTAGE * BK * RS * 8 + 1023) / 1024 * 1024;
   static constexpr size_t aslice_bytes = (size_t)BM * BK * 2;  // one slice, one stage
   static constexpr size_t bslice_bytes = (size_t)BN * BK * 2;
   static constexpr size_t off_a = fp64_bytes;
@@ -155,7 +157,7 @@ __global__ void __launch_bounds__(NT, 1) stream_gemm_kernel(StreamParams p) {
   auto issue_loads = [&](int ls) {
     const int kst = st_begin + ls;
     const int k0 = kst * BK;
-    double* dst = ring + (size_t)(ls % NSTAGE) * BK * BM;
+    double* dst = ring + (size_t)(ls % NSTAGE) * BK * RS;
     const double* A = p.A;
     const int64_t lda = p.lda;
     bool lower_map = true;
@@ -175,7 +177,7 @@ __global__ void __launch_bounds__(NT, 1) stream_gemm_kernel(StreamParams p) {
           else
             src = A + gi + (int64_t)gk * lda;
         }
-        tc::cp_async8(dst + k * BM + i, src, in ? 8u : 0u);
+        tc::cp_async8(dst + k * RS + i, src, in ? 8u : 0u);
       }
     } else {
 #pragma unroll 4
@@ -184,7 +186,7 @@ __global__ void __launch_bounds__(NT, 1) stream_gemm_kernel(StreamParams p) {
         const int gi = i0 + i, gk = k0 + k;
         const bool in = gi < p.M && gk < p.K;
         const double* src = in ? A + gk + (int64_t)gi * lda : A;
-        tc::cp_async8(dst + k * BM + i, src, in ? 8u : 0u);
+        tc::cp_async8(dst + k * RS + i, src, in ? 8u : 0u);
       }
     }
     // B slices of this stage: S * BN * BK bf16, contiguous in the packed blob.
@@ -213,13 +215,13 @@ __global__ void __launch_bounds__(NT, 1) stream_gemm_kernel(StreamParams p) {
           float v[32];
           tc::tmem_ld32(taddr + part * 32, v);
 #pragma unroll
-          for (int cc = 0; cc < 32; ++cc) acc[part * 32 + cc] += (double)v[cc];
+          for (int cc = 0; cc < 32; ++cc) acc[part * 32 + cc] += tc::f32_to_f64(v[cc]);
         }
       } else {
         float v[16];
         tc::tmem_ld16(taddr, v);
 #pragma unroll
-        for (int cc = 0; cc < 16; ++cc) acc[cc] += (double)v[cc];
+        for (int cc = 0; cc < 16; ++cc) acc[cc] += tc::f32_to_f64(v[cc]);
       }
     }
     tc::fence_before_sync();
@@ -247,7 +249,7 @@ __global__ void __launch_bounds__(NT, 1) stream_gemm_kernel(StreamParams p) {
 
     // ---- convert the FP64 stage into S bf16 slices (K-major core layout)
     {
-      const double* src = ring + (size_t)(st % NSTAGE) * BK * BM;
+      const double* src = ring + (size_t)(st % NSTAGE) * BK * RS;
       unsigned char* adst = aslices + (size_t)sb * S * L::aslice_bytes;
 #pragma unroll
       for (int q = 0; q < (BM * (BK / 8)) / NT; ++q) {
@@ -256,8 +258,8 @@ __global__ void __launch_bounds__(NT, 1) stream_gemm_kernel(StreamParams p) {
 #pragma unroll
         for (int kk = 0; kk < 8; kk += 2) {
           __nv_bfloat16 a[S], b[S];
-          range_ok &= tc::split_bf16<S>(src[(kg * 8 + kk) * BM + i], a);
-          range_ok &= tc::split_bf16<S>(src[(kg * 8 + kk + 1) * BM + i], b);
+          range_ok &= tc::split_bf16<S>(src[(kg * 8 + kk) * RS + i], a);
+          range_ok &= tc::split_bf16<S>(src[(kg * 8 + kk + 1) * RS + i], b);
 #pragma unroll
           for (int s = 0; s < S; ++s)
             words[s][kk / 2] = (uint32_t)__bfloat16_as_ushort(a[s]) | ((uint32_t)__bfloat16_as_ushort(b[s]) << 16);
@@ -415,14 +417,23 @@ __global__ void __launch_bounds__(NT) rank_update_kernel(RankParams p) {
     for (int part = 0; part < 2; ++part) {
       float v[32];
       tc::tmem_ld32(taddr + part * 32, v);
-      if (row < p.M) {
+      const int colb = J * BM + h * 64 + part * 32;
+      // Issue all loads of this thread's 32 entries before any store (independent
+      // accesses: one memory latency instead of 32).
+      double old[32];
 #pragma unroll
-        for (int c = 0; c < 32; ++c) {
-          const int col = J * BM + h * 64 + part * 32 + c;
-          if (col < p.N && col >= p.col0 && col < p.col1 && (!p.lower || row >= col)) {
-            double* cp = p.C + row + (int64_t)col * p.ldc;
-            *cp = fma(p.alpha, (double)v[c], *cp);
-          }
+      for (int c = 0; c < 32; ++c) {
+        const int col = colb + c;
+        const bool in = row < p.M && col < p.N && col >= p.col0 && col < p.col1 && (!p.lower || row >= col);
+        old[c] = in ? p.C[row + (int64_t)col * p.ldc] : 0.0;
+      }
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        const int col = colb + c;
+        const bool in = row < p.M && col < p.N && col >= p.col0 && col < p.col1 && (!p.lower || row >= col);
+        if (in) {
+          const double d = tc::f32_to_f64(v[c]);
+          p.C[row + (int64_t)col * p.ldc] = (p.alpha == 1.0) ? old[c] + d : fma(p.alpha, d, old[c]);
         }
       }
     }

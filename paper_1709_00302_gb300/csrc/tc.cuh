@@ -153,6 +153,21 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// FP32 -> FP64 by bit manipulation: the conversion instruction runs on the FP64 pipe,
+// which GB300 issues at two operations per clock per SM.  Zero, subnormal, infinite and
+// NaN inputs take the ordinary conversion.
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xFFu;
+  if (e == 0u || e == 0xFFu) {
+    if ((u & 0x7FFFFFFFu) == 0u) return __longlong_as_double((long long)((unsigned long long)(u & 0x80000000u) << 32));
+    return (double)f;
+  }
+  const unsigned long long d = ((unsigned long long)(u & 0x80000000u) << 32) |
+                               ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)d);
+}
+
 // ---------------------------------------------------------------- FP64 -> bf16 slices
 // x ~= s0 + s1 (+ s2): s0 is x truncated to bf16 (8 significant bits, exponent kept),
 // s1 = bf16_rn(x - s0), s2 = bf16_rn(x - s0 - s1).  Integer and FP32 operations only (the
