@@ -37,33 +37,62 @@ __device__ __forceinline__ void red_release_add(unsigned int* p, unsigned int v)
 // awaited (0 in normal use; a positive value makes the wait unsatisfiable, which is how
 // the tests exercise the timeout path).  Returns false when the wait timed out or
 // another CTA aborted; the caller must then return without touching shared results.
+// Ordering: the CTA's writes before the call happen before its release-add (bar.sync,
+// then a gpu-scope release by thread 0); the acquire-load that sees the final count makes
+// every other CTA's writes visible to this CTA after the closing bar.sync.
 __device__ __forceinline__ bool grid_barrier(GridSync* gs, unsigned int generation, unsigned int extra,
                                              int* status, unsigned long long limit_ns) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    __threadfence();
     red_release_add(&gs->count, 1u);
     const unsigned int target = generation * (gridDim.x + extra);
-    const unsigned long long t0 = global_ns();
+    unsigned long long t0 = 0;
     unsigned int spins = 0;
     while (true) {
       if (ld_acquire_gpu(&gs->count) >= target) break;
-      if (ld_acquire_gpu(&gs->abort) != 0u) { ok = 0; break; }
-      if ((++spins & 63u) == 0u && global_ns() - t0 > limit_ns) {
-        atomicExch(&gs->abort, 1u);
-        if (status) atomicCAS(status, 0, BANDRED_DEV_TIMEOUT);
-        ok = 0;
-        break;
+      if ((++spins & 15u) == 0u) {
+        if (ld_acquire_gpu(&gs->abort) != 0u) { ok = 0; break; }
+        const unsigned long long t = global_ns();
+        if (t0 == 0) t0 = t;
+        else if (t - t0 > limit_ns) {
+          atomicExch(&gs->abort, 1u);
+          if (status) atomicCAS(status, 0, BANDRED_DEV_TIMEOUT);
+          ok = 0;
+          break;
+        }
       }
-      __nanosleep(20);
     }
-    __threadfence();
     s_ok = ok;
   }
   __syncthreads();
   return s_ok != 0;
+}
+
+// The two halves of grid_barrier, for CTAs that overlap independent work with the wait:
+// grid_arrive (thread 0 only, after a __syncthreads that follows the writes to publish)
+// and grid_wait (thread 0 only; the caller follows it with a __syncthreads).
+__device__ __forceinline__ void grid_arrive(GridSync* gs) { red_release_add(&gs->count, 1u); }
+
+__device__ __forceinline__ bool grid_wait(GridSync* gs, unsigned int generation, unsigned int extra, int* status,
+                                          unsigned long long limit_ns) {
+  const unsigned int target = generation * (gridDim.x + extra);
+  unsigned long long t0 = 0;
+  unsigned int spins = 0;
+  while (true) {
+    if (ld_acquire_gpu(&gs->count) >= target) return true;
+    if ((++spins & 15u) == 0u) {
+      if (ld_acquire_gpu(&gs->abort) != 0u) return false;
+      const unsigned long long t = global_ns();
+      if (t0 == 0) t0 = t;
+      else if (t - t0 > limit_ns) {
+        atomicExch(&gs->abort, 1u);
+        if (status) atomicCAS(status, 0, BANDRED_DEV_TIMEOUT);
+        return false;
+      }
+    }
+  }
 }
 
 __device__ __forceinline__ double warp_sum(double v) {

@@ -247,6 +247,7 @@ static int run_panel(double* A, int64_t rs, int64_t cs, int j, int bk, double* t
   p.limit_ns = o.limit_ns;
   p.extra = extra;
   p.w_in_smem = w_smem;
+  p.w_fp32 = is_split(o);
   CK(launch_panel(p, G, s));
   return 0;
 }

@@ -24,6 +24,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "tc.cuh"
 #include "prof.h"
 
 namespace bandred {
@@ -38,7 +39,98 @@ constexpr int kPanelThreads = 256;
 // across runs to rounding, not bit for bit.
 constexpr int kAccStride = 32;  // doubles between accumulated values (one 256-byte line)
 
-__device__ __forceinline__ void red_add(double* p, double v) { atomicAdd(p, v); }
+// Reciprocal square root and reciprocal of a positive normal FP64 number: an FP32
+// hardware estimate of the mantissa's value (exponent handled with integer operations)
+// refined by two Newton steps in FP64.  Each FP64 instruction costs tens of cycles on
+// this GPU; this takes 6 (rsqrt) and 4 (reciprocal) of them, about half the library's.
+__device__ __forceinline__ double rsqrt_newton(double q) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(q);
+  const int e = (int)((u >> 52) & 0x7FF) - 1023;
+  const int k = e >> 1;  // floor(e / 2)
+  const int em = e - 2 * k;  // 0 or 1: q = m 2^(2k), m in [1, 4)
+  const double m = __longlong_as_double((long long)((u & 0x000FFFFFFFFFFFFFull) | ((unsigned long long)(1023 + em) << 52)));
+  const double hm = __longlong_as_double((long long)((u & 0x000FFFFFFFFFFFFFull) | ((unsigned long long)(1022 + em) << 52)));
+  (void)m;
+  const float mf = __uint_as_float(((uint32_t)(127 + em) << 23) | (uint32_t)((u >> 29) & 0x7FFFFFu));
+  double r = tc::f32_to_f64(rsqrtf(mf));
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const double t = fma(-hm, r * r, 1.5);
+    r = r * t;
+  }
+  return __longlong_as_double(__double_as_longlong(r) - ((long long)k << 52));
+}
+
+__device__ __forceinline__ double rcp_newton(double s) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(s);
+  const int e = (int)((u >> 52) & 0x7FF) - 1023;
+  const double m = __longlong_as_double((long long)((u & 0x000FFFFFFFFFFFFFull) | (1023ull << 52)));
+  const float mf = __uint_as_float((127u << 23) | (uint32_t)((u >> 29) & 0x7FFFFFu));
+  double r = tc::f32_to_f64(__frcp_rn(mf));
+#pragma unroll
+  for (int it = 0; it < 2; ++it) r = fma(r, fma(-m, r, 1.0), r);
+  return __longlong_as_double(__double_as_longlong(r) - ((long long)e << 52));
+}
+
+// FP64 -> FP32 by integer truncation of the mantissa (no FP64 instruction); values
+// outside FP32's normal range take the ordinary conversion.
+__device__ __forceinline__ float f64_to_f32_rz(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((u >> 52) & 0x7FF) - 1023;
+  if (e < -126 || e > 127) return (float)x;
+  return __uint_as_float((uint32_t)((u >> 32) & 0x80000000u) | ((uint32_t)(e + 127) << 23) |
+                         (uint32_t)((u >> 29) & 0x7FFFFFu));
+}
+
+// W(:, i) in FP32 (used when W only feeds split-precision products, whose bf16 slices
+// keep 24 bits): same recurrence, eight lanes per row.
+__device__ __forceinline__ void w_column_f32(int i, float tau, const float* g, const double* slab, int Rp, int rb,
+                                             int nr, float* wl) {
+  constexpr int PARTS = 8;
+  const int part = threadIdx.x % PARTS;
+  for (int r0 = 0; r0 < nr; r0 += kPanelThreads / PARTS) {
+    const int r = r0 + threadIdx.x / PARTS;
+    float s = 0.f;
+    if (r < nr)
+      for (int q = part; q < i; q += PARTS) s = fmaf(wl[r + q * Rp], g[q], s);
+#pragma unroll
+    for (int o = PARTS / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (part == 0 && r < nr) {
+      const int gr = rb + r;
+      const float y = gr > i ? f64_to_f32_rz(slab[(size_t)i * Rp + r]) : (gr == i ? 1.f : 0.f);
+      wl[r + i * Rp] = -tau * (y + s);
+    }
+  }
+}
+
+// W(:, i) = -tau_i (y_i + W(:, 0:i) g) for this CTA's rows, g = Y(:, 0:i)^T y_i.  Eight
+// lanes share a row (each sums every eighth term), so every warp of the CTA takes part:
+// an FP64 instruction costs the same pipe time whether one lane or 32 are active.
+__device__ __forceinline__ void w_column(int i, double tau, const double* g, const double* slab, int Rp, int rb,
+                                         int nr, double* wl, int64_t wld) {
+  constexpr int PARTS = 8;
+  const int part = threadIdx.x % PARTS;
+  for (int r0 = 0; r0 < nr; r0 += kPanelThreads / PARTS) {
+    const int r = r0 + threadIdx.x / PARTS;
+    double s0 = 0.0, s1 = 0.0;
+    if (r < nr) {
+      int q = part;
+      for (; q + PARTS < i; q += 2 * PARTS) {
+        s0 = fma(wl[r + (int64_t)q * wld], g[q], s0);
+        s1 = fma(wl[r + (int64_t)(q + PARTS) * wld], g[q + PARTS], s1);
+      }
+      if (q < i) s0 = fma(wl[r + (int64_t)q * wld], g[q], s0);
+    }
+    s0 += s1;
+#pragma unroll
+    for (int o = PARTS / 2; o > 0; o >>= 1) s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    if (part == 0 && r < nr) {
+      const int gr = rb + r;
+      const double y = gr > i ? slab[(size_t)i * Rp + r] : (gr == i ? 1.0 : 0.0);
+      wl[r + (int64_t)i * wld] = -tau * (y + s0);
+    }
+  }
+}
 
 __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams p) {
   extern __shared__ double smem[];
@@ -51,14 +143,20 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
   double* slab = smem;                        // bk columns x Rp rows
   double* dsum = slab + (size_t)bk * Rp;      // bk + 1 combined sums
   double* rowi = dsum + bk + 1;               // row i of the panel
-  double* coef = rowi + bk;                   // z_c (c > i) and Y^T y_i (p < i)
+  double* coef = rowi + bk;                   // z_c (c > i) and, for c < i, Y^T y_i
   double* coef2 = coef + bk;                  // -z_c * scal (c > i)
-  // This CTA's rows of W: in shared memory when they fit, else in the W output itself.
-  double* wl = p.w_in_smem ? coef2 + bk : p.W + rb;
+  double* gprev = coef2 + bk;                 // Y^T y of the previous reflector (for W)
+  float* gprevf = reinterpret_cast<float*>(gprev + bk);  // the same in FP32 (bk floats)
+  double* after = gprev + bk + (bk + 1) / 2;
+  // This CTA's rows of W: in shared memory when they fit (FP32 when p.w_fp32), else in
+  // the W output itself.
+  const bool wf32 = p.w_in_smem && p.w_fp32;
+  double* wl = p.w_in_smem ? after : p.W + rb;
+  float* wlf = reinterpret_cast<float*>(after);
   const int64_t wld = p.w_in_smem ? Rp : p.ldy;
-  __shared__ double s_beta, s_tau, s_scal, s_xnorm;
+  __shared__ double s_beta, s_tau, s_scal, s_tau_prev;
   __shared__ double s_red[NT / 32];
-  __shared__ int s_rescale;
+  __shared__ int s_rescale, s_ok;
 
   if (p.rs == 1) {
     for (int idx = tid; idx < nr * bk; idx += NT) {
@@ -90,44 +188,90 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
       for (int v = tid; v <= bk; v += NT) nxt[(size_t)v * kAccStride] = 0.0;
     }
 
-    // Partial dot products of x2 = column i below row i with every panel column.
+    // Partial dot products of x2 = column i below row i with every panel column, added
+    // into the L2 accumulators (two independent FMA chains per thread).
     for (int c0 = 0; c0 < bk; c0 += CPP) {
       const int c = c0 + tid / TPC;
-      double s = 0.0;
+      double s = 0.0, t = 0.0;
       if (c < bk) {
         const double* ac = slab + (size_t)c * Rp;
-        for (int r = lo + sub; r < nr; r += TPC) s = fma(xi[r], ac[r], s);
+        int r = lo + sub;
+        for (; r + TPC < nr; r += 2 * TPC) {
+          s = fma(xi[r], ac[r], s);
+          t = fma(xi[r + TPC], ac[r + TPC], t);
+        }
+        if (r < nr) s = fma(xi[r], ac[r], s);
       }
+      s += t;
       for (int o = TPC / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (sub == 0 && c < bk) red_add(&acc[(size_t)c * kAccStride], s);
+      if (sub == 0 && c < bk) atomicAdd(&acc[(size_t)c * kAccStride], s);
     }
-    // max |x2| (decides whether the plain sum of squares is safe): one warp
+    // max |x2| by integer comparison of the bit patterns (no FP64 instruction): one warp
     if (tid < 32) {
-      double m = 0.0;
-      for (int r = lo + lane; r < nr; r += 32) m = fmax(m, fabs(xi[r]));
-      m = warp_max(m);
-      if (lane == 0)
-        atomicMax(reinterpret_cast<unsigned long long*>(&acc[(size_t)bk * kAccStride]),
-                  (unsigned long long)__double_as_longlong(m));
+      unsigned long long m = 0ull;
+      for (int r = lo + lane; r < nr; r += 32) {
+        const unsigned long long u = (unsigned long long)__double_as_longlong(xi[r]) & 0x7FFFFFFFFFFFFFFFull;
+        m = u > m ? u : m;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long v = __shfl_xor_sync(0xffffffffu, m, o);
+        m = v > m ? v : m;
+      }
+      if (lane == 0) atomicMax(reinterpret_cast<unsigned long long*>(&acc[(size_t)bk * kAccStride]), m);
     }
     if (own_row)
       for (int c = tid; c < bk; c += NT) __stcg(&rowg[c], slab[(size_t)c * Rp + (i - rb)]);
-
-    if (!grid_barrier(p.gs, ++gen, p.extra, p.status, p.limit_ns)) return;
-
-    for (int v = tid; v <= bk; v += NT) dsum[v] = ldcg(&acc[(size_t)v * kAccStride]);
-    for (int c = tid; c < bk; c += NT) rowi[c] = ldcg(&rowg[c]);
     __syncthreads();
+    if (tid == 0) grid_arrive(p.gs);
+    ++gen;
+    // W column of the previous reflector: off the critical path, overlaps the barrier.
+    if (i > 0) {
+      if (wf32)
+        w_column_f32(i - 1, (float)s_tau_prev, gprevf, slab, Rp, rb, nr, wlf);
+      else
+        w_column(i - 1, s_tau_prev, gprev, slab, Rp, rb, nr, wl, wld);
+    }
+    if (tid == 0) s_ok = grid_wait(p.gs, gen, p.extra, p.status, p.limit_ns) ? 1 : 0;
+    __syncthreads();
+    if (!s_ok) return;
 
-    // ||x2||: plain sum of squares unless it over/underflows; then a scaled second pass.
+    // Thread 0 reads the three numbers the reflector needs and derives it while warps
+    // 1..7 fetch the remaining sums and row i (warp 0 does nothing else, so the two do
+    // not serialise through divergence).
     if (tid == 0) {
-      const double ssq = dsum[i], amax = dsum[bk];
-      s_rescale = (p.j - i > 1) && (amax > 0.0) && !(ssq < 0x1p1000 && amax > 0x1p-450);
-      s_xnorm = sqrt(ssq);
+      const double alpha = ldcg(&rowg[i]);
+      const double ssq = ldcg(&acc[(size_t)i * kAccStride]);
+      const double amax = ldcg(&acc[(size_t)bk * kAccStride]);
+      const int rescale = (p.j - i > 1) && (amax > 0.0) && !(ssq < 0x1p1000 && amax > 0x1p-450);
+      s_rescale = rescale || !(fabs(alpha) < 0x1p500);
+      // Common path: h = ||[alpha; x2]|| = q / sqrt(q) with q = alpha^2 + ||x2||^2 (no
+      // overflow: both terms are bounded here); tau = (beta - alpha) / beta = 1 + |alpha|/h
+      // and scal = 1 / (alpha - beta) = sign(alpha) / (|alpha| + h).
+      double tau = 0.0, beta = alpha, scal = 1.0;
+      if (!s_rescale && p.j - i > 1 && ssq != 0.0) {
+        const double q = fma(alpha, alpha, ssq);
+        const double rq = rsqrt_newton(q);
+        const double h = q * rq;
+        const double aa = fabs(alpha);
+        beta = (alpha >= 0.0) ? -h : h;
+        tau = fma(aa, rq, 1.0);
+        const double rs = rcp_newton(aa + h);
+        scal = (alpha >= 0.0) ? rs : -rs;
+      }
+      s_beta = beta;
+      s_tau = tau;
+      s_scal = scal;
+    } else if (tid >= 32) {
+      for (int v = tid - 32; v <= bk; v += NT - 32) dsum[v] = ldcg(&acc[(size_t)v * kAccStride]);
+      for (int c = tid - 32; c < bk; c += NT - 32) rowi[c] = ldcg(&rowg[c]);
     }
     __syncthreads();
-    if (s_rescale) {  // same decision in every CTA: the inputs of the test are identical
-      const double inv = 1.0 / dsum[bk];
+
+    // Rare path: the plain sum of squares over/underflows (or |alpha| is huge): a scaled
+    // second pass over x2 and the overflow-safe formulas.  Same decision in every CTA.
+    if (s_rescale) {
+      const double inv = dsum[bk] > 0.0 ? 1.0 / dsum[bk] : 0.0;
       double s = 0.0;
       for (int r = lo + tid; r < nr; r += NT) {
         const double t = xi[r] * inv;
@@ -146,78 +290,73 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
         double t = 0.0;
         for (int q = lane; q < G; q += 32) t += ldcg(&p.part2[q]);
         t = warp_sum(t);
-        if (lane == 0) s_xnorm = dsum[bk] * sqrt(t);
+        if (lane == 0) {
+          const double amax = dsum[bk];
+          const bool rescaled = (p.j - i > 1) && (amax > 0.0) && !(dsum[i] < 0x1p1000 && amax > 0x1p-450);
+          const double xnorm = rescaled ? amax * sqrt(t) : sqrt(dsum[i]);
+          const double alpha = rowi[i];
+          double tau = 0.0, beta = alpha, scal = 1.0;
+          if (p.j - i > 1 && xnorm != 0.0) {
+            const double h = hypot(alpha, xnorm);
+            beta = (alpha >= 0.0) ? -h : h;
+            tau = (beta - alpha) / beta;
+            scal = 1.0 / (alpha - beta);
+          }
+          s_beta = beta;
+          s_tau = tau;
+          s_scal = scal;
+        }
       }
       __syncthreads();
     }
+    if (tid == 0 && g == 0) p.tau[i] = s_tau;
 
-    // Reflector (larfg convention).
-    if (tid == 0) {
-      const double alpha = rowi[i];
-      const double xnorm = s_xnorm;
-      double tau = 0.0, beta = alpha, scal = 1.0;
-      if (p.j - i > 1 && xnorm != 0.0) {
-        const double h = hypot(alpha, xnorm);
-        beta = (alpha >= 0.0) ? -h : h;
-        tau = (beta - alpha) / beta;
-        scal = 1.0 / (alpha - beta);
-      }
-      s_beta = beta;
-      s_tau = tau;
-      s_scal = scal;
-      if (g == 0) p.tau[i] = tau;
-    }
-    __syncthreads();
     const double tau = s_tau, scal = s_scal;
-    for (int c = tid; c < bk; c += NT) {
-      if (c > i) {
-        const double z = tau * (rowi[c] + scal * dsum[c]);  // tau * v^T a_c
-        coef[c] = z;
-        coef2[c] = -z * scal;
-      } else if (c < i) {
-        coef[c] = rowi[c] + scal * dsum[c];  // (Y^T y_i)_c
+    // Coefficients and the in-panel update, one column per group of TPU threads:
+    // z_c = tau v^T a_c, a_c -= z_c v (c > i); and (Y^T y_i)_c for c < i (for W).
+    {
+      const int TPU = bk >= 128 ? 2 : (bk >= 64 ? 4 : 8);
+      for (int c0 = 0; c0 < bk; c0 += NT / TPU) {
+        const int c = c0 + tid / TPU, rg = tid % TPU;
+        if (c > i && c < bk) {
+          const double z = tau * fma(scal, dsum[c], rowi[c]);
+          if (tau != 0.0) {
+            const double z2 = -z * scal;
+            double* ac = slab + (size_t)c * Rp;
+            for (int r = lo + rg; r < nr; r += TPU) ac[r] = fma(z2, xi[r], ac[r]);
+            if (own_row && rg == 0) ac[i - rb] -= z;
+          }
+        } else if (c < i && rg == 0) {
+          const double gv = fma(scal, dsum[c], rowi[c]);
+          gprev[c] = gv;
+          gprevf[c] = f64_to_f32_rz(gv);
+        }
       }
     }
     __syncthreads();
-
-    // In-panel update of the columns right of i, then scale x2 into v.
-    if (tau != 0.0) {
-      const int nrow = nr - lo, ncol = bk - i - 1;
-      for (int idx = tid; idx < nrow * ncol; idx += NT) {
-        const int r = lo + idx % nrow, c = i + 1 + idx / nrow;
-        slab[(size_t)c * Rp + r] = fma(coef2[c], xi[r], slab[(size_t)c * Rp + r]);
-      }
-      if (own_row)
-        for (int c = i + 1 + tid; c < bk; c += NT) slab[(size_t)c * Rp + (i - rb)] -= coef[c];
-      __syncthreads();
+    if (tau != 0.0)
       for (int r = lo + tid; r < nr; r += NT) slab[(size_t)i * Rp + r] *= scal;
-    }
     if (own_row && tid == 0) slab[(size_t)i * Rp + (i - rb)] = s_beta;
-    __syncthreads();
-
-    // W(:, i) = -tau (y_i + W(:, 0:i) (Y^T y_i)) for this CTA's rows.
-    for (int r = tid; r < nr; r += NT) {
-      const int gr = rb + r;
-      double s0 = gr > i ? slab[(size_t)i * Rp + r] : (gr == i ? 1.0 : 0.0);
-      double s1 = 0.0, s2 = 0.0, s3 = 0.0;
-      int q = 0;
-      for (; q + 3 < i; q += 4) {
-        s0 = fma(wl[r + (int64_t)q * wld], coef[q], s0);
-        s1 = fma(wl[r + (int64_t)(q + 1) * wld], coef[q + 1], s1);
-        s2 = fma(wl[r + (int64_t)(q + 2) * wld], coef[q + 2], s2);
-        s3 = fma(wl[r + (int64_t)(q + 3) * wld], coef[q + 3], s3);
-      }
-      for (; q < i; ++q) s0 = fma(wl[r + (int64_t)q * wld], coef[q], s0);
-      wl[r + (int64_t)i * wld] = -tau * ((s0 + s1) + (s2 + s3));
-    }
+    if (tid == 0) s_tau_prev = tau;
     __syncthreads();
   }
+  if (wf32)
+    w_column_f32(bk - 1, (float)s_tau_prev, gprevf, slab, Rp, rb, nr, wlf);
+  else
+    w_column(bk - 1, s_tau_prev, gprev, slab, Rp, rb, nr, wl, wld);
+  __syncthreads();
 
-  if (p.w_in_smem)
+  if (wf32) {
+    for (int idx = tid; idx < nr * bk; idx += NT) {
+      const int r = idx % nr, c = idx / nr;
+      p.W[rb + r + (int64_t)c * p.ldy] = tc::f32_to_f64(wlf[r + c * Rp]);
+    }
+  } else if (p.w_in_smem) {
     for (int idx = tid; idx < nr * bk; idx += NT) {
       const int r = idx % nr, c = idx / nr;
       p.W[rb + r + (int64_t)c * p.ldy] = wl[r + (int64_t)c * wld];
     }
+  }
 
   // Write back: packed reflectors/R into the matrix, Y into the workspace.
   if (p.rs == 1) {
@@ -244,7 +383,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
 }  // namespace
 
 size_t panel_smem_bytes(int bk, int Rp, bool w_in_smem) {
-  return ((size_t)bk * Rp * (w_in_smem ? 2 : 1) + 4 * (size_t)bk + 1) * sizeof(double);
+  return ((size_t)bk * Rp * (w_in_smem ? 2 : 1) + 5 * (size_t)bk + 1 + (bk + 1) / 2) * sizeof(double);
 }
 
 size_t panel_sync_bytes(int bk) { return 256 + 3 * (size_t)(bk + 1) * kAccStride * sizeof(double); }
