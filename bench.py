@@ -206,7 +206,7 @@ def main():
     ap.add_argument("--n", type=int, default=8192)
     ap.add_argument("--w", type=int, default=64)
     ap.add_argument("--b", type=int, default=64)
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "bf16x3", "bf16x6", "ozaki"])
+    ap.add_argument("--precision", default="bf16x6", choices=["fp64", "bf16x3", "bf16x6", "ozaki"])
     ap.add_argument("--lookahead", type=int, default=-1)
     ap.add_argument("--no-fp64-path", action="store_true", help="skip the FP64 comparison line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -310,11 +310,15 @@ def main():
     roof = None
     if dom is not None:
         per_launch_ms = dom["ms"] / dom["launches"]
-        if args.precision == "fp64":
+        # The panel (FP64 reflectors) and the whole FP64 path are bound by the FP64 pipe;
+        # the split-precision trailing updates stream A2 through HBM.
+        alu = args.precision == "fp64" or dom["name"] in ("panel_qr_f64", "gemm")
+        if alu:
             achieved = dom["flops"] / (dom["ms"] / 1e3) / 1e12
             peak = 1.25
             roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "kernel": dom["name"], "peak_source": "nominal FP64 rate of GB300 (1.25 TFLOP/s)"}
+                    "kernel": dom["name"], "peak_source": "nominal FP64 rate of GB300 (1.25 TFLOP/s; 1.20 measured "
+                                                          "with an FMA loop)"}
         else:
             achieved = dom["bytes"] / (dom["ms"] / 1e3) / 1e9
             peak = peaks["hbm_gbs"]
@@ -324,7 +328,7 @@ def main():
         roof["traffic"] = None if traffic is None else traffic * dom["bytes"] / dom["launches"]
         roof["launches"] = dom["launches"]
         roof["avg_launch_ms"] = per_launch_ms
-        roof["algorithmic_per_launch"] = (dom["flops"] if args.precision == "fp64" else dom["bytes"]) / dom["launches"]
+        roof["algorithmic_per_launch"] = (dom["flops"] if alu else dom["bytes"]) / dom["launches"]
         roof["kernels"] = {s["name"]: {"launches": s["launches"], "ms": s["ms"]} for s in stats}
 
     # ---- e2e through the C ABI with host buffers
