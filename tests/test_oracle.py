@@ -272,3 +272,32 @@ def test_pins_catch_planted_mistakes_ge2gb(mistake):
     elif mistake == "vp_sign":
         Am[3, 3 + w + 1:] *= -1.0
     assert gen_report(A, Am, tqm, tpm, w)["backward"] > tol
+
+
+# --------------------------------------------------------------------------- frozen outputs
+def _read_golden(name):
+    import os
+
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)
+    out, key, rows = {}, None, []
+    for line in open(path):
+        if line.startswith("#"):
+            if key:
+                out[key] = np.array(rows)
+            key, rows = line.split()[1], []
+        else:
+            rows.append([float(x) for x in line.split()])
+    out[key] = np.array(rows)
+    return out
+
+
+def test_oracle_matches_its_frozen_outputs():
+    g = _read_golden("sy2sb_n12_w3.txt")
+    Aout, tau = oracle.sy2sb(g["A"], 3)
+    np.testing.assert_allclose(np.tril(Aout), g["Aout_lower"], rtol=0, atol=1e-14)
+    np.testing.assert_allclose(tau, g["tau"].ravel(), rtol=0, atol=1e-15)
+    h = _read_golden("ge2gb_m10_n8_w2.txt")
+    Gout, tq, tp = oracle.ge2gb(h["A"], 2)
+    np.testing.assert_allclose(Gout, h["Aout"], rtol=0, atol=1e-14)
+    np.testing.assert_allclose(tq, h["tauq"].ravel(), rtol=0, atol=1e-15)
+    np.testing.assert_allclose(tp, h["taup"].ravel(), rtol=0, atol=1e-15)
