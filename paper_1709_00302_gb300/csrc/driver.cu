@@ -175,9 +175,18 @@ static Sy2sbWs carve_sy2sb(void* work, int64_t n, int64_t w, const Options& o, i
   return ws;
 }
 
+// Buffers of the split-precision engine for one stream: packed B operand, packed rank-k
+// operands, split-K partial products.
+struct SplitBufs {
+  __nv_bfloat16 *bblob, *ablob, *rblob;
+  double* P;
+  size_t P_cap;
+};
+
 struct Ge2gbWs {
-  double *Yu, *Wu, *Yv, *Wv, *Z, *P, *splitk, *part, *rowbuf, *part2;
+  double *Yu[2], *Wu[2], *Yv, *Wv, *Z[2], *ZT, *P, *splitk[2], *part, *rowbuf, *part2;
   GridSync* gs;
+  SplitBufs sb[2];  // [0] caller's stream, [1] panel stream (look-ahead)
   int* status;
   int64_t ldu, ldv;
   size_t splitk_cap;
@@ -188,20 +197,41 @@ static Ge2gbWs carve_ge2gb(void* work, int64_t m, int64_t n, const Options& o, i
   Carver c{static_cast<char*>(work)};
   Ge2gbWs ws{};
   const int64_t b = o.b;
+  const int nbuf = o.lookahead == 0 ? 1 : 2;
   ws.ldu = std::max<int64_t>(m, 1);
   ws.ldv = std::max<int64_t>(n, 1);
-  ws.Yu = c.take<double>(ws.ldu * b);
-  ws.Wu = c.take<double>(ws.ldu * b);
+  for (int q = 0; q < 2; ++q) {
+    ws.Yu[q] = q < nbuf ? c.take<double>(ws.ldu * b) : ws.Yu[0];
+    ws.Wu[q] = q < nbuf ? c.take<double>(ws.ldu * b) : ws.Wu[0];
+  }
   ws.Yv = c.take<double>(ws.ldv * b);
   ws.Wv = c.take<double>(ws.ldv * b);
-  ws.Z = c.take<double>(b * ws.ldv);
   ws.P = c.take<double>(ws.ldu * b);
-  ws.splitk_cap = (size_t)kMaxSplits * b * b * 4;
-  ws.splitk = c.take<double>(ws.splitk_cap);
+  ws.splitk_cap = (size_t)kSmallSplits * b * b * 4;
+  for (int q = 0; q < 2; ++q) {
+    ws.Z[q] = q < nbuf ? c.take<double>(b * ws.ldv) : ws.Z[0];
+    ws.splitk[q] = q < nbuf ? c.take<double>(ws.splitk_cap) : ws.splitk[0];
+  }
   ws.rowbuf = c.take<double>(2 * (size_t)b);
   ws.part2 = c.take<double>((size_t)sms);
   ws.gs = c.take<GridSync>(1);  // 256 bytes, immediately followed by the accumulators
   ws.part = c.take<double>((panel_sync_bytes((int)b) - 256) / sizeof(double));
+  if (is_split(o)) {
+    const int S = split::slices_of(o.precision);
+    const int BN = split::stream_bn((int)b);
+    const int Kr = (int)((b + 63) / 64 * 64);
+    const int64_t big = std::max(ws.ldu, ws.ldv);
+    ws.ZT = c.take<double>(ws.ldv * b);
+    for (int q = 0; q < nbuf; ++q) {
+      SplitBufs& sb = ws.sb[q];
+      sb.bblob = c.take<__nv_bfloat16>(split::packed_bytes(BN, (int)big, BN, 32, S) / 2);
+      sb.ablob = c.take<__nv_bfloat16>(split::packed_bytes((int)big, Kr, 128, 64, S) / 2);
+      sb.rblob = c.take<__nv_bfloat16>(split::packed_bytes((int)big, Kr, 128, 64, S) / 2);
+      sb.P_cap = (size_t)kMaxStreamSplits * big * BN;
+      sb.P = c.take<double>(sb.P_cap);
+    }
+    if (nbuf == 1) ws.sb[1] = ws.sb[0];
+  }
   ws.status = c.take<int>(1);  // last piece: the short forms read it at bytes - 256
   ws.bytes = c.off;
   return ws;
@@ -629,62 +659,267 @@ size_t sy2sb_workspace_bytes(int64_t n, int64_t w, const Options& o) {
 }
 
 // ---------------------------------------------------------------------------------
+// Split-precision building blocks shared by the ge2gb steps.
+namespace {
+
+// C (M x N) = alpha op(A) Bm + beta C with op(A) M x K streamed from FP64 (mode plain /
+// trans) and Bm the K x N FP64 matrix Bsrc[k + n*ldb] (packed here).
+int split_product(int M, int N, int K, const double* A, int64_t lda, int mode, const double* Bsrc, int64_t ldb,
+                  double alpha, double beta, double* C, int64_t ldc, const SplitBufs& sb, int S, int sms, int* status,
+                  unsigned long long limit_ns, cudaStream_t s) {
+  if (M <= 0 || N <= 0) return 0;
+  const int BN = split::stream_bn(N);
+  const int nkb = (K + 31) / 32;
+  split::PackParams pp{};
+  pp.M1 = Bsrc;
+  pp.ld1 = ldb;
+  pp.K1 = K;
+  pp.t1 = 1;
+  pp.scale1 = pp.scale2 = 1.0;
+  pp.R = N;
+  pp.TR = BN;
+  pp.TK = 32;
+  pp.nrb = 1;
+  pp.nkb = std::max(nkb, 1);
+  pp.S = S;
+  pp.out = sb.bblob;
+  pp.status = status;
+  CK(split::pack(pp, s));
+  split::StreamParams sp{};
+  sp.A = A;
+  sp.lda = lda;
+  sp.mode = mode;
+  sp.M = M;
+  sp.K = K;
+  sp.N = N;
+  sp.Bblob = sb.bblob;
+  sp.nkb = pp.nkb;
+  const int tiles = (M + 127) / 128;
+  int splits = stream_splits(tiles, pp.nkb, sms, kMaxStreamSplits);
+  while (splits > 1 && (size_t)splits * M * N > sb.P_cap) --splits;
+  sp.stages_per_split = (pp.nkb + splits - 1) / splits;
+  splits = (pp.nkb + sp.stages_per_split - 1) / sp.stages_per_split;
+  sp.P = sb.P;
+  sp.ldp = M;
+  sp.split_stride = (int64_t)M * N;
+  sp.status = status;
+  sp.limit_ns = limit_ns;
+  CK(split::stream_gemm(sp, S, splits, s));
+  CK(split::reduce(M, N, splits, sb.P, M, (int64_t)M * N, alpha, beta, C, ldc, s));
+  return 0;
+}
+
+// C (M x N) += Am Bm^T with Am (M x K) and Bm (N x K) FP64 column-major, K <= 128.
+int split_rank(int M, int N, int K, const double* Am, int64_t lda, const double* Bm, int64_t ldb, double* C,
+               int64_t ldc, const SplitBufs& sb, int S, int* status, unsigned long long limit_ns, cudaStream_t s) {
+  if (M <= 0 || N <= 0 || K <= 0) return 0;
+  const int Kr = (K + 63) / 64 * 64;
+  split::PackParams pp{};
+  pp.M1 = Am;
+  pp.ld1 = lda;
+  pp.K1 = K;
+  pp.t1 = 0;
+  pp.K2 = 0;
+  pp.scale1 = pp.scale2 = 1.0;
+  pp.R = M;
+  pp.TR = 128;
+  pp.TK = 64;
+  pp.nrb = (M + 127) / 128;
+  pp.nkb = Kr / 64;
+  pp.S = S;
+  pp.out = sb.ablob;
+  pp.status = status;
+  CK(split::pack(pp, s));
+  pp.M1 = Bm;
+  pp.ld1 = ldb;
+  pp.R = N;
+  pp.nrb = (N + 127) / 128;
+  pp.out = sb.rblob;
+  CK(split::pack(pp, s));
+  split::RankParams rp{};
+  rp.Ablob = sb.ablob;
+  rp.Bblob = sb.rblob;
+  rp.Kr = Kr;
+  rp.C = C;
+  rp.ldc = ldc;
+  rp.M = M;
+  rp.N = N;
+  rp.col0 = 0;
+  rp.col1 = N;
+  rp.lower = 0;
+  rp.tj0 = 0;
+  rp.alpha = 1.0;
+  rp.status = status;
+  rp.limit_ns = limit_ns;
+  CK(split::rank_update(rp, S, (M + 127) / 128, (N + 127) / 128, s));
+  return 0;
+}
+
+struct Ge2gb {
+  int64_t m, n, w, lda;
+  double* A;
+  double *tauq, *taup;
+  Options o;
+  Ge2gbWs ws;
+  int* status;
+  int sms, pmax, S;
+  unsigned int extra;
+
+  int bk_of(int64_t k) const { return (int)std::min<int64_t>(o.b, n - k); }
+
+  // QR of B = A(k:m, k:k+bk) (Eq. updateB).
+  int left_panel(int64_t k, int buf, cudaStream_t s) {
+    const int bk = bk_of(k);
+    const int j = (int)(m - k);
+    prof::Scope sc(prof::kPanel, s, panel_flops(j, bk), panel_bytes(j, bk));
+    int rc = run_panel(A + k + k * lda, 1, lda, j, bk, tauq + k, ws.Yu[buf], ws.Wu[buf], ws.ldu, ws.part,
+                       ws.rowbuf, ws.part2, ws.gs, status, o, pmax, extra, s);
+    extra = 0;
+    return rc;
+  }
+
+  // E = A(k:m, k+bk:n) columns [c0, c1) += Y_U (W_U^T E) (Eq. updateCD).
+  int e_update(int64_t k, int buf, int c0, int c1, int q, cudaStream_t s) {
+    const int bk = bk_of(k);
+    const int j = (int)(m - k);
+    c1 = std::min<int>(c1, (int)(n - k - bk));
+    if (c1 <= c0) return 0;
+    const int nc = c1 - c0;
+    double* E = A + k + (k + bk + c0) * lda;
+    prof::Scope sc(prof::kGemm, s, 4.0 * j * nc * bk, 8.0 * (3.0 * j * nc + 2.0 * j * bk));
+    if (!is_split(o)) {
+      const int sp = choose_splits(bk, nc, j, ws.splitk_cap, sms);
+      CK(gemm_f64(bk, nc, j, 1.0, MatView{ws.Wu[buf], ws.ldu, 1}, MatView{E, 1, lda}, 0.0, ws.Z[q], bk, sp,
+                  ws.splitk[q], s));
+      CK(gemm_f64(j, nc, bk, 1.0, MatView{ws.Yu[buf], 1, ws.ldu}, MatView{ws.Z[q], 1, bk}, 1.0, E, lda, 1, nullptr,
+                  s));
+      return 0;
+    }
+    // Z^T = E^T W_U (nc x bk), then E += Y_U (Z^T)^T
+    double* ZT = ws.ZT + c0;
+    if (int rc = split_product(nc, bk, j, E, lda, split::kModeTrans, ws.Wu[buf], ws.ldu, 1.0, 0.0, ZT, ws.ldv,
+                               ws.sb[q], S, sms, status, o.limit_ns, s))
+      return rc;
+    return split_rank(j, nc, bk, ws.Yu[buf], ws.ldu, ZT, ws.ldv, E, lda, ws.sb[q], S, status, o.limit_ns, s);
+  }
+
+  // LQ of C = A(k:k+bkr, k+w:n) (Eq. updateC).
+  int right_panel(int64_t k, cudaStream_t s) {
+    const int bk = bk_of(k);
+    const int64_t bkr = std::min<int64_t>(bk, n - w - 1 - k);
+    if (bkr <= 0) return 0;
+    const int jr = (int)(n - k - w);
+    prof::Scope sc(prof::kPanel, s, panel_flops(jr, (int)bkr), panel_bytes(jr, (int)bkr));
+    return run_panel(A + k + (k + w) * lda, lda, 1, jr, (int)bkr, taup + k, ws.Yv, ws.Wv, ws.ldv, ws.part, ws.rowbuf,
+                     ws.part2, ws.gs, status, o, pmax, 0u, s);
+  }
+
+  // D = A(k+bkr:m, k+w:n) += (D W_V) Y_V^T (Eq. updateD).
+  int d_update(int64_t k, cudaStream_t s) {
+    const int bk = bk_of(k);
+    const int64_t bkr = std::min<int64_t>(bk, n - w - 1 - k);
+    if (bkr <= 0) return 0;
+    const int jr = (int)(n - k - w);
+    const int nrow = (int)(m - k - bkr);
+    if (nrow <= 0) return 0;
+    double* D = A + (k + bkr) + (k + w) * lda;
+    prof::Scope sc(prof::kGemm, s, 4.0 * nrow * jr * bkr, 8.0 * (3.0 * nrow * jr + 2.0 * nrow * bkr));
+    if (!is_split(o)) {
+      const int sp = choose_splits(nrow, (int)bkr, jr, ws.splitk_cap, sms);
+      CK(gemm_f64(nrow, (int)bkr, jr, 1.0, MatView{D, 1, lda}, MatView{ws.Wv, 1, ws.ldv}, 0.0, ws.P, ws.ldu, sp,
+                  ws.splitk[0], s));
+      CK(gemm_f64(nrow, jr, (int)bkr, 1.0, MatView{ws.P, 1, ws.ldu}, MatView{ws.Yv, ws.ldv, 1}, 1.0, D, lda, 1,
+                  nullptr, s));
+      return 0;
+    }
+    if (int rc = split_product(nrow, (int)bkr, jr, D, lda, split::kModePlain, ws.Wv, ws.ldv, 1.0, 0.0, ws.P, ws.ldu,
+                               ws.sb[0], S, sms, status, o.limit_ns, s))
+      return rc;
+    return split_rank(nrow, jr, (int)bkr, ws.P, ws.ldu, ws.Yv, ws.ldv, D, lda, ws.sb[0], S, status, o.limit_ns, s);
+  }
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------
 // ge2gb: Section 3.1 loop.  Iteration k: QR of B = A(k:m, k:k+bk) (Eq. updateB),
 // E = A(k:m, k+bk:n) += Y_U (W_U^T E) (Eq. updateCD), LQ of C = A(k:k+bkr, k+w:n)
 // (Eq. updateC), D = A(k+bkr:m, k+w:n) += (D W_V) Y_V^T (Eq. updateD).
+//
+// Look-ahead (Section 3.2): with w >= 2b the next column panel lies in the first b
+// columns of E and is untouched by this iteration's right update, so the panel stream
+// updates those columns and factors the next panel while the caller's stream finishes
+// the left update; the row panel follows on the panel stream (panels never run
+// concurrently: they share their reduction scratch and each is a cooperative grid over
+// all SMs), then the right update on the caller's stream.  (The paper's second overlap,
+// which needs w >= 3b, is not used.)  With w < 2b the steps run in order.
 int ge2gb_run(int64_t m, int64_t n, int64_t w, double* A, int64_t lda, double* tauq, double* taup,
               const Options& o, void* work, int* dev_status, cudaStream_t s) {
-  const int sms = current_sms();
-  Ge2gbWs ws = carve_ge2gb(work, m, n, o, sms);
-  int* status = dev_status ? dev_status : ws.status;
-  CK(cudaMemsetAsync(status, 0, sizeof(int), s));
+  Ge2gb R{};
+  R.m = m;
+  R.n = n;
+  R.w = w;
+  R.A = A;
+  R.lda = lda;
+  R.tauq = tauq;
+  R.taup = taup;
+  R.o = o;
+  R.sms = current_sms();
+  R.ws = carve_ge2gb(work, m, n, o, R.sms);
+  R.status = dev_status ? dev_status : R.ws.status;
+  R.pmax = panel_max_ctas(R.sms, o);
+  R.S = is_split(o) ? split::slices_of(o.precision) : 0;
+  R.extra = o.debug ? 1u : 0u;
+  if (o.precision == BANDRED_OZAKI) return BANDRED_ERR_UNSUPPORTED;
+  CK(cudaMemsetAsync(R.status, 0, sizeof(int), s));
   if (n <= 0) return 0;
   CK(cudaMemsetAsync(tauq, 0, sizeof(double) * n, s));
   if (n - w > 0) CK(cudaMemsetAsync(taup, 0, sizeof(double) * (n - w), s));
   const int b = o.b;
-  const int pmax = panel_max_ctas(sms, o);
-  unsigned int extra = o.debug ? 1u : 0u;
-  for (int64_t k = 0; k < n; k += b) {
-    const int bk = (int)std::min<int64_t>(b, n - k);
-    const int j = (int)(m - k);
-    int rc;
-    {
-      prof::Scope sc(prof::kPanel, s, panel_flops(j, bk), panel_bytes(j, bk));
-      rc = run_panel(A + k + k * lda, 1, lda, j, bk, tauq + k, ws.Yu, ws.Wu, ws.ldu, ws.part, ws.rowbuf, ws.part2,
-                     ws.gs, status, o, pmax, extra, s);
+  const bool la = o.lookahead != 0 && 2 * b <= w && n > b;
+  int rc;
+  if (!la) {
+    for (int64_t k = 0; k < n; k += b) {
+      if ((rc = R.left_panel(k, 0, s))) return rc;
+      if ((rc = R.e_update(k, 0, 0, (int)n, 0, s))) return rc;
+      if ((rc = R.right_panel(k, s))) return rc;
+      if ((rc = R.d_update(k, s))) return rc;
     }
-    if (rc) return rc;
-    extra = 0;
-    const int ncol = (int)(n - k - bk);
-    if (ncol > 0) {
-      double* E = A + k + (k + bk) * lda;
-      const int sp = choose_splits(bk, ncol, j, ws.splitk_cap, sms);
-      prof::Scope sc(prof::kGemm, s, 4.0 * j * ncol * bk, 8.0 * (2.0 * j * ncol + 2.0 * j * bk));
-      CK(gemm_f64(bk, ncol, j, 1.0, MatView{ws.Wu, ws.ldu, 1}, MatView{E, 1, lda}, 0.0, ws.Z, bk, sp, ws.splitk,
-                  s));
-      CK(gemm_f64(j, ncol, bk, 1.0, MatView{ws.Yu, 1, ws.ldu}, MatView{ws.Z, 1, bk}, 1.0, E, lda, 1, nullptr, s));
-    }
-    const int64_t bkr = std::min<int64_t>(bk, n - w - 1 - k);
-    if (bkr > 0) {
-      const int jr = (int)(n - k - w);
-      {
-        prof::Scope sc(prof::kPanel, s, panel_flops(jr, (int)bkr), panel_bytes(jr, (int)bkr));
-        rc = run_panel(A + k + (k + w) * lda, lda, 1, jr, (int)bkr, taup + k, ws.Yv, ws.Wv, ws.ldv, ws.part,
-                       ws.rowbuf, ws.part2, ws.gs, status, o, pmax, 0u, s);
-      }
-      if (rc) return rc;
-      const int nrow = (int)(m - k - bkr);
-      if (nrow > 0) {
-        double* D = A + (k + bkr) + (k + w) * lda;
-        const int sp = choose_splits(nrow, (int)bkr, jr, ws.splitk_cap, sms);
-        prof::Scope sc(prof::kGemm, s, 4.0 * nrow * jr * bkr, 8.0 * (2.0 * nrow * jr + 2.0 * nrow * bkr));
-        CK(gemm_f64(nrow, (int)bkr, jr, 1.0, MatView{D, 1, lda}, MatView{ws.Wv, 1, ws.ldv}, 0.0, ws.P, ws.ldu, sp,
-                    ws.splitk, s));
-        CK(gemm_f64(nrow, jr, (int)bkr, 1.0, MatView{ws.P, 1, ws.ldu}, MatView{ws.Yv, ws.ldv, 1}, 1.0, D, lda, 1,
-                    nullptr, s));
-      }
-    }
+    return 0;
   }
+  AuxStreams* ax = nullptr;
+  if ((rc = aux_streams(&ax))) return rc;
+  cudaStream_t sp = ax->panel;
+  cudaEvent_t ev_fork = ax->ev[0], ev_panel = ax->ev[1], ev_e = ax->ev[2];
+  CK(cudaEventRecord(ev_fork, s));
+  CK(cudaStreamWaitEvent(sp, ev_fork, 0));
+  if ((rc = R.left_panel(0, 0, sp))) return rc;
+  CK(cudaEventRecord(ev_panel, sp));
+  int buf = 0;
+  for (int64_t k = 0; k < n; k += b, buf ^= 1) {
+    const int64_t kn = k + b;
+    const bool has_next = kn < n;
+    CK(cudaStreamWaitEvent(s, ev_panel, 0));  // left panel k done
+    if (has_next) {
+      const int bkn = R.bk_of(kn);
+      CK(cudaEventRecord(ev_fork, s));  // iteration k-1 is complete on s
+      CK(cudaStreamWaitEvent(sp, ev_fork, 0));
+      if ((rc = R.e_update(k, buf, 0, bkn, 1, sp))) return rc;
+      if ((rc = R.left_panel(kn, buf ^ 1, sp))) return rc;
+      if ((rc = R.e_update(k, buf, bkn, (int)n, 0, s))) return rc;
+      CK(cudaEventRecord(ev_e, s));
+      CK(cudaStreamWaitEvent(sp, ev_e, 0));
+      if ((rc = R.right_panel(k, sp))) return rc;
+      CK(cudaEventRecord(ev_panel, sp));  // covers left panel k+1 and row panel k
+      CK(cudaStreamWaitEvent(s, ev_panel, 0));
+    } else {
+      if ((rc = R.e_update(k, buf, 0, (int)n, 0, s))) return rc;
+      if ((rc = R.right_panel(k, s))) return rc;
+    }
+    if ((rc = R.d_update(k, s))) return rc;
+  }
+  CK(cudaEventRecord(ev_fork, sp));
+  CK(cudaStreamWaitEvent(s, ev_fork, 0));
   return 0;
 }
 
