@@ -20,6 +20,8 @@ namespace {
 
 constexpr size_t kAlign = 256;
 constexpr int kMinPanelRows = 32;
+constexpr int kClusterMax = 16;    // CTAs of a cluster panel
+constexpr int kClusterRows = 32;   // a panel of at most kClusterMax * kClusterRows rows uses a cluster
 constexpr int kMaxSplits = 128;
 constexpr int kSmallSplits = 32;       // split-K of the FP64 products with a b-wide output
 constexpr int kMaxStreamSplits = 8;    // split-K of the streamed X1 = A2 W product
@@ -254,10 +256,35 @@ static int current_sms() {
 static int run_panel(double* A, int64_t rs, int64_t cs, int j, int bk, double* tau, double* Y, double* W,
                      int64_t ldy, double* acc, double* rowbuf, double* part2, GridSync* gs, int* status,
                      const Options& o, int max_ctas, unsigned int extra, cudaStream_t s) {
+  PanelParams p{};
+  // Short panels: one thread-block cluster (no grid-wide barrier, deterministic sums).
+  if (extra == 0) {
+    int C = 1;
+    while (C < kClusterMax && (j + C - 1) / C > kClusterRows) C *= 2;
+    const int Rc = (j + C - 1) / C;
+    if (Rc <= kClusterRows) {
+      p.A = A;
+      p.rs = rs;
+      p.cs = cs;
+      p.j = j;
+      p.bk = bk;
+      p.R = Rc;
+      p.Rp = Rc | 1;
+      p.tau = tau;
+      p.Y = Y;
+      p.W = W;
+      p.ldy = ldy;
+      p.status = status;
+      p.limit_ns = o.limit_ns;
+      p.w_in_smem = true;
+      p.w_fp32 = is_split(o);
+      CK(launch_panel_cluster(&p, nullptr, 1, C, p.Rp, bk, s));
+      return 0;
+    }
+  }
   int G, R, Rp;
   bool w_smem = false;
   if (panel_geometry(j, bk, max_ctas, kMinPanelRows, &G, &R, &Rp, &w_smem) != 0) return BANDRED_ERR_UNSUPPORTED;
-  PanelParams p{};
   p.A = A;
   p.rs = rs;
   p.cs = cs;

@@ -34,6 +34,14 @@ size_t panel_sync_bytes(int bk);  // bytes from gs to the end of acc
 int panel_geometry(int j, int bk, int max_ctas, int min_rows, int* G, int* R, int* Rp, bool* w_in_smem);
 cudaError_t launch_panel(const PanelParams& p, int G, cudaStream_t s);
 
+// One thread-block cluster of C CTAs per panel (panel_cluster.cu).  `single` (host
+// struct) or `dev_probs` (device array of nprob structs, inactive when bk == 0) gives the
+// problems; each uses rows-per-CTA R = p.R and stride p.Rp <= Rp_max, bk <= bk_max.
+size_t panel_cluster_smem_bytes(int bk, int Rp);
+int panel_cluster_rows(int j, int bk, int C);
+cudaError_t launch_panel_cluster(const PanelParams* single, const PanelParams* dev_probs, int nprob, int C, int Rp_max,
+                                 int bk_max, cudaStream_t s);
+
 // ---------------------------------------------------------------- FP64 kernels (gemm_f64.cu)
 // A strided matrix view: element (i, k) at p[i * rs + k * cs].
 struct MatView {
