@@ -169,6 +169,43 @@ int bandred_ge2gb_ex(int64_t m, int64_t n, int64_t w, double* A, int64_t lda, do
                      double* taup, const bandred_opts* opts, void* work, size_t work_bytes,
                      int* dev_status, cudaStream_t stream);
 
+/* ---------------------------------------------------------------- batched -----------
+ * Many independent matrices of uneven sizes (Sections 2.1 and 3.1 applied to each).
+ * The matrices advance in lockstep: iteration t of every matrix still active runs in the
+ * same kernel launches (one thread-block cluster per panel, batched split-precision
+ * products), matrices ordered by their number of iterations.  Split precision only
+ * (BANDRED_BF16X3 or BANDRED_BF16X6); opts->b is the panel width (0: min(w, 32), clamped
+ * to each matrix's w).
+ *   count         number of matrices
+ *   n, w (m)      host arrays of sizes (ge2gb: m[q] >= n[q])
+ *   A, tau(q/p)   host arrays of DEVICE pointers (column-major FP64 matrices, lda[q];
+ *                 lda == NULL means lda[q] = n[q] (sy2sb) or m[q] (ge2gb))
+ *   work          device, 256-byte aligned, >= the _workspace bytes, one per batch shape
+ * _plan builds the launch schedule for these sizes and pointers, writes its parameter
+ * tables into `work` (one host-to-device copy) and clears the tau arrays; it is not
+ * capturable.  _run issues the schedule's kernel launches and memsets only (no
+ * allocation, no synchronisation, no host copy), so it can be captured in a CUDA graph
+ * and replayed; call it with the same arguments as the last _plan on this workspace.
+ * dev_status (device int, may be NULL) receives the BANDRED_DEV_* code of the run.
+ * Outputs per matrix: the packed layouts of bandred_sy2sb / bandred_ge2gb. */
+size_t bandred_sy2sb_batched_workspace(int count, const int64_t* n, const int64_t* w, const bandred_opts* opts);
+int bandred_sy2sb_batched_plan(int count, const int64_t* n, const int64_t* w, double* const* A,
+                               const int64_t* lda, double* const* tau, const bandred_opts* opts,
+                               void* work, size_t work_bytes, cudaStream_t stream);
+int bandred_sy2sb_batched_run(int count, const int64_t* n, const int64_t* w, double* const* A,
+                              const int64_t* lda, double* const* tau, const bandred_opts* opts,
+                              void* work, size_t work_bytes, int* dev_status, cudaStream_t stream);
+size_t bandred_ge2gb_batched_workspace(int count, const int64_t* m, const int64_t* n, const int64_t* w,
+                                       const bandred_opts* opts);
+int bandred_ge2gb_batched_plan(int count, const int64_t* m, const int64_t* n, const int64_t* w,
+                               double* const* A, const int64_t* lda, double* const* tauq,
+                               double* const* taup, const bandred_opts* opts, void* work,
+                               size_t work_bytes, cudaStream_t stream);
+int bandred_ge2gb_batched_run(int count, const int64_t* m, const int64_t* n, const int64_t* w,
+                              double* const* A, const int64_t* lda, double* const* tauq,
+                              double* const* taup, const bandred_opts* opts, void* work,
+                              size_t work_bytes, int* dev_status, cudaStream_t stream);
+
 /* ---------------------------------------------------------------- split-precision engine
  * The tensor-core products of the trailing updates, usable on their own.  FP64 operands
  * are cut into bf16 slices (x ~ s0 + s1 [+ s2]; s0 keeps the leading 8 bits); the slice

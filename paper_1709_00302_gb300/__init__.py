@@ -26,7 +26,7 @@ __all__ = [
     "bandred_ge2gb_workspace", "bandred_ge2gb_ex", "bandred_ge2gb",
     "bandred_status_string", "bandred_last_error", "bandred_profile_begin", "bandred_profile_end",
     "bandred_launch_count", "bandred_kernel_stat", "bandred_gemm_split", "bandred_gemm_split_workspace",
-    "bandred_syr2k_split", "bandred_syr2k_split_workspace", "sy2sb", "ge2gb", "BandredError",
+    "bandred_syr2k_split", "bandred_syr2k_split_workspace", "SyBatch", "GeBatch", "sy2sb", "ge2gb", "BandredError",
 ]
 
 PRECISIONS = {"fp64": 0, "bf16x3": 1, "bf16x6": 2, "ozaki": 3}
@@ -102,6 +102,20 @@ def lib():
         L.bandred_syr2k_split_workspace.restype = sz
         L.bandred_syr2k_split.argtypes = [i64, i64, vp, i64, vp, i64, vp, i64, ci, vp, sz, vp, vp]
         L.bandred_syr2k_split.restype = ci
+        p64 = ctypes.POINTER(ctypes.c_int64)
+        pvp = ctypes.POINTER(ctypes.c_void_p)
+        L.bandred_sy2sb_batched_workspace.argtypes = [ci, p64, p64, op]
+        L.bandred_sy2sb_batched_workspace.restype = sz
+        L.bandred_sy2sb_batched_plan.argtypes = [ci, p64, p64, pvp, p64, pvp, op, vp, sz, vp]
+        L.bandred_sy2sb_batched_plan.restype = ci
+        L.bandred_sy2sb_batched_run.argtypes = [ci, p64, p64, pvp, p64, pvp, op, vp, sz, vp, vp]
+        L.bandred_sy2sb_batched_run.restype = ci
+        L.bandred_ge2gb_batched_workspace.argtypes = [ci, p64, p64, p64, op]
+        L.bandred_ge2gb_batched_workspace.restype = sz
+        L.bandred_ge2gb_batched_plan.argtypes = [ci, p64, p64, p64, pvp, p64, pvp, pvp, op, vp, sz, vp]
+        L.bandred_ge2gb_batched_plan.restype = ci
+        L.bandred_ge2gb_batched_run.argtypes = [ci, p64, p64, p64, pvp, p64, pvp, pvp, op, vp, sz, vp, vp]
+        L.bandred_ge2gb_batched_run.restype = ci
         L.bandred_sy2sb_noalloc.argtypes = [i64, i64, vp, i64, vp, op, vp, vp]
         L.bandred_sy2sb_noalloc.restype = ci
         L.bandred_profile_begin.argtypes = []
@@ -256,6 +270,71 @@ def bandred_profile_end(max_entries: int = 16) -> list:
 
 def bandred_launch_count() -> int:
     return lib().bandred_launch_count()
+
+
+# ------------------------------------------------------------------ batched
+def _i64(vals):
+    return (ctypes.c_int64 * max(len(vals), 1))(*[int(v) for v in vals])
+
+
+def _ptrs(ts):
+    return (ctypes.c_void_p * max(len(ts), 1))(*[t.data_ptr() if t is not None and t.numel() else 0 for t in ts])
+
+
+class SyBatch:
+    """Arguments of bandred_sy2sb_batched_* for lists of column-major CUDA matrices and
+    tau vectors (kept alive by this object)."""
+
+    def __init__(self, As, w, taus, opts=None):
+        self.As, self.taus = As, taus
+        self.n = _i64([a.shape[0] for a in As])
+        self.w = _i64(w)
+        self.lda = _i64([_lda(a) for a in As])
+        self.A = _ptrs(As)
+        self.tau = _ptrs(taus)
+        self.count = len(As)
+        self.opts = opts if opts is not None else make_opts(precision="bf16x6")
+
+    def workspace(self):
+        return lib().bandred_sy2sb_batched_workspace(self.count, self.n, self.w, ctypes.byref(self.opts))
+
+    def plan(self, work, stream=None):
+        return lib().bandred_sy2sb_batched_plan(self.count, self.n, self.w, self.A, self.lda, self.tau,
+                                                ctypes.byref(self.opts), _ptr(work), work.numel(), _stream(stream))
+
+    def run(self, work, dev_status=None, stream=None):
+        return lib().bandred_sy2sb_batched_run(self.count, self.n, self.w, self.A, self.lda, self.tau,
+                                               ctypes.byref(self.opts), _ptr(work), work.numel(), _ptr(dev_status),
+                                               _stream(stream))
+
+
+class GeBatch:
+    """Arguments of bandred_ge2gb_batched_* (see SyBatch)."""
+
+    def __init__(self, As, w, tauqs, taups, opts=None):
+        self.As, self.tauqs, self.taups = As, tauqs, taups
+        self.m = _i64([a.shape[0] for a in As])
+        self.n = _i64([a.shape[1] for a in As])
+        self.w = _i64(w)
+        self.lda = _i64([_lda(a) for a in As])
+        self.A = _ptrs(As)
+        self.tauq = _ptrs(tauqs)
+        self.taup = _ptrs(taups)
+        self.count = len(As)
+        self.opts = opts if opts is not None else make_opts(precision="bf16x6")
+
+    def workspace(self):
+        return lib().bandred_ge2gb_batched_workspace(self.count, self.m, self.n, self.w, ctypes.byref(self.opts))
+
+    def plan(self, work, stream=None):
+        return lib().bandred_ge2gb_batched_plan(self.count, self.m, self.n, self.w, self.A, self.lda, self.tauq,
+                                                self.taup, ctypes.byref(self.opts), _ptr(work), work.numel(),
+                                                _stream(stream))
+
+    def run(self, work, dev_status=None, stream=None):
+        return lib().bandred_ge2gb_batched_run(self.count, self.m, self.n, self.w, self.A, self.lda, self.tauq,
+                                               self.taup, ctypes.byref(self.opts), _ptr(work), work.numel(),
+                                               _ptr(dev_status), _stream(stream))
 
 
 # ------------------------------------------------------------------ conveniences

@@ -34,4 +34,14 @@ size_t ge2gb_workspace_bytes(int64_t m, int64_t n, int64_t w, const Options& o);
 int ge2gb_run(int64_t m, int64_t n, int64_t w, double* A, int64_t lda, double* tauq, double* taup,
               const Options& o, void* work, int* dev_status, cudaStream_t s);
 
+// Batched reductions (batched.cu).  mode 1 = plan (upload the schedule's tables), 2 = run.
+int sy2sb_batched(int count, const int64_t* n, const int64_t* w, double* const* A, const int64_t* lda,
+                  double* const* tau, const Options& o, void* work, size_t work_bytes, int* dev_status,
+                  cudaStream_t s, int mode);
+size_t sy2sb_batched_workspace(int count, const int64_t* n, const int64_t* w, const Options& o);
+int ge2gb_batched(int count, const int64_t* m, const int64_t* n, const int64_t* w, double* const* A,
+                  const int64_t* lda, double* const* tauq, double* const* taup, const Options& o, void* work,
+                  size_t work_bytes, int* dev_status, cudaStream_t s, int mode);
+size_t ge2gb_batched_workspace(int count, const int64_t* m, const int64_t* n, const int64_t* w, const Options& o);
+
 }  // namespace bandred

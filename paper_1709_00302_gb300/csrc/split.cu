@@ -42,7 +42,9 @@ __device__ __forceinline__ void report(int* status, int code) {
 }
 
 // ================================================================= pack
-__global__ void pack_kernel(PackParams p) {
+__global__ void pack_kernel(PackParams single, const PackParams* probs) {
+  const PackParams p = probs ? probs[blockIdx.y] : single;
+  if (p.R <= 0) return;
   const int groups_per_tile = p.TR * (p.TK / 8);
   const int64_t total = (int64_t)p.nrb * p.nkb * groups_per_tile;
   const int K = p.K1 + p.K2;
@@ -117,8 +119,13 @@ struct StreamSmem {
 };
 
 template <int BN, int S, int NSTAGE>
-__global__ void __launch_bounds__(NT, 1) stream_gemm_kernel(StreamParams p) {
+__global__ void __launch_bounds__(NT, 1) stream_gemm_kernel(StreamParams single, const StreamParams* probs) {
   using L = StreamSmem<BN, S, NSTAGE>;
+  const StreamParams p = probs ? probs[blockIdx.z] : single;
+  if (probs) {  // batched: this CTA's tile or split may lie beyond its problem
+    if (p.M <= 0 || p.nkb <= 0 || (int)blockIdx.x * BM >= p.M) return;
+    if ((int)blockIdx.y * p.stages_per_split >= p.nkb) return;
+  }
   using PR = Products<S>;
   extern __shared__ __align__(1024) unsigned char smem[];
   double* ring = reinterpret_cast<double*>(smem);
@@ -352,10 +359,13 @@ struct RankSmem {
 };
 
 template <int S>
-__global__ void __launch_bounds__(NT) rank_update_kernel(RankParams p) {
+__global__ void __launch_bounds__(NT) rank_update_kernel(RankParams single, const RankParams* probs) {
   using L = RankSmem<S>;
   using PR = Products<S>;
+  const RankParams p = probs ? probs[blockIdx.z] : single;
   const int I = blockIdx.x, J = p.tj0 + blockIdx.y;
+  if (p.M <= 0 || p.N <= 0 || p.col1 <= p.col0) return;
+  if (I * BM >= p.M || J * BM >= min(p.N, p.col1)) return;
   if (p.lower && I < J) return;
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* as = smem;
@@ -449,20 +459,20 @@ __global__ void __launch_bounds__(NT) rank_update_kernel(RankParams p) {
 }
 
 // ================================================================= split-K reduce
-__global__ void reduce_kernel(int M, int N, int splits, const double* P, int64_t ldp, int64_t sstride, double alpha,
-                              double beta, double* C, int64_t ldc) {
-  const int64_t total = (int64_t)M * N;
+__global__ void reduce_kernel(ReduceParams single, const ReduceParams* probs) {
+  const ReduceParams r = probs ? probs[blockIdx.y] : single;
+  const int64_t total = (int64_t)r.M * r.N;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e % M), c = (int)(e / M);
+    const int i = (int)(e % r.M), c = (int)(e / r.M);
     double s = 0.0;
-    for (int z = 0; z < splits; ++z) s += P[(size_t)z * sstride + i + (int64_t)c * ldp];
-    double* cp = &C[i + (int64_t)c * ldc];
-    *cp = (beta == 0.0) ? alpha * s : fma(alpha, s, beta * *cp);
+    for (int z = 0; z < r.splits; ++z) s += r.P[(size_t)z * r.sstride + i + (int64_t)c * r.ldp];
+    double* cp = &r.C[i + (int64_t)c * r.ldc];
+    *cp = (r.beta == 0.0) ? r.alpha * s : fma(r.alpha, s, r.beta * *cp);
   }
 }
 
 template <int BN, int S, int NSTAGE>
-cudaError_t launch_stream(const StreamParams& p, int splits, cudaStream_t s) {
+cudaError_t launch_stream(const StreamParams& p, const StreamParams* probs, dim3 grid, cudaStream_t s) {
   using L = StreamSmem<BN, S, NSTAGE>;
   static_assert(L::total <= 227 * 1024, "stream GEMM shared memory");
   static int configured = -1;
@@ -474,14 +484,13 @@ cudaError_t launch_stream(const StreamParams& p, int splits, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     configured = dev;
   }
-  dim3 grid((p.M + BM - 1) / BM, splits);
-  stream_gemm_kernel<BN, S, NSTAGE><<<grid, NT, L::total, s>>>(p);
+  stream_gemm_kernel<BN, S, NSTAGE><<<grid, NT, L::total, s>>>(p, probs);
   prof::count_launch();
   return cudaGetLastError();
 }
 
 template <int S>
-cudaError_t launch_rank(const RankParams& p, int tiles_i, int tiles_j, cudaStream_t s) {
+cudaError_t launch_rank(const RankParams& p, const RankParams* probs, dim3 grid, cudaStream_t s) {
   using L = RankSmem<S>;
   static int configured = -1;
   int dev = 0;
@@ -492,7 +501,7 @@ cudaError_t launch_rank(const RankParams& p, int tiles_i, int tiles_j, cudaStrea
     if (e != cudaSuccess) return e;
     configured = dev;
   }
-  rank_update_kernel<S><<<dim3(tiles_i, tiles_j), NT, L::total, s>>>(p);
+  rank_update_kernel<S><<<grid, NT, L::total, s>>>(p, probs);
   prof::count_launch();
   return cudaGetLastError();
 }
@@ -511,23 +520,41 @@ cudaError_t pack(const PackParams& pp, cudaStream_t s) {
   const int64_t total = (int64_t)pp.nrb * pp.nkb * pp.TR * (pp.TK / 8);
   if (total <= 0) return cudaSuccess;
   const int blocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
-  pack_kernel<<<blocks, 256, 0, s>>>(pp);
+  pack_kernel<<<blocks, 256, 0, s>>>(pp, nullptr);
+  prof::count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t pack_batched(const PackParams* probs, int nprob, int64_t max_groups, cudaStream_t s) {
+  if (nprob <= 0 || max_groups <= 0) return cudaSuccess;
+  const int blocks = (int)std::min<int64_t>((max_groups + 255) / 256, 1024);
+  pack_kernel<<<dim3(blocks, nprob), 256, 0, s>>>(PackParams{}, probs);
   prof::count_launch();
   return cudaGetLastError();
 }
 
 int stream_bn(int N) { return N <= 32 ? 32 : (N <= 64 ? 64 : 128); }
 
+template <int S>
+static cudaError_t stream_dispatch(int BN, const StreamParams& p, const StreamParams* probs, dim3 grid,
+                                   cudaStream_t s) {
+  if (BN == 32) return launch_stream<32, S, 3>(p, probs, grid, s);
+  if (BN == 64) return launch_stream<64, S, 3>(p, probs, grid, s);
+  return launch_stream<128, S, 2>(p, probs, grid, s);
+}
+
 cudaError_t stream_gemm(const StreamParams& p, int S, int splits, cudaStream_t s) {
   const int BN = stream_bn(p.N);
-  if (S == 2) {
-    if (BN == 32) return launch_stream<32, 2, 3>(p, splits, s);
-    if (BN == 64) return launch_stream<64, 2, 3>(p, splits, s);
-    return launch_stream<128, 2, 2>(p, splits, s);
-  }
-  if (BN == 32) return launch_stream<32, 3, 3>(p, splits, s);
-  if (BN == 64) return launch_stream<64, 3, 3>(p, splits, s);
-  return launch_stream<128, 3, 2>(p, splits, s);
+  const dim3 grid((p.M + BM - 1) / BM, splits);
+  return S == 2 ? stream_dispatch<2>(BN, p, nullptr, grid, s) : stream_dispatch<3>(BN, p, nullptr, grid, s);
+}
+
+cudaError_t stream_gemm_batched(const StreamParams* probs, int nprob, int S, int BN, int max_tiles, int max_splits,
+                                cudaStream_t s) {
+  if (nprob <= 0 || max_tiles <= 0 || max_splits <= 0) return cudaSuccess;
+  const dim3 grid(max_tiles, max_splits, nprob);
+  return S == 2 ? stream_dispatch<2>(BN, StreamParams{}, probs, grid, s)
+                : stream_dispatch<3>(BN, StreamParams{}, probs, grid, s);
 }
 
 cudaError_t reduce(int M, int N, int splits, const double* P, int64_t ldp, int64_t sstride, double alpha, double beta,
@@ -535,14 +562,30 @@ cudaError_t reduce(int M, int N, int splits, const double* P, int64_t ldp, int64
   const int64_t total = (int64_t)M * N;
   if (total <= 0) return cudaSuccess;
   const int blocks = (int)std::min<int64_t>((total + 255) / 256, 2048);
-  reduce_kernel<<<blocks, 256, 0, s>>>(M, N, splits, P, ldp, sstride, alpha, beta, C, ldc);
+  ReduceParams r{M, N, splits, P, ldp, sstride, alpha, beta, C, ldc};
+  reduce_kernel<<<blocks, 256, 0, s>>>(r, nullptr);
+  prof::count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t reduce_batched(const ReduceParams* probs, int nprob, int64_t max_total, cudaStream_t s) {
+  if (nprob <= 0 || max_total <= 0) return cudaSuccess;
+  const int blocks = (int)std::min<int64_t>((max_total + 255) / 256, 256);
+  reduce_kernel<<<dim3(blocks, nprob), 256, 0, s>>>(ReduceParams{}, probs);
   prof::count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t rank_update(const RankParams& p, int S, int tiles_i, int tiles_j, cudaStream_t s) {
   if (tiles_i <= 0 || tiles_j <= 0) return cudaSuccess;
-  return S == 2 ? launch_rank<2>(p, tiles_i, tiles_j, s) : launch_rank<3>(p, tiles_i, tiles_j, s);
+  const dim3 grid(tiles_i, tiles_j);
+  return S == 2 ? launch_rank<2>(p, nullptr, grid, s) : launch_rank<3>(p, nullptr, grid, s);
+}
+
+cudaError_t rank_update_batched(const RankParams* probs, int nprob, int S, int max_ti, int max_tj, cudaStream_t s) {
+  if (nprob <= 0 || max_ti <= 0 || max_tj <= 0) return cudaSuccess;
+  const dim3 grid(max_ti, max_tj, nprob);
+  return S == 2 ? launch_rank<2>(RankParams{}, probs, grid, s) : launch_rank<3>(RankParams{}, probs, grid, s);
 }
 
 }  // namespace split

@@ -61,6 +61,15 @@ struct RankParams {
   unsigned long long limit_ns;
 };
 
+struct ReduceParams {
+  int M, N, splits;
+  const double* P;
+  int64_t ldp, sstride;
+  double alpha, beta;
+  double* C;
+  int64_t ldc;
+};
+
 int slices_of(int precision);
 int stream_bn(int N);
 size_t packed_bytes(int R, int K, int TR, int TK, int S);
@@ -69,6 +78,14 @@ cudaError_t stream_gemm(const StreamParams& p, int S, int splits, cudaStream_t s
 cudaError_t reduce(int M, int N, int splits, const double* P, int64_t ldp, int64_t sstride, double alpha, double beta,
                    double* C, int64_t ldc, cudaStream_t s);
 cudaError_t rank_update(const RankParams& p, int S, int tiles_i, int tiles_j, cudaStream_t s);
+
+// Batched forms: one launch over nprob problems whose parameters are a device array (an
+// entry with an empty size is skipped); grids cover the largest problem.
+cudaError_t pack_batched(const PackParams* probs, int nprob, int64_t max_groups, cudaStream_t s);
+cudaError_t stream_gemm_batched(const StreamParams* probs, int nprob, int S, int BN, int max_tiles, int max_splits,
+                                cudaStream_t s);
+cudaError_t reduce_batched(const ReduceParams* probs, int nprob, int64_t max_total, cudaStream_t s);
+cudaError_t rank_update_batched(const RankParams* probs, int nprob, int S, int max_ti, int max_tj, cudaStream_t s);
 
 }  // namespace split
 }  // namespace bandred

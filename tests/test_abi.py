@@ -25,7 +25,7 @@ def L():
 
 def test_every_declared_symbol_is_exported(L):
     syms = declared_symbols()
-    assert len(syms) >= 17
+    assert len(syms) >= 23
     for s in syms:
         assert hasattr(L, s), s
 
