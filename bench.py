@@ -45,6 +45,9 @@ sys.path.insert(0, ROOT)
 HEADLINE_METRIC = "band-reduction TFLOP/s & speedup vs FP64 path at equal backward error; mats/s"
 
 
+DTYPES = {"fp64": "f64", "bf16x3": "bf16x3->f64", "bf16x6": "bf16x6->f64", "ozaki": "ozaki-bf16->f64"}
+
+
 def nominal_flops(n: int) -> float:
     return 4.0 * n ** 3 / 3.0
 
@@ -162,67 +165,120 @@ def run_cpu_baseline(A_host, n, w, target_s: float):
                       f"nominal flops of those reflectors)"}
 
 
+def ge2gb_sample_flops(m: int, n: int, w: int, ncols: int) -> float:
+    """Nominal flops of the first ncols left/right reflector pairs: the left reflector of
+    column c updates (m-c) x (n-c), the right one (m-c) x (n-c-w), 4 flops per entry each
+    (the sum over all columns is 4(mn^2 - n^3/3) + O(w))."""
+    return sum(4.0 * (m - c) * (n - c) + 4.0 * (m - c) * max(n - c - w, 0) for c in range(ncols))
+
+
 def reference_arm(args, n, w, b):
     """CPU reference arm: the FP64 oracle, each step a bounded sample of the workload."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    import numpy as np
+
     import oracle
     import workloads
 
-    A, _ = workloads.sym_known_spectrum(n, 0, 1)
     cores = oracle.set_threads(0)
     ncols = args.ref_cols
-    fl = sample_flops(n, w, ncols)
+    wl = args.workload
+    unit = "TFLOP/s"
+    if wl == "batched":
+        sym, gen = workloads.batched_mix(args.batch_sym, args.batch_gen, seed=0)
+        k = max(1, ncols // 16)
+        mats = [("sym", i, sym[i]) for i in range(k)] + [("gen", i, gen[i]) for i in range(k)]
+        inputs = [workloads.batched_matrix(kind, i, (sh[0],) if kind == "sym" else sh[:2]) for kind, i, sh in mats]
+
+        def step():
+            for (kind, _, sh), M in zip(mats, inputs):
+                if kind == "sym":
+                    oracle.sy2sb(M, sh[1])
+                else:
+                    oracle.ge2gb(M, sh[2])
+        units, unit = len(mats), "mats/s"
+        desc = f"batched: the first {k} symmetric and {k} general matrices of the 1000 + 1000 mix per step"
+        sample = f"{len(mats)} whole matrices per step"
+        dtype_cfg = {"count": len(mats)}
+    elif wl == "ge2gb":
+        A = workloads.gen_gaussian(n, n, 0)
+
+        def step():
+            oracle.ge2gb(A, w, ncols=ncols)
+        units = ge2gb_sample_flops(n, n, w, ncols)
+        desc = f"ge2gb m=n={n} w={w} b={b} N(0,1) FP64 (bounded sample: first {ncols} columns per step)"
+        sample = f"first {ncols} of {n} left/right reflector pairs per step"
+        dtype_cfg = {"m": n, "n": n, "w": w, "b": b}
+    else:
+        if wl == "sy2sb_large":
+            G = np.random.Generator(np.random.PCG64(0)).standard_normal((n, n))
+            A = np.asfortranarray((G + G.T) * 0.5)
+            del G
+        else:
+            A, _ = workloads.sym_known_spectrum(n, 0, 1)
+
+        def step():
+            oracle.sy2sb(A, w, ncols=ncols)
+        units = sample_flops(n, w, ncols)
+        desc = f"sy2sb n={n} w={w} b={b} FP64 (bounded sample: first {ncols} reflectors per step)"
+        sample = f"first {ncols} of {n - w} reflectors per step"
+        dtype_cfg = {"n": n, "w": w, "b": b}
     for _ in range(args.warmup):
-        oracle.sy2sb(A, w, ncols=max(2, ncols // 8))
+        step()
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.sy2sb(A, w, ncols=ncols)
+        step()
         times.append(time.perf_counter() - t0)
     ms = 1e3 * sum(times) / len(times)
-    value = fl / (ms / 1e3) / 1e12
+    value = units / (ms / 1e3) / (1e12 if unit == "TFLOP/s" else 1.0)
     line = {
-        "impl": "reference", "metric": HEADLINE_METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus,
+        "impl": "reference", "metric": HEADLINE_METRIC, "value": value, "unit": unit, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"sy2sb n={n} w={w} b={b} known-spectrum FP64 (bounded sample: first {ncols} "
-                               f"reflectors per step)", "n": n, "w": w, "b": b},
-        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
-                         "sample": f"first {ncols} of {n - w} reflectors per step"},
-        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "config": dict({"workload": desc}, **dtype_cfg),
+        "cpu_baseline": {"value": value, "unit": unit, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--n", type=int, default=8192)
-    ap.add_argument("--w", type=int, default=64)
-    ap.add_argument("--b", type=int, default=64)
-    ap.add_argument("--precision", default="bf16x6", choices=["fp64", "bf16x3", "bf16x6", "ozaki"])
-    ap.add_argument("--lookahead", type=int, default=-1)
-    ap.add_argument("--no-fp64-path", action="store_true", help="skip the FP64 comparison line")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--ref-cols", type=int, default=96, help="reflectors per reference-arm step")
-    args = ap.parse_args()
-    n, w, b = args.n, args.w, args.b
+def roofline(stats, precision):
+    """Roofline of the dominant kernel class of a profiled run: its algorithmic flops or
+    bytes over its CUDA-event time, against the bound's peak."""
+    peaks, peak_src = load_peaks()
+    dom = max(stats, key=lambda s: s["ms"]) if stats else None
+    if dom is None:
+        return None
+    per_launch_ms = dom["ms"] / dom["launches"]
+    # The panel (FP64 reflectors) and the whole FP64 path are bound by the FP64 pipe;
+    # the split-precision trailing updates stream the trailing matrix through HBM.
+    alu = precision == "fp64" or dom["name"] == "panel_qr_f64"
+    if alu:
+        achieved = dom["flops"] / (dom["ms"] / 1e3) / 1e12
+        peak = 1.25
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "kernel": dom["name"], "peak_source": "nominal FP64 rate of GB300 (1.25 TFLOP/s; 1.20 measured "
+                                                      "with an FMA loop)"}
+    else:
+        achieved = dom["bytes"] / (dom["ms"] / 1e3) / 1e9
+        peak = peaks["hbm_gbs"]
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "kernel": dom["name"], "peak_source": f"hbm_gbs ({peak_src})"}
+    traffic = kernel_traffic(dom["name"])
+    roof["traffic"] = None if traffic is None else traffic * dom["bytes"] / dom["launches"]
+    roof["launches"] = dom["launches"]
+    roof["avg_launch_ms"] = per_launch_ms
+    roof["algorithmic_per_launch"] = (dom["flops"] if alu else dom["bytes"]) / dom["launches"]
+    roof["kernels"] = {s["name"]: {"launches": s["launches"], "ms": s["ms"]} for s in stats}
+    return roof
 
-    if args.impl == "reference":
-        return reference_arm(args, n, w, b)
 
-    import numpy as np
+def setup_distributed():
     import torch
-
-    import paper_1709_00302_gb300 as br
-    import workloads
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -235,25 +291,305 @@ def main():
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
+    return world, rank, local, dist, dev
+
+
+def make_problem(args, br, dev, stream):
+    """Workload -> dict with the device input A0 (restored before every step), the call,
+    the nominal flops of one step and the backward-error check."""
+    import numpy as np
+    import torch
+
+    import workloads
+
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from checks import gen_probe_backward, sym_probe_backward
+
+    wl = args.workload
+    if wl in ("sy2sb", "sy2sb_large"):
+        n, w, b = args.n, args.w, args.b
+        if wl == "sy2sb_large":
+            # 8.6 GB: drawn on the device (torch Philox, seed 0), symmetrised there
+            g = torch.Generator(device=dev)
+            g.manual_seed(0)
+            G = torch.randn((n, n), dtype=torch.float64, device=dev, generator=g)
+            A0 = ((G + G.t()) * 0.5).t().contiguous().t()
+            del G
+            A_host = None
+            desc = f"sy2sb n={n} w={w} b={b} N(0,1) symmetrised (drawn on the device)"
+        else:
+            A_host, _ = workloads.sym_known_spectrum(n, 0, 1)
+            A0 = torch.from_numpy(A_host).to(dev)
+            desc = (f"sy2sb n={n} w={w} b={b} known-spectrum (lam log-uniform [1e-6,1], random signs)")
+
+        def make_call(precision, lookahead):
+            o = br.make_opts(b=b, lookahead=lookahead, precision=precision)
+            tau = torch.zeros(n - w, dtype=torch.float64, device=dev)
+            work = torch.empty(br.bandred_sy2sb_workspace(n, w, o), dtype=torch.uint8, device=dev)
+            status = torch.zeros(1, dtype=torch.int32, device=dev)
+
+            def call(M):
+                rc = br.bandred_sy2sb_ex(M, w, tau, o, work, status, stream)
+                if rc != 0:
+                    raise br.BandredError(rc, "bandred_sy2sb_ex")
+            return call, (tau,), status
+
+        def backward(A, outs):
+            if A_host is None:
+                return None
+            return sym_probe_backward(A_host, A.cpu().numpy(), outs[0].cpu().numpy(), w, probes=4)
+
+        return dict(A0=A0, make_call=make_call, flops=nominal_flops(n), backward=backward, desc=desc,
+                    config={"n": n, "w": w, "b": b}, units=1)
+    if wl == "ge2gb":
+        m = n = args.n
+        w, b = args.w, args.b
+        A_host = workloads.gen_gaussian(m, n, 0)
+        A0 = torch.from_numpy(A_host).to(dev)
+
+        def make_call(precision, lookahead):
+            o = br.make_opts(b=b, lookahead=lookahead, precision=precision)
+            tq = torch.zeros(n, dtype=torch.float64, device=dev)
+            tp = torch.zeros(max(n - w, 0), dtype=torch.float64, device=dev)
+            work = torch.empty(br.bandred_ge2gb_workspace(m, n, w, o), dtype=torch.uint8, device=dev)
+            status = torch.zeros(1, dtype=torch.int32, device=dev)
+
+            def call(M):
+                rc = br.bandred_ge2gb_ex(M, w, tq, tp, o, work, status, stream)
+                if rc != 0:
+                    raise br.BandredError(rc, "bandred_ge2gb_ex")
+            return call, (tq, tp), status
+
+        def backward(A, outs):
+            return gen_probe_backward(A_host, A.cpu().numpy(), outs[0].cpu().numpy(), outs[1].cpu().numpy(), w,
+                                      probes=4)
+
+        return dict(A0=A0, make_call=make_call, flops=4.0 * (m * n * n - n ** 3 / 3.0), backward=backward,
+                    desc=f"ge2gb m=n={n} w={w} b={b} N(0,1)", config={"m": m, "n": n, "w": w, "b": b}, units=1)
+    raise ValueError(wl)
+
+
+def bench_batched(args, br, dev, stream, world, rank, dist):
+    """1000 symmetric (n ~ U[64,1024]) and 1000 general (n ~ U[64,1024], m ~ U[n,2n])
+    matrices, w in {16, 32}; every step restores the inputs and replays one captured CUDA
+    graph holding both batched runs."""
+    import torch
+
+    import workloads
+
+    sym, gen = workloads.batched_mix(args.batch_sym, args.batch_gen, seed=0)
+    # one flat device buffer per kind; matrices are column-major views into it
+    tot_s = sum(n * n for n, _ in sym)
+    tot_g = sum(m * n for m, n, _ in gen)
+    g = torch.Generator(device=dev)
+    g.manual_seed(0)
+    flat_s0 = torch.randn(tot_s, dtype=torch.float64, device=dev, generator=g)
+    flat_g0 = torch.randn(tot_g, dtype=torch.float64, device=dev, generator=g)
+    flat_s, flat_g = flat_s0.clone(), flat_g0.clone()
+    offs = [0]
+    for n, _ in sym:
+        offs.append(offs[-1] + n * n)
+    offg = [0]
+    for m, n, _ in gen:
+        offg.append(offg[-1] + m * n)
+    As, off = [], 0
+    for n, _ in sym:
+        v = flat_s[off:off + n * n].view(n, n).t()  # column-major view
+        As.append(v)
+        off += n * n
+    # symmetrise each symmetric matrix's lower triangle source: (G + G^T)/2
+    for a in As:
+        a.copy_((a + a.t()) * 0.5)
+    flat_s0.copy_(flat_s)
+    Gs, off = [], 0
+    for m, n, _ in gen:
+        Gs.append(flat_g[off:off + m * n].view(n, m).t())
+        off += m * n
+    opts = br.make_opts(b=args.batch_b, precision=args.precision)
+    taus = [torch.zeros(max(n - w, 0), dtype=torch.float64, device=dev) for n, w in sym]
+    tqs = [torch.zeros(n, dtype=torch.float64, device=dev) for _, n, _ in gen]
+    tps = [torch.zeros(max(n - w, 0), dtype=torch.float64, device=dev) for _, n, w in gen]
+    sb = br.SyBatch(As, [w for _, w in sym], taus, opts)
+    gb = br.GeBatch(Gs, [w for _, _, w in gen], tqs, tps, opts)
+    ws = torch.empty(max(sb.workspace(), 256), dtype=torch.uint8, device=dev)
+    wg = torch.empty(max(gb.workspace(), 256), dtype=torch.uint8, device=dev)
+    st = torch.zeros(2, dtype=torch.int32, device=dev)
+    cap = torch.cuda.Stream(device=dev)
+    cap.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(cap):
+        assert sb.plan(ws, cap) == 0, br.bandred_last_error()
+        assert gb.plan(wg, cap) == 0, br.bandred_last_error()
+        cap.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        l0 = br.bandred_launch_count()
+        with torch.cuda.graph(graph, stream=cap):
+            flat_s.copy_(flat_s0)
+            flat_g.copy_(flat_g0)
+            assert sb.run(ws, st[0:1], cap) == 0
+            assert gb.run(wg, st[1:2], cap) == 0
+        launches_per_step = br.bandred_launch_count() - l0
+    # replays run on the current stream: make it the stream the events are recorded on
+    with torch.cuda.stream(cap):
+        for _ in range(args.warmup):
+            graph.replay()
+        torch.cuda.synchronize(dev)
+        if dist is not None:
+            dist.barrier()
+        sampler = ClockSampler(dev.index or 0)
+        sampler.start()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for e0, e1 in ev:
+            e0.record(cap)
+            graph.replay()
+            e1.record(cap)
+        torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    assert int(st.sum().item()) == 0, st
+    # one profiled step outside the graph: per-kernel-class times for the roofline
+    with torch.cuda.stream(cap):
+        flat_s.copy_(flat_s0)
+        flat_g.copy_(flat_g0)
+        torch.cuda.synchronize(dev)
+        br.bandred_profile_begin()
+        assert sb.run(ws, st[0:1], cap) == 0
+        assert gb.run(wg, st[1:2], cap) == 0
+        stats = br.bandred_profile_end()
+    roof = roofline(stats, args.precision)
+    # end to end: pinned host inputs -> device, both batched runs, outputs -> host
+    hs, hg = flat_s0.cpu().pin_memory(), flat_g0.cpu().pin_memory()
+    bs, bg = torch.empty_like(hs).pin_memory(), torch.empty_like(hg).pin_memory()
+    e2e_ms = []
+    with torch.cuda.stream(cap):
+        for it in range(3):
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(cap)
+            flat_s.copy_(hs, non_blocking=True)
+            flat_g.copy_(hg, non_blocking=True)
+            assert sb.run(ws, st[0:1], cap) == 0
+            assert gb.run(wg, st[1:2], cap) == 0
+            bs.copy_(flat_s, non_blocking=True)
+            bg.copy_(flat_g, non_blocking=True)
+            e1.record(cap)
+            torch.cuda.synchronize(dev)
+            if it > 0:
+                e2e_ms.append(e0.elapsed_time(e1))
+    e2e_step = sum(e2e_ms) / len(e2e_ms)
+    tau_bytes = sum(t.numel() * 8 for t in taus + tqs + tps)
+    e2e = {"value": world * (len(sym) + len(gen)) / (e2e_step / 1e3), "unit": "mats/s",
+           "h2d_bytes_per_step": (hs.numel() + hg.numel()) * 8,
+           "d2h_bytes_per_step": (bs.numel() + bg.numel()) * 8, "ms_per_step": e2e_step,
+           "note": f"the packed outputs (band + reflectors) are copied back; the {tau_bytes} bytes of tau "
+                   f"vectors stay on the device"}
+    del hs, hg, bs, bg
+    cpu = None
+    if world == 1 and rank == 0 and not args.no_cpu_baseline:
+        import oracle
+
+        cores = oracle.set_threads(0)
+        t0 = time.perf_counter()
+        done = 0
+        for q in range(min(len(sym), len(gen))):
+            n_, w_ = sym[q]
+            oracle.sy2sb(flat_s0[offs[q]:offs[q] + n_ * n_].view(n_, n_).t().cpu().numpy(), w_)
+            m_, n2, w2 = gen[q]
+            oracle.ge2gb(flat_g0[offg[q]:offg[q] + m_ * n2].view(n2, m_).t().cpu().numpy(), w2)
+            done += 2
+            if time.perf_counter() - t0 > args.cpu_seconds:
+                break
+        dt = time.perf_counter() - t0
+        cpu = {"value": done / dt, "unit": "mats/s", "cores": cores, "kind": "oracle",
+               "sample": f"the first {done // 2} symmetric and {done // 2} general shapes of the mix ({dt:.1f} s)"}
+    ms_step = sum(ms) / len(ms)
+    t = torch.tensor([ms_step], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    count = len(sym) + len(gen)
+    value = world * count / (ms_max / 1e3)
+    flops = sum(nominal_flops(n) for n, _ in sym) + sum(4.0 * (m * n * n - n ** 3 / 3.0) for m, n, _ in gen)
+    # accuracy of one matrix of each kind, checked against its input on the host
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from checks import gen_probe_backward, sym_probe_backward
+
+    i_s = max(range(len(sym)), key=lambda q: sym[q][0])
+    i_g = max(range(len(gen)), key=lambda q: gen[q][1])
+    n_s, w_s = sym[i_s]
+    A_in = flat_s0[offs[i_s]:offs[i_s] + n_s * n_s].view(n_s, n_s).t().cpu().numpy()
+    bw_s = sym_probe_backward(A_in, As[i_s].cpu().numpy(), taus[i_s].cpu().numpy(), w_s, probes=4)
+    m_g, n_g, w_g = gen[i_g]
+    G_in = flat_g0[offg[i_g]:offg[i_g] + m_g * n_g].view(n_g, m_g).t().cpu().numpy()
+    bw_g = gen_probe_backward(G_in, Gs[i_g].cpu().numpy(), tqs[i_g].cpu().numpy(), tps[i_g].cpu().numpy(), w_g,
+                              probes=4)
+    if rank == 0:
+        line = {
+            "metric": HEADLINE_METRIC, "value": value, "unit": "mats/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": DTYPES[args.precision],
+            "data": "synthetic",
+            "config": {"workload": f"batched: {len(sym)} sy2sb n~U[64,1024] + {len(gen)} ge2gb n~U[64,1024] "
+                                   f"m~U[n,2n], w in {{16,32}}, N(0,1) drawn on the device, one CUDA graph "
+                                   f"replay per step", "count": count, "precision": args.precision,
+                       "b": args.batch_b, "l2": "inputs restored from resident copies inside the graph"},
+            "tflops_nominal": flops / (ms_max / 1e3) / 1e12,
+            "backward_error": {"sy2sb_largest": bw_s, "ge2gb_largest": bw_g},
+            "roofline": roof, "e2e": e2e, "cpu_baseline": cpu,
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clocks, "step_ms": ms,
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="sy2sb", choices=["sy2sb", "ge2gb", "sy2sb_large", "batched"],
+                    help="sy2sb: n=8192 w=b=64 known spectrum (headline); ge2gb: 8192^2 w=64; "
+                         "sy2sb_large: n=32768 w=b=128; batched: 1000 + 1000 uneven matrices")
+    ap.add_argument("--n", type=int, default=None)
+    ap.add_argument("--w", type=int, default=None)
+    ap.add_argument("--b", type=int, default=None)
+    ap.add_argument("--precision", default="bf16x6", choices=["fp64", "bf16x3", "bf16x6", "ozaki"])
+    ap.add_argument("--lookahead", type=int, default=-1)
+    ap.add_argument("--batch-sym", type=int, default=1000)
+    ap.add_argument("--batch-gen", type=int, default=1000)
+    ap.add_argument("--batch-b", type=int, default=0)
+    ap.add_argument("--no-fp64-path", action="store_true", help="skip the FP64 comparison line")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-cols", type=int, default=96, help="reflectors per reference-arm step")
+    args = ap.parse_args()
+    defaults = {"sy2sb": (8192, 64, 64), "ge2gb": (8192, 64, 64), "sy2sb_large": (32768, 128, 128),
+                "batched": (0, 0, 0)}[args.workload]
+    args.n = args.n or defaults[0]
+    args.w = args.w or defaults[1]
+    args.b = args.b or defaults[2]
+    n, w, b = args.n, args.w, args.b
+
+    if args.impl == "reference":
+        return reference_arm(args, n, w, b)
+
+    import torch
+
+    import paper_1709_00302_gb300 as br
+
+    world, rank, local, dist, dev = setup_distributed()
     br.build()
     br.lib()
-
-    A_host, lam = workloads.sym_known_spectrum(n, 0, 1)
-    A0 = torch.from_numpy(A_host).to(dev)  # column-major (Fortran) strides are kept
-    A = torch.empty_like(A0)
     stream = torch.cuda.current_stream(dev)
+    if args.workload == "batched":
+        return bench_batched(args, br, dev, stream, world, rank, dist)
 
-    def make_call(precision, lookahead):
-        o = br.make_opts(b=b, lookahead=lookahead, precision=precision)
-        tau = torch.zeros(n - w, dtype=torch.float64, device=dev)
-        work = torch.empty(br.bandred_sy2sb_workspace(n, w, o), dtype=torch.uint8, device=dev)
-        status = torch.zeros(1, dtype=torch.int32, device=dev)
-
-        def call(M):
-            rc = br.bandred_sy2sb_ex(M, w, tau, o, work, status, stream)
-            if rc != 0:
-                raise br.BandredError(rc, "bandred_sy2sb_ex")
-        return call, tau, status
+    prob = make_problem(args, br, dev, stream)
+    A0 = prob["A0"]
+    A = torch.empty_like(A0)
+    A.copy_(A0)
+    make_call = prob["make_call"]
 
     def barrier():
         if dist is not None:
@@ -284,57 +620,26 @@ def main():
         return ms, stats, launches, clocks
 
     # ---- headline: the configured precision with look-ahead
-    call, tau, status = make_call(args.precision, args.lookahead)
+    call, outs, status = make_call(args.precision, args.lookahead)
     ms, stats, launches, clocks = timed_steps(call, args.steps, args.warmup, profile=True)
     st = int(status.item())
     if st != 0:
         raise br.BandredError(st, "device status")
-    my_ms = max(ms)
     ms_step = sum(ms) / len(ms)
     tot = torch.tensor([ms_step], dtype=torch.float64, device=dev)
     if dist is not None:
         dist.all_reduce(tot, op=dist.ReduceOp.MAX)
     ms_step_max = float(tot.item())
-    value = world * nominal_flops(n) / (ms_step_max / 1e3) / 1e12
-
-    # backward error of the headline result, estimated with Gaussian probes (test helper)
-    sys.path.insert(0, os.path.join(ROOT, "tests"))
-    from checks import sym_probe_backward
-
-    Aout = A.cpu().numpy()
-    bwd = sym_probe_backward(A_host, Aout, tau.cpu().numpy(), w, probes=4)
+    value = world * prob["flops"] / (ms_step_max / 1e3) / 1e12
+    bwd = prob["backward"](A, outs)
 
     # ---- roofline of the dominant kernel class (live CUDA-event timing above)
-    peaks, peak_src = load_peaks()
-    dom = max(stats, key=lambda s: s["ms"]) if stats else None
-    roof = None
-    if dom is not None:
-        per_launch_ms = dom["ms"] / dom["launches"]
-        # The panel (FP64 reflectors) and the whole FP64 path are bound by the FP64 pipe;
-        # the split-precision trailing updates stream A2 through HBM.
-        alu = args.precision == "fp64" or dom["name"] in ("panel_qr_f64", "gemm")
-        if alu:
-            achieved = dom["flops"] / (dom["ms"] / 1e3) / 1e12
-            peak = 1.25
-            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "kernel": dom["name"], "peak_source": "nominal FP64 rate of GB300 (1.25 TFLOP/s; 1.20 measured "
-                                                          "with an FMA loop)"}
-        else:
-            achieved = dom["bytes"] / (dom["ms"] / 1e3) / 1e9
-            peak = peaks["hbm_gbs"]
-            roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                    "kernel": dom["name"], "peak_source": f"hbm_gbs ({peak_src})"}
-        traffic = kernel_traffic(dom["name"])
-        roof["traffic"] = None if traffic is None else traffic * dom["bytes"] / dom["launches"]
-        roof["launches"] = dom["launches"]
-        roof["avg_launch_ms"] = per_launch_ms
-        roof["algorithmic_per_launch"] = (dom["flops"] if alu else dom["bytes"]) / dom["launches"]
-        roof["kernels"] = {s["name"]: {"launches": s["launches"], "ms": s["ms"]} for s in stats}
+    roof = roofline(stats, args.precision)
 
     # ---- e2e through the C ABI with host buffers
-    A_pin = torch.from_numpy(A_host).pin_memory()
+    A_pin = A0.cpu().pin_memory()
     A_back = torch.empty_like(A_pin).pin_memory()
-    tau_back = torch.empty(n - w, dtype=torch.float64).pin_memory()
+    outs_back = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in outs]
     e2e_ms = []
     for it in range(max(2, min(args.steps, 3)) + 1):
         torch.cuda.synchronize(dev)
@@ -343,41 +648,42 @@ def main():
         A.copy_(A_pin, non_blocking=True)
         call(A)
         A_back.copy_(A, non_blocking=True)
-        tau_back.copy_(tau, non_blocking=True)
+        for t, tb in zip(outs, outs_back):
+            tb.copy_(t, non_blocking=True)
         e1.record(stream)
         torch.cuda.synchronize(dev)
         if it > 0:
             e2e_ms.append(e0.elapsed_time(e1))
     e2e_step = sum(e2e_ms) / len(e2e_ms)
-    e2e = {"value": nominal_flops(n) / (e2e_step / 1e3) / 1e12 * world, "unit": "TFLOP/s",
-           "h2d_bytes_per_step": A_pin.numel() * 8, "d2h_bytes_per_step": A_back.numel() * 8 + tau_back.numel() * 8,
+    e2e = {"value": prob["flops"] / (e2e_step / 1e3) / 1e12 * world, "unit": "TFLOP/s",
+           "h2d_bytes_per_step": A_pin.numel() * 8,
+           "d2h_bytes_per_step": A_back.numel() * 8 + sum(t.numel() * 8 for t in outs_back),
            "ms_per_step": e2e_step}
+    del A_pin, A_back
 
     # ---- plain FP64 GPU path on the same matrix (comparison line)
     fp64 = None
     if args.precision != "fp64" and not args.no_fp64_path:
-        call64, tau64, _ = make_call("fp64", args.lookahead)
+        call64, outs64, _ = make_call("fp64", args.lookahead)
         ms64, _, _, _ = timed_steps(call64, 1, 1)
-        b64 = sym_probe_backward(A_host, A.cpu().numpy(), tau64.cpu().numpy(), w, probes=4)
-        fp64 = {"ms_per_step": ms64[0], "value": nominal_flops(n) / (ms64[0] / 1e3) / 1e12,
+        b64 = prob["backward"](A, outs64)
+        fp64 = {"ms_per_step": ms64[0], "value": prob["flops"] / (ms64[0] / 1e3) / 1e12,
                 "backward_error": b64, "speedup_of_headline": ms64[0] / ms_step}
 
     # ---- CPU baseline: the oracle on the host cores, bounded sample
     cpu = None
-    if world == 1 and rank == 0 and not args.no_cpu_baseline:
-        cpu = run_cpu_baseline(A_host, n, w, args.cpu_seconds)
+    if world == 1 and rank == 0 and not args.no_cpu_baseline and args.workload == "sy2sb":
+        cpu = run_cpu_baseline(A0.cpu().numpy(), n, w, args.cpu_seconds)
 
     if rank == 0:
-        dtype = {"fp64": "f64", "bf16x3": "bf16x3->f64", "bf16x6": "bf16x6->f64", "ozaki": "ozaki-bf16->f64"}
         line = {
             "metric": HEADLINE_METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step_max, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": dtype[args.precision], "data": "synthetic",
-            "config": {"workload": f"sy2sb n={n} w={w} b={b} known-spectrum (lam log-uniform [1e-6,1], random "
-                                   f"signs) precision={args.precision} lookahead={args.lookahead}",
-                       "n": n, "w": w, "b": b, "precision": args.precision, "lookahead": args.lookahead,
-                       "l2": "inputs (512 MB) larger than L2; matrix restored from a resident copy between steps",
-                       "parallelism": "replicas" if world > 1 else "single"},
+            "vs_baseline": None, "dtype": DTYPES[args.precision], "data": "synthetic",
+            "config": dict({"workload": f"{prob['desc']} precision={args.precision} lookahead={args.lookahead}",
+                            "precision": args.precision, "lookahead": args.lookahead,
+                            "l2": "inputs larger than L2; matrix restored from a resident copy between steps",
+                            "parallelism": "replicas" if world > 1 else "single"}, **prob["config"]),
             "backward_error": bwd,
             "roofline": roof,
             "cpu_baseline": cpu,

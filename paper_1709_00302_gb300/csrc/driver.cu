@@ -695,6 +695,8 @@ int split_product(int M, int N, int K, const double* A, int64_t lda, int mode, c
                   double alpha, double beta, double* C, int64_t ldc, const SplitBufs& sb, int S, int sms, int* status,
                   unsigned long long limit_ns, cudaStream_t s) {
   if (M <= 0 || N <= 0) return 0;
+  // algorithmic: one read of op(A) and of Bm, one write of C
+  prof::Scope sc(prof::kStream, s, 2.0 * M * N * K, 8.0 * ((double)M * K + (double)K * N + (double)M * N));
   const int BN = split::stream_bn(N);
   const int nkb = (K + 31) / 32;
   split::PackParams pp{};
@@ -740,6 +742,8 @@ int split_product(int M, int N, int K, const double* A, int64_t lda, int mode, c
 int split_rank(int M, int N, int K, const double* Am, int64_t lda, const double* Bm, int64_t ldb, double* C,
                int64_t ldc, const SplitBufs& sb, int S, int* status, unsigned long long limit_ns, cudaStream_t s) {
   if (M <= 0 || N <= 0 || K <= 0) return 0;
+  // algorithmic: C read and written once, Am and Bm read once
+  prof::Scope sc(prof::kRank, s, 2.0 * M * N * K, 8.0 * (2.0 * M * N + (double)(M + N) * K));
   const int Kr = (K + 63) / 64 * 64;
   split::PackParams pp{};
   pp.M1 = Am;
@@ -813,8 +817,8 @@ struct Ge2gb {
     if (c1 <= c0) return 0;
     const int nc = c1 - c0;
     double* E = A + k + (k + bk + c0) * lda;
-    prof::Scope sc(prof::kGemm, s, 4.0 * j * nc * bk, 8.0 * (3.0 * j * nc + 2.0 * j * bk));
     if (!is_split(o)) {
+      prof::Scope sc(prof::kGemm, s, 4.0 * j * nc * bk, 8.0 * (3.0 * j * nc + 2.0 * j * bk));
       const int sp = choose_splits(bk, nc, j, ws.splitk_cap, sms);
       CK(gemm_f64(bk, nc, j, 1.0, MatView{ws.Wu[buf], ws.ldu, 1}, MatView{E, 1, lda}, 0.0, ws.Z[q], bk, sp,
                   ws.splitk[q], s));
@@ -850,8 +854,8 @@ struct Ge2gb {
     const int nrow = (int)(m - k - bkr);
     if (nrow <= 0) return 0;
     double* D = A + (k + bkr) + (k + w) * lda;
-    prof::Scope sc(prof::kGemm, s, 4.0 * nrow * jr * bkr, 8.0 * (3.0 * nrow * jr + 2.0 * nrow * bkr));
     if (!is_split(o)) {
+      prof::Scope sc(prof::kGemm, s, 4.0 * nrow * jr * bkr, 8.0 * (3.0 * nrow * jr + 2.0 * nrow * bkr));
       const int sp = choose_splits(nrow, (int)bkr, jr, ws.splitk_cap, sms);
       CK(gemm_f64(nrow, (int)bkr, jr, 1.0, MatView{D, 1, lda}, MatView{ws.Wv, 1, ws.ldv}, 0.0, ws.P, ws.ldu, sp,
                   ws.splitk[0], s));

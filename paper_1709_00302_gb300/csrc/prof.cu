@@ -35,7 +35,8 @@ cudaEvent_t take_event() {
   return g_pool[g_pool_used++];
 }
 
-const char* const kNames[kNumKinds] = {"panel_qr_f64", "symm", "syr2k", "gemm", "splitk_reduce", "convert", "other"};
+const char* const kNames[kNumKinds] = {"panel_qr_f64", "symm", "syr2k", "gemm", "splitk_reduce", "convert", "other",
+                                           "stream_gemm", "rank_update"};
 
 }  // namespace
 

@@ -6,7 +6,10 @@
 namespace bandred {
 namespace prof {
 
-enum Kind { kPanel = 0, kSymm, kSyr2k, kGemm, kSplitReduce, kConvert, kOther, kNumKinds };
+// kStream / kRank: the general split-precision products of ge2gb (C = op(A) B streaming A
+// once; C += A B^T reading and writing C once); kGemm: FP64 products and the small
+// split-precision products of sy2sb.
+enum Kind { kPanel = 0, kSymm, kSyr2k, kGemm, kSplitReduce, kConvert, kOther, kStream, kRank, kNumKinds };
 
 const char* kind_name(int k);
 void count_launch(int n = 1);

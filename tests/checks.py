@@ -142,3 +142,35 @@ def sym_probe_backward(A: np.ndarray, Aout: np.ndarray, tau: np.ndarray, w: int,
             BY[:-d] += diag[:, None] * Y[d:]
     QBY = sym_apply_q(Aout, tau, w, BY)
     return float(np.linalg.norm(AX - QBY) / np.linalg.norm(AX))
+
+
+def gen_probe_backward(A: np.ndarray, Aout: np.ndarray, tauq: np.ndarray, taup: np.ndarray, w: int,
+                       probes: int = 8, seed: int = 5) -> float:
+    """||(A - U B V^T) X||_F / ||A X||_F for Gaussian probes X (n x probes), with U and V
+    applied through the reflectors (ge2gb layout) and B read from the upper band."""
+    m, n = A.shape
+    X = np.random.Generator(np.random.PCG64(seed)).standard_normal((n, probes))
+    AX = A @ X
+    # Y = V^T X: V = Hp_0 Hp_1 ..., so V^T X applies Hp_0 first
+    Y = np.array(X, copy=True)
+    for c in range(len(taup)):
+        t = taup[c]
+        if t == 0.0:
+            continue
+        r0 = c + w
+        v = np.concatenate(([1.0], Aout[c, r0 + 1:]))
+        Y[r0:] -= t * np.outer(v, v @ Y[r0:])
+    BY = np.zeros((m, probes))
+    for d in range(0, w + 1):
+        diag = np.diagonal(Aout, d)  # B(i, i+d)
+        k = len(diag)
+        BY[:k] += diag[:, None] * Y[d:d + k]
+    # U BY: U = Hq_0 Hq_1 ..., applied last-first
+    Z = BY
+    for c in reversed(range(len(tauq))):
+        t = tauq[c]
+        if t == 0.0:
+            continue
+        v = np.concatenate(([1.0], Aout[c + 1:, c]))
+        Z[c:] -= t * np.outer(v, v @ Z[c:])
+    return float(np.linalg.norm(AX - Z) / np.linalg.norm(AX))
