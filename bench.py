@@ -405,7 +405,7 @@ def bench_batched(args, br, dev, stream, world, rank, dist):
     for m, n, _ in gen:
         Gs.append(flat_g[off:off + m * n].view(n, m).t())
         off += m * n
-    opts = br.make_opts(b=args.batch_b, precision=args.precision)
+    opts = br.make_opts(b=args.batch_b, precision=args.precision, panel_ctas=args.panel_ctas)
     taus = [torch.zeros(max(n - w, 0), dtype=torch.float64, device=dev) for n, w in sym]
     tqs = [torch.zeros(n, dtype=torch.float64, device=dev) for _, n, _ in gen]
     tps = [torch.zeros(max(n - w, 0), dtype=torch.float64, device=dev) for _, n, w in gen]
@@ -531,7 +531,7 @@ def bench_batched(args, br, dev, stream, world, rank, dist):
             "config": {"workload": f"batched: {len(sym)} sy2sb n~U[64,1024] + {len(gen)} ge2gb n~U[64,1024] "
                                    f"m~U[n,2n], w in {{16,32}}, N(0,1) drawn on the device, one CUDA graph "
                                    f"replay per step", "count": count, "precision": args.precision,
-                       "b": args.batch_b, "l2": "inputs restored from resident copies inside the graph"},
+                       "b": args.batch_b, "panel_ctas": args.panel_ctas, "l2": "inputs restored from resident copies inside the graph"},
             "tflops_nominal": flops / (ms_max / 1e3) / 1e12,
             "backward_error": {"sy2sb_largest": bw_s, "ge2gb_largest": bw_g},
             "roofline": roof, "e2e": e2e, "cpu_baseline": cpu,
@@ -559,6 +559,7 @@ def main():
     ap.add_argument("--batch-sym", type=int, default=1000)
     ap.add_argument("--batch-gen", type=int, default=1000)
     ap.add_argument("--batch-b", type=int, default=0)
+    ap.add_argument("--panel-ctas", type=int, default=0, help="panel_ctas option (batched: CTAs per matrix panel)")
     ap.add_argument("--no-fp64-path", action="store_true", help="skip the FP64 comparison line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

@@ -62,7 +62,9 @@ typedef struct bandred_opts {
     int precision;         /* enum bandred_precision */
     int slices;            /* slices for BANDRED_OZAKI (2..8); ignored otherwise */
     int panel_ctas;        /* CTAs of the panel factorisation (0 = all SMs when no
-                              look-ahead, a tuned share otherwise) */
+                              look-ahead, a tuned share otherwise).  Batched calls: CTAs
+                              (one thread-block cluster, rounded up to a power of two
+                              <= 16) per matrix panel; 0 = about 128 rows per CTA */
     int timeout_ms;        /* limit of every device-side wait (0 = 2000 ms) */
     int debug;             /* 0.  Tests only: 1 makes the first device-side wait
                               unsatisfiable, so the call ends through its bounded-wait

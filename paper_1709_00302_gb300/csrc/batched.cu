@@ -92,9 +92,22 @@ constexpr int kBatchSplits = 4;
 
 int batch_b(const Options& o, int64_t w) { return (int)std::min<int64_t>(o.b > 0 ? o.b : std::min<int64_t>(w, 32), w); }
 
-int cluster_size_for(int jmax) {
+// Rows per CTA of the batched panels when the cluster size is not given: small enough
+// that four CTAs share an SM (the FP64 work of one CTA overlaps the cluster barriers of
+// the others), large enough that the barriers are few per row.
+constexpr int kBatchPanelRows = 128;
+
+// CTAs per problem (cluster size, a power of two <= 16) for panels of up to jmax x bkmax:
+// `want` (the panel_ctas option) rounded up to a power of two, else the size that gives
+// about kBatchPanelRows rows per CTA; raised until the slab fits in shared memory.
+int cluster_size_for(int jmax, int bkmax, int want) {
   int C = 1;
-  while (C < 16 && (jmax + C - 1) / C > 64) C *= 2;
+  if (want > 0) {
+    while (C < 16 && C < want) C *= 2;
+  } else {
+    while (C < 16 && (jmax + C - 1) / C > kBatchPanelRows) C *= 2;
+  }
+  while (C < 16 && panel_cluster_rows(jmax, bkmax, C) == 0) C *= 2;
   return C;
 }
 
@@ -144,7 +157,8 @@ int64_t pack_groups(const PackParams& pp) { return (int64_t)pp.nrb * pp.nkb * pp
 struct Batcher {
   Schedule& S;
   int sms;
-  explicit Batcher(Schedule& s, int n_sms) : S(s), sms(n_sms) {}
+  int cluster;  // panel_ctas option: CTAs per problem of the panel launches (0 = auto)
+  Batcher(Schedule& s, int n_sms, int cl) : S(s), sms(n_sms), cluster(cl) {}
 
   void packs(const std::vector<PackParams>& v) {
     if (v.empty()) return;
@@ -199,7 +213,7 @@ struct Batcher {
       jmax = std::max(jmax, p.j);
       bkmax = std::max(bkmax, p.bk);
     }
-    const int C = cluster_size_for(jmax);
+    const int C = cluster_size_for(jmax, bkmax, cluster);
     std::vector<PanelParams> w = v;
     int Rpmax = 1;
     for (auto& p : w) {
@@ -312,7 +326,7 @@ void build_sy2sb(std::vector<SyMat>& mats, const Options& o, int S, int sms, int
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return mats[a].iters > mats[b].iters; });
   const int tmax = mats.empty() ? 0 : mats[order[0]].iters;
-  Batcher B(sch, sms);
+  Batcher B(sch, sms, o.panel_ctas);
   for (int t = 0; t < tmax; ++t) {
     std::vector<int> act;
     for (int q : order)
@@ -468,7 +482,7 @@ void build_ge2gb(std::vector<GeMat>& mats, const Options& o, int S, int sms, int
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return mats[a].iters > mats[b].iters; });
   const int tmax = mats.empty() ? 0 : mats[order[0]].iters;
-  Batcher B(sch, sms);
+  Batcher B(sch, sms, o.panel_ctas);
   for (int t = 0; t < tmax; ++t) {
     std::vector<int> act;
     for (int q : order)

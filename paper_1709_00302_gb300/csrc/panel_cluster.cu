@@ -23,7 +23,7 @@ namespace cg = cooperative_groups;
 __device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
 __device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
 
-__global__ void __launch_bounds__(kPanelThreads, 1)
+__global__ void __launch_bounds__(kPanelThreads, 4)
     panel_cluster_kernel(PanelParams single, const PanelParams* probs) {
   extern __shared__ double smem[];
   constexpr int NT = kPanelThreads;
