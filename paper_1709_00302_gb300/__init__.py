@@ -27,6 +27,8 @@ __all__ = [
     "bandred_status_string", "bandred_last_error", "bandred_profile_begin", "bandred_profile_end",
     "bandred_launch_count", "bandred_kernel_stat", "bandred_gemm_split", "bandred_gemm_split_workspace",
     "bandred_syr2k_split", "bandred_syr2k_split_workspace", "SyBatch", "GeBatch", "sy2sb", "ge2gb", "BandredError",
+    "bandred_mlp_param_count", "bandred_mlp_workspace", "bandred_mlp_forward", "bandred_mlp_loss_grad",
+    "bandred_mlp_adam",
 ]
 
 PRECISIONS = {"fp64": 0, "bf16x3": 1, "bf16x6": 2, "ozaki": 3}
@@ -124,6 +126,18 @@ def lib():
         L.bandred_profile_end.restype = ci
         L.bandred_launch_count.argtypes = []
         L.bandred_launch_count.restype = ctypes.c_longlong
+        # cost model of the autotuner (include/bandred_tune.h)
+        f32 = ctypes.c_float
+        L.bandred_mlp_param_count.argtypes = [ci, ci]
+        L.bandred_mlp_param_count.restype = sz
+        L.bandred_mlp_workspace.argtypes = [ci, ci, ci]
+        L.bandred_mlp_workspace.restype = sz
+        L.bandred_mlp_forward.argtypes = [ci, ci, vp, vp, ci, vp, vp]
+        L.bandred_mlp_forward.restype = ci
+        L.bandred_mlp_loss_grad.argtypes = [ci, ci, vp, vp, vp, ci, vp, vp, vp, sz, vp]
+        L.bandred_mlp_loss_grad.restype = ci
+        L.bandred_mlp_adam.argtypes = [ci, vp, vp, vp, vp, ci, f32, f32, f32, f32, vp]
+        L.bandred_mlp_adam.restype = ci
         _lib = L
     return _lib
 
@@ -270,6 +284,30 @@ def bandred_profile_end(max_entries: int = 16) -> list:
 
 def bandred_launch_count() -> int:
     return lib().bandred_launch_count()
+
+
+# ------------------------------------------------------------------ cost model (bandred_tune.h)
+def bandred_mlp_param_count(d_in: int, hidden: int) -> int:
+    return lib().bandred_mlp_param_count(d_in, hidden)
+
+
+def bandred_mlp_workspace(d_in: int, hidden: int, rows: int) -> int:
+    return lib().bandred_mlp_workspace(d_in, hidden, rows)
+
+
+def bandred_mlp_forward(d_in, hidden, params, X, rows, y, stream=None) -> int:
+    return lib().bandred_mlp_forward(d_in, hidden, _ptr(params), _ptr(X), rows, _ptr(y), _stream(stream))
+
+
+def bandred_mlp_loss_grad(d_in, hidden, params, X, t, rows, grad, loss, work, stream=None) -> int:
+    return lib().bandred_mlp_loss_grad(d_in, hidden, _ptr(params), _ptr(X), _ptr(t), rows, _ptr(grad), _ptr(loss),
+                                       _ptr(work), 0 if work is None else work.numel() * work.element_size(),
+                                       _stream(stream))
+
+
+def bandred_mlp_adam(count, params, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None) -> int:
+    return lib().bandred_mlp_adam(count, _ptr(params), _ptr(grad), _ptr(m), _ptr(v), step, lr, beta1, beta2, eps,
+                                  _stream(stream))
 
 
 # ------------------------------------------------------------------ batched

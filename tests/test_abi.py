@@ -1,6 +1,7 @@
-"""The C-ABI library builds, loads and exports every entry point of include/bandred.h
+"""The C-ABI library builds, loads and exports every entry point declared in include/*.h
 (CPU only: no call here launches device work)."""
 import ctypes
+import glob
 import os
 import re
 
@@ -10,9 +11,11 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def declared_symbols():
-    hdr = open(os.path.join(ROOT, "include", "bandred.h")).read()
-    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
-    return sorted(set(re.findall(r"\b(bandred_[a-z0-9_]+)\s*\(", hdr)))
+    syms = set()
+    for path in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        hdr = re.sub(r"/\*.*?\*/", "", open(path).read(), flags=re.S)
+        syms |= set(re.findall(r"\b(bandred_[a-z0-9_]+)\s*\(", hdr))
+    return sorted(syms)
 
 
 @pytest.fixture(scope="module")
@@ -25,7 +28,8 @@ def L():
 
 def test_every_declared_symbol_is_exported(L):
     syms = declared_symbols()
-    assert len(syms) >= 23
+    assert len(syms) >= 28
+    assert "bandred_mlp_loss_grad" in syms
     for s in syms:
         assert hasattr(L, s), s
 
@@ -67,6 +71,16 @@ def test_invalid_arguments_are_rejected_before_any_device_work(L):
     assert L.bandred_ge2gb_ex(6, 5, 1, fake, 5, fake, fake, None, null, 0, null, null) == -5
     assert L.bandred_ge2gb_ex(6, 5, 1, fake, 6, null, fake, None, null, 0, null, null) == -6
     assert L.bandred_ge2gb_ex(6, 5, 1, fake, 6, fake, null, None, null, 0, null, null) == -7
+    # cost model: shape limits, missing pointers
+    assert L.bandred_mlp_param_count(8, 32) == 8 * 32 + 32 + 32 * 32 + 3 * 32 + 1 - 32
+    assert L.bandred_mlp_param_count(0, 4) == 0 and L.bandred_mlp_param_count(4, 65) == 0
+    assert L.bandred_mlp_forward(33, 4, null, null, 0, null, null) == -1
+    assert L.bandred_mlp_forward(4, 0, null, null, 0, null, null) == -2
+    assert L.bandred_mlp_forward(4, 4, null, null, 0, null, null) == -3
+    assert L.bandred_mlp_loss_grad(4, 4, fake, fake, fake, 0, fake, fake, fake, 1 << 20, null) == -6
+    assert L.bandred_mlp_loss_grad(4, 4, fake, fake, fake, 10, fake, fake, fake, 8, null) == -9
+    assert L.bandred_mlp_adam(4, fake, fake, fake, fake, 0, ctypes.c_float(0.1), ctypes.c_float(0.9),
+                              ctypes.c_float(0.999), ctypes.c_float(1e-8), null) == -6
 
 
 def test_product_path_does_not_import_the_oracle():
