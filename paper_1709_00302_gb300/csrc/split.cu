@@ -17,6 +17,9 @@
 //   rank_update_kernel  C += alpha A B^T for pre-packed A, B with a short reduction
 //                       (Eq. updateA2syr2k on the lower triangle; Eqs. updateCD, updateD).
 #include <algorithm>
+#include <cstring>
+
+#include <cuda.h>  // CUtensorMap and its enums (types only: the encoder is fetched at run time)
 
 #include "common.cuh"
 #include "kernels.h"
@@ -347,6 +350,259 @@ __global__ void __launch_bounds__(NT, 1) stream_gemm_kernel(StreamParams single,
   }
 }
 
+// ================================================================= stream GEMM, TMA
+// The same product as stream_gemm_kernel with the FP64 tiles moved by the tensor-memory
+// accelerator: a stage is one 2-D box of the tensor map (128 rows x 32 k, or for tiles
+// read transposed two 16 x 128 boxes in the 128-byte swizzled layout, whose rows a warp
+// reads without bank conflicts) plus one bulk copy of the packed B slices, both
+// completing on the stage's mbarrier, loaded two stages ahead into a ring of four.  Tiles
+// that cross the diagonal of a symmetric A take the lower box and fetch their upper
+// entries from the mirror position directly.  Slicing works on pairs of entries with
+// integer and FP32 operations (tc::split_pair), and the FP32 chunk sums are accumulated
+// as double-float pairs, so the streamed elements cost no FP64 instruction.
+template <int BN, int S>
+struct TmaSmem {
+  static constexpr int NS = 4;
+  static constexpr size_t tile_bytes = (size_t)BM * BK * 8;
+  static constexpr size_t aslice_bytes = (size_t)BM * BK * 2;
+  static constexpr size_t bslice_bytes = (size_t)BN * BK * 2;
+  static constexpr size_t bstage_bytes = (size_t)S * bslice_bytes;
+  static constexpr size_t off_b = (size_t)NS * tile_bytes;
+  static constexpr size_t off_a = off_b + (size_t)NS * bstage_bytes;
+  static constexpr size_t off_bar = off_a + 2 * (size_t)S * aslice_bytes;
+  static constexpr size_t total = off_bar + 128 + 1024;  // + alignment of the base to 1024
+};
+
+template <int BN, int S>
+__global__ void __launch_bounds__(NT, 1)
+    stream_tma_kernel(StreamParams p, const __grid_constant__ CUtensorMap tm_lower,
+                      const __grid_constant__ CUtensorMap tm_upper) {
+  using L = TmaSmem<BN, S>;
+  constexpr int NS = L::NS;
+  using PR = Products<S>;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
+  double* ring = reinterpret_cast<double*>(smem);
+  unsigned char* bring = smem + L::off_b;
+  unsigned char* aslices = smem + L::off_a;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::off_bar);  // [NS]
+  uint64_t* bar_mma = full + NS;                                      // [2]
+  uint64_t* bar_acc = bar_mma + 2;                                    // [2]
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bar_acc + 2);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int i0 = blockIdx.x * BM;
+  const int z = blockIdx.y;
+  const int st_begin = z * p.stages_per_split;
+  const int st_end = min(p.nkb, st_begin + p.stages_per_split);
+  const int nst = st_end - st_begin;
+  constexpr uint32_t kTmemCols = 2 * BN;
+  const unsigned long long deadline = global_ns() + p.limit_ns;
+
+  if (tid == 0) {
+    for (int q = 0; q < NS; ++q) tc::mbar_init(&full[q], 1);
+    tc::mbar_init(&bar_mma[0], 1);
+    tc::mbar_init(&bar_mma[1], 1);
+    tc::mbar_init(&bar_acc[0], 1);
+    tc::mbar_init(&bar_acc[1], 1);
+    tc::fence_mbar_init();
+    tc::prefetch_tmap(&tm_lower);
+    tc::prefetch_tmap(&tm_upper);
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(tmem_holder, kTmemCols);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_holder;
+
+  // 0: every entry of the tile read in place (A(i, k) at A[i + k lda]); 1: every entry read
+  // transposed (A[k + i lda]); 2: a symmetric tile across the diagonal
+  auto kind_of = [&](int kst) -> int {
+    if (p.mode == kModePlain) return 0;
+    if (p.mode == kModeTrans) return 1;
+    const int k0 = kst * BK;
+    if (k0 + BK - 1 <= i0) return 0;
+    if (k0 >= i0 + BM - 1) return 1;
+    return 2;
+  };
+  auto issue = [&](int ls) {  // one thread
+    const int kst = st_begin + ls, slot = ls % NS, k0 = kst * BK;
+    double* dst = ring + (size_t)slot * BM * BK;
+    tc::mbar_arrive_expect_tx(&full[slot], (uint32_t)(L::tile_bytes + L::bstage_bytes));
+    if (kind_of(kst) == 1) {
+      tc::tma_load_2d(dst, &tm_upper, k0, i0, &full[slot]);
+      tc::tma_load_2d(dst + BM * 16, &tm_upper, k0 + 16, i0, &full[slot]);
+    } else {
+      tc::tma_load_2d(dst, &tm_lower, i0, k0, &full[slot]);
+    }
+    tc::bulk_g2s(bring + (size_t)slot * L::bstage_bytes,
+                 reinterpret_cast<const unsigned char*>(p.Bblob) + (size_t)kst * L::bstage_bytes,
+                 (uint32_t)L::bstage_bytes, &full[slot]);
+  };
+
+  float acc_hi[BN / 2], acc_lo[BN / 2];
+#pragma unroll
+  for (int c = 0; c < BN / 2; ++c) acc_hi[c] = acc_lo[c] = 0.0f;
+  int timed_out = 0;
+  bool range_ok = true;
+
+  auto drain_chunk = [&](int c) {
+    int to = tc::mbar_wait(&bar_acc[c & 1], (c >> 1) & 1, deadline) ? 0 : 1;
+    tc::fence_after_sync();
+    const uint32_t q = warp & 3, h = warp >> 2;
+    const uint32_t taddr = tmem + ((q * 32) << 16) + (uint32_t)((c & 1) * BN + h * (BN / 2));
+    auto add = [&](int cc, float v) {  // (hi, lo) += v, error-free (Knuth's two-sum)
+      const float s = acc_hi[cc] + v;
+      const float bb = s - acc_hi[cc];
+      const float err = (acc_hi[cc] - (s - bb)) + (v - bb);
+      acc_hi[cc] = s;
+      acc_lo[cc] += err;
+    };
+    if (!to) {
+      if constexpr (BN / 2 >= 32) {
+#pragma unroll
+        for (int part = 0; part < BN / 64; ++part) {
+          float v[32];
+          tc::tmem_ld32(taddr + part * 32, v);
+#pragma unroll
+          for (int cc = 0; cc < 32; ++cc) add(part * 32 + cc, v[cc]);
+        }
+      } else {
+        float v[16];
+        tc::tmem_ld16(taddr, v);
+#pragma unroll
+        for (int cc = 0; cc < 16; ++cc) add(cc, v[cc]);
+      }
+    }
+    tc::fence_before_sync();
+    return to;
+  };
+
+  if (tid == 0) {
+    for (int ls = 0; ls < 2 && ls < nst; ++ls) issue(ls);
+  }
+
+  const int ti = tid & (BM - 1), half = tid >> 7;  // this thread: row ti, k in [16 half, 16 half + 16)
+  for (int st = 0; st < nst && !timed_out; ++st) {
+    const int sb = st & 1, slot = st % NS;
+    const int kst = st_begin + st, k0 = kst * BK;
+    int to = 0;
+    if (st >= 2) to = tc::mbar_wait(&bar_mma[sb], ((st - 2) >> 1) & 1, deadline) ? 0 : 1;
+    if (__syncthreads_or(to)) {
+      timed_out = 1;
+      break;
+    }
+    if (tid == 0 && st + 2 < nst) issue(st + 2);
+
+    const int kind = kind_of(kst);
+    double x[16];
+    const int gi = i0 + ti;
+    if (kind == 2) {  // upper entries of a diagonal tile, from the stored mirror A(k, i)
+#pragma unroll
+      for (int kk = 0; kk < 16; ++kk) {
+        const int gk = k0 + 16 * half + kk;
+        x[kk] = (gi < gk && gk < p.K && gi < p.M) ? __ldg(p.A + gk + (int64_t)gi * p.lda) : 0.0;
+      }
+    }
+    to = tc::mbar_wait(&full[slot], (uint32_t)(st / NS) & 1u, deadline) ? 0 : 1;
+    if (__syncthreads_or(to)) {
+      timed_out = 1;
+      break;
+    }
+    const double* tile = ring + (size_t)slot * BM * BK;
+    if (kind == 1) {
+      const double* box = tile + half * (BM * 16) + ti * 16;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const double2 v = *reinterpret_cast<const double2*>(box + 2 * (c ^ (ti & 7)));
+        x[2 * c] = v.x;
+        x[2 * c + 1] = v.y;
+      }
+    } else {
+#pragma unroll
+      for (int kk = 0; kk < 16; ++kk) {
+        const double v = tile[(16 * half + kk) * BM + ti];
+        if (kind == 0 || gi >= k0 + 16 * half + kk) x[kk] = v;
+      }
+    }
+    unsigned char* adst = aslices + (size_t)sb * S * L::aslice_bytes;
+#pragma unroll
+    for (int g = 0; g < 2; ++g) {
+      uint32_t w[4][S];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) range_ok &= tc::split_pair<S>(x[8 * g + 2 * c], x[8 * g + 2 * c + 1], w[c]);
+      const uint32_t off = tc::kmajor_offset(ti, (2 * half + g) * 8, BM);
+#pragma unroll
+      for (int sl = 0; sl < S; ++sl)
+        *reinterpret_cast<uint4*>(adst + sl * L::aslice_bytes + off) = make_uint4(w[0][sl], w[1][sl], w[2][sl], w[3][sl]);
+    }
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+
+    const int chunk = st / CH;
+    if (tid == 0) {
+      tc::fence_after_sync();
+      const uint32_t d = tmem + (uint32_t)((chunk & 1) * BN);
+      constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
+      const uint32_t abase = tc::smem_u32(adst);
+      const uint32_t bbase = tc::smem_u32(bring + (size_t)slot * L::bstage_bytes);
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk) {
+#pragma unroll
+        for (int q = 0; q < PR::n; ++q) {
+          const uint64_t ad = tc::smem_desc(abase + PR::s(q) * L::aslice_bytes + kk * 2 * (BM / 8) * 128,
+                                            (BM / 8) * 128, 128);
+          const uint64_t bd = tc::smem_desc(bbase + PR::t(q) * L::bslice_bytes + kk * 2 * (BN / 8) * 128,
+                                            (BN / 8) * 128, 128);
+          const uint32_t accum = (st % CH == 0 && kk == 0 && q == 0) ? 0u : 1u;
+          tc::mma_bf16(d, ad, bd, idesc, accum);
+        }
+      }
+      tc::mma_commit(&bar_mma[sb]);
+      if (st % CH == CH - 1 || st == nst - 1) tc::mma_commit(&bar_acc[chunk & 1]);
+    }
+    if (st % CH == 0 && st > 0) {
+      to = drain_chunk(chunk - 1);
+      if (__syncthreads_or(to)) timed_out = 1;
+    }
+  }
+  if (!timed_out && nst > 0) {
+    const int to = drain_chunk((nst - 1) / CH);
+    if (__syncthreads_or(to)) timed_out = 1;
+  }
+
+  if (timed_out) {
+    report(p.status, BANDRED_DEV_TIMEOUT);
+    if (tid == 0) {  // let copies and MMAs in flight land before the CTA leaves (bounded)
+      const unsigned long long dl = global_ns() + p.limit_ns;
+      for (int q = 0; q < NS; ++q) tc::mbar_wait(&full[q], 0, dl);
+      for (int b = 0; b < 2; ++b) tc::mbar_wait(&bar_mma[b], 0, dl);
+    }
+  } else {
+    const int q = warp & 3, h = warp >> 2;
+    const int row = i0 + q * 32 + lane;
+    double* P = p.P + (size_t)z * p.split_stride;
+    if (row < p.M) {
+#pragma unroll
+      for (int c = 0; c < BN / 2; ++c) {
+        const int col = h * (BN / 2) + c;
+        if (col < p.N) P[row + (int64_t)col * p.ldp] = tc::f32_to_f64(acc_hi[c]) + tc::f32_to_f64(acc_lo[c]);
+      }
+    }
+  }
+  if (!__syncthreads_and(range_ok ? 1 : 0) && tid == 0) report(p.status, BANDRED_DEV_RANGE);
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
 // ================================================================= rank update
 constexpr int RK = 64;  // reduction depth per smem load
 
@@ -489,6 +745,79 @@ cudaError_t launch_stream(const StreamParams& p, const StreamParams* probs, dim3
   return cudaGetLastError();
 }
 
+template <int BN, int S>
+cudaError_t launch_stream_tma(const StreamParams& p, const CUtensorMap& lo, const CUtensorMap& up, dim3 grid,
+                              cudaStream_t s) {
+  using L = TmaSmem<BN, S>;
+  static_assert(L::total <= 227 * 1024, "TMA stream GEMM shared memory");
+  static int configured = -1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (configured != dev) {
+    cudaError_t e =
+        cudaFuncSetAttribute(stream_tma_kernel<BN, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::total);
+    if (e != cudaSuccess) return e;
+    configured = dev;
+  }
+  stream_tma_kernel<BN, S><<<grid, NT, L::total, s>>>(p, lo, up);
+  prof::count_launch();
+  return cudaGetLastError();
+}
+
+// cuTensorMapEncodeTiled, fetched from the driver once (the library links no libcuda).
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encoder() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(f);
+  }
+  return fn;
+}
+
+// FP64 column-major rows x cols matrix with leading dimension ld, boxes of box0 (along
+// the rows) x box1; `swz` selects the 128-byte swizzle.
+bool encode_f64(CUtensorMap* m, const double* base, int64_t rows, int64_t cols, int64_t ld, uint32_t box0,
+                uint32_t box1, bool swz) {
+  EncodeTiledFn fn = encoder();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)rows, (cuuint64_t)cols};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 8};
+  const cuuint32_t box[2] = {box0, box1};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<double*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, swz ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Tensor maps of the streamed operand when the TMA kernel can take it: 16-byte aligned
+// base, even leading dimension (16-byte row stride), N <= 64.
+bool stream_maps(const StreamParams& p, CUtensorMap* lo, CUtensorMap* up) {
+  if (stream_bn(p.N) > 64 || p.M <= 0 || p.K <= 0) return false;
+  if ((reinterpret_cast<uintptr_t>(p.A) & 15u) != 0 || (p.lda & 1) != 0) return false;
+  bool ok = true;
+  if (p.mode == kModePlain || p.mode == kModeSymLower) {
+    if (p.lda < p.M) return false;
+    ok = ok && encode_f64(lo, p.A, p.M, p.K, p.lda, BM, BK, false);
+  }
+  if (p.mode == kModeTrans || p.mode == kModeSymLower) {
+    if (p.lda < p.K) return false;
+    ok = ok && encode_f64(up, p.A, p.K, p.M, p.lda, 16, BM, true);
+  }
+  if (!ok) return false;
+  if (p.mode == kModePlain) std::memcpy(up, lo, sizeof(CUtensorMap));
+  if (p.mode == kModeTrans) std::memcpy(lo, up, sizeof(CUtensorMap));
+  return true;
+}
+
 template <int S>
 cudaError_t launch_rank(const RankParams& p, const RankParams* probs, dim3 grid, cudaStream_t s) {
   using L = RankSmem<S>;
@@ -546,6 +875,11 @@ static cudaError_t stream_dispatch(int BN, const StreamParams& p, const StreamPa
 cudaError_t stream_gemm(const StreamParams& p, int S, int splits, cudaStream_t s) {
   const int BN = stream_bn(p.N);
   const dim3 grid((p.M + BM - 1) / BM, splits);
+  alignas(64) CUtensorMap lo, up;
+  if (stream_maps(p, &lo, &up)) {
+    if (S == 2) return BN == 32 ? launch_stream_tma<32, 2>(p, lo, up, grid, s) : launch_stream_tma<64, 2>(p, lo, up, grid, s);
+    return BN == 32 ? launch_stream_tma<32, 3>(p, lo, up, grid, s) : launch_stream_tma<64, 3>(p, lo, up, grid, s);
+  }
   return S == 2 ? stream_dispatch<2>(BN, p, nullptr, grid, s) : stream_dispatch<3>(BN, p, nullptr, grid, s);
 }
 

@@ -50,6 +50,21 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                "l"(src), "r"(bytes), "r"(smem_u32(bar))
                : "memory");
 }
+// Tiled 2-D tensor copy global -> shared (TMA): the box of the tensor map at element
+// coordinates (x, y), x along the contiguous dimension; x * 8 bytes must be a multiple of
+// 16 for FP64 maps.  Completes on *bar with the box's byte count (out-of-range elements
+// are written as zeros and counted).
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void prefetch_tmap(const void* tmap) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tmap)) : "memory");
+}
+
 // 8-byte asynchronous copy global -> shared; src_bytes = 0 fills zeros.
 __device__ __forceinline__ void cp_async8(void* dst, const void* src, uint32_t src_bytes) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
@@ -198,6 +213,46 @@ __device__ __forceinline__ bool split_bf16(double x, __nv_bfloat16 (&out)[S]) {
     if (S > 2) out[2] = __float2bfloat16_rn(r - __bfloat162float(s1));
   }
   return true;
+}
+
+
+// FP64 -> FP32 rounded to 24 significant bits (ties away from zero) with integer
+// operations only; false when x is outside 2^-95 <= |x| < 2^127 and not zero (the range
+// in which the slices below stay normal).  Zero gives +0.
+__device__ __forceinline__ bool f64_to_f32_int(double x, float& f) {
+  const uint32_t lo = (uint32_t)__double2loint(x), hi = (uint32_t)__double2hiint(x);
+  const uint32_t mag = hi & 0x7FFFFFFFu;
+  const uint32_t t = mag - (896u << 20);           // FP32 biased exponent in bits 20..27
+  uint32_t m = __funnelshift_l(lo, t, 3);           // (t << 3) | (lo >> 29): 23 mantissa bits
+  m += (lo >> 28) & 1u;                             // round on the first dropped bit
+  const bool zero = (mag | lo) == 0u;
+  f = zero ? 0.0f : __uint_as_float(m | (hi & 0x80000000u));
+  return zero || ((mag >> 20) - 928u <= 221u);
+}
+
+// The S bf16 slices of a pair (a, b) as packed words (low half a, high half b):
+// f = fp32(x); s0 = f truncated to bf16 (its upper half), s1 = bf16_rn(f - s0),
+// s2 = bf16_rn(f - s0 - s1).  The differences are exact in FP32, so s0 + s1 + s2 agrees
+// with x to about 2^-24 relative (2^-17 for S = 2).
+template <int S>
+__device__ __forceinline__ bool split_pair(double a, double b, uint32_t (&w)[S]) {
+  float fa, fb;
+  const bool ok = f64_to_f32_int(a, fa) & f64_to_f32_int(b, fb);
+  const uint32_t ua = __float_as_uint(fa), ub = __float_as_uint(fb);
+  w[0] = __byte_perm(ua, ub, 0x7632);
+  if constexpr (S > 1) {
+    const float da = fa - __uint_as_float(ua & 0xFFFF0000u);
+    const float db = fb - __uint_as_float(ub & 0xFFFF0000u);
+    const __nv_bfloat162 p1 = __floats2bfloat162_rn(da, db);
+    w[1] = *reinterpret_cast<const uint32_t*>(&p1);
+    if constexpr (S > 2) {
+      const float ea = da - __uint_as_float(w[1] << 16);
+      const float eb = db - __uint_as_float(w[1] & 0xFFFF0000u);
+      const __nv_bfloat162 p2 = __floats2bfloat162_rn(ea, eb);
+      w[2] = *reinterpret_cast<const uint32_t*>(&p2);
+    }
+  }
+  return ok;
 }
 
 }  // namespace tc
