@@ -373,8 +373,10 @@ struct TmaSmem {
   static constexpr size_t total = off_bar + 128 + 1024;  // + alignment of the base to 1024
 };
 
+constexpr int kTmaThreads = NT + 32;  // eight converter warps and one control warp
+
 template <int BN, int S>
-__global__ void __launch_bounds__(NT, 1)
+__global__ void __launch_bounds__(kTmaThreads, 1)
     stream_tma_kernel(StreamParams p, const __grid_constant__ CUtensorMap tm_lower,
                       const __grid_constant__ CUtensorMap tm_upper) {
   using L = TmaSmem<BN, S>;
@@ -385,9 +387,10 @@ __global__ void __launch_bounds__(NT, 1)
   double* ring = reinterpret_cast<double*>(smem);
   unsigned char* bring = smem + L::off_b;
   unsigned char* aslices = smem + L::off_a;
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::off_bar);  // [NS]
-  uint64_t* bar_mma = full + NS;                                      // [2]
-  uint64_t* bar_acc = bar_mma + 2;                                    // [2]
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::off_bar);  // [NS] copies landed
+  uint64_t* sliced = full + NS;                                       // [2] slices written
+  uint64_t* bar_mma = sliced + 2;                                     // [2] MMAs of a stage done
+  uint64_t* bar_acc = bar_mma + 2;                                    // [2] MMAs of a chunk done
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bar_acc + 2);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -397,17 +400,17 @@ __global__ void __launch_bounds__(NT, 1)
   const int st_end = min(p.nkb, st_begin + p.stages_per_split);
   const int nst = st_end - st_begin;
   constexpr uint32_t kTmemCols = 2 * BN;
+  constexpr int kConvWarps = NT / 32;
   const unsigned long long deadline = global_ns() + p.limit_ns;
 
   if (tid == 0) {
     for (int q = 0; q < NS; ++q) tc::mbar_init(&full[q], 1);
-    tc::mbar_init(&bar_mma[0], 1);
-    tc::mbar_init(&bar_mma[1], 1);
-    tc::mbar_init(&bar_acc[0], 1);
-    tc::mbar_init(&bar_acc[1], 1);
+    for (int q = 0; q < 2; ++q) {
+      tc::mbar_init(&sliced[q], kConvWarps);
+      tc::mbar_init(&bar_mma[q], 1);
+      tc::mbar_init(&bar_acc[q], 1);
+    }
     tc::fence_mbar_init();
-    tc::prefetch_tmap(&tm_lower);
-    tc::prefetch_tmap(&tm_upper);
   }
   if (warp == 0) {
     tc::tmem_alloc(tmem_holder, kTmemCols);
@@ -428,40 +431,89 @@ __global__ void __launch_bounds__(NT, 1)
     if (k0 >= i0 + BM - 1) return 1;
     return 2;
   };
-  auto issue = [&](int ls) {  // one thread
-    const int kst = st_begin + ls, slot = ls % NS, k0 = kst * BK;
-    double* dst = ring + (size_t)slot * BM * BK;
-    tc::mbar_arrive_expect_tx(&full[slot], (uint32_t)(L::tile_bytes + L::bstage_bytes));
-    if (kind_of(kst) == 1) {
-      tc::tma_load_2d(dst, &tm_upper, k0, i0, &full[slot]);
-      tc::tma_load_2d(dst + BM * 16, &tm_upper, k0 + 16, i0, &full[slot]);
-    } else {
-      tc::tma_load_2d(dst, &tm_lower, i0, k0, &full[slot]);
-    }
-    tc::bulk_g2s(bring + (size_t)slot * L::bstage_bytes,
-                 reinterpret_cast<const unsigned char*>(p.Bblob) + (size_t)kst * L::bstage_bytes,
-                 (uint32_t)L::bstage_bytes, &full[slot]);
-  };
 
+  int timed_out = 0;
+  bool range_ok = true;
   float acc_hi[BN / 2], acc_lo[BN / 2];
 #pragma unroll
   for (int c = 0; c < BN / 2; ++c) acc_hi[c] = acc_lo[c] = 0.0f;
-  int timed_out = 0;
-  bool range_ok = true;
 
-  auto drain_chunk = [&](int c) {
-    int to = tc::mbar_wait(&bar_acc[c & 1], (c >> 1) & 1, deadline) ? 0 : 1;
-    tc::fence_after_sync();
-    const uint32_t q = warp & 3, h = warp >> 2;
-    const uint32_t taddr = tmem + ((q * 32) << 16) + (uint32_t)((c & 1) * BN + h * (BN / 2));
-    auto add = [&](int cc, float v) {  // (hi, lo) += v, error-free (Knuth's two-sum)
-      const float s = acc_hi[cc] + v;
-      const float bb = s - acc_hi[cc];
-      const float err = (acc_hi[cc] - (s - bb)) + (v - bb);
-      acc_hi[cc] = s;
-      acc_lo[cc] += err;
-    };
-    if (!to) {
+  if (warp == kConvWarps) {
+    // ---------------- control warp, one lane: TMA copies three stages ahead, MMAs
+    if (lane == 0 && nst > 0) {
+      tc::prefetch_tmap(&tm_lower);
+      tc::prefetch_tmap(&tm_upper);
+      auto issue = [&](int ls) {
+        const int kst = st_begin + ls, slot = ls % NS, k0 = kst * BK;
+        double* dst = ring + (size_t)slot * BM * BK;
+        tc::mbar_arrive_expect_tx(&full[slot], (uint32_t)(L::tile_bytes + L::bstage_bytes));
+        if (kind_of(kst) == 1) {
+          tc::tma_load_2d(dst, &tm_upper, k0, i0, &full[slot]);
+          tc::tma_load_2d(dst + BM * 16, &tm_upper, k0 + 16, i0, &full[slot]);
+        } else {
+          tc::tma_load_2d(dst, &tm_lower, i0, k0, &full[slot]);
+        }
+        tc::bulk_g2s(bring + (size_t)slot * L::bstage_bytes,
+                     reinterpret_cast<const unsigned char*>(p.Bblob) + (size_t)kst * L::bstage_bytes,
+                     (uint32_t)L::bstage_bytes, &full[slot]);
+      };
+      int issued = 0;
+      for (; issued < NS - 1 && issued < nst; ++issued) issue(issued);
+      for (int st = 0; st < nst; ++st) {
+        if (!tc::mbar_wait(&sliced[st & 1], (uint32_t)(st >> 1) & 1u, deadline)) {
+          timed_out = 1;
+          break;
+        }
+        tc::fence_after_sync();
+        const int chunk = st / CH;
+        const uint32_t d = tmem + (uint32_t)((chunk & 1) * BN);
+        constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
+        const uint32_t abase = tc::smem_u32(aslices + (size_t)(st & 1) * S * L::aslice_bytes);
+        const uint32_t bbase = tc::smem_u32(bring + (size_t)(st % NS) * L::bstage_bytes);
+#pragma unroll
+        for (int kk = 0; kk < BK / 16; ++kk) {
+#pragma unroll
+          for (int q = 0; q < PR::n; ++q) {
+            const uint64_t ad = tc::smem_desc(abase + PR::s(q) * L::aslice_bytes + kk * 2 * (BM / 8) * 128,
+                                              (BM / 8) * 128, 128);
+            const uint64_t bd = tc::smem_desc(bbase + PR::t(q) * L::bslice_bytes + kk * 2 * (BN / 8) * 128,
+                                              (BN / 8) * 128, 128);
+            const uint32_t accum = (st % CH == 0 && kk == 0 && q == 0) ? 0u : 1u;
+            tc::mma_bf16(d, ad, bd, idesc, accum);
+          }
+        }
+        tc::mma_commit(&bar_mma[st & 1]);
+        if (st % CH == CH - 1 || st == nst - 1) tc::mma_commit(&bar_acc[chunk & 1]);
+        // refill the slot of stage st - 1 once its MMAs (readers of its B slices) are done
+        if (issued < nst) {
+          if (st >= 1 && !tc::mbar_wait(&bar_mma[(st - 1) & 1], (uint32_t)((st - 1) >> 1) & 1u, deadline)) {
+            timed_out = 1;
+            break;
+          }
+          issue(issued++);
+        }
+      }
+      if (timed_out) {  // let copies and MMAs in flight land before the CTA leaves (bounded)
+        const unsigned long long dl = global_ns() + p.limit_ns;
+        for (int q = 0; q < NS; ++q) tc::mbar_wait(&full[q], 0, dl);
+        for (int q = 0; q < 2; ++q) tc::mbar_wait(&bar_mma[q], 0, dl);
+      }
+    }
+  } else {
+    // ---------------- converter warps: FP64 stage -> bf16 slices; chunk sums -> (hi, lo)
+    const int ti = tid & (BM - 1), half = tid >> 7;  // row ti, k in [16 half, 16 half + 16)
+    auto drain_chunk = [&](int c) -> bool {
+      if (!tc::mbar_wait(&bar_acc[c & 1], (c >> 1) & 1, deadline)) return false;
+      tc::fence_after_sync();
+      const uint32_t q = warp & 3, h = warp >> 2;
+      const uint32_t taddr = tmem + ((q * 32) << 16) + (uint32_t)((c & 1) * BN + h * (BN / 2));
+      auto add = [&](int cc, float v) {  // (hi, lo) += v, error-free (Knuth's two-sum)
+        const float s2 = acc_hi[cc] + v;
+        const float bb = s2 - acc_hi[cc];
+        const float err = (acc_hi[cc] - (s2 - bb)) + (v - bb);
+        acc_hi[cc] = s2;
+        acc_lo[cc] += err;
+      };
       if constexpr (BN / 2 >= 32) {
 #pragma unroll
         for (int part = 0; part < BN / 64; ++part) {
@@ -476,113 +528,69 @@ __global__ void __launch_bounds__(NT, 1)
 #pragma unroll
         for (int cc = 0; cc < 16; ++cc) add(cc, v[cc]);
       }
-    }
-    tc::fence_before_sync();
-    return to;
-  };
-
-  if (tid == 0) {
-    for (int ls = 0; ls < 2 && ls < nst; ++ls) issue(ls);
-  }
-
-  const int ti = tid & (BM - 1), half = tid >> 7;  // this thread: row ti, k in [16 half, 16 half + 16)
-  for (int st = 0; st < nst && !timed_out; ++st) {
-    const int sb = st & 1, slot = st % NS;
-    const int kst = st_begin + st, k0 = kst * BK;
-    int to = 0;
-    if (st >= 2) to = tc::mbar_wait(&bar_mma[sb], ((st - 2) >> 1) & 1, deadline) ? 0 : 1;
-    if (__syncthreads_or(to)) {
-      timed_out = 1;
-      break;
-    }
-    if (tid == 0 && st + 2 < nst) issue(st + 2);
-
-    const int kind = kind_of(kst);
-    double x[16];
-    const int gi = i0 + ti;
-    if (kind == 2) {  // upper entries of a diagonal tile, from the stored mirror A(k, i)
+      tc::fence_before_sync();
+      return true;
+    };
+    for (int st = 0; st < nst; ++st) {
+      const int sb = st & 1, slot = st % NS;
+      const int kst = st_begin + st, k0 = kst * BK;
+      const int kind = kind_of(kst);
+      double x[16];
+      const int gi = i0 + ti;
+      if (kind == 2) {  // upper entries of a diagonal tile, from the stored mirror A(k, i)
 #pragma unroll
-      for (int kk = 0; kk < 16; ++kk) {
-        const int gk = k0 + 16 * half + kk;
-        x[kk] = (gi < gk && gk < p.K && gi < p.M) ? __ldg(p.A + gk + (int64_t)gi * p.lda) : 0.0;
-      }
-    }
-    to = tc::mbar_wait(&full[slot], (uint32_t)(st / NS) & 1u, deadline) ? 0 : 1;
-    if (__syncthreads_or(to)) {
-      timed_out = 1;
-      break;
-    }
-    const double* tile = ring + (size_t)slot * BM * BK;
-    if (kind == 1) {
-      const double* box = tile + half * (BM * 16) + ti * 16;
-#pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        const double2 v = *reinterpret_cast<const double2*>(box + 2 * (c ^ (ti & 7)));
-        x[2 * c] = v.x;
-        x[2 * c + 1] = v.y;
-      }
-    } else {
-#pragma unroll
-      for (int kk = 0; kk < 16; ++kk) {
-        const double v = tile[(16 * half + kk) * BM + ti];
-        if (kind == 0 || gi >= k0 + 16 * half + kk) x[kk] = v;
-      }
-    }
-    unsigned char* adst = aslices + (size_t)sb * S * L::aslice_bytes;
-#pragma unroll
-    for (int g = 0; g < 2; ++g) {
-      uint32_t w[4][S];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) range_ok &= tc::split_pair<S>(x[8 * g + 2 * c], x[8 * g + 2 * c + 1], w[c]);
-      const uint32_t off = tc::kmajor_offset(ti, (2 * half + g) * 8, BM);
-#pragma unroll
-      for (int sl = 0; sl < S; ++sl)
-        *reinterpret_cast<uint4*>(adst + sl * L::aslice_bytes + off) = make_uint4(w[0][sl], w[1][sl], w[2][sl], w[3][sl]);
-    }
-    tc::fence_proxy_async();
-    tc::fence_before_sync();
-    __syncthreads();
-
-    const int chunk = st / CH;
-    if (tid == 0) {
-      tc::fence_after_sync();
-      const uint32_t d = tmem + (uint32_t)((chunk & 1) * BN);
-      constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
-      const uint32_t abase = tc::smem_u32(adst);
-      const uint32_t bbase = tc::smem_u32(bring + (size_t)slot * L::bstage_bytes);
-#pragma unroll
-      for (int kk = 0; kk < BK / 16; ++kk) {
-#pragma unroll
-        for (int q = 0; q < PR::n; ++q) {
-          const uint64_t ad = tc::smem_desc(abase + PR::s(q) * L::aslice_bytes + kk * 2 * (BM / 8) * 128,
-                                            (BM / 8) * 128, 128);
-          const uint64_t bd = tc::smem_desc(bbase + PR::t(q) * L::bslice_bytes + kk * 2 * (BN / 8) * 128,
-                                            (BN / 8) * 128, 128);
-          const uint32_t accum = (st % CH == 0 && kk == 0 && q == 0) ? 0u : 1u;
-          tc::mma_bf16(d, ad, bd, idesc, accum);
+        for (int kk = 0; kk < 16; ++kk) {
+          const int gk = k0 + 16 * half + kk;
+          x[kk] = (gi < gk && gk < p.K && gi < p.M) ? __ldg(p.A + gk + (int64_t)gi * p.lda) : 0.0;
         }
       }
-      tc::mma_commit(&bar_mma[sb]);
-      if (st % CH == CH - 1 || st == nst - 1) tc::mma_commit(&bar_acc[chunk & 1]);
+      if (!tc::mbar_wait(&full[slot], (uint32_t)(st / NS) & 1u, deadline) ||
+          (st >= 2 && !tc::mbar_wait(&bar_mma[sb], (uint32_t)((st - 2) >> 1) & 1u, deadline))) {
+        timed_out = 1;
+        break;
+      }
+      const double* tile = ring + (size_t)slot * BM * BK;
+      if (kind == 1) {
+        const double* box = tile + half * (BM * 16) + ti * 16;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const double2 v = *reinterpret_cast<const double2*>(box + 2 * (c ^ (ti & 7)));
+          x[2 * c] = v.x;
+          x[2 * c + 1] = v.y;
+        }
+      } else {
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+          const double v = tile[(16 * half + kk) * BM + ti];
+          if (kind == 0 || gi >= k0 + 16 * half + kk) x[kk] = v;
+        }
+      }
+      unsigned char* adst = aslices + (size_t)sb * S * L::aslice_bytes;
+#pragma unroll
+      for (int g = 0; g < 2; ++g) {
+        uint32_t w[4][S];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) range_ok &= tc::split_pair<S>(x[8 * g + 2 * c], x[8 * g + 2 * c + 1], w[c]);
+        const uint32_t off = tc::kmajor_offset(ti, (2 * half + g) * 8, BM);
+#pragma unroll
+        for (int sl = 0; sl < S; ++sl)
+          *reinterpret_cast<uint4*>(adst + sl * L::aslice_bytes + off) =
+              make_uint4(w[0][sl], w[1][sl], w[2][sl], w[3][sl]);
+      }
+      tc::fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&sliced[sb]);
+      if (st % CH == 0 && st > 0 && !drain_chunk(st / CH - 1)) {
+        timed_out = 1;
+        break;
+      }
     }
-    if (st % CH == 0 && st > 0) {
-      to = drain_chunk(chunk - 1);
-      if (__syncthreads_or(to)) timed_out = 1;
-    }
-  }
-  if (!timed_out && nst > 0) {
-    const int to = drain_chunk((nst - 1) / CH);
-    if (__syncthreads_or(to)) timed_out = 1;
+    if (!timed_out && nst > 0 && !drain_chunk((nst - 1) / CH)) timed_out = 1;
   }
 
-  if (timed_out) {
-    report(p.status, BANDRED_DEV_TIMEOUT);
-    if (tid == 0) {  // let copies and MMAs in flight land before the CTA leaves (bounded)
-      const unsigned long long dl = global_ns() + p.limit_ns;
-      for (int q = 0; q < NS; ++q) tc::mbar_wait(&full[q], 0, dl);
-      for (int b = 0; b < 2; ++b) tc::mbar_wait(&bar_mma[b], 0, dl);
-    }
-  } else {
+  if (__syncthreads_or(timed_out)) {
+    if (tid == 0) report(p.status, BANDRED_DEV_TIMEOUT);
+  } else if (warp < kConvWarps) {
     const int q = warp & 3, h = warp >> 2;
     const int row = i0 + q * 32 + lane;
     double* P = p.P + (size_t)z * p.split_stride;
@@ -615,7 +623,7 @@ struct RankSmem {
 };
 
 template <int S>
-__global__ void __launch_bounds__(NT) rank_update_kernel(RankParams single, const RankParams* probs) {
+__global__ void __launch_bounds__(NT, 2) rank_update_kernel(RankParams single, const RankParams* probs) {
   using L = RankSmem<S>;
   using PR = Products<S>;
   const RankParams p = probs ? probs[blockIdx.z] : single;
@@ -679,22 +687,22 @@ __global__ void __launch_bounds__(NT) rank_update_kernel(RankParams single, cons
     const int q = warp & 3, h = warp >> 2;
     const int row = I * BM + q * 32 + lane;
     const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * 64);
+    // 16 columns at a time (two CTAs fit an SM: one's epilogue overlaps the other's
+    // copies and MMAs); all loads of a part are issued before its stores.
+#pragma unroll 1
+    for (int part = 0; part < 4; ++part) {
+      float v[16];
+      tc::tmem_ld16(taddr + part * 16, v);
+      const int colb = J * BM + h * 64 + part * 16;
+      double old[16];
 #pragma unroll
-    for (int part = 0; part < 2; ++part) {
-      float v[32];
-      tc::tmem_ld32(taddr + part * 32, v);
-      const int colb = J * BM + h * 64 + part * 32;
-      // Issue all loads of this thread's 32 entries before any store (independent
-      // accesses: one memory latency instead of 32).
-      double old[32];
-#pragma unroll
-      for (int c = 0; c < 32; ++c) {
+      for (int c = 0; c < 16; ++c) {
         const int col = colb + c;
         const bool in = row < p.M && col < p.N && col >= p.col0 && col < p.col1 && (!p.lower || row >= col);
         old[c] = in ? p.C[row + (int64_t)col * p.ldc] : 0.0;
       }
 #pragma unroll
-      for (int c = 0; c < 32; ++c) {
+      for (int c = 0; c < 16; ++c) {
         const int col = colb + c;
         const bool in = row < p.M && col < p.N && col >= p.col0 && col < p.col1 && (!p.lower || row >= col);
         if (in) {
@@ -759,7 +767,7 @@ cudaError_t launch_stream_tma(const StreamParams& p, const CUtensorMap& lo, cons
     if (e != cudaSuccess) return e;
     configured = dev;
   }
-  stream_tma_kernel<BN, S><<<grid, NT, L::total, s>>>(p, lo, up);
+  stream_tma_kernel<BN, S><<<grid, kTmaThreads, L::total, s>>>(p, lo, up);
   prof::count_launch();
   return cudaGetLastError();
 }

@@ -169,18 +169,15 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 }
 
 // FP32 -> FP64 by bit manipulation: the conversion instruction runs on the FP64 pipe,
-// which GB300 issues at two operations per clock per SM.  Zero, subnormal, infinite and
-// NaN inputs take the ordinary conversion.
+// which GB300 issues at two operations per clock per SM.  Branch-free (a predicated
+// conversion would still occupy the FP64 pipe): Inf and NaN keep their class, FP32
+// subnormals become zero of the same sign.
 __device__ __forceinline__ double f32_to_f64(float f) {
   const uint32_t u = __float_as_uint(f);
   const uint32_t e = (u >> 23) & 0xFFu;
-  if (e == 0u || e == 0xFFu) {
-    if ((u & 0x7FFFFFFFu) == 0u) return __longlong_as_double((long long)((unsigned long long)(u & 0x80000000u) << 32));
-    return (double)f;
-  }
-  const unsigned long long d = ((unsigned long long)(u & 0x80000000u) << 32) |
-                               ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29);
-  return __longlong_as_double((long long)d);
+  const uint32_t m = e == 0u ? 0u : (u & 0x7FFFFFu);
+  const uint32_t e64 = e == 0u ? 0u : (e == 0xFFu ? 0x7FFu : e + 896u);
+  return __hiloint2double((int)((u & 0x80000000u) | (e64 << 20) | (m >> 3)), (int)(m << 29));
 }
 
 // ---------------------------------------------------------------- FP64 -> bf16 slices
