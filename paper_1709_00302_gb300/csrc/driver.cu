@@ -157,7 +157,7 @@ static Sy2sbWs carve_sy2sb(void* work, int64_t n, int64_t w, const Options& o, i
     ws.Z[q] = q < nbuf ? c.take<double>(b * std::max<int64_t>(w, 1)) : ws.Z[0];
     ws.splitk[q] = q < nbuf ? c.take<double>(ws.splitk_cap) : ws.splitk[0];
   }
-  ws.rowbuf = c.take<double>(2 * (size_t)b);
+  ws.rowbuf = c.take<double>(4 * (size_t)b);  // two rows per step, two steps
   ws.part2 = c.take<double>((size_t)sms);
   ws.gs = c.take<GridSync>(1);  // 256 bytes, immediately followed by the accumulators
   ws.part = c.take<double>((panel_sync_bytes((int)b) - 256) / sizeof(double));
@@ -214,7 +214,7 @@ static Ge2gbWs carve_ge2gb(void* work, int64_t m, int64_t n, const Options& o, i
     ws.Z[q] = q < nbuf ? c.take<double>(b * ws.ldv) : ws.Z[0];
     ws.splitk[q] = q < nbuf ? c.take<double>(ws.splitk_cap) : ws.splitk[0];
   }
-  ws.rowbuf = c.take<double>(2 * (size_t)b);
+  ws.rowbuf = c.take<double>(4 * (size_t)b);  // two rows per step, two steps
   ws.part2 = c.take<double>((size_t)sms);
   ws.gs = c.take<GridSync>(1);  // 256 bytes, immediately followed by the accumulators
   ws.part = c.take<double>((panel_sync_bytes((int)b) - 256) / sizeof(double));

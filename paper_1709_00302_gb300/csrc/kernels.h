@@ -18,8 +18,8 @@ struct PanelParams {
   double* Y;             // j x bk, column-major, ld = ldy (unit lower trapezoidal copy of V)
   double* W;             // j x bk, column-major, ld = ldy (W = -Y T)
   int64_t ldy;
-  double* acc;           // 3 * (bk + 1) * 32 doubles, directly after *gs (zeroed with it)
-  double* rowbuf;        // 2 * bk doubles
+  double* acc;           // 3 * (2 bk + 2) * 32 doubles, directly after *gs (zeroed with it)
+  double* rowbuf;        // 4 * bk doubles
   double* part2;         // G doubles
   GridSync* gs;
   int* status;

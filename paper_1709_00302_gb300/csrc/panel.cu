@@ -18,6 +18,9 @@
 //   updates its own rows without further communication.  GB300 issues FP64 at two
 //   operations per clock per SM, so the kernel keeps FP64 instructions to the FMAs the
 //   method needs (no per-CTA re-summation of partials, hoisted scalings).
+//   Reflectors are taken two per grid-wide reduction when the second one's norm can be
+//   updated without cancellation (H_i is orthogonal, so the sums of column i + 1 against
+//   the panel determine those of H_i applied to it): half the barriers, the same FMAs.
 //   W's column i follows from the recurrence W(:, i) = -tau_i (y_i + W(:, 0:i) Y(:, 0:i)^T y_i),
 //   which equals -Y T with T built column by column as in the compact-WY definition.
 #include <cmath>
@@ -40,22 +43,24 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
   const int rb = g * p.R;
   const int nr = max(0, min(p.R, p.j - rb));
   double* slab = smem;                        // bk columns x Rp rows
-  double* dsum = slab + (size_t)bk * Rp;      // bk + 1 combined sums
-  double* rowi = dsum + bk + 1;               // row i of the panel
-  double* coef = rowi + bk;                   // z_c (c > i) and, for c < i, Y^T y_i
-  double* coef2 = coef + bk;                  // -z_c * scal (c > i)
-  double* gprev = coef2 + bk;                 // Y^T y of the previous reflector (for W)
-  float* gprevf = reinterpret_cast<float*>(gprev + bk);  // the same in FP32 (bk floats)
-  double* after = gprev + bk + (bk + 1) / 2;
+  double* dsum = slab + (size_t)bk * Rp;      // 2 bk + 2 combined sums (S_a, max|x2|, S_b)
+  double* rowi = dsum + 2 * bk + 2;           // row i of the panel (before the step)
+  double* rowi1 = rowi + bk;                  // row i + 1 (paired steps)
+  double* gq0 = rowi1 + bk;                   // Y^T y of the step's first reflector (for W)
+  double* gq1 = gq0 + bk;                     // ... and of its second
+  float* gqf0 = reinterpret_cast<float*>(gq1 + bk);  // the same in FP32 (bk floats each)
+  float* gqf1 = gqf0 + bk;
+  double* after = gq1 + 2 * bk;
   // This CTA's rows of W: in shared memory when they fit (FP32 when p.w_fp32), else in
   // the W output itself.
   const bool wf32 = p.w_in_smem && p.w_fp32;
   double* wl = p.w_in_smem ? after : p.W + rb;
   float* wlf = reinterpret_cast<float*>(after);
   const int64_t wld = p.w_in_smem ? Rp : p.ldy;
-  __shared__ double s_beta, s_tau, s_scal, s_tau_prev;
+  __shared__ double s_beta, s_tau, s_scal, s_beta2, s_tau2, s_scal2, s_zb, s_Taa, s_Tab;
+  __shared__ double s_ptau[2];
   __shared__ double s_red[NT / 32];
-  __shared__ int s_rescale, s_ok;
+  __shared__ int s_rescale, s_ok, s_pair;
 
   if (p.rs == 1) {
     for (int idx = tid; idx < nr * bk; idx += NT) {
@@ -70,46 +75,85 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
   }
   __syncthreads();
 
+  // W columns of the previous step's reflectors (their T entries are in gq0 / gq1).
+  auto pending_w = [&](int npend, int pi) {
+    for (int q = 0; q < npend; ++q) {
+      if (q) __syncthreads();
+      if (wf32)
+        w_column_f32(pi + q, (float)s_ptau[q], q ? gqf1 : gqf0, slab, Rp, rb, nr, wlf);
+      else
+        w_column(pi + q, s_ptau[q], q ? gq1 : gq0, slab, Rp, rb, nr, wl, wld);
+    }
+  };
+
   // Threads per column in the dot products (a power of two dividing 32).
   const int TPC = bk >= 128 ? 2 : (bk >= 64 ? 4 : 8);
   const int CPP = NT / TPC;  // columns per pass
   const int sub = tid % TPC;
-  const size_t accsz = (size_t)(bk + 1) * kAccStride;
+  const size_t accsz = (size_t)(2 * bk + 2) * kAccStride;
   unsigned int gen = 0;
-  for (int i = 0; i < bk; ++i) {
-    double* acc = p.acc + (size_t)(i % 3) * accsz;
-    double* rowg = p.rowbuf + (size_t)(i & 1) * bk;
+  int npend = 0, pend_i = 0;
+  for (int i = 0, step = 0; i < bk; ++step) {
+    // A paired step computes reflectors i and i + 1 from one grid-wide reduction: the
+    // sums over the rows below row i of column i and of column i + 1 against every
+    // column; the second reflector's norm and coefficients follow from them and rows i,
+    // i + 1 by the orthogonality of the first (see the pair branch below).
+    const bool want_pair = (i + 1 < bk) && (p.j - i - 2 >= 1);
+    double* acc = p.acc + (size_t)(step % 3) * accsz;
+    double* rowg = p.rowbuf + (size_t)(step & 1) * 2 * bk;
     const int lo = min(max(i + 1 - rb, 0), nr);
-    const double* xi = slab + (size_t)i * Rp;
-    const bool own_row = (i >= rb) && (i < rb + nr);
-    if (g == 0) {  // clear the buffer of step i+1 (last read at step i-2, before barrier i-1)
-      double* nxt = p.acc + (size_t)((i + 1) % 3) * accsz;
-      for (int v = tid; v <= bk; v += NT) nxt[(size_t)v * kAccStride] = 0.0;
+    double* xa = slab + (size_t)i * Rp;
+    double* xb = slab + (size_t)(want_pair ? i + 1 : i) * Rp;
+    const bool own0 = (i >= rb) && (i < rb + nr);
+    const bool own1 = (i + 1 >= rb) && (i + 1 < rb + nr);
+    if (g == 0) {  // clear the buffer of the next step (last read two steps ago)
+      double* nxt = p.acc + (size_t)((step + 1) % 3) * accsz;
+      for (int v = tid; v < 2 * bk + 2; v += NT) nxt[(size_t)v * kAccStride] = 0.0;
     }
 
-    // Partial dot products of x2 = column i below row i with every panel column, added
-    // into the L2 accumulators (two independent FMA chains per thread).
+    // Partial dot products over this CTA's rows below row i, added into L2 accumulators.
     for (int c0 = 0; c0 < bk; c0 += CPP) {
       const int c = c0 + tid / TPC;
-      double s = 0.0, t = 0.0;
+      double sa = 0.0, ta = 0.0, sbv = 0.0, tbv = 0.0;
       if (c < bk) {
         const double* ac = slab + (size_t)c * Rp;
         int r = lo + sub;
-        for (; r + TPC < nr; r += 2 * TPC) {
-          s = fma(xi[r], ac[r], s);
-          t = fma(xi[r + TPC], ac[r + TPC], t);
+        if (want_pair) {
+          for (; r + TPC < nr; r += 2 * TPC) {
+            const double v0 = ac[r], v1 = ac[r + TPC];
+            sa = fma(xa[r], v0, sa);
+            sbv = fma(xb[r], v0, sbv);
+            ta = fma(xa[r + TPC], v1, ta);
+            tbv = fma(xb[r + TPC], v1, tbv);
+          }
+          if (r < nr) {
+            sa = fma(xa[r], ac[r], sa);
+            sbv = fma(xb[r], ac[r], sbv);
+          }
+        } else {
+          for (; r + TPC < nr; r += 2 * TPC) {
+            sa = fma(xa[r], ac[r], sa);
+            ta = fma(xa[r + TPC], ac[r + TPC], ta);
+          }
+          if (r < nr) sa = fma(xa[r], ac[r], sa);
         }
-        if (r < nr) s = fma(xi[r], ac[r], s);
       }
-      s += t;
-      for (int o = TPC / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (sub == 0 && c < bk) atomicAdd(&acc[(size_t)c * kAccStride], s);
+      sa += ta;
+      sbv += tbv;
+      for (int o = TPC / 2; o > 0; o >>= 1) {
+        sa += __shfl_xor_sync(0xffffffffu, sa, o);
+        if (want_pair) sbv += __shfl_xor_sync(0xffffffffu, sbv, o);
+      }
+      if (sub == 0 && c < bk) {
+        atomicAdd(&acc[(size_t)c * kAccStride], sa);
+        if (want_pair) atomicAdd(&acc[(size_t)(bk + 1 + c) * kAccStride], sbv);
+      }
     }
     // max |x2| by integer comparison of the bit patterns (no FP64 instruction): one warp
     if (tid < 32) {
       unsigned long long m = 0ull;
       for (int r = lo + lane; r < nr; r += 32) {
-        const unsigned long long u = (unsigned long long)__double_as_longlong(xi[r]) & 0x7FFFFFFFFFFFFFFFull;
+        const unsigned long long u = (unsigned long long)__double_as_longlong(xa[r]) & 0x7FFFFFFFFFFFFFFFull;
         m = u > m ? u : m;
       }
 #pragma unroll
@@ -119,25 +163,20 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
       }
       if (lane == 0) atomicMax(reinterpret_cast<unsigned long long*>(&acc[(size_t)bk * kAccStride]), m);
     }
-    if (own_row)
+    if (own0)
       for (int c = tid; c < bk; c += NT) __stcg(&rowg[c], slab[(size_t)c * Rp + (i - rb)]);
+    if (want_pair && own1)
+      for (int c = tid; c < bk; c += NT) __stcg(&rowg[bk + c], slab[(size_t)c * Rp + (i + 1 - rb)]);
     __syncthreads();
     if (tid == 0) grid_arrive(p.gs);
     ++gen;
-    // W column of the previous reflector: off the critical path, overlaps the barrier.
-    if (i > 0) {
-      if (wf32)
-        w_column_f32(i - 1, (float)s_tau_prev, gprevf, slab, Rp, rb, nr, wlf);
-      else
-        w_column(i - 1, s_tau_prev, gprev, slab, Rp, rb, nr, wl, wld);
-    }
+    // W columns of the previous step: off the critical path, overlap the barrier.
+    pending_w(npend, pend_i);
     if (tid == 0) s_ok = grid_wait(p.gs, gen, p.extra, p.status, p.limit_ns) ? 1 : 0;
     __syncthreads();
     if (!s_ok) return;
 
-    // Thread 0 reads the three numbers the reflector needs and derives it while warps
-    // 1..7 fetch the remaining sums and row i (warp 0 does nothing else, so the two do
-    // not serialise through divergence).
+    // Thread 0 derives the reflector(s) from a few sums while warps 1..7 fetch the rest.
     if (tid == 0) {
       const double alpha = ldcg(&rowg[i]);
       const double ssq = ldcg(&acc[(size_t)i * kAccStride]);
@@ -161,9 +200,47 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
       s_beta = beta;
       s_tau = tau;
       s_scal = scal;
+      // Second reflector.  With a = column i, b = column i + 1 and sums over rows >= i + 1
+      // (S_aa, S_ab, S_bb), H_i b = b - z_b v_i has z_b = tau (b_i + scal S_ab); below row
+      // i + 1 its entries are b_r - zs a_r (zs = z_b scal), so their squared norm is
+      //   n2 = T_bb - 2 zs T_ab + zs^2 T_aa,  T_xy = S_xy - x_{i+1} y_{i+1},
+      // and the new diagonal entry is b_{i+1} - zs a_{i+1}.  The step is paired only when
+      // n2 keeps at least 1/8 of S_bb + zs^2 S_aa (a bound on the terms that cancel), so
+      // its relative error stays a small multiple of the unit roundoff; otherwise the
+      // step takes reflector i alone and the next step starts from a fresh reduction.
+      int pair = 0;
+      if (want_pair && !s_rescale) {
+        const double Sab = ldcg(&acc[(size_t)(i + 1) * kAccStride]);
+        const double Sbb = ldcg(&acc[(size_t)(bk + 2 + i) * kAccStride]);
+        const double bi = ldcg(&rowg[i + 1]), ai1 = ldcg(&rowg[bk + i]), bi1 = ldcg(&rowg[bk + i + 1]);
+        const double zb = tau * fma(scal, Sab, bi);
+        const double zs = zb * scal;
+        const double Taa = fma(-ai1, ai1, ssq), Tab = fma(-ai1, bi1, Sab), Tbb = fma(-bi1, bi1, Sbb);
+        const double n2 = fma(zs * zs, Taa, fma(-2.0 * zs, Tab, Tbb));
+        const double alpha2 = fma(-zs, ai1, bi1);
+        const double bound = fma(zs * zs, ssq, Sbb);
+        if (n2 > 0.125 * bound && n2 < 0x1p1000 && n2 > 0x1p-900 && fabs(alpha2) < 0x1p500) {
+          const double q = fma(alpha2, alpha2, n2);
+          const double rq = rsqrt_newton(q);
+          const double h = q * rq;
+          const double aa = fabs(alpha2);
+          s_beta2 = (alpha2 >= 0.0) ? -h : h;
+          s_tau2 = fma(aa, rq, 1.0);
+          const double rs = rcp_newton(aa + h);
+          s_scal2 = (alpha2 >= 0.0) ? rs : -rs;
+          s_zb = zb;
+          s_Taa = Taa;
+          s_Tab = Tab;
+          pair = 1;
+        }
+      }
+      s_pair = pair;
     } else if (tid >= 32) {
-      for (int v = tid - 32; v <= bk; v += NT - 32) dsum[v] = ldcg(&acc[(size_t)v * kAccStride]);
+      const int nsum = want_pair ? 2 * bk + 1 : bk + 1;
+      for (int v = tid - 32; v < nsum; v += NT - 32) dsum[v] = ldcg(&acc[(size_t)v * kAccStride]);
       for (int c = tid - 32; c < bk; c += NT - 32) rowi[c] = ldcg(&rowg[c]);
+      if (want_pair)
+        for (int c = tid - 32; c < bk; c += NT - 32) rowi1[c] = ldcg(&rowg[bk + c]);
     }
     __syncthreads();
 
@@ -173,7 +250,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
       const double inv = dsum[bk] > 0.0 ? 1.0 / dsum[bk] : 0.0;
       double s = 0.0;
       for (int r = lo + tid; r < nr; r += NT) {
-        const double t = xi[r] * inv;
+        const double t = xa[r] * inv;
         s = fma(t, t, s);
       }
       s = warp_sum(s);
@@ -208,13 +285,17 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
       }
       __syncthreads();
     }
-    if (tid == 0 && g == 0) p.tau[i] = s_tau;
+    const bool paired = s_pair != 0;
+    if (tid == 0 && g == 0) {
+      p.tau[i] = s_tau;
+      if (paired) p.tau[i + 1] = s_tau2;
+    }
 
     const double tau = s_tau, scal = s_scal;
-    // Coefficients and the in-panel update, one column per group of TPU threads:
-    // z_c = tau v^T a_c, a_c -= z_c v (c > i); and (Y^T y_i)_c for c < i (for W).
-    {
-      const int TPU = bk >= 128 ? 2 : (bk >= 64 ? 4 : 8);
+    const int TPU = bk >= 128 ? 2 : (bk >= 64 ? 4 : 8);
+    if (!paired) {
+      // Coefficients and the in-panel update, one column per group of TPU threads:
+      // z_c = tau v^T a_c, a_c -= z_c v (c > i); and (Y^T y_i)_c for c < i (for W).
       for (int c0 = 0; c0 < bk; c0 += NT / TPU) {
         const int c = c0 + tid / TPU, rg = tid % TPU;
         if (c > i && c < bk) {
@@ -222,29 +303,89 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
           if (tau != 0.0) {
             const double z2 = -z * scal;
             double* ac = slab + (size_t)c * Rp;
-            for (int r = lo + rg; r < nr; r += TPU) ac[r] = fma(z2, xi[r], ac[r]);
-            if (own_row && rg == 0) ac[i - rb] -= z;
+            for (int r = lo + rg; r < nr; r += TPU) ac[r] = fma(z2, xa[r], ac[r]);
+            if (own0 && rg == 0) ac[i - rb] -= z;
           }
         } else if (c < i && rg == 0) {
           const double gv = fma(scal, dsum[c], rowi[c]);
-          gprev[c] = gv;
-          gprevf[c] = f64_to_f32_rz(gv);
+          gq0[c] = gv;
+          gqf0[c] = f64_to_f32_rz(gv);
         }
       }
+      __syncthreads();
+      if (tau != 0.0)
+        for (int r = lo + tid; r < nr; r += NT) xa[r] *= scal;
+      if (own0 && tid == 0) xa[i - rb] = s_beta;
+      if (tid == 0) s_ptau[0] = tau;
+      npend = 1;
+    } else {
+      // Paired update.  For a column c > i + 1 the first reflector gives
+      // z_c = tau (c_i + scal S_ac) and c'_{i+1} = c_{i+1} - z_c scal a_{i+1}; the second needs
+      // (b')^T c' below row i + 1 = T_bc - z_c scal T_ab - zs T_ac + zs z_c scal T_aa, so
+      // z'_c = tau2 (c'_{i+1} + scal2 (b')^T c') and below row i + 1
+      //   c'' = c - (z_c scal - z'_c scal2 zs) a - z'_c scal2 b   (two FMAs per entry).
+      const double tau2 = s_tau2, scal2 = s_scal2, zb = s_zb, Taa = s_Taa, Tab = s_Tab;
+      const double zs = zb * scal;
+      const double ai1 = rowi1[i], bi1 = rowi1[i + 1];
+      const int lo2 = min(max(i + 2 - rb, 0), nr);
+      for (int c0 = 0; c0 < bk; c0 += NT / TPU) {
+        const int c = c0 + tid / TPU, rg = tid % TPU;
+        if (c > i + 1 && c < bk) {
+          const double z = tau * fma(scal, dsum[c], rowi[c]);
+          const double zsc = z * scal;
+          const double c1 = fma(-zsc, ai1, rowi1[c]);
+          const double Tbc = fma(-bi1, rowi1[c], dsum[bk + 1 + c]);
+          const double Tac = fma(-ai1, rowi1[c], dsum[c]);
+          const double dot = fma(zs * zsc, Taa, fma(-zs, Tac, fma(-zsc, Tab, Tbc)));
+          const double z2 = tau2 * fma(scal2, dot, c1);
+          const double ca = fma(z2 * scal2, zs, -zsc);
+          const double cb = -z2 * scal2;
+          double* ac = slab + (size_t)c * Rp;
+          for (int r = lo2 + rg; r < nr; r += TPU) ac[r] = fma(cb, xb[r], fma(ca, xa[r], ac[r]));
+          if (rg == 0) {
+            if (own0) ac[i - rb] -= z;
+            if (own1) ac[i + 1 - rb] = c1 - z2;
+          }
+        } else if (c < i && rg == 0) {
+          // y_c^T y_i and y_c^T y_{i+1} (y_c[i + 1] = row i + 1 of column c)
+          const double g0 = fma(scal, dsum[c], rowi[c]);
+          const double Tbq = fma(-rowi1[c], bi1, dsum[bk + 1 + c]);
+          const double Taq = fma(-rowi1[c], ai1, dsum[c]);
+          const double g1 = fma(scal2, fma(-zs, Taq, Tbq), rowi1[c]);
+          gq0[c] = g0;
+          gqf0[c] = f64_to_f32_rz(g0);
+          gq1[c] = g1;
+          gqf1[c] = f64_to_f32_rz(g1);
+        }
+      }
+      if (tid == 0) {  // y_i^T y_{i+1} = scal a_{i+1} + scal2 scal (T_ab - zs T_aa)
+        const double gi = fma(scal2 * scal, fma(-zs, Taa, Tab), scal * ai1);
+        gq1[i] = gi;
+        gqf1[i] = f64_to_f32_rz(gi);
+        s_ptau[0] = tau;
+        s_ptau[1] = tau2;
+      }
+      __syncthreads();
+      // columns i and i + 1 become v_i and v_{i+1}: rows below i + 1 hold scal a_r and
+      // scal2 (b_r - zs a_r); row i + 1 holds scal a_{i+1} and beta2; row i holds beta and
+      // b_i - z_b.
+      for (int r = lo + tid; r < nr; r += NT) {
+        const double ar = xa[r];
+        xa[r] = ar * scal;
+        xb[r] = (rb + r == i + 1) ? s_beta2 : fma(-zs, ar, xb[r]) * scal2;
+      }
+      if (own0 && tid == 0) {
+        xa[i - rb] = s_beta;
+        xb[i - rb] = rowi[i + 1] - zb;
+      }
+      npend = 2;
     }
-    __syncthreads();
-    if (tau != 0.0)
-      for (int r = lo + tid; r < nr; r += NT) slab[(size_t)i * Rp + r] *= scal;
-    if (own_row && tid == 0) slab[(size_t)i * Rp + (i - rb)] = s_beta;
-    if (tid == 0) s_tau_prev = tau;
+    pend_i = i;
+    i += paired ? 2 : 1;
     __syncthreads();
   }
-  if (wf32)
-    w_column_f32(bk - 1, (float)s_tau_prev, gprevf, slab, Rp, rb, nr, wlf);
-  else
-    w_column(bk - 1, s_tau_prev, gprev, slab, Rp, rb, nr, wl, wld);
+  pending_w(npend, pend_i);
   __syncthreads();
-
   if (wf32) {
     for (int idx = tid; idx < nr * bk; idx += NT) {
       const int r = idx % nr, c = idx / nr;
@@ -282,10 +423,10 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
 }  // namespace
 
 size_t panel_smem_bytes(int bk, int Rp, bool w_in_smem) {
-  return ((size_t)bk * Rp * (w_in_smem ? 2 : 1) + 5 * (size_t)bk + 1 + (bk + 1) / 2) * sizeof(double);
+  return ((size_t)bk * Rp * (w_in_smem ? 2 : 1) + 7 * (size_t)bk + 2) * sizeof(double);
 }
 
-size_t panel_sync_bytes(int bk) { return 256 + 3 * (size_t)(bk + 1) * kAccStride * sizeof(double); }
+size_t panel_sync_bytes(int bk) { return 256 + 3 * (size_t)(2 * bk + 2) * kAccStride * sizeof(double); }
 
 int panel_geometry(int j, int bk, int max_ctas, int min_rows, int* G, int* R, int* Rp, bool* w_in_smem) {
   if (j <= 0 || bk <= 0) return -1;
