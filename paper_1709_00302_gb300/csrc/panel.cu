@@ -76,13 +76,21 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
   __syncthreads();
 
   // W columns of the previous step's reflectors (their T entries are in gq0 / gq1).
-  auto pending_w = [&](int npend, int pi) {
+  // all = false: warps 1..7 only (named barrier 1 between the columns), while thread 0
+  // derives the next reflectors.
+  auto pending_w = [&](int npend, int pi, bool all) {
+    const int t0 = all ? 0 : 32, nth = all ? NT : NT - 32;
     for (int q = 0; q < npend; ++q) {
-      if (q) __syncthreads();
+      if (q) {
+        if (all)
+          __syncthreads();
+        else
+          asm volatile("bar.sync 1, %0;" ::"r"(NT - 32) : "memory");
+      }
       if (wf32)
-        w_column_f32(pi + q, (float)s_ptau[q], q ? gqf1 : gqf0, slab, Rp, rb, nr, wlf);
+        w_column_f32(pi + q, (float)s_ptau[q], q ? gqf1 : gqf0, slab, Rp, rb, nr, wlf, t0, nth);
       else
-        w_column(pi + q, s_ptau[q], q ? gq1 : gq0, slab, Rp, rb, nr, wl, wld);
+        w_column(pi + q, s_ptau[q], q ? gq1 : gq0, slab, Rp, rb, nr, wl, wld, t0, nth);
     }
   };
 
@@ -170,8 +178,6 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
     __syncthreads();
     if (tid == 0) grid_arrive(p.gs);
     ++gen;
-    // W columns of the previous step: off the critical path, overlap the barrier.
-    pending_w(npend, pend_i);
     if (tid == 0) s_ok = grid_wait(p.gs, gen, p.extra, p.status, p.limit_ns) ? 1 : 0;
     __syncthreads();
     if (!s_ok) return;
@@ -241,6 +247,8 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
       for (int c = tid - 32; c < bk; c += NT - 32) rowi[c] = ldcg(&rowg[c]);
       if (want_pair)
         for (int c = tid - 32; c < bk; c += NT - 32) rowi1[c] = ldcg(&rowg[bk + c]);
+      // W columns of the previous step, hidden behind thread 0's scalar chain
+      pending_w(npend, pend_i, false);
     }
     __syncthreads();
 
@@ -384,7 +392,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
     i += paired ? 2 : 1;
     __syncthreads();
   }
-  pending_w(npend, pend_i);
+  pending_w(npend, pend_i, true);
   __syncthreads();
   if (wf32) {
     for (int idx = tid; idx < nr * bk; idx += NT) {

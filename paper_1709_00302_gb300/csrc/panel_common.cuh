@@ -63,12 +63,14 @@ __device__ __forceinline__ float f64_to_f32_rz(double x) {
 
 // W(:, i) in FP32 (used when W only feeds split-precision products, whose bf16 slices
 // keep 24 bits): same recurrence, eight lanes per row.
+// Threads t0 .. t0 + nth - 1 of the CTA take part (nth a multiple of 8).
 __device__ __forceinline__ void w_column_f32(int i, float tau, const float* g, const double* slab, int Rp, int rb,
-                                             int nr, float* wl) {
+                                             int nr, float* wl, int t0 = 0, int nth = kPanelThreads) {
   constexpr int PARTS = 8;
-  const int part = threadIdx.x % PARTS;
-  for (int r0 = 0; r0 < nr; r0 += kPanelThreads / PARTS) {
-    const int r = r0 + threadIdx.x / PARTS;
+  const int lt = (int)threadIdx.x - t0;
+  const int part = lt % PARTS;
+  for (int r0 = 0; r0 < nr; r0 += nth / PARTS) {
+    const int r = r0 + lt / PARTS;
     float s = 0.f;
     if (r < nr)
       for (int q = part; q < i; q += PARTS) s = fmaf(wl[r + q * Rp], g[q], s);
@@ -86,11 +88,12 @@ __device__ __forceinline__ void w_column_f32(int i, float tau, const float* g, c
 // lanes share a row (each sums every eighth term), so every warp of the CTA takes part:
 // an FP64 instruction costs the same pipe time whether one lane or 32 are active.
 __device__ __forceinline__ void w_column(int i, double tau, const double* g, const double* slab, int Rp, int rb,
-                                         int nr, double* wl, int64_t wld) {
+                                         int nr, double* wl, int64_t wld, int t0 = 0, int nth = kPanelThreads) {
   constexpr int PARTS = 8;
-  const int part = threadIdx.x % PARTS;
-  for (int r0 = 0; r0 < nr; r0 += kPanelThreads / PARTS) {
-    const int r = r0 + threadIdx.x / PARTS;
+  const int lt = (int)threadIdx.x - t0;
+  const int part = lt % PARTS;
+  for (int r0 = 0; r0 < nr; r0 += nth / PARTS) {
+    const int r = r0 + lt / PARTS;
     double s0 = 0.0, s1 = 0.0;
     if (r < nr) {
       int q = part;
