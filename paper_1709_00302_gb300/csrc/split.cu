@@ -654,6 +654,17 @@ __global__ void __launch_bounds__(NT, 2) rank_update_kernel(RankParams single, c
   const uint32_t tmem = *tmem_holder;
   const int nkb = p.Kr / RK;
   const size_t blk = (size_t)S * L::slice_bytes;  // one (row block, K block) of a blob
+  // Start fetching this CTA's C tile into L2 now, so the epilogue's reads overlap the
+  // slice copies and the MMAs instead of following them: one 128-byte line per
+  // (column, 16-row group), columns this CTA will update.
+  {
+    const int row0 = I * BM;
+    for (int q = tid; q < BM * (BM / 16); q += NT) {
+      const int col = J * BM + q / (BM / 16), r = row0 + (q % (BM / 16)) * 16;
+      if (r < p.M && col < p.N && col >= p.col0 && col < p.col1 && (!p.lower || r + 15 >= col))
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(p.C + r + (int64_t)col * p.ldc));
+    }
+  }
   int to = 0;
   for (int kb = 0; kb < nkb && !to; ++kb) {
     if (tid == 0) {
