@@ -56,9 +56,13 @@ struct Carver {
   }
 };
 
+// Panel CTAs per SM (two per SM were measured slower: the per-step barrier and scalar
+// chain do not shrink, while the CTAs compete for the FP64 pipe).
+constexpr int kPanelCtasPerSm = 1;
+
 int panel_max_ctas(int sms, const Options& o) {
-  if (o.panel_ctas > 0) return std::min(o.panel_ctas, sms);
-  return sms;
+  if (o.panel_ctas > 0) return std::min(o.panel_ctas, kPanelCtasPerSm * sms);
+  return kPanelCtasPerSm * sms;
 }
 
 int choose_splits(int M, int N, int K, size_t capacity_doubles, int sms) {
@@ -158,7 +162,7 @@ static Sy2sbWs carve_sy2sb(void* work, int64_t n, int64_t w, const Options& o, i
     ws.splitk[q] = q < nbuf ? c.take<double>(ws.splitk_cap) : ws.splitk[0];
   }
   ws.rowbuf = c.take<double>(4 * (size_t)b);  // two rows per step, two steps
-  ws.part2 = c.take<double>((size_t)sms);
+  ws.part2 = c.take<double>((size_t)kPanelCtasPerSm * sms);
   ws.gs = c.take<GridSync>(1);  // 256 bytes, immediately followed by the accumulators
   ws.part = c.take<double>((panel_sync_bytes((int)b) - 256) / sizeof(double));
   if (is_split(o)) {
@@ -215,7 +219,7 @@ static Ge2gbWs carve_ge2gb(void* work, int64_t m, int64_t n, const Options& o, i
     ws.splitk[q] = q < nbuf ? c.take<double>(ws.splitk_cap) : ws.splitk[0];
   }
   ws.rowbuf = c.take<double>(4 * (size_t)b);  // two rows per step, two steps
-  ws.part2 = c.take<double>((size_t)sms);
+  ws.part2 = c.take<double>((size_t)kPanelCtasPerSm * sms);
   ws.gs = c.take<GridSync>(1);  // 256 bytes, immediately followed by the accumulators
   ws.part = c.take<double>((panel_sync_bytes((int)b) - 256) / sizeof(double));
   if (is_split(o)) {

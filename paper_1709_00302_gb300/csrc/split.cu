@@ -698,6 +698,7 @@ __global__ void __launch_bounds__(NT, 2) rank_update_kernel(RankParams single, c
     const int q = warp & 3, h = warp >> 2;
     const int row = I * BM + q * 32 + lane;
     const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * 64);
+    const bool unit_alpha = p.alpha == 1.0;
     // 16 columns at a time (two CTAs fit an SM: one's epilogue overlaps the other's
     // copies and MMAs); all loads of a part are issued before its stores.
 #pragma unroll 1
@@ -712,13 +713,21 @@ __global__ void __launch_bounds__(NT, 2) rank_update_kernel(RankParams single, c
         const bool in = row < p.M && col < p.N && col >= p.col0 && col < p.col1 && (!p.lower || row >= col);
         old[c] = in ? p.C[row + (int64_t)col * p.ldc] : 0.0;
       }
+      // one FP64 instruction per entry (the FP64 pipe bounds this epilogue): alpha = 1
+      // adds, other values take the FMA in a separate, uniform branch
+      if (unit_alpha) {
 #pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        const int col = colb + c;
-        const bool in = row < p.M && col < p.N && col >= p.col0 && col < p.col1 && (!p.lower || row >= col);
-        if (in) {
-          const double d = tc::f32_to_f64(v[c]);
-          p.C[row + (int64_t)col * p.ldc] = (p.alpha == 1.0) ? old[c] + d : fma(p.alpha, d, old[c]);
+        for (int c = 0; c < 16; ++c) {
+          const int col = colb + c;
+          const bool in = row < p.M && col < p.N && col >= p.col0 && col < p.col1 && (!p.lower || row >= col);
+          if (in) p.C[row + (int64_t)col * p.ldc] = old[c] + tc::f32_to_f64(v[c]);
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const int col = colb + c;
+          const bool in = row < p.M && col < p.N && col >= p.col0 && col < p.col1 && (!p.lower || row >= col);
+          if (in) p.C[row + (int64_t)col * p.ldc] = fma(p.alpha, tc::f32_to_f64(v[c]), old[c]);
         }
       }
     }
