@@ -561,6 +561,7 @@ def main():
     ap.add_argument("--batch-b", type=int, default=0)
     ap.add_argument("--panel-ctas", type=int, default=0, help="panel_ctas option (batched: CTAs per matrix panel)")
     ap.add_argument("--no-fp64-path", action="store_true", help="skip the FP64 comparison line")
+    ap.add_argument("--no-ozaki-path", action="store_true", help="skip the Ozaki-scheme comparison line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-cols", type=int, default=96, help="reflectors per reference-arm step")
@@ -671,6 +672,17 @@ def main():
         fp64 = {"ms_per_step": ms64[0], "value": prob["flops"] / (ms64[0] / 1e3) / 1e12,
                 "backward_error": b64, "speedup_of_headline": ms64[0] / ms_step}
 
+    # ---- Ozaki-scheme path (FP64-class accuracy on the tensor cores) on the same matrix:
+    # the speedup over the FP64 path at equal backward error
+    ozaki = None
+    if args.precision != "ozaki" and not args.no_ozaki_path:
+        callz, outsz, _ = make_call("ozaki", args.lookahead)
+        msz, _, _, _ = timed_steps(callz, 1, 1)
+        bz = prob["backward"](A, outsz)
+        ozaki = {"ms_per_step": msz[0], "value": prob["flops"] / (msz[0] / 1e3) / 1e12, "backward_error": bz}
+        if fp64 is not None:
+            ozaki["speedup_vs_fp64_path"] = fp64["ms_per_step"] / msz[0]
+
     # ---- CPU baseline: the oracle on the host cores, bounded sample
     cpu = None
     if world == 1 and rank == 0 and not args.no_cpu_baseline and args.workload == "sy2sb":
@@ -690,6 +702,7 @@ def main():
             "cpu_baseline": cpu,
             "e2e": e2e,
             "fp64_path": fp64,
+            "ozaki_path": ozaki,
             "gpu_launches": launches,
             "clocks": clocks,
             "step_ms": ms,

@@ -50,8 +50,12 @@ enum bandred_precision {
                               products hi*hi + hi*lo + lo*hi, FP32 accumulation in TMEM,
                               FP64 recombination (FP32-class accuracy) */
     BANDRED_BF16X6 = 2,    /* three bf16 slices, the six products of order <= 2 */
-    BANDRED_OZAKI = 3      /* `slices` bf16 slices with exponent alignment per row/column,
-                              exact chunked FP32 accumulation, FP64 recombination */
+    BANDRED_OZAKI = 3      /* FP64-class accuracy on the tensor cores (Ozaki scheme): each
+                              row of an operand scaled by a power of two and cut into 7
+                              signed 8-bit digits (exact in bf16); digit-pair products
+                              accumulated exactly (FP32 sums below 2^24, then 64-bit
+                              integers) and combined in FP64; error below 2^-56 of the
+                              row and column scales.  `slices` is ignored (7 digits) */
 };
 
 /* Look-ahead variant (Section 2.2): 0 = none (the basic right-looking loop), 1 = V1
@@ -60,7 +64,7 @@ typedef struct bandred_opts {
     int b;                 /* panel width (algorithmic block size), 1 <= b <= w; 0 = default */
     int lookahead;         /* -1 auto, 0 none, 1 V1, 2 V2 */
     int precision;         /* enum bandred_precision */
-    int slices;            /* slices for BANDRED_OZAKI (2..8); ignored otherwise */
+    int slices;            /* reserved for the digit count of BANDRED_OZAKI; ignored */
     int panel_ctas;        /* CTAs of the panel factorisation (0 = all SMs when no
                               look-ahead, a tuned share otherwise).  Batched calls: CTAs
                               (one thread-block cluster, rounded up to a power of two
@@ -216,6 +220,8 @@ int bandred_ge2gb_batched_run(int count, const int64_t* m, const int64_t* n, con
  * recombined in FP64 every 256 reduction steps.  Accuracy is FP32-class (about 1e-5
  * relative for BF16X3 and 1e-6 for BF16X6, relative to sum_k |a_ik||b_kj|).  Entries must
  * be zero or lie in 2^-95 <= |x| < 2^127; otherwise dev_status reports BANDRED_DEV_RANGE.
+ * BANDRED_OZAKI takes any finite entries and is accurate to about 2^-56 of
+ * max_k |a_ik| max_k |b_kj| per term (FP64-class).
  * Arguments are device pointers (column-major FP64) except sizes; work is a device
  * buffer (256-byte aligned) of at least the queried size.  No allocation, stream-ordered.
  */

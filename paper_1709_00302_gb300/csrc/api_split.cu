@@ -5,6 +5,7 @@
 #include <cstdint>
 
 #include "driver.h"
+#include "ozaki.h"
 #include "prof.h"
 #include "split.h"
 
@@ -29,7 +30,7 @@ int sms_now() {
   return sms > 0 ? sms : 1;
 }
 
-bool valid_split_precision(int p) { return p == BANDRED_BF16X3 || p == BANDRED_BF16X6; }
+bool valid_split_precision(int p) { return p == BANDRED_BF16X3 || p == BANDRED_BF16X6 || p == BANDRED_OZAKI; }
 
 }  // namespace
 
@@ -37,6 +38,10 @@ extern "C" {
 
 size_t bandred_gemm_split_workspace(int64_t m, int64_t n, int64_t k, int precision) {
   if (m < 0 || n < 1 || n > 128 || k < 0 || !valid_split_precision(precision)) return 0;
+  if (precision == BANDRED_OZAKI) {
+    const int sp = ozaki::choose_splits((int)m, (int)n, (int)k, sms_now());
+    return ozaki::bytes((int)m, (int)n, (int)k, sp) + 256;
+  }
   const int S = split::slices_of(precision);
   const int BN = split::stream_bn((int)n);
   const int splits = gemm_splits((int)m, (int)k, sms_now());
@@ -60,6 +65,17 @@ int bandred_gemm_split(int64_t m, int64_t n, int64_t k, const double* A, int64_t
   if (!work || (reinterpret_cast<uintptr_t>(work) & 255u)) return -12;
   if (work_bytes < bandred_gemm_split_workspace(m, n, k, precision)) return -13;
   if (m == 0) return 0;
+  if (precision == BANDRED_OZAKI) {
+    if (dev_status && cudaMemsetAsync(dev_status, 0, sizeof(int), stream) != cudaSuccess) return BANDRED_ERR_CUDA;
+    const int sp = ozaki::choose_splits((int)m, (int)n, (int)k, sms_now());
+    const ozaki::Bufs b = ozaki::carve(work, (int)m, (int)n, (int)k, sp);
+    const ozaki::Operand opA{A, lda, transA ? 1 : 0, (int)k, nullptr, 0, 0, 0, (int)m};
+    const ozaki::Operand opB{B, ldb, 1, (int)k, nullptr, 0, 0, 0, (int)n};
+    if (ozaki::product(opA, opB, (int)m, (int)n, (int)k, 1.0, 0.0, C, ldc, b, sp, dev_status, 2000ull * 1000000ull,
+                       stream) != cudaSuccess)
+      return BANDRED_ERR_CUDA;
+    return 0;
+  }
   const int S = split::slices_of(precision);
   const int BN = split::stream_bn((int)n);
   const int K = (int)std::max<int64_t>(k, 1);
@@ -114,6 +130,7 @@ int bandred_gemm_split(int64_t m, int64_t n, int64_t k, const double* A, int64_t
 
 size_t bandred_syr2k_split_workspace(int64_t n, int64_t kb, int precision) {
   if (n < 0 || kb < 1 || !valid_split_precision(precision)) return 0;
+  if (precision == BANDRED_OZAKI) return ozaki::bytes((int)n, (int)n, (int)(2 * kb), 1, false) + 256;
   const int S = split::slices_of(precision);
   const int Kr = (int)((2 * kb + 63) / 64 * 64);
   return 2 * al(split::packed_bytes((int)std::max<int64_t>(n, 1), Kr, 128, 64, S)) + 256;
@@ -134,6 +151,17 @@ int bandred_syr2k_split(int64_t n, int64_t kb, const double* X, int64_t ldx, con
   if (!work || (reinterpret_cast<uintptr_t>(work) & 255u)) return -10;
   if (work_bytes < bandred_syr2k_split_workspace(n, kb, precision)) return -11;
   if (n == 0) return 0;
+  if (precision == BANDRED_OZAKI) {
+    if (dev_status && cudaMemsetAsync(dev_status, 0, sizeof(int), stream) != cudaSuccess) return BANDRED_ERR_CUDA;
+    const ozaki::Bufs b = ozaki::carve(work, (int)n, (int)n, (int)(2 * kb), 1);
+    const ozaki::Operand opA{X, ldx, 0, (int)kb, Y, ldy, 0, (int)kb, (int)n};  // [X | Y]
+    const ozaki::Operand opB{Y, ldy, 0, (int)kb, X, ldx, 0, (int)kb, (int)n};  // [Y | X]
+    if (ozaki::prepare(opA, opB, b, stream) != cudaSuccess) return BANDRED_ERR_CUDA;
+    if (ozaki::rank_apply((int)n, (int)n, (int)(2 * kb), 1.0, C, ldc, 0, (int)n, 1, b, dev_status,
+                          2000ull * 1000000ull, stream) != cudaSuccess)
+      return BANDRED_ERR_CUDA;
+    return 0;
+  }
   const int S = split::slices_of(precision);
   const int Kr = (int)((2 * kb + 63) / 64 * 64);
   const size_t blob = al(split::packed_bytes((int)n, Kr, 128, 64, S));

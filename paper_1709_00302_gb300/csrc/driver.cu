@@ -10,6 +10,7 @@
 
 #include "common.cuh"
 #include "driver.h"
+#include "ozaki.h"
 #include "kernels.h"
 #include "prof.h"
 #include "split.h"
@@ -134,6 +135,10 @@ struct Sy2sbWs {
   __nv_bfloat16 *wblob, *x2blob, *ablob, *bblob;
   double* P;
   size_t P_cap;
+  // Ozaki-scheme buffers: products (exponents, packed operands, split partials) and the
+  // packed operands of the rank-2k update
+  char *ozp, *ozr;
+  size_t ozp_cap;
   int64_t ld;
   size_t splitk_cap;
   int* status;
@@ -176,6 +181,12 @@ static Sy2sbWs carve_sy2sb(void* work, int64_t n, int64_t w, const Options& o, i
     ws.P_cap = std::max<size_t>((size_t)kMaxStreamSplits * jmax * BN, (size_t)kMaxSmallSplits * BN * BN);
     ws.P = c.take<double>(ws.P_cap);
   }
+  if (o.precision == BANDRED_OZAKI) {
+    const int J = (int)jmax, B = (int)b;
+    ws.ozp_cap = ozaki::bytes(J, B, J, ozaki::choose_splits(J, B, J, sms));
+    ws.ozp = c.take<char>(ws.ozp_cap);
+    ws.ozr = c.take<char>(ozaki::bytes(J, J, 2 * B, 1, false));
+  }
   ws.status = c.take<int>(1);  // last piece: the short forms read it at bytes - 256
   ws.bytes = c.off;
   return ws;
@@ -193,6 +204,8 @@ struct Ge2gbWs {
   double *Yu[2], *Wu[2], *Yv, *Wv, *Z[2], *ZT, *P, *splitk[2], *part, *rowbuf, *part2;
   GridSync* gs;
   SplitBufs sb[2];  // [0] caller's stream, [1] panel stream (look-ahead)
+  char *ozp[2], *ozr[2];  // Ozaki-scheme buffers per stream (see Sy2sbWs)
+  size_t ozp_cap;
   int* status;
   int64_t ldu, ldv;
   size_t splitk_cap;
@@ -237,6 +250,19 @@ static Ge2gbWs carve_ge2gb(void* work, int64_t m, int64_t n, const Options& o, i
       sb.P = c.take<double>(sb.P_cap);
     }
     if (nbuf == 1) ws.sb[1] = ws.sb[0];
+  }
+  if (o.precision == BANDRED_OZAKI) {
+    const int big = (int)std::max(ws.ldu, ws.ldv), B = (int)b;
+    ws.ZT = c.take<double>(ws.ldv * b);
+    ws.ozp_cap = ozaki::bytes(big, B, big, ozaki::choose_splits(big, B, big, sms));
+    for (int q = 0; q < nbuf; ++q) {
+      ws.ozp[q] = c.take<char>(ws.ozp_cap);
+      ws.ozr[q] = c.take<char>(ozaki::bytes(big, big, B, 1, false));
+    }
+    if (nbuf == 1) {
+      ws.ozp[1] = ws.ozp[0];
+      ws.ozr[1] = ws.ozr[0];
+    }
   }
   ws.status = c.take<int>(1);  // last piece: the short forms read it at bytes - 256
   ws.bytes = c.off;
@@ -405,6 +431,35 @@ struct Sy2sb {
     double* A2 = A + r0 + r0 * lda;
     const double* Y = ws.Y[buf];
     const double* W = ws.W[buf];
+    if (o.precision == BANDRED_OZAKI) {
+      using ozaki::Operand;
+      const int B = bk;
+      const unsigned long long lim = o.limit_ns;
+      {
+        // X1 = A2 W (A2 symmetric, lower stored; row (n, k) of the right operand is W(k, n))
+        prof::Scope sc(prof::kSymm, s, symm_flops(j, bk), symm_bytes(j, bk));
+        const int sp = ozaki::fit_splits(j, B, j, ozaki::choose_splits(j, B, j, sms), ws.ozp_cap);
+        const Operand a{A2, lda, 2, j, nullptr, 0, 0, 0, j}, w{W, ld, 1, j, nullptr, 0, 0, 0, B};
+        CK(ozaki::product(a, w, j, B, j, 1.0, 0.0, ws.X, ld, ozaki::carve(ws.ozp, j, B, j, sp), sp, status, lim, s));
+      }
+      prof::Scope sc(prof::kGemm, s, 4.0 * j * bk * bk, 8.0 * 4.0 * j * bk);
+      {
+        // X2 = X1^T W / 2
+        const int sp = ozaki::fit_splits(B, B, j, ozaki::choose_splits(B, B, j, sms), ws.ozp_cap);
+        const Operand x{ws.X, ld, 1, j, nullptr, 0, 0, 0, B}, w{W, ld, 1, j, nullptr, 0, 0, 0, B};
+        CK(ozaki::product(x, w, B, B, j, 0.5, 0.0, ws.X2, B, ozaki::carve(ws.ozp, B, B, j, sp), sp, status, lim, s));
+      }
+      {
+        // X3 = X1 + Y X2
+        const int sp = ozaki::fit_splits(j, B, B, ozaki::choose_splits(j, B, B, sms), ws.ozp_cap);
+        const Operand y{Y, ld, 0, B, nullptr, 0, 0, 0, j}, x2{ws.X2, B, 1, B, nullptr, 0, 0, 0, B};
+        CK(ozaki::product(y, x2, j, B, B, 1.0, 1.0, ws.X, ld, ozaki::carve(ws.ozp, j, B, B, sp), sp, status, lim, s));
+      }
+      // operands of A2 += X3 Y^T + Y X3^T: [X3 | Y] and [Y | X3]
+      const Operand l{ws.X, ld, 0, B, Y, ld, 0, B, j}, r{Y, ld, 0, B, ws.X, ld, 0, B, j};
+      CK(ozaki::prepare(l, r, ozaki::carve(ws.ozr, j, j, 2 * B, 1), s));
+      return 0;
+    }
     if (!is_split(o)) {
       {
         prof::Scope sc(prof::kSymm, s, symm_flops(j, bk), symm_bytes(j, bk));
@@ -548,6 +603,11 @@ struct Sy2sb {
     if (c1 <= c0) return 0;
     double* A2 = A + r0 + r0 * lda;
     prof::Scope sc(prof::kSyr2k, s, syr2k_flops(j, c0, c1, bk), syr2k_bytes(j, c0, c1, bk));
+    if (o.precision == BANDRED_OZAKI) {
+      CK(ozaki::rank_apply(j, j, 2 * bk, 1.0, A2, lda, c0, c1, 1, ozaki::carve(ws.ozr, j, j, 2 * bk, 1), status,
+                           o.limit_ns, s));
+      return 0;
+    }
     if (!is_split(o)) {
       CK(syr2k_lower_f64(j, bk, A2, lda, ws.X, ws.ld, ws.Y[buf], ws.ld, c0, c1, s));
       return 0;
@@ -602,7 +662,6 @@ int sy2sb_run(int64_t n, int64_t w, double* A, int64_t lda, double* tau, const O
   R.pmax = panel_max_ctas(R.sms, o);
   R.S = is_split(o) ? split::slices_of(o.precision) : 0;
   R.extra = o.debug ? 1u : 0u;
-  if (o.precision == BANDRED_OZAKI) return BANDRED_ERR_UNSUPPORTED;
   CK(cudaMemsetAsync(R.status, 0, sizeof(int), s));
   const int64_t nref = n - w;
   if (nref <= 0) return 0;
@@ -821,7 +880,7 @@ struct Ge2gb {
     if (c1 <= c0) return 0;
     const int nc = c1 - c0;
     double* E = A + k + (k + bk + c0) * lda;
-    if (!is_split(o)) {
+    if (o.precision == BANDRED_FP64) {
       prof::Scope sc(prof::kGemm, s, 4.0 * j * nc * bk, 8.0 * (3.0 * j * nc + 2.0 * j * bk));
       const int sp = choose_splits(bk, nc, j, ws.splitk_cap, sms);
       CK(gemm_f64(bk, nc, j, 1.0, MatView{ws.Wu[buf], ws.ldu, 1}, MatView{E, 1, lda}, 0.0, ws.Z[q], bk, sp,
@@ -832,6 +891,22 @@ struct Ge2gb {
     }
     // Z^T = E^T W_U (nc x bk), then E += Y_U (Z^T)^T
     double* ZT = ws.ZT + c0;
+    if (o.precision == BANDRED_OZAKI) {
+      using ozaki::Operand;
+      const Operand et{E, lda, 1, j, nullptr, 0, 0, 0, nc}, wu{ws.Wu[buf], ws.ldu, 1, j, nullptr, 0, 0, 0, bk};
+      {
+        prof::Scope sc(prof::kStream, s, 2.0 * nc * bk * j, 8.0 * ((double)j * nc + (double)j * bk + (double)nc * bk));
+        const int sp = ozaki::fit_splits(nc, bk, j, ozaki::choose_splits(nc, bk, j, sms), ws.ozp_cap);
+        CK(ozaki::product(et, wu, nc, bk, j, 1.0, 0.0, ZT, ws.ldv, ozaki::carve(ws.ozp[q], nc, bk, j, sp), sp, status,
+                          o.limit_ns, s));
+      }
+      prof::Scope sc(prof::kRank, s, 2.0 * j * nc * bk, 8.0 * (2.0 * j * nc + (double)(j + nc) * bk));
+      const Operand yu{ws.Yu[buf], ws.ldu, 0, bk, nullptr, 0, 0, 0, j}, zt{ZT, ws.ldv, 0, bk, nullptr, 0, 0, 0, nc};
+      const ozaki::Bufs rb = ozaki::carve(ws.ozr[q], j, nc, bk, 1);
+      CK(ozaki::prepare(yu, zt, rb, s));
+      CK(ozaki::rank_apply(j, nc, bk, 1.0, E, lda, 0, nc, 0, rb, status, o.limit_ns, s));
+      return 0;
+    }
     if (int rc = split_product(nc, bk, j, E, lda, split::kModeTrans, ws.Wu[buf], ws.ldu, 1.0, 0.0, ZT, ws.ldv,
                                ws.sb[q], S, sms, status, o.limit_ns, s))
       return rc;
@@ -858,13 +933,30 @@ struct Ge2gb {
     const int nrow = (int)(m - k - bkr);
     if (nrow <= 0) return 0;
     double* D = A + (k + bkr) + (k + w) * lda;
-    if (!is_split(o)) {
+    if (o.precision == BANDRED_FP64) {
       prof::Scope sc(prof::kGemm, s, 4.0 * nrow * jr * bkr, 8.0 * (3.0 * nrow * jr + 2.0 * nrow * bkr));
       const int sp = choose_splits(nrow, (int)bkr, jr, ws.splitk_cap, sms);
       CK(gemm_f64(nrow, (int)bkr, jr, 1.0, MatView{D, 1, lda}, MatView{ws.Wv, 1, ws.ldv}, 0.0, ws.P, ws.ldu, sp,
                   ws.splitk[0], s));
       CK(gemm_f64(nrow, jr, (int)bkr, 1.0, MatView{ws.P, 1, ws.ldu}, MatView{ws.Yv, ws.ldv, 1}, 1.0, D, lda, 1,
                   nullptr, s));
+      return 0;
+    }
+    if (o.precision == BANDRED_OZAKI) {
+      using ozaki::Operand;
+      const int B = (int)bkr;
+      const Operand d{D, lda, 0, jr, nullptr, 0, 0, 0, nrow}, wv{ws.Wv, ws.ldv, 1, jr, nullptr, 0, 0, 0, B};
+      {
+        prof::Scope sc(prof::kStream, s, 2.0 * nrow * B * jr, 8.0 * ((double)nrow * jr + (double)jr * B + (double)nrow * B));
+        const int sp = ozaki::fit_splits(nrow, B, jr, ozaki::choose_splits(nrow, B, jr, sms), ws.ozp_cap);
+        CK(ozaki::product(d, wv, nrow, B, jr, 1.0, 0.0, ws.P, ws.ldu, ozaki::carve(ws.ozp[0], nrow, B, jr, sp), sp,
+                          status, o.limit_ns, s));
+      }
+      prof::Scope sc(prof::kRank, s, 2.0 * nrow * jr * B, 8.0 * (2.0 * nrow * jr + (double)(nrow + jr) * B));
+      const Operand pp{ws.P, ws.ldu, 0, B, nullptr, 0, 0, 0, nrow}, yv{ws.Yv, ws.ldv, 0, B, nullptr, 0, 0, 0, jr};
+      const ozaki::Bufs rb = ozaki::carve(ws.ozr[0], nrow, jr, B, 1);
+      CK(ozaki::prepare(pp, yv, rb, s));
+      CK(ozaki::rank_apply(nrow, jr, B, 1.0, D, lda, 0, jr, 0, rb, status, o.limit_ns, s));
       return 0;
     }
     if (int rc = split_product(nrow, (int)bkr, jr, D, lda, split::kModePlain, ws.Wv, ws.ldv, 1.0, 0.0, ws.P, ws.ldu,
@@ -905,7 +997,6 @@ int ge2gb_run(int64_t m, int64_t n, int64_t w, double* A, int64_t lda, double* t
   R.pmax = panel_max_ctas(R.sms, o);
   R.S = is_split(o) ? split::slices_of(o.precision) : 0;
   R.extra = o.debug ? 1u : 0u;
-  if (o.precision == BANDRED_OZAKI) return BANDRED_ERR_UNSUPPORTED;
   CK(cudaMemsetAsync(R.status, 0, sizeof(int), s));
   if (n <= 0) return 0;
   CK(cudaMemsetAsync(tauq, 0, sizeof(double) * n, s));

@@ -1,0 +1,516 @@
+// FP64-accurate products on BF16 tensor cores (Ozaki scheme); see ozaki.h.
+//
+// Digits.  A row r with largest biased exponent E_r is scaled by 2^-(E_r - 1021), so
+// every entry x has |x| 2^-(E_r - 1021) < 1/2 and F = round(x 2^(56 - (E_r - 1021))) is an
+// integer with |F| < 2^55.  F is written as S = 7 balanced base-256 digits
+// d_0 .. d_6 in [-128, 128] (d_0 most significant): x ~= 2^(E_r - 1021) sum_s d_s 2^-8(s+1).
+// For C = A B^T the digit pairs (s, t) with s + t <= 6 are multiplied on the tensor cores
+// (exact: |d d'| <= 2^14) and accumulated in FP32 per diagonal D = s + t in tensor memory;
+// over 128 reduction steps a diagonal's sum stays below 7 * 128 * 2^14 < 2^24, so it is
+// exact.  Every 128 steps the diagonals are read out as integers and added into
+//   T_hi = P_0 2^16 + P_1 2^8 + P_2,   T_lo = P_3 2^24 + P_4 2^16 + P_5 2^8 + P_6,
+// 64-bit integers, and at the end
+//   C(i, j) = 2^(E_i - 1021) 2^(E_j - 1021) (T_hi 2^-32 + T_lo 2^-64).
+// The dropped pairs (s + t >= 7) weigh at most 2^-72 of the scales per term.
+#include <algorithm>
+#include <cstring>
+
+#include "bandred.h"
+#include "common.cuh"
+#include "ozaki.h"
+#include "prof.h"
+#include "tc.cuh"
+
+namespace bandred {
+namespace ozaki {
+
+namespace {
+
+constexpr int NT = 256;
+constexpr int S = kDigits;
+constexpr int kChunkBlocks = 4;  // 4 x 32 = 128 reduction steps per exact FP32 accumulation
+
+__device__ __forceinline__ int biased_exp(double x) {
+  return (int)(((uint32_t)__double2hiint(x) >> 20) & 0x7FFu);
+}
+
+__device__ __forceinline__ double elem(const double* M, int64_t ld, int mode, int r, int k) {
+  if (mode == 0) return M[r + (int64_t)k * ld];
+  if (mode == 1) return M[k + (int64_t)r * ld];
+  return k <= r ? M[r + (int64_t)k * ld] : M[k + (int64_t)r * ld];
+}
+
+// ---------------------------------------------------------------- row exponents
+// entries M[r + k ld] (k in [k0, k1), k <= r when `lower`): one thread per row
+__global__ void rowexp_cols_kernel(const double* M, int64_t ld, int R, int k0, int k1, int lower, int* e) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  const int per = (k1 - k0 + gridDim.y - 1) / gridDim.y;
+  const int kb = k0 + blockIdx.y * per, ke = min(k1, kb + per);
+  int m = 0;
+  for (int k = kb; k < ke; ++k) {
+    if (lower && k > r) break;
+    m = max(m, biased_exp(M[r + (int64_t)k * ld]));
+  }
+  if (m) atomicMax(&e[r], m);
+}
+
+// entries M[k + r ld] (k in [k0, k1), k > r when `upper`): one warp per row
+__global__ void rowexp_rows_kernel(const double* M, int64_t ld, int R, int k0, int k1, int upper, int* e) {
+  const int r = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x & 31;
+  if (r >= R) return;
+  const int per = (k1 - k0 + gridDim.y - 1) / gridDim.y;
+  int kb = k0 + blockIdx.y * per;
+  const int ke = min(k1, kb + per);
+  if (upper) kb = max(kb, r + 1);
+  int m = 0;
+  for (int k = kb + lane; k < ke; k += 32) m = max(m, biased_exp(M[k + (int64_t)r * ld]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0 && m) atomicMax(&e[r], m);
+}
+
+// ---------------------------------------------------------------- digits
+// x -> 7 balanced digits (most significant first), row exponent E.
+__device__ __forceinline__ void digits(double x, int E, int (&d)[S]) {
+  const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+  const int ea = (int)((hi >> 20) & 0x7FFu);
+  unsigned long long m = ((unsigned long long)(hi & 0xFFFFFu) << 32) | lo;
+  if (ea) m |= 1ull << 52;
+  const int sh = max(ea, 1) - E + 2;  // F = m 2^sh, sh <= 2
+  long long F;
+  if (sh >= 0)
+    F = (long long)(m << sh);
+  else if (sh > -60)
+    F = (long long)((m + (1ull << (-sh - 1))) >> (-sh));
+  else
+    F = 0;
+  if (hi & 0x80000000u) F = -F;
+#pragma unroll
+  for (int s = S - 1; s >= 0; --s) {
+    int v = (int)(F & 0xFF);
+    if (v >= 128) v -= 256;
+    d[s] = v;
+    F = (F - v) >> 8;
+  }
+  d[0] += (int)F * 256;  // |x| < 1/2 leaves no carry; kept for safety
+}
+
+__device__ __forceinline__ uint32_t bf16_pair(int a, int b) {
+  const uint32_t fa = __float_as_uint(__int2float_rn(a)), fb = __float_as_uint(__int2float_rn(b));
+  return __byte_perm(fa, fb, 0x7632);  // exact: |digit| <= 256 has at most 8 significant bits
+}
+
+__global__ void pack_kernel(Operand op, const int* e, int TR, int nrb, int nkb, __nv_bfloat16* out) {
+  const int groups = TR * (kDepth / 8);
+  const int64_t total = (int64_t)nrb * nkb * groups;
+  const int K = op.K1 + op.K2;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
+    const int within = (int)(g % groups);
+    const int64_t tile = g / groups;
+    const int kb = (int)(tile % nkb), rb = (int)(tile / nkb);
+    const int r = within % TR, kg = within / TR;
+    const int row = rb * TR + r;
+    const int E = row < op.R ? e[row] : 0;
+    int d[8][S];
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) {
+      const int k = kb * kDepth + kg * 8 + kk;
+      double x = 0.0;
+      if (row < op.R && k < K)
+        x = k < op.K1 ? elem(op.M1, op.ld1, op.mode1, row, k) : elem(op.M2, op.ld2, op.mode2, row, k - op.K1);
+      digits(x, E, d[kk]);
+    }
+    const size_t plane = (size_t)TR * kDepth;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      __nv_bfloat16* base = out + ((size_t)tile * S + s) * plane;
+      uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<char*>(base) + tc::kmajor_offset(r, kg * 8, TR));
+      *dst = make_uint4(bf16_pair(d[0][s], d[1][s]), bf16_pair(d[2][s], d[3][s]), bf16_pair(d[4][s], d[5][s]),
+                        bf16_pair(d[6][s], d[7][s]));
+    }
+  }
+}
+
+// ---------------------------------------------------------------- GEMM
+struct Smem {
+  static constexpr size_t a_plane = (size_t)kTileA * kDepth * 2;
+  static constexpr size_t b_plane = (size_t)kTileB * kDepth * 2;
+  static constexpr size_t a_block = S * a_plane;
+  static constexpr size_t b_block = S * b_plane;
+  static constexpr size_t stage = a_block + b_block;
+  static constexpr size_t off_bar = 2 * stage;
+  static constexpr size_t total = off_bar + 128;
+};
+constexpr int kGemmThreads = NT + 32;  // eight drain/epilogue warps, one control warp
+constexpr uint32_t kTmemCols = 512;    // S diagonals x 64 columns = 448, rounded up
+
+__device__ __forceinline__ double pow2(int k) {  // 2^k for -1022 <= k <= 1023
+  return __longlong_as_double((long long)(k + 1023) << 52);
+}
+// v 2^k for any k (two exact power-of-two factors)
+__device__ __forceinline__ double scale2(double v, int k) {
+  const int k1 = max(-1022, min(1023, k / 2));
+  return v * pow2(k1) * pow2(max(-1022, min(1023, k - k1)));
+}
+
+__global__ void __launch_bounds__(kGemmThreads, 1) gemm_kernel(GemmParams p) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + Smem::off_bar);  // [2]
+  uint64_t* freed = full + 2;                                           // [2] MMAs of a stage done
+  uint64_t* acc_ready = freed + 2;                                      // chunk's MMAs done
+  uint64_t* drained = acc_ready + 1;                                    // tensor memory read
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(drained + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int I = blockIdx.x, J = blockIdx.y, z = blockIdx.z;
+  const int kb0 = z * p.kb_per_split, kb1 = min(p.nkb, kb0 + p.kb_per_split);
+  const int nst = kb1 - kb0;
+  if (p.C && p.lower && (I + 1) * kTileA <= J * kTileB) return;  // tile above the diagonal
+  if (p.C && (J * kTileB >= p.col1 || (J + 1) * kTileB <= p.col0)) return;
+  const unsigned long long deadline = global_ns() + p.limit_ns;
+  if (tid == 0) {
+    for (int q = 0; q < 2; ++q) {
+      tc::mbar_init(&full[q], 1);
+      tc::mbar_init(&freed[q], 1);
+    }
+    tc::mbar_init(acc_ready, 1);
+    tc::mbar_init(drained, NT / 32);
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(tmem_holder, kTmemCols);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_holder;
+  int timed_out = 0;
+  long long thi[32], tlo[32];
+#pragma unroll
+  for (int c = 0; c < 32; ++c) thi[c] = tlo[c] = 0;
+
+  if (warp == NT / 32) {
+    if (lane == 0 && nst > 0) {
+      auto issue = [&](int st) {
+        const int kb = kb0 + st, slot = st & 1;
+        unsigned char* dst = smem + slot * Smem::stage;
+        tc::mbar_arrive_expect_tx(&full[slot], (uint32_t)Smem::stage);
+        tc::bulk_g2s(dst, reinterpret_cast<const unsigned char*>(p.A) + ((size_t)I * p.nkb + kb) * Smem::a_block,
+                     (uint32_t)Smem::a_block, &full[slot]);
+        tc::bulk_g2s(dst + Smem::a_block,
+                     reinterpret_cast<const unsigned char*>(p.B) + ((size_t)J * p.nkb + kb) * Smem::b_block,
+                     (uint32_t)Smem::b_block, &full[slot]);
+      };
+      issue(0);
+      if (nst > 1) issue(1);
+      constexpr uint32_t idesc = tc::idesc_bf16_f32(kTileA, kTileB);
+      for (int st = 0; st < nst && !timed_out; ++st) {
+        const int slot = st & 1, chunk = st / kChunkBlocks;
+        if (!tc::mbar_wait(&full[slot], (uint32_t)(st >> 1) & 1u, deadline)) {
+          timed_out = 1;
+          break;
+        }
+        // the chunk's first MMAs overwrite the accumulators: the previous chunk must be read
+        if (st % kChunkBlocks == 0 && chunk > 0 &&
+            !tc::mbar_wait(drained, (uint32_t)(chunk - 1) & 1u, deadline)) {
+          timed_out = 1;
+          break;
+        }
+        tc::fence_after_sync();
+        const uint32_t abase = tc::smem_u32(smem + slot * Smem::stage);
+        const uint32_t bbase = abase + (uint32_t)Smem::a_block;
+#pragma unroll 1
+        for (int kk = 0; kk < kDepth / 16; ++kk) {
+#pragma unroll 1
+          for (int s = 0; s < S; ++s) {
+#pragma unroll 1
+            for (int t = 0; s + t < S; ++t) {
+              const int D = s + t;
+              const uint64_t ad = tc::smem_desc(abase + s * (uint32_t)Smem::a_plane + kk * 2 * (kTileA / 8) * 128,
+                                                (kTileA / 8) * 128, 128);
+              const uint64_t bd = tc::smem_desc(bbase + t * (uint32_t)Smem::b_plane + kk * 2 * (kTileB / 8) * 128,
+                                                (kTileB / 8) * 128, 128);
+              // the chunk's first product of diagonal D (s = 0, t = D) starts its accumulator
+              const bool first = (st % kChunkBlocks == 0) && kk == 0 && s == 0;
+              tc::mma_bf16(tmem + (uint32_t)(D * kTileB), ad, bd, idesc, first ? 0u : 1u);
+            }
+          }
+        }
+        tc::mma_commit(&freed[slot]);
+        if (st % kChunkBlocks == kChunkBlocks - 1 || st == nst - 1) tc::mma_commit(acc_ready);
+        // refill the other slot (stage st - 1's) with stage st + 1 once its MMAs are done;
+        // stage st's MMAs are already queued behind them
+        if (st >= 1 && st + 1 < nst) {
+          if (!tc::mbar_wait(&freed[(st - 1) & 1], (uint32_t)((st - 1) >> 1) & 1u, deadline)) {
+            timed_out = 1;
+            break;
+          }
+          issue(st + 1);
+        }
+      }
+      if (timed_out) {
+        const unsigned long long dl = global_ns() + p.limit_ns;
+        for (int q = 0; q < 2; ++q) {
+          tc::mbar_wait(&full[q], 0, dl);
+          tc::mbar_wait(&freed[q], 0, dl);
+        }
+      }
+    }
+  } else {
+    // drain warps: lane quadrant warp & 3, columns 32 (warp >> 2) .. + 31
+    const uint32_t q = warp & 3, h = warp >> 2;
+    const int nchunks = (nst + kChunkBlocks - 1) / kChunkBlocks;
+    for (int c = 0; c < nchunks; ++c) {
+      if (!tc::mbar_wait(acc_ready, (uint32_t)c & 1u, deadline)) {
+        timed_out = 1;
+        break;
+      }
+      tc::fence_after_sync();
+#pragma unroll 1
+      for (int D = 0; D < S; ++D) {
+        float v[32];
+        tc::tmem_ld32(tmem + ((q * 32) << 16) + (uint32_t)(D * kTileB + h * 32), v);
+        const int shift = D <= 2 ? 8 * (2 - D) : 8 * (6 - D);
+#pragma unroll
+        for (int cc = 0; cc < 32; ++cc) {
+          const long long iv = (long long)__float2int_rn(v[cc]) << shift;
+          if (D <= 2)
+            thi[cc] += iv;
+          else
+            tlo[cc] += iv;
+        }
+      }
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(drained);
+    }
+  }
+
+  if (__syncthreads_or(timed_out)) {
+    if (tid == 0 && p.status) atomicCAS(p.status, 0, BANDRED_DEV_TIMEOUT);
+  } else if (warp < NT / 32) {
+    const int q = warp & 3, h = warp >> 2;
+    const int row = I * kTileA + q * 32 + lane;
+    if (row < p.M) {
+      if (p.Phi) {
+        int64_t* Ph = p.Phi + (size_t)z * p.sstride;
+        int64_t* Pl = p.Plo + (size_t)z * p.sstride;
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          const int col = J * kTileB + h * 32 + c;
+          if (col < p.N) {
+            Ph[row + (int64_t)col * p.ldp] = thi[c];
+            Pl[row + (int64_t)col * p.ldp] = tlo[c];
+          }
+        }
+      } else {
+        const int ei = p.eA[row];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          const int col = J * kTileB + h * 32 + c;
+          if (col < p.N && col >= p.col0 && col < p.col1 && (!p.lower || row >= col)) {
+            const double v = fma((double)thi[c], 0x1p-32, (double)tlo[c] * 0x1p-64);
+            double* cp = p.C + row + (int64_t)col * p.ldc;
+            *cp = fma(p.alpha, scale2(v, (ei - 1021) + (p.eB[col] - 1021)), *cp);
+          }
+        }
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+__global__ void reduce_kernel(const int64_t* Phi, const int64_t* Plo, int64_t ldp, int64_t sstride, int splits,
+                              const int* eA, const int* eB, int M, int N, double alpha, double beta, double* C,
+                              int64_t ldc) {
+  const int64_t total = (int64_t)M * N;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % M), j = (int)(idx / M);
+    long long h = 0, l = 0;
+    for (int z = 0; z < splits; ++z) {
+      h += Phi[(size_t)z * sstride + i + (int64_t)j * ldp];
+      l += Plo[(size_t)z * sstride + i + (int64_t)j * ldp];
+    }
+    const double v = scale2(fma((double)h, 0x1p-32, (double)l * 0x1p-64), (eA[i] - 1021) + (eB[j] - 1021));
+    double* cp = C + i + (int64_t)j * ldc;
+    *cp = beta == 0.0 ? alpha * v : fma(alpha, v, beta * *cp);
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host API
+cudaError_t row_exponents(const Operand& op, int* e, cudaStream_t s) {
+  if (op.R <= 0) return cudaSuccess;
+  cudaError_t err = cudaMemsetAsync(e, 0, sizeof(int) * (size_t)op.R, s);
+  if (err != cudaSuccess) return err;
+  auto one = [&](const double* M, int64_t ld, int mode, int K) -> cudaError_t {
+    if (K <= 0 || !M) return cudaSuccess;
+    const int ks = std::max(1, std::min(64, K / 256));
+    if (mode == 0 || mode == 2) {
+      rowexp_cols_kernel<<<dim3((op.R + 255) / 256, ks), 256, 0, s>>>(M, ld, op.R, 0, K, mode == 2, e);
+      prof::count_launch();
+    }
+    if (mode == 1 || mode == 2) {
+      rowexp_rows_kernel<<<dim3((op.R + 7) / 8, ks), 256, 0, s>>>(M, ld, op.R, 0, K, mode == 2, e);
+      prof::count_launch();
+    }
+    return cudaGetLastError();
+  };
+  err = one(op.M1, op.ld1, op.mode1, op.K1);
+  if (err != cudaSuccess) return err;
+  return one(op.M2, op.ld2, op.mode2, op.K2);
+}
+
+size_t packed_bytes(int R, int K, int TR) {
+  const size_t nrb = (R + TR - 1) / TR, nkb = (K + kDepth - 1) / kDepth;
+  return nrb * nkb * (size_t)S * TR * kDepth * 2;
+}
+
+cudaError_t pack(const Operand& op, const int* e, int TR, __nv_bfloat16* out, cudaStream_t s) {
+  const int K = op.K1 + op.K2;
+  if (op.R <= 0 || K <= 0) return cudaSuccess;
+  const int nrb = (op.R + TR - 1) / TR, nkb = (K + kDepth - 1) / kDepth;
+  const int64_t total = (int64_t)nrb * nkb * TR * (kDepth / 8);
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 8192);
+  pack_kernel<<<blocks, 256, 0, s>>>(op, e, TR, nrb, nkb, out);
+  prof::count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t gemm(const GemmParams& p, int splits, cudaStream_t s) {
+  if (p.M <= 0 || p.N <= 0 || p.nkb <= 0) return cudaSuccess;
+  static int configured = -1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (configured != dev) {
+    cudaError_t e = cudaFuncSetAttribute(gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Smem::total);
+    if (e != cudaSuccess) return e;
+    configured = dev;
+  }
+  const dim3 grid((p.M + kTileA - 1) / kTileA, (p.N + kTileB - 1) / kTileB, splits);
+  gemm_kernel<<<grid, kGemmThreads, Smem::total, s>>>(p);
+  prof::count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t reduce(const GemmParams& p, int splits, double alpha, double beta, double* C, int64_t ldc,
+                   cudaStream_t s) {
+  const int64_t total = (int64_t)p.M * p.N;
+  if (total <= 0) return cudaSuccess;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
+  reduce_kernel<<<blocks, 256, 0, s>>>(p.Phi, p.Plo, p.ldp, p.sstride, splits, p.eA, p.eB, p.M, p.N, alpha, beta, C,
+                                       ldc);
+  prof::count_launch();
+  return cudaGetLastError();
+}
+
+static size_t al256(size_t x) { return (x + 255) / 256 * 256; }
+
+int choose_splits(int M, int N, int K, int sms) {
+  const int tiles = ((M + kTileA - 1) / kTileA) * ((N + kTileB - 1) / kTileB);
+  const int nkb = (K + kDepth - 1) / kDepth;
+  int sp = std::max(1, sms / std::max(tiles, 1));
+  sp = std::min(sp, std::max(1, nkb / kChunkBlocks));  // at least one exact chunk per split
+  return std::min(sp, 64);
+}
+
+size_t bytes(int M, int N, int K, int splits, bool partials) {
+  M = std::max(M, 1);
+  N = std::max(N, 1);
+  K = std::max(K, 1);
+  return al256(sizeof(int) * (size_t)M) + al256(sizeof(int) * (size_t)N) + al256(packed_bytes(M, K, kTileA)) +
+         al256(packed_bytes(N, K, kTileB)) + (partials ? al256(2 * sizeof(int64_t) * (size_t)splits * M * N) : 0);
+}
+
+int fit_splits(int M, int N, int K, int want, size_t cap) {
+  int sp = std::max(1, want);
+  while (sp > 1 && bytes(M, N, K, sp) > cap) --sp;
+  return sp;
+}
+
+Bufs carve(void* base, int M, int N, int K, int splits) {
+  M = std::max(M, 1);
+  N = std::max(N, 1);
+  K = std::max(K, 1);
+  char* w = static_cast<char*>(base);
+  Bufs b;
+  b.eA = reinterpret_cast<int*>(w);
+  w += al256(sizeof(int) * (size_t)M);
+  b.eB = reinterpret_cast<int*>(w);
+  w += al256(sizeof(int) * (size_t)N);
+  b.Ablob = reinterpret_cast<__nv_bfloat16*>(w);
+  w += al256(packed_bytes(M, K, kTileA));
+  b.Bblob = reinterpret_cast<__nv_bfloat16*>(w);
+  w += al256(packed_bytes(N, K, kTileB));
+  b.P = reinterpret_cast<int64_t*>(w);
+  return b;
+}
+
+cudaError_t prepare(const Operand& A, const Operand& B, const Bufs& b, cudaStream_t s) {
+  cudaError_t e = row_exponents(A, b.eA, s);
+  if (e == cudaSuccess) e = row_exponents(B, b.eB, s);
+  if (e == cudaSuccess) e = pack(A, b.eA, kTileA, b.Ablob, s);
+  if (e == cudaSuccess) e = pack(B, b.eB, kTileB, b.Bblob, s);
+  return e;
+}
+
+cudaError_t product(const Operand& A, const Operand& B, int M, int N, int K, double alpha, double beta, double* C,
+                    int64_t ldc, const Bufs& b, int splits, int* status, unsigned long long limit_ns,
+                    cudaStream_t s) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  cudaError_t e = prepare(A, B, b, s);
+  if (e != cudaSuccess) return e;
+  GemmParams p{};
+  p.A = b.Ablob;
+  p.B = b.Bblob;
+  p.eA = b.eA;
+  p.eB = b.eB;
+  p.M = M;
+  p.N = N;
+  p.nkb = std::max(1, (K + kDepth - 1) / kDepth);
+  p.kb_per_split = (p.nkb + splits - 1) / splits;
+  const int used = (p.nkb + p.kb_per_split - 1) / p.kb_per_split;
+  p.Phi = b.P;
+  p.sstride = (int64_t)M * N;
+  p.Plo = b.P + (size_t)used * p.sstride;
+  p.ldp = M;
+  p.status = status;
+  p.limit_ns = limit_ns;
+  e = gemm(p, used, s);
+  if (e != cudaSuccess) return e;
+  return reduce(p, used, alpha, beta, C, ldc, s);
+}
+
+cudaError_t rank_apply(int M, int N, int K, double alpha, double* C, int64_t ldc, int col0, int col1, int lower,
+                       const Bufs& b, int* status, unsigned long long limit_ns, cudaStream_t s) {
+  if (M <= 0 || N <= 0 || col1 <= col0) return cudaSuccess;
+  GemmParams p{};
+  p.A = b.Ablob;
+  p.B = b.Bblob;
+  p.eA = b.eA;
+  p.eB = b.eB;
+  p.M = M;
+  p.N = N;
+  p.nkb = std::max(1, (K + kDepth - 1) / kDepth);
+  p.kb_per_split = p.nkb;
+  p.C = C;
+  p.ldc = ldc;
+  p.col0 = col0;
+  p.col1 = col1;
+  p.lower = lower;
+  p.alpha = alpha;
+  p.status = status;
+  p.limit_ns = limit_ns;
+  return gemm(p, 1, s);
+}
+
+}  // namespace ozaki
+}  // namespace bandred
