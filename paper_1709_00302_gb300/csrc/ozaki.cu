@@ -28,7 +28,8 @@ namespace {
 
 constexpr int NT = 256;
 constexpr int S = kDigits;
-constexpr int kChunkBlocks = 4;  // 4 x 32 = 128 reduction steps per exact FP32 accumulation
+constexpr int kChunkBlocks = 128 / kDepth;  // 128 reduction steps per exact FP32 accumulation
+constexpr int kSlots = 4;                     // pipeline stages in shared memory
 
 __device__ __forceinline__ int biased_exp(double x) {
   return (int)(((uint32_t)__double2hiint(x) >> 20) & 0x7FFu);
@@ -41,18 +42,25 @@ __device__ __forceinline__ double elem(const double* M, int64_t ld, int mode, in
 }
 
 // ---------------------------------------------------------------- row exponents
-// entries M[r + k ld] (k in [k0, k1), k <= r when `lower`): one thread per row
-__global__ void rowexp_cols_kernel(const double* M, int64_t ld, int R, int k0, int k1, int lower, int* e) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= R) return;
-  const int per = (k1 - k0 + gridDim.y - 1) / gridDim.y;
-  const int kb = k0 + blockIdx.y * per, ke = min(k1, kb + per);
+// entries M[r + k ld]: one 32 x 32 tile per block (lanes along rows, eight warps of four
+// columns each), row maxima combined across the warps
+__global__ void rowexp_cols_kernel(const double* M, int64_t ld, int R, int K, int* e) {
+  __shared__ int rowmax[8][32];
+  const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + lane;
   int m = 0;
-  for (int k = kb; k < ke; ++k) {
-    if (lower && k > r) break;
-    m = max(m, biased_exp(M[r + (int64_t)k * ld]));
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int k = blockIdx.y * 32 + wy * 4 + q;
+    if (i < R && k < K) m = max(m, biased_exp(M[i + (int64_t)k * ld]));
   }
-  if (m) atomicMax(&e[r], m);
+  rowmax[wy][lane] = m;
+  __syncthreads();
+  if (wy == 0) {
+#pragma unroll
+    for (int q = 1; q < 8; ++q) m = max(m, rowmax[q][lane]);
+    if (m && i < R) atomicMax(&e[i], m);
+  }
 }
 
 // entries M[k + r ld] (k in [k0, k1), k > r when `upper`): one warp per row
@@ -68,6 +76,49 @@ __global__ void rowexp_rows_kernel(const double* M, int64_t ld, int R, int k0, i
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
   if (lane == 0 && m) atomicMax(&e[r], m);
+}
+
+// symmetric, lower triangle stored: one pass over the stored entries; each 32 x 32 tile
+// (i >= k) contributes its row maxima to e[i] and its column maxima to e[k] (= row k of
+// the symmetric matrix).  Block (tx, ty) = 32 x 8 threads per tile.
+__global__ void rowexp_sym_kernel(const double* M, int64_t ld, int R, int* e) {
+  const int ti = blockIdx.x, tk = blockIdx.y;
+  if (tk > ti) return;
+  __shared__ int colmax[8][32];
+  const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+  const int i = ti * 32 + lane;
+  int rmax = 0, cm[4] = {0, 0, 0, 0};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int k = tk * 32 + wy * 4 + q;
+    if (i < R && k < R && k <= i) {
+      const int v = biased_exp(M[i + (int64_t)k * ld]);
+      rmax = max(rmax, v);
+      cm[q] = v;
+    }
+  }
+  // row maxima: across the eight warps
+  __shared__ int rowmax[8][32];
+  rowmax[wy][lane] = rmax;
+  // column maxima: across the 32 lanes of each warp, for its four columns
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    int v = cm[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) colmax[wy][q] = v;
+  }
+  __syncthreads();
+  if (wy == 0) {
+    int m = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) m = max(m, rowmax[q][lane]);
+    if (m && i < R) atomicMax(&e[i], m);
+  } else if (wy == 1 && lane < 32) {
+    const int k = tk * 32 + lane;  // column lane = (warp lane / 4, q = lane % 4)
+    const int m = colmax[lane >> 2][lane & 3];
+    if (m && k < R) atomicMax(&e[k], m);
+  }
 }
 
 // ---------------------------------------------------------------- digits
@@ -139,7 +190,7 @@ struct Smem {
   static constexpr size_t a_block = S * a_plane;
   static constexpr size_t b_block = S * b_plane;
   static constexpr size_t stage = a_block + b_block;
-  static constexpr size_t off_bar = 2 * stage;
+  static constexpr size_t off_bar = kSlots * stage;
   static constexpr size_t total = off_bar + 128;
 };
 constexpr int kGemmThreads = NT + 32;  // eight drain/epilogue warps, one control warp
@@ -156,9 +207,9 @@ __device__ __forceinline__ double scale2(double v, int k) {
 
 __global__ void __launch_bounds__(kGemmThreads, 1) gemm_kernel(GemmParams p) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + Smem::off_bar);  // [2]
-  uint64_t* freed = full + 2;                                           // [2] MMAs of a stage done
-  uint64_t* acc_ready = freed + 2;                                      // chunk's MMAs done
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + Smem::off_bar);  // [kSlots]
+  uint64_t* freed = full + kSlots;                                      // [kSlots] MMAs of a stage done
+  uint64_t* acc_ready = freed + kSlots;                                 // chunk's MMAs done
   uint64_t* drained = acc_ready + 1;                                    // tensor memory read
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(drained + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -169,7 +220,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_kernel(GemmParams p) {
   if (p.C && (J * kTileB >= p.col1 || (J + 1) * kTileB <= p.col0)) return;
   const unsigned long long deadline = global_ns() + p.limit_ns;
   if (tid == 0) {
-    for (int q = 0; q < 2; ++q) {
+    for (int q = 0; q < kSlots; ++q) {
       tc::mbar_init(&full[q], 1);
       tc::mbar_init(&freed[q], 1);
     }
@@ -193,7 +244,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_kernel(GemmParams p) {
   if (warp == NT / 32) {
     if (lane == 0 && nst > 0) {
       auto issue = [&](int st) {
-        const int kb = kb0 + st, slot = st & 1;
+        const int kb = kb0 + st, slot = st % kSlots;
         unsigned char* dst = smem + slot * Smem::stage;
         tc::mbar_arrive_expect_tx(&full[slot], (uint32_t)Smem::stage);
         tc::bulk_g2s(dst, reinterpret_cast<const unsigned char*>(p.A) + ((size_t)I * p.nkb + kb) * Smem::a_block,
@@ -202,12 +253,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_kernel(GemmParams p) {
                      reinterpret_cast<const unsigned char*>(p.B) + ((size_t)J * p.nkb + kb) * Smem::b_block,
                      (uint32_t)Smem::b_block, &full[slot]);
       };
-      issue(0);
-      if (nst > 1) issue(1);
+      for (int q = 0; q < kSlots - 1 && q < nst; ++q) issue(q);
       constexpr uint32_t idesc = tc::idesc_bf16_f32(kTileA, kTileB);
       for (int st = 0; st < nst && !timed_out; ++st) {
-        const int slot = st & 1, chunk = st / kChunkBlocks;
-        if (!tc::mbar_wait(&full[slot], (uint32_t)(st >> 1) & 1u, deadline)) {
+        const int slot = st % kSlots, chunk = st / kChunkBlocks;
+        if (!tc::mbar_wait(&full[slot], (uint32_t)(st / kSlots) & 1u, deadline)) {
           timed_out = 1;
           break;
         }
@@ -239,19 +289,21 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_kernel(GemmParams p) {
         }
         tc::mma_commit(&freed[slot]);
         if (st % kChunkBlocks == kChunkBlocks - 1 || st == nst - 1) tc::mma_commit(acc_ready);
-        // refill the other slot (stage st - 1's) with stage st + 1 once its MMAs are done;
+        // refill stage st - 1's slot with stage st + kSlots - 1 once its MMAs are done;
         // stage st's MMAs are already queued behind them
-        if (st >= 1 && st + 1 < nst) {
-          if (!tc::mbar_wait(&freed[(st - 1) & 1], (uint32_t)((st - 1) >> 1) & 1u, deadline)) {
+        // (slot kSlots - 1 starts empty: stage kSlots - 1 goes there at st = 0)
+        if (st + kSlots - 1 < nst) {
+          if (st >= 1 &&
+              !tc::mbar_wait(&freed[(st - 1) % kSlots], (uint32_t)((st - 1) / kSlots) & 1u, deadline)) {
             timed_out = 1;
             break;
           }
-          issue(st + 1);
+          issue(st + kSlots - 1);
         }
       }
       if (timed_out) {
         const unsigned long long dl = global_ns() + p.limit_ns;
-        for (int q = 0; q < 2; ++q) {
+        for (int q = 0; q < kSlots; ++q) {
           tc::mbar_wait(&full[q], 0, dl);
           tc::mbar_wait(&freed[q], 0, dl);
         }
@@ -354,12 +406,17 @@ cudaError_t row_exponents(const Operand& op, int* e, cudaStream_t s) {
   auto one = [&](const double* M, int64_t ld, int mode, int K) -> cudaError_t {
     if (K <= 0 || !M) return cudaSuccess;
     const int ks = std::max(1, std::min(64, K / 256));
-    if (mode == 0 || mode == 2) {
-      rowexp_cols_kernel<<<dim3((op.R + 255) / 256, ks), 256, 0, s>>>(M, ld, op.R, 0, K, mode == 2, e);
+    if (mode == 2) {
+      const int T = (op.R + 31) / 32;
+      rowexp_sym_kernel<<<dim3(T, T), 256, 0, s>>>(M, ld, op.R, e);
       prof::count_launch();
     }
-    if (mode == 1 || mode == 2) {
-      rowexp_rows_kernel<<<dim3((op.R + 7) / 8, ks), 256, 0, s>>>(M, ld, op.R, 0, K, mode == 2, e);
+    if (mode == 0) {
+      rowexp_cols_kernel<<<dim3((op.R + 31) / 32, (K + 31) / 32), 256, 0, s>>>(M, ld, op.R, K, e);
+      prof::count_launch();
+    }
+    if (mode == 1) {
+      rowexp_rows_kernel<<<dim3((op.R + 7) / 8, ks), 256, 0, s>>>(M, ld, op.R, 0, K, 0, e);
       prof::count_launch();
     }
     return cudaGetLastError();

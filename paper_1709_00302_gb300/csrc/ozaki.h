@@ -16,7 +16,7 @@ namespace ozaki {
 constexpr int kDigits = 7;   // S: 56 bits of each row-scaled entry
 constexpr int kTileA = 128;  // rows of an A tile (TMEM lanes)
 constexpr int kTileB = 64;   // rows of a B tile (columns of C)
-constexpr int kDepth = 32;   // reduction depth of one packed block
+constexpr int kDepth = 16;   // reduction depth of one packed block (one pipeline stage)
 
 // An operand op(X) with rows r and reduction index k, possibly two matrices side by side
 // along k (k < K1 from M1, then M2).  mode: 0 = M[r + k ld], 1 = M[k + r ld], 2 = symmetric
