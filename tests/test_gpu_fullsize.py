@@ -1,7 +1,8 @@
 """Full-size parity: the benchmark's workloads in the benchmark's launch configuration.
 
-sy2sb n = 8192, w = b = 64 on the known-spectrum matrix (look-ahead auto, as bench.py
-times it): the oracle runs the whole reduction once on the host cores (about a minute),
+The batched workload (2000 uneven matrices) runs whole, with sampled matrices checked
+against the oracle.  sy2sb n = 8192, w = b = 64 on the known-spectrum matrix (look-ahead
+auto, as bench.py times it): the oracle runs the whole reduction once on the host cores (about a minute),
 and the FP64 and Ozaki GPU paths must match it elementwise.  The split (bf16x6) path must
 meet its stated backward error and the invariants of an orthogonal similarity: the band's
 Frobenius norm and trace equal those of A (sqrt(sum lam^2) and sum lam, known exactly).
@@ -128,3 +129,53 @@ def test_sy2sb_config4_invariants_on_device(br):
     print(f"\nn=32768: |dF|/F {abs(fb - fa) / fa:.2e}, |dtrace|/F {abs(tb - tr) / fa:.2e}")
     assert abs(fb - fa) <= SPLIT_TOL * fa and abs(tb - tr) <= SPLIT_TOL * fa
     assert torch.all(torch.isfinite(tau)).item()
+
+
+def test_batched_config5_sampled_against_oracle(br):
+    """The whole batched workload (1000 sy2sb n ~ U[64,1024] and 1000 ge2gb m ~ U[n,2n],
+    w in {16,32}, as bench.py runs it: both kinds planned, then run), with six matrices of
+    each kind (the largest, the smallest and four more) checked against the oracle: the
+    bf16x6 backward error, FP64 orthogonality, and the spectrum of the band."""
+    import torch
+
+    from checks import gen_band, gen_report, sym_band, sym_report
+
+    sym, gen = workloads.batched_mix(1000, 1000, seed=0)
+    mats_s = [workloads.batched_matrix("sym", q, (n,)) for q, (n, _) in enumerate(sym)]
+    mats_g = [workloads.batched_matrix("gen", q, (m, n)) for q, (m, n, _) in enumerate(gen)]
+    dS = [to_dev(a) for a in mats_s]
+    dG = [to_dev(a) for a in mats_g]
+    taus = [torch.zeros(max(n - w, 0), dtype=torch.float64, device="cuda") for n, w in sym]
+    tqs = [torch.zeros(n, dtype=torch.float64, device="cuda") for _, n, _ in gen]
+    tps = [torch.zeros(max(n - w, 0), dtype=torch.float64, device="cuda") for _, n, w in gen]
+    opts = br.make_opts(precision="bf16x6")
+    sb = br.SyBatch(dS, [w for _, w in sym], taus, opts)
+    gb = br.GeBatch(dG, [w for _, _, w in gen], tqs, tps, opts)
+    ws = torch.empty(sb.workspace(), dtype=torch.uint8, device="cuda")
+    wg = torch.empty(gb.workspace(), dtype=torch.uint8, device="cuda")
+    st = torch.zeros(2, dtype=torch.int32, device="cuda")
+    assert sb.plan(ws) == 0 and gb.plan(wg) == 0, br.bandred_last_error()
+    assert sb.run(ws, st[0:1]) == 0 and gb.run(wg, st[1:2]) == 0
+    torch.cuda.synchronize()
+    assert int(st.sum().item()) == 0
+    pick = lambda sizes: sorted({int(np.argmax(sizes)), int(np.argmax([0] + sizes[1:])), int(np.argmin(sizes)), 1, 250,
+                                 500, 999})
+    # ||Q^T Q - I||_F of a product of Householder reflectors grows like m u; these reach m = 2048
+    orth_tol = lambda m: max(1e-13, m * 1.2e-16)
+    for q in pick([n for n, _ in sym]):
+        (n, w), A = sym[q], mats_s[q]
+        Aout, tau = to_host(dS[q]), taus[q].cpu().numpy()
+        r = sym_report(A, Aout, tau, w)
+        assert r["backward"] <= SPLIT_TOL and r["orth"] <= orth_tol(n), (q, n, w, r)
+        Ao, _ = oracle.sy2sb(A, w)
+        lg, lo = np.linalg.eigvalsh(sym_band(Aout, w)), np.linalg.eigvalsh(sym_band(Ao, w))
+        assert np.max(np.abs(lg - lo)) <= 2e-5 * np.linalg.norm(A, 2), (q, n, w)
+    for q in pick([n for _, n, _ in gen]):
+        (m, n, w), A = gen[q], mats_g[q]
+        Aout = to_host(dG[q])
+        r = gen_report(A, Aout, tqs[q].cpu().numpy(), tps[q].cpu().numpy(), w)
+        assert r["backward"] <= SPLIT_TOL and r["orth_u"] <= orth_tol(m) and r["orth_v"] <= orth_tol(n), (q, m, n, w, r)
+        Ao, _, _ = oracle.ge2gb(A, w)
+        sg = np.linalg.svd(gen_band(Aout, w), compute_uv=False)
+        so = np.linalg.svd(gen_band(Ao, w), compute_uv=False)
+        assert np.max(np.abs(sg - so)) <= 2e-5 * so[0], (q, m, n, w)
