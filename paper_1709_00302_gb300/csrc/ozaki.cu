@@ -270,21 +270,19 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_kernel(GemmParams p) {
         tc::fence_after_sync();
         const uint32_t abase = tc::smem_u32(smem + slot * Smem::stage);
         const uint32_t bbase = abase + (uint32_t)Smem::a_block;
-#pragma unroll 1
-        for (int kk = 0; kk < kDepth / 16; ++kk) {
-#pragma unroll 1
-          for (int s = 0; s < S; ++s) {
-#pragma unroll 1
-            for (int t = 0; s + t < S; ++t) {
-              const int D = s + t;
-              const uint64_t ad = tc::smem_desc(abase + s * (uint32_t)Smem::a_plane + kk * 2 * (kTileA / 8) * 128,
-                                                (kTileA / 8) * 128, 128);
-              const uint64_t bd = tc::smem_desc(bbase + t * (uint32_t)Smem::b_plane + kk * 2 * (kTileB / 8) * 128,
-                                                (kTileB / 8) * 128, 128);
-              // the chunk's first product of diagonal D (s = 0, t = D) starts its accumulator
-              const bool first = (st % kChunkBlocks == 0) && kk == 0 && s == 0;
-              tc::mma_bf16(tmem + (uint32_t)(D * kTileB), ad, bd, idesc, first ? 0u : 1u);
-            }
+        // descriptors of plane 0; plane s starts s * plane bytes later, which adds
+        // (s * plane) >> 4 to the address field (shared addresses stay below 2^18)
+        const uint64_t ad0 = tc::smem_desc(abase, (kTileA / 8) * 128, 128);
+        const uint64_t bd0 = tc::smem_desc(bbase, (kTileB / 8) * 128, 128);
+        static_assert(kDepth == 16, "one MMA depth per stage");
+        const uint32_t fresh = (st % kChunkBlocks == 0) ? 0u : 1u;
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+#pragma unroll
+          for (int t = 0; s + t < S; ++t) {
+            // the chunk's first product of diagonal s + t (s = 0) starts its accumulator
+            tc::mma_bf16(tmem + (uint32_t)((s + t) * kTileB), ad0 + (uint64_t)((s * Smem::a_plane) >> 4),
+                         bd0 + (uint64_t)((t * Smem::b_plane) >> 4), idesc, s == 0 ? fresh : 1u);
           }
         }
         tc::mma_commit(&freed[slot]);
