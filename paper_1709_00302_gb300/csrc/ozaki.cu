@@ -172,11 +172,12 @@ __global__ void pack_kernel(Operand op, const int* e, int TR, int nrb, int nkb, 
         x = k < op.K1 ? elem(op.M1, op.ld1, op.mode1, row, k) : elem(op.M2, op.ld2, op.mode2, row, k - op.K1);
       digits(x, E, d[kk]);
     }
-    const size_t plane = (size_t)TR * kDepth;
+    // the block's S planes stacked along the rows: one S TR x kDepth K-major operand, so
+    // that consecutive planes form one wider MMA operand
+    __nv_bfloat16* base = out + (size_t)tile * S * TR * kDepth;
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-      __nv_bfloat16* base = out + ((size_t)tile * S + s) * plane;
-      uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<char*>(base) + tc::kmajor_offset(r, kg * 8, TR));
+      uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<char*>(base) + tc::kmajor_offset(s * TR + r, kg * 8, S * TR));
       *dst = make_uint4(bf16_pair(d[0][s], d[1][s]), bf16_pair(d[2][s], d[3][s]), bf16_pair(d[4][s], d[5][s]),
                         bf16_pair(d[6][s], d[7][s]));
     }
@@ -203,6 +204,113 @@ __device__ __forceinline__ double pow2(int k) {  // 2^k for -1022 <= k <= 1023
 __device__ __forceinline__ double scale2(double v, int k) {
   const int k1 = max(-1022, min(1023, k / 2));
   return v * pow2(k1) * pow2(max(-1022, min(1023, k - k1)));
+}
+
+// (thi 2^32 + tlo) 2^(k - 64) rounded to nearest even, from integer operations only (a
+// 128-bit magnitude normalised to a 64-bit window plus a sticky bit), so that the epilogue
+// spends a single FP64 instruction per entry of C on this FP64-poor part.  False when the
+// result is not a normal number (the caller then takes the FP64 route).
+__device__ __forceinline__ bool fixed_to_f64(long long thi, long long tlo, int k, double& v) {
+  const long long h = thi + (tlo >> 32);  // T = h 2^32 + l, 0 <= l < 2^32, |h| < 2^45
+  const unsigned long long l = (unsigned long long)tlo & 0xFFFFFFFFull;
+  const unsigned long long neg = h < 0 ? 1ull : 0ull;
+  unsigned long long H = (unsigned long long)h, L = l;
+  if (neg) {  // |T| = (-h - 1) 2^32 + (2^32 - l), or -h 2^32 when l = 0
+    H = l ? ~(unsigned long long)h : (unsigned long long)(-h);
+    L = l ? (1ull << 32) - l : 0ull;
+  }
+  if ((H | L) == 0) {
+    v = 0.0;
+    return true;
+  }
+  unsigned long long W, sticky = 0;
+  int nb;  // bit length of |T|
+  if (H >> 32) {
+    nb = 96 - __clzll((long long)H);
+    const int r = nb - 64;  // 1 .. 13
+    W = (H << (32 - r)) | (L >> r);
+    sticky = L & ((1ull << r) - 1);
+  } else {
+    const unsigned long long X = (H << 32) | L;
+    nb = 64 - __clzll((long long)X);
+    W = X << (64 - nb);
+  }
+  unsigned long long m = W >> 11;  // 53 bits, leading bit set
+  const bool round_bit = (W >> 10) & 1ull, below = (W & 0x3FFull) | sticky;
+  if (round_bit && (below || (m & 1ull))) ++m;
+  if (m >> 53) {
+    m >>= 1;
+    ++nb;
+  }
+  const int e = nb - 1 + k - 64 + 1023;
+  if (e < 1 || e > 2046) return false;
+  v = __longlong_as_double((long long)((neg << 63) | ((unsigned long long)e << 52) | (m & 0xFFFFFFFFFFFFFull)));
+  return true;
+}
+
+// C(row, col) += alpha (thi 2^-32 + tlo 2^-64) 2^(e_row + e_col - 2042) for the 32 columns
+// col0 .. col0 + 31 of one row held by a thread, restricted to [p.col0, p.col1) (and
+// col <= row when p.lower).  Loads of C and of the column exponents go out four columns at
+// a time ahead of the stores, so a tile pays eight memory round trips instead of 32.
+constexpr int kEpiGroup = 4;
+// Pulls the row's entries of C that add_row_products will update into L2 while the
+// tile's MMAs are still running.
+__device__ __forceinline__ void prefetch_row(const GemmParams& p, int row, int col0) {
+  const double* crow = p.C + row;
+#pragma unroll 4
+  for (int c = 0; c < 32; ++c) {
+    const int col = col0 + c;
+    if (col < p.N && col >= p.col0 && col < p.col1 && (!p.lower || row >= col))
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(crow + (int64_t)col * p.ldc));
+  }
+}
+__device__ __forceinline__ void add_row_products(const GemmParams& p, int row, int col0, const long long (&thi)[32],
+                                                 const long long (&tlo)[32]) {
+  const int ei = p.eA[row];
+  double* crow = p.C + row;
+#pragma unroll
+  for (int g = 0; g < 32; g += kEpiGroup) {
+    double cv[kEpiGroup];
+    int ej[kEpiGroup];
+#pragma unroll
+    for (int c = 0; c < kEpiGroup; ++c) {
+      const int col = col0 + g + c;
+      const bool ok = col < p.N && col >= p.col0 && col < p.col1 && (!p.lower || row >= col);
+      cv[c] = ok ? crow[(int64_t)col * p.ldc] : 0.0;
+      ej[c] = ok ? p.eB[col] : -1;
+    }
+#pragma unroll
+    for (int c = 0; c < kEpiGroup; ++c) {
+      if (ej[c] < 0) continue;
+      const int k = (ei - 1021) + (ej[c] - 1021);
+      double v;
+      if (!fixed_to_f64(thi[g + c], tlo[g + c], k, v))
+        v = scale2(fma((double)thi[g + c], 0x1p-32, (double)tlo[g + c] * 0x1p-64), k);
+      crow[(int64_t)(col0 + g + c) * p.ldc] = fma(p.alpha, v, cv[c]);
+    }
+  }
+}
+
+// All digit products of one stage: A_s times the stacked planes B_t0 .. B_t0+nt-1 (N = nt x
+// kTileB <= 256) in one MMA into diagonals s + t0 .., since diagonal D sits at tensor-memory
+// columns D kTileB and plane t of B at rows t kTileB of the stacked operand.  10 MMAs
+// instead of 28 single-plane ones, each reading its A plane once.  s = 0 covers every
+// diagonal first, so `fresh` (0 at a chunk's first stage) there restarts the accumulators.
+__device__ __forceinline__ void digit_products(uint32_t tmem, uint64_t ad0, uint64_t bd0, uint32_t fresh) {
+  constexpr uint64_t a_step = ((kTileA / 8) * 128) >> 4, b_step = ((kTileB / 8) * 128) >> 4;
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+#pragma unroll
+    for (int t0 = 0; t0 < S - s; t0 += 4) {
+      const int nt = (S - s - t0) < 4 ? (S - s - t0) : 4;
+      const uint32_t idesc = nt == 4   ? tc::idesc_bf16_f32(kTileA, 4 * kTileB)
+                             : nt == 3 ? tc::idesc_bf16_f32(kTileA, 3 * kTileB)
+                             : nt == 2 ? tc::idesc_bf16_f32(kTileA, 2 * kTileB)
+                                       : tc::idesc_bf16_f32(kTileA, kTileB);
+      tc::mma_bf16(tmem + (uint32_t)((s + t0) * kTileB), ad0 + (uint64_t)s * a_step, bd0 + (uint64_t)t0 * b_step,
+                   idesc, s == 0 ? fresh : 1u);
+    }
+  }
 }
 
 __global__ void __launch_bounds__(kGemmThreads, 1) gemm_kernel(GemmParams p) {
@@ -254,7 +362,6 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_kernel(GemmParams p) {
                      (uint32_t)Smem::b_block, &full[slot]);
       };
       for (int q = 0; q < kSlots - 1 && q < nst; ++q) issue(q);
-      constexpr uint32_t idesc = tc::idesc_bf16_f32(kTileA, kTileB);
       for (int st = 0; st < nst && !timed_out; ++st) {
         const int slot = st % kSlots, chunk = st / kChunkBlocks;
         if (!tc::mbar_wait(&full[slot], (uint32_t)(st / kSlots) & 1u, deadline)) {
@@ -270,21 +377,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_kernel(GemmParams p) {
         tc::fence_after_sync();
         const uint32_t abase = tc::smem_u32(smem + slot * Smem::stage);
         const uint32_t bbase = abase + (uint32_t)Smem::a_block;
-        // descriptors of plane 0; plane s starts s * plane bytes later, which adds
-        // (s * plane) >> 4 to the address field (shared addresses stay below 2^18)
-        const uint64_t ad0 = tc::smem_desc(abase, (kTileA / 8) * 128, 128);
-        const uint64_t bd0 = tc::smem_desc(bbase, (kTileB / 8) * 128, 128);
+        // descriptors of plane 0 of the stacked operands; plane s starts s (TR / 8) 128 bytes
+        // later, which adds that >> 4 to the address field (shared addresses stay below 2^18)
+        const uint64_t ad0 = tc::smem_desc(abase, (S * kTileA / 8) * 128, 128);
+        const uint64_t bd0 = tc::smem_desc(bbase, (S * kTileB / 8) * 128, 128);
         static_assert(kDepth == 16, "one MMA depth per stage");
-        const uint32_t fresh = (st % kChunkBlocks == 0) ? 0u : 1u;
-#pragma unroll
-        for (int s = 0; s < S; ++s) {
-#pragma unroll
-          for (int t = 0; s + t < S; ++t) {
-            // the chunk's first product of diagonal s + t (s = 0) starts its accumulator
-            tc::mma_bf16(tmem + (uint32_t)((s + t) * kTileB), ad0 + (uint64_t)((s * Smem::a_plane) >> 4),
-                         bd0 + (uint64_t)((t * Smem::b_plane) >> 4), idesc, s == 0 ? fresh : 1u);
-          }
-        }
+        digit_products(tmem, ad0, bd0, (st % kChunkBlocks == 0) ? 0u : 1u);
         tc::mma_commit(&freed[slot]);
         if (st % kChunkBlocks == kChunkBlocks - 1 || st == nst - 1) tc::mma_commit(acc_ready);
         // refill stage st - 1's slot with stage st + kSlots - 1 once its MMAs are done;
@@ -311,6 +409,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_kernel(GemmParams p) {
     // drain warps: lane quadrant warp & 3, columns 32 (warp >> 2) .. + 31
     const uint32_t q = warp & 3, h = warp >> 2;
     const int nchunks = (nst + kChunkBlocks - 1) / kChunkBlocks;
+    if (!p.Phi && I * kTileA + (int)(q * 32) + lane < p.M) prefetch_row(p, I * kTileA + q * 32 + lane, J * kTileB + h * 32);
     for (int c = 0; c < nchunks; ++c) {
       if (!tc::mbar_wait(acc_ready, (uint32_t)c & 1u, deadline)) {
         timed_out = 1;
@@ -355,19 +454,159 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_kernel(GemmParams p) {
           }
         }
       } else {
-        const int ei = p.eA[row];
-#pragma unroll
-        for (int c = 0; c < 32; ++c) {
-          const int col = J * kTileB + h * 32 + c;
-          if (col < p.N && col >= p.col0 && col < p.col1 && (!p.lower || row >= col)) {
-            const double v = fma((double)thi[c], 0x1p-32, (double)tlo[c] * 0x1p-64);
-            double* cp = p.C + row + (int64_t)col * p.ldc;
-            *cp = fma(p.alpha, scale2(v, (ei - 1021) + (p.eB[col] - 1021)), *cp);
-          }
-        }
+        add_row_products(p, row, J * kTileB + h * 32, thi, tlo);
       }
     }
   }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+// Persistent form of the direct mode (C += alpha A B^T, the rank-2k updates): one CTA per
+// SM walks its tiles (every gridDim.x-th tile of the lower triangle / column range) with one
+// continuous copy and MMA pipeline, so a tile's epilogue (reading and writing C) runs
+// while the next tile's MMAs do; only the read-out of tensor memory stalls the MMAs.
+constexpr int kMaxTilesPerCta = 1024;
+
+__global__ void __launch_bounds__(kGemmThreads, 1) rank_kernel(GemmParams p) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + Smem::off_bar);
+  uint64_t* freed = full + kSlots;
+  uint64_t* acc_ready = freed + kSlots;
+  uint64_t* drained = acc_ready + 1;
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(drained + 1);
+  int* tiles = reinterpret_cast<int*>(smem + Smem::total);  // this CTA's tiles
+  __shared__ int s_nt;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nI = (p.M + kTileA - 1) / kTileA, nJ = (p.N + kTileB - 1) / kTileB;
+  const int nkb = p.nkb, cpt = (nkb + kChunkBlocks - 1) / kChunkBlocks;
+  const unsigned long long deadline = global_ns() + p.limit_ns;
+  if (tid == 0) {
+    int n = 0;
+    for (int L = blockIdx.x; L < nI * nJ && n < kMaxTilesPerCta; L += gridDim.x) {
+      const int I = L % nI, J = L / nI;
+      if (p.lower && (I + 1) * kTileA <= J * kTileB) continue;
+      if (J * kTileB >= p.col1 || (J + 1) * kTileB <= p.col0) continue;
+      tiles[n++] = L;
+    }
+    s_nt = n;
+    for (int q = 0; q < kSlots; ++q) {
+      tc::mbar_init(&full[q], 1);
+      tc::mbar_init(&freed[q], 1);
+    }
+    tc::mbar_init(acc_ready, 1);
+    tc::mbar_init(drained, NT / 32);
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(tmem_holder, kTmemCols);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_holder;
+  const int nt = s_nt;
+  const int total = nt * nkb;
+  int timed_out = 0;
+
+  if (warp == NT / 32) {
+    if (lane == 0 && total > 0) {
+      auto issue = [&](int qs) {
+        const int L = tiles[qs / nkb], kb = qs % nkb, slot = qs % kSlots;
+        const int I = L % nI, J = L / nI;
+        unsigned char* dst = smem + slot * Smem::stage;
+        tc::mbar_arrive_expect_tx(&full[slot], (uint32_t)Smem::stage);
+        tc::bulk_g2s(dst, reinterpret_cast<const unsigned char*>(p.A) + ((size_t)I * nkb + kb) * Smem::a_block,
+                     (uint32_t)Smem::a_block, &full[slot]);
+        tc::bulk_g2s(dst + Smem::a_block,
+                     reinterpret_cast<const unsigned char*>(p.B) + ((size_t)J * nkb + kb) * Smem::b_block,
+                     (uint32_t)Smem::b_block, &full[slot]);
+      };
+      for (int q = 0; q < kSlots - 1 && q < total; ++q) issue(q);
+      for (int q = 0; q < total && !timed_out; ++q) {
+        const int slot = q % kSlots, kb = q % nkb;
+        const int gc = (q / nkb) * cpt + kb / kChunkBlocks;  // chunk index across tiles
+        if (!tc::mbar_wait(&full[slot], (uint32_t)(q / kSlots) & 1u, deadline)) {
+          timed_out = 1;
+          break;
+        }
+        if (kb % kChunkBlocks == 0 && gc > 0 && !tc::mbar_wait(drained, (uint32_t)(gc - 1) & 1u, deadline)) {
+          timed_out = 1;
+          break;
+        }
+        tc::fence_after_sync();
+        const uint32_t abase = tc::smem_u32(smem + slot * Smem::stage);
+        const uint64_t ad0 = tc::smem_desc(abase, (S * kTileA / 8) * 128, 128);
+        const uint64_t bd0 = tc::smem_desc(abase + (uint32_t)Smem::a_block, (S * kTileB / 8) * 128, 128);
+        digit_products(tmem, ad0, bd0, (kb % kChunkBlocks == 0) ? 0u : 1u);
+        tc::mma_commit(&freed[slot]);
+        if (kb % kChunkBlocks == kChunkBlocks - 1 || kb == nkb - 1) tc::mma_commit(acc_ready);
+        if (q + kSlots - 1 < total) {
+          if (q >= 1 && !tc::mbar_wait(&freed[(q - 1) % kSlots], (uint32_t)((q - 1) / kSlots) & 1u, deadline)) {
+            timed_out = 1;
+            break;
+          }
+          issue(q + kSlots - 1);
+        }
+      }
+      if (timed_out) {
+        const unsigned long long dl = global_ns() + p.limit_ns;
+        for (int q = 0; q < kSlots; ++q) {
+          tc::mbar_wait(&full[q], 0, dl);
+          tc::mbar_wait(&freed[q], 0, dl);
+        }
+      }
+    }
+  } else {
+    const uint32_t qd = warp & 3, h = warp >> 2;
+    for (int lt = 0; lt < nt && !timed_out; ++lt) {
+      {
+        const int L = tiles[lt], row = (L % nI) * kTileA + qd * 32 + lane;
+        if (row < p.M) prefetch_row(p, row, (L / nI) * kTileB + h * 32);
+      }
+      long long thi[32], tlo[32];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) thi[c] = tlo[c] = 0;
+      for (int c = 0; c < cpt; ++c) {
+        const int gc = lt * cpt + c;
+        if (!tc::mbar_wait(acc_ready, (uint32_t)gc & 1u, deadline)) {
+          timed_out = 1;
+          break;
+        }
+        tc::fence_after_sync();
+#pragma unroll 1
+        for (int D = 0; D < S; ++D) {
+          float v[32];
+          tc::tmem_ld32(tmem + ((qd * 32) << 16) + (uint32_t)(D * kTileB + h * 32), v);
+          const int shift = D <= 2 ? 8 * (2 - D) : 8 * (6 - D);
+#pragma unroll
+          for (int cc = 0; cc < 32; ++cc) {
+            const long long iv = (long long)__float2int_rn(v[cc]) << shift;
+            if (D <= 2)
+              thi[cc] += iv;
+            else
+              tlo[cc] += iv;
+          }
+        }
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(drained);
+      }
+      if (timed_out) break;
+      // epilogue of this tile while the next tile's MMAs run
+      const int L = tiles[lt], I = L % nI, J = L / nI;
+      const int row = I * kTileA + qd * 32 + lane;
+      if (row < p.M) {
+        add_row_products(p, row, J * kTileB + h * 32, thi, tlo);
+      }
+    }
+  }
+  if (__syncthreads_or(timed_out) && tid == 0 && p.status) atomicCAS(p.status, 0, BANDRED_DEV_TIMEOUT);
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) {
@@ -564,7 +803,29 @@ cudaError_t rank_apply(int M, int N, int K, double alpha, double* C, int64_t ldc
   p.alpha = alpha;
   p.status = status;
   p.limit_ns = limit_ns;
-  return gemm(p, 1, s);
+  static int configured = -1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  constexpr size_t smem = Smem::total + sizeof(int) * kMaxTilesPerCta;
+  if (configured != dev) {
+    cudaError_t e = cudaFuncSetAttribute(rank_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = dev;
+  }
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // tiles that hold part of the update: columns in [col0, col1), rows reaching the diagonal
+  const int nI = (M + kTileA - 1) / kTileA, nJ = (N + kTileB - 1) / kTileB;
+  int64_t valid = 0;
+  for (int J = col0 / kTileB; J < nJ && J * kTileB < col1; ++J)
+    valid += lower ? std::max(0, nI - (J * kTileB) / kTileA) : nI;
+  if (valid == 0) return cudaSuccess;
+  const int64_t all = (int64_t)nI * nJ;
+  const int grid =
+      (int)std::max<int64_t>(std::min<int64_t>(sms, valid), (all + kMaxTilesPerCta - 1) / kMaxTilesPerCta);
+  rank_kernel<<<grid, kGemmThreads, smem, s>>>(p);
+  prof::count_launch();
+  return cudaGetLastError();
 }
 
 }  // namespace ozaki

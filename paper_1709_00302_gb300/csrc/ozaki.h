@@ -35,8 +35,9 @@ struct Operand {
 cudaError_t row_exponents(const Operand& op, int* e, cudaStream_t s);
 
 // Digits of op, rows scaled by 2^-(e_r - 1021), into blocks of TR rows x kDepth (TR = kTileA
-// for the left operand, kTileB for the right one): block (rb, kb) holds kDigits planes of
-// TR x kDepth bf16 in the canonical K-major layout of tcgen05 operands.
+// for the left operand, kTileB for the right one): block (rb, kb) holds the kDigits planes
+// stacked along the rows, one (kDigits TR) x kDepth bf16 operand in the canonical K-major
+// layout of tcgen05 (plane s = rows s TR .. s TR + TR - 1).
 size_t packed_bytes(int R, int K, int TR);
 cudaError_t pack(const Operand& op, const int* e, int TR, __nv_bfloat16* out, cudaStream_t s);
 
