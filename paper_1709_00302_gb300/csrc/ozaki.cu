@@ -15,10 +15,13 @@
 #include <algorithm>
 #include <cstring>
 
+#include <cuda.h>  // CUtensorMap (type only)
+
 #include "bandred.h"
 #include "common.cuh"
 #include "ozaki.h"
 #include "prof.h"
+#include "split.h"
 #include "tc.cuh"
 
 namespace bandred {
@@ -615,6 +618,252 @@ __global__ void __launch_bounds__(kGemmThreads, 1) rank_kernel(GemmParams p) {
   }
 }
 
+// ---------------------------------------------------------------- streamed left operand
+// C_partial = op(A) B^T with op(A) read as FP64 by the TMA (plain, transposed, or
+// symmetric with the lower triangle stored) and cut into digits in shared memory by the
+// worker warps, so the left operand is read once and never written back as digits.  A
+// stage is one 128 x 16 FP64 box (or, above the diagonal of a symmetric A, one 16 x 128
+// box of the mirror, 128-byte swizzled) plus the packed digits of B (N <= kTileB), in a
+// ring of four; the digits of A are double-buffered.  Tiles across the diagonal take the
+// lower box and fetch their upper entries from the mirror directly.  Sixteen worker warps
+// convert and drain (16 columns each), one control warp moves data and issues the MMAs.
+struct StreamSmem {
+  static constexpr int NS = 4;
+  static constexpr size_t tile = (size_t)kTileA * kDepth * 8;
+  static constexpr size_t off_b = NS * tile;
+  static constexpr size_t off_a = off_b + NS * Smem::b_block;
+  static constexpr size_t off_bar = off_a + 2 * Smem::a_block;
+  static constexpr size_t total = off_bar + 128 + 1024;  // + alignment of the base to 1024
+};
+constexpr int kStreamWorkers = 16;
+constexpr int kStreamThreads = kStreamWorkers * 32 + 32;
+
+struct StreamParams {
+  const double* A;  // op(A)(r, k): mode 0 A[r + k lda], 1 A[k + r lda], 2 symmetric (lower stored)
+  int64_t lda;
+  int mode;
+  int M, K, N;
+  const int* eA;           // row exponents of op(A)
+  const __nv_bfloat16* B;  // digits of B, packed with TR = kTileB (one row block)
+  int nkb, kb_per_split;
+  int64_t* Phi;
+  int64_t* Plo;
+  int64_t ldp, sstride;
+  int* status;
+  unsigned long long limit_ns;
+};
+
+__global__ void __launch_bounds__(kStreamThreads, 1)
+    stream_kernel(StreamParams p, const __grid_constant__ CUtensorMap tm_lo, const __grid_constant__ CUtensorMap tm_up) {
+  using L = StreamSmem;
+  constexpr int NS = L::NS;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
+  double* ring = reinterpret_cast<double*>(smem);
+  unsigned char* bring = smem + L::off_b;
+  unsigned char* adig = smem + L::off_a;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::off_bar);  // [NS] copies landed
+  uint64_t* converted = full + NS;                                    // [2] digits of A written
+  uint64_t* mma_done = converted + 2;                                 // [2] MMAs of a stage done
+  uint64_t* acc_ready = mma_done + 2;                                 // MMAs of a chunk done
+  uint64_t* drained = acc_ready + 1;                                  // tensor memory read
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(drained + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int i0 = blockIdx.x * kTileA, z = blockIdx.y;
+  const int kb0 = z * p.kb_per_split, kb1 = min(p.nkb, kb0 + p.kb_per_split);
+  const int nst = kb1 - kb0;
+  const unsigned long long deadline = global_ns() + p.limit_ns;
+  if (tid == 0) {
+    for (int q = 0; q < NS; ++q) tc::mbar_init(&full[q], 1);
+    for (int q = 0; q < 2; ++q) {
+      tc::mbar_init(&converted[q], kStreamWorkers);
+      tc::mbar_init(&mma_done[q], 1);
+    }
+    tc::mbar_init(acc_ready, 1);
+    tc::mbar_init(drained, kStreamWorkers);
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(tmem_holder, kTmemCols);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_holder;
+
+  // 0: box read in place; 1: box of the mirror (transposed); 2: symmetric box across the diagonal
+  auto kind_of = [&](int kb) -> int {
+    if (p.mode != 2) return p.mode;
+    const int k0 = kb * kDepth;
+    if (k0 + kDepth - 1 <= i0) return 0;
+    if (k0 >= i0 + kTileA) return 1;
+    return 2;
+  };
+  int timed_out = 0;
+  long long thi[16], tlo[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) thi[c] = tlo[c] = 0;
+
+  if (warp == kStreamWorkers) {
+    if (lane == 0 && nst > 0) {
+      tc::prefetch_tmap(&tm_lo);
+      tc::prefetch_tmap(&tm_up);
+      auto issue = [&](int ls) {
+        const int kb = kb0 + ls, slot = ls % NS, k0 = kb * kDepth;
+        double* dst = ring + (size_t)slot * kTileA * kDepth;
+        tc::mbar_arrive_expect_tx(&full[slot], (uint32_t)(L::tile + Smem::b_block));
+        if (kind_of(kb) == 1)
+          tc::tma_load_2d(dst, &tm_up, k0, i0, &full[slot]);
+        else
+          tc::tma_load_2d(dst, &tm_lo, i0, k0, &full[slot]);
+        tc::bulk_g2s(bring + (size_t)slot * Smem::b_block,
+                     reinterpret_cast<const unsigned char*>(p.B) + (size_t)kb * Smem::b_block,
+                     (uint32_t)Smem::b_block, &full[slot]);
+      };
+      int issued = 0;
+      for (; issued < NS - 1 && issued < nst; ++issued) issue(issued);
+      for (int st = 0; st < nst; ++st) {
+        const int sb = st & 1, chunk = st / kChunkBlocks;
+        if (!tc::mbar_wait(&converted[sb], (uint32_t)(st >> 1) & 1u, deadline)) {
+          timed_out = 1;
+          break;
+        }
+        // the chunk's first MMAs overwrite the accumulators: the previous chunk must be read
+        if (st % kChunkBlocks == 0 && chunk > 0 &&
+            !tc::mbar_wait(drained, (uint32_t)(chunk - 1) & 1u, deadline)) {
+          timed_out = 1;
+          break;
+        }
+        tc::fence_after_sync();
+        const uint32_t abase = tc::smem_u32(adig + (size_t)sb * Smem::a_block);
+        const uint32_t bbase = tc::smem_u32(bring + (size_t)(st % NS) * Smem::b_block);
+        digit_products(tmem, tc::smem_desc(abase, (S * kTileA / 8) * 128, 128),
+                       tc::smem_desc(bbase, (S * kTileB / 8) * 128, 128), (st % kChunkBlocks == 0) ? 0u : 1u);
+        tc::mma_commit(&mma_done[sb]);
+        if (st % kChunkBlocks == kChunkBlocks - 1 || st == nst - 1) tc::mma_commit(acc_ready);
+        // refill the slot of stage st - 1 (its box was converted, its B digits multiplied)
+        if (issued < nst) {
+          if (st >= 1 &&
+              !tc::mbar_wait(&mma_done[(st - 1) & 1], (uint32_t)((st - 1) >> 1) & 1u, deadline)) {
+            timed_out = 1;
+            break;
+          }
+          issue(issued++);
+        }
+      }
+      if (timed_out) {  // let copies and MMAs in flight land before the CTA leaves (bounded)
+        const unsigned long long dl = global_ns() + p.limit_ns;
+        for (int q = 0; q < NS; ++q) tc::mbar_wait(&full[q], 0, dl);
+        for (int q = 0; q < 2; ++q) tc::mbar_wait(&mma_done[q], 0, dl);
+      }
+    }
+  } else {
+    const int r = tid & (kTileA - 1), kq = tid >> 7;  // row r, k in [4 kq, 4 kq + 4) of a stage
+    const int gi = i0 + r;
+    const int E = gi < p.M ? p.eA[gi] : 0;
+    const uint32_t q = warp & 3, h = warp >> 2;  // tensor-memory lane quadrant, 16-column group
+    auto drain = [&](int c) -> bool {
+      if (!tc::mbar_wait(acc_ready, (uint32_t)c & 1u, deadline)) return false;
+      tc::fence_after_sync();
+#pragma unroll 1
+      for (int D = 0; D < S; ++D) {
+        float v[16];
+        tc::tmem_ld16(tmem + ((q * 32) << 16) + (uint32_t)(D * kTileB + h * 16), v);
+        const int shift = D <= 2 ? 8 * (2 - D) : 8 * (6 - D);
+#pragma unroll
+        for (int cc = 0; cc < 16; ++cc) {
+          const long long iv = (long long)__float2int_rn(v[cc]) << shift;
+          if (D <= 2)
+            thi[cc] += iv;
+          else
+            tlo[cc] += iv;
+        }
+      }
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(drained);
+      return true;
+    };
+    for (int st = 0; st < nst; ++st) {
+      const int sb = st & 1, slot = st % NS, kb = kb0 + st, k0 = kb * kDepth;
+      const int kind = kind_of(kb);
+      double x[4];
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) x[kk] = 0.0;
+      if (kind == 2) {  // upper entries of a diagonal box, from the stored mirror A(k, r)
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const int gk = k0 + 4 * kq + kk;
+          if (gi < gk && gk < p.K && gi < p.M) x[kk] = __ldg(p.A + gk + (int64_t)gi * p.lda);
+        }
+      }
+      if (!tc::mbar_wait(&full[slot], (uint32_t)(st / NS) & 1u, deadline) ||
+          (st >= 2 && !tc::mbar_wait(&mma_done[sb], (uint32_t)((st - 2) >> 1) & 1u, deadline))) {
+        timed_out = 1;
+        break;
+      }
+      const double* tile = ring + (size_t)slot * kTileA * kDepth;
+      if (kind == 1) {  // row r holds 16 entries in eight 16-byte chunks, chunk c at c ^ (r & 7)
+        const double* row = tile + r * kDepth;
+#pragma unroll
+        for (int c2 = 0; c2 < 2; ++c2) {
+          const double2 v = *reinterpret_cast<const double2*>(row + 2 * ((2 * kq + c2) ^ (r & 7)));
+          x[2 * c2] = v.x;
+          x[2 * c2 + 1] = v.y;
+        }
+      } else {
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const double v = tile[(4 * kq + kk) * kTileA + r];
+          if (kind == 0 || gi >= k0 + 4 * kq + kk) x[kk] = v;
+        }
+      }
+      int d[4][S];
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) digits(x[kk], E, d[kk]);
+      unsigned char* dst = adig + (size_t)sb * Smem::a_block;
+#pragma unroll
+      for (int s = 0; s < S; ++s)
+        *reinterpret_cast<uint2*>(dst + tc::kmajor_offset(s * kTileA + r, 4 * kq, S * kTileA)) =
+            make_uint2(bf16_pair(d[0][s], d[1][s]), bf16_pair(d[2][s], d[3][s]));
+      tc::fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&converted[sb]);
+      if (st % kChunkBlocks == 0 && st > 0 && !drain(st / kChunkBlocks - 1)) {
+        timed_out = 1;
+        break;
+      }
+    }
+    if (!timed_out && nst > 0 && !drain((nst - 1) / kChunkBlocks)) timed_out = 1;
+  }
+
+  if (__syncthreads_or(timed_out)) {
+    if (tid == 0 && p.status) atomicCAS(p.status, 0, BANDRED_DEV_TIMEOUT);
+  } else if (warp < kStreamWorkers) {
+    const int q = warp & 3, h = warp >> 2;
+    const int row = i0 + q * 32 + lane;
+    if (row < p.M) {
+      int64_t* Ph = p.Phi + (size_t)z * p.sstride;
+      int64_t* Pl = p.Plo + (size_t)z * p.sstride;
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const int col = h * 16 + c;
+        if (col < p.N) {
+          Ph[row + (int64_t)col * p.ldp] = thi[c];
+          Pl[row + (int64_t)col * p.ldp] = tlo[c];
+        }
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
 __global__ void reduce_kernel(const int64_t* Phi, const int64_t* Plo, int64_t ldp, int64_t sstride, int splits,
                               const int* eA, const int* eB, int M, int N, double alpha, double beta, double* C,
                               int64_t ldc) {
@@ -756,11 +1005,84 @@ cudaError_t prepare(const Operand& A, const Operand& B, const Bufs& b, cudaStrea
   return e;
 }
 
+namespace {
+
+// The streamed path: a single-source left operand whose base and columns are 16-byte
+// aligned (the TMA's rule), N <= kTileB.  False (nothing launched) when it does not apply.
+bool stream_product(const Operand& A, const Operand& B, int M, int N, int K, double alpha, double beta, double* C,
+                    int64_t ldc, const Bufs& b, int splits, int* status, unsigned long long limit_ns,
+                    cudaStream_t s, cudaError_t* err) {
+  if (A.M2 || A.K2 != 0 || N > kTileB || A.K1 != K || A.R != M) return false;
+  if ((reinterpret_cast<uintptr_t>(A.M1) & 15u) != 0 || (A.ld1 & 1) != 0) return false;
+  CUtensorMap lo, up;
+  const int mode = A.mode1;
+  if (mode == 0 || mode == 2) {
+    if (A.ld1 < M || !split::encode_tile_map_f64(&lo, A.M1, M, K, A.ld1, kTileA, kDepth, false)) return false;
+  }
+  if (mode == 1 || mode == 2) {
+    if (A.ld1 < K || !split::encode_tile_map_f64(&up, A.M1, K, M, A.ld1, kDepth, kTileA, true)) return false;
+  }
+  if (mode == 0) std::memcpy(&up, &lo, sizeof(CUtensorMap));
+  if (mode == 1) std::memcpy(&lo, &up, sizeof(CUtensorMap));
+  static int configured = -1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  auto run = [&]() -> cudaError_t {
+    if (configured != dev) {
+      cudaError_t e = cudaFuncSetAttribute(stream_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)StreamSmem::total);
+      if (e != cudaSuccess) return e;
+      configured = dev;
+    }
+    cudaError_t e = row_exponents(A, b.eA, s);
+    if (e != cudaSuccess) return e;
+    if ((e = row_exponents(B, b.eB, s)) != cudaSuccess) return e;
+    if ((e = pack(B, b.eB, kTileB, b.Bblob, s)) != cudaSuccess) return e;
+    StreamParams sp{};
+    sp.A = A.M1;
+    sp.lda = A.ld1;
+    sp.mode = mode;
+    sp.M = M;
+    sp.K = K;
+    sp.N = N;
+    sp.eA = b.eA;
+    sp.B = b.Bblob;
+    sp.nkb = std::max(1, (K + kDepth - 1) / kDepth);
+    sp.kb_per_split = (sp.nkb + splits - 1) / splits;
+    const int used = (sp.nkb + sp.kb_per_split - 1) / sp.kb_per_split;
+    sp.Phi = b.P;
+    sp.sstride = (int64_t)M * N;
+    sp.Plo = b.P + (size_t)used * sp.sstride;
+    sp.ldp = M;
+    sp.status = status;
+    sp.limit_ns = limit_ns;
+    stream_kernel<<<dim3((M + kTileA - 1) / kTileA, used), kStreamThreads, StreamSmem::total, s>>>(sp, lo, up);
+    prof::count_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    GemmParams gp{};
+    gp.Phi = sp.Phi;
+    gp.Plo = sp.Plo;
+    gp.ldp = sp.ldp;
+    gp.sstride = sp.sstride;
+    gp.eA = b.eA;
+    gp.eB = b.eB;
+    gp.M = M;
+    gp.N = N;
+    return reduce(gp, used, alpha, beta, C, ldc, s);
+  };
+  *err = run();
+  return true;
+}
+
+}  // namespace
+
 cudaError_t product(const Operand& A, const Operand& B, int M, int N, int K, double alpha, double beta, double* C,
                     int64_t ldc, const Bufs& b, int splits, int* status, unsigned long long limit_ns,
                     cudaStream_t s) {
   if (M <= 0 || N <= 0) return cudaSuccess;
-  cudaError_t e = prepare(A, B, b, s);
+  cudaError_t e = cudaSuccess;
+  if (K > 0 && stream_product(A, B, M, N, K, alpha, beta, C, ldc, b, splits, status, limit_ns, s, &e)) return e;
+  e = prepare(A, B, b, s);
   if (e != cudaSuccess) return e;
   GemmParams p{};
   p.A = b.Ablob;

@@ -866,6 +866,11 @@ cudaError_t launch_rank(const RankParams& p, const RankParams* probs, dim3 grid,
 }  // namespace
 
 // ================================================================= host API
+bool encode_tile_map_f64(CUtensorMap* m, const double* base, int64_t rows, int64_t cols, int64_t ld, uint32_t box0,
+                         uint32_t box1, bool swz) {
+  return encode_f64(m, base, rows, cols, ld, box0, box1, swz);
+}
+
 int slices_of(int precision) { return precision == BANDRED_BF16X3 ? 2 : 3; }
 
 size_t packed_bytes(int R, int K, int TR, int TK, int S) {

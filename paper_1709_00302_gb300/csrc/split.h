@@ -2,11 +2,19 @@
 #pragma once
 #include <cstddef>
 #include <cstdint>
+#include <cuda.h>  // CUtensorMap (type only)
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 namespace bandred {
 namespace split {
+
+// TMA descriptor of an FP64 column-major rows x cols matrix (leading dimension ld) read in
+// boxes of box0 (along the rows) x box1, 128-byte swizzled when `swz`; false when the
+// driver's encoder is unavailable or rejects the layout (the caller then takes a path
+// without TMA).
+bool encode_tile_map_f64(CUtensorMap* m, const double* base, int64_t rows, int64_t cols, int64_t ld, uint32_t box0,
+                         uint32_t box1, bool swz);
 
 // Streamed operand access modes: element (i, k) of A is
 //   kModePlain     A[i + k * lda]
