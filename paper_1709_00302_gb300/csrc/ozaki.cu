@@ -125,8 +125,16 @@ __global__ void rowexp_sym_kernel(const double* M, int64_t ld, int R, int* e) {
 }
 
 // ---------------------------------------------------------------- digits
-// x -> 7 balanced digits (most significant first), row exponent E.
-__device__ __forceinline__ void digits(double x, int E, int (&d)[S]) {
+// x -> its 7 balanced digits (most significant first) as FP32 values, row exponent E.
+// F = round(x 2^(56 - (E - 1021))) is a 56-bit integer, |F| < 2^55.  Adding
+// C = 0x808080808080 (128 in each of the six low byte positions) leaves bytes g_1 .. g_6
+// of G = F + C with d_s = g_s - 128 in [-128, 127] (positions 6 .. 1, least significant
+// first) and the top digit d_0 = floor(G / 2^48) in [-128, 128], since
+// sum_{s >= 1} d_s 256^(6-s) = (G mod 2^48) - C.  These are the balanced base-256 digits
+// (every low digit in [-128, 127]), obtained with one 64-bit add instead of a
+// carry loop.  A byte g becomes the float 2^23 + g by a byte permute into the bits of 2^23,
+// and one FP32 subtraction of 2^23 + 128 gives g - 128 exactly.
+__device__ __forceinline__ void digits(double x, int E, float (&f)[S]) {
   const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
   const int ea = (int)((hi >> 20) & 0x7FFu);
   unsigned long long m = ((unsigned long long)(hi & 0xFFFFFu) << 32) | lo;
@@ -140,19 +148,21 @@ __device__ __forceinline__ void digits(double x, int E, int (&d)[S]) {
   else
     F = 0;
   if (hi & 0x80000000u) F = -F;
-#pragma unroll
-  for (int s = S - 1; s >= 0; --s) {
-    int v = (int)(F & 0xFF);
-    if (v >= 128) v -= 256;
-    d[s] = v;
-    F = (F - v) >> 8;
-  }
-  d[0] += (int)F * 256;  // |x| < 1/2 leaves no carry; kept for safety
+  const unsigned long long G = (unsigned long long)F + 0x808080808080ull;
+  const uint32_t g0 = (uint32_t)G, g1 = (uint32_t)(G >> 32);
+  constexpr float kBias = 8388736.0f;  // 2^23 + 128
+  f[6] = __uint_as_float(__byte_perm(g0, 0x4B000000u, 0x7540)) - kBias;
+  f[5] = __uint_as_float(__byte_perm(g0, 0x4B000000u, 0x7541)) - kBias;
+  f[4] = __uint_as_float(__byte_perm(g0, 0x4B000000u, 0x7542)) - kBias;
+  f[3] = __uint_as_float(__byte_perm(g0, 0x4B000000u, 0x7543)) - kBias;
+  f[2] = __uint_as_float(__byte_perm(g1, 0x4B000000u, 0x7540)) - kBias;
+  f[1] = __uint_as_float(__byte_perm(g1, 0x4B000000u, 0x7541)) - kBias;
+  f[0] = __uint_as_float((uint32_t)(((int)g1 >> 16) + (0x4B000000 + 128))) - kBias;  // d_0 + 128 in [0, 256]
 }
 
-__device__ __forceinline__ uint32_t bf16_pair(int a, int b) {
-  const uint32_t fa = __float_as_uint(__int2float_rn(a)), fb = __float_as_uint(__int2float_rn(b));
-  return __byte_perm(fa, fb, 0x7632);  // exact: |digit| <= 256 has at most 8 significant bits
+// two digits -> one 32-bit word of two bf16 (exact: a digit has at most 8 significant bits)
+__device__ __forceinline__ uint32_t bf16_pair(float a, float b) {
+  return __byte_perm(__float_as_uint(a), __float_as_uint(b), 0x7632);
 }
 
 __global__ void pack_kernel(Operand op, const int* e, int TR, int nrb, int nkb, __nv_bfloat16* out) {
@@ -166,7 +176,7 @@ __global__ void pack_kernel(Operand op, const int* e, int TR, int nrb, int nkb, 
     const int r = within % TR, kg = within / TR;
     const int row = rb * TR + r;
     const int E = row < op.R ? e[row] : 0;
-    int d[8][S];
+    float d[8][S];
 #pragma unroll
     for (int kk = 0; kk < 8; ++kk) {
       const int k = kb * kDepth + kg * 8 + kk;
@@ -819,7 +829,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
           if (kind == 0 || gi >= k0 + 4 * kq + kk) x[kk] = v;
         }
       }
-      int d[4][S];
+      float d[4][S];
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk) digits(x[kk], E, d[kk]);
       unsigned char* dst = adig + (size_t)sb * Smem::a_block;
@@ -875,6 +885,44 @@ __global__ void reduce_kernel(const int64_t* Phi, const int64_t* Plo, int64_t ld
     for (int z = 0; z < splits; ++z) {
       h += Phi[(size_t)z * sstride + i + (int64_t)j * ldp];
       l += Plo[(size_t)z * sstride + i + (int64_t)j * ldp];
+    }
+    const double v = scale2(fma((double)h, 0x1p-32, (double)l * 0x1p-64), (eA[i] - 1021) + (eB[j] - 1021));
+    double* cp = C + i + (int64_t)j * ldc;
+    *cp = beta == 0.0 ? alpha * v : fma(alpha, v, beta * *cp);
+  }
+}
+
+// The same sums for outputs with many splits (X2 = X1^T W / 2 splits its reduction of
+// length j over up to 64 CTAs): 32 consecutive outputs per block, the splits dealt to the
+// block's eight warps and their partial sums added in shared memory.  The sums are
+// integers, so the result is the one of reduce_kernel bit for bit.
+constexpr int kWideSplits = 8;  // splits above which reduce() takes this kernel
+__global__ void __launch_bounds__(256)
+    reduce_wide_kernel(const int64_t* Phi, const int64_t* Plo, int64_t ldp, int64_t sstride, int splits, const int* eA,
+                       const int* eB, int M, int N, double alpha, double beta, double* C, int64_t ldc) {
+  __shared__ long long ph[8][32], pl[8][32];
+  const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+  const int64_t total = (int64_t)M * N;
+  const int64_t e = blockIdx.x * 32ll + lane;
+  const bool live = e < total;
+  const int i = live ? (int)(e % M) : 0, j = live ? (int)(e / M) : 0;
+  long long h = 0, l = 0;
+  if (live) {
+    const size_t off = i + (size_t)j * ldp;
+#pragma unroll 4
+    for (int z = wy; z < splits; z += 8) {
+      h += Phi[(size_t)z * sstride + off];
+      l += Plo[(size_t)z * sstride + off];
+    }
+  }
+  ph[wy][lane] = h;
+  pl[wy][lane] = l;
+  __syncthreads();
+  if (wy == 0 && live) {
+#pragma unroll
+    for (int q = 1; q < 8; ++q) {
+      h += ph[q][lane];
+      l += pl[q][lane];
     }
     const double v = scale2(fma((double)h, 0x1p-32, (double)l * 0x1p-64), (eA[i] - 1021) + (eB[j] - 1021));
     double* cp = C + i + (int64_t)j * ldc;
@@ -948,6 +996,12 @@ cudaError_t reduce(const GemmParams& p, int splits, double alpha, double beta, d
                    cudaStream_t s) {
   const int64_t total = (int64_t)p.M * p.N;
   if (total <= 0) return cudaSuccess;
+  if (splits > kWideSplits) {
+    reduce_wide_kernel<<<(unsigned)((total + 31) / 32), 256, 0, s>>>(p.Phi, p.Plo, p.ldp, p.sstride, splits, p.eA, p.eB,
+                                                                       p.M, p.N, alpha, beta, C, ldc);
+    prof::count_launch();
+    return cudaGetLastError();
+  }
   const int blocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
   reduce_kernel<<<blocks, 256, 0, s>>>(p.Phi, p.Plo, p.ldp, p.sstride, splits, p.eA, p.eB, p.M, p.N, alpha, beta, C,
                                        ldc);

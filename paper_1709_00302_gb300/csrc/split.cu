@@ -755,6 +755,41 @@ __global__ void reduce_kernel(ReduceParams single, const ReduceParams* probs) {
   }
 }
 
+// The same sums for outputs with many splits (the b x b product X1^T W splits its long
+// reduction over up to 256 CTAs): 32 consecutive outputs per block, the splits dealt to the
+// block's eight warps (z = warp, warp + 8, ...) and the eight partial sums added in warp
+// order, so a thread waits on about splits / 8 loads instead of all of them.  The order
+// is fixed, so results repeat bit for bit.
+constexpr int kWideSplits = 8;  // splits above which reduce() takes this kernel
+__global__ void __launch_bounds__(256) reduce_wide_kernel(ReduceParams r) {
+  __shared__ double part[8][32];
+  const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+  const int64_t total = (int64_t)r.M * r.N;
+  const int64_t e = blockIdx.x * 32ll + lane;
+  const bool live = e < total;
+  const int i = live ? (int)(e % r.M) : 0, c = live ? (int)(e / r.M) : 0;
+  double s0 = 0.0, s1 = 0.0;
+  if (live) {
+    const double* src = r.P + i + (int64_t)c * r.ldp;
+    int z = wy;
+#pragma unroll 4
+    for (; z + 8 < r.splits; z += 16) {
+      s0 += src[(size_t)z * r.sstride];
+      s1 += src[(size_t)(z + 8) * r.sstride];
+    }
+    if (z < r.splits) s0 += src[(size_t)z * r.sstride];
+  }
+  part[wy][lane] = s0 + s1;
+  __syncthreads();
+  if (wy == 0 && live) {
+    double v = part[0][lane];
+#pragma unroll
+    for (int q = 1; q < 8; ++q) v += part[q][lane];
+    double* cp = &r.C[i + (int64_t)c * r.ldc];
+    *cp = (r.beta == 0.0) ? r.alpha * v : fma(r.alpha, v, r.beta * *cp);
+  }
+}
+
 template <int BN, int S, int NSTAGE>
 cudaError_t launch_stream(const StreamParams& p, const StreamParams* probs, dim3 grid, cudaStream_t s) {
   using L = StreamSmem<BN, S, NSTAGE>;
@@ -928,8 +963,13 @@ cudaError_t reduce(int M, int N, int splits, const double* P, int64_t ldp, int64
                    double* C, int64_t ldc, cudaStream_t s) {
   const int64_t total = (int64_t)M * N;
   if (total <= 0) return cudaSuccess;
-  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 2048);
   ReduceParams r{M, N, splits, P, ldp, sstride, alpha, beta, C, ldc};
+  if (splits > kWideSplits) {
+    reduce_wide_kernel<<<(unsigned)((total + 31) / 32), 256, 0, s>>>(r);
+    prof::count_launch();
+    return cudaGetLastError();
+  }
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 2048);
   reduce_kernel<<<blocks, 256, 0, s>>>(r, nullptr);
   prof::count_launch();
   return cudaGetLastError();
