@@ -261,39 +261,41 @@ __device__ __forceinline__ bool fixed_to_f64(long long thi, long long tlo, int k
   return true;
 }
 
-// C(row, col) += alpha (thi 2^-32 + tlo 2^-64) 2^(e_row + e_col - 2042) for the 32 columns
-// col0 .. col0 + 31 of one row held by a thread, restricted to [p.col0, p.col1) (and
-// col <= row when p.lower).  Loads of C and of the column exponents go out four columns at
-// a time ahead of the stores, so a tile pays eight memory round trips instead of 32.
 constexpr int kEpiGroup = 4;
 // Pulls the row's entries of C that add_row_products will update into L2 while the
 // tile's MMAs are still running.
+template <int NC = 32>
 __device__ __forceinline__ void prefetch_row(const GemmParams& p, int row, int col0) {
   const double* crow = p.C + row;
 #pragma unroll 4
-  for (int c = 0; c < 32; ++c) {
+  for (int c = 0; c < NC; ++c) {
     const int col = col0 + c;
     if (col < p.N && col >= p.col0 && col < p.col1 && (!p.lower || row >= col))
       asm volatile("prefetch.global.L2 [%0];" ::"l"(crow + (int64_t)col * p.ldc));
   }
 }
-__device__ __forceinline__ void add_row_products(const GemmParams& p, int row, int col0, const long long (&thi)[32],
-                                                 const long long (&tlo)[32]) {
+// C(row, col) += alpha (thi 2^-32 + tlo 2^-64) 2^(e_row + e_col - 2042) for the NC columns
+// col0 .. col0 + NC - 1 of one row held by a thread, restricted to [p.col0, p.col1) (and
+// col <= row when p.lower).  Loads of C and of the column exponents go out G columns at a
+// time ahead of the stores, so a row pays NC / G memory round trips.
+template <int NC = 32, int G = kEpiGroup>
+__device__ __forceinline__ void add_row_products(const GemmParams& p, int row, int col0, const long long (&thi)[NC],
+                                                 const long long (&tlo)[NC]) {
   const int ei = p.eA[row];
   double* crow = p.C + row;
 #pragma unroll
-  for (int g = 0; g < 32; g += kEpiGroup) {
-    double cv[kEpiGroup];
-    int ej[kEpiGroup];
+  for (int g = 0; g < NC; g += G) {
+    double cv[G];
+    int ej[G];
 #pragma unroll
-    for (int c = 0; c < kEpiGroup; ++c) {
+    for (int c = 0; c < G; ++c) {
       const int col = col0 + g + c;
       const bool ok = col < p.N && col >= p.col0 && col < p.col1 && (!p.lower || row >= col);
       cv[c] = ok ? crow[(int64_t)col * p.ldc] : 0.0;
       ej[c] = ok ? p.eB[col] : -1;
     }
 #pragma unroll
-    for (int c = 0; c < kEpiGroup; ++c) {
+    for (int c = 0; c < G; ++c) {
       if (ej[c] < 0) continue;
       const int k = (ei - 1021) + (ej[c] - 1021);
       double v;
@@ -483,9 +485,15 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_kernel(GemmParams p) {
 // SM walks its tiles (every gridDim.x-th tile of the lower triangle / column range) with one
 // continuous copy and MMA pipeline, so a tile's epilogue (reading and writing C) runs
 // while the next tile's MMAs do; only the read-out of tensor memory stalls the MMAs.
+// Sixteen drain/epilogue warps of 16 columns each (lane quadrant warp & 3, column group
+// warp >> 2): twice the warps of the tile kernel to hide the latency of the C loads and of
+// the FP64 adds, with half the 64-bit sums per thread.
 constexpr int kMaxTilesPerCta = 1024;
+constexpr int kRankWorkers = 16;
+constexpr int kRankThreads = kRankWorkers * 32 + 32;
+constexpr int kRankCols = kTileB / 4;  // columns per worker thread
 
-__global__ void __launch_bounds__(kGemmThreads, 1) rank_kernel(GemmParams p) {
+__global__ void __launch_bounds__(kRankThreads, 1) rank_kernel(GemmParams p) {
   extern __shared__ __align__(1024) unsigned char smem[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + Smem::off_bar);
   uint64_t* freed = full + kSlots;
@@ -512,7 +520,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) rank_kernel(GemmParams p) {
       tc::mbar_init(&freed[q], 1);
     }
     tc::mbar_init(acc_ready, 1);
-    tc::mbar_init(drained, NT / 32);
+    tc::mbar_init(drained, kRankWorkers);
     tc::fence_mbar_init();
   }
   if (warp == 0) {
@@ -527,7 +535,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) rank_kernel(GemmParams p) {
   const int total = nt * nkb;
   int timed_out = 0;
 
-  if (warp == NT / 32) {
+  if (warp == kRankWorkers) {
     if (lane == 0 && total > 0) {
       auto issue = [&](int qs) {
         const int L = tiles[qs / nkb], kb = qs % nkb, slot = qs % kSlots;
@@ -580,11 +588,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1) rank_kernel(GemmParams p) {
     for (int lt = 0; lt < nt && !timed_out; ++lt) {
       {
         const int L = tiles[lt], row = (L % nI) * kTileA + qd * 32 + lane;
-        if (row < p.M) prefetch_row(p, row, (L / nI) * kTileB + h * 32);
+        if (row < p.M) prefetch_row<kRankCols>(p, row, (L / nI) * kTileB + h * kRankCols);
       }
-      long long thi[32], tlo[32];
+      long long thi[kRankCols], tlo[kRankCols];
 #pragma unroll
-      for (int c = 0; c < 32; ++c) thi[c] = tlo[c] = 0;
+      for (int c = 0; c < kRankCols; ++c) thi[c] = tlo[c] = 0;
       for (int c = 0; c < cpt; ++c) {
         const int gc = lt * cpt + c;
         if (!tc::mbar_wait(acc_ready, (uint32_t)gc & 1u, deadline)) {
@@ -594,11 +602,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1) rank_kernel(GemmParams p) {
         tc::fence_after_sync();
 #pragma unroll 1
         for (int D = 0; D < S; ++D) {
-          float v[32];
-          tc::tmem_ld32(tmem + ((qd * 32) << 16) + (uint32_t)(D * kTileB + h * 32), v);
+          float v[kRankCols];
+          tc::tmem_ld16(tmem + ((qd * 32) << 16) + (uint32_t)(D * kTileB + h * kRankCols), v);
           const int shift = D <= 2 ? 8 * (2 - D) : 8 * (6 - D);
 #pragma unroll
-          for (int cc = 0; cc < 32; ++cc) {
+          for (int cc = 0; cc < kRankCols; ++cc) {
             const long long iv = (long long)__float2int_rn(v[cc]) << shift;
             if (D <= 2)
               thi[cc] += iv;
@@ -615,7 +623,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) rank_kernel(GemmParams p) {
       const int L = tiles[lt], I = L % nI, J = L / nI;
       const int row = I * kTileA + qd * 32 + lane;
       if (row < p.M) {
-        add_row_products(p, row, J * kTileB + h * 32, thi, tlo);
+        add_row_products<kRankCols, 8>(p, row, J * kTileB + h * kRankCols, thi, tlo);
       }
     }
   }
@@ -1199,7 +1207,7 @@ cudaError_t rank_apply(int M, int N, int K, double alpha, double* C, int64_t ldc
   const int64_t all = (int64_t)nI * nJ;
   const int grid =
       (int)std::max<int64_t>(std::min<int64_t>(sms, valid), (all + kMaxTilesPerCta - 1) / kMaxTilesPerCta);
-  rank_kernel<<<grid, kGemmThreads, smem, s>>>(p);
+  rank_kernel<<<grid, kRankThreads, smem, s>>>(p);
   prof::count_launch();
   return cudaGetLastError();
 }
