@@ -110,4 +110,16 @@ __device__ __forceinline__ double warp_max(double v) {
 // Loads of data written by other CTAs during the same launch: skip L1.
 __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
 
+// Programmatic dependent launch.  A kernel launched with launch_pdl (launch.h) may start
+// while the kernel before it in the stream is still running.  Every thread calls this
+// once, after the prologue that touches only parameters, shared and tensor memory, and
+// before its first access to global memory that an earlier kernel writes: the wait
+// returns once the previous grid has completed and its writes are visible, and the
+// release then lets the next kernel of the stream begin its own launch.  Without the
+// launch attribute both instructions return at once.
+__device__ __forceinline__ void pdl_wait_and_release() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 }  // namespace bandred

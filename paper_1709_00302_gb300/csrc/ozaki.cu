@@ -19,6 +19,7 @@
 
 #include "bandred.h"
 #include "common.cuh"
+#include "launch.h"
 #include "ozaki.h"
 #include "prof.h"
 #include "split.h"
@@ -49,6 +50,7 @@ __device__ __forceinline__ double elem(const double* M, int64_t ld, int mode, in
 // columns each), row maxima combined across the warps
 __global__ void rowexp_cols_kernel(const double* M, int64_t ld, int R, int K, int* e) {
   __shared__ int rowmax[8][32];
+  pdl_wait_and_release();
   const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
   const int i = blockIdx.x * 32 + lane;
   int m = 0;
@@ -68,6 +70,7 @@ __global__ void rowexp_cols_kernel(const double* M, int64_t ld, int R, int K, in
 
 // entries M[k + r ld] (k in [k0, k1), k > r when `upper`): one warp per row
 __global__ void rowexp_rows_kernel(const double* M, int64_t ld, int R, int k0, int k1, int upper, int* e) {
+  pdl_wait_and_release();
   const int r = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x & 31;
   if (r >= R) return;
   const int per = (k1 - k0 + gridDim.y - 1) / gridDim.y;
@@ -87,6 +90,7 @@ __global__ void rowexp_rows_kernel(const double* M, int64_t ld, int R, int k0, i
 __global__ void rowexp_sym_kernel(const double* M, int64_t ld, int R, int* e) {
   const int ti = blockIdx.x, tk = blockIdx.y;
   if (tk > ti) return;
+  pdl_wait_and_release();
   __shared__ int colmax[8][32];
   const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
   const int i = ti * 32 + lane;
@@ -166,6 +170,7 @@ __device__ __forceinline__ uint32_t bf16_pair(float a, float b) {
 }
 
 __global__ void pack_kernel(Operand op, const int* e, int TR, int nrb, int nkb, __nv_bfloat16* out) {
+  pdl_wait_and_release();
   const int groups = TR * (kDepth / 8);
   const int64_t total = (int64_t)nrb * nkb * groups;
   const int K = op.K1 + op.K2;
@@ -359,6 +364,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_kernel(GemmParams p) {
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_holder;
+  pdl_wait_and_release();
   int timed_out = 0;
   long long thi[32], tlo[32];
 #pragma unroll
@@ -531,6 +537,7 @@ __global__ void __launch_bounds__(kRankThreads, 1) rank_kernel(GemmParams p) {
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_holder;
+  pdl_wait_and_release();
   const int nt = s_nt;
   const int total = nt * nkb;
   int timed_out = 0;
@@ -709,6 +716,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_holder;
+  pdl_wait_and_release();
 
   // 0: box read in place; 1: box of the mirror (transposed); 2: symmetric box across the diagonal
   auto kind_of = [&](int kb) -> int {
@@ -885,6 +893,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
 __global__ void reduce_kernel(const int64_t* Phi, const int64_t* Plo, int64_t ldp, int64_t sstride, int splits,
                               const int* eA, const int* eB, int M, int N, double alpha, double beta, double* C,
                               int64_t ldc) {
+  pdl_wait_and_release();
   const int64_t total = (int64_t)M * N;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
@@ -909,6 +918,7 @@ __global__ void __launch_bounds__(256)
     reduce_wide_kernel(const int64_t* Phi, const int64_t* Plo, int64_t ldp, int64_t sstride, int splits, const int* eA,
                        const int* eB, int M, int N, double alpha, double beta, double* C, int64_t ldc) {
   __shared__ long long ph[8][32], pl[8][32];
+  pdl_wait_and_release();
   const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
   const int64_t total = (int64_t)M * N;
   const int64_t e = blockIdx.x * 32ll + lane;
@@ -950,16 +960,20 @@ cudaError_t row_exponents(const Operand& op, int* e, cudaStream_t s) {
     const int ks = std::max(1, std::min(64, K / 256));
     if (mode == 2) {
       const int T = (op.R + 31) / 32;
-      rowexp_sym_kernel<<<dim3(T, T), 256, 0, s>>>(M, ld, op.R, e);
       prof::count_launch();
+      if (cudaError_t le = launch_pdl(rowexp_sym_kernel, dim3(T, T), dim3(256), 0, s, M, ld, op.R, e)) return le;
     }
     if (mode == 0) {
-      rowexp_cols_kernel<<<dim3((op.R + 31) / 32, (K + 31) / 32), 256, 0, s>>>(M, ld, op.R, K, e);
       prof::count_launch();
+      if (cudaError_t le = launch_pdl(rowexp_cols_kernel, dim3((op.R + 31) / 32, (K + 31) / 32), dim3(256), 0, s, M, ld,
+                                      op.R, K, e))
+        return le;
     }
     if (mode == 1) {
-      rowexp_rows_kernel<<<dim3((op.R + 7) / 8, ks), 256, 0, s>>>(M, ld, op.R, 0, K, 0, e);
       prof::count_launch();
+      if (cudaError_t le = launch_pdl(rowexp_rows_kernel, dim3((op.R + 7) / 8, ks), dim3(256), 0, s, M, ld, op.R, 0, K, 0,
+                                      e))
+        return le;
     }
     return cudaGetLastError();
   };
@@ -979,9 +993,8 @@ cudaError_t pack(const Operand& op, const int* e, int TR, __nv_bfloat16* out, cu
   const int nrb = (op.R + TR - 1) / TR, nkb = (K + kDepth - 1) / kDepth;
   const int64_t total = (int64_t)nrb * nkb * TR * (kDepth / 8);
   const int blocks = (int)std::min<int64_t>((total + 255) / 256, 8192);
-  pack_kernel<<<blocks, 256, 0, s>>>(op, e, TR, nrb, nkb, out);
   prof::count_launch();
-  return cudaGetLastError();
+  return launch_pdl(pack_kernel, dim3(blocks), dim3(256), 0, s, op, e, TR, nrb, nkb, out);
 }
 
 cudaError_t gemm(const GemmParams& p, int splits, cudaStream_t s) {
@@ -995,9 +1008,8 @@ cudaError_t gemm(const GemmParams& p, int splits, cudaStream_t s) {
     configured = dev;
   }
   const dim3 grid((p.M + kTileA - 1) / kTileA, (p.N + kTileB - 1) / kTileB, splits);
-  gemm_kernel<<<grid, kGemmThreads, Smem::total, s>>>(p);
   prof::count_launch();
-  return cudaGetLastError();
+  return launch_pdl(gemm_kernel, grid, dim3(kGemmThreads), Smem::total, s, p);
 }
 
 cudaError_t reduce(const GemmParams& p, int splits, double alpha, double beta, double* C, int64_t ldc,
@@ -1005,16 +1017,14 @@ cudaError_t reduce(const GemmParams& p, int splits, double alpha, double beta, d
   const int64_t total = (int64_t)p.M * p.N;
   if (total <= 0) return cudaSuccess;
   if (splits > kWideSplits) {
-    reduce_wide_kernel<<<(unsigned)((total + 31) / 32), 256, 0, s>>>(p.Phi, p.Plo, p.ldp, p.sstride, splits, p.eA, p.eB,
-                                                                       p.M, p.N, alpha, beta, C, ldc);
     prof::count_launch();
-    return cudaGetLastError();
+    return launch_pdl(reduce_wide_kernel, dim3((unsigned)((total + 31) / 32)), dim3(256), 0, s, p.Phi, p.Plo, p.ldp,
+                      p.sstride, splits, p.eA, p.eB, p.M, p.N, alpha, beta, C, ldc);
   }
   const int blocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
-  reduce_kernel<<<blocks, 256, 0, s>>>(p.Phi, p.Plo, p.ldp, p.sstride, splits, p.eA, p.eB, p.M, p.N, alpha, beta, C,
-                                       ldc);
   prof::count_launch();
-  return cudaGetLastError();
+  return launch_pdl(reduce_kernel, dim3(blocks), dim3(256), 0, s, p.Phi, p.Plo, p.ldp, p.sstride, splits, p.eA, p.eB,
+                    p.M, p.N, alpha, beta, C, ldc);
 }
 
 static size_t al256(size_t x) { return (x + 255) / 256 * 256; }
@@ -1118,9 +1128,10 @@ bool stream_product(const Operand& A, const Operand& B, int M, int N, int K, dou
     sp.ldp = M;
     sp.status = status;
     sp.limit_ns = limit_ns;
-    stream_kernel<<<dim3((M + kTileA - 1) / kTileA, used), kStreamThreads, StreamSmem::total, s>>>(sp, lo, up);
     prof::count_launch();
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launch_pdl(stream_kernel, dim3((M + kTileA - 1) / kTileA, used), dim3(kStreamThreads), StreamSmem::total, s,
+                        sp, lo, up)) != cudaSuccess)
+      return e;
     GemmParams gp{};
     gp.Phi = sp.Phi;
     gp.Plo = sp.Plo;
@@ -1207,9 +1218,8 @@ cudaError_t rank_apply(int M, int N, int K, double alpha, double* C, int64_t ldc
   const int64_t all = (int64_t)nI * nJ;
   const int grid =
       (int)std::max<int64_t>(std::min<int64_t>(sms, valid), (all + kMaxTilesPerCta - 1) / kMaxTilesPerCta);
-  rank_kernel<<<grid, kRankThreads, smem, s>>>(p);
   prof::count_launch();
-  return cudaGetLastError();
+  return launch_pdl(rank_kernel, dim3(grid), dim3(kRankThreads), smem, s, p);
 }
 
 }  // namespace ozaki

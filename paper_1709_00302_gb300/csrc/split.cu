@@ -23,6 +23,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "launch.h"
 #include "prof.h"
 #include "split.h"
 #include "tc.cuh"
@@ -48,6 +49,7 @@ __device__ __forceinline__ void report(int* status, int code) {
 __global__ void pack_kernel(PackParams single, const PackParams* probs) {
   const PackParams p = probs ? probs[blockIdx.y] : single;
   if (p.R <= 0) return;
+  pdl_wait_and_release();
   const int groups_per_tile = p.TR * (p.TK / 8);
   const int64_t total = (int64_t)p.nrb * p.nkb * groups_per_tile;
   const int K = p.K1 + p.K2;
@@ -162,6 +164,7 @@ __global__ void __launch_bounds__(NT, 1) stream_gemm_kernel(StreamParams single,
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_holder;
+  pdl_wait_and_release();
 
   // ---- loads of one stage: the FP64 A tile (BK x BM, [k][i]) and the B slices
   auto issue_loads = [&](int ls) {
@@ -420,6 +423,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_holder;
+  pdl_wait_and_release();
 
   // 0: every entry of the tile read in place (A(i, k) at A[i + k lda]); 1: every entry read
   // transposed (A[k + i lda]); 2: a symmetric tile across the diagonal
@@ -652,6 +656,7 @@ __global__ void __launch_bounds__(NT, 2) rank_update_kernel(RankParams single, c
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_holder;
+  pdl_wait_and_release();
   const int nkb = p.Kr / RK;
   const size_t blk = (size_t)S * L::slice_bytes;  // one (row block, K block) of a blob
   // Start fetching this CTA's C tile into L2 now, so the epilogue's reads overlap the
@@ -745,6 +750,7 @@ __global__ void __launch_bounds__(NT, 2) rank_update_kernel(RankParams single, c
 // ================================================================= split-K reduce
 __global__ void reduce_kernel(ReduceParams single, const ReduceParams* probs) {
   const ReduceParams r = probs ? probs[blockIdx.y] : single;
+  pdl_wait_and_release();
   const int64_t total = (int64_t)r.M * r.N;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(e % r.M), c = (int)(e / r.M);
@@ -763,6 +769,7 @@ __global__ void reduce_kernel(ReduceParams single, const ReduceParams* probs) {
 constexpr int kWideSplits = 8;  // splits above which reduce() takes this kernel
 __global__ void __launch_bounds__(256) reduce_wide_kernel(ReduceParams r) {
   __shared__ double part[8][32];
+  pdl_wait_and_release();
   const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
   const int64_t total = (int64_t)r.M * r.N;
   const int64_t e = blockIdx.x * 32ll + lane;
@@ -803,9 +810,12 @@ cudaError_t launch_stream(const StreamParams& p, const StreamParams* probs, dim3
     if (e != cudaSuccess) return e;
     configured = dev;
   }
-  stream_gemm_kernel<BN, S, NSTAGE><<<grid, NT, L::total, s>>>(p, probs);
   prof::count_launch();
-  return cudaGetLastError();
+  if (probs) {
+    stream_gemm_kernel<BN, S, NSTAGE><<<grid, NT, L::total, s>>>(p, probs);
+    return cudaGetLastError();
+  }
+  return launch_pdl(stream_gemm_kernel<BN, S, NSTAGE>, grid, dim3(NT), L::total, s, p, probs);
 }
 
 template <int BN, int S>
@@ -822,9 +832,8 @@ cudaError_t launch_stream_tma(const StreamParams& p, const CUtensorMap& lo, cons
     if (e != cudaSuccess) return e;
     configured = dev;
   }
-  stream_tma_kernel<BN, S><<<grid, kTmaThreads, L::total, s>>>(p, lo, up);
   prof::count_launch();
-  return cudaGetLastError();
+  return launch_pdl(stream_tma_kernel<BN, S>, grid, dim3(kTmaThreads), L::total, s, p, lo, up);
 }
 
 // cuTensorMapEncodeTiled, fetched from the driver once (the library links no libcuda).
@@ -893,9 +902,12 @@ cudaError_t launch_rank(const RankParams& p, const RankParams* probs, dim3 grid,
     if (e != cudaSuccess) return e;
     configured = dev;
   }
-  rank_update_kernel<S><<<grid, NT, L::total, s>>>(p, probs);
   prof::count_launch();
-  return cudaGetLastError();
+  if (probs) {
+    rank_update_kernel<S><<<grid, NT, L::total, s>>>(p, probs);
+    return cudaGetLastError();
+  }
+  return launch_pdl(rank_update_kernel<S>, grid, dim3(NT), L::total, s, p, probs);
 }
 
 }  // namespace
@@ -917,9 +929,8 @@ cudaError_t pack(const PackParams& pp, cudaStream_t s) {
   const int64_t total = (int64_t)pp.nrb * pp.nkb * pp.TR * (pp.TK / 8);
   if (total <= 0) return cudaSuccess;
   const int blocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
-  pack_kernel<<<blocks, 256, 0, s>>>(pp, nullptr);
   prof::count_launch();
-  return cudaGetLastError();
+  return launch_pdl(pack_kernel, dim3(blocks), dim3(256), 0, s, pp, (const PackParams*)nullptr);
 }
 
 cudaError_t pack_batched(const PackParams* probs, int nprob, int64_t max_groups, cudaStream_t s) {
@@ -965,14 +976,12 @@ cudaError_t reduce(int M, int N, int splits, const double* P, int64_t ldp, int64
   if (total <= 0) return cudaSuccess;
   ReduceParams r{M, N, splits, P, ldp, sstride, alpha, beta, C, ldc};
   if (splits > kWideSplits) {
-    reduce_wide_kernel<<<(unsigned)((total + 31) / 32), 256, 0, s>>>(r);
     prof::count_launch();
-    return cudaGetLastError();
+    return launch_pdl(reduce_wide_kernel, dim3((unsigned)((total + 31) / 32)), dim3(256), 0, s, r);
   }
   const int blocks = (int)std::min<int64_t>((total + 255) / 256, 2048);
-  reduce_kernel<<<blocks, 256, 0, s>>>(r, nullptr);
   prof::count_launch();
-  return cudaGetLastError();
+  return launch_pdl(reduce_kernel, dim3(blocks), dim3(256), 0, s, r, (const ReduceParams*)nullptr);
 }
 
 cudaError_t reduce_batched(const ReduceParams* probs, int nprob, int64_t max_total, cudaStream_t s) {
