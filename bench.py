@@ -371,18 +371,28 @@ def make_problem(args, br, dev, stream):
 
 def bench_batched(args, br, dev, stream, world, rank, dist):
     """1000 symmetric (n ~ U[64,1024]) and 1000 general (n ~ U[64,1024], m ~ U[n,2n])
-    matrices, w in {16, 32}; every step restores the inputs and replays one captured CUDA
-    graph holding both batched runs."""
+    matrices per GPU, w in {16, 32}; every step restores the inputs and replays one
+    captured CUDA graph holding both batched runs.  With N ranks the batch is N times as
+    large and split between them by LPT on nominal flops (paper_1709_00302_gb300.shard):
+    no data crosses ranks, only the step times (max) and the status words (sum)."""
     import torch
 
     import workloads
 
-    sym, gen = workloads.batched_mix(args.batch_sym, args.batch_gen, seed=0)
+    sym_all, gen_all = workloads.batched_mix(world * args.batch_sym, world * args.batch_gen, seed=0)
+    if world > 1:
+        from paper_1709_00302_gb300 import shard
+
+        si, gi = shard.batched_shard(sym_all, gen_all, world, rank)
+        sym, gen = [sym_all[i] for i in si], [gen_all[i] for i in gi]
+    else:
+        sym, gen = sym_all, gen_all
+    total_count = len(sym_all) + len(gen_all)
     # one flat device buffer per kind; matrices are column-major views into it
     tot_s = sum(n * n for n, _ in sym)
     tot_g = sum(m * n for m, n, _ in gen)
     g = torch.Generator(device=dev)
-    g.manual_seed(0)
+    g.manual_seed(rank)
     flat_s0 = torch.randn(tot_s, dtype=torch.float64, device=dev, generator=g)
     flat_g0 = torch.randn(tot_g, dtype=torch.float64, device=dev, generator=g)
     flat_s, flat_g = flat_s0.clone(), flat_g0.clone()
@@ -477,7 +487,7 @@ def bench_batched(args, br, dev, stream, world, rank, dist):
                 e2e_ms.append(e0.elapsed_time(e1))
     e2e_step = sum(e2e_ms) / len(e2e_ms)
     tau_bytes = sum(t.numel() * 8 for t in taus + tqs + tps)
-    e2e = {"value": world * (len(sym) + len(gen)) / (e2e_step / 1e3), "unit": "mats/s",
+    e2e = {"value": total_count / (e2e_step / 1e3), "unit": "mats/s",
            "h2d_bytes_per_step": (hs.numel() + hg.numel()) * 8,
            "d2h_bytes_per_step": (bs.numel() + bg.numel()) * 8, "ms_per_step": e2e_step,
            "note": f"the packed outputs (band + reflectors) are copied back; the {tau_bytes} bytes of tau "
@@ -503,12 +513,15 @@ def bench_batched(args, br, dev, stream, world, rank, dist):
                "sample": f"the first {done // 2} symmetric and {done // 2} general shapes of the mix ({dt:.1f} s)"}
     ms_step = sum(ms) / len(ms)
     t = torch.tensor([ms_step], dtype=torch.float64, device=dev)
+    bad = st.sum().to(torch.float64).reshape(1)
     if dist is not None:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(bad, op=dist.ReduceOp.SUM)  # device status words of every rank
+    assert float(bad.item()) == 0.0, "a rank reported a device-side failure"
     ms_max = float(t.item())
-    count = len(sym) + len(gen)
-    value = world * count / (ms_max / 1e3)
-    flops = sum(nominal_flops(n) for n, _ in sym) + sum(4.0 * (m * n * n - n ** 3 / 3.0) for m, n, _ in gen)
+    count = total_count
+    value = count / (ms_max / 1e3)
+    flops = sum(nominal_flops(n) for n, _ in sym_all) + sum(4.0 * (m * n * n - n ** 3 / 3.0) for m, n, _ in gen_all)
     # accuracy of one matrix of each kind, checked against its input on the host
     sys.path.insert(0, os.path.join(ROOT, "tests"))
     from checks import gen_probe_backward, sym_probe_backward
@@ -528,9 +541,12 @@ def bench_batched(args, br, dev, stream, world, rank, dist):
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": DTYPES[args.precision],
             "data": "synthetic",
-            "config": {"workload": f"batched: {len(sym)} sy2sb n~U[64,1024] + {len(gen)} ge2gb n~U[64,1024] "
+            "config": {"workload": f"batched: {len(sym_all)} sy2sb n~U[64,1024] + {len(gen_all)} ge2gb n~U[64,1024] "
                                    f"m~U[n,2n], w in {{16,32}}, N(0,1) drawn on the device, one CUDA graph "
-                                   f"replay per step", "count": count, "precision": args.precision,
+                                   f"replay per step" + (f", split over {world} GPUs by LPT on nominal flops"
+                                                         if world > 1 else ""),
+                       "count": count, "precision": args.precision,
+                       "parallelism": f"batch sharded over {world} ranks" if world > 1 else "single",
                        "b": args.batch_b, "panel_ctas": args.panel_ctas, "l2": "inputs restored from resident copies inside the graph"},
             "tflops_nominal": flops / (ms_max / 1e3) / 1e12,
             "backward_error": {"sy2sb_largest": bw_s, "ge2gb_largest": bw_g},
