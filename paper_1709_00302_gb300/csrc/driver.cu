@@ -421,6 +421,14 @@ struct Sy2sb {
     return 0;
   }
 
+  // Ozaki buffers of the rank-2k operands [X3 | Y] and [Y | X3] (j rows, K = 2 bk): one
+  // row-exponent array serves both.
+  ozaki::Bufs rank2k_bufs(int j, int bk) const {
+    ozaki::Bufs b = ozaki::carve(ws.ozr, j, j, 2 * bk, 1);
+    b.eB = b.eA;
+    return b;
+  }
+
   // X1 = A2 W, X2 = X1^T W / 2, X3 = X1 + Y X2 (into ws.X); for the split path also packs
   // the operands of the rank-2k update.
   int compute_x(int64_t k, int buf, cudaStream_t s) {
@@ -455,9 +463,10 @@ struct Sy2sb {
         const Operand y{Y, ld, 0, B, nullptr, 0, 0, 0, j}, x2{ws.X2, B, 1, B, nullptr, 0, 0, 0, B};
         CK(ozaki::product(y, x2, j, B, B, 1.0, 1.0, ws.X, ld, ozaki::carve(ws.ozp, j, B, B, sp), sp, status, lim, s));
       }
-      // operands of A2 += X3 Y^T + Y X3^T: [X3 | Y] and [Y | X3]
+      // operands of A2 += X3 Y^T + Y X3^T: [X3 | Y] and [Y | X3], whose rows hold the same
+      // entries and so share their row exponents
       const Operand l{ws.X, ld, 0, B, Y, ld, 0, B, j}, r{Y, ld, 0, B, ws.X, ld, 0, B, j};
-      CK(ozaki::prepare(l, r, ozaki::carve(ws.ozr, j, j, 2 * B, 1), s));
+      CK(ozaki::prepare(l, r, rank2k_bufs(j, B), s));
       return 0;
     }
     if (!is_split(o)) {
@@ -604,7 +613,7 @@ struct Sy2sb {
     double* A2 = A + r0 + r0 * lda;
     prof::Scope sc(prof::kSyr2k, s, syr2k_flops(j, c0, c1, bk), syr2k_bytes(j, c0, c1, bk));
     if (o.precision == BANDRED_OZAKI) {
-      CK(ozaki::rank_apply(j, j, 2 * bk, 1.0, A2, lda, c0, c1, 1, ozaki::carve(ws.ozr, j, j, 2 * bk, 1), status,
+      CK(ozaki::rank_apply(j, j, 2 * bk, 1.0, A2, lda, c0, c1, 1, rank2k_bufs(j, bk), status,
                            o.limit_ns, s));
       return 0;
     }

@@ -46,6 +46,14 @@ __device__ __forceinline__ double elem(const double* M, int64_t ld, int mode, in
 }
 
 // ---------------------------------------------------------------- row exponents
+// e[0 .. n) = 0, as a kernel of the launch chain (a memset would end the programmatic
+// overlap of the kernels around it); it waits for the previous kernel, which may still
+// read the array.
+__global__ void zero_kernel(int* e, int n) {
+  pdl_wait_and_release();
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) e[i] = 0;
+}
+
 // entries M[r + k ld]: one 32 x 32 tile per block (lanes along rows, eight warps of four
 // columns each), row maxima combined across the warps
 __global__ void rowexp_cols_kernel(const double* M, int64_t ld, int R, int K, int* e) {
@@ -953,7 +961,8 @@ __global__ void __launch_bounds__(256)
 // ---------------------------------------------------------------- host API
 cudaError_t row_exponents(const Operand& op, int* e, cudaStream_t s) {
   if (op.R <= 0) return cudaSuccess;
-  cudaError_t err = cudaMemsetAsync(e, 0, sizeof(int) * (size_t)op.R, s);
+  prof::count_launch();
+  cudaError_t err = launch_pdl(zero_kernel, dim3((unsigned)std::min(1024, (op.R + 255) / 256)), dim3(256), 0, s, e, op.R);
   if (err != cudaSuccess) return err;
   auto one = [&](const double* M, int64_t ld, int mode, int K) -> cudaError_t {
     if (K <= 0 || !M) return cudaSuccess;
@@ -1071,7 +1080,7 @@ Bufs carve(void* base, int M, int N, int K, int splits) {
 
 cudaError_t prepare(const Operand& A, const Operand& B, const Bufs& b, cudaStream_t s) {
   cudaError_t e = row_exponents(A, b.eA, s);
-  if (e == cudaSuccess) e = row_exponents(B, b.eB, s);
+  if (e == cudaSuccess && b.eB != b.eA) e = row_exponents(B, b.eB, s);
   if (e == cudaSuccess) e = pack(A, b.eA, kTileA, b.Ablob, s);
   if (e == cudaSuccess) e = pack(B, b.eB, kTileB, b.Bblob, s);
   return e;

@@ -88,7 +88,8 @@ cudaError_t product(const Operand& A, const Operand& B, int M, int N, int K, dou
                     int64_t ldc, const Bufs& b, int splits, int* status, unsigned long long limit_ns,
                     cudaStream_t s);
 // Row exponents and digits of both operands into b (for rank_apply; products pack their
-// own operands).
+// own operands).  When b.eB == b.eA the caller states that every row of B holds the same
+// entries as that row of A (in another order), and B's exponents are not computed again.
 cudaError_t prepare(const Operand& A, const Operand& B, const Bufs& b, cudaStream_t s);
 // C += alpha opA opB^T on columns [col0, col1) (and the lower triangle when `lower`), from
 // operands packed by prepare (several calls, on any streams, may share them).
