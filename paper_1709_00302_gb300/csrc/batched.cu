@@ -50,6 +50,9 @@ struct Launch {
   int a = 0, b = 0;          // panel: C, Rp_max | stream: max_tiles, max_splits | rank: max_ti, max_tj
   int c = 0;                 // panel: bk_max | stream: BN
   int64_t big = 0;           // pack: max groups | reduce: max total
+  // algorithmic flops and HBM bytes of all the launch's problems (profiler attribution;
+  // the same counts as the single-matrix driver)
+  double flops = 0.0, bytes = 0.0;
 };
 
 // Host side of a schedule: launch records plus the bytes of every parameter table.
@@ -163,21 +166,34 @@ struct Batcher {
   void packs(const std::vector<PackParams>& v) {
     if (v.empty()) return;
     Launch L{kLPack, S.add(v), (int)v.size()};
-    for (const auto& p : v) L.big = std::max(L.big, pack_groups(p));
+    for (const auto& p : v) {
+      L.big = std::max(L.big, pack_groups(p));
+      L.bytes += (8.0 + 2.0 * p.S) * p.R * (double)(p.K1 + p.K2);  // FP64 in, S bf16 slices out
+    }
     S.launches.push_back(L);
   }
   void reduces(const std::vector<ReduceParams>& v) {
     if (v.empty()) return;
     Launch L{kLReduce, S.add(v), (int)v.size()};
-    for (const auto& r : v) L.big = std::max<int64_t>(L.big, (int64_t)r.M * r.N);
+    for (const auto& r : v) {
+      L.big = std::max<int64_t>(L.big, (int64_t)r.M * r.N);
+      L.bytes += 8.0 * r.M * (double)r.N * (r.splits + 1 + (r.beta != 0.0 ? 1 : 0));
+    }
     S.launches.push_back(L);
   }
-  void ranks(const std::vector<RankParams>& v) {
+  // kt[q]: the reduction length of problem q before padding to Kr
+  void ranks(const std::vector<RankParams>& v, const std::vector<int>& kt) {
     if (v.empty()) return;
     Launch L{kLRank, S.add(v), (int)v.size()};
-    for (const auto& r : v) {
+    for (size_t q = 0; q < v.size(); ++q) {
+      const RankParams& r = v[q];
       L.a = std::max(L.a, (r.M + 127) / 128);
       L.b = std::max(L.b, (std::min(r.N, r.col1) - 1) / 128 - r.tj0 + 1);
+      const double nc = (double)(std::min(r.N, r.col1) - r.col0);
+      // entries of C that change: the lower triangle (rows >= column) or the whole block
+      const double entries = r.lower ? nc * r.M - nc * (nc - 1.0) / 2.0 : nc * r.M;
+      L.flops += 2.0 * kt[q] * entries;
+      L.bytes += 8.0 * (2.0 * entries + (double)(r.M + r.N) * kt[q]);
     }
     S.launches.push_back(L);
   }
@@ -196,6 +212,9 @@ struct Batcher {
     L.c = BN;
     for (size_t q = 0; q < v.size(); ++q) {
       StreamParams& p = v[q];
+      L.flops += 2.0 * p.M * (double)p.K * p.N;
+      L.bytes += p.mode == split::kModeSymLower ? 8.0 * ((double)p.M * (p.M + 1) / 2.0 + 2.0 * p.M * (double)p.N)
+                                                 : 8.0 * ((double)p.M * p.K + (double)p.K * p.N + (double)p.M * p.N);
       p.stages_per_split = (p.nkb + splits - 1) / splits;
       const int used = (p.nkb + p.stages_per_split - 1) / p.stages_per_split;
       red[q].splits = used;
@@ -222,6 +241,10 @@ struct Batcher {
       Rpmax = std::max(Rpmax, p.Rp);
     }
     Launch L{kLPanel, S.add(w), (int)w.size()};
+    for (const auto& p : w) {  // Householder QR (2 j bk^2) and W = -Y T (j bk^2); 4 j bk doubles moved
+      L.flops += 3.0 * p.j * (double)p.bk * p.bk;
+      L.bytes += 32.0 * p.j * (double)p.bk;
+    }
     L.a = C;
     L.b = Rpmax;
     L.c = bkmax;
@@ -369,6 +392,7 @@ void build_sy2sb(std::vector<SyMat>& mats, const Options& o, int S, int sms, int
         std::vector<ReduceParams> rd1;
         std::vector<PackParams> pa, pb;
         std::vector<RankParams> rk;
+        std::vector<int> kt;
         for (int q : g) {
           const SyMat& M = mats[q];
           int bk, j;
@@ -383,11 +407,12 @@ void build_sy2sb(std::vector<SyMat>& mats, const Options& o, int S, int sms, int
           pa.push_back(pack_rows(M.r.Y, M.n - M.w, bk, nullptr, 0, 0, j, Kr, S, M.r.ablob));
           pb.push_back(pack_rows(M.r.ZT, M.w, bk, nullptr, 0, 0, na, Kr, S, M.r.bblob));
           rk.push_back(rank_of(M.r.ablob, M.r.bblob, Kr, A1, M.lda, j, na, 0, o, status));
+          kt.push_back(bk);
         }
         B.streams(st1, rd1, BN);
         B.packs(pa);
         B.packs(pb);
-        B.ranks(rk);
+        B.ranks(rk, kt);
       }
       // X1 = A2 W
       for (int q : g) {
@@ -430,6 +455,7 @@ void build_sy2sb(std::vector<SyMat>& mats, const Options& o, int S, int sms, int
       // A2 += X3 Y^T + Y X3^T (lower)
       std::vector<PackParams> pa, pb;
       std::vector<RankParams> rk;
+      std::vector<int> kt;
       for (int q : g) {
         const SyMat& M = mats[q];
         int bk, j;
@@ -441,10 +467,11 @@ void build_sy2sb(std::vector<SyMat>& mats, const Options& o, int S, int sms, int
         pb.push_back(pack_rows(M.r.Y, ld, bk, M.r.X, ld, bk, j, Kr, S, M.r.bblob));
         double* A2 = M.A + (k + M.w) * (1 + M.lda);
         rk.push_back(rank_of(M.r.ablob, M.r.bblob, Kr, A2, M.lda, j, j, 1, o, status));
+        kt.push_back(2 * bk);
       }
       B.packs(pa);
       B.packs(pb);
-      B.ranks(rk);
+      B.ranks(rk, kt);
     }
   }
 }
@@ -505,6 +532,7 @@ void build_ge2gb(std::vector<GeMat>& mats, const Options& o, int S, int sms, int
       std::vector<StreamParams> st;
       std::vector<ReduceParams> rd;
       std::vector<RankParams> rk;
+      std::vector<int> kt;
       for (int q : g) {
         const GeMat& M = mats[q];
         const int64_t k = (int64_t)t * M.b;
@@ -520,12 +548,13 @@ void build_ge2gb(std::vector<GeMat>& mats, const Options& o, int S, int sms, int
         pa.push_back(pack_rows(M.r.Y, M.m, bk, nullptr, 0, 0, j, Kr, S, M.r.ablob));
         pb.push_back(pack_rows(M.r.ZT, M.n, bk, nullptr, 0, 0, nc, Kr, S, M.r.bblob));
         rk.push_back(rank_of(M.r.ablob, M.r.bblob, Kr, E, M.lda, j, nc, 0, o, status));
+        kt.push_back(bk);
       }
       B.packs(pk);
       B.streams(st, rd, BN);
       B.packs(pa);
       B.packs(pb);
-      B.ranks(rk);
+      B.ranks(rk, kt);
     }
     // row panels
     pan.clear();
@@ -544,6 +573,7 @@ void build_ge2gb(std::vector<GeMat>& mats, const Options& o, int S, int sms, int
       std::vector<StreamParams> st;
       std::vector<ReduceParams> rd;
       std::vector<RankParams> rk;
+      std::vector<int> kt;
       for (int q : act) {
         const GeMat& M = mats[q];
         if (split::stream_bn(M.b) != BN) continue;
@@ -562,12 +592,13 @@ void build_ge2gb(std::vector<GeMat>& mats, const Options& o, int S, int sms, int
         pa.push_back(pack_rows(M.r.Pd, M.m, bkr, nullptr, 0, 0, nrow, Kr, S, M.r.ablob));
         pb.push_back(pack_rows(M.r.Yv, M.n, bkr, nullptr, 0, 0, jr, Kr, S, M.r.bblob));
         rk.push_back(rank_of(M.r.ablob, M.r.bblob, Kr, D, M.lda, nrow, jr, 0, o, status));
+        kt.push_back(bkr);
       }
       B.packs(pk);
       B.streams(st, rd, BN);
       B.packs(pa);
       B.packs(pb);
-      B.ranks(rk);
+      B.ranks(rk, kt);
     }
   }
 }
@@ -579,27 +610,27 @@ int launch_schedule(const Schedule& sch, const unsigned char* table, int S, cuda
     cudaError_t e = cudaSuccess;
     switch (L.type) {
       case kLPanel: {
-        prof::Scope sc(prof::kPanel, s, 0.0, 0.0);
+        prof::Scope sc(prof::kPanel, s, L.flops, L.bytes);
         e = launch_panel_cluster(nullptr, static_cast<const PanelParams*>(p), L.count, L.a, L.b, L.c, s);
         break;
       }
       case kLPack: {
-        prof::Scope sc(prof::kConvert, s, 0.0, 0.0);
+        prof::Scope sc(prof::kConvert, s, L.flops, L.bytes);
         e = split::pack_batched(static_cast<const PackParams*>(p), L.count, L.big, s);
         break;
       }
       case kLStream: {
-        prof::Scope sc(prof::kSymm, s, 0.0, 0.0);
+        prof::Scope sc(prof::kSymm, s, L.flops, L.bytes);
         e = split::stream_gemm_batched(static_cast<const StreamParams*>(p), L.count, S, L.c, L.a, L.b, s);
         break;
       }
       case kLReduce: {
-        prof::Scope sc(prof::kSplitReduce, s, 0.0, 0.0);
+        prof::Scope sc(prof::kSplitReduce, s, L.flops, L.bytes);
         e = split::reduce_batched(static_cast<const ReduceParams*>(p), L.count, L.big, s);
         break;
       }
       case kLRank: {
-        prof::Scope sc(prof::kSyr2k, s, 0.0, 0.0);
+        prof::Scope sc(prof::kSyr2k, s, L.flops, L.bytes);
         e = split::rank_update_batched(static_cast<const RankParams*>(p), L.count, S, L.a, L.b, s);
         break;
       }
