@@ -73,7 +73,12 @@ typedef struct bandred_opts {
     int debug;             /* 0.  Tests only: 1 makes the first device-side wait
                               unsatisfiable, so the call ends through its bounded-wait
                               path and reports BANDRED_DEV_TIMEOUT in dev_status */
-    int reserved[9];       /* must be zero */
+    int panel_group;       /* reflectors taken per grid-wide reduction in the FP64 panel
+                              factorisation: 0 = default (2), 2 (pairs) or 4 (half the grid
+                              barriers, four times the serial scalar work; slower on GB300).
+                              Both give the Householder reflectors of Section 2.1 up to
+                              rounding */
+    int reserved[8];       /* must be zero */
 } bandred_opts;
 
 /* Device-side status codes written to dev_status. */

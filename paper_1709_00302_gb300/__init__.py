@@ -43,7 +43,8 @@ class bandred_opts(ctypes.Structure):
         ("panel_ctas", ctypes.c_int),
         ("timeout_ms", ctypes.c_int),
         ("debug", ctypes.c_int),
-        ("reserved", ctypes.c_int * 9),
+        ("panel_group", ctypes.c_int),
+        ("reserved", ctypes.c_int * 8),
     ]
 
 
@@ -143,7 +144,7 @@ def lib():
 
 
 def make_opts(b: int = 0, lookahead: int = -1, precision="fp64", slices: int = 0, panel_ctas: int = 0,
-              timeout_ms: int = 0, debug: int = 0) -> bandred_opts:
+              timeout_ms: int = 0, debug: int = 0, panel_group: int = 0) -> bandred_opts:
     o = bandred_opts()
     lib().bandred_default_opts(ctypes.byref(o))
     o.b = b
@@ -153,6 +154,7 @@ def make_opts(b: int = 0, lookahead: int = -1, precision="fp64", slices: int = 0
     o.panel_ctas = panel_ctas
     o.timeout_ms = timeout_ms
     o.debug = debug
+    o.panel_group = panel_group
     return o
 
 

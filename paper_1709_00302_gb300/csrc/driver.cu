@@ -114,6 +114,7 @@ int resolve_options(const bandred_opts* in, int64_t w, Options* o) {
   if (d.precision < 0 || d.precision > 3) return -1;
   if (d.panel_ctas < 0 || d.timeout_ms < 0) return -1;
   if (d.debug < 0 || d.debug > 1) return -1;
+  if (d.panel_group != 0 && d.panel_group != 2 && d.panel_group != 4) return -1;
   o->b = d.b;
   o->lookahead = d.lookahead;
   o->precision = d.precision;
@@ -121,6 +122,7 @@ int resolve_options(const bandred_opts* in, int64_t w, Options* o) {
   o->panel_ctas = d.panel_ctas;
   o->limit_ns = (unsigned long long)(d.timeout_ms ? d.timeout_ms : 2000) * 1000000ull;
   o->debug = d.debug;
+  o->panel_group = d.panel_group ? d.panel_group : 2;
   return 0;
 }
 
@@ -166,7 +168,7 @@ static Sy2sbWs carve_sy2sb(void* work, int64_t n, int64_t w, const Options& o, i
     ws.Z[q] = q < nbuf ? c.take<double>(b * std::max<int64_t>(w, 1)) : ws.Z[0];
     ws.splitk[q] = q < nbuf ? c.take<double>(ws.splitk_cap) : ws.splitk[0];
   }
-  ws.rowbuf = c.take<double>(4 * (size_t)b);  // two rows per step, two steps
+  ws.rowbuf = c.take<double>(8 * (size_t)b);  // up to four rows per step, two steps
   ws.part2 = c.take<double>((size_t)kPanelCtasPerSm * sms);
   ws.gs = c.take<GridSync>(1);  // 256 bytes, immediately followed by the accumulators
   ws.part = c.take<double>((panel_sync_bytes((int)b) - 256) / sizeof(double));
@@ -231,7 +233,7 @@ static Ge2gbWs carve_ge2gb(void* work, int64_t m, int64_t n, const Options& o, i
     ws.Z[q] = q < nbuf ? c.take<double>(b * ws.ldv) : ws.Z[0];
     ws.splitk[q] = q < nbuf ? c.take<double>(ws.splitk_cap) : ws.splitk[0];
   }
-  ws.rowbuf = c.take<double>(4 * (size_t)b);  // two rows per step, two steps
+  ws.rowbuf = c.take<double>(8 * (size_t)b);  // up to four rows per step, two steps
   ws.part2 = c.take<double>((size_t)kPanelCtasPerSm * sms);
   ws.gs = c.take<GridSync>(1);  // 256 bytes, immediately followed by the accumulators
   ws.part = c.take<double>((panel_sync_bytes((int)b) - 256) / sizeof(double));
@@ -335,6 +337,15 @@ static int run_panel(double* A, int64_t rs, int64_t cs, int j, int bk, double* t
   p.extra = extra;
   p.w_in_smem = w_smem;
   p.w_fp32 = is_split(o);
+  // four reflectors per grid-wide reduction when the caller asks for them and their larger
+  // shared-memory footprint fits; pairs otherwise (the default: on GB300 the four-reflector
+  // derivation's serial FP64 work costs more than the grid barrier it saves)
+  constexpr size_t kSmemMax = 226 * 1024;  // the opt-in limit less the kernel's static shared memory
+  if (o.panel_group == 4 && panel4_smem_bytes(bk, Rp, false) <= kSmemMax) {
+    p.w_in_smem = panel4_smem_bytes(bk, Rp, true) <= kSmemMax;
+    CK(launch_panel4(p, G, s));
+    return 0;
+  }
   CK(launch_panel(p, G, s));
   return 0;
 }

@@ -16,6 +16,7 @@ struct Options {
   int panel_ctas;
   unsigned long long limit_ns;
   int debug;
+  int panel_group;  // reflectors per grid-wide reduction of the panel: 2 (default) or 4
 };
 
 // Records a failed CUDA call (readable through bandred_last_error) and returns

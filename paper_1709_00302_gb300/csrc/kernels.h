@@ -18,8 +18,8 @@ struct PanelParams {
   double* Y;             // j x bk, column-major, ld = ldy (unit lower trapezoidal copy of V)
   double* W;             // j x bk, column-major, ld = ldy (W = -Y T)
   int64_t ldy;
-  double* acc;           // 3 * (2 bk + 2) * 32 doubles, directly after *gs (zeroed with it)
-  double* rowbuf;        // 4 * bk doubles
+  double* acc;           // 3 * (4 bk + 2) * 32 doubles, directly after *gs (zeroed with it)
+  double* rowbuf;        // 8 * bk doubles
   double* part2;         // G doubles
   GridSync* gs;
   int* status;
@@ -33,6 +33,10 @@ size_t panel_smem_bytes(int bk, int Rp, bool w_in_smem);
 size_t panel_sync_bytes(int bk);  // bytes from gs to the end of acc
 int panel_geometry(int j, int bk, int max_ctas, int min_rows, int* G, int* R, int* Rp, bool* w_in_smem);
 cudaError_t launch_panel(const PanelParams& p, int G, cudaStream_t s);
+// The same factorisation with up to four reflectors per grid-wide reduction (panel4.cu):
+// same parameters, geometry and outputs; its shared memory is panel4_smem_bytes.
+size_t panel4_smem_bytes(int bk, int Rp, bool w_in_smem);
+cudaError_t launch_panel4(const PanelParams& p, int G, cudaStream_t s);
 
 // One thread-block cluster of C CTAs per panel (panel_cluster.cu).  `single` (host
 // struct) or `dev_probs` (device array of nprob structs, inactive when bk == 0) gives the

@@ -434,7 +434,9 @@ size_t panel_smem_bytes(int bk, int Rp, bool w_in_smem) {
   return ((size_t)bk * Rp * (w_in_smem ? 2 : 1) + 7 * (size_t)bk + 2) * sizeof(double);
 }
 
-size_t panel_sync_bytes(int bk) { return 256 + 3 * (size_t)(2 * bk + 2) * kAccStride * sizeof(double); }
+// three rotating accumulator buffers of 4 bk + 2 sums (the four-reflector kernel's size; the
+// pair kernel uses the first 2 bk + 2 of each)
+size_t panel_sync_bytes(int bk) { return 256 + 3 * (size_t)(4 * bk + 2) * kAccStride * sizeof(double); }
 
 int panel_geometry(int j, int bk, int max_ctas, int min_rows, int* G, int* R, int* Rp, bool* w_in_smem) {
   if (j <= 0 || bk <= 0) return -1;

@@ -147,3 +147,52 @@ def test_short_form_allocates_and_matches(br):
     tau = torch.zeros(n - w, dtype=torch.float64, device="cuda")
     assert br.bandred_sy2sb(dA, w, tau) == 0
     check_sy2sb_parity(A, to_host(dA), tau.cpu().numpy(), w)
+
+
+# Panels taller than one thread-block cluster holds (j > 512) run on the cooperative grid
+# kernel, which takes its reflectors either in pairs or in groups of four per grid-wide
+# reduction (option panel_group); both must give the oracle's reflectors.  Orthogonality of
+# the Q formed from them is bounded by 3e-16 n (the oracle's own reaches about 8e-17 n).
+@pytest.mark.parametrize("group", [2, 4])
+@pytest.mark.parametrize("n,w,b,la", [(1200, 64, 64, 0), (1100, 40, 16, -1), (1030, 21, 5, 0), (1100, 64, 32, -1)])
+def test_sy2sb_grid_panel_parity(br, n, w, b, la, group):
+    A = workloads.sym_gaussian(n, seed=n + b + group)
+    Aout, tau = run_sy2sb(br, A, w, b=b, lookahead=la, panel_group=group)
+    check_sy2sb_parity(A, Aout, tau, w)
+    r = sym_report(A, Aout, tau, w)
+    assert r["backward"] < 1e-13 and r["orth"] < 3e-16 * n and r["eig"] < 1e-13, r
+
+
+@pytest.mark.parametrize("group", [2, 4])
+def test_ge2gb_grid_panel_parity(br, group):
+    m, n, w, b = 1100, 900, 24, 8
+    A = workloads.gen_gaussian(m, n, seed=7 + group)
+    dA = to_dev(A)
+    _, tq, tp, _ = br.ge2gb(dA, w, br.make_opts(b=b, lookahead=-1, panel_group=group))
+    Aout, tq, tp = to_host(dA), tq.cpu().numpy(), tp.cpu().numpy()
+    Ao, tqo, tpo = oracle.ge2gb(A, w)
+    fa = np.linalg.norm(A)
+    i, j = np.indices((m, n))
+    band = (j - i >= 0) & (j - i <= w)
+    assert np.max(np.abs(Aout[band] - Ao[band])) <= B_TOL * fa
+    assert np.max(np.abs(Aout[~band] - Ao[~band]), initial=0.0) <= V_TOL
+    assert np.max(np.abs(tq - tqo), initial=0.0) <= V_TOL
+    assert np.max(np.abs(tp - tpo), initial=0.0) <= V_TOL
+    r = gen_report(A, Aout, tq, tp, w)
+    assert r["backward"] < 1e-13 and r["sv"] < 1e-13, r
+
+
+@pytest.mark.parametrize("group", [2, 4])
+def test_sy2sb_rank_deficient_grid_panels(br, group):
+    """A symmetric matrix of rank 30: the trailing panels' columns become dependent, the
+    grouped reflectors hit their cancellation guard and fall back to fewer per reduction.
+    The reflectors of a rank-deficient panel are set by rounding, so the checks are the
+    invariants: backward error, orthogonality and the spectrum."""
+    n, w, b = 1100, 32, 32
+    rng = np.random.Generator(np.random.PCG64(41))
+    U, _ = np.linalg.qr(rng.standard_normal((n, 30)))
+    A = (U * rng.uniform(0.5, 2.0, 30)) @ U.T
+    A = np.asfortranarray((A + A.T) / 2)
+    Aout, tau = run_sy2sb(br, A, w, b=b, lookahead=0, panel_group=group)
+    r = sym_report(A, Aout, tau, w)
+    assert r["backward"] < 1e-13 and r["orth"] < 3e-16 * n and r["eig"] < 1e-13, r
