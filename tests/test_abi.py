@@ -90,3 +90,30 @@ def test_product_path_does_not_import_the_oracle():
     code = ("import sys; import paper_1709_00302_gb300 as br; br.lib(); "
             "assert 'oracle' not in sys.modules, 'oracle imported by the product path'")
     subprocess.run([sys.executable, "-c", code], check=True, cwd=ROOT)
+
+
+def test_python_opts_struct_mirrors_the_header(L):
+    """The binding's bandred_opts has the header's fields, in order, all int, and the same
+    size (a layout slip would shift every option the library reads)."""
+    import paper_1709_00302_gb300 as br
+
+    hdr = open(os.path.join(ROOT, "include", "bandred.h")).read()
+    body = re.search(r"typedef struct bandred_opts \{(.*?)\} bandred_opts;", hdr, flags=re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"\bint\s+([a-z_]+)(?:\[(\d+)\])?\s*;", body)
+    assert [name for name, _ in fields] == [name for name, _ in br.bandred_opts._fields_]
+    count = sum(int(n) if n else 1 for _, n in fields)
+    assert ctypes.sizeof(br.bandred_opts) == 4 * count
+    for (name, n), (pname, ptype) in zip(fields, br.bandred_opts._fields_):
+        want = ctypes.c_int * int(n) if n else ctypes.c_int
+        assert ctypes.sizeof(ptype) == ctypes.sizeof(want), name
+
+
+def test_panel_group_is_validated(L):
+    import paper_1709_00302_gb300 as br
+
+    fake = ctypes.c_void_p(4096)
+    null = ctypes.c_void_p(0)
+    for bad_group in (1, 3, 8, -2):
+        o = br.make_opts(b=2, panel_group=bad_group)
+        assert L.bandred_sy2sb_ex(10, 4, fake, 10, fake, ctypes.byref(o), null, 0, null, null) == -6
