@@ -68,23 +68,29 @@ def load_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi samples (every 200 ms) while the timed region runs."""
+    """nvidia-smi samples (every 100 ms) kept for the timed region only: the sampler starts
+    before the warm-up (so that nvidia-smi is already running when the timed steps begin),
+    each line is stamped with its arrival time, and the statistics use the lines that
+    arrived between mark_start() and one interval after mark_end()."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    INTERVAL_MS = 100
 
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.lines = []
+        self.lines = []  # (arrival time, line)
         self.thread = None
+        self.t0 = None
+        self.t1 = None
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", str(self.INTERVAL_MS)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
             return
@@ -93,7 +99,15 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
+
+    def mark_start(self):
+        self.t0 = time.monotonic()
+
+    def mark_end(self):
+        self.t1 = time.monotonic()
+        if self.proc is not None:  # let the sample that covers the end of the region arrive
+            time.sleep(1.5 * self.INTERVAL_MS / 1e3)
 
     def stop(self):
         if self.proc is None:
@@ -105,9 +119,13 @@ class ClockSampler:
             self.proc.kill()
         if self.thread:
             self.thread.join(timeout=2)
+        lo = self.t0 if self.t0 is not None else float("-inf")
+        hi = (self.t1 + self.INTERVAL_MS / 1e3) if self.t1 is not None else float("inf")
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for t, ln in self.lines:
+            if not lo <= t <= hi:
+                continue
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -440,19 +458,21 @@ def bench_batched(args, br, dev, stream, world, rank, dist):
         launches_per_step = br.bandred_launch_count() - l0
     # replays run on the current stream: make it the stream the events are recorded on
     with torch.cuda.stream(cap):
+        sampler = ClockSampler(dev.index or 0)
+        sampler.start()
         for _ in range(args.warmup):
             graph.replay()
         torch.cuda.synchronize(dev)
         if dist is not None:
             dist.barrier()
-        sampler = ClockSampler(dev.index or 0)
-        sampler.start()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        sampler.mark_start()
         for e0, e1 in ev:
             e0.record(cap)
             graph.replay()
             e1.record(cap)
         torch.cuda.synchronize(dev)
+        sampler.mark_end()
     clocks = sampler.stop()
     ms = [a.elapsed_time(b) for a, b in ev]
     assert int(st.sum().item()) == 0, st
@@ -615,6 +635,8 @@ def main():
         torch.cuda.synchronize(dev)
 
     def timed_steps(call, steps, warmup, profile=False):
+        sampler = ClockSampler(local)
+        sampler.start()
         for _ in range(warmup):
             A.copy_(A0)
             call(A)
@@ -623,14 +645,14 @@ def main():
         l0 = br.bandred_launch_count()
         if profile:
             br.bandred_profile_begin()
-        sampler = ClockSampler(local)
-        sampler.start()
+        sampler.mark_start()
         for e0, e1 in ev:
             A.copy_(A0)
             e0.record(stream)
             call(A)
             e1.record(stream)
         barrier()
+        sampler.mark_end()
         clocks = sampler.stop()
         stats = br.bandred_profile_end() if profile else []
         launches = br.bandred_launch_count() - l0
