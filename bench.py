@@ -226,7 +226,8 @@ def reference_arm(args, n, w, b):
         def step():
             oracle.ge2gb(A, w, ncols=ncols)
         units = ge2gb_sample_flops(n, n, w, ncols)
-        desc = f"ge2gb m=n={n} w={w} b={b} N(0,1) FP64 (bounded sample: first {ncols} columns per step)"
+        desc = (f"ge2gb m=n={n} w={w} b={b} N(0,1) precision=fp64 "
+                f"(FP64 oracle; bounded sample: first {ncols} columns per step)")
         sample = f"first {ncols} of {n} left/right reflector pairs per step"
         dtype_cfg = {"m": n, "n": n, "w": w, "b": b}
     else:
@@ -234,13 +235,15 @@ def reference_arm(args, n, w, b):
             G = np.random.Generator(np.random.PCG64(0)).standard_normal((n, n))
             A = np.asfortranarray((G + G.T) * 0.5)
             del G
+            base = f"sy2sb n={n} w={w} b={b} N(0,1) symmetrised (drawn on the host: same distribution)"
         else:
             A, _ = workloads.sym_known_spectrum(n, 0, 1)
+            base = f"sy2sb n={n} w={w} b={b} known-spectrum (lam log-uniform [1e-6,1], random signs)"
 
         def step():
             oracle.sy2sb(A, w, ncols=ncols)
         units = sample_flops(n, w, ncols)
-        desc = f"sy2sb n={n} w={w} b={b} FP64 (bounded sample: first {ncols} reflectors per step)"
+        desc = f"{base} precision=fp64 (FP64 oracle; bounded sample: first {ncols} reflectors per step)"
         sample = f"first {ncols} of {n - w} reflectors per step"
         dtype_cfg = {"n": n, "w": w, "b": b}
     for _ in range(args.warmup):
