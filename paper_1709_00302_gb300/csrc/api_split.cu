@@ -154,8 +154,16 @@ int bandred_syr2k_split(int64_t n, int64_t kb, const double* X, int64_t ldx, con
   if (precision == BANDRED_OZAKI) {
     if (dev_status && cudaMemsetAsync(dev_status, 0, sizeof(int), stream) != cudaSuccess) return BANDRED_ERR_CUDA;
     const ozaki::Bufs b = ozaki::carve(work, (int)n, (int)n, (int)(2 * kb), 1);
-    const ozaki::Operand opA{X, ldx, 0, (int)kb, Y, ldy, 0, (int)kb, (int)n};  // [X | Y]
-    const ozaki::Operand opB{Y, ldy, 0, (int)kb, X, ldx, 0, (int)kb, (int)n};  // [Y | X]
+    // [X 2^-sigma | Y 2^sigma] and [Y 2^sigma | X 2^-sigma]: the same product, with the two
+    // halves of each row brought near one magnitude (the largest exponents of X and Y go
+    // in the last 256 bytes of the workspace)
+    int* sh = reinterpret_cast<int*>(static_cast<char*>(work) + ozaki::bytes((int)n, (int)n, (int)(2 * kb), 1, false));
+    ozaki::Operand opA{X, ldx, 0, (int)kb, Y, ldy, 0, (int)kb, (int)n};  // [X | Y]
+    ozaki::Operand opB{Y, ldy, 0, (int)kb, X, ldx, 0, (int)kb, (int)n};  // [Y | X]
+    opA.sh = opB.sh = sh;
+    opA.shsign = 1;
+    opB.shsign = -1;
+    if (ozaki::balance(opA, sh, stream) != cudaSuccess) return BANDRED_ERR_CUDA;
     if (ozaki::prepare(opA, opB, b, stream) != cudaSuccess) return BANDRED_ERR_CUDA;
     if (ozaki::rank_apply((int)n, (int)n, (int)(2 * kb), 1.0, C, ldc, 0, (int)n, 1, b, dev_status,
                           2000ull * 1000000ull, stream) != cudaSuccess)

@@ -18,9 +18,8 @@ struct PanelParams {
   double* Y;             // j x bk, column-major, ld = ldy (unit lower trapezoidal copy of V)
   double* W;             // j x bk, column-major, ld = ldy (W = -Y T)
   int64_t ldy;
-  double* acc;           // 3 * (4 bk + 2) * 32 doubles, directly after *gs (zeroed with it)
+  double* acc;           // 3 * panel_acc_entries(bk) * 32 doubles, directly after *gs (zeroed with it)
   double* rowbuf;        // 8 * bk doubles
-  double* part2;         // G doubles
   GridSync* gs;
   int* status;
   unsigned long long limit_ns;

@@ -46,6 +46,19 @@ __device__ __forceinline__ double elem(const double* M, int64_t ld, int mode, in
 }
 
 // ---------------------------------------------------------------- row exponents
+// sigma of a balanced two-source operand (see Operand in ozaki.h)
+__device__ __forceinline__ int balance_sigma(const int* sh) {
+  if (!sh) return 0;
+  const int a = sh[0], b = sh[1];
+  return (a && b) ? (a - b) >> 1 : 0;
+}
+
+// biased exponent of x 2^shift for a nonzero x (kept >= 1), 0 for x = 0
+__device__ __forceinline__ int shifted_exp(double x, int shift) {
+  const int v = biased_exp(x);
+  return v ? max(v + shift, 1) : 0;
+}
+
 // e[0 .. n) = 0, as a kernel of the launch chain (a memset would end the programmatic
 // overlap of the kernels around it); it waits for the previous kernel, which may still
 // read the array.
@@ -56,16 +69,17 @@ __global__ void zero_kernel(int* e, int n) {
 
 // entries M[r + k ld]: one 32 x 32 tile per block (lanes along rows, eight warps of four
 // columns each), row maxima combined across the warps
-__global__ void rowexp_cols_kernel(const double* M, int64_t ld, int R, int K, int* e) {
+__global__ void rowexp_cols_kernel(const double* M, int64_t ld, int R, int K, int* e, const int* sh, int dir) {
   __shared__ int rowmax[8][32];
   pdl_wait_and_release();
+  const int shift = dir * balance_sigma(sh);
   const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
   const int i = blockIdx.x * 32 + lane;
   int m = 0;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int k = blockIdx.y * 32 + wy * 4 + q;
-    if (i < R && k < K) m = max(m, biased_exp(M[i + (int64_t)k * ld]));
+    if (i < R && k < K) m = max(m, shifted_exp(M[i + (int64_t)k * ld], shift));
   }
   rowmax[wy][lane] = m;
   __syncthreads();
@@ -77,8 +91,10 @@ __global__ void rowexp_cols_kernel(const double* M, int64_t ld, int R, int K, in
 }
 
 // entries M[k + r ld] (k in [k0, k1), k > r when `upper`): one warp per row
-__global__ void rowexp_rows_kernel(const double* M, int64_t ld, int R, int k0, int k1, int upper, int* e) {
+__global__ void rowexp_rows_kernel(const double* M, int64_t ld, int R, int k0, int k1, int upper, int* e,
+                                   const int* sh, int dir) {
   pdl_wait_and_release();
+  const int shift = dir * balance_sigma(sh);
   const int r = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x & 31;
   if (r >= R) return;
   const int per = (k1 - k0 + gridDim.y - 1) / gridDim.y;
@@ -86,7 +102,7 @@ __global__ void rowexp_rows_kernel(const double* M, int64_t ld, int R, int k0, i
   const int ke = min(k1, kb + per);
   if (upper) kb = max(kb, r + 1);
   int m = 0;
-  for (int k = kb + lane; k < ke; k += 32) m = max(m, biased_exp(M[k + (int64_t)r * ld]));
+  for (int k = kb + lane; k < ke; k += 32) m = max(m, shifted_exp(M[k + (int64_t)r * ld], shift));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
   if (lane == 0 && m) atomicMax(&e[r], m);
@@ -136,6 +152,33 @@ __global__ void rowexp_sym_kernel(const double* M, int64_t ld, int R, int* e) {
   }
 }
 
+// largest biased exponent of each source of a two-source operand into sh[0], sh[1]: one
+// 32 x 32 tile of source blockIdx.z per block
+__global__ void maxexp_kernel(Operand op, int* sh) {
+  __shared__ int wmax[8];
+  pdl_wait_and_release();
+  const int src = blockIdx.z;
+  const double* M = src ? op.M2 : op.M1;
+  const int64_t ld = src ? op.ld2 : op.ld1;
+  const int mode = src ? op.mode2 : op.mode1, K = src ? op.K2 : op.K1;
+  const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + lane;
+  int m = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int k = blockIdx.y * 32 + wy * 4 + q;
+    if (M && i < op.R && k < K) m = max(m, biased_exp(elem(M, ld, mode, i, k)));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) wmax[wy] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 1; q < 8; ++q) m = max(m, wmax[q]);
+    if (m) atomicMax(&sh[src], m);
+  }
+}
+
 // ---------------------------------------------------------------- digits
 // x -> its 7 balanced digits (most significant first) as FP32 values, row exponent E.
 // F = round(x 2^(56 - (E - 1021))) is a 56-bit integer, |F| < 2^55.  Adding
@@ -182,6 +225,7 @@ __global__ void pack_kernel(Operand op, const int* e, int TR, int nrb, int nkb, 
   const int groups = TR * (kDepth / 8);
   const int64_t total = (int64_t)nrb * nkb * groups;
   const int K = op.K1 + op.K2;
+  const int sigma = op.shsign * balance_sigma(op.sh);  // M1 entries times 2^-sigma, M2 entries times 2^sigma
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
     const int within = (int)(g % groups);
     const int64_t tile = g / groups;
@@ -194,9 +238,12 @@ __global__ void pack_kernel(Operand op, const int* e, int TR, int nrb, int nkb, 
     for (int kk = 0; kk < 8; ++kk) {
       const int k = kb * kDepth + kg * 8 + kk;
       double x = 0.0;
-      if (row < op.R && k < K)
+      int Es = E;
+      if (row < op.R && k < K) {
         x = k < op.K1 ? elem(op.M1, op.ld1, op.mode1, row, k) : elem(op.M2, op.ld2, op.mode2, row, k - op.K1);
-      digits(x, E, d[kk]);
+        Es = k < op.K1 ? E + sigma : E - sigma;
+      }
+      digits(x, Es, d[kk]);
     }
     // the block's S planes stacked along the rows: one S TR x kDepth K-major operand, so
     // that consecutive planes form one wider MMA operand
@@ -964,7 +1011,7 @@ cudaError_t row_exponents(const Operand& op, int* e, cudaStream_t s) {
   prof::count_launch();
   cudaError_t err = launch_pdl(zero_kernel, dim3((unsigned)std::min(1024, (op.R + 255) / 256)), dim3(256), 0, s, e, op.R);
   if (err != cudaSuccess) return err;
-  auto one = [&](const double* M, int64_t ld, int mode, int K) -> cudaError_t {
+  auto one = [&](const double* M, int64_t ld, int mode, int K, int dir) -> cudaError_t {
     if (K <= 0 || !M) return cudaSuccess;
     const int ks = std::max(1, std::min(64, K / 256));
     if (mode == 2) {
@@ -975,20 +1022,30 @@ cudaError_t row_exponents(const Operand& op, int* e, cudaStream_t s) {
     if (mode == 0) {
       prof::count_launch();
       if (cudaError_t le = launch_pdl(rowexp_cols_kernel, dim3((op.R + 31) / 32, (K + 31) / 32), dim3(256), 0, s, M, ld,
-                                      op.R, K, e))
+                                      op.R, K, e, op.sh, dir))
         return le;
     }
     if (mode == 1) {
       prof::count_launch();
       if (cudaError_t le = launch_pdl(rowexp_rows_kernel, dim3((op.R + 7) / 8, ks), dim3(256), 0, s, M, ld, op.R, 0, K, 0,
-                                      e))
+                                      e, op.sh, dir))
         return le;
     }
     return cudaGetLastError();
   };
-  err = one(op.M1, op.ld1, op.mode1, op.K1);
+  err = one(op.M1, op.ld1, op.mode1, op.K1, op.sh ? -op.shsign : 0);
   if (err != cudaSuccess) return err;
-  return one(op.M2, op.ld2, op.mode2, op.K2);
+  return one(op.M2, op.ld2, op.mode2, op.K2, op.sh ? op.shsign : 0);
+}
+
+cudaError_t balance(const Operand& op, int* sh, cudaStream_t s) {
+  prof::count_launch();
+  cudaError_t err = launch_pdl(zero_kernel, dim3(1), dim3(32), 0, s, sh, 2);
+  if (err != cudaSuccess) return err;
+  const int K = std::max(std::max(op.K1, op.K2), 1);
+  if (op.R <= 0) return cudaSuccess;
+  prof::count_launch();
+  return launch_pdl(maxexp_kernel, dim3((op.R + 31) / 32, (K + 31) / 32, 2), dim3(256), 0, s, op, sh);
 }
 
 size_t packed_bytes(int R, int K, int TR) {
@@ -1188,7 +1245,7 @@ cudaError_t product(const Operand& A, const Operand& B, int M, int N, int K, dou
 }
 
 cudaError_t rank_apply(int M, int N, int K, double alpha, double* C, int64_t ldc, int col0, int col1, int lower,
-                       const Bufs& b, int* status, unsigned long long limit_ns, cudaStream_t s) {
+                       const Bufs& b, int* status, unsigned long long limit_ns, cudaStream_t s, int max_ctas) {
   if (M <= 0 || N <= 0 || col1 <= col0) return cudaSuccess;
   GemmParams p{};
   p.A = b.Ablob;
@@ -1225,8 +1282,9 @@ cudaError_t rank_apply(int M, int N, int K, double alpha, double* C, int64_t ldc
     valid += lower ? std::max(0, nI - (J * kTileB) / kTileA) : nI;
   if (valid == 0) return cudaSuccess;
   const int64_t all = (int64_t)nI * nJ;
+  const int cap = max_ctas > 0 ? std::min(max_ctas, sms) : sms;
   const int grid =
-      (int)std::max<int64_t>(std::min<int64_t>(sms, valid), (all + kMaxTilesPerCta - 1) / kMaxTilesPerCta);
+      (int)std::max<int64_t>(std::min<int64_t>(cap, valid), (all + kMaxTilesPerCta - 1) / kMaxTilesPerCta);
   prof::count_launch();
   return launch_pdl(rank_kernel, dim3(grid), dim3(kRankThreads), smem, s, p);
 }

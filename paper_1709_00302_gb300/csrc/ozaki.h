@@ -21,6 +21,11 @@ constexpr int kDepth = 16;   // reduction depth of one packed block (one pipelin
 // An operand op(X) with rows r and reduction index k, possibly two matrices side by side
 // along k (k < K1 from M1, then M2).  mode: 0 = M[r + k ld], 1 = M[k + r ld], 2 = symmetric
 // with the lower triangle stored (R == K; only for a single source).
+// With `sh` set (two sources), the entries of M1 are taken times 2^(-shsign sigma) and those
+// of M2 times 2^(+shsign sigma), sigma = floor((sh[0] - sh[1]) / 2) from the largest biased
+// exponents sh[0], sh[1] that `balance` writes (sigma = 0 when either source is zero).  A
+// product of two such operands with opposite shsign is unchanged, and the two halves of
+// every row meet near the same magnitude, so neither is lost below the row's scale.
 struct Operand {
   const double* M1;
   int64_t ld1;
@@ -29,7 +34,12 @@ struct Operand {
   int64_t ld2;
   int mode2, K2;
   int R;
+  const int* sh = nullptr;
+  int shsign = 0;
 };
+
+// sh[0], sh[1] = the largest biased exponents of the two sources of op (0 for a zero source).
+cudaError_t balance(const Operand& op, int* sh, cudaStream_t s);
 
 // Largest biased FP64 exponent of every row of op (0 for a zero row) into e[0..R).
 cudaError_t row_exponents(const Operand& op, int* e, cudaStream_t s);
@@ -92,9 +102,11 @@ cudaError_t product(const Operand& A, const Operand& B, int M, int N, int K, dou
 // entries as that row of A (in another order), and B's exponents are not computed again.
 cudaError_t prepare(const Operand& A, const Operand& B, const Bufs& b, cudaStream_t s);
 // C += alpha opA opB^T on columns [col0, col1) (and the lower triangle when `lower`), from
-// operands packed by prepare (several calls, on any streams, may share them).
+// operands packed by prepare (several calls, on any streams, may share them).  One
+// persistent CTA per SM, or at most max_ctas CTAs (> 0), so that another kernel can hold
+// the remaining SMs at the same time.
 cudaError_t rank_apply(int M, int N, int K, double alpha, double* C, int64_t ldc, int col0, int col1, int lower,
-                       const Bufs& b, int* status, unsigned long long limit_ns, cudaStream_t s);
+                       const Bufs& b, int* status, unsigned long long limit_ns, cudaStream_t s, int max_ctas = 0);
 
 }  // namespace ozaki
 }  // namespace bandred

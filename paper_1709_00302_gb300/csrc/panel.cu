@@ -57,9 +57,8 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
   double* wl = p.w_in_smem ? after : p.W + rb;
   float* wlf = reinterpret_cast<float*>(after);
   const int64_t wld = p.w_in_smem ? Rp : p.ldy;
-  __shared__ double s_beta, s_tau, s_scal, s_beta2, s_tau2, s_scal2, s_zb, s_Taa, s_Tab;
+  __shared__ double s_beta, s_tau, s_scal, s_dscal, s_beta2, s_tau2, s_scal2, s_zb, s_Taa, s_Tab;
   __shared__ double s_ptau[2];
-  __shared__ double s_red[NT / 32];
   __shared__ int s_rescale, s_ok, s_pair;
 
   if (p.rs == 1) {
@@ -98,7 +97,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
   const int TPC = bk >= 128 ? 2 : (bk >= 64 ? 4 : 8);
   const int CPP = NT / TPC;  // columns per pass
   const int sub = tid % TPC;
-  const size_t accsz = (size_t)(2 * bk + 2) * kAccStride;
+  const size_t accsz = panel_acc_entries(bk) * kAccStride;
   unsigned int gen = 0;
   int npend = 0, pend_i = 0;
   for (int i = 0, step = 0; i < bk; ++step) {
@@ -117,6 +116,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
     if (g == 0) {  // clear the buffer of the next step (last read two steps ago)
       double* nxt = p.acc + (size_t)((step + 1) % 3) * accsz;
       for (int v = tid; v < 2 * bk + 2; v += NT) nxt[(size_t)v * kAccStride] = 0.0;
+      for (int v = tid; v < bk; v += NT) nxt[(size_t)(kRescaleSlot * bk + 2 + v) * kAccStride] = 0.0;
     }
 
     // Partial dot products over this CTA's rows below row i, added into L2 accumulators.
@@ -206,6 +206,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
       s_beta = beta;
       s_tau = tau;
       s_scal = scal;
+      s_dscal = scal;
       // Second reflector.  With a = column i, b = column i + 1 and sums over rows >= i + 1
       // (S_aa, S_ab, S_bb), H_i b = b - z_b v_i has z_b = tau (b_i + scal S_ab); below row
       // i + 1 its entries are b_r - zs a_r (zs = z_b scal), so their squared norm is
@@ -250,46 +251,56 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
       // W columns of the previous step, hidden behind thread 0's scalar chain
       pending_w(npend, pend_i, false);
     }
-    __syncthreads();
+    // A sum outside the range where the plain formulas hold (not finite, or near the
+    // overflow threshold, as when some entries exceed 2^500) forces the scaled path too.
+    int bad = 0;
+    if (tid >= 32) {
+      const int nsum = want_pair ? 2 * bk + 1 : bk + 1;
+      for (int v = tid - 32; v < nsum; v += NT - 32) bad |= !(fabs(dsum[v]) < 0x1p1000);
+    }
+    const int force = __syncthreads_or(bad);
 
-    // Rare path: the plain sum of squares over/underflows (or |alpha| is huge): a scaled
-    // second pass over x2 and the overflow-safe formulas.  Same decision in every CTA.
-    if (s_rescale) {
-      const double inv = dsum[bk] > 0.0 ? 1.0 / dsum[bk] : 0.0;
-      double s = 0.0;
-      for (int r = lo + tid; r < nr; r += NT) {
-        const double t = xa[r] * inv;
-        s = fma(t, t, s);
-      }
-      s = warp_sum(s);
-      if (lane == 0) s_red[tid >> 5] = s;
-      __syncthreads();
-      if (tid == 0) {
-        double t = 0.0;
-        for (int q = 0; q < NT / 32; ++q) t += s_red[q];
-        __stcg(&p.part2[g], t);
+    // Rare path: the plain sums over/underflow (or |alpha| is huge).  Column i is scaled
+    // by the power of two 2^-e with 2^e <= max|x2| < 2^(e+1) (exact), and a second
+    // reduction forms ||x2 2^-e||^2 and the dot products (x2 2^-e)^T a_c of every column,
+    // so no square or product leaves the range; the coefficients then take scal 2^e for
+    // the dot terms.  One reflector this step.  Same decision in every CTA.
+    if (s_rescale || force) {
+      const double amax = dsum[bk];
+      const int e = amax > 0.0 ? max(-1022, min(1022, ilogb(amax))) : 0;
+      const double inv = ldexp(1.0, -e), sc = ldexp(1.0, e);
+      double* resc = acc + (size_t)(kRescaleSlot * bk + 2) * kAccStride;
+      for (int c0 = 0; c0 < bk; c0 += CPP) {
+        const int c = c0 + tid / TPC;
+        double sv = 0.0;
+        if (c < bk) {
+          const double* ac = slab + (size_t)c * Rp;
+          for (int r = lo + sub; r < nr; r += TPC) {
+            const double t = xa[r] * inv;
+            sv = fma(t, c == i ? t : ac[r], sv);
+          }
+        }
+        for (int o = TPC / 2; o > 0; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
+        if (sub == 0 && c < bk) atomicAdd(&resc[(size_t)c * kAccStride], sv);
       }
       if (!grid_barrier(p.gs, ++gen, p.extra, p.status, p.limit_ns)) return;
-      if (tid < 32) {
-        double t = 0.0;
-        for (int q = lane; q < G; q += 32) t += ldcg(&p.part2[q]);
-        t = warp_sum(t);
-        if (lane == 0) {
-          const double amax = dsum[bk];
-          const bool rescaled = (p.j - i > 1) && (amax > 0.0) && !(dsum[i] < 0x1p1000 && amax > 0x1p-450);
-          const double xnorm = rescaled ? amax * sqrt(t) : sqrt(dsum[i]);
-          const double alpha = rowi[i];
-          double tau = 0.0, beta = alpha, scal = 1.0;
-          if (p.j - i > 1 && xnorm != 0.0) {
-            const double h = hypot(alpha, xnorm);
-            beta = (alpha >= 0.0) ? -h : h;
-            tau = (beta - alpha) / beta;
-            scal = 1.0 / (alpha - beta);
-          }
-          s_beta = beta;
-          s_tau = tau;
-          s_scal = scal;
+      for (int c = tid; c < bk; c += NT) dsum[c] = ldcg(&resc[(size_t)c * kAccStride]);
+      __syncthreads();
+      if (tid == 0) {
+        const double xnorm = amax > 0.0 ? sqrt(dsum[i]) * sc : 0.0;
+        const double alpha = rowi[i];
+        double tau = 0.0, beta = alpha, scal = 1.0;
+        if (p.j - i > 1 && xnorm != 0.0) {
+          const double h = hypot(alpha, xnorm);
+          beta = (alpha >= 0.0) ? -h : h;
+          tau = (beta - alpha) / beta;
+          scal = 1.0 / (alpha - beta);
         }
+        s_beta = beta;
+        s_tau = tau;
+        s_scal = scal;
+        s_dscal = scal * sc;
+        s_pair = 0;
       }
       __syncthreads();
     }
@@ -299,7 +310,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
       if (paired) p.tau[i + 1] = s_tau2;
     }
 
-    const double tau = s_tau, scal = s_scal;
+    const double tau = s_tau, scal = s_scal, dscal = s_dscal;
     const int TPU = bk >= 128 ? 2 : (bk >= 64 ? 4 : 8);
     if (!paired) {
       // Coefficients and the in-panel update, one column per group of TPU threads:
@@ -307,7 +318,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
       for (int c0 = 0; c0 < bk; c0 += NT / TPU) {
         const int c = c0 + tid / TPU, rg = tid % TPU;
         if (c > i && c < bk) {
-          const double z = tau * fma(scal, dsum[c], rowi[c]);
+          const double z = tau * fma(dscal, dsum[c], rowi[c]);
           if (tau != 0.0) {
             const double z2 = -z * scal;
             double* ac = slab + (size_t)c * Rp;
@@ -315,7 +326,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
             if (own0 && rg == 0) ac[i - rb] -= z;
           }
         } else if (c < i && rg == 0) {
-          const double gv = fma(scal, dsum[c], rowi[c]);
+          const double gv = fma(dscal, dsum[c], rowi[c]);
           gq0[c] = gv;
           gqf0[c] = f64_to_f32_rz(gv);
         }
@@ -434,9 +445,8 @@ size_t panel_smem_bytes(int bk, int Rp, bool w_in_smem) {
   return ((size_t)bk * Rp * (w_in_smem ? 2 : 1) + 7 * (size_t)bk + 2) * sizeof(double);
 }
 
-// three rotating accumulator buffers of 4 bk + 2 sums (the four-reflector kernel's size; the
-// pair kernel uses the first 2 bk + 2 of each)
-size_t panel_sync_bytes(int bk) { return 256 + 3 * (size_t)(4 * bk + 2) * kAccStride * sizeof(double); }
+// three rotating accumulator buffers of panel_acc_entries(bk) sums each
+size_t panel_sync_bytes(int bk) { return 256 + 3 * panel_acc_entries(bk) * kAccStride * sizeof(double); }
 
 int panel_geometry(int j, int bk, int max_ctas, int min_rows, int* G, int* R, int* Rp, bool* w_in_smem) {
   if (j <= 0 || bk <= 0) return -1;

@@ -51,8 +51,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr4_kernel(PanelParams
   // on the explicit rows at the time of reflector k (s_tb); the block's T factor (s_T)
   __shared__ double s_beta[MB], s_tau[MB], s_scal[MB], s_v[MB][MB], s_coef[MB][MB], s_tb[MB][MB], s_T[MB][MB];
   __shared__ double s_ptau[MB];
-  __shared__ double s_red[NT / 32];
-  __shared__ double s_amax;
+  __shared__ double s_amax, s_dfac;
   __shared__ int s_rescale, s_ok, s_meff;
 
   if (p.rs == 1) {
@@ -89,7 +88,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr4_kernel(PanelParams
   const int TPC = bk >= 128 ? 2 : (bk >= 64 ? 4 : 8);  // threads per column in the sums
   const int CPP = NT / TPC;
   const int sub = tid % TPC;
-  const size_t accsz = (size_t)(MB * bk + 2) * kAccStride;
+  const size_t accsz = panel_acc_entries(bk) * kAccStride;
   unsigned int gen = 0;
   int npend = 0, pend_i = 0;
   for (int i = 0, step = 0; i < bk; ++step) {
@@ -105,6 +104,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr4_kernel(PanelParams
     if (g == 0) {  // clear the buffer of the next step (last read two steps ago)
       double* nxt = p.acc + (size_t)((step + 1) % 3) * accsz;
       for (int v = tid; v < MB * bk + 2; v += NT) nxt[(size_t)v * kAccStride] = 0.0;
+      for (int v = tid; v < bk; v += NT) nxt[(size_t)(kRescaleSlot * bk + 2 + v) * kAccStride] = 0.0;
     }
 
     // ---- tail sums of the block columns against every column, added into L2
@@ -193,6 +193,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr4_kernel(PanelParams
       const int rescale = (p.j - i > 1) && (amax > 0.0) && !(ssq < 0x1p1000 && amax > 0x1p-450);
       s_rescale = rescale || !(fabs(tb[0][0]) < 0x1p500);
       s_amax = amax;
+      s_dfac = 1.0;
 #pragma unroll
       for (int k = 0; k < MB; ++k)
 #pragma unroll
@@ -318,55 +319,66 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr4_kernel(PanelParams
       }
       pending_w(npend, pend_i, false);
     }
-    __syncthreads();
+    // A tail sum outside the range where the plain formulas hold (not finite, or near the
+    // overflow threshold) forces the scaled path too.
+    int bad = 0;
+    if (tid >= 32)
+      for (int v = tid - 32; v < mt * bk; v += NT - 32) bad |= !(fabs(dsum[v]) < 0x1p1000);
+    const int force = __syncthreads_or(bad);
 
-    // Rare path: the plain sum of squares of reflector 0 over/underflows (or |alpha| is
-    // huge): a scaled second pass and the overflow-safe formulas; one reflector this step.
-    if (s_rescale) {
-      const double inv = s_amax > 0.0 ? 1.0 / s_amax : 0.0;
-      double s = 0.0;
-      for (int r = lo + tid; r < nr; r += NT) {
-        const double t = x0[r] * inv;
-        s = fma(t, t, s);
-      }
-      s = warp_sum(s);
-      if (lane == 0) s_red[tid >> 5] = s;
-      __syncthreads();
-      if (tid == 0) {
-        double t = 0.0;
-        for (int q = 0; q < NT / 32; ++q) t += s_red[q];
-        __stcg(&p.part2[g], t);
+    // Rare path: the plain sums of reflector 0 over/underflow (or |alpha| is huge).  Column
+    // i is scaled by the power of two 2^-e with 2^e <= max|x2| < 2^(e+1) (exact), and a
+    // second reduction forms the tail's ||x 2^-e||^2 and the tail dot products
+    // (x 2^-e)^T a_c of every column; the dot terms then take the factor 2^e (s_dfac).
+    // One reflector this step.
+    if (s_rescale || force) {
+      const int e = s_amax > 0.0 ? max(-1022, min(1022, ilogb(s_amax))) : 0;
+      const double inv = ldexp(1.0, -e), sc = ldexp(1.0, e);
+      double* resc = acc + (size_t)(kRescaleSlot * bk + 2) * kAccStride;
+      for (int c0 = 0; c0 < bk; c0 += CPP) {
+        const int c = c0 + tid / TPC;
+        double sv = 0.0;
+        if (c < bk) {
+          const double* ac = slab + (size_t)c * Rp;
+          for (int r = lo + sub; r < nr; r += TPC) {
+            const double t = x0[r] * inv;
+            sv = fma(t, c == i ? t : ac[r], sv);
+          }
+        }
+        for (int o = TPC / 2; o > 0; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
+        if (sub == 0 && c < bk) atomicAdd(&resc[(size_t)c * kAccStride], sv);
       }
       if (!grid_barrier(p.gs, ++gen, p.extra, p.status, p.limit_ns)) return;
-      if (tid < 32) {
-        double t = 0.0;
-        for (int q = lane; q < G; q += 32) t += ldcg(&p.part2[q]);
-        t = warp_sum(t);
-        if (lane == 0) {
-          for (int sr = 1; sr < mt; ++sr) {
-            const double u = top[sr * bk + i] * inv;
-            t = fma(u, u, t);
-          }
-          const double xnorm = s_amax * sqrt(t);
-          const double alpha = top[i];
-          double tau = 0.0, beta = alpha, scal = 1.0;
-          if (p.j - i > 1 && xnorm != 0.0) {
-            const double h = hypot(alpha, xnorm);
-            beta = (alpha >= 0.0) ? -h : h;
-            tau = (beta - alpha) / beta;
-            scal = 1.0 / (alpha - beta);
-          }
-          s_beta[0] = beta;
-          s_tau[0] = tau;
-          s_scal[0] = scal;
-          for (int sr = 0; sr < MB; ++sr) {
-            s_v[0][sr] = (sr > 0 && sr < mt) ? scal * top[sr * bk + i] : 0.0;
-            s_coef[0][sr] = sr == 0 ? scal : 0.0;
-            s_tb[0][sr] = sr < mt ? top[sr * bk + i] : 0.0;
-          }
-          s_T[0][0] = tau;
-          s_meff = 1;
+      for (int c = tid; c < bk; c += NT) dsum[c] = ldcg(&resc[(size_t)c * kAccStride]);
+      __syncthreads();
+      if (tid == 0) {
+        double t = dsum[i];
+        for (int sr = 1; sr < mt; ++sr) {
+          const double u = top[sr * bk + i] * inv;
+          t = fma(u, u, t);
         }
+        const double xnorm = s_amax > 0.0 ? sqrt(t) * sc : 0.0;
+        const double alpha = top[i];
+        double tau = 0.0, beta = alpha, scal = 1.0;
+        if (p.j - i > 1 && xnorm != 0.0) {
+          const double h = hypot(alpha, xnorm);
+          beta = (alpha >= 0.0) ? -h : h;
+          tau = (beta - alpha) / beta;
+          scal = 1.0 / (alpha - beta);
+        }
+        s_beta[0] = beta;
+        s_tau[0] = tau;
+        s_scal[0] = scal;
+        for (int k = 0; k < MB; ++k)
+          for (int sr = 0; sr < MB; ++sr) {
+            s_v[k][sr] = (k == 0 && sr > 0 && sr < mt) ? scal * top[sr * bk + i] : 0.0;
+            s_coef[k][sr] = (k == 0 && sr == 0) ? scal : 0.0;
+            s_tb[k][sr] = (k == 0 && sr < mt) ? top[sr * bk + i] : 0.0;
+            s_T[k][sr] = 0.0;
+          }
+        s_T[0][0] = tau;
+        s_dfac = sc;
+        s_meff = 1;
       }
       __syncthreads();
     }
@@ -376,6 +388,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr4_kernel(PanelParams
 
     // ---- every column: w = V^T c (lane k of a group of four), z = T^T w; columns right of
     // the block get their explicit rows and tail coefficients, columns left of it the W dots
+    const double dfac = s_dfac;
     for (int c0 = 0; c0 < bk; c0 += NT / MB) {
       const int c = c0 + tid / MB, t = tid % MB;
       const bool in = c < bk && !(c >= i && c < i + meff);
@@ -387,7 +400,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr4_kernel(PanelParams
           if (s > t && s < mt) w = fma(s_v[t][s], top[s * bk + c], w);
 #pragma unroll
         for (int q = 0; q < MB; ++q)
-          if (q <= t) w = fma(s_coef[t][q], dsum[q * bk + c], w);
+          if (q <= t) w = fma(q == 0 ? s_coef[t][0] * dfac : s_coef[t][q], dsum[q * bk + c], w);
       }
       if (in && c < i && t < meff) {
         gq[t * bk + c] = w;

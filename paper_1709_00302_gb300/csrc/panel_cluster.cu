@@ -38,18 +38,18 @@ __global__ void __launch_bounds__(kPanelThreads, 4)
   const int rb = rank * R;
   const int nr = max(0, min(R, p.j - rb));
   double* slab = smem;                             // bk columns x Rp rows
-  double* part = slab + (size_t)bk * Rp;           // 2 x (bk + 2): partial sums (+ amax bits, rescale sum)
+  double* part = slab + (size_t)bk * Rp;           // 2 x (bk + 2): partial sums (+ amax bits)
   double* rowpub = part + 2 * (bk + 2);            // 2 x bk: row i, when this CTA owns it
   double* dsum = rowpub + 2 * bk;                  // bk + 1
   double* rowi = dsum + bk + 1;                    // bk
   double* gprev = rowi + bk;                       // bk
   float* gprevf = reinterpret_cast<float*>(gprev + bk);
-  double* after = gprev + bk + (bk + 1) / 2;
+  double* resc = gprev + bk + (bk + 1) / 2;        // bk: partial sums of the rare path's scaled pass
+  double* after = resc + bk;
   const bool wf32 = p.w_fp32;
   double* wl = after;                              // W rows: FP64 or FP32, always in shared memory
   float* wlf = reinterpret_cast<float*>(after);
-  __shared__ double s_beta, s_tau, s_scal, s_tau_prev;
-  __shared__ double s_red[NT / 32];
+  __shared__ double s_beta, s_tau, s_scal, s_dscal, s_tau_prev;
   __shared__ int s_rescale;
 
   if (p.rs == 1) {
@@ -155,30 +155,43 @@ __global__ void __launch_bounds__(kPanelThreads, 4)
       s_beta = beta;
       s_tau = tau;
       s_scal = scal;
+      s_dscal = scal;
     }
-    __syncthreads();
-    if (s_rescale) {  // same decision in every CTA of the cluster
+    // A sum outside the range where the plain formulas hold (not finite, or near the
+    // overflow threshold) forces the scaled path too.
+    int bad = 0;
+    for (int v = tid; v < bk; v += NT) bad |= !(fabs(dsum[v]) < 0x1p1000);
+    const int force = __syncthreads_or(bad);
+    // Rare path: column i scaled by the power of two 2^-e with 2^e <= max|x2| < 2^(e+1)
+    // (exact); a second cluster reduction forms ||x2 2^-e||^2 and the dot products
+    // (x2 2^-e)^T a_c, and the coefficients take scal 2^e for the dot terms.  Same
+    // decision in every CTA of the cluster.
+    if (s_rescale || force) {
       const double amax = dsum[bk];
-      const double inv = amax > 0.0 ? 1.0 / amax : 0.0;
-      double s = 0.0;
-      for (int r = lo + tid; r < nr; r += NT) {
-        const double t = xi[r] * inv;
-        s = fma(t, t, s);
-      }
-      s = warp_sum(s);
-      if (lane == 0) s_red[tid >> 5] = s;
-      __syncthreads();
-      if (tid == 0) {
-        double t = 0.0;
-        for (int q = 0; q < NT / 32; ++q) t += s_red[q];
-        mypart[bk + 1] = t;
+      const int e = amax > 0.0 ? max(-1022, min(1022, ilogb(amax))) : 0;
+      const double inv = ldexp(1.0, -e), sc = ldexp(1.0, e);
+      for (int c0 = 0; c0 < bk; c0 += CPP) {
+        const int c = c0 + tid / TPC;
+        double sv = 0.0;
+        if (c < bk) {
+          const double* ac = slab + (size_t)c * Rp;
+          for (int r = lo + sub; r < nr; r += TPC) {
+            const double t = xi[r] * inv;
+            sv = fma(t, c == i ? t : ac[r], sv);
+          }
+        }
+        for (int o = TPC / 2; o > 0; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
+        if (sub == 0 && c < bk) resc[c] = sv;
       }
       cluster.sync();
-      if (tid == 0) {
+      for (int v = tid; v < bk; v += NT) {
         double t = 0.0;
-        for (int q = 0; q < C; ++q) t += *cluster.map_shared_rank(&mypart[bk + 1], q);
-        const bool rescaled = (p.j - i > 1) && (amax > 0.0) && !(dsum[i] < 0x1p1000 && amax > 0x1p-450);
-        const double xnorm = rescaled ? amax * sqrt(t) : sqrt(dsum[i]);
+        for (int q = 0; q < C; ++q) t += *cluster.map_shared_rank(&resc[v], q);
+        dsum[v] = t;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        const double xnorm = amax > 0.0 ? sqrt(dsum[i]) * sc : 0.0;
         const double alpha = rowi[i];
         double tau = 0.0, beta = alpha, scal = 1.0;
         if (p.j - i > 1 && xnorm != 0.0) {
@@ -190,18 +203,19 @@ __global__ void __launch_bounds__(kPanelThreads, 4)
         s_beta = beta;
         s_tau = tau;
         s_scal = scal;
+        s_dscal = scal * sc;
       }
       __syncthreads();
     }
     if (tid == 0 && rank == 0) p.tau[i] = s_tau;
-    const double tau = s_tau, scal = s_scal;
+    const double tau = s_tau, scal = s_scal, dscal = s_dscal;
     const bool own_row = rank == owner;
     {
       const int TPU = bk >= 128 ? 2 : (bk >= 64 ? 4 : 8);
       for (int c0 = 0; c0 < bk; c0 += NT / TPU) {
         const int c = c0 + tid / TPU, rg = tid % TPU;
         if (c > i && c < bk) {
-          const double z = tau * fma(scal, dsum[c], rowi[c]);
+          const double z = tau * fma(dscal, dsum[c], rowi[c]);
           if (tau != 0.0) {
             const double z2 = -z * scal;
             double* ac = slab + (size_t)c * Rp;
@@ -209,7 +223,7 @@ __global__ void __launch_bounds__(kPanelThreads, 4)
             if (own_row && rg == 0) ac[i - rb] -= z;
           }
         } else if (c < i && rg == 0) {
-          const double gv = fma(scal, dsum[c], rowi[c]);
+          const double gv = fma(dscal, dsum[c], rowi[c]);
           gprev[c] = gv;
           gprevf[c] = f64_to_f32_rz(gv);
         }
@@ -257,7 +271,8 @@ __global__ void __launch_bounds__(kPanelThreads, 4)
 }  // namespace
 
 size_t panel_cluster_smem_bytes(int bk, int Rp) {
-  return ((size_t)bk * Rp * 2 + 2 * (size_t)(bk + 2) + 2 * (size_t)bk + (bk + 1) + 2 * (size_t)bk + (bk + 1) / 2) *
+  return ((size_t)bk * Rp * 2 + 2 * (size_t)(bk + 2) + 2 * (size_t)bk + (bk + 1) + 2 * (size_t)bk + (bk + 1) / 2 +
+          (size_t)bk) *
          sizeof(double);
 }
 

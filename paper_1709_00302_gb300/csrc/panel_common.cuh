@@ -18,18 +18,26 @@ constexpr int kPanelThreads = 256;
 // across runs to rounding, not bit for bit.
 constexpr int kAccStride = 32;  // doubles between accumulated values (one 256-byte line)
 
-// Reciprocal square root and reciprocal of a positive normal FP64 number: an FP32
-// hardware estimate of the mantissa's value (exponent handled with integer operations)
-// refined by two Newton steps in FP64.  Each FP64 instruction costs tens of cycles on
-// this GPU; this takes 6 (rsqrt) and 4 (reciprocal) of them, about half the library's.
+// One accumulator buffer holds, kAccStride doubles apart: the sums of a step (2 bk + 2 for
+// the pair kernel, 4 bk + 2 for the four-reflector kernel), then, from entry
+// kRescaleSlot bk + 2, the bk sums of the rare path's scaled second pass.
+constexpr int kRescaleSlot = 4;
+__host__ __device__ inline size_t panel_acc_entries(int bk) { return (size_t)(kRescaleSlot + 1) * bk + 2; }
+
+// Reciprocal square root and reciprocal of a positive normal FP64 number by Newton-Raphson
+// iteration.  The start is the FP32 hardware estimate for the mantissa (rsqrtf / __frcp_rn,
+// about 22 correct bits), with the exponent handled by integer operations; two
+// Newton-Raphson steps in FP64 follow, r <- r (3/2 - (q/2) r^2) for 1/sqrt(q) and
+// r <- r + r (1 - s r) for 1/s, each roughly doubling the number of correct bits, so the
+// result is within a few units in the last place of the exact value.  They stand in for
+// FP64 square root and division on the reflector's critical path: 6 and 4 dependent FP64
+// operations.
 __device__ __forceinline__ double rsqrt_newton(double q) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(q);
   const int e = (int)((u >> 52) & 0x7FF) - 1023;
   const int k = e >> 1;  // floor(e / 2)
   const int em = e - 2 * k;  // 0 or 1: q = m 2^(2k), m in [1, 4)
-  const double m = __longlong_as_double((long long)((u & 0x000FFFFFFFFFFFFFull) | ((unsigned long long)(1023 + em) << 52)));
   const double hm = __longlong_as_double((long long)((u & 0x000FFFFFFFFFFFFFull) | ((unsigned long long)(1022 + em) << 52)));
-  (void)m;
   const float mf = __uint_as_float(((uint32_t)(127 + em) << 23) | (uint32_t)((u >> 29) & 0x7FFFFFu));
   double r = tc::f32_to_f64(rsqrtf(mf));
 #pragma unroll
