@@ -9,16 +9,24 @@ reduction of a fresh copy of A (the matrix is restored from a resident copy betw
 outside the timed calls).  A is 512 MB, larger than the 129 MB L2, so no L2 flush is
 needed between steps.
 
-Metric: TFLOP/s with the nominal 4n^3/3 flop count of the method (Section 2.1).
+Metric: TFLOP/s with the nominal 4n^3/3 flop count of the method (Section 2.1), for the
+precision that matches the FP64 path's backward error: the Ozaki scheme (FP64-accurate
+products on the BF16 tensor cores).  Its speedup over the plain FP64 GPU path at equal
+backward error is the metric's second part; mats/s (the batched workload) its third.
 
 The JSON line adds
   roofline      the dominant kernel class, timed live with CUDA events on its stream
-                during the timed steps, against the measured peak of its bound;
+                during the timed steps, against the measured peak of its bound; the FP64
+                rate of this GPU measured in the same run; the FP64 and split-precision
+                rooflines of the step and its HBM fraction (12 sum j^2 bytes);
   cpu_baseline  the FP64 oracle (one reflector at a time) on the host cores, on a bounded
                 sample: the first reflectors of the same matrix;
   e2e           the same metric through the C ABI with host buffers: pinned host A ->
                 device, reduction, device -> host of A and tau, all inside the timing;
-  fp64_path     the plain FP64 GPU path on the same matrix, with its backward error;
+  fp64_path     the plain FP64 GPU path on the same matrix (several steps), with its
+                backward error, and speedup_vs_fp64_at_equal_backward_error;
+  bf16x6_path   the FP32-class split path on the same matrix, with its (larger) error;
+  ge2gb, batched  compact records of the other two workloads (few steps);
   clocks        nvidia-smi samples taken during the timed steps.
 
 --impl reference times the oracle instead (the CPU reference arm), each step one bounded
@@ -267,9 +275,38 @@ def reference_arm(args, n, w, b):
     return 0
 
 
-def roofline(stats, precision):
+def measure_fp64_peak(br, dev, stream):
+    """FP64 rate of this GPU, measured in the run: the library's FMA probe (eight
+    independent FMA chains per thread, two CTAs of 512 threads per SM), timed with CUDA
+    events on `stream`; the median of five launches after one warm-up launch."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks, threads, iters = 2 * sms, 512, 4096
+    sink = torch.empty(blocks * threads, dtype=torch.float64, device=dev)
+    flops = 16.0 * blocks * threads * iters
+    rates = []
+    for it in range(6):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc = br.bandred_fp64_probe(blocks, threads, iters, sink, stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        if rc != 0:
+            raise br.BandredError(rc, "bandred_fp64_probe")
+        if it:
+            rates.append(flops / (e0.elapsed_time(e1) / 1e3) / 1e12)
+    return {"tflops": statistics.median(rates), "best_tflops": max(rates), "launches": len(rates),
+            "flops_per_launch": flops,
+            "how": f"bandred_fp64_probe: {blocks} CTAs x {threads} threads x 8 chains x {iters} FP64 FMAs, "
+                   f"CUDA events, median of {len(rates)} launches"}
+
+
+def roofline(stats, precision, fp64_peak):
     """Roofline of the dominant kernel class of a profiled run: its algorithmic flops or
-    bytes over its CUDA-event time, against the bound's peak."""
+    bytes over its CUDA-event time, against the bound's peak (the FP64 rate measured in
+    this run for the FP64-bound classes, MEASURED_PEAKS.json's copy bandwidth for the
+    classes that stream the trailing matrix)."""
     peaks, peak_src = load_peaks()
     dom = max(stats, key=lambda s: s["ms"]) if stats else None
     if dom is None:
@@ -280,10 +317,9 @@ def roofline(stats, precision):
     alu = precision == "fp64" or dom["name"] == "panel_qr_f64"
     if alu:
         achieved = dom["flops"] / (dom["ms"] / 1e3) / 1e12
-        peak = 1.25
+        peak = fp64_peak["tflops"]
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "kernel": dom["name"], "peak_source": "nominal FP64 rate of GB300 (1.25 TFLOP/s; 1.20 measured "
-                                                      "with an FMA loop)"}
+                "kernel": dom["name"], "peak_source": "FP64 rate measured in this run (" + fp64_peak["how"] + ")"}
     else:
         achieved = dom["bytes"] / (dom["ms"] / 1e3) / 1e9
         peak = peaks["hbm_gbs"]
@@ -294,8 +330,47 @@ def roofline(stats, precision):
     roof["launches"] = dom["launches"]
     roof["avg_launch_ms"] = per_launch_ms
     roof["algorithmic_per_launch"] = (dom["flops"] if alu else dom["bytes"]) / dom["launches"]
-    roof["kernels"] = {s["name"]: {"launches": s["launches"], "ms": s["ms"]} for s in stats}
+    roof["kernels"] = {s["name"]: {"launches": s["launches"], "ms": s["ms"],
+                                   "tflops": s["flops"] / (s["ms"] / 1e3) / 1e12 if s["ms"] > 0 else None,
+                                   "gbs": s["bytes"] / (s["ms"] / 1e3) / 1e9 if s["ms"] > 0 else None}
+                       for s in stats}
     return roof
+
+
+# digit-pair (or slice-pair) products per FP64 product of each split precision
+PRODUCTS = {"ozaki": 28, "bf16x6": 6, "bf16x3": 3}
+
+
+def step_rooflines(n, w, b, fp64_peak, times):
+    """The step-level rooflines of the sy2sb workload.  Per iteration k the trailing update
+    reads lower(A2) (X1 = A2 W), then reads and writes it (the rank-2k update): 12 j_k^2
+    bytes, with j_k = n - w - k, for 4 j_k^2 b flops: an intensity of b/3 flop/byte.  The
+    FP64 roofline is min(P_fp64, BW b/3); a split precision with p products per FP64
+    product has min(P_bf16_sustained / p, BW b/3).  `times` maps a precision to its
+    measured ms per step."""
+    peaks, src = load_peaks()
+    bw = peaks["hbm_gbs"] * 1e9
+    algo_bytes = sum(12.0 * (n - w - k) ** 2 for k in range(0, n - w - 1, b))
+    inten = nominal_flops(n) / algo_bytes
+    out = {"algorithmic_bytes_per_step": algo_bytes, "intensity_flop_per_byte": inten,
+           "hbm_gbs_peak": peaks["hbm_gbs"], "bf16_tflops_sustained": peaks.get("bf16_tflops_sustained"),
+           "peaks_source": src}
+    mem_roof = bw * inten / 1e12
+    for prec, ms in times.items():
+        if ms is None:
+            continue
+        achieved = nominal_flops(n) / (ms / 1e3) / 1e12
+        if prec == "fp64":
+            roof = min(fp64_peak["tflops"], mem_roof)
+            bound = "fp64 pipe" if fp64_peak["tflops"] < mem_roof else "hbm"
+        else:
+            p = PRODUCTS[prec]
+            roof = min(peaks["bf16_tflops_sustained"] / p, mem_roof)
+            bound = f"bf16 tensor / {p}" if peaks["bf16_tflops_sustained"] / p < mem_roof else "hbm"
+        out[prec] = {"roofline_tflops": roof, "bound": bound, "achieved_tflops": achieved, "frac": achieved / roof,
+                     "hbm_gbs": algo_bytes / (ms / 1e3) / 1e9,
+                     "hbm_frac": algo_bytes / (ms / 1e3) / bw}
+    return out
 
 
 def setup_distributed():
@@ -390,7 +465,7 @@ def make_problem(args, br, dev, stream):
     raise ValueError(wl)
 
 
-def bench_batched(args, br, dev, stream, world, rank, dist):
+def bench_batched(args, br, dev, stream, world, rank, dist, compact=False):
     """1000 symmetric (n ~ U[64,1024]) and 1000 general (n ~ U[64,1024], m ~ U[n,2n])
     matrices per GPU, w in {16, 32}; every step restores the inputs and replays one
     captured CUDA graph holding both batched runs.  With N ranks the batch is N times as
@@ -488,7 +563,7 @@ def bench_batched(args, br, dev, stream, world, rank, dist):
         assert sb.run(ws, st[0:1], cap) == 0
         assert gb.run(wg, st[1:2], cap) == 0
         stats = br.bandred_profile_end()
-    roof = roofline(stats, args.precision)
+    roof = roofline(stats, args.precision, measure_fp64_peak(br, dev, cap))
     # end to end: pinned host inputs -> device, both batched runs, outputs -> host
     hs, hg = flat_s0.cpu().pin_memory(), flat_g0.cpu().pin_memory()
     bs, bg = torch.empty_like(hs).pin_memory(), torch.empty_like(hg).pin_memory()
@@ -517,7 +592,7 @@ def bench_batched(args, br, dev, stream, world, rank, dist):
                    f"vectors stay on the device"}
     del hs, hg, bs, bg
     cpu = None
-    if world == 1 and rank == 0 and not args.no_cpu_baseline:
+    if world == 1 and rank == 0 and not args.no_cpu_baseline and not compact:
         import oracle
 
         cores = oracle.set_threads(0)
@@ -577,8 +652,8 @@ def bench_batched(args, br, dev, stream, world, rank, dist):
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks, "step_ms": ms,
         }
-        print(json.dumps(line), flush=True)
-    return 0
+        return line
+    return None
 
 
 def main():
@@ -593,7 +668,7 @@ def main():
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--w", type=int, default=None)
     ap.add_argument("--b", type=int, default=None)
-    ap.add_argument("--precision", default="bf16x6", choices=["fp64", "bf16x3", "bf16x6", "ozaki"])
+    ap.add_argument("--precision", default="ozaki", choices=["fp64", "bf16x3", "bf16x6", "ozaki"])
     ap.add_argument("--lookahead", type=int, default=-1)
     ap.add_argument("--batch-sym", type=int, default=1000)
     ap.add_argument("--batch-gen", type=int, default=1000)
@@ -601,6 +676,9 @@ def main():
     ap.add_argument("--panel-ctas", type=int, default=0, help="panel_ctas option (batched: CTAs per matrix panel)")
     ap.add_argument("--no-fp64-path", action="store_true", help="skip the FP64 comparison line")
     ap.add_argument("--no-ozaki-path", action="store_true", help="skip the Ozaki-scheme comparison line")
+    ap.add_argument("--no-bf16x6-path", action="store_true", help="skip the bf16x6 comparison line")
+    ap.add_argument("--no-extras", action="store_true", help="skip the compact ge2gb and batched records")
+    ap.add_argument("--cmp-steps", type=int, default=3, help="timed steps of each comparison path")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-cols", type=int, default=96, help="reflectors per reference-arm step")
@@ -624,7 +702,13 @@ def main():
     br.lib()
     stream = torch.cuda.current_stream(dev)
     if args.workload == "batched":
-        return bench_batched(args, br, dev, stream, world, rank, dist)
+        line = bench_batched(args, br, dev, stream, world, rank, dist)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
+        return 0
 
     prob = make_problem(args, br, dev, stream)
     A0 = prob["A0"]
@@ -662,6 +746,9 @@ def main():
         ms = [e0.elapsed_time(e1) for e0, e1 in ev]
         return ms, stats, launches, clocks
 
+    # ---- FP64 rate of this GPU (the FP64 roofline's denominator), measured before the timing
+    fp64_peak = measure_fp64_peak(br, dev, stream)
+
     # ---- headline: the configured precision with look-ahead
     call, outs, status = make_call(args.precision, args.lookahead)
     ms, stats, launches, clocks = timed_steps(call, args.steps, args.warmup, profile=True)
@@ -677,7 +764,7 @@ def main():
     bwd = prob["backward"](A, outs)
 
     # ---- roofline of the dominant kernel class (live CUDA-event timing above)
-    roof = roofline(stats, args.precision)
+    roof = roofline(stats, args.precision, fp64_peak)
 
     # ---- e2e through the C ABI with host buffers
     A_pin = A0.cpu().pin_memory()
@@ -704,25 +791,63 @@ def main():
            "ms_per_step": e2e_step}
     del A_pin, A_back
 
-    # ---- plain FP64 GPU path on the same matrix (comparison line)
+    def comparison(precision):
+        """Another precision on the same matrix: --cmp-steps timed steps after one warm-up,
+        median and spread, and its backward error."""
+        c, o, stc = make_call(precision, args.lookahead)
+        msc, _, _, _ = timed_steps(c, max(1, args.cmp_steps), 1)
+        if int(stc.item()) != 0:
+            raise br.BandredError(int(stc.item()), f"device status ({precision})")
+        med = statistics.median(msc)
+        return {"precision": precision, "steps": len(msc), "ms_per_step": med, "ms_min": min(msc),
+                "ms_max": max(msc), "value": prob["flops"] / (med / 1e3) / 1e12, "unit": "TFLOP/s",
+                "backward_error": prob["backward"](A, o)}
+
+    # ---- plain FP64 GPU path on the same matrix: the denominator of the speedup at equal
+    # backward error
     fp64 = None
     if args.precision != "fp64" and not args.no_fp64_path:
-        call64, outs64, _ = make_call("fp64", args.lookahead)
-        ms64, _, _, _ = timed_steps(call64, 1, 1)
-        b64 = prob["backward"](A, outs64)
-        fp64 = {"ms_per_step": ms64[0], "value": prob["flops"] / (ms64[0] / 1e3) / 1e12,
-                "backward_error": b64, "speedup_of_headline": ms64[0] / ms_step}
-
-    # ---- Ozaki-scheme path (FP64-class accuracy on the tensor cores) on the same matrix:
-    # the speedup over the FP64 path at equal backward error
+        fp64 = comparison("fp64")
+        fp64["speedup_of_headline"] = fp64["ms_per_step"] / statistics.median(ms)
     ozaki = None
     if args.precision != "ozaki" and not args.no_ozaki_path:
-        callz, outsz, _ = make_call("ozaki", args.lookahead)
-        msz, _, _, _ = timed_steps(callz, 1, 1)
-        bz = prob["backward"](A, outsz)
-        ozaki = {"ms_per_step": msz[0], "value": prob["flops"] / (msz[0] / 1e3) / 1e12, "backward_error": bz}
+        ozaki = comparison("ozaki")
         if fp64 is not None:
-            ozaki["speedup_vs_fp64_path"] = fp64["ms_per_step"] / msz[0]
+            ozaki["speedup_vs_fp64_path"] = fp64["ms_per_step"] / ozaki["ms_per_step"]
+    bf16 = None
+    if args.precision != "bf16x6" and not args.no_bf16x6_path:
+        bf16 = comparison("bf16x6")
+        bf16["note"] = "FP32-class products (six bf16 slice products): backward error about 1e-6, not FP64's"
+        if fp64 is not None:
+            bf16["speedup_vs_fp64_path"] = fp64["ms_per_step"] / bf16["ms_per_step"]
+    eq = None
+    if fp64 is not None and args.precision == "ozaki":
+        eq = {"value": fp64["ms_per_step"] / statistics.median(ms), "fp64_ms_per_step": fp64["ms_per_step"],
+              "ozaki_ms_per_step": statistics.median(ms), "fp64_backward_error": fp64["backward_error"],
+              "ozaki_backward_error": bwd,
+              "note": "median step times of the two paths on the same matrix, both at FP64-class backward error"}
+
+    # ---- step rooflines (FP64 and split) and the step's HBM fraction
+    step_roof = None
+    if args.workload == "sy2sb":
+        times = {args.precision: statistics.median(ms)}
+        for cmp_ in (fp64, ozaki, bf16):
+            if cmp_ is not None:
+                times[cmp_["precision"]] = cmp_["ms_per_step"]
+        step_roof = step_rooflines(n, w, b, fp64_peak, times)
+    if roof is not None:
+        roof["fp64_peak_measured"] = fp64_peak
+        roof["step"] = step_roof
+
+    # ---- compact records of the other workloads (few steps), so that one run observes all
+    extras = {}
+    if args.workload == "sy2sb" and not args.no_extras and world == 1:
+        del A
+        torch.cuda.empty_cache()
+        extras["ge2gb"] = compact_ge2gb(args, br, dev, stream)
+        torch.cuda.empty_cache()
+        extras["batched"] = compact_batched(args, br, dev, stream, world, rank, dist)
+        torch.cuda.empty_cache()
 
     # ---- CPU baseline: the oracle on the host cores, bounded sample
     cpu = None
@@ -739,20 +864,70 @@ def main():
                             "l2": "inputs larger than L2; matrix restored from a resident copy between steps",
                             "parallelism": "replicas" if world > 1 else "single"}, **prob["config"]),
             "backward_error": bwd,
+            "speedup_vs_fp64_at_equal_backward_error": eq,
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "fp64_path": fp64,
             "ozaki_path": ozaki,
+            "bf16x6_path": bf16,
             "gpu_launches": launches,
             "clocks": clocks,
             "step_ms": ms,
         }
+        line.update(extras)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def compact_ge2gb(args, br, dev, stream):
+    """ge2gb m = n = 8192, w = b = 64, N(0,1), Ozaki precision: 3 timed steps after one
+    warm-up, with its probe backward error."""
+    import torch
+
+    a2 = argparse.Namespace(**vars(args))
+    a2.workload, a2.n, a2.w, a2.b = "ge2gb", 8192, 64, 64
+    prob = make_problem(a2, br, dev, stream)
+    A0 = prob["A0"]
+    A = torch.empty_like(A0)
+    call, outs, st = prob["make_call"]("ozaki", args.lookahead)
+    A.copy_(A0)
+    call(A)
+    torch.cuda.synchronize(dev)
+    ms = []
+    for _ in range(3):
+        A.copy_(A0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        call(A)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms.append(e0.elapsed_time(e1))
+    if int(st.item()) != 0:
+        raise br.BandredError(int(st.item()), "device status (ge2gb)")
+    med = statistics.median(ms)
+    out = {"workload": prob["desc"] + " precision=ozaki", "steps": len(ms), "ms_per_step": med,
+           "value": prob["flops"] / (med / 1e3) / 1e12, "unit": "TFLOP/s (4(mn^2 - n^3/3))",
+           "backward_error": prob["backward"](A, outs), "step_ms": ms}
+    del A, A0
+    return out
+
+
+def compact_batched(args, br, dev, stream, world, rank, dist):
+    """The batched workload (1000 + 1000 uneven matrices, bf16x6: the batched path has no
+    FP64-class precision) with 2 timed graph replays after one warm-up."""
+    a2 = argparse.Namespace(**vars(args))
+    a2.workload, a2.precision, a2.steps, a2.warmup = "batched", "bf16x6", 2, 1
+    line = bench_batched(a2, br, dev, stream, world, rank, dist, compact=True)
+    if line is None:
+        return None
+    keep = ("value", "unit", "ms_per_step", "steps", "dtype", "tflops_nominal", "backward_error", "config")
+    out = {k: line[k] for k in keep if k in line}
+    out["e2e_mats_per_s"] = line["e2e"]["value"] if line.get("e2e") else None
+    return out
 
 
 if __name__ == "__main__":

@@ -130,7 +130,11 @@ int bandred_sy2sb(int64_t n, int64_t w, double* A, int64_t lda, double* tau,
 /* Non-allocating form.  work: device, 256-byte aligned, at least
  * bandred_sy2sb_workspace(n, w, opts) bytes, not shared with a concurrent call.
  * dev_status: device int (may be NULL) set to 0 at the start and to a BANDRED_DEV_* code
- * on a device-side failure. */
+ * on a device-side failure.
+ * Every entry point runs on the device that owns A and leaves the caller's current device
+ * as it found it.  With look-ahead (the default), the first call of a host thread on a
+ * device creates a high-priority stream and four events that the thread's later calls
+ * reuse; they live until the process exits. */
 int bandred_sy2sb_ex(int64_t n, int64_t w, double* A, int64_t lda, double* tau,
                      const bandred_opts* opts, void* work, size_t work_bytes, int* dev_status,
                      cudaStream_t stream);
@@ -148,7 +152,11 @@ int bandred_sy2sb_ex(int64_t n, int64_t w, double* A, int64_t lda, double* tau,
  *     return BANDRED_ERR_SCRATCH before any device work.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call before any
- *     stream capture that includes this entry point.
+ *     stream capture that includes this entry point.  With look-ahead (opts->lookahead
+ *     != 0, the default), the first call of a host thread on a device also creates a
+ *     high-priority stream and four events that the thread's later calls reuse (as
+ *     bandred_sy2sb_ex does); that first call belongs before any capture as well.
+ *   - The caller's current device is the same after the call as before it.
  *   - All calls on a device share the one array, and it keeps the previous call's
  *     contents.  Each call zeroes the counters and status word it relies on; everything
  *     else is written before it is read.  Calls that can overlap on the GPU (different
@@ -268,6 +276,27 @@ int bandred_profile_end(bandred_kernel_stat* out, int max_entries);
 
 /* Number of kernel launches the library has issued since it was loaded. */
 long long bandred_launch_count(void);
+
+/* ---------------------------------------------------------------- diagnostics -------
+ * The reciprocal square root and reciprocal that the panel kernels use in place of FP64
+ * square root and division when they form a reflector (Section 2.1, Eq. updateA0: beta,
+ * tau and 1/(alpha - beta) of the Householder vector): an FP32 hardware estimate refined
+ * by two Newton-Raphson steps in FP64.  For i < count: rsqrt[i] = 1/sqrt(x[i]) for x[i] in
+ * [2^-1022, 2^1023), and rcp[i] = 1/x[i] for x[i] in [2^-1021, 2^1021] (the panels use
+ * [2^-900, 2^1002) and [2^-451, 2^502]); outside those ranges the outputs are undefined.
+ * x, rsqrt, rcp: device arrays of count doubles (rsqrt or rcp may be NULL).  Returns 0,
+ * -i for an invalid i-th argument, or BANDRED_ERR_CUDA.  Stream-ordered, no allocation.
+ */
+int bandred_newton_eval(int64_t count, const double* x, double* rsqrt, double* rcp, cudaStream_t stream);
+
+/* FP64 throughput probe: `blocks` CTAs of `threads` threads each run 8 independent chains
+ * of `iters` dependent FP64 fused multiply-adds (2 flops each), then write one value per
+ * thread to sink (device, blocks * threads doubles) so that no work is dropped.  The flop
+ * count is 16 * blocks * threads * iters; time the launch with CUDA events on `stream`
+ * to obtain the FP64 rate.  Returns 0, -i for an invalid i-th argument, or
+ * BANDRED_ERR_CUDA.  No counterpart in the paper: it measures the FP64 roofline.
+ */
+int bandred_fp64_probe(int blocks, int threads, int iters, double* sink, cudaStream_t stream);
 
 #ifdef __cplusplus
 }

@@ -127,6 +127,10 @@ def lib():
         L.bandred_profile_end.restype = ci
         L.bandred_launch_count.argtypes = []
         L.bandred_launch_count.restype = ctypes.c_longlong
+        L.bandred_newton_eval.argtypes = [i64, vp, vp, vp, vp]
+        L.bandred_newton_eval.restype = ci
+        L.bandred_fp64_probe.argtypes = [ci, ci, ci, vp, vp]
+        L.bandred_fp64_probe.restype = ci
         # cost model of the autotuner (include/bandred_tune.h)
         f32 = ctypes.c_float
         L.bandred_mlp_param_count.argtypes = [ci, ci]
@@ -375,6 +379,16 @@ class GeBatch:
         return lib().bandred_ge2gb_batched_run(self.count, self.m, self.n, self.w, self.A, self.lda, self.tauq,
                                                self.taup, ctypes.byref(self.opts), _ptr(work), work.numel(),
                                                _ptr(dev_status), _stream(stream))
+
+
+def bandred_newton_eval(x, rsqrt=None, rcp=None, stream=None) -> int:
+    """The panel kernels' Newton-Raphson 1/sqrt(x) and 1/x of the device FP64 tensor x."""
+    return lib().bandred_newton_eval(x.numel(), _ptr(x), _ptr(rsqrt), _ptr(rcp), _stream(stream))
+
+
+def bandred_fp64_probe(blocks: int, threads: int, iters: int, sink, stream=None) -> int:
+    """FP64 FMA throughput probe (16 * blocks * threads * iters flops); sink: device FP64."""
+    return lib().bandred_fp64_probe(blocks, threads, iters, _ptr(sink), _stream(stream))
 
 
 # ------------------------------------------------------------------ conveniences

@@ -10,35 +10,7 @@ using bandred::Options;
 
 namespace {
 
-// Makes the device that owns `ptr` current (the library may run beside other CUDA
-// runtimes in the same process, e.g. PyTorch's, which keep their own current device).
-bool select_device_of(const void* ptr) {
-  if (!ptr) return true;
-  cudaPointerAttributes at;
-  if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return false;
-  int cur = -1;
-  cudaGetDevice(&cur);
-  if (cur != at.device && cudaSetDevice(at.device) != cudaSuccess) return false;
-  return true;
-}
-
 bool aligned(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 255u) == 0; }
-
-int sy2sb_check(int64_t n, int64_t w, const double* A, int64_t lda, const double* tau, const bandred_opts* opts,
-                Options* o) {
-  if (n < 0) return -1;
-  if (w < 1) return -2;
-  if (n > 0 && !A) return -3;
-  if (lda < (n > 1 ? n : 1)) return -4;
-  if (n - w > 0 && !tau) return -5;
-  if (n > INT32_MAX / 2) return BANDRED_ERR_UNSUPPORTED;
-  if (bandred::resolve_options(opts, w, o) != 0) return -6;
-  return 0;
-}
 
 int ge2gb_check(int64_t m, int64_t n, int64_t w, const double* A, int64_t lda, const double* tauq,
                 const double* taup, const bandred_opts* opts, Options* o) {
@@ -55,6 +27,18 @@ int ge2gb_check(int64_t m, int64_t n, int64_t w, const double* A, int64_t lda, c
 }
 
 }  // namespace
+
+int bandred::sy2sb_check(int64_t n, int64_t w, const double* A, int64_t lda, const double* tau,
+                         const bandred_opts* opts, Options* o) {
+  if (n < 0) return -1;
+  if (w < 1) return -2;
+  if (n > 0 && !A) return -3;
+  if (lda < (n > 1 ? n : 1)) return -4;
+  if (n - w > 0 && !tau) return -5;
+  if (n > INT32_MAX / 2) return BANDRED_ERR_UNSUPPORTED;
+  if (bandred::resolve_options(opts, w, o) != 0) return -6;
+  return 0;
+}
 
 extern "C" {
 
@@ -95,9 +79,10 @@ size_t bandred_sy2sb_workspace(int64_t n, int64_t w, const bandred_opts* opts) {
 int bandred_sy2sb_ex(int64_t n, int64_t w, double* A, int64_t lda, double* tau, const bandred_opts* opts,
                      void* work, size_t work_bytes, int* dev_status, cudaStream_t stream) {
   Options o;
-  int rc = sy2sb_check(n, w, A, lda, tau, opts, &o);
+  int rc = bandred::sy2sb_check(n, w, A, lda, tau, opts, &o);
   if (rc) return rc;
-  if (!select_device_of(A)) return -3;
+  bandred::DeviceGuard dg;
+  if (!dg.select(A)) return -3;
   if (!work || !aligned(work)) return -7;
   if (work_bytes < bandred::sy2sb_workspace_bytes(n, w, o)) return -8;
   return bandred::sy2sb_run(n, w, A, lda, tau, o, work, dev_status, stream);
@@ -106,9 +91,10 @@ int bandred_sy2sb_ex(int64_t n, int64_t w, double* A, int64_t lda, double* tau, 
 int bandred_sy2sb(int64_t n, int64_t w, double* A, int64_t lda, double* tau, const bandred_opts* opts,
                   cudaStream_t stream) {
   Options o;
-  int rc = sy2sb_check(n, w, A, lda, tau, opts, &o);
+  int rc = bandred::sy2sb_check(n, w, A, lda, tau, opts, &o);
   if (rc) return rc;
-  if (!select_device_of(A)) return -3;
+  bandred::DeviceGuard dg;
+  if (!dg.select(A)) return -3;
   const size_t bytes = bandred::sy2sb_workspace_bytes(n, w, o);
   void* work = nullptr;
   if (cudaError_t e = cudaMallocAsync(&work, bytes, stream); e != cudaSuccess) {
@@ -140,7 +126,8 @@ int bandred_ge2gb_ex(int64_t m, int64_t n, int64_t w, double* A, int64_t lda, do
   Options o;
   int rc = ge2gb_check(m, n, w, A, lda, tauq, taup, opts, &o);
   if (rc) return rc;
-  if (!select_device_of(A)) return -4;
+  bandred::DeviceGuard dg;
+  if (!dg.select(A)) return -4;
   if (!work || !aligned(work)) return -9;
   if (work_bytes < bandred::ge2gb_workspace_bytes(m, n, w, o)) return -10;
   return bandred::ge2gb_run(m, n, w, A, lda, tauq, taup, o, work, dev_status, stream);
@@ -151,7 +138,8 @@ int bandred_ge2gb(int64_t m, int64_t n, int64_t w, double* A, int64_t lda, doubl
   Options o;
   int rc = ge2gb_check(m, n, w, A, lda, tauq, taup, opts, &o);
   if (rc) return rc;
-  if (!select_device_of(A)) return -4;
+  bandred::DeviceGuard dg;
+  if (!dg.select(A)) return -4;
   const size_t bytes = bandred::ge2gb_workspace_bytes(m, n, w, o);
   void* work = nullptr;
   if (cudaError_t e = cudaMallocAsync(&work, bytes, stream); e != cudaSuccess) {

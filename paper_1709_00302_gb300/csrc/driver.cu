@@ -36,12 +36,15 @@ struct DeviceInfo {
   int sms = 0;
 };
 
+constexpr int kMaxDevices = 64;  // devices a process may use with this library
+
 DeviceInfo& device_info(int dev) {
   static std::mutex mu;
-  static DeviceInfo info[64];
+  static DeviceInfo info[kMaxDevices];
+  static DeviceInfo other;  // beyond kMaxDevices: asked every time
   std::lock_guard<std::mutex> lock(mu);
-  DeviceInfo& d = info[dev & 63];
-  if (d.sms == 0) cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
+  DeviceInfo& d = (dev >= 0 && dev < kMaxDevices) ? info[dev] : other;
+  if (d.sms == 0 || &d == &other) cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
   return d;
 }
 
@@ -131,7 +134,7 @@ int resolve_options(const bandred_opts* in, int64_t w, Options* o) {
 struct Sy2sbWs {
   double *Y[2], *W[2], *X, *X2;
   double *Z[2], *splitk[2];  // FP64 small products; [1] belongs to the panel stream
-  double *part, *rowbuf, *part2;
+  double *part, *rowbuf;
   GridSync* gs;
   // split-precision buffers
   __nv_bfloat16 *wblob, *x2blob, *ablob, *bblob;
@@ -169,7 +172,6 @@ static Sy2sbWs carve_sy2sb(void* work, int64_t n, int64_t w, const Options& o, i
     ws.splitk[q] = q < nbuf ? c.take<double>(ws.splitk_cap) : ws.splitk[0];
   }
   ws.rowbuf = c.take<double>(8 * (size_t)b);  // up to four rows per step, two steps
-  ws.part2 = c.take<double>((size_t)kPanelCtasPerSm * sms);
   ws.gs = c.take<GridSync>(1);  // 256 bytes, immediately followed by the accumulators
   ws.part = c.take<double>((panel_sync_bytes((int)b) - 256) / sizeof(double));
   if (is_split(o)) {
@@ -203,7 +205,7 @@ struct SplitBufs {
 };
 
 struct Ge2gbWs {
-  double *Yu[2], *Wu[2], *Yv, *Wv, *Z[2], *ZT, *P, *splitk[2], *part, *rowbuf, *part2;
+  double *Yu[2], *Wu[2], *Yv, *Wv, *Z[2], *ZT, *P, *splitk[2], *part, *rowbuf;
   GridSync* gs;
   SplitBufs sb[2];  // [0] caller's stream, [1] panel stream (look-ahead)
   char *ozp[2], *ozr[2];  // Ozaki-scheme buffers per stream (see Sy2sbWs)
@@ -234,7 +236,6 @@ static Ge2gbWs carve_ge2gb(void* work, int64_t m, int64_t n, const Options& o, i
     ws.splitk[q] = q < nbuf ? c.take<double>(ws.splitk_cap) : ws.splitk[0];
   }
   ws.rowbuf = c.take<double>(8 * (size_t)b);  // up to four rows per step, two steps
-  ws.part2 = c.take<double>((size_t)kPanelCtasPerSm * sms);
   ws.gs = c.take<GridSync>(1);  // 256 bytes, immediately followed by the accumulators
   ws.part = c.take<double>((panel_sync_bytes((int)b) - 256) / sizeof(double));
   if (is_split(o)) {
@@ -286,7 +287,7 @@ static int current_sms() {
 // One panel factorisation: QR of the j x bk panel at `A` (rs = 1, cs = lda) or LQ of the
 // bk x j row panel (rs = lda, cs = 1).
 static int run_panel(double* A, int64_t rs, int64_t cs, int j, int bk, double* tau, double* Y, double* W,
-                     int64_t ldy, double* acc, double* rowbuf, double* part2, GridSync* gs, int* status,
+                     int64_t ldy, double* acc, double* rowbuf, GridSync* gs, int* status,
                      const Options& o, int max_ctas, unsigned int extra, cudaStream_t s) {
   PanelParams p{};
   // Short panels: one thread-block cluster (no grid-wide barrier, deterministic sums).
@@ -330,7 +331,6 @@ static int run_panel(double* A, int64_t rs, int64_t cs, int j, int bk, double* t
   p.ldy = ldy;
   p.acc = acc;
   p.rowbuf = rowbuf;
-  p.part2 = part2;
   p.gs = gs;
   p.status = status;
   p.limit_ns = o.limit_ns;
@@ -352,17 +352,19 @@ static int run_panel(double* A, int64_t rs, int64_t cs, int j, int bk, double* t
 
 // ---------------------------------------------------------------------------------
 // Auxiliary stream (highest priority) and events used for look-ahead, one set per host
-// thread and device, created on first use.
+// thread and device, created by the first look-ahead call of that thread on that device
+// and kept (never destroyed) for the thread's later calls.
 struct AuxStreams {
   cudaStream_t panel = nullptr;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
 static int aux_streams(AuxStreams** out) {
-  thread_local AuxStreams per_dev[16];
+  thread_local AuxStreams per_dev[kMaxDevices];
   int dev = 0;
   CK(cudaGetDevice(&dev));
-  AuxStreams& a = per_dev[dev & 15];
+  if (dev < 0 || dev >= kMaxDevices) return record_cuda_error(cudaErrorInvalidDevice, "look-ahead streams");
+  AuxStreams& a = per_dev[dev];
   if (!a.panel) {
     int lo = 0, hi = 0;
     CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
@@ -405,13 +407,15 @@ struct Sy2sb {
   int sms, pmax, S;
   unsigned int extra;
 
-  int panel(int64_t k, int buf, cudaStream_t s) {
+  // ctas > 0: at most that many CTAs for a grid panel (the look-ahead panel that shares
+  // the GPU with the rest of the trailing update)
+  int panel(int64_t k, int buf, cudaStream_t s, int ctas = 0) {
     const int bk = (int)std::min<int64_t>(o.b, n - w - 1 - k);
     const int64_t r0 = k + w;
     const int j = (int)(n - r0);
     prof::Scope sc(prof::kPanel, s, panel_flops(j, bk), panel_bytes(j, bk));
     int rc = run_panel(A + r0 + k * lda, 1, lda, j, bk, tau + k, ws.Y[buf], ws.W[buf], ws.ld, ws.part, ws.rowbuf,
-                       ws.part2, ws.gs, status, o, pmax, extra, s);
+                       ws.gs, status, o, ctas > 0 ? std::min(ctas, pmax) : pmax, extra, s);
     extra = 0;
     return rc;
   }
@@ -433,12 +437,14 @@ struct Sy2sb {
   }
 
   // Ozaki buffers of the rank-2k operands [X3 | Y] and [Y | X3] (j rows, K = 2 bk): one
-  // row-exponent array serves both.
+  // row-exponent array serves both, and the second one's space holds the two largest
+  // exponents that balance the halves.
   ozaki::Bufs rank2k_bufs(int j, int bk) const {
     ozaki::Bufs b = ozaki::carve(ws.ozr, j, j, 2 * bk, 1);
     b.eB = b.eA;
     return b;
   }
+  int* rank2k_shift(int j, int bk) const { return ozaki::carve(ws.ozr, j, j, 2 * bk, 1).eB; }
 
   // X1 = A2 W, X2 = X1^T W / 2, X3 = X1 + Y X2 (into ws.X); for the split path also packs
   // the operands of the rank-2k update.
@@ -474,9 +480,16 @@ struct Sy2sb {
         const Operand y{Y, ld, 0, B, nullptr, 0, 0, 0, j}, x2{ws.X2, B, 1, B, nullptr, 0, 0, 0, B};
         CK(ozaki::product(y, x2, j, B, B, 1.0, 1.0, ws.X, ld, ozaki::carve(ws.ozp, j, B, B, sp), sp, status, lim, s));
       }
-      // operands of A2 += X3 Y^T + Y X3^T: [X3 | Y] and [Y | X3], whose rows hold the same
-      // entries and so share their row exponents
-      const Operand l{ws.X, ld, 0, B, Y, ld, 0, B, j}, r{Y, ld, 0, B, ws.X, ld, 0, B, j};
+      // operands of A2 += X3 Y^T + Y X3^T: [X3 2^-sigma | Y 2^sigma] and [Y 2^sigma | X3 2^-sigma],
+      // whose rows hold the same entries and so share their row exponents; sigma, half the
+      // gap between the largest exponents of X3 and Y, keeps Y's digits from falling below
+      // the scale of rows dominated by X3 (X3 carries the matrix's magnitude, |Y| <= 1)
+      int* sh = rank2k_shift(j, B);
+      Operand l{ws.X, ld, 0, B, Y, ld, 0, B, j}, r{Y, ld, 0, B, ws.X, ld, 0, B, j};
+      l.sh = r.sh = sh;
+      l.shsign = 1;
+      r.shsign = -1;
+      CK(ozaki::balance(l, sh, s));
       CK(ozaki::prepare(l, r, rank2k_bufs(j, B), s));
       return 0;
     }
@@ -614,8 +627,9 @@ struct Sy2sb {
     return 0;
   }
 
-  // A2 += X3 Y^T + Y X3^T on the lower triangle of A2's columns [c0, c1).
-  int syr2k(int64_t k, int buf, int c0, int c1, cudaStream_t s) {
+  // A2 += X3 Y^T + Y X3^T on the lower triangle of A2's columns [c0, c1); max_ctas > 0
+  // keeps the update to that many CTAs (Ozaki precision), leaving SMs to the panel.
+  int syr2k(int64_t k, int buf, int c0, int c1, cudaStream_t s, int max_ctas = 0) {
     const int bk = (int)std::min<int64_t>(o.b, n - w - 1 - k);
     const int64_t r0 = k + w;
     const int j = (int)(n - r0);
@@ -625,7 +639,7 @@ struct Sy2sb {
     prof::Scope sc(prof::kSyr2k, s, syr2k_flops(j, c0, c1, bk), syr2k_bytes(j, c0, c1, bk));
     if (o.precision == BANDRED_OZAKI) {
       CK(ozaki::rank_apply(j, j, 2 * bk, 1.0, A2, lda, c0, c1, 1, rank2k_bufs(j, bk), status,
-                           o.limit_ns, s));
+                           o.limit_ns, s, max_ctas));
       return 0;
     }
     if (!is_split(o)) {
@@ -707,6 +721,14 @@ int sy2sb_run(int64_t n, int64_t w, double* A, int64_t lda, double* tau, const O
   }
 
   if (last < 0) return 0;  // no panel: every reflector has length <= 1
+  // V2's two streams at once: the next panel on la_panel SMs while the rest of the rank-2k
+  // update holds the others (the Ozaki update can be held to a CTA count; the other
+  // precisions' updates take every SM, so their panel waits for free SMs instead).
+  int la_panel = 0, la_update = 0;
+  if (la == 2 && o.precision == BANDRED_OZAKI) {
+    la_panel = o.panel_ctas > 0 ? std::min(o.panel_ctas, R.sms - 1) : std::max(1, R.sms / 2);
+    la_update = R.sms - la_panel;
+  }
   AuxStreams* ax = nullptr;
   if (int rc = aux_streams(&ax)) return rc;
   cudaStream_t sp = ax->panel;
@@ -734,9 +756,9 @@ int sy2sb_run(int64_t n, int64_t w, double* A, int64_t lda, double* tau, const O
         CK(cudaEventRecord(ev_fork, s));
         CK(cudaStreamWaitEvent(sp, ev_fork, 0));
         if ((rc = R.syr2k(k, buf, 0, cL, sp))) return rc;
-        if ((rc = R.panel(kn, buf ^ 1, sp))) return rc;
+        if ((rc = R.panel(kn, buf ^ 1, sp, la_panel))) return rc;
         CK(cudaEventRecord(ev_panel, sp));
-        if ((rc = R.syr2k(k, buf, cL, j, s))) return rc;
+        if ((rc = R.syr2k(k, buf, cL, j, s, la_update))) return rc;
       } else {
         if ((rc = R.syr2k(k, buf, 0, j, s))) return rc;
         if (has_next) {
@@ -887,7 +909,7 @@ struct Ge2gb {
     const int j = (int)(m - k);
     prof::Scope sc(prof::kPanel, s, panel_flops(j, bk), panel_bytes(j, bk));
     int rc = run_panel(A + k + k * lda, 1, lda, j, bk, tauq + k, ws.Yu[buf], ws.Wu[buf], ws.ldu, ws.part,
-                       ws.rowbuf, ws.part2, ws.gs, status, o, pmax, extra, s);
+                       ws.rowbuf, ws.gs, status, o, pmax, extra, s);
     extra = 0;
     return rc;
   }
@@ -941,7 +963,7 @@ struct Ge2gb {
     const int jr = (int)(n - k - w);
     prof::Scope sc(prof::kPanel, s, panel_flops(jr, (int)bkr), panel_bytes(jr, (int)bkr));
     return run_panel(A + k + (k + w) * lda, lda, 1, jr, (int)bkr, taup + k, ws.Yv, ws.Wv, ws.ldv, ws.part, ws.rowbuf,
-                     ws.part2, ws.gs, status, o, pmax, 0u, s);
+                     ws.gs, status, o, pmax, 0u, s);
   }
 
   // D = A(k+bkr:m, k+w:n) += (D W_V) Y_V^T (Eq. updateD).

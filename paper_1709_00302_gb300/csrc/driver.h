@@ -27,6 +27,43 @@ const char* last_cuda_error();
 // Validates and completes the caller's options for bandwidth w; returns 0 or -1.
 int resolve_options(const bandred_opts* in, int64_t w, Options* o);
 
+// Argument checks of bandred_sy2sb_ex / bandred_sy2sb_noalloc (everything but the
+// workspace): 0, a negative argument index or BANDRED_ERR_UNSUPPORTED; fills *o.
+int sy2sb_check(int64_t n, int64_t w, const double* A, int64_t lda, const double* tau, const bandred_opts* opts,
+                Options* o);
+
+// Makes the device that owns a pointer current while the guard lives, and gives the
+// caller's current device back when it goes out of scope: the library may share the
+// process with other CUDA users (PyTorch, for one) that keep their own current device.
+class DeviceGuard {
+ public:
+  DeviceGuard() = default;
+  DeviceGuard(const DeviceGuard&) = delete;
+  DeviceGuard& operator=(const DeviceGuard&) = delete;
+  // false when ptr is not device (or managed) memory; nullptr selects nothing
+  bool select(const void* ptr) {
+    if (!ptr) return true;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return false;
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) return false;
+    if (cur == at.device) return true;
+    if (cudaSetDevice(at.device) != cudaSuccess) return false;
+    prev_ = cur;
+    return true;
+  }
+  ~DeviceGuard() {
+    if (prev_ >= 0) cudaSetDevice(prev_);
+  }
+
+ private:
+  int prev_ = -1;
+};
+
 size_t sy2sb_workspace_bytes(int64_t n, int64_t w, const Options& o);
 int sy2sb_run(int64_t n, int64_t w, double* A, int64_t lda, double* tau, const Options& o, void* work,
               int* dev_status, cudaStream_t s);

@@ -51,30 +51,15 @@ void* scratch_address(int* rc) {
   return g_scratch_addr[dev];
 }
 
-bool make_owner_current(const void* ptr) {
-  cudaPointerAttributes at;
-  if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return false;
-  int cur = -1;
-  cudaGetDevice(&cur);
-  return cur == at.device || cudaSetDevice(at.device) == cudaSuccess;
-}
-
 }  // namespace
 
 extern "C" int bandred_sy2sb_noalloc(int64_t n, int64_t w, double* A, int64_t lda, double* tau,
                                      const bandred_opts* opts, int* dev_status, cudaStream_t stream) {
-  if (n < 0) return -1;
-  if (w < 1) return -2;
-  if (n > 0 && !A) return -3;
-  if (lda < (n > 1 ? n : 1)) return -4;
-  if (n - w > 0 && !tau) return -5;
   bandred::Options o;
-  if (bandred::resolve_options(opts, w, &o) != 0) return -6;
-  if (n > 0 && !make_owner_current(A)) return -3;
+  const int chk = bandred::sy2sb_check(n, w, A, lda, tau, opts, &o);
+  if (chk) return chk;
+  bandred::DeviceGuard dg;  // the device of A while the call runs; the caller's device afterwards
+  if (n > 0 && !dg.select(A)) return -3;
   if (bandred::sy2sb_workspace_bytes(n, w, o) > kScratchBytes) return BANDRED_ERR_SCRATCH;
   int rc = 0;
   void* scratch = scratch_address(&rc);

@@ -4,15 +4,19 @@ It exists for callers that cannot allocate device memory when they call (inside 
 stream capture, under a fixed memory budget, or in a process whose allocator they do not
 own): it runs the same reduction as bandred_sy2sb_ex with the library's fixed device
 scratch array as workspace.  These tests check, on a GPU, that two calls in a row give
-the same result as the existing entry point within the tolerances of the FP64 parity
-tests, and that a problem too large for the scratch is refused before any device work.
-The file is named so that pytest collects it last.
+the same result as the existing entry point and as the FP64 oracle within the tolerances
+of the FP64 parity tests (the Ozaki precision included; bf16x6 by the spectrum of its
+band, at its stated tolerance), with the default options (look-ahead on) as well as
+without look-ahead, that the caller's current device is left alone, and that a problem
+too large for the scratch is refused before any device work.  The file is named so that
+pytest collects it last.
 """
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 import workloads
 from gpu_util import lower_band_and_v, to_dev, to_host
 
@@ -45,9 +49,11 @@ def call_noalloc(br, A, w, opts):
     tau = torch.zeros(max(n - w, 0), dtype=torch.float64, device="cuda")
     status = torch.full((1,), -7, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
+    dev = torch.cuda.current_device()
     rc = br.lib().bandred_sy2sb_noalloc(n, w, ctypes.c_void_p(dA.data_ptr()), dA.stride(1),
                                         ctypes.c_void_p(tau.data_ptr()), ctypes.byref(opts),
                                         ctypes.c_void_p(status.data_ptr()), ctypes.c_void_p(stream.cuda_stream))
+    assert torch.cuda.current_device() == dev
     torch.cuda.synchronize()
     return rc, to_host(dA), tau.cpu().numpy(), int(status.item())
 
@@ -81,6 +87,40 @@ def test_noalloc_matches_existing_entry_point_twice(br, n, w, b):
         assert np.max(np.abs(vg - vref), initial=0.0) <= V_TOL
         assert np.max(np.abs(tout - tref), initial=0.0) <= V_TOL
         assert np.all(np.isfinite(Aout[np.tril_indices(n)]))
+
+
+# the Ozaki buffers are larger (packed digits), so its problem is smaller to fit the scratch
+@pytest.mark.parametrize("precision,n,w", [("fp64", 1000, 40), ("ozaki", 600, 32)])
+def test_noalloc_default_options_match_the_oracle_twice(br, precision, n, w):
+    # default b (= w here, so the V2 look-ahead with its side stream) and default look-ahead
+    A = workloads.sym_gaussian(n, seed=n + w + 3)
+    opts = br.make_opts(precision=precision)
+    assert br.bandred_sy2sb_workspace(n, w, opts) <= br.NOALLOC_SCRATCH_BYTES
+    Ao, to = oracle.sy2sb(A, w)
+    bo, vo = lower_band_and_v(Ao, w)
+    fa = np.linalg.norm(A)
+    for _ in range(2):
+        rc, Aout, tout, st = call_noalloc(br, A, w, opts)
+        assert rc == 0 and st == 0
+        bg, vg = lower_band_and_v(Aout, w)
+        assert np.max(np.abs(bg - bo)) <= B_TOL * fa
+        assert np.max(np.abs(vg - vo), initial=0.0) <= V_TOL
+        assert np.max(np.abs(tout - to), initial=0.0) <= V_TOL
+
+
+def test_noalloc_split_precision_keeps_the_spectrum_twice(br):
+    # bf16x6 products (FP32-class): the band's eigenvalues within the stated 2e-5 ||A||_2
+    n, w = 800, 32
+    A = workloads.sym_gaussian(n, seed=n + w + 5)
+    lam = np.linalg.eigvalsh(A)
+    opts = br.make_opts(precision="bf16x6")
+    i, j = np.indices((n, n))
+    for _ in range(2):
+        rc, Aout, tout, st = call_noalloc(br, A, w, opts)
+        assert rc == 0 and st == 0
+        L = np.where((i - j >= 0) & (i - j <= w), Aout, 0.0)
+        B = L + np.tril(L, -1).T
+        assert np.max(np.abs(np.linalg.eigvalsh(B) - lam)) <= 2e-5 * np.max(np.abs(lam))
 
 
 def test_noalloc_refuses_problems_beyond_the_scratch(br):
