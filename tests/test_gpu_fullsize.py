@@ -7,6 +7,11 @@ and the FP64 and Ozaki GPU paths must match it elementwise.  The split (bf16x6) 
 meet its stated backward error and the invariants of an orthogonal similarity: the band's
 Frobenius norm and trace equal those of A (sqrt(sum lam^2) and sum lam, known exactly).
 
+ge2gb m = n = 8192, w = b = 64 on N(0,1) runs against the oracle in the same way, and
+the singular values of its band are compared with those of the oracle's band and of A.
+sy2sb n = 32768, w = b = 128 is checked on the device: a 16-probe backward error with Q
+applied through the reflectors, and the band's Frobenius norm and trace.
+
 Tolerances at this size: entries of the band differ from the oracle's by rounding in a
 different summation order, which grows with n: below 1e-11 ||A||_F (n u ~ 1e-12, ten
 times margin; measured 8e-16).  A reflector is determined only to about
@@ -107,28 +112,111 @@ def test_ge2gb_config3_split_and_ozaki(br):
         assert bwd <= tol and abs(fb - fa) <= ftol * fa
 
 
-def test_sy2sb_config4_invariants_on_device(br):
-    """n = 32768, w = b = 128 (8.6 GB, drawn and checked on the device): Frobenius norm and
-    trace of the band against those of A, relative to ||A||_F."""
+@pytest.fixture(scope="module")
+def config3():
+    A = workloads.gen_gaussian(N, N, 0)
+    oracle.set_threads(0)
+    Ao, tqo, tpo = oracle.ge2gb(A, W)
+    return A, Ao, tqo, tpo
+
+
+def svdvals_on_device(M):
+    """Singular values of a host matrix, by the GPU's dense SVD (test-side check only)."""
     import torch
 
-    n, w = 32768, 128
+    return torch.linalg.svdvals(torch.from_numpy(np.ascontiguousarray(M)).cuda()).cpu().numpy()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "ozaki"])
+def test_ge2gb_config3_matches_oracle(br, config3, precision):
+    """m = n = 8192, w = b = 64, N(0,1), look-ahead as bench.py runs it: the band, the
+    reflectors and tau elementwise against the oracle, and the singular values of the band
+    against those of the oracle's band and of A (the reduction is an orthogonal
+    equivalence, so all three agree to rounding relative to sigma_max)."""
+    A, Ao, tqo, tpo = config3
+    dA = to_dev(A)
+    _, tq, tp, st = br.ge2gb(dA, W, br.make_opts(b=W, lookahead=-1, precision=precision))
+    assert int(st.item()) == 0
+    Aout, tq, tp = to_host(dA), tq.cpu().numpy(), tp.cpu().numpy()
+    fa = np.linalg.norm(A)
+    i, j = np.indices((N, N))
+    band = (j - i >= 0) & (j - i <= W)
+    db = np.max(np.abs(Aout[band] - Ao[band]))
+    dv = np.max(np.abs(Aout[~band] - Ao[~band]))
+    dq, dp = np.max(np.abs(tq - tqo)), np.max(np.abs(tp - tpo))
+    Bg, Bo = np.where(band, Aout, 0.0), np.where(band, Ao, 0.0)
+    sg, so, sa = svdvals_on_device(Bg), svdvals_on_device(Bo), svdvals_on_device(A)
+    e_go, e_ga = np.max(np.abs(sg - so)) / sa[0], np.max(np.abs(sg - sa)) / sa[0]
+    print(f"\nge2gb {precision}: band {db / fa:.2e} ||A||_F, v {dv:.2e}, tauq {dq:.2e}, taup {dp:.2e}, "
+          f"sigma vs oracle band {e_go:.2e}, vs A {e_ga:.2e} (of sigma_max)")
+    assert db <= B_TOL * fa and dv <= 1e-8 and dq <= 1e-8 and dp <= 1e-8
+    assert e_go <= 1e-11 and e_ga <= 1e-11
+    assert gen_probe_backward(A, Aout, tq, tp, W, probes=4) < 1e-13
+
+
+def apply_reflectors_on_device(Aout, tau, w, X, transpose):
+    """Q^T X (transpose) or Q X through the packed reflectors of a sy2sb result held on the
+    device: H_c = I - tau_c v_c v_c^T on rows c+w.., v_c = [1; Aout(c+w+1:, c)]."""
+    import torch
+
+    X = X.clone()
+    order = range(tau.numel()) if transpose else reversed(range(tau.numel()))
+    taus = tau.cpu().numpy()
+    one = torch.ones(1, dtype=X.dtype, device=X.device)
+    for c in order:
+        t = float(taus[c])
+        if t == 0.0:
+            continue
+        r0 = c + w
+        v = torch.cat((one, Aout[r0 + 1:, c]))
+        X[r0:] -= t * torch.outer(v, v @ X[r0:])
+    return X
+
+
+def sym_band_times_on_device(Aout, w, Y):
+    """B Y with B the symmetric band held in the lower band of Aout."""
+    import torch
+
+    BY = torch.diagonal(Aout)[:, None] * Y
+    for d in range(1, w + 1):
+        dg = torch.diagonal(Aout, -d)[:, None]  # B(i + d, i)
+        BY[d:] += dg * Y[:-d]
+        BY[:-d] += dg * Y[d:]
+    return BY
+
+
+@pytest.mark.parametrize("precision,tol", [("bf16x6", SPLIT_TOL), ("ozaki", 1e-13)])
+def test_sy2sb_config4_probe_backward_on_device(br, precision, tol):
+    """n = 32768, w = b = 128 (8.6 GB, drawn and checked on the device): with 16 Gaussian
+    probes X, ||A X - Q B Q^T X||_F / ||A X||_F, Q applied through the reflectors on the
+    device (test code, torch); also the Frobenius norm and trace of the band against
+    those of A."""
+    import torch
+
+    n, w, probes = 32768, 128, 16
     g = torch.Generator(device="cuda")
     g.manual_seed(0)
     G = torch.randn((n, n), dtype=torch.float64, device="cuda", generator=g)
     A = ((G + G.t()) * 0.5).t().contiguous().t()
     del G
+    X = torch.randn((n, probes), dtype=torch.float64, device="cuda", generator=g)
+    AX = A @ X
     fa = torch.linalg.norm(A).item()
     tr = torch.trace(A).item()
-    _, tau, st = br.sy2sb(A, w, br.make_opts(b=w, lookahead=-1, precision="bf16x6"))
+    _, tau, st = br.sy2sb(A, w, br.make_opts(b=w, lookahead=-1, precision=precision))
     assert int(st.item()) == 0
+    assert torch.all(torch.isfinite(tau)).item()
+    QtX = apply_reflectors_on_device(A, tau, w, X, transpose=True)
+    QBQtX = apply_reflectors_on_device(A, tau, w, sym_band_times_on_device(A, w, QtX), transpose=False)
+    bwd = (torch.linalg.norm(AX - QBQtX) / torch.linalg.norm(AX)).item()
     d = torch.diagonal(A)
     off = sum(torch.sum(torch.diagonal(A, -k) ** 2).item() for k in range(1, w + 1))
     fb = float(np.sqrt(torch.sum(d * d).item() + 2.0 * off))
     tb = torch.sum(d).item()
-    print(f"\nn=32768: |dF|/F {abs(fb - fa) / fa:.2e}, |dtrace|/F {abs(tb - tr) / fa:.2e}")
-    assert abs(fb - fa) <= SPLIT_TOL * fa and abs(tb - tr) <= SPLIT_TOL * fa
-    assert torch.all(torch.isfinite(tau)).item()
+    print(f"\nn=32768 {precision}: probe backward {bwd:.2e}, |dF|/F {abs(fb - fa) / fa:.2e}, "
+          f"|dtrace|/F {abs(tb - tr) / fa:.2e}")
+    assert bwd <= tol
+    assert abs(fb - fa) <= max(tol, 1e-12) * fa and abs(tb - tr) <= max(tol, 1e-12) * fa
 
 
 def test_batched_config5_sampled_against_oracle(br):
