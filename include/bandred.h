@@ -277,6 +277,27 @@ int bandred_profile_end(bandred_kernel_stat* out, int max_entries);
 /* Number of kernel launches the library has issued since it was loaded. */
 long long bandred_launch_count(void);
 
+/* Device trace of the look-ahead timeline (Section 2.2's overlap, observed on the GPU).
+ * bandred_trace_begin(buf, bytes): buf is a device buffer (256-byte aligned) of 16 bytes
+ * per record; it synchronises the device, fills buf and arms the trace.  Until
+ * bandred_trace_end, every traced kernel launch of the reductions (the panels, the two
+ * halves of the rank-2k update of the Ozaki path, the X1 = A2 W product of the Ozaki
+ * path) takes one record, in launch order, and its CTAs store the earliest start and the
+ * latest end of the launch, read from the GPU's globaltimer (ns).  bandred_trace_end
+ * synchronises the device, copies up to max_records records into out and disarms the
+ * trace; it returns the number written, or a negative code.  kind: 0 panel (QR of a
+ * column panel), 1 rank-2k update of the next panel's columns (A2^L), 2 rank-2k update
+ * of the rest (A2^R, or all of A2 without look-ahead), 3 X1 = A2 W, 4 row panel (LQ),
+ * 5 left update (ge2gb), 6 right update (ge2gb); iteration = the panel's first column.
+ * Host-side, one trace at a time per process; a diagnostic, not for the hot path. */
+typedef struct bandred_trace_record {
+    int kind;
+    long long iteration;
+    unsigned long long t0_ns, t1_ns;
+} bandred_trace_record;
+int bandred_trace_begin(void* buf, size_t bytes);
+int bandred_trace_end(bandred_trace_record* out, int max_records);
+
 /* ---------------------------------------------------------------- diagnostics -------
  * The reciprocal square root and reciprocal that the panel kernels use in place of FP64
  * square root and division when they form a reflector (Section 2.1, Eq. updateA0: beta,

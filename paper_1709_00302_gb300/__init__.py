@@ -48,6 +48,15 @@ class bandred_opts(ctypes.Structure):
     ]
 
 
+class bandred_trace_record(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int),
+        ("iteration", ctypes.c_longlong),
+        ("t0_ns", ctypes.c_ulonglong),
+        ("t1_ns", ctypes.c_ulonglong),
+    ]
+
+
 class bandred_kernel_stat(ctypes.Structure):
     _fields_ = [
         ("name", ctypes.c_char * 32),
@@ -127,6 +136,10 @@ def lib():
         L.bandred_profile_end.restype = ci
         L.bandred_launch_count.argtypes = []
         L.bandred_launch_count.restype = ctypes.c_longlong
+        L.bandred_trace_begin.argtypes = [vp, sz]
+        L.bandred_trace_begin.restype = ci
+        L.bandred_trace_end.argtypes = [ctypes.POINTER(bandred_trace_record), ci]
+        L.bandred_trace_end.restype = ci
         L.bandred_newton_eval.argtypes = [i64, vp, vp, vp, vp]
         L.bandred_newton_eval.restype = ci
         L.bandred_fp64_probe.argtypes = [ci, ci, ci, vp, vp]
@@ -379,6 +392,25 @@ class GeBatch:
         return lib().bandred_ge2gb_batched_run(self.count, self.m, self.n, self.w, self.A, self.lda, self.tauq,
                                                self.taup, ctypes.byref(self.opts), _ptr(work), work.numel(),
                                                _ptr(dev_status), _stream(stream))
+
+
+TRACE_KINDS = {0: "panel", 1: "rank_next_panel", 2: "rank_rest", 3: "x1_product", 4: "row_panel", 5: "left_update",
+               6: "right_update"}
+
+
+def bandred_trace_begin(buf) -> int:
+    """Arms the device trace with a device uint8 tensor (16 bytes per record)."""
+    return lib().bandred_trace_begin(_ptr(buf), buf.numel() * buf.element_size())
+
+
+def bandred_trace_end(max_records: int = 65536) -> list:
+    """The records since bandred_trace_begin: dicts with kind, iteration, t0_ns, t1_ns."""
+    arr = (bandred_trace_record * max_records)()
+    n = lib().bandred_trace_end(arr, max_records)
+    if n < 0:
+        raise BandredError(n, "bandred_trace_end")
+    return [{"kind": TRACE_KINDS.get(arr[i].kind, str(arr[i].kind)), "iteration": arr[i].iteration,
+             "t0_ns": arr[i].t0_ns, "t1_ns": arr[i].t1_ns} for i in range(n)]
 
 
 def bandred_newton_eval(x, rsqrt=None, rcp=None, stream=None) -> int:

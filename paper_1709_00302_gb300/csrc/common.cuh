@@ -95,6 +95,15 @@ __device__ __forceinline__ bool grid_wait(GridSync* gs, unsigned int generation,
   }
 }
 
+// Device trace stamps (see prof.h): the earliest start and the latest end over the CTAs
+// of a launch, the end stored complemented so that both take an atomic minimum.
+__device__ __forceinline__ void trace_start(unsigned long long* rec) {
+  if (rec && threadIdx.x == 0) atomicMin(rec, global_ns());
+}
+__device__ __forceinline__ void trace_end(unsigned long long* rec) {
+  if (rec && threadIdx.x == 0) atomicMin(rec + 1, ~global_ns());
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -290,6 +290,7 @@ static int run_panel(double* A, int64_t rs, int64_t cs, int j, int bk, double* t
                      int64_t ldy, double* acc, double* rowbuf, GridSync* gs, int* status,
                      const Options& o, int max_ctas, unsigned int extra, cudaStream_t s) {
   PanelParams p{};
+  p.trace = prof::trace_take();
   // Short panels: one thread-block cluster (no grid-wide barrier, deterministic sums).
   if (extra == 0) {
     int C = 1;
@@ -414,6 +415,7 @@ struct Sy2sb {
     const int64_t r0 = k + w;
     const int j = (int)(n - r0);
     prof::Scope sc(prof::kPanel, s, panel_flops(j, bk), panel_bytes(j, bk));
+    prof::TraceScope tr(prof::kTracePanel, k);
     int rc = run_panel(A + r0 + k * lda, 1, lda, j, bk, tau + k, ws.Y[buf], ws.W[buf], ws.ld, ws.part, ws.rowbuf,
                        ws.gs, status, o, ctas > 0 ? std::min(ctas, pmax) : pmax, extra, s);
     extra = 0;
@@ -463,6 +465,7 @@ struct Sy2sb {
       {
         // X1 = A2 W (A2 symmetric, lower stored; row (n, k) of the right operand is W(k, n))
         prof::Scope sc(prof::kSymm, s, symm_flops(j, bk), symm_bytes(j, bk));
+        prof::TraceScope tr(prof::kTraceSymm, k);
         const int sp = ozaki::fit_splits(j, B, j, ozaki::choose_splits(j, B, j, sms), ws.ozp_cap);
         const Operand a{A2, lda, 2, j, nullptr, 0, 0, 0, j}, w{W, ld, 1, j, nullptr, 0, 0, 0, B};
         CK(ozaki::product(a, w, j, B, j, 1.0, 0.0, ws.X, ld, ozaki::carve(ws.ozp, j, B, j, sp), sp, status, lim, s));
@@ -638,6 +641,7 @@ struct Sy2sb {
     double* A2 = A + r0 + r0 * lda;
     prof::Scope sc(prof::kSyr2k, s, syr2k_flops(j, c0, c1, bk), syr2k_bytes(j, c0, c1, bk));
     if (o.precision == BANDRED_OZAKI) {
+      prof::TraceScope tr(c0 == 0 && c1 < j ? prof::kTraceRankL : prof::kTraceRankR, k);
       CK(ozaki::rank_apply(j, j, 2 * bk, 1.0, A2, lda, c0, c1, 1, rank2k_bufs(j, bk), status,
                            o.limit_ns, s, max_ctas));
       return 0;
@@ -908,6 +912,7 @@ struct Ge2gb {
     const int bk = bk_of(k);
     const int j = (int)(m - k);
     prof::Scope sc(prof::kPanel, s, panel_flops(j, bk), panel_bytes(j, bk));
+    prof::TraceScope tr(prof::kTracePanel, k);
     int rc = run_panel(A + k + k * lda, 1, lda, j, bk, tauq + k, ws.Yu[buf], ws.Wu[buf], ws.ldu, ws.part,
                        ws.rowbuf, ws.gs, status, o, pmax, extra, s);
     extra = 0;
@@ -946,6 +951,7 @@ struct Ge2gb {
       const Operand yu{ws.Yu[buf], ws.ldu, 0, bk, nullptr, 0, 0, 0, j}, zt{ZT, ws.ldv, 0, bk, nullptr, 0, 0, 0, nc};
       const ozaki::Bufs rb = ozaki::carve(ws.ozr[q], j, nc, bk, 1);
       CK(ozaki::prepare(yu, zt, rb, s));
+      prof::TraceScope tr(prof::kTraceLeft, k);
       CK(ozaki::rank_apply(j, nc, bk, 1.0, E, lda, 0, nc, 0, rb, status, o.limit_ns, s));
       return 0;
     }
@@ -962,6 +968,7 @@ struct Ge2gb {
     if (bkr <= 0) return 0;
     const int jr = (int)(n - k - w);
     prof::Scope sc(prof::kPanel, s, panel_flops(jr, (int)bkr), panel_bytes(jr, (int)bkr));
+    prof::TraceScope tr(prof::kTracePanelRow, k);
     return run_panel(A + k + (k + w) * lda, lda, 1, jr, (int)bkr, taup + k, ws.Yv, ws.Wv, ws.ldv, ws.part, ws.rowbuf,
                      ws.gs, status, o, pmax, 0u, s);
   }
@@ -998,6 +1005,7 @@ struct Ge2gb {
       const Operand pp{ws.P, ws.ldu, 0, B, nullptr, 0, 0, 0, nrow}, yv{ws.Yv, ws.ldv, 0, B, nullptr, 0, 0, 0, jr};
       const ozaki::Bufs rb = ozaki::carve(ws.ozr[0], nrow, jr, B, 1);
       CK(ozaki::prepare(pp, yv, rb, s));
+      prof::TraceScope tr(prof::kTraceRight, k);
       CK(ozaki::rank_apply(nrow, jr, B, 1.0, D, lda, 0, jr, 0, rb, status, o.limit_ns, s));
       return 0;
     }

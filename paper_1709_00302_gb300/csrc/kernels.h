@@ -26,6 +26,7 @@ struct PanelParams {
   unsigned int extra;    // extra awaited arrivals (tests of the timeout path)
   bool w_in_smem;        // this CTA's rows of W kept in shared memory during the panel
   bool w_fp32;           // W formed in FP32 (it only feeds split-precision products)
+  unsigned long long* trace;  // device trace record of this launch, or nullptr
 };
 
 size_t panel_smem_bytes(int bk, int Rp, bool w_in_smem);

@@ -420,6 +420,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_kernel(GemmParams p) {
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_holder;
   pdl_wait_and_release();
+  trace_start(p.trace);
   int timed_out = 0;
   long long thi[32], tlo[32];
 #pragma unroll
@@ -540,6 +541,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_kernel(GemmParams p) {
     tc::fence_after_sync();
     tc::tmem_dealloc(tmem, kTmemCols);
   }
+  trace_end(p.trace);
 }
 
 // Persistent form of the direct mode (C += alpha A B^T, the rank-2k updates): one CTA per
@@ -593,6 +595,7 @@ __global__ void __launch_bounds__(kRankThreads, 1) rank_kernel(GemmParams p) {
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_holder;
   pdl_wait_and_release();
+  trace_start(p.trace);
   const int nt = s_nt;
   const int total = nt * nkb;
   int timed_out = 0;
@@ -696,6 +699,7 @@ __global__ void __launch_bounds__(kRankThreads, 1) rank_kernel(GemmParams p) {
     tc::fence_after_sync();
     tc::tmem_dealloc(tmem, kTmemCols);
   }
+  trace_end(p.trace);
 }
 
 // ---------------------------------------------------------------- streamed left operand
@@ -731,6 +735,7 @@ struct StreamParams {
   int64_t ldp, sstride;
   int* status;
   unsigned long long limit_ns;
+  unsigned long long* trace;
 };
 
 __global__ void __launch_bounds__(kStreamThreads, 1)
@@ -772,6 +777,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_holder;
   pdl_wait_and_release();
+  trace_start(p.trace);
 
   // 0: box read in place; 1: box of the mirror (transposed); 2: symmetric box across the diagonal
   auto kind_of = [&](int kb) -> int {
@@ -943,6 +949,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
     tc::fence_after_sync();
     tc::tmem_dealloc(tmem, kTmemCols);
   }
+  trace_end(p.trace);
 }
 
 __global__ void reduce_kernel(const int64_t* Phi, const int64_t* Plo, int64_t ldp, int64_t sstride, int splits,
@@ -1194,6 +1201,7 @@ bool stream_product(const Operand& A, const Operand& B, int M, int N, int K, dou
     sp.ldp = M;
     sp.status = status;
     sp.limit_ns = limit_ns;
+    sp.trace = prof::trace_take();
     prof::count_launch();
     if ((e = launch_pdl(stream_kernel, dim3((M + kTileA - 1) / kTileA, used), dim3(kStreamThreads), StreamSmem::total, s,
                         sp, lo, up)) != cudaSuccess)
@@ -1239,6 +1247,7 @@ cudaError_t product(const Operand& A, const Operand& B, int M, int N, int K, dou
   p.ldp = M;
   p.status = status;
   p.limit_ns = limit_ns;
+  p.trace = prof::trace_take();
   e = gemm(p, used, s);
   if (e != cudaSuccess) return e;
   return reduce(p, used, alpha, beta, C, ldc, s);
@@ -1264,6 +1273,7 @@ cudaError_t rank_apply(int M, int N, int K, double alpha, double* C, int64_t ldc
   p.alpha = alpha;
   p.status = status;
   p.limit_ns = limit_ns;
+  p.trace = prof::trace_take();
   static int configured = -1;
   int dev = 0;
   cudaGetDevice(&dev);

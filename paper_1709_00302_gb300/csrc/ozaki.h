@@ -70,6 +70,7 @@ struct GemmParams {
   double alpha;
   int* status;
   unsigned long long limit_ns;
+  unsigned long long* trace;  // device trace record of this launch, or nullptr
 };
 cudaError_t gemm(const GemmParams& p, int splits, cudaStream_t s);
 

@@ -60,6 +60,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
   __shared__ double s_beta, s_tau, s_scal, s_dscal, s_beta2, s_tau2, s_scal2, s_zb, s_Taa, s_Tab;
   __shared__ double s_ptau[2];
   __shared__ int s_rescale, s_ok, s_pair;
+  trace_start(p.trace);
 
   if (p.rs == 1) {
     for (int idx = tid; idx < nr * bk; idx += NT) {
@@ -437,6 +438,8 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
       p.Y[gr + (int64_t)c * p.ldy] = gr > c ? slab[(size_t)c * Rp + r] : (gr == c ? 1.0 : 0.0);
     }
   }
+  __syncthreads();
+  trace_end(p.trace);
 }
 
 }  // namespace

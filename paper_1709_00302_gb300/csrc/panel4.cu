@@ -53,6 +53,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr4_kernel(PanelParams
   __shared__ double s_ptau[MB];
   __shared__ double s_amax, s_dfac;
   __shared__ int s_rescale, s_ok, s_meff;
+  trace_start(p.trace);
 
   if (p.rs == 1) {
     for (int idx = tid; idx < nr * bk; idx += NT) {
@@ -514,6 +515,8 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr4_kernel(PanelParams
       p.Y[gr + (int64_t)c * p.ldy] = gr > c ? slab[(size_t)c * Rp + r] : (gr == c ? 1.0 : 0.0);
     }
   }
+  __syncthreads();
+  trace_end(p.trace);
 }
 
 }  // namespace

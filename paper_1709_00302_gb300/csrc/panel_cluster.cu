@@ -51,6 +51,7 @@ __global__ void __launch_bounds__(kPanelThreads, 4)
   float* wlf = reinterpret_cast<float*>(after);
   __shared__ double s_beta, s_tau, s_scal, s_dscal, s_tau_prev;
   __shared__ int s_rescale;
+  trace_start(p.trace);
 
   if (p.rs == 1) {
     for (int idx = tid; idx < nr * bk; idx += NT) {
@@ -266,6 +267,7 @@ __global__ void __launch_bounds__(kPanelThreads, 4)
     }
   }
   cluster.sync();  // no CTA leaves while a peer may still read its shared memory
+  trace_end(p.trace);
 }
 
 }  // namespace

@@ -1,6 +1,8 @@
 // Implementation of the event-based kernel profiler (see prof.h) and the C entry points
 // bandred_profile_begin / bandred_profile_end / bandred_launch_count.
+#include <algorithm>
 #include <atomic>
+#include <cstdint>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -60,6 +62,40 @@ Scope::~Scope() {
   if (slot_ < (int)g_records.size()) cudaEventRecord(g_records[slot_].e1, s_);
 }
 
+// ---------------------------------------------------------------- device trace
+namespace {
+
+struct TraceMeta {
+  int kind;
+  long long iteration;
+};
+
+std::mutex g_tmu;
+unsigned long long* g_tbuf = nullptr;  // device: 2 words per record (min start, min of ~end)
+size_t g_tcap = 0;
+std::vector<TraceMeta> g_tmeta;
+thread_local int t_pending_kind = -1;
+thread_local long long t_pending_iter = 0;
+
+}  // namespace
+
+TraceScope::TraceScope(int kind, long long iteration) {
+  t_pending_kind = kind;
+  t_pending_iter = iteration;
+}
+
+TraceScope::~TraceScope() { t_pending_kind = -1; }
+
+unsigned long long* trace_take() {
+  if (t_pending_kind < 0) return nullptr;
+  std::lock_guard<std::mutex> lock(g_tmu);
+  const int kind = t_pending_kind;
+  t_pending_kind = -1;
+  if (!g_tbuf || g_tmeta.size() >= g_tcap) return nullptr;
+  g_tmeta.push_back(TraceMeta{kind, t_pending_iter});
+  return g_tbuf + 2 * (g_tmeta.size() - 1);
+}
+
 }  // namespace prof
 }  // namespace bandred
 
@@ -102,5 +138,44 @@ int bandred_profile_end(bandred_kernel_stat* out, int max_entries) {
 }
 
 long long bandred_launch_count(void) { return launches(); }
+
+int bandred_trace_begin(void* dev_buf, size_t bytes) {
+  if (!dev_buf || (reinterpret_cast<uintptr_t>(dev_buf) & 255u)) return -1;
+  if (bytes < 16) return -2;
+  std::lock_guard<std::mutex> lock(g_tmu);
+  // every word all ones: the start stamps and the complemented end stamps both take the minimum
+  if (cudaMemset(dev_buf, 0xFF, bytes / 16 * 16) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
+    return BANDRED_ERR_CUDA;
+  g_tbuf = static_cast<unsigned long long*>(dev_buf);
+  g_tcap = bytes / 16;
+  g_tmeta.clear();
+  return 0;
+}
+
+int bandred_trace_end(bandred_trace_record* out, int max_records) {
+  if (max_records < 0 || (max_records > 0 && !out)) return -2;
+  std::vector<TraceMeta> meta;
+  unsigned long long* buf;
+  {
+    std::lock_guard<std::mutex> lock(g_tmu);
+    meta.swap(g_tmeta);
+    buf = g_tbuf;
+    g_tbuf = nullptr;
+    g_tcap = 0;
+  }
+  if (!buf) return 0;
+  const int n = (int)std::min<size_t>(meta.size(), (size_t)max_records);
+  std::vector<unsigned long long> host(2 * (size_t)n);
+  if (cudaDeviceSynchronize() != cudaSuccess) return BANDRED_ERR_CUDA;
+  if (n && cudaMemcpy(host.data(), buf, host.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return BANDRED_ERR_CUDA;
+  for (int i = 0; i < n; ++i) {
+    out[i].kind = meta[i].kind;
+    out[i].iteration = meta[i].iteration;
+    out[i].t0_ns = host[2 * i];
+    out[i].t1_ns = ~host[2 * i + 1];  // ~0 when the kernel never ran
+  }
+  return n;
+}
 
 }  // extern "C"

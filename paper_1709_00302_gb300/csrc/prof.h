@@ -29,5 +29,21 @@ class Scope {
   cudaStream_t s_;
 };
 
+// Device trace (bandred_trace_begin / bandred_trace_end).  A TraceScope names the next
+// traced launch on this host thread (its kind and panel column); the launcher of that
+// kernel takes the record with trace_take() (nullptr when tracing is off or the buffer is
+// full) and passes it to the kernel, whose CTAs stamp their start and end into it
+// (trace_start / trace_end in common.cuh).
+enum TraceKind { kTracePanel = 0, kTraceRankL, kTraceRankR, kTraceSymm, kTracePanelRow, kTraceLeft, kTraceRight };
+
+class TraceScope {
+ public:
+  TraceScope(int kind, long long iteration);
+  ~TraceScope();
+  TraceScope(const TraceScope&) = delete;
+  TraceScope& operator=(const TraceScope&) = delete;
+};
+unsigned long long* trace_take();
+
 }  // namespace prof
 }  // namespace bandred
