@@ -185,9 +185,14 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
 
     // Thread 0 derives the reflector(s) from a few sums while warps 1..7 fetch the rest.
     if (tid == 0) {
+      // every sum and row entry thread 0 needs, loaded at once (one round trip to L2);
+      // the pair's are read even when the step takes one reflector (valid addresses)
       const double alpha = ldcg(&rowg[i]);
       const double ssq = ldcg(&acc[(size_t)i * kAccStride]);
       const double amax = ldcg(&acc[(size_t)bk * kAccStride]);
+      const double Sab = ldcg(&acc[(size_t)(i + 1) * kAccStride]);
+      const double Sbb = ldcg(&acc[(size_t)(bk + 2 + i) * kAccStride]);
+      const double bi = ldcg(&rowg[i + 1]), ai1 = ldcg(&rowg[bk + i]), bi1 = ldcg(&rowg[bk + i + 1]);
       const int rescale = (p.j - i > 1) && (amax > 0.0) && !(ssq < 0x1p1000 && amax > 0x1p-450);
       s_rescale = rescale || !(fabs(alpha) < 0x1p500);
       // Common path: h = ||[alpha; x2]|| = q / sqrt(q) with q = alpha^2 + ||x2||^2 (no
@@ -218,9 +223,6 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
       // step takes reflector i alone and the next step starts from a fresh reduction.
       int pair = 0;
       if (want_pair && !s_rescale) {
-        const double Sab = ldcg(&acc[(size_t)(i + 1) * kAccStride]);
-        const double Sbb = ldcg(&acc[(size_t)(bk + 2 + i) * kAccStride]);
-        const double bi = ldcg(&rowg[i + 1]), ai1 = ldcg(&rowg[bk + i]), bi1 = ldcg(&rowg[bk + i + 1]);
         const double zb = tau * fma(scal, Sab, bi);
         const double zs = zb * scal;
         const double Taa = fma(-ai1, ai1, ssq), Tab = fma(-ai1, bi1, Sab), Tbb = fma(-bi1, bi1, Sbb);
