@@ -65,10 +65,12 @@ typedef struct bandred_opts {
     int lookahead;         /* -1 auto, 0 none, 1 V1, 2 V2 */
     int precision;         /* enum bandred_precision */
     int slices;            /* reserved for the digit count of BANDRED_OZAKI; ignored */
-    int panel_ctas;        /* CTAs of the panel factorisation (0 = all SMs when no
-                              look-ahead, a tuned share otherwise).  Batched calls: CTAs
-                              (one thread-block cluster, rounded up to a power of two
-                              <= 16) per matrix panel; 0 = about 128 rows per CTA */
+    int panel_ctas;        /* CTAs of the panel factorisation (0 = all SMs; with V2
+                              look-ahead and BANDRED_OZAKI the next panel takes half the
+                              SMs and the rest of the trailing update the others; a value
+                              > 0 sets that share).  Batched calls: CTAs (one thread-block
+                              cluster, rounded up to a power of two <= 16) per matrix
+                              panel; 0 = about 128 rows per CTA */
     int timeout_ms;        /* limit of every device-side wait (0 = 2000 ms) */
     int debug;             /* 0.  Tests only: 1 makes the first device-side wait
                               unsatisfiable, so the call ends through its bounded-wait
@@ -78,7 +80,10 @@ typedef struct bandred_opts {
                               barriers, four times the serial scalar work; slower on GB300).
                               Both give the Householder reflectors of Section 2.1 up to
                               rounding */
-    int reserved[8];       /* must be zero */
+    int depth;             /* look-ahead depth: 0 = default (1); 2 factors the panel two
+                              iterations ahead, only with V1 and 3b <= w (that panel is then
+                              reached by one-sided updates alone); otherwise 1 is used */
+    int reserved[7];       /* must be zero */
 } bandred_opts;
 
 /* Device-side status codes written to dev_status. */

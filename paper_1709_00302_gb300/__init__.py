@@ -44,7 +44,8 @@ class bandred_opts(ctypes.Structure):
         ("timeout_ms", ctypes.c_int),
         ("debug", ctypes.c_int),
         ("panel_group", ctypes.c_int),
-        ("reserved", ctypes.c_int * 8),
+        ("depth", ctypes.c_int),
+        ("reserved", ctypes.c_int * 7),
     ]
 
 
@@ -161,7 +162,7 @@ def lib():
 
 
 def make_opts(b: int = 0, lookahead: int = -1, precision="fp64", slices: int = 0, panel_ctas: int = 0,
-              timeout_ms: int = 0, debug: int = 0, panel_group: int = 0) -> bandred_opts:
+              timeout_ms: int = 0, debug: int = 0, panel_group: int = 0, depth: int = 0) -> bandred_opts:
     o = bandred_opts()
     lib().bandred_default_opts(ctypes.byref(o))
     o.b = b
@@ -172,6 +173,7 @@ def make_opts(b: int = 0, lookahead: int = -1, precision="fp64", slices: int = 0
     o.timeout_ms = timeout_ms
     o.debug = debug
     o.panel_group = panel_group
+    o.depth = depth
     return o
 
 

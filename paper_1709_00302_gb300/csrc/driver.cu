@@ -118,6 +118,7 @@ int resolve_options(const bandred_opts* in, int64_t w, Options* o) {
   if (d.panel_ctas < 0 || d.timeout_ms < 0) return -1;
   if (d.debug < 0 || d.debug > 1) return -1;
   if (d.panel_group != 0 && d.panel_group != 2 && d.panel_group != 4) return -1;
+  if (d.depth < 0 || d.depth > 2) return -1;
   o->b = d.b;
   o->lookahead = d.lookahead;
   o->precision = d.precision;
@@ -126,13 +127,14 @@ int resolve_options(const bandred_opts* in, int64_t w, Options* o) {
   o->limit_ns = (unsigned long long)(d.timeout_ms ? d.timeout_ms : 2000) * 1000000ull;
   o->debug = d.debug;
   o->panel_group = d.panel_group ? d.panel_group : 2;
+  o->depth = d.depth ? d.depth : 1;
   return 0;
 }
 
 // Workspace of sy2sb (layout shared by sizing and carving).  Y and W are double-buffered:
 // with look-ahead the next panel writes one pair while the current update reads the other.
 struct Sy2sbWs {
-  double *Y[2], *W[2], *X, *X2;
+  double *Y[3], *W[3], *X, *X2;
   double *Z[2], *splitk[2];  // FP64 small products; [1] belongs to the panel stream
   double *part, *rowbuf;
   GridSync* gs;
@@ -152,17 +154,35 @@ struct Sy2sbWs {
 
 static bool is_split(const Options& o) { return o.precision == BANDRED_BF16X3 || o.precision == BANDRED_BF16X6; }
 
+// Look-ahead of sy2sb (Section 2.2): 0 none, 1 Variant V1 (2b <= w: the next panel lies in
+// A1), 2 Variant V2 (2b > w: it lies in A2).  Auto picks the variant the sizes allow.
+static int sy2sb_variant(const Options& o, int64_t w) {
+  int la = o.lookahead;
+  if (la < 0) la = (2 * o.b > w) ? 2 : 1;
+  if (la == 1 && 2 * o.b > w) la = 0;  // V1 needs 2b <= w
+  if (la == 2 && 2 * o.b <= w) la = 1;
+  return la;
+}
+
+// Depth 2 (the panel two iterations ahead) is open to V1 when 3b <= w: that panel's columns
+// then lie in A1 of this iteration and of the next, so one-sided updates alone reach it.
+static int sy2sb_depth(const Options& o, int64_t w) {
+  return (o.depth == 2 && sy2sb_variant(o, w) == 1 && 3 * (int64_t)o.b <= w) ? 2 : 1;
+}
+
 static Sy2sbWs carve_sy2sb(void* work, int64_t n, int64_t w, const Options& o, int sms) {
   Carver c{static_cast<char*>(work)};
   Sy2sbWs ws{};
   const int64_t jmax = std::max<int64_t>(n - w, 1);
   const int64_t b = o.b;
   ws.ld = jmax;
-  // the second Y/W pair and the panel stream's product buffers exist only with look-ahead
+  // Y/W: one pair per panel alive at once (1 without look-ahead, 2 at depth 1, 3 at depth
+  // 2); the panel stream's product buffers exist only with look-ahead
   const int nbuf = o.lookahead == 0 ? 1 : 2;
-  for (int q = 0; q < 2; ++q) {
-    ws.Y[q] = q < nbuf ? c.take<double>(jmax * b) : ws.Y[0];
-    ws.W[q] = q < nbuf ? c.take<double>(jmax * b) : ws.W[0];
+  const int nyw = o.lookahead == 0 ? 1 : 1 + sy2sb_depth(o, w);
+  for (int q = 0; q < 3; ++q) {
+    ws.Y[q] = q < nyw ? c.take<double>(jmax * b) : ws.Y[0];
+    ws.W[q] = q < nyw ? c.take<double>(jmax * b) : ws.W[0];
   }
   ws.X = c.take<double>(jmax * b);
   ws.X2 = c.take<double>(b * b);
@@ -705,10 +725,7 @@ int sy2sb_run(int64_t n, int64_t w, double* A, int64_t lda, double* tau, const O
   if (nref <= 0) return 0;
   CK(cudaMemsetAsync(tau, 0, sizeof(double) * nref, s));
   const int b = o.b;
-  int la = o.lookahead;
-  if (la < 0) la = (2 * b > w) ? 2 : 1;
-  if (la == 1 && 2 * b > w) la = 0;  // V1 needs 2b <= w
-  if (la == 2 && 2 * b <= w) la = 1;
+  const int la = sy2sb_variant(o, w);
   const int64_t last = n - w - 2;  // panels start at k <= n-w-2
 
   if (la == 0) {
@@ -743,6 +760,45 @@ int sy2sb_run(int64_t n, int64_t w, double* A, int64_t lda, double* tau, const O
   int rc = R.panel(0, 0, sp);
   if (rc) return rc;
   CK(cudaEventRecord(ev_panel, sp));
+
+  if (sy2sb_depth(o, w) == 2) {
+    // Depth 2 (V1 with 3b <= w): when iteration t starts, panels t and t + 1 are factored.
+    // The panel stream applies Q_t^T and Q_{t+1}^T to the columns of panel t + 2 (they lie
+    // in A1 of both iterations, so no two-sided update reaches them) and factors it while
+    // the caller's stream updates the rest of A1 and A2 for iteration t.  Y/W of panels t,
+    // t + 1, t + 2 live in buffers t mod 3 ..; evp[t & 1] marks panel t factored.
+    cudaEvent_t evp[2] = {ev_panel, ax->ev[2]};
+    if (b <= last) {
+      const int b1 = (int)std::min<int64_t>(b, n - w - 1 - b);
+      if ((rc = R.update_a1(0, 0, 0, b1, 1, sp))) return rc;
+      if ((rc = R.panel(b, 1, sp))) return rc;
+      CK(cudaEventRecord(evp[1], sp));
+    }
+    for (int64_t k = 0, t = 0; k <= last; k += b, ++t) {
+      const int bt = (int)std::min<int64_t>(b, n - w - 1 - k);
+      const int64_t k1 = k + b, k2 = k + 2 * b;
+      const int b1 = k1 <= last ? (int)std::min<int64_t>(b, n - w - 1 - k1) : 0;
+      const int b2 = k2 <= last ? (int)std::min<int64_t>(b, n - w - 1 - k2) : 0;
+      const int bt0 = (int)(t % 3), bt1 = (int)((t + 1) % 3), bt2 = (int)((t + 2) % 3);
+      CK(cudaStreamWaitEvent(s, evp[t & 1], 0));  // panel t factored
+      if (b2 > 0) {
+        CK(cudaEventRecord(ev_fork, s));  // iteration t - 1 done (its A1 update reached panel t + 2)
+        CK(cudaStreamWaitEvent(sp, ev_fork, 0));
+        if ((rc = R.update_a1(k, bt0, b1, b1 + b2, 1, sp))) return rc;  // Q_t^T (A1 of iteration t)
+        if ((rc = R.update_a1(k1, bt1, 0, b2, 1, sp))) return rc;       // Q_{t+1}^T (A1 of t + 1)
+        if ((rc = R.panel(k2, bt2, sp))) return rc;
+        CK(cudaEventRecord(evp[t & 1], sp));  // panel t + 2: the same parity as t
+      }
+      // A1 of iteration t without the columns of panels t + 1 and t + 2, then A2
+      if ((rc = R.update_a1(k, bt0, b1 + b2, (int)(w - bt), 0, s))) return rc;
+      if ((rc = R.compute_x(k, bt0, s))) return rc;
+      if ((rc = R.syr2k(k, bt0, 0, (int)(n - k - w), s))) return rc;
+    }
+    CK(cudaEventRecord(ev_fork, sp));
+    CK(cudaStreamWaitEvent(s, ev_fork, 0));
+    return 0;
+  }
+
   int buf = 0;
   for (int64_t k = 0; k <= last; k += b, buf ^= 1) {
     const int bk = (int)std::min<int64_t>(b, n - w - 1 - k);

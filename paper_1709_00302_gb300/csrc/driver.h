@@ -17,6 +17,7 @@ struct Options {
   unsigned long long limit_ns;
   int debug;
   int panel_group;  // reflectors per grid-wide reduction of the panel: 2 (default) or 4
+  int depth;        // look-ahead depth: 1, or 2 (V1 with 3b <= w)
 };
 
 // Records a failed CUDA call (readable through bandred_last_error) and returns

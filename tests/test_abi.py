@@ -65,6 +65,9 @@ def test_invalid_arguments_are_rejected_before_any_device_work(L):
     bad.b = 2
     bad.reserved[3] = 1
     assert L.bandred_sy2sb_ex(10, 4, fake, 10, fake, ctypes.byref(bad), null, 0, null, null) == -6
+    bad.reserved[3] = 0
+    bad.depth = 3  # look-ahead depth beyond 2
+    assert L.bandred_sy2sb_ex(10, 4, fake, 10, fake, ctypes.byref(bad), null, 0, null, null) == -6
     # ge2gb: n > m, w < 1, lda < m
     assert L.bandred_ge2gb_ex(4, 5, 1, fake, 4, fake, fake, None, null, 0, null, null) == -2
     assert L.bandred_ge2gb_ex(6, 5, 0, fake, 6, fake, fake, None, null, 0, null, null) == -3
