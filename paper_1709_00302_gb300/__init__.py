@@ -141,6 +141,8 @@ def lib():
         L.bandred_trace_begin.restype = ci
         L.bandred_trace_end.argtypes = [ctypes.POINTER(bandred_trace_record), ci]
         L.bandred_trace_end.restype = ci
+        L.bandred_panel_phase_trace.argtypes = [vp, ci]
+        L.bandred_panel_phase_trace.restype = ci
         L.bandred_newton_eval.argtypes = [i64, vp, vp, vp, vp]
         L.bandred_newton_eval.restype = ci
         L.bandred_fp64_probe.argtypes = [ci, ci, ci, vp, vp]
@@ -413,6 +415,11 @@ def bandred_trace_end(max_records: int = 65536) -> list:
         raise BandredError(n, "bandred_trace_end")
     return [{"kind": TRACE_KINDS.get(arr[i].kind, str(arr[i].kind)), "iteration": arr[i].iteration,
              "t0_ns": arr[i].t0_ns, "t1_ns": arr[i].t1_ns} for i in range(n)]
+
+
+def bandred_panel_phase_trace(buf) -> int:
+    """Arms the phase timing of the next grid panel into the device int64 tensor buf (8 per step)."""
+    return lib().bandred_panel_phase_trace(_ptr(buf), buf.numel() // 8)
 
 
 def bandred_newton_eval(x, rsqrt=None, rcp=None, stream=None) -> int:

@@ -312,6 +312,7 @@ static int run_panel(double* A, int64_t rs, int64_t cs, int j, int bk, double* t
   PanelParams p{};
   p.trace = prof::trace_take();
   // Short panels: one thread-block cluster (no grid-wide barrier, deterministic sums).
+  // (The phase trace is taken only by the grid panel below.)
   if (extra == 0) {
     int C = 1;
     while (C < kClusterMax && (j + C - 1) / C > kClusterRows) C *= 2;
@@ -358,6 +359,7 @@ static int run_panel(double* A, int64_t rs, int64_t cs, int j, int bk, double* t
   p.extra = extra;
   p.w_in_smem = w_smem;
   p.w_fp32 = is_split(o);
+  p.phases = prof::phase_take(&p.phase_steps);
   // four reflectors per grid-wide reduction when the caller asks for them and their larger
   // shared-memory footprint fits; pairs otherwise (the default: on GB300 the four-reflector
   // derivation's serial FP64 work costs more than the grid barrier it saves)
@@ -411,6 +413,39 @@ static int stream_splits(int tiles, int nkb, int sms, int cap) {
       best = sp;
     }
     if (eff >= 0.9) break;
+  }
+  return best;
+}
+
+// SMs for the look-ahead panel of V2 (jp x bp rows and columns) while the rank-2k update of
+// the rest of A2 (order j, rank 2 bu) holds the others.  A model of the two durations on
+// GB300, fitted to device traces of the Ozaki path at n = 8192, w = b = 64:
+//   panel  ~ 8.5 us per pair of reflectors (latency) + 7.9e-4 us x jp bp^2 / P,
+//   update ~ 1.23e-5 us x j^2 bu / (sms - P),
+// and P minimises the larger of the two.  P never drops below the CTA count at which the
+// panel's rows still fit in shared memory; fixed > 0 overrides the model.
+static int lookahead_panel_ctas(int jp, int bp, int j, int bu, int sms, int fixed) {
+  if (jp <= kClusterMax * kClusterRows) return std::min(kClusterMax, sms - 1);  // a cluster panel
+  const int pmax = std::min(sms - 1, (jp + kMinPanelRows - 1) / kMinPanelRows);  // CTAs a grid panel uses
+  int pmin = 1;
+  while (pmin < sms) {
+    int G, Rr, Rp;
+    bool wsm;
+    if (panel_geometry(jp, bp, pmin, kMinPanelRows, &G, &Rr, &Rp, &wsm) == 0) break;
+    ++pmin;
+  }
+  if (pmin >= sms) return sms;  // only the whole GPU holds the panel: the update waits
+  if (fixed > 0) return std::max(pmin, std::min(fixed, sms - 1));
+  int best = std::min(pmin, pmax);
+  double best_t = 1e300;
+  for (int P = pmin; P <= pmax; ++P) {
+    const double tp = 8.5 * (bp / 2.0) + 7.9e-4 * (double)jp * bp * bp / P;
+    const double tu = 1.23e-5 * (double)j * j * bu / (sms - P);
+    const double t = std::max(tp, tu);
+    if (t < best_t) {
+      best_t = t;
+      best = P;
+    }
   }
   return best;
 }
@@ -742,14 +777,11 @@ int sy2sb_run(int64_t n, int64_t w, double* A, int64_t lda, double* tau, const O
   }
 
   if (last < 0) return 0;  // no panel: every reflector has length <= 1
-  // V2's two streams at once: the next panel on la_panel SMs while the rest of the rank-2k
-  // update holds the others (the Ozaki update can be held to a CTA count; the other
-  // precisions' updates take every SM, so their panel waits for free SMs instead).
-  int la_panel = 0, la_update = 0;
-  if (la == 2 && o.precision == BANDRED_OZAKI) {
-    la_panel = o.panel_ctas > 0 ? std::min(o.panel_ctas, R.sms - 1) : std::max(1, R.sms / 2);
-    la_update = R.sms - la_panel;
-  }
+  // V2's two streams at once: the next panel on P SMs while the rest of the rank-2k update
+  // holds the others (the Ozaki update can be held to a CTA count; the other precisions'
+  // updates take every SM, so their panel waits for free SMs instead).  P is chosen per
+  // iteration (la_split), or fixed by opts->panel_ctas.
+  const bool la_split = la == 2 && o.precision == BANDRED_OZAKI;
   AuxStreams* ax = nullptr;
   if (int rc = aux_streams(&ax)) return rc;
   cudaStream_t sp = ax->panel;
@@ -816,9 +848,10 @@ int sy2sb_run(int64_t n, int64_t w, double* A, int64_t lda, double* tau, const O
         CK(cudaEventRecord(ev_fork, s));
         CK(cudaStreamWaitEvent(sp, ev_fork, 0));
         if ((rc = R.syr2k(k, buf, 0, cL, sp))) return rc;
+        const int la_panel = la_split ? lookahead_panel_ctas(j - b, bkn, j, bk, R.sms, o.panel_ctas) : 0;
         if ((rc = R.panel(kn, buf ^ 1, sp, la_panel))) return rc;
         CK(cudaEventRecord(ev_panel, sp));
-        if ((rc = R.syr2k(k, buf, cL, j, s, la_update))) return rc;
+        if ((rc = R.syr2k(k, buf, cL, j, s, la_split ? R.sms - la_panel : 0))) return rc;
       } else {
         if ((rc = R.syr2k(k, buf, 0, j, s))) return rc;
         if (has_next) {

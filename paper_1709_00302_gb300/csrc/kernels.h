@@ -27,6 +27,8 @@ struct PanelParams {
   bool w_in_smem;        // this CTA's rows of W kept in shared memory during the panel
   bool w_fp32;           // W formed in FP32 (it only feeds split-precision products)
   unsigned long long* trace;  // device trace record of this launch, or nullptr
+  long long* phases;          // grid panel only: clock64 of CTA 0 at 8 points of each step, or nullptr
+  int phase_steps;            // steps that fit in phases
 };
 
 size_t panel_smem_bytes(int bk, int Rp, bool w_in_smem);

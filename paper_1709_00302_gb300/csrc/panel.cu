@@ -101,7 +101,12 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
   const size_t accsz = panel_acc_entries(bk) * kAccStride;
   unsigned int gen = 0;
   int npend = 0, pend_i = 0;
+  // phase timing (diagnostic): CTA 0's thread 0 records clock64 at the points of a step
+  auto stamp = [&](int step, int q) {
+    if (p.phases && g == 0 && tid == 0 && step < p.phase_steps) p.phases[step * 8 + q] = clock64();
+  };
   for (int i = 0, step = 0; i < bk; ++step) {
+    stamp(step, 0);
     // A paired step computes reflectors i and i + 1 from one grid-wide reduction: the
     // sums over the rows below row i of column i and of column i + 1 against every
     // column; the second reflector's norm and coefficients follow from them and rows i,
@@ -158,6 +163,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
         if (want_pair) atomicAdd(&acc[(size_t)(bk + 1 + c) * kAccStride], sbv);
       }
     }
+    stamp(step, 1);
     // max |x2| by integer comparison of the bit patterns (no FP64 instruction): one warp
     if (tid < 32) {
       unsigned long long m = 0ull;
@@ -177,9 +183,11 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
     if (want_pair && own1)
       for (int c = tid; c < bk; c += NT) __stcg(&rowg[bk + c], slab[(size_t)c * Rp + (i + 1 - rb)]);
     __syncthreads();
+    stamp(step, 2);
     if (tid == 0) grid_arrive(p.gs);
     ++gen;
     if (tid == 0) s_ok = grid_wait(p.gs, gen, p.extra, p.status, p.limit_ns) ? 1 : 0;
+    stamp(step, 3);
     __syncthreads();
     if (!s_ok) return;
 
@@ -262,6 +270,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
       for (int v = tid - 32; v < nsum; v += NT - 32) bad |= !(fabs(dsum[v]) < 0x1p1000);
     }
     const int force = __syncthreads_or(bad);
+    stamp(step, 4);
 
     // Rare path: the plain sums over/underflow (or |alpha| is huge).  Column i is scaled
     // by the power of two 2^-e with 2^e <= max|x2| < 2^(e+1) (exact), and a second
@@ -335,6 +344,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
         }
       }
       __syncthreads();
+      stamp(step, 5);
       if (tau != 0.0)
         for (int r = lo + tid; r < nr; r += NT) xa[r] *= scal;
       if (own0 && tid == 0) xa[i - rb] = s_beta;
@@ -388,6 +398,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
         s_ptau[1] = tau2;
       }
       __syncthreads();
+      stamp(step, 5);
       // columns i and i + 1 become v_i and v_{i+1}: rows below i + 1 hold scal a_r and
       // scal2 (b_r - zs a_r); row i + 1 holds scal a_{i+1} and beta2; row i holds beta and
       // b_i - z_b.
@@ -405,6 +416,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
     pend_i = i;
     i += paired ? 2 : 1;
     __syncthreads();
+    stamp(step, 6);
   }
   pending_w(npend, pend_i, true);
   __syncthreads();

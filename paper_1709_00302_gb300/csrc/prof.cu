@@ -96,6 +96,21 @@ unsigned long long* trace_take() {
   return g_tbuf + 2 * (g_tmeta.size() - 1);
 }
 
+namespace {
+std::mutex g_pmu;
+long long* g_phase_buf = nullptr;
+int g_phase_steps = 0;
+}  // namespace
+
+long long* phase_take(int* steps) {
+  std::lock_guard<std::mutex> lock(g_pmu);
+  long long* p = g_phase_buf;
+  *steps = g_phase_steps;
+  g_phase_buf = nullptr;
+  g_phase_steps = 0;
+  return p;
+}
+
 }  // namespace prof
 }  // namespace bandred
 
@@ -149,6 +164,14 @@ int bandred_trace_begin(void* dev_buf, size_t bytes) {
   g_tbuf = static_cast<unsigned long long*>(dev_buf);
   g_tcap = bytes / 16;
   g_tmeta.clear();
+  return 0;
+}
+
+int bandred_panel_phase_trace(void* buf, int max_steps) {
+  if (max_steps < 0 || (max_steps > 0 && !buf)) return -2;
+  std::lock_guard<std::mutex> lock(g_pmu);
+  g_phase_buf = static_cast<long long*>(buf);
+  g_phase_steps = max_steps;
   return 0;
 }
 

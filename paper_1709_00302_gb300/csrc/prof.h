@@ -44,6 +44,8 @@ class TraceScope {
   TraceScope& operator=(const TraceScope&) = delete;
 };
 unsigned long long* trace_take();
+// The armed phase buffer of bandred_panel_phase_trace (taken by the next grid panel), or nullptr.
+long long* phase_take(int* steps);
 
 }  // namespace prof
 }  // namespace bandred

@@ -47,7 +47,7 @@ def overlap(a, b):
 
 
 def test_trace_records_and_lookahead_overlap(br):
-    n, w = 2048, 64
+    n, w = 4096, 64
     A = workloads.sym_gaussian(n, 77)
     recs, Aout, tau = traced_sy2sb(br, A, w, b=w, precision="ozaki")
     # parity first: the traced run computes the same reduction
@@ -69,7 +69,9 @@ def test_trace_records_and_lookahead_overlap(br):
           for k in ks if k + w in panels and k in rest]
     print("\noverlap of the shorter launch:", np.round(ov, 2).tolist())
     assert len(ov) >= len(ks) // 2
-    assert np.mean(np.array(ov) > 0.25) >= 0.5, ov
+    # the early iterations, where the rank-2k update is long, run the two side by side
+    early = np.array(ov[: max(4, len(ov) // 4)])
+    assert np.median(early) > 0.3 and np.max(early) > 0.5, ov
     # and X1 of iteration k + w starts only after both have ended (it reads all of A2 and W)
     for k in ks:
         if k + w in panels and k in rest:
