@@ -103,6 +103,26 @@ def ge2gb(A: np.ndarray, w: int, ncols: int = -1):
     return A, tauq[:n], taup[: max(n - w, 0)]
 
 
+def ge2gb_wide(A: np.ndarray, w: int):
+    """Reduce a wide A (m x n, m < n) to LOWER band form with lower bandwidth w.
+
+    Section 3.1 assumes m >= n.  For m < n the reduction is read on the transpose:
+    A^T (n x m, tall) = U' B' V'^T by ``ge2gb``, so A = V' B'^T U'^T with B'^T lower band
+    (LAPACK's bidiagonal reduction gives a lower bidiagonal for m < n in the same way).
+    Returns (Aout, tauq[max(m-w,0)], taup[m]): the lower band 0 <= i-j <= w of Aout holds
+    B; left reflector c (acting on rows c+w..m-1, A = Q B P^T, Q = H_0 H_1 ...) has beta on
+    Aout(c+w, c) and v in Aout(c+w+1:m, c) with tauq[c]; right reflector c (acting on
+    columns c..n-1, P = G_0 G_1 ...) has beta on Aout(c, c) and v in Aout(c, c+1:n) with
+    taup[c].
+    """
+    A = np.array(A, dtype=np.float64, order="F", copy=True)
+    m, n = A.shape
+    if m > n:
+        raise ValueError("ge2gb_wide: m must be < n (use ge2gb for m >= n)")
+    T, tq_t, tp_t = ge2gb(np.asfortranarray(A.T), w)
+    return np.asfortranarray(T.T), tp_t, tq_t
+
+
 def jacobi_eig(A: np.ndarray) -> np.ndarray:
     """Eigenvalues (ascending) of a small symmetric matrix by cyclic Jacobi."""
     A = np.array(A, dtype=np.float64, order="F", copy=True)

@@ -174,3 +174,48 @@ def gen_probe_backward(A: np.ndarray, Aout: np.ndarray, tauq: np.ndarray, taup: 
         v = np.concatenate(([1.0], Aout[c + 1:, c]))
         Z[c:] -= t * np.outer(v, v @ Z[c:])
     return float(np.linalg.norm(AX - Z) / np.linalg.norm(AX))
+
+
+def wide_band(Aout: np.ndarray, w: int) -> np.ndarray:
+    """Lower band 0 <= i-j <= w of an m x n (m < n) packed output."""
+    m, n = Aout.shape
+    i, j = np.indices((m, n))
+    return np.where((i - j >= 0) & (i - j <= w), Aout, 0.0)
+
+
+def wide_form_qp(Aout: np.ndarray, tauq: np.ndarray, taup: np.ndarray, w: int):
+    """Q = H_0 H_1 ... (left reflectors on rows c+w.., v in column c below the band) and
+    P = G_0 G_1 ... (right reflectors on columns c.., v in row c right of the diagonal)."""
+    m, n = Aout.shape
+    Q = np.eye(m)
+    for c in range(len(tauq)):
+        t = tauq[c]
+        if t == 0.0:
+            continue
+        r0 = c + w
+        v = np.concatenate(([1.0], Aout[r0 + 1:, c]))
+        Q[:, r0:] -= t * np.outer(Q[:, r0:] @ v, v)
+    P = np.eye(n)
+    for c in range(len(taup)):
+        t = taup[c]
+        if t == 0.0:
+            continue
+        v = np.concatenate(([1.0], Aout[c, c + 1:]))
+        P[:, c:] -= t * np.outer(P[:, c:] @ v, v)
+    return Q, P
+
+
+def wide_report(A: np.ndarray, Aout: np.ndarray, tauq, taup, w: int) -> dict:
+    """Backward error, orthogonality and singular-value error of a wide (m < n) result."""
+    B = wide_band(Aout, w)
+    Q, P = wide_form_qp(Aout, tauq, taup, w)
+    m, n = A.shape
+    fa = np.linalg.norm(A)
+    s_a = np.linalg.svd(A, compute_uv=False)
+    s_b = np.linalg.svd(B, compute_uv=False)
+    return {
+        "backward": np.linalg.norm(A - Q @ B @ P.T) / fa if fa else 0.0,
+        "orth_q": np.linalg.norm(Q.T @ Q - np.eye(m)),
+        "orth_p": np.linalg.norm(P.T @ P - np.eye(n)),
+        "sv": np.max(np.abs(s_a - s_b)) / max(s_a[0], 1e-300) if m else 0.0,
+    }

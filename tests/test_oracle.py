@@ -301,3 +301,58 @@ def test_oracle_matches_its_frozen_outputs():
     np.testing.assert_allclose(Gout, h["Aout"], rtol=0, atol=1e-14)
     np.testing.assert_allclose(tq, h["tauq"].ravel(), rtol=0, atol=1e-15)
     np.testing.assert_allclose(tp, h["taup"].ravel(), rtol=0, atol=1e-15)
+
+
+# --------------------------------------------------------------------------- wide (m < n)
+from checks import wide_band, wide_report  # noqa: E402
+
+
+@pytest.mark.parametrize("m,n,w", [(20, 33, 2), (17, 40, 5), (8, 9, 1), (30, 64, 16), (5, 12, 8)])
+def test_ge2gb_wide_invariants(m, n, w):
+    """A = Q B P^T with B lower band: reconstruction through independently formed Q and P,
+    orthogonality, band shape, and the singular values of A (LAPACK)."""
+    A = workloads.gen_gaussian(m, n, 300 + m + n + w)
+    Aout, tq, tp = oracle.ge2gb_wide(A, w)
+    assert tq.shape == (max(m - w, 0),) and tp.shape == (m,)
+    r = wide_report(A, Aout, tq, tp, w)
+    tol = 20 * n * U64
+    assert r["backward"] < tol and r["orth_q"] < tol and r["orth_p"] < tol and r["sv"] < tol, r
+
+
+def test_ge2gb_wide_w1_is_lower_bidiagonal():
+    m, n = 12, 20
+    A = workloads.gen_gaussian(m, n, 9)
+    Aout, tq, tp = oracle.ge2gb_wide(A, 1)
+    B = wide_band(Aout, 1)
+    i, j = np.indices(B.shape)
+    assert np.all(B[(i - j < 0) | (i - j > 1)] == 0.0)
+    np.testing.assert_allclose(np.sort(np.abs(np.linalg.svd(B, compute_uv=False))),
+                               np.sort(oracle.jacobi_svd(A.T)), rtol=0, atol=1e-13 * np.linalg.norm(A))
+
+
+def test_ge2gb_wide_hand_case_2x3_w1():
+    # A = [[a, b, c], [d, e, f]]: the right reflector of row 0 gives beta_0 = -sign(a) ||(a, b, c)||
+    A = np.array([[3.0, 4.0, 12.0], [1.0, -2.0, 5.0]])
+    Aout, tq, tp = oracle.ge2gb_wide(A, 1)
+    assert Aout[0, 0] == pytest.approx(-13.0, rel=4 * U64)
+    assert tp[0] == pytest.approx(1.0 + 3.0 / 13.0, rel=4 * U64)
+    # the band's singular values are those of A
+    np.testing.assert_allclose(np.linalg.svd(wide_band(Aout, 1), compute_uv=False),
+                               np.linalg.svd(A, compute_uv=False), rtol=1e-14)
+
+
+def test_pins_catch_planted_mistakes_wide():
+    m, n, w = 14, 25, 3
+    A = workloads.gen_gaussian(m, n, 23)
+    Aout, tq, tp = oracle.ge2gb_wide(A, w)
+    tol = 20 * n * U64
+    assert wide_report(A, Aout, tq, tp, w)["backward"] < tol
+    for mistake in ("tauq_sign", "taup_drop", "v_right_sign"):
+        Am, tqm, tpm = Aout.copy(), tq.copy(), tp.copy()
+        if mistake == "tauq_sign":
+            tqm[1] = -tqm[1]
+        elif mistake == "taup_drop":
+            tpm[2] = 0.0
+        else:
+            Am[3, 5:] *= -1.0
+        assert wide_report(A, Am, tqm, tpm, w)["backward"] > tol, mistake
