@@ -172,7 +172,8 @@ int bandred_sy2sb_noalloc(int64_t n, int64_t w, double* A, int64_t lda, double* 
                           const bandred_opts* opts, int* dev_status, cudaStream_t stream);
 
 /* ---------------------------------------------------------------- ge2gb -------------
- * Reduction to upper triangular band form, Section 3.1: A = U B V^T, m >= n.
+ * Reduction to upper triangular band form, Section 3.1: A = U B V^T, m >= n.  (m < n: see
+ * the end of this comment.)
  *   A     device, m x n, lda >= max(1, m).  On exit the band 0 <= j - i <= w holds B;
  *         left reflector c (c = 0 .. n-1): beta on A(c, c), v below the diagonal in
  *         A(c+1 : m, c); right reflector c (c = 0 .. n-w-1): beta on A(c, c+w), v in row c,
@@ -182,7 +183,12 @@ int bandred_sy2sb_noalloc(int64_t n, int64_t w, double* A, int64_t lda, double* 
  *         rows c .. m-1).
  *   taup  device, max(n - w, 0) entries (right reflectors; V = Hp_0 Hp_1 ..., Hp_c acting
  *         on columns c+w .. n-1).
- * Returns -2 when n > m (the transposed problem is not handled).
+ * m < n (Section 3.1 assumes m >= n; the reduction is applied to the tall A^T and
+ * written back transposed): A = Q B P^T with B LOWER band, 0 <= i - j <= w.  tauq holds
+ * max(m - w, 0) left reflectors: reflector c acts on rows c+w .. m-1, beta on A(c+w, c),
+ * v in A(c+w+1 : m, c); Q = Hq_0 Hq_1 ....  taup holds m right reflectors: reflector c
+ * acts on columns c .. n-1, beta on A(c, c), v in A(c, c+1 : n); P = Hp_0 Hp_1 ....
+ * The workspace then also holds a copy of A^T.
  */
 size_t bandred_ge2gb_workspace(int64_t m, int64_t n, int64_t w, const bandred_opts* opts);
 

@@ -457,14 +457,16 @@ def sy2sb(A, w: int, opts: bandred_opts | None = None, stream=None, check: bool 
 
 
 def ge2gb(A, w: int, opts: bandred_opts | None = None, stream=None, check: bool = True):
-    """In-place reduction of the column-major CUDA tensor A (m x n, m >= n) to upper
-    triangular band form.  Returns (A, tauq, taup, dev_status)."""
+    """In-place reduction of the column-major CUDA tensor A (m x n) to band form: upper
+    triangular band for m >= n, lower band for m < n (see include/bandred.h).  Returns
+    (A, tauq, taup, dev_status)."""
     import torch
 
     m, n = A.shape
     opts = make_opts() if opts is None else opts
-    tauq = torch.zeros(n, dtype=torch.float64, device=A.device)
-    taup = torch.zeros(max(n - w, 0), dtype=torch.float64, device=A.device)
+    nq, np_ = (n, max(n - w, 0)) if m >= n else (max(m - w, 0), m)
+    tauq = torch.zeros(nq, dtype=torch.float64, device=A.device)
+    taup = torch.zeros(np_, dtype=torch.float64, device=A.device)
     work = torch.empty(max(bandred_ge2gb_workspace(m, n, w, opts), 256), dtype=torch.uint8, device=A.device)
     status = torch.zeros(1, dtype=torch.int32, device=A.device)
     rc = bandred_ge2gb_ex(A, w, tauq, taup, opts, work, status, stream)

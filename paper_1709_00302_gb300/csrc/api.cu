@@ -1,6 +1,7 @@
 // The extern "C" entry points declared in include/bandred.h: argument validation
 // (LAPACK-style negative codes), workspace checks, device selection, and the allocating
 // short forms.  The computation itself is in driver.cu and the kernels.
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 
@@ -15,13 +16,16 @@ bool aligned(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 255u) == 
 int ge2gb_check(int64_t m, int64_t n, int64_t w, const double* A, int64_t lda, const double* tauq,
                 const double* taup, const bandred_opts* opts, Options* o) {
   if (m < 0) return -1;
-  if (n < 0 || n > m) return -2;
+  if (n < 0) return -2;
   if (w < 1) return -3;
   if (n > 0 && !A) return -4;
   if (lda < (m > 1 ? m : 1)) return -5;
-  if (n > 0 && !tauq) return -6;
-  if (n - w > 0 && !taup) return -7;
-  if (m > INT32_MAX / 2) return BANDRED_ERR_UNSUPPORTED;
+  // m >= n: n left and max(n - w, 0) right reflectors; m < n (lower band of the
+  // transpose): max(m - w, 0) left and m right ones
+  const int64_t nq = m >= n ? n : std::max<int64_t>(m - w, 0), np = m >= n ? std::max<int64_t>(n - w, 0) : m;
+  if (nq > 0 && !tauq) return -6;
+  if (np > 0 && !taup) return -7;
+  if (std::max(m, n) > INT32_MAX / 2) return BANDRED_ERR_UNSUPPORTED;
   if (bandred::resolve_options(opts, w, o) != 0) return -8;
   return 0;
 }
@@ -117,7 +121,7 @@ int bandred_sy2sb(int64_t n, int64_t w, double* A, int64_t lda, double* tau, con
 
 size_t bandred_ge2gb_workspace(int64_t m, int64_t n, int64_t w, const bandred_opts* opts) {
   Options o;
-  if (m < 0 || n < 0 || n > m || w < 1 || bandred::resolve_options(opts, w, &o) != 0) return 0;
+  if (m < 0 || n < 0 || w < 1 || bandred::resolve_options(opts, w, &o) != 0) return 0;
   return bandred::ge2gb_workspace_bytes(m, n, w, o);
 }
 

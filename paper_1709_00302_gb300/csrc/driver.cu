@@ -1121,6 +1121,18 @@ struct Ge2gb {
 // which needs w >= 3b, is not used.)  With w < 2b the steps run in order.
 int ge2gb_run(int64_t m, int64_t n, int64_t w, double* A, int64_t lda, double* tauq, double* taup,
               const Options& o, void* work, int* dev_status, cudaStream_t s) {
+  if (n > m) {
+    // m < n: Section 3.1's reduction of the tall A^T (n x m) = U' B' V'^T, written back
+    // transposed: A = V' B'^T U'^T with B'^T lower band.  A^T lives at the front of the
+    // workspace; the left reflectors of A^T are A's right ones (taup, m of them), its
+    // right reflectors A's left ones (tauq, max(m - w, 0)).
+    double* T = static_cast<double*>(work);
+    void* rest = static_cast<char*>(work) + align_up((size_t)m * n * sizeof(double));
+    CK(transpose_f64((int)m, (int)n, A, lda, T, n, s));
+    if (int rc = ge2gb_run(n, m, w, T, n, taup, tauq, o, rest, dev_status, s)) return rc;
+    CK(transpose_f64((int)n, (int)m, T, n, A, lda, s));
+    return 0;
+  }
   Ge2gb R{};
   R.m = m;
   R.n = n;
@@ -1189,6 +1201,7 @@ int ge2gb_run(int64_t m, int64_t n, int64_t w, double* A, int64_t lda, double* t
 }
 
 size_t ge2gb_workspace_bytes(int64_t m, int64_t n, int64_t w, const Options& o) {
+  if (n > m) return align_up((size_t)m * n * sizeof(double)) + ge2gb_workspace_bytes(n, m, w, o);
   return carve_ge2gb(nullptr, m, n, o, current_sms()).bytes;
 }
 

@@ -299,4 +299,32 @@ cudaError_t syr2k_lower_f64(int n, int nb, double* S, int64_t lds, const double*
   return cudaGetLastError();
 }
 
+namespace {
+
+// D (cols x rows) = S^T for S (rows x cols): 32 x 32 tiles through shared memory (one
+// padding column against bank conflicts), reads and writes coalesced along columns.
+__global__ void transpose_kernel(int rows, int cols, const double* S, int64_t lds, double* D, int64_t ldd) {
+  __shared__ double tile[32][33];
+  const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+  for (int q = threadIdx.y; q < 32; q += blockDim.y) {
+    const int r = r0 + threadIdx.x, c = c0 + q;
+    if (r < rows && c < cols) tile[q][threadIdx.x] = S[r + (int64_t)c * lds];
+  }
+  __syncthreads();
+  for (int q = threadIdx.y; q < 32; q += blockDim.y) {
+    const int c = c0 + threadIdx.x, r = r0 + q;
+    if (r < rows && c < cols) D[c + (int64_t)r * ldd] = tile[threadIdx.x][q];
+  }
+}
+
+}  // namespace
+
+cudaError_t transpose_f64(int rows, int cols, const double* S, int64_t lds, double* D, int64_t ldd, cudaStream_t s) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  const dim3 grid((rows + 31) / 32, (cols + 31) / 32);
+  prof::count_launch();
+  transpose_kernel<<<grid, dim3(32, 8), 0, s>>>(rows, cols, S, lds, D, ldd);
+  return cudaGetLastError();
+}
+
 }  // namespace bandred

@@ -73,4 +73,7 @@ cudaError_t symm_lower_f64(int n, int nb, const double* S, int64_t lds, const do
 cudaError_t syr2k_lower_f64(int n, int nb, double* S, int64_t lds, const double* X, int64_t ldx, const double* Y,
                             int64_t ldy, int col0, int col1, cudaStream_t s);
 
+// D (cols x rows, column-major, ldd) = S^T for S (rows x cols, column-major, lds).
+cudaError_t transpose_f64(int rows, int cols, const double* S, int64_t lds, double* D, int64_t ldd, cudaStream_t s);
+
 }  // namespace bandred

@@ -68,8 +68,8 @@ def test_invalid_arguments_are_rejected_before_any_device_work(L):
     bad.reserved[3] = 0
     bad.depth = 3  # look-ahead depth beyond 2
     assert L.bandred_sy2sb_ex(10, 4, fake, 10, fake, ctypes.byref(bad), null, 0, null, null) == -6
-    # ge2gb: n > m, w < 1, lda < m
-    assert L.bandred_ge2gb_ex(4, 5, 1, fake, 4, fake, fake, None, null, 0, null, null) == -2
+    # ge2gb: n < 0, w < 1, lda < m (n > m is the wide case: allowed)
+    assert L.bandred_ge2gb_ex(4, -5, 1, fake, 4, fake, fake, None, null, 0, null, null) == -2
     assert L.bandred_ge2gb_ex(6, 5, 0, fake, 6, fake, fake, None, null, 0, null, null) == -3
     assert L.bandred_ge2gb_ex(6, 5, 1, fake, 5, fake, fake, None, null, 0, null, null) == -5
     assert L.bandred_ge2gb_ex(6, 5, 1, fake, 6, null, fake, None, null, 0, null, null) == -6
