@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
 
   // W columns of the previous step's reflectors (their T entries are in gq0 / gq1).
   // all = false: warps 1..7 only (named barrier 1 between the columns), while thread 0
-  // derives the next reflectors.
+  // waits at the grid barrier.
   auto pending_w = [&](int npend, int pi, bool all) {
     const int t0 = all ? 0 : 32, nth = all ? NT : NT - 32;
     for (int q = 0; q < npend; ++q) {
@@ -186,7 +186,13 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
     stamp(step, 2);
     if (tid == 0) grid_arrive(p.gs);
     ++gen;
-    if (tid == 0) s_ok = grid_wait(p.gs, gen, p.extra, p.status, p.limit_ns) ? 1 : 0;
+    // While thread 0 waits for the barrier, warps 1..7 form the W columns of the previous
+    // step: the FP64 pipe is otherwise idle here, and kept off the scalar chain after it.
+    if (tid == 0)
+      s_ok = grid_wait(p.gs, gen, p.extra, p.status, p.limit_ns) ? 1 : 0;
+    else if (tid >= 32)
+      pending_w(npend, pend_i, false);
+    npend = 0;
     stamp(step, 3);
     __syncthreads();
     if (!s_ok) return;
@@ -259,8 +265,6 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
       for (int c = tid - 32; c < bk; c += NT - 32) rowi[c] = ldcg(&rowg[c]);
       if (want_pair)
         for (int c = tid - 32; c < bk; c += NT - 32) rowi1[c] = ldcg(&rowg[bk + c]);
-      // W columns of the previous step, hidden behind thread 0's scalar chain
-      pending_w(npend, pend_i, false);
     }
     // A sum outside the range where the plain formulas hold (not finite, or near the
     // overflow threshold, as when some entries exceed 2^500) forces the scaled path too.
