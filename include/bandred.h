@@ -199,6 +199,30 @@ int bandred_ge2gb_ex(int64_t m, int64_t n, int64_t w, double* A, int64_t lda, do
                      double* taup, const bandred_opts* opts, void* work, size_t work_bytes,
                      int* dev_status, cudaStream_t stream);
 
+/* ---------------------------------------------------------------- forming Q, U, V ---
+ * The orthogonal factors of a finished reduction, formed on the GPU from the packed
+ * reflectors (the step that eigenvector and singular-vector solvers take after the band
+ * reduction; the paper's introduction).  The reflectors are applied in groups of b
+ * (opts->b, 0 = 64, at most 64) in compact-WY form (Section 4.1), last group first; the
+ * products run in FP64 for BANDRED_FP64 and as Ozaki-scheme products (FP64-accurate, on the
+ * tensor cores) for any other precision.  Q is N x N, column-major, ldq >= max(1, N),
+ * device memory owned by the caller and overwritten; A and tau are the outputs of the
+ * reduction and are not changed.  work: device, 256-byte aligned, at least
+ * bandred_form_workspace(N, opts) bytes.  Stream-ordered; no allocation.  Returns 0, -i
+ * for an invalid i-th argument, or a BANDRED_ERR_* code; dev_status as for the reductions.
+ *   bandred_sy2sb_form_q: Q of A = Q B Q^T (N = n).
+ *   bandred_ge2gb_form:   side 0: U of A = U B V^T (N = m; for m < n the Q of A = Q B P^T);
+ *                         side 1: V (N = n; for m < n the P).  tau: tauq for side 0, taup
+ *                         for side 1, as the reduction wrote them.
+ */
+size_t bandred_form_workspace(int64_t N, const bandred_opts* opts);
+int bandred_sy2sb_form_q(int64_t n, int64_t w, const double* A, int64_t lda, const double* tau, double* Q,
+                         int64_t ldq, const bandred_opts* opts, void* work, size_t work_bytes, int* dev_status,
+                         cudaStream_t stream);
+int bandred_ge2gb_form(int64_t m, int64_t n, int64_t w, const double* A, int64_t lda, const double* tau, int side,
+                       double* Q, int64_t ldq, const bandred_opts* opts, void* work, size_t work_bytes,
+                       int* dev_status, cudaStream_t stream);
+
 /* ---------------------------------------------------------------- batched -----------
  * Many independent matrices of uneven sizes (Sections 2.1 and 3.1 applied to each).
  * The matrices advance in lockstep: iteration t of every matrix still active runs in the

@@ -143,6 +143,12 @@ def lib():
         L.bandred_trace_end.restype = ci
         L.bandred_panel_phase_trace.argtypes = [vp, ci]
         L.bandred_panel_phase_trace.restype = ci
+        L.bandred_form_workspace.argtypes = [i64, op]
+        L.bandred_form_workspace.restype = sz
+        L.bandred_sy2sb_form_q.argtypes = [i64, i64, vp, i64, vp, vp, i64, op, vp, sz, vp, vp]
+        L.bandred_sy2sb_form_q.restype = ci
+        L.bandred_ge2gb_form.argtypes = [i64, i64, i64, vp, i64, vp, ci, vp, i64, op, vp, sz, vp, vp]
+        L.bandred_ge2gb_form.restype = ci
         L.bandred_newton_eval.argtypes = [i64, vp, vp, vp, vp]
         L.bandred_newton_eval.restype = ci
         L.bandred_fp64_probe.argtypes = [ci, ci, ci, vp, vp]
@@ -415,6 +421,41 @@ def bandred_trace_end(max_records: int = 65536) -> list:
         raise BandredError(n, "bandred_trace_end")
     return [{"kind": TRACE_KINDS.get(arr[i].kind, str(arr[i].kind)), "iteration": arr[i].iteration,
              "t0_ns": arr[i].t0_ns, "t1_ns": arr[i].t1_ns} for i in range(n)]
+
+
+def _form_buffers(N: int, opts, device):
+    import torch
+
+    Q = torch.empty((N, N), dtype=torch.float64, device=device).t()  # column-major
+    work = torch.empty(max(lib().bandred_form_workspace(N, ctypes.byref(opts)), 256), dtype=torch.uint8,
+                       device=device)
+    status = torch.zeros(1, dtype=torch.int32, device=device)
+    return Q, work, status
+
+
+def sy2sb_form_q(A, w: int, tau, opts: bandred_opts | None = None, stream=None):
+    """Q (n x n, column-major CUDA tensor) of the finished sy2sb reduction held in A, tau."""
+    n = A.shape[0]
+    opts = make_opts() if opts is None else opts
+    Q, work, status = _form_buffers(n, opts, A.device)
+    rc = lib().bandred_sy2sb_form_q(n, w, _ptr(A), _lda(A), _ptr(tau), _ptr(Q), Q.stride(1), ctypes.byref(opts),
+                                    _ptr(work), work.numel(), _ptr(status), _stream(stream))
+    if rc != 0:
+        raise BandredError(rc, "bandred_sy2sb_form_q")
+    return Q, status
+
+
+def ge2gb_form(A, w: int, tau, side: int, opts: bandred_opts | None = None, stream=None):
+    """side 0: U (m x m; Q when m < n), side 1: V (n x n; P when m < n) of a finished ge2gb."""
+    m, n = A.shape
+    N = m if side == 0 else n
+    opts = make_opts() if opts is None else opts
+    Q, work, status = _form_buffers(N, opts, A.device)
+    rc = lib().bandred_ge2gb_form(m, n, w, _ptr(A), _lda(A), _ptr(tau), side, _ptr(Q), Q.stride(1),
+                                  ctypes.byref(opts), _ptr(work), work.numel(), _ptr(status), _stream(stream))
+    if rc != 0:
+        raise BandredError(rc, "bandred_ge2gb_form")
+    return Q, status
 
 
 def bandred_panel_phase_trace(buf) -> int:

@@ -162,4 +162,57 @@ int bandred_ge2gb(int64_t m, int64_t n, int64_t w, double* A, int64_t lda, doubl
   return rc ? rc : status;
 }
 
+size_t bandred_form_workspace(int64_t N, const bandred_opts* opts) {
+  Options o;
+  if (N < 0 || bandred::resolve_options(opts, 1 << 20, &o) != 0) return 0;
+  return bandred::form_workspace_bytes(N, o);
+}
+
+namespace {
+
+// Shared checks and launch of the three forming entry points.
+int form_call(int64_t N, int64_t nref, int64_t shift, const double* A, int64_t lda, int64_t need_lda, int64_t es,
+              int64_t cs, const double* tau, double* Q, int64_t ldq, const bandred_opts* opts, void* work,
+              size_t work_bytes, int* dev_status, cudaStream_t stream) {
+  Options o;
+  if (N > INT32_MAX / 2) return BANDRED_ERR_UNSUPPORTED;
+  if (N > 0 && !A) return -3;
+  if (lda < std::max<int64_t>(1, need_lda)) return -4;
+  if (nref > 0 && !tau) return -5;
+  if (N > 0 && !Q) return -6;
+  if (ldq < std::max<int64_t>(1, N)) return -7;
+  if (bandred::resolve_options(opts, 1 << 20, &o) != 0) return -8;
+  if (!work || !aligned(work)) return -9;
+  if (work_bytes < bandred::form_workspace_bytes(N, o)) return -10;
+  bandred::DeviceGuard dg;
+  if (N > 0 && !dg.select(Q)) return -6;
+  return bandred::form_run(N, nref, shift, A, es, cs, tau, Q, ldq, o, work, dev_status, stream);
+}
+
+}  // namespace
+
+int bandred_sy2sb_form_q(int64_t n, int64_t w, const double* A, int64_t lda, const double* tau, double* Q,
+                         int64_t ldq, const bandred_opts* opts, void* work, size_t work_bytes, int* dev_status,
+                         cudaStream_t stream) {
+  if (n < 0) return -1;
+  if (w < 1) return -2;
+  return form_call(n, std::max<int64_t>(n - w, 0), w, A, lda, n, 1, lda, tau, Q, ldq, opts, work, work_bytes,
+                   dev_status, stream);
+}
+
+int bandred_ge2gb_form(int64_t m, int64_t n, int64_t w, const double* A, int64_t lda, const double* tau, int side,
+                       double* Q, int64_t ldq, const bandred_opts* opts, void* work, size_t work_bytes,
+                       int* dev_status, cudaStream_t stream) {
+  if (m < 0) return -1;
+  if (n < 0 || w < 1) return -2;
+  if (side != 0 && side != 1) return -5;
+  const bool tall = m >= n;
+  if (side == 0)  // U (m >= n: n reflectors on rows c..) or Q (m < n: m - w reflectors on rows c+w..)
+    return form_call(m, tall ? n : std::max<int64_t>(m - w, 0), tall ? 0 : w, A, lda, m, 1, lda, tau, Q, ldq, opts,
+                     work, work_bytes, dev_status, stream);
+  // V (m >= n: n - w reflectors on columns c+w..) or P (m < n: m reflectors on columns c..)
+  return form_call(n, tall ? std::max<int64_t>(n - w, 0) : m, tall ? w : 0, A, lda, m, lda, 1, tau, Q, ldq, opts,
+                   work, work_bytes, dev_status, stream);
+}
+
 }  // extern "C"

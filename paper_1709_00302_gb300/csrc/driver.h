@@ -73,6 +73,13 @@ size_t ge2gb_workspace_bytes(int64_t m, int64_t n, int64_t w, const Options& o);
 int ge2gb_run(int64_t m, int64_t n, int64_t w, double* A, int64_t lda, double* tauq, double* taup,
               const Options& o, void* work, int* dev_status, cudaStream_t s);
 
+// Orthogonal factor of N x N from packed reflectors (form.cu): Q = H_0 .. H_{nref-1},
+// H_c acting on indices c + shift .. N-1, v_c's stored entries at P[(c + shift + 1 + t) es
+// + c cs].  FP64 products for BANDRED_FP64, Ozaki-scheme products otherwise.
+size_t form_workspace_bytes(int64_t N, const Options& o);
+int form_run(int64_t N, int64_t nref, int64_t shift, const double* P, int64_t es, int64_t cs, const double* tau,
+             double* Q, int64_t ldq, const Options& o, void* work, int* dev_status, cudaStream_t s);
+
 // Batched reductions (batched.cu).  mode 1 = plan (upload the schedule's tables), 2 = run.
 int sy2sb_batched(int count, const int64_t* n, const int64_t* w, double* const* A, const int64_t* lda,
                   double* const* tau, const Options& o, void* work, size_t work_bytes, int* dev_status,
