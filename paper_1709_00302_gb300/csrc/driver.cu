@@ -136,7 +136,7 @@ int resolve_options(const bandred_opts* in, int64_t w, Options* o) {
 struct Sy2sbWs {
   double *Y[3], *W[3], *X, *X2;
   double *Z[2], *splitk[2];  // FP64 small products; [1] belongs to the panel stream
-  double *part, *rowbuf;
+  double *part, *rowbuf, *gram;
   GridSync* gs;
   // split-precision buffers
   __nv_bfloat16 *wblob, *x2blob, *ablob, *bblob;
@@ -192,6 +192,7 @@ static Sy2sbWs carve_sy2sb(void* work, int64_t n, int64_t w, const Options& o, i
     ws.splitk[q] = q < nbuf ? c.take<double>(ws.splitk_cap) : ws.splitk[0];
   }
   ws.rowbuf = c.take<double>(8 * (size_t)b);  // up to four rows per step, two steps
+  ws.gram = c.take<double>((size_t)b * b);    // Gram coefficients of the panel (W formed after it)
   ws.gs = c.take<GridSync>(1);  // 256 bytes, immediately followed by the accumulators
   ws.part = c.take<double>((panel_sync_bytes((int)b) - 256) / sizeof(double));
   if (is_split(o)) {
@@ -225,7 +226,7 @@ struct SplitBufs {
 };
 
 struct Ge2gbWs {
-  double *Yu[2], *Wu[2], *Yv, *Wv, *Z[2], *ZT, *P, *splitk[2], *part, *rowbuf;
+  double *Yu[2], *Wu[2], *Yv, *Wv, *Z[2], *ZT, *P, *splitk[2], *part, *rowbuf, *gram;
   GridSync* gs;
   SplitBufs sb[2];  // [0] caller's stream, [1] panel stream (look-ahead)
   char *ozp[2], *ozr[2];  // Ozaki-scheme buffers per stream (see Sy2sbWs)
@@ -256,6 +257,7 @@ static Ge2gbWs carve_ge2gb(void* work, int64_t m, int64_t n, const Options& o, i
     ws.splitk[q] = q < nbuf ? c.take<double>(ws.splitk_cap) : ws.splitk[0];
   }
   ws.rowbuf = c.take<double>(8 * (size_t)b);  // up to four rows per step, two steps
+  ws.gram = c.take<double>((size_t)b * b);    // Gram coefficients of the panel (W formed after it)
   ws.gs = c.take<GridSync>(1);  // 256 bytes, immediately followed by the accumulators
   ws.part = c.take<double>((panel_sync_bytes((int)b) - 256) / sizeof(double));
   if (is_split(o)) {
@@ -307,7 +309,7 @@ static int current_sms() {
 // One panel factorisation: QR of the j x bk panel at `A` (rs = 1, cs = lda) or LQ of the
 // bk x j row panel (rs = lda, cs = 1).
 static int run_panel(double* A, int64_t rs, int64_t cs, int j, int bk, double* tau, double* Y, double* W,
-                     int64_t ldy, double* acc, double* rowbuf, GridSync* gs, int* status,
+                     int64_t ldy, double* acc, double* rowbuf, double* gram, GridSync* gs, int* status,
                      const Options& o, int max_ctas, unsigned int extra, cudaStream_t s) {
   PanelParams p{};
   p.trace = prof::trace_take();
@@ -367,6 +369,16 @@ static int run_panel(double* A, int64_t rs, int64_t cs, int j, int bk, double* t
   if (o.panel_group == 4 && panel4_smem_bytes(bk, Rp, false) <= kSmemMax) {
     p.w_in_smem = panel4_smem_bytes(bk, Rp, true) <= kSmemMax;
     CK(launch_panel4(p, G, s));
+    return 0;
+  }
+  // FP64 W (every precision but the split ones, whose W is FP32 and cheap in the panel): the
+  // panel stores its Gram coefficients and a row-parallel kernel forms W after it, keeping
+  // that FP64 work off the panel's per-reflector critical path.
+  if (!is_split(o) && bk <= 128) {
+    p.G = gram;
+    p.w_in_smem = false;
+    CK(launch_panel(p, G, s));
+    CK(launch_w_from_gram(j, bk, Y, tau, gram, W, ldy, s));
     return 0;
   }
   CK(launch_panel(p, G, s));
@@ -472,7 +484,7 @@ struct Sy2sb {
     prof::Scope sc(prof::kPanel, s, panel_flops(j, bk), panel_bytes(j, bk));
     prof::TraceScope tr(prof::kTracePanel, k);
     int rc = run_panel(A + r0 + k * lda, 1, lda, j, bk, tau + k, ws.Y[buf], ws.W[buf], ws.ld, ws.part, ws.rowbuf,
-                       ws.gs, status, o, ctas > 0 ? std::min(ctas, pmax) : pmax, extra, s);
+                       ws.gram, ws.gs, status, o, ctas > 0 ? std::min(ctas, pmax) : pmax, extra, s);
     extra = 0;
     return rc;
   }
@@ -1003,7 +1015,7 @@ struct Ge2gb {
     prof::Scope sc(prof::kPanel, s, panel_flops(j, bk), panel_bytes(j, bk));
     prof::TraceScope tr(prof::kTracePanel, k);
     int rc = run_panel(A + k + k * lda, 1, lda, j, bk, tauq + k, ws.Yu[buf], ws.Wu[buf], ws.ldu, ws.part,
-                       ws.rowbuf, ws.gs, status, o, pmax, extra, s);
+                       ws.rowbuf, ws.gram, ws.gs, status, o, pmax, extra, s);
     extra = 0;
     return rc;
   }
@@ -1059,7 +1071,7 @@ struct Ge2gb {
     prof::Scope sc(prof::kPanel, s, panel_flops(jr, (int)bkr), panel_bytes(jr, (int)bkr));
     prof::TraceScope tr(prof::kTracePanelRow, k);
     return run_panel(A + k + (k + w) * lda, lda, 1, jr, (int)bkr, taup + k, ws.Yv, ws.Wv, ws.ldv, ws.part, ws.rowbuf,
-                     ws.gs, status, o, pmax, 0u, s);
+                     ws.gram, ws.gs, status, o, pmax, 0u, s);
   }
 
   // D = A(k+bkr:m, k+w:n) += (D W_V) Y_V^T (Eq. updateD).

@@ -29,7 +29,15 @@ struct PanelParams {
   unsigned long long* trace;  // device trace record of this launch, or nullptr
   long long* phases;          // grid panel only: clock64 of CTA 0 at 8 points of each step, or nullptr
   int phase_steps;            // steps that fit in phases
+  double* G;                  // grid panel, FP64 W: the strict upper triangle of Y^T Y (bk x bk, ld bk)
+                              // written instead of W, which w_from_gram then forms (nullptr: W in the panel)
 };
+
+// W = -Y T for a factored panel from its Gram coefficients: row r of W solves the forward
+// substitution w_r[q] = -tau_q (Y(r, q) + sum_{p<q} w_r[p] G(p, q)) (T^{-1} = strict upper of
+// Y^T Y + diag(1 / tau)).  j rows, bk columns, Y and W with leading dimension ldy.
+cudaError_t launch_w_from_gram(int j, int bk, const double* Y, const double* tau, const double* G, double* W,
+                               int64_t ldy, cudaStream_t s);
 
 size_t panel_smem_bytes(int bk, int Rp, bool w_in_smem);
 size_t panel_sync_bytes(int bk);  // bytes from gs to the end of acc

@@ -25,6 +25,7 @@
 //   which equals -Y T with T built column by column as in the compact-WY definition.
 #include <cmath>
 
+#include "launch.h"
 #include "panel_common.cuh"
 #include "prof.h"
 
@@ -54,6 +55,8 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
   // This CTA's rows of W: in shared memory when they fit (FP32 when p.w_fp32), else in
   // the W output itself.
   const bool wf32 = p.w_in_smem && p.w_fp32;
+  // gram: no W in the panel; CTA 0 stores the T coefficients (y_c^T y_i) into p.G instead
+  const bool gram = p.G != nullptr;
   double* wl = p.w_in_smem ? after : p.W + rb;
   float* wlf = reinterpret_cast<float*>(after);
   const int64_t wld = p.w_in_smem ? Rp : p.ldy;
@@ -190,7 +193,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
     // step: the FP64 pipe is otherwise idle here, and kept off the scalar chain after it.
     if (tid == 0)
       s_ok = grid_wait(p.gs, gen, p.extra, p.status, p.limit_ns) ? 1 : 0;
-    else if (tid >= 32)
+    else if (tid >= 32 && !gram)
       pending_w(npend, pend_i, false);
     npend = 0;
     stamp(step, 3);
@@ -345,6 +348,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
           const double gv = fma(dscal, dsum[c], rowi[c]);
           gq0[c] = gv;
           gqf0[c] = f64_to_f32_rz(gv);
+          if (gram && g == 0) p.G[c + (size_t)i * bk] = gv;
         }
       }
       __syncthreads();
@@ -392,12 +396,17 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
           gqf0[c] = f64_to_f32_rz(g0);
           gq1[c] = g1;
           gqf1[c] = f64_to_f32_rz(g1);
+          if (gram && g == 0) {
+            p.G[c + (size_t)i * bk] = g0;
+            p.G[c + (size_t)(i + 1) * bk] = g1;
+          }
         }
       }
       if (tid == 0) {  // y_i^T y_{i+1} = scal a_{i+1} + scal2 scal (T_ab - zs T_aa)
         const double gi = fma(scal2 * scal, fma(-zs, Taa, Tab), scal * ai1);
         gq1[i] = gi;
         gqf1[i] = f64_to_f32_rz(gi);
+        if (gram && g == 0) p.G[i + (size_t)(i + 1) * bk] = gi;
         s_ptau[0] = tau;
         s_ptau[1] = tau2;
       }
@@ -422,9 +431,11 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
     __syncthreads();
     stamp(step, 6);
   }
-  pending_w(npend, pend_i, true);
+  if (!gram) pending_w(npend, pend_i, true);
   __syncthreads();
-  if (wf32) {
+  if (gram) {
+    // W is formed after the panel from G (w_from_gram)
+  } else if (wf32) {
     for (int idx = tid; idx < nr * bk; idx += NT) {
       const int r = idx % nr, c = idx / nr;
       p.W[rb + r + (int64_t)c * p.ldy] = tc::f32_to_f64(wlf[r + c * Rp]);
@@ -511,6 +522,60 @@ cudaError_t launch_panel(const PanelParams& prm, int G, cudaStream_t s) {
   void* args[] = {&p};
   prof::count_launch();
   return cudaLaunchCooperativeKernel((const void*)panel_qr_kernel, dim3(G), dim3(kPanelThreads), args, smem, s);
+}
+
+namespace {
+
+// One thread per row; the strict upper triangle of G and tau staged in shared memory; the
+// row's earlier entries of W read back from W (L1-resident).  Four independent partial sums
+// shorten the dependent FP64 chains.
+__global__ void w_from_gram_kernel(int j, int bk, const double* Y, const double* tau, const double* G, double* W,
+                                   int64_t ldy) {
+  extern __shared__ double wg_smem[];
+  double* sTau = wg_smem;       // bk
+  double* sG = wg_smem + bk;    // bk (bk - 1) / 2: column q at offset q (q - 1) / 2
+  pdl_wait_and_release();
+  for (int q = threadIdx.x; q < bk; q += blockDim.x) sTau[q] = tau[q];
+  for (int q = 1; q < bk; ++q)
+    for (int c = threadIdx.x; c < q; c += blockDim.x) sG[q * (q - 1) / 2 + c] = G[c + (size_t)q * bk];
+  __syncthreads();
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= j) return;
+  double* wr = W + r;
+#pragma unroll 1
+  for (int q = 0; q < bk; ++q) {
+    const double* gq = sG + q * (q - 1) / 2;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int c = 0;
+    for (; c + 3 < q; c += 4) {
+      s0 = fma(wr[(int64_t)c * ldy], gq[c], s0);
+      s1 = fma(wr[(int64_t)(c + 1) * ldy], gq[c + 1], s1);
+      s2 = fma(wr[(int64_t)(c + 2) * ldy], gq[c + 2], s2);
+      s3 = fma(wr[(int64_t)(c + 3) * ldy], gq[c + 3], s3);
+    }
+    for (; c < q; ++c) s0 = fma(wr[(int64_t)c * ldy], gq[c], s0);
+    wr[(int64_t)q * ldy] = -sTau[q] * (Y[r + (int64_t)q * ldy] + ((s0 + s1) + (s2 + s3)));
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_w_from_gram(int j, int bk, const double* Y, const double* tau, const double* G, double* W,
+                               int64_t ldy, cudaStream_t s) {
+  if (j <= 0 || bk <= 0) return cudaSuccess;
+  if (bk > 128) return cudaErrorInvalidValue;
+  static int configured_device = -1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (configured_device != dev) {
+    cudaError_t e = cudaFuncSetAttribute(w_from_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)((128 + 128 * 127 / 2) * sizeof(double)));
+    if (e != cudaSuccess) return e;
+    configured_device = dev;
+  }
+  const size_t smem = ((size_t)bk + (size_t)bk * (bk - 1) / 2) * sizeof(double);
+  prof::count_launch();
+  return launch_pdl(w_from_gram_kernel, dim3((j + 63) / 64), dim3(64), smem, s, j, bk, Y, tau, G, W, ldy);
 }
 
 }  // namespace bandred
