@@ -29,7 +29,7 @@ from dataclasses import asdict, dataclass
 import numpy as np
 
 OPS = ("sy2sb", "ge2gb")
-PRECISION_IDS = {"fp64": 0, "bf16x3": 1, "bf16x6": 2}
+PRECISION_IDS = {"fp64": 0, "bf16x3": 1, "bf16x6": 2, "ozaki": 3}
 N_FEATURES = 9
 
 
@@ -38,6 +38,7 @@ class Config:
     b: int
     lookahead: int  # -1 = the variant that b and w allow (Section 2.2 / 3.2), 0 = none
     panel_ctas: int  # 0 = the library's choice (all SMs for a large panel)
+    depth: int = 1  # look-ahead depth (2: V1 with 3b <= w, the panel two iterations ahead)
 
 
 def default_config(op: str, m: int, n: int, w: int) -> Config:
@@ -47,13 +48,17 @@ def default_config(op: str, m: int, n: int, w: int) -> Config:
 
 def candidates(op: str, m: int, n: int, w: int, sms: int = 152) -> list[Config]:
     """Candidate configurations of one size class: b from powers of two up to w (and w
-    itself), with and without look-ahead, all SMs or half of them for the panel."""
+    itself), with and without look-ahead, all SMs or half of them for the panel, and for
+    sy2sb with 3b <= w look-ahead depth 2 (Variant V1)."""
     bs = sorted({b for b in (8, 16, 32, 64, 128, w) if 8 <= b <= w and b < max(n - w, 2)} or {min(w, max(1, n))})
     out = []
     for b in bs:
         for la in (0, -1):
             for pc in (0, sms // 2):
                 out.append(Config(b, la, pc))
+        if op == "sy2sb" and 3 * b <= w:
+            for pc in (0, sms // 2):
+                out.append(Config(b, 1, pc, 2))
     return out
 
 
@@ -73,7 +78,7 @@ def features(op: str, m: int, n: int, w: int, cfg: Config, precision: str, sms: 
         math.log2(w) / 4.0 - 1.0,
         math.log2(cfg.b) / 4.0 - 1.0,
         cfg.b / w,
-        1.0 if cfg.lookahead != 0 else 0.0,
+        float(cfg.depth) if cfg.lookahead != 0 else 0.0,
         pc / sms,
         1.0 if op == "ge2gb" else 0.0,
         PRECISION_IDS.get(precision, 2) / 2.0,
@@ -167,8 +172,9 @@ def pick(cands: list[Config], timed_ms: dict, predicted_ms=None, budget: int | N
 
 
 def records_to_arrays(records: list[dict]):
-    X = np.stack([features(r["op"], r["m"], r["n"], r["w"], Config(r["b"], r["lookahead"], r["panel_ctas"]),
-                           r["precision"]) for r in records])
+    X = np.stack([features(r["op"], r["m"], r["n"], r["w"],
+                           Config(r["b"], r["lookahead"], r["panel_ctas"], r.get("depth", 1)), r["precision"])
+                  for r in records])
     return X, np.array([r["ms"] for r in records], dtype=np.float64)
 
 
@@ -182,7 +188,8 @@ def time_config(op: str, m: int, n: int, w: int, cfg: Config, precision: str, A0
                    bandred_sy2sb_workspace, make_opts)
 
     dev = A0.device
-    o = make_opts(b=cfg.b, lookahead=cfg.lookahead, precision=precision, panel_ctas=cfg.panel_ctas)
+    o = make_opts(b=cfg.b, lookahead=cfg.lookahead, precision=precision, panel_ctas=cfg.panel_ctas,
+                  depth=cfg.depth)
     A = torch.empty_like(A0)
     st = torch.zeros(1, dtype=torch.int32, device=dev)
     s = torch.cuda.current_stream(dev)
@@ -263,14 +270,14 @@ class Tuner:
         """The cached plan of the size class, else the packaged plan measured on GB300."""
         key = size_class(op, m, n, w, precision)
         p = self.plans.get(key) or packaged_plans().get(key)
-        return None if p is None else Config(p["b"], p["lookahead"], p["panel_ctas"])
+        return None if p is None else Config(p["b"], p["lookahead"], p["panel_ctas"], p.get("depth", 1))
 
     def opts(self, op: str, m: int, n: int, w: int, precision: str):
         """bandred_opts of the cached plan (the library defaults when the class is untuned)."""
         from . import make_opts
 
         c = self.lookup(op, m, n, w, precision) or default_config(op, m, n, w)
-        return make_opts(b=c.b, lookahead=c.lookahead, precision=precision, panel_ctas=c.panel_ctas)
+        return make_opts(b=c.b, lookahead=c.lookahead, precision=precision, panel_ctas=c.panel_ctas, depth=c.depth)
 
     def tune(self, op: str, m: int, n: int, w: int, precision: str = "bf16x6", model: CostModel | None = None,
              budget: int | None = None, reps: int = 3, seed: int = 0) -> Config:

@@ -15,7 +15,12 @@ def test_candidates_are_valid_and_contain_the_default(op, m, n, w):
     c = tune.candidates(op, m, n, w)
     assert len(c) == len(set(c)) > 0
     for cfg in c:
-        assert 1 <= cfg.b <= w and cfg.lookahead in (0, -1) and cfg.panel_ctas >= 0
+        assert 1 <= cfg.b <= w and cfg.panel_ctas >= 0
+        # depth 2 only as Variant V1 of sy2sb with 3b <= w; otherwise none or auto, depth 1
+        if cfg.depth == 2:
+            assert op == "sy2sb" and cfg.lookahead == 1 and 3 * cfg.b <= w
+        else:
+            assert cfg.depth == 1 and cfg.lookahead in (0, -1)
     d = tune.default_config(op, m, n, w)
     if d.b >= 8 and d.b < n - w:
         assert d in c
