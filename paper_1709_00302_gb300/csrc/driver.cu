@@ -335,6 +335,12 @@ static int run_panel(double* A, int64_t rs, int64_t cs, int j, int bk, double* t
       p.limit_ns = o.limit_ns;
       p.w_in_smem = true;
       p.w_fp32 = is_split(o);
+      if (!is_split(o) && bk <= 128) {  // FP64 W formed after the panel, as for the grid panel
+        p.G = gram;
+        CK(launch_panel_cluster(&p, nullptr, 1, C, p.Rp, bk, s));
+        CK(launch_w_from_gram(j, bk, Y, tau, gram, W, ldy, s));
+        return 0;
+      }
       CK(launch_panel_cluster(&p, nullptr, 1, C, p.Rp, bk, s));
       return 0;
     }

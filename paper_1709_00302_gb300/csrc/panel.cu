@@ -526,35 +526,41 @@ cudaError_t launch_panel(const PanelParams& prm, int G, cudaStream_t s) {
 
 namespace {
 
-// One thread per row; the strict upper triangle of G and tau staged in shared memory; the
-// row's earlier entries of W read back from W (L1-resident).  Four independent partial sums
-// shorten the dependent FP64 chains.
+// One thread per row (kWgRows rows per block).  The strict upper triangle of G, tau and the
+// block's rows of Y are staged in shared memory, and each row's entries of W stay there
+// while the substitution runs (a global store followed by a load of the same address would
+// wait for L2 on every term); four partial sums shorten the dependent FP64 chains.
+constexpr int kWgRows = 32;
 __global__ void w_from_gram_kernel(int j, int bk, const double* Y, const double* tau, const double* G, double* W,
                                    int64_t ldy) {
   extern __shared__ double wg_smem[];
-  double* sTau = wg_smem;       // bk
-  double* sG = wg_smem + bk;    // bk (bk - 1) / 2: column q at offset q (q - 1) / 2
+  double* sTau = wg_smem;                     // bk
+  double* sG = sTau + bk;                     // bk (bk - 1) / 2: column q at offset q (q - 1) / 2
+  double* sW = sG + (size_t)bk * (bk - 1) / 2;  // bk x kWgRows: entry (q, t) at q kWgRows + t
   pdl_wait_and_release();
-  for (int q = threadIdx.x; q < bk; q += blockDim.x) sTau[q] = tau[q];
+  const int t = threadIdx.x, r0 = blockIdx.x * kWgRows, r = r0 + t;
+  for (int q = t; q < bk; q += blockDim.x) sTau[q] = tau[q];
   for (int q = 1; q < bk; ++q)
-    for (int c = threadIdx.x; c < q; c += blockDim.x) sG[q * (q - 1) / 2 + c] = G[c + (size_t)q * bk];
+    for (int c = t; c < q; c += blockDim.x) sG[q * (q - 1) / 2 + c] = G[c + (size_t)q * bk];
+  if (r < j)
+    for (int q = 0; q < bk; ++q) sW[q * kWgRows + t] = Y[r + (int64_t)q * ldy];  // y_r, replaced by w_r
   __syncthreads();
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= j) return;
-  double* wr = W + r;
 #pragma unroll 1
   for (int q = 0; q < bk; ++q) {
     const double* gq = sG + q * (q - 1) / 2;
     double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
     int c = 0;
     for (; c + 3 < q; c += 4) {
-      s0 = fma(wr[(int64_t)c * ldy], gq[c], s0);
-      s1 = fma(wr[(int64_t)(c + 1) * ldy], gq[c + 1], s1);
-      s2 = fma(wr[(int64_t)(c + 2) * ldy], gq[c + 2], s2);
-      s3 = fma(wr[(int64_t)(c + 3) * ldy], gq[c + 3], s3);
+      s0 = fma(sW[c * kWgRows + t], gq[c], s0);
+      s1 = fma(sW[(c + 1) * kWgRows + t], gq[c + 1], s1);
+      s2 = fma(sW[(c + 2) * kWgRows + t], gq[c + 2], s2);
+      s3 = fma(sW[(c + 3) * kWgRows + t], gq[c + 3], s3);
     }
-    for (; c < q; ++c) s0 = fma(wr[(int64_t)c * ldy], gq[c], s0);
-    wr[(int64_t)q * ldy] = -sTau[q] * (Y[r + (int64_t)q * ldy] + ((s0 + s1) + (s2 + s3)));
+    for (; c < q; ++c) s0 = fma(sW[c * kWgRows + t], gq[c], s0);
+    const double wq = -sTau[q] * (sW[q * kWgRows + t] + ((s0 + s1) + (s2 + s3)));
+    sW[q * kWgRows + t] = wq;
+    W[r + (int64_t)q * ldy] = wq;
   }
 }
 
@@ -569,13 +575,14 @@ cudaError_t launch_w_from_gram(int j, int bk, const double* Y, const double* tau
   cudaGetDevice(&dev);
   if (configured_device != dev) {
     cudaError_t e = cudaFuncSetAttribute(w_from_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)((128 + 128 * 127 / 2) * sizeof(double)));
+                                         (int)((128 + 128 * 127 / 2 + 128 * kWgRows) * sizeof(double)));
     if (e != cudaSuccess) return e;
     configured_device = dev;
   }
-  const size_t smem = ((size_t)bk + (size_t)bk * (bk - 1) / 2) * sizeof(double);
+  const size_t smem = ((size_t)bk + (size_t)bk * (bk - 1) / 2 + (size_t)bk * kWgRows) * sizeof(double);
   prof::count_launch();
-  return launch_pdl(w_from_gram_kernel, dim3((j + 63) / 64), dim3(64), smem, s, j, bk, Y, tau, G, W, ldy);
+  return launch_pdl(w_from_gram_kernel, dim3((j + kWgRows - 1) / kWgRows), dim3(kWgRows), smem, s, j, bk, Y, tau, G,
+                    W, ldy);
 }
 
 }  // namespace bandred

@@ -47,6 +47,9 @@ __global__ void __launch_bounds__(kPanelThreads, 4)
   double* resc = gprev + bk + (bk + 1) / 2;        // bk: partial sums of the rare path's scaled pass
   double* after = resc + bk;
   const bool wf32 = p.w_fp32;
+  // gram: W is formed after the panel (w_from_gram) from the T coefficients that rank 0
+  // stores into p.G; no W recurrence inside the panel
+  const bool gram = p.G != nullptr;
   double* wl = after;                              // W rows: FP64 or FP32, always in shared memory
   float* wlf = reinterpret_cast<float*>(after);
   __shared__ double s_beta, s_tau, s_scal, s_dscal, s_tau_prev;
@@ -111,7 +114,7 @@ __global__ void __launch_bounds__(kPanelThreads, 4)
       for (int c = tid; c < bk; c += NT) myrow[c] = slab[(size_t)c * Rp + (i - rb)];
     __syncthreads();
     cluster_arrive();
-    if (i > 0) {
+    if (i > 0 && !gram) {
       if (wf32)
         w_column_f32(i - 1, (float)s_tau_prev, gprevf, slab, Rp, rb, nr, wlf);
       else
@@ -226,6 +229,7 @@ __global__ void __launch_bounds__(kPanelThreads, 4)
         } else if (c < i && rg == 0) {
           const double gv = fma(dscal, dsum[c], rowi[c]);
           gprev[c] = gv;
+          if (gram && rank == 0) p.G[c + (size_t)i * bk] = gv;
           gprevf[c] = f64_to_f32_rz(gv);
         }
       }
@@ -237,15 +241,16 @@ __global__ void __launch_bounds__(kPanelThreads, 4)
     if (tid == 0) s_tau_prev = tau;
     __syncthreads();
   }
-  if (wf32)
-    w_column_f32(bk - 1, (float)s_tau_prev, gprevf, slab, Rp, rb, nr, wlf);
-  else
-    w_column(bk - 1, s_tau_prev, gprev, slab, Rp, rb, nr, wl, Rp);
-  __syncthreads();
-
-  for (int idx = tid; idx < nr * bk; idx += NT) {
-    const int r = idx % nr, c = idx / nr;
-    p.W[rb + r + (int64_t)c * p.ldy] = wf32 ? tc::f32_to_f64(wlf[r + c * Rp]) : wl[r + (int64_t)c * Rp];
+  if (!gram) {
+    if (wf32)
+      w_column_f32(bk - 1, (float)s_tau_prev, gprevf, slab, Rp, rb, nr, wlf);
+    else
+      w_column(bk - 1, s_tau_prev, gprev, slab, Rp, rb, nr, wl, Rp);
+    __syncthreads();
+    for (int idx = tid; idx < nr * bk; idx += NT) {
+      const int r = idx % nr, c = idx / nr;
+      p.W[rb + r + (int64_t)c * p.ldy] = wf32 ? tc::f32_to_f64(wlf[r + c * Rp]) : wl[r + (int64_t)c * Rp];
+    }
   }
   if (p.rs == 1) {
     for (int idx = tid; idx < nr * bk; idx += NT) {
