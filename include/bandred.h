@@ -323,7 +323,8 @@ long long bandred_launch_count(void);
  * trace; it returns the number written, or a negative code.  kind: 0 panel (QR of a
  * column panel), 1 rank-2k update of the next panel's columns (A2^L), 2 rank-2k update
  * of the rest (A2^R, or all of A2 without look-ahead), 3 X1 = A2 W, 4 row panel (LQ),
- * 5 left update (ge2gb), 6 right update (ge2gb); iteration = the panel's first column.
+ * 5 left update (ge2gb), 6 right update (ge2gb), 7 W = -Y T formed after a panel
+ * (iteration 0); iteration = the panel's first column.
  * Host-side, one trace at a time per process; a diagnostic, not for the hot path. */
 typedef struct bandred_trace_record {
     int kind;

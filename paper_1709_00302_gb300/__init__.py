@@ -405,7 +405,7 @@ class GeBatch:
 
 
 TRACE_KINDS = {0: "panel", 1: "rank_next_panel", 2: "rank_rest", 3: "x1_product", 4: "row_panel", 5: "left_update",
-               6: "right_update"}
+               6: "right_update", 7: "w_from_gram"}
 
 
 def bandred_trace_begin(buf) -> int:

@@ -226,7 +226,7 @@ struct SplitBufs {
 };
 
 struct Ge2gbWs {
-  double *Yu[2], *Wu[2], *Yv, *Wv, *Z[2], *ZT, *P, *splitk[2], *part, *rowbuf, *gram;
+  double *Yu[2], *Wu[2], *Yv[2], *Wv[2], *Z[2], *ZT, *MT, *P, *splitk[2], *part, *rowbuf, *gram;
   GridSync* gs;
   SplitBufs sb[2];  // [0] caller's stream, [1] panel stream (look-ahead)
   char *ozp[2], *ozr[2];  // Ozaki-scheme buffers per stream (see Sy2sbWs)
@@ -237,7 +237,7 @@ struct Ge2gbWs {
   size_t bytes;
 };
 
-static Ge2gbWs carve_ge2gb(void* work, int64_t m, int64_t n, const Options& o, int sms) {
+static Ge2gbWs carve_ge2gb(void* work, int64_t m, int64_t n, int64_t w, const Options& o, int sms) {
   Carver c{static_cast<char*>(work)};
   Ge2gbWs ws{};
   const int64_t b = o.b;
@@ -248,8 +248,15 @@ static Ge2gbWs carve_ge2gb(void* work, int64_t m, int64_t n, const Options& o, i
     ws.Yu[q] = q < nbuf ? c.take<double>(ws.ldu * b) : ws.Yu[0];
     ws.Wu[q] = q < nbuf ? c.take<double>(ws.ldu * b) : ws.Wu[0];
   }
-  ws.Yv = c.take<double>(ws.ldv * b);
-  ws.Wv = c.take<double>(ws.ldv * b);
+  // row-panel Y/W: two pairs with the second look-ahead overlap (w >= 3b), which keeps the
+  // previous row panel's reflectors while the next one is factored
+  const int nbv = (o.lookahead != 0 && 3 * b <= w) ? 2 : 1;
+  for (int q = 0; q < 2; ++q) {
+    ws.Yv[q] = q < nbv ? c.take<double>(ws.ldv * b) : ws.Yv[0];
+    ws.Wv[q] = q < nbv ? c.take<double>(ws.ldv * b) : ws.Wv[0];
+  }
+  ws.MT = c.take<double>((size_t)b * b);
+  ws.ZT = c.take<double>(ws.ldv * b);
   ws.P = c.take<double>(ws.ldu * b);
   ws.splitk_cap = (size_t)kSmallSplits * b * b * 4;
   for (int q = 0; q < 2; ++q) {
@@ -265,7 +272,6 @@ static Ge2gbWs carve_ge2gb(void* work, int64_t m, int64_t n, const Options& o, i
     const int BN = split::stream_bn((int)b);
     const int Kr = (int)((b + 63) / 64 * 64);
     const int64_t big = std::max(ws.ldu, ws.ldv);
-    ws.ZT = c.take<double>(ws.ldv * b);
     for (int q = 0; q < nbuf; ++q) {
       SplitBufs& sb = ws.sb[q];
       sb.bblob = c.take<__nv_bfloat16>(split::packed_bytes(BN, (int)big, BN, 32, S) / 2);
@@ -278,7 +284,6 @@ static Ge2gbWs carve_ge2gb(void* work, int64_t m, int64_t n, const Options& o, i
   }
   if (o.precision == BANDRED_OZAKI) {
     const int big = (int)std::max(ws.ldu, ws.ldv), B = (int)b;
-    ws.ZT = c.take<double>(ws.ldv * b);
     ws.ozp_cap = ozaki::bytes(big, B, big, ozaki::choose_splits(big, B, big, sms));
     for (int q = 0; q < nbuf; ++q) {
       ws.ozp[q] = c.take<char>(ws.ozp_cap);
@@ -1068,20 +1073,87 @@ struct Ge2gb {
     return split_rank(j, nc, bk, ws.Yu[buf], ws.ldu, ZT, ws.ldv, E, lda, ws.sb[q], S, status, o.limit_ns, s);
   }
 
-  // LQ of C = A(k:k+bkr, k+w:n) (Eq. updateC).
-  int right_panel(int64_t k, cudaStream_t s) {
+  // ---- building blocks of the second look-ahead overlap (ge2gb_run, w >= 3b), in the
+  // precision of the options; q selects the stream's buffers (0 caller, 1 panel stream).
+  // C (M x N, ldc) = As^T Bs with As K x M (lda) and Bs K x N (ldb), column-major.
+  int prod_t(int M, int N, int K, const double* As, int64_t lda, const double* Bs, int64_t ldb, double* C, int64_t ldc,
+             int q, cudaStream_t s) {
+    if (M <= 0 || N <= 0) return 0;
+    prof::Scope sc(prof::kStream, s, 2.0 * M * N * K, 8.0 * ((double)M * K + (double)K * N + (double)M * N));
+    if (o.precision == BANDRED_FP64) {
+      const int sp = choose_splits(M, N, K, ws.splitk_cap, sms);
+      CK(gemm_f64(M, N, K, 1.0, MatView{As, lda, 1}, MatView{Bs, 1, ldb}, 0.0, C, ldc, sp, ws.splitk[q], s));
+      return 0;
+    }
+    if (o.precision == BANDRED_OZAKI) {
+      using ozaki::Operand;
+      const Operand a{As, lda, 1, K, nullptr, 0, 0, 0, M}, bo{Bs, ldb, 1, K, nullptr, 0, 0, 0, N};
+      const int sp = ozaki::fit_splits(M, N, K, ozaki::choose_splits(M, N, K, sms), ws.ozp_cap);
+      CK(ozaki::product(a, bo, M, N, K, 1.0, 0.0, C, ldc, ozaki::carve(ws.ozp[q], M, N, K, sp), sp, status, o.limit_ns,
+                        s));
+      return 0;
+    }
+    return split_product(M, N, K, As, lda, split::kModeTrans, Bs, ldb, 1.0, 0.0, C, ldc, ws.sb[q], S, sms, status,
+                         o.limit_ns, s);
+  }
+  // C (M x N, ldc) = As Bs with As M x K (lda) and Bs K x N (ldb).
+  int prod_n(int M, int N, int K, const double* As, int64_t lda, const double* Bs, int64_t ldb, double* C, int64_t ldc,
+             int q, cudaStream_t s) {
+    if (M <= 0 || N <= 0) return 0;
+    prof::Scope sc(prof::kStream, s, 2.0 * M * N * K, 8.0 * ((double)M * K + (double)K * N + (double)M * N));
+    if (o.precision == BANDRED_FP64) {
+      const int sp = choose_splits(M, N, K, ws.splitk_cap, sms);
+      CK(gemm_f64(M, N, K, 1.0, MatView{As, 1, lda}, MatView{Bs, 1, ldb}, 0.0, C, ldc, sp, ws.splitk[q], s));
+      return 0;
+    }
+    if (o.precision == BANDRED_OZAKI) {
+      using ozaki::Operand;
+      const Operand a{As, lda, 0, K, nullptr, 0, 0, 0, M}, bo{Bs, ldb, 1, K, nullptr, 0, 0, 0, N};
+      const int sp = ozaki::fit_splits(M, N, K, ozaki::choose_splits(M, N, K, sms), ws.ozp_cap);
+      CK(ozaki::product(a, bo, M, N, K, 1.0, 0.0, C, ldc, ozaki::carve(ws.ozp[q], M, N, K, sp), sp, status, o.limit_ns,
+                        s));
+      return 0;
+    }
+    return split_product(M, N, K, As, lda, split::kModePlain, Bs, ldb, 1.0, 0.0, C, ldc, ws.sb[q], S, sms, status,
+                         o.limit_ns, s);
+  }
+  // C (M x N, ldc) += L R^T with L M x K (ldl) and R N x K (ldr).
+  int rank_k(int M, int N, int K, const double* L, int64_t ldl, const double* Rm, int64_t ldr, double* C, int64_t ldc,
+             int q, cudaStream_t s) {
+    if (M <= 0 || N <= 0 || K <= 0) return 0;
+    prof::Scope sc(prof::kRank, s, 2.0 * M * N * K, 8.0 * (2.0 * M * N + (double)(M + N) * K));
+    if (o.precision == BANDRED_FP64) {
+      CK(gemm_f64(M, N, K, 1.0, MatView{L, 1, ldl}, MatView{Rm, ldr, 1}, 1.0, C, ldc, 1, nullptr, s));
+      return 0;
+    }
+    if (o.precision == BANDRED_OZAKI) {
+      using ozaki::Operand;
+      const Operand l{L, ldl, 0, K, nullptr, 0, 0, 0, M}, r{Rm, ldr, 0, K, nullptr, 0, 0, 0, N};
+      const ozaki::Bufs rb = ozaki::carve(ws.ozr[q], M, N, K, 1);
+      CK(ozaki::prepare(l, r, rb, s));
+      CK(ozaki::rank_apply(M, N, K, 1.0, C, ldc, 0, N, 0, rb, status, o.limit_ns, s));
+      return 0;
+    }
+    return split_rank(M, N, K, L, ldl, Rm, ldr, C, ldc, ws.sb[q], S, status, o.limit_ns, s);
+  }
+
+  // LQ of C = A(k:k+bkr, k+w:n) (Eq. updateC) into row-panel buffer bvi.
+  int right_panel(int64_t k, cudaStream_t s, int bvi = 0) {
     const int bk = bk_of(k);
     const int64_t bkr = std::min<int64_t>(bk, n - w - 1 - k);
     if (bkr <= 0) return 0;
     const int jr = (int)(n - k - w);
     prof::Scope sc(prof::kPanel, s, panel_flops(jr, (int)bkr), panel_bytes(jr, (int)bkr));
     prof::TraceScope tr(prof::kTracePanelRow, k);
-    return run_panel(A + k + (k + w) * lda, lda, 1, jr, (int)bkr, taup + k, ws.Yv, ws.Wv, ws.ldv, ws.part, ws.rowbuf,
+    return run_panel(A + k + (k + w) * lda, lda, 1, jr, (int)bkr, taup + k, ws.Yv[bvi], ws.Wv[bvi], ws.ldv, ws.part,
+                     ws.rowbuf,
                      ws.gram, ws.gs, status, o, pmax, 0u, s);
   }
 
-  // D = A(k+bkr:m, k+w:n) += (D W_V) Y_V^T (Eq. updateD).
-  int d_update(int64_t k, cudaStream_t s) {
+  // D = A(k+bkr:m, k+w:n) += (D W_V) Y_V^T (Eq. updateD), row panel from buffer bvi.
+  int d_update(int64_t k, cudaStream_t s, int bvi = 0) {
+    const double* Yv = ws.Yv[bvi];
+    const double* Wv = ws.Wv[bvi];
     const int bk = bk_of(k);
     const int64_t bkr = std::min<int64_t>(bk, n - w - 1 - k);
     if (bkr <= 0) return 0;
@@ -1092,16 +1164,16 @@ struct Ge2gb {
     if (o.precision == BANDRED_FP64) {
       prof::Scope sc(prof::kGemm, s, 4.0 * nrow * jr * bkr, 8.0 * (3.0 * nrow * jr + 2.0 * nrow * bkr));
       const int sp = choose_splits(nrow, (int)bkr, jr, ws.splitk_cap, sms);
-      CK(gemm_f64(nrow, (int)bkr, jr, 1.0, MatView{D, 1, lda}, MatView{ws.Wv, 1, ws.ldv}, 0.0, ws.P, ws.ldu, sp,
+      CK(gemm_f64(nrow, (int)bkr, jr, 1.0, MatView{D, 1, lda}, MatView{Wv, 1, ws.ldv}, 0.0, ws.P, ws.ldu, sp,
                   ws.splitk[0], s));
-      CK(gemm_f64(nrow, jr, (int)bkr, 1.0, MatView{ws.P, 1, ws.ldu}, MatView{ws.Yv, ws.ldv, 1}, 1.0, D, lda, 1,
+      CK(gemm_f64(nrow, jr, (int)bkr, 1.0, MatView{ws.P, 1, ws.ldu}, MatView{Yv, ws.ldv, 1}, 1.0, D, lda, 1,
                   nullptr, s));
       return 0;
     }
     if (o.precision == BANDRED_OZAKI) {
       using ozaki::Operand;
       const int B = (int)bkr;
-      const Operand d{D, lda, 0, jr, nullptr, 0, 0, 0, nrow}, wv{ws.Wv, ws.ldv, 1, jr, nullptr, 0, 0, 0, B};
+      const Operand d{D, lda, 0, jr, nullptr, 0, 0, 0, nrow}, wv{Wv, ws.ldv, 1, jr, nullptr, 0, 0, 0, B};
       {
         prof::Scope sc(prof::kStream, s, 2.0 * nrow * B * jr, 8.0 * ((double)nrow * jr + (double)jr * B + (double)nrow * B));
         const int sp = ozaki::fit_splits(nrow, B, jr, ozaki::choose_splits(nrow, B, jr, sms), ws.ozp_cap);
@@ -1109,17 +1181,17 @@ struct Ge2gb {
                           status, o.limit_ns, s));
       }
       prof::Scope sc(prof::kRank, s, 2.0 * nrow * jr * B, 8.0 * (2.0 * nrow * jr + (double)(nrow + jr) * B));
-      const Operand pp{ws.P, ws.ldu, 0, B, nullptr, 0, 0, 0, nrow}, yv{ws.Yv, ws.ldv, 0, B, nullptr, 0, 0, 0, jr};
+      const Operand pp{ws.P, ws.ldu, 0, B, nullptr, 0, 0, 0, nrow}, yv{Yv, ws.ldv, 0, B, nullptr, 0, 0, 0, jr};
       const ozaki::Bufs rb = ozaki::carve(ws.ozr[0], nrow, jr, B, 1);
       CK(ozaki::prepare(pp, yv, rb, s));
       prof::TraceScope tr(prof::kTraceRight, k);
       CK(ozaki::rank_apply(nrow, jr, B, 1.0, D, lda, 0, jr, 0, rb, status, o.limit_ns, s));
       return 0;
     }
-    if (int rc = split_product(nrow, (int)bkr, jr, D, lda, split::kModePlain, ws.Wv, ws.ldv, 1.0, 0.0, ws.P, ws.ldu,
+    if (int rc = split_product(nrow, (int)bkr, jr, D, lda, split::kModePlain, Wv, ws.ldv, 1.0, 0.0, ws.P, ws.ldu,
                                ws.sb[0], S, sms, status, o.limit_ns, s))
       return rc;
-    return split_rank(nrow, jr, (int)bkr, ws.P, ws.ldu, ws.Yv, ws.ldv, D, lda, ws.sb[0], S, status, o.limit_ns, s);
+    return split_rank(nrow, jr, (int)bkr, ws.P, ws.ldu, Yv, ws.ldv, D, lda, ws.sb[0], S, status, o.limit_ns, s);
   }
 };
 
@@ -1161,7 +1233,7 @@ int ge2gb_run(int64_t m, int64_t n, int64_t w, double* A, int64_t lda, double* t
   R.taup = taup;
   R.o = o;
   R.sms = current_sms();
-  R.ws = carve_ge2gb(work, m, n, o, R.sms);
+  R.ws = carve_ge2gb(work, m, n, w, o, R.sms);
   R.status = dev_status ? dev_status : R.ws.status;
   R.pmax = panel_max_ctas(R.sms, o);
   R.S = is_split(o) ? split::slices_of(o.precision) : 0;
@@ -1190,6 +1262,82 @@ int ge2gb_run(int64_t m, int64_t n, int64_t w, double* A, int64_t lda, double* t
   CK(cudaStreamWaitEvent(sp, ev_fork, 0));
   if ((rc = R.left_panel(0, 0, sp))) return rc;
   CK(cudaEventRecord(ev_panel, sp));
+
+  if (3 * b <= w && (o.lookahead == -1 || o.lookahead == 2)) {
+    // Both overlaps of Section 3.2's third case (w >= 3b): the row panel L^k V^k runs beside
+    // the right update of the previous iteration, and the next column panel beside the left
+    // update.  The left update U_k^T (rows >= k) and the pending right update V_{k-1}
+    // (columns >= k - b + w) commute, so both are written from products of the state before
+    // either: Z = W_U^T E, P = D W_V and Z V = Z + (Z W_V) Y_V^T give
+    //   U_k^T A V_{k-1} = A + P Y_V^T + Y_U (Z V)      (on the rows >= k of E and D).
+    // The panel stream applies that to row block k (b rows) and factors L^k V^k, then to the
+    // next column panel's columns (below the row block) and factors it, while the caller's
+    // stream applies it to everything else.  Iterations with a narrower last panel finish
+    // without look-ahead.
+    int64_t k = 0, kprev = -1;
+    int bu = 0, bvp = 0;
+    for (; k + 2 * b <= n - w - 1; k += b, bu ^= 1) {
+      const int bk = b, j = (int)(m - k), nc = (int)(n - k - bk);
+      double* E = A + k + (k + bk) * lda;
+      CK(cudaStreamWaitEvent(s, ev_panel, 0));  // column panel k (and row panel kprev) factored
+      // pre-state products on the caller's stream: Z^T = E^T W_U (nc x bk)
+      if ((rc = R.prod_t(nc, bk, j, E, lda, R.ws.Wu[bu], R.ws.ldu, R.ws.ZT, R.ws.ldv, 0, s))) return rc;
+      int c0v = 0, jr = 0;
+      if (kprev >= 0) {
+        c0v = (int)(kprev + w - (k + bk));  // first column of E in the pending right update's range
+        jr = (int)(n - (kprev + w));
+        // P = D W_V, D = A(k:m, kprev+w:n) (its rows start at kprev + b = k)
+        if ((rc = R.prod_n(j, b, jr, A + k + (kprev + w) * lda, lda, R.ws.Wv[bvp], R.ws.ldv, R.ws.P, R.ws.ldu, 0, s)))
+          return rc;
+        // Z V on that range: (Z V)^T = Z^T + Y_V MT^T with MT = (Z^T)^T W_V restricted to it
+        if ((rc = R.prod_t(bk, b, jr, R.ws.ZT + c0v, R.ws.ldv, R.ws.Wv[bvp], R.ws.ldv, R.ws.MT, bk, 0, s))) return rc;
+        if ((rc = R.rank_k(jr, bk, b, R.ws.Yv[bvp], R.ws.ldv, R.ws.MT, bk, R.ws.ZT + c0v, R.ws.ldv, 0, s))) return rc;
+      }
+      CK(cudaEventRecord(ev_e, s));
+      CK(cudaStreamWaitEvent(sp, ev_e, 0));
+      const int bkn = R.bk_of(k + b);
+      // panel stream: row block k (rows k .. k+bk), then row panel k; the next column
+      // panel's columns below the row block, then that panel
+      if ((rc = R.rank_k(bk, nc, bk, R.ws.Yu[bu], R.ws.ldu, R.ws.ZT, R.ws.ldv, E, lda, 1, sp))) return rc;
+      if (kprev >= 0 &&
+          (rc = R.rank_k(bk, jr, b, R.ws.P, R.ws.ldu, R.ws.Yv[bvp], R.ws.ldv, A + k + (kprev + w) * lda, lda, 1, sp)))
+        return rc;
+      if ((rc = R.right_panel(k, sp, bvp ^ 1))) return rc;
+      if ((rc = R.rank_k(j - bk, bkn, bk, R.ws.Yu[bu] + bk, R.ws.ldu, R.ws.ZT, R.ws.ldv, E + bk, lda, 1, sp)))
+        return rc;
+      if ((rc = R.left_panel(k + b, bu ^ 1, sp))) return rc;
+      CK(cudaEventRecord(ev_panel, sp));
+      // caller's stream: the rest (rows below the row block, columns past the next panel)
+      {
+        prof::TraceScope tr(prof::kTraceLeft, k);
+        if ((rc = R.rank_k(j - bk, nc - bkn, bk, R.ws.Yu[bu] + bk, R.ws.ldu, R.ws.ZT + bkn, R.ws.ldv,
+                           E + bk + (int64_t)bkn * lda, lda, 0, s)))
+          return rc;
+      }
+      if (kprev >= 0) {
+        prof::TraceScope tr(prof::kTraceRight, kprev);
+        if ((rc = R.rank_k(j - bk, jr, b, R.ws.P + bk, R.ws.ldu, R.ws.Yv[bvp], R.ws.ldv,
+                           A + k + bk + (kprev + w) * lda, lda, 0, s)))
+          return rc;
+      }
+      kprev = k;
+      bvp ^= 1;
+    }
+    // the rest without look-ahead: the pending right update, then iteration k onwards
+    // (column panel k is already factored, in buffer bu)
+    CK(cudaStreamWaitEvent(s, ev_panel, 0));
+    if (kprev >= 0 && (rc = R.d_update(kprev, s, bvp))) return rc;
+    for (bool first = true; k < n; k += b, bu ^= 1, first = false) {
+      if (!first && (rc = R.left_panel(k, bu, s))) return rc;
+      if ((rc = R.e_update(k, bu, 0, (int)n, 0, s))) return rc;
+      if ((rc = R.right_panel(k, s, 0))) return rc;
+      if ((rc = R.d_update(k, s, 0))) return rc;
+    }
+    CK(cudaEventRecord(ev_fork, sp));
+    CK(cudaStreamWaitEvent(s, ev_fork, 0));
+    return 0;
+  }
+
   int buf = 0;
   for (int64_t k = 0; k < n; k += b, buf ^= 1) {
     const int64_t kn = k + b;
@@ -1220,7 +1368,7 @@ int ge2gb_run(int64_t m, int64_t n, int64_t w, double* A, int64_t lda, double* t
 
 size_t ge2gb_workspace_bytes(int64_t m, int64_t n, int64_t w, const Options& o) {
   if (n > m) return align_up((size_t)m * n * sizeof(double)) + ge2gb_workspace_bytes(n, m, w, o);
-  return carve_ge2gb(nullptr, m, n, o, current_sms()).bytes;
+  return carve_ge2gb(nullptr, m, n, w, o, current_sms()).bytes;
 }
 
 }  // namespace bandred

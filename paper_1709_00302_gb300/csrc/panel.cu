@@ -532,12 +532,13 @@ namespace {
 // wait for L2 on every term); four partial sums shorten the dependent FP64 chains.
 constexpr int kWgRows = 32;
 __global__ void w_from_gram_kernel(int j, int bk, const double* Y, const double* tau, const double* G, double* W,
-                                   int64_t ldy) {
+                                   int64_t ldy, unsigned long long* trace) {
   extern __shared__ double wg_smem[];
   double* sTau = wg_smem;                     // bk
   double* sG = sTau + bk;                     // bk (bk - 1) / 2: column q at offset q (q - 1) / 2
   double* sW = sG + (size_t)bk * (bk - 1) / 2;  // bk x kWgRows: entry (q, t) at q kWgRows + t
   pdl_wait_and_release();
+  trace_start(trace);
   const int t = threadIdx.x, r0 = blockIdx.x * kWgRows, r = r0 + t;
   for (int q = t; q < bk; q += blockDim.x) sTau[q] = tau[q];
   for (int q = 1; q < bk; ++q)
@@ -545,7 +546,7 @@ __global__ void w_from_gram_kernel(int j, int bk, const double* Y, const double*
   if (r < j)
     for (int q = 0; q < bk; ++q) sW[q * kWgRows + t] = Y[r + (int64_t)q * ldy];  // y_r, replaced by w_r
   __syncthreads();
-  if (r >= j) return;
+  if (r < j) {
 #pragma unroll 1
   for (int q = 0; q < bk; ++q) {
     const double* gq = sG + q * (q - 1) / 2;
@@ -562,6 +563,9 @@ __global__ void w_from_gram_kernel(int j, int bk, const double* Y, const double*
     sW[q * kWgRows + t] = wq;
     W[r + (int64_t)q * ldy] = wq;
   }
+  }
+  __syncthreads();
+  trace_end(trace);
 }
 
 }  // namespace
@@ -580,9 +584,11 @@ cudaError_t launch_w_from_gram(int j, int bk, const double* Y, const double* tau
     configured_device = dev;
   }
   const size_t smem = ((size_t)bk + (size_t)bk * (bk - 1) / 2 + (size_t)bk * kWgRows) * sizeof(double);
+  prof::TraceScope tr(prof::kTraceW, 0);
+  unsigned long long* rec = prof::trace_take();
   prof::count_launch();
   return launch_pdl(w_from_gram_kernel, dim3((j + kWgRows - 1) / kWgRows), dim3(kWgRows), smem, s, j, bk, Y, tau, G,
-                    W, ldy);
+                    W, ldy, rec);
 }
 
 }  // namespace bandred

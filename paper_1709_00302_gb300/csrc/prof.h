@@ -34,7 +34,7 @@ class Scope {
 // kernel takes the record with trace_take() (nullptr when tracing is off or the buffer is
 // full) and passes it to the kernel, whose CTAs stamp their start and end into it
 // (trace_start / trace_end in common.cuh).
-enum TraceKind { kTracePanel = 0, kTraceRankL, kTraceRankR, kTraceSymm, kTracePanelRow, kTraceLeft, kTraceRight };
+enum TraceKind { kTracePanel = 0, kTraceRankL, kTraceRankR, kTraceSymm, kTracePanelRow, kTraceLeft, kTraceRight, kTraceW };
 
 class TraceScope {
  public:
