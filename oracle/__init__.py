@@ -46,6 +46,8 @@ def _load():
         lib.oracle_sy2sb.restype = c_int
         lib.oracle_ge2gb.argtypes = [i64, i64, i64, dp, i64, dp, dp, i64]
         lib.oracle_ge2gb.restype = c_int
+        lib.oracle_ge2bb.argtypes = [i64, i64, i64, dp, i64, dp, dp, i64]
+        lib.oracle_ge2bb.restype = c_int
         lib.oracle_jacobi_eig.argtypes = [i64, dp, i64, dp]
         lib.oracle_jacobi_eig.restype = c_int
         lib.oracle_jacobi_svd.argtypes = [i64, i64, dp, i64, dp]
@@ -101,6 +103,24 @@ def ge2gb(A: np.ndarray, w: int, ncols: int = -1):
     if info != 0:
         raise ValueError(f"oracle_ge2gb: info={info}")
     return A, tauq[:n], taup[: max(n - w, 0)]
+
+
+def ge2bb(A: np.ndarray, w: int, ncols: int = -1):
+    """Reduce general A (m x n) to a band with lower and upper bandwidth w (Section 3.3).
+
+    Returns (Aout, tauq[max(min(n, m-w), 0)], taup[max(min(m, n-w), 0)]); the band
+    |i - j| <= w of Aout holds B, left reflector c has v in Aout(c+w+1:m, c), right
+    reflector c has v in Aout(c, c+w+1:n).
+    """
+    A = np.array(A, dtype=np.float64, order="F", copy=True)
+    m, n = A.shape
+    nlq, nrq = max(min(n, m - w), 0), max(min(m, n - w), 0)
+    tauq = np.zeros(nlq + 1, dtype=np.float64)
+    taup = np.zeros(nrq + 1, dtype=np.float64)
+    info = _load().oracle_ge2bb(m, n, w, _ptr(A), max(m, 1), _ptr(tauq), _ptr(taup), ncols)
+    if info != 0:
+        raise ValueError(f"oracle_ge2bb: info={info}")
+    return A, tauq[:nlq], taup[:nrq]
 
 
 def ge2gb_wide(A: np.ndarray, w: int):

@@ -240,6 +240,81 @@ int oracle_ge2gb(int64_t m, int64_t n, int64_t w, double *A, int64_t lda, double
 }
 
 /* ---------------------------------------------------------------------------------
+ * General A (m x n) -> band with lower AND upper bandwidth w (the SVD band form of
+ * Section 3.3, Eqs. updateB0 .. gebrd_2k, read unblocked): for c = 0, 1, ... a left
+ * reflector annihilates A(c+w+1 : m, c) (acting on rows c+w .. m-1) and a right reflector
+ * annihilates A(c, c+w+1 : n) (acting on columns c+w .. n-1).  With b <= w the blocked
+ * algorithm gives the same reflectors in exact arithmetic: a block's left reflectors act
+ * on rows >= k+w, below its right panel's rows, and its right reflectors on columns
+ * >= k+w, right of its left panel's columns.
+ * Outputs: B in the band |i-j| <= w; left reflector c (c = 0 .. min(n, m-w)-1): beta on
+ * A(c+w, c), v in A(c+w+1 : m, c), tauq[c]; right reflector c (c = 0 .. min(m, n-w)-1):
+ * beta on A(c, c+w), v in A(c, c+w+1 : n), taup[c].
+ * ncols >= 0 stops after that many (left, right) pairs.
+ * ---------------------------------------------------------------------------------*/
+int oracle_ge2bb(int64_t m, int64_t n, int64_t w, double *A, int64_t lda, double *tauq,
+                 double *taup, int64_t ncols) {
+    if (m < 0) return -1;
+    if (n < 0) return -2;
+    if (w < 1) return -3;
+    if (lda < (m > 1 ? m : 1)) return -5;
+    int64_t nlq = (m - w < n ? m - w : n), nrq = (n - w < m ? n - w : m);
+    if (nlq < 0) nlq = 0;
+    if (nrq < 0) nrq = 0;
+    for (int64_t c = 0; c < nlq; ++c) tauq[c] = 0.0;
+    for (int64_t c = 0; c < nrq; ++c) taup[c] = 0.0;
+    int64_t maxlen = m > n ? m : n;
+    double *v = (double *)malloc(sizeof(double) * (size_t)(maxlen + 1));
+    double *p = (double *)malloc(sizeof(double) * (size_t)(maxlen + 1));
+    if (!v || !p) { free(v); free(p); return -100; }
+    int64_t cmax = nlq > nrq ? nlq : nrq;
+    int64_t last = (ncols >= 0 && ncols < cmax) ? ncols : cmax;
+    for (int64_t c = 0; c < last; ++c) {
+        double t;
+        /* Left reflector on column c, rows c+w..m-1, applied to columns c+1..n-1. */
+        if (c < nlq) {
+            int64_t r0 = c + w, len = m - r0;
+            house(len, &AT(A, lda, r0, c), 1, &t);
+            tauq[c] = t;
+            if (t != 0.0) {
+                v[0] = 1.0;
+                for (int64_t i = 1; i < len; ++i) v[i] = AT(A, lda, r0 + i, c);
+                int64_t ncol = n - (c + 1);
+#pragma omp parallel for num_threads(oracle_threads) schedule(static) if (oracle_threads > 1)
+                for (int64_t jj = 0; jj < ncol; ++jj) {
+                    double *col = &AT(A, lda, r0, c + 1 + jj);
+                    double s = 0.0;
+                    for (int64_t i = 0; i < len; ++i) s += v[i] * col[i];
+                    s *= t;
+                    for (int64_t i = 0; i < len; ++i) col[i] -= s * v[i];
+                }
+            }
+        }
+        /* Right reflector on row c, columns c+w..n-1, applied to rows c+1..m-1. */
+        if (c < nrq) {
+            int64_t r0 = c + w, rlen = n - r0;
+            house(rlen, &AT(A, lda, c, r0), lda, &t);
+            taup[c] = t;
+            if (t != 0.0) {
+                v[0] = 1.0;
+                for (int64_t j = 1; j < rlen; ++j) v[j] = AT(A, lda, c, r0 + j);
+                int64_t nrow = m - (c + 1);
+                row_times_v(nrow, rlen, &AT(A, lda, c + 1, r0), lda, v, t, p);
+#pragma omp parallel for num_threads(oracle_threads) schedule(static) if (oracle_threads > 1)
+                for (int64_t jj = 0; jj < rlen; ++jj) {
+                    double *col = &AT(A, lda, c + 1, r0 + jj);
+                    double vj = v[jj];
+                    for (int64_t ii = 0; ii < nrow; ++ii) col[ii] -= p[ii] * vj;
+                }
+            }
+        }
+    }
+    free(v);
+    free(p);
+    return 0;
+}
+
+/* ---------------------------------------------------------------------------------
  * Eigenvalues of a small symmetric matrix by the cyclic Jacobi method (Golub & Van
  * Loan, "Matrices Computations", the symmetric Schur decomposition of 2x2 blocks
  * applied row by row until the off-diagonal norm is negligible).  Only the lower

@@ -219,3 +219,48 @@ def wide_report(A: np.ndarray, Aout: np.ndarray, tauq, taup, w: int) -> dict:
         "orth_p": np.linalg.norm(P.T @ P - np.eye(n)),
         "sv": np.max(np.abs(s_a - s_b)) / max(s_a[0], 1e-300) if m else 0.0,
     }
+
+
+def bb_band(Aout: np.ndarray, w: int) -> np.ndarray:
+    """Band |i-j| <= w of an m x n packed equal-bandwidth output."""
+    m, n = Aout.shape
+    i, j = np.indices((m, n))
+    return np.where(np.abs(i - j) <= w, Aout, 0.0)
+
+
+def bb_form_uv(Aout: np.ndarray, tauq: np.ndarray, taup: np.ndarray, w: int):
+    """U = Hq_0 Hq_1 ... (left reflector c on rows c+w.., v in column c below the band) and
+    V = Hp_0 Hp_1 ... (right reflector c on columns c+w.., v in row c right of the band)."""
+    m, n = Aout.shape
+    U = np.eye(m)
+    for c in range(len(tauq)):
+        t = tauq[c]
+        if t == 0.0:
+            continue
+        r0 = c + w
+        v = np.concatenate(([1.0], Aout[r0 + 1:, c]))
+        U[:, r0:] -= t * np.outer(U[:, r0:] @ v, v)
+    V = np.eye(n)
+    for c in range(len(taup)):
+        t = taup[c]
+        if t == 0.0:
+            continue
+        r0 = c + w
+        v = np.concatenate(([1.0], Aout[c, r0 + 1:]))
+        V[:, r0:] -= t * np.outer(V[:, r0:] @ v, v)
+    return U, V
+
+
+def bb_report(A: np.ndarray, Aout: np.ndarray, tauq, taup, w: int) -> dict:
+    B = bb_band(Aout, w)
+    U, V = bb_form_uv(Aout, tauq, taup, w)
+    m, n = A.shape
+    fa = np.linalg.norm(A)
+    s_a = np.linalg.svd(A, compute_uv=False)
+    s_b = np.linalg.svd(B, compute_uv=False)
+    return {
+        "backward": np.linalg.norm(A - U @ B @ V.T) / fa if fa else 0.0,
+        "orth_u": np.linalg.norm(U.T @ U - np.eye(m)),
+        "orth_v": np.linalg.norm(V.T @ V - np.eye(n)),
+        "sv": np.max(np.abs(s_a - s_b)) / max(s_a[0], 1e-300) if min(m, n) else 0.0,
+    }

@@ -356,3 +356,57 @@ def test_pins_catch_planted_mistakes_wide():
         else:
             Am[3, 5:] *= -1.0
         assert wide_report(A, Am, tqm, tpm, w)["backward"] > tol, mistake
+
+
+# --------------------------------------------------------------------------- equal bandwidth (Section 3.3)
+from checks import bb_band, bb_report  # noqa: E402
+
+
+@pytest.mark.parametrize("m,n,w", [(30, 24, 3), (24, 30, 3), (40, 40, 1), (50, 35, 8), (17, 60, 5), (33, 33, 32)])
+def test_ge2bb_invariants(m, n, w):
+    """A = U B V^T with |i-j| <= w on B: reconstruction through independently formed U and
+    V, orthogonality, band shape, and the singular values of A (LAPACK)."""
+    A = workloads.gen_gaussian(m, n, 400 + m + n + w)
+    Aout, tq, tp = oracle.ge2bb(A, w)
+    assert tq.shape == (max(min(n, m - w), 0),) and tp.shape == (max(min(m, n - w), 0),)
+    r = bb_report(A, Aout, tq, tp, w)
+    tol = 20 * max(m, n) * U64
+    assert r["backward"] < tol and r["orth_u"] < tol and r["orth_v"] < tol and r["sv"] < tol, r
+
+
+def test_ge2bb_w1_is_tridiagonal_with_the_singular_values_of_A():
+    m, n = 25, 18
+    A = workloads.gen_gaussian(m, n, 11)
+    Aout, tq, tp = oracle.ge2bb(A, 1)
+    B = bb_band(Aout, 1)
+    i, j = np.indices(B.shape)
+    assert np.all(B[np.abs(i - j) > 1] == 0.0)
+    np.testing.assert_allclose(np.sort(np.linalg.svd(B, compute_uv=False)), np.sort(oracle.jacobi_svd(A)),
+                               rtol=0, atol=1e-13 * np.linalg.norm(A))
+
+
+def test_ge2bb_hand_case_4x4_w2():
+    # the first left reflector acts on rows 2..3 of column 0: beta = -sign(a20) ||(a20, a30)||
+    A = np.array([[1.0, 2.0, 3.0, 4.0], [5.0, 6.0, 7.0, 8.0], [3.0, 1.0, 2.0, 5.0], [4.0, 9.0, 1.0, 2.0]])
+    Aout, tq, tp = oracle.ge2bb(A, 2)
+    assert Aout[2, 0] == pytest.approx(-5.0, rel=4 * U64)
+    assert tq[0] == pytest.approx(1.0 + 3.0 / 5.0, rel=4 * U64)
+    # column 0 above row 2 is untouched by it: the band keeps a00 and a10
+    assert Aout[0, 0] == 1.0 and Aout[1, 0] == 5.0
+
+
+def test_pins_catch_planted_mistakes_ge2bb():
+    m, n, w = 30, 26, 4
+    A = workloads.gen_gaussian(m, n, 29)
+    Aout, tq, tp = oracle.ge2bb(A, w)
+    tol = 20 * m * U64
+    assert bb_report(A, Aout, tq, tp, w)["backward"] < tol
+    for mistake in ("tauq_sign", "taup_drop", "vq_shift"):
+        Am, tqm, tpm = Aout.copy(), tq.copy(), tp.copy()
+        if mistake == "tauq_sign":
+            tqm[2] = -tqm[2]
+        elif mistake == "taup_drop":
+            tpm[3] = 0.0
+        else:
+            Am[w + 3:, 1] = np.roll(Am[w + 3:, 1], 1)
+        assert bb_report(A, Am, tqm, tpm, w)["backward"] > tol, mistake
