@@ -662,7 +662,8 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="sy2sb", choices=["sy2sb", "ge2gb", "sy2sb_large", "batched"],
+    ap.add_argument("--workload", default="sy2sb",
+                    choices=["sy2sb", "ge2gb", "sy2sb_large", "batched", "paper_sweep"],
                     help="sy2sb: n=8192 w=b=64 known spectrum (headline); ge2gb: 8192^2 w=64; "
                          "sy2sb_large: n=32768 w=b=128; batched: 1000 + 1000 uneven matrices")
     ap.add_argument("--n", type=int, default=None)
@@ -679,11 +680,14 @@ def main():
     ap.add_argument("--no-bf16x6-path", action="store_true", help="skip the bf16x6 comparison line")
     ap.add_argument("--no-extras", action="store_true", help="skip the compact ge2gb and batched records")
     ap.add_argument("--cmp-steps", type=int, default=3, help="timed steps of each comparison path")
+    ap.add_argument("--sweep-n", default="2500,5000,7500,10000", help="paper_sweep: orders n")
+    ap.add_argument("--sweep-w", default="32,64,128,256", help="paper_sweep: bandwidths w")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-cols", type=int, default=96, help="reflectors per reference-arm step")
     args = ap.parse_args()
     defaults = {"sy2sb": (8192, 64, 64), "ge2gb": (8192, 64, 64), "sy2sb_large": (32768, 128, 128),
+                "paper_sweep": (0, 0, 0),
                 "batched": (0, 0, 0)}[args.workload]
     args.n = args.n or defaults[0]
     args.w = args.w or defaults[1]
@@ -701,6 +705,11 @@ def main():
     br.build()
     br.lib()
     stream = torch.cuda.current_stream(dev)
+    if args.workload == "paper_sweep":
+        line = paper_sweep(args, br, dev, stream) if rank == 0 else None
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return 0
     if args.workload == "batched":
         line = bench_batched(args, br, dev, stream, world, rank, dist)
         if line is not None:
@@ -881,6 +890,61 @@ def main():
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def paper_sweep(args, br, dev, stream):
+    """The paper's experiment shape (Section 4.2): symmetric matrices with entries uniform in
+    (0, 1), n up to 10000, w in {32 .. 256}, b swept in steps of 16 up to w, with and without
+    look-ahead (the variant b and w allow), timed per configuration (median of 2 runs after
+    one warm-up) in the precision of --precision.  Reports TFLOP/s (4n^3/3) per point and the
+    best b per (n, w) with and without look-ahead."""
+    import torch
+
+    ns = [int(x) for x in args.sweep_n.split(",")]
+    ws = [int(x) for x in args.sweep_w.split(",")]
+    rows, best = [], {}
+    clocks = ClockSampler(dev.index or 0)
+    clocks.start()
+    clocks.mark_start()
+    for n in ns:
+        g = torch.Generator(device=dev)
+        g.manual_seed(n)
+        U = torch.rand((n, n), dtype=torch.float64, device=dev, generator=g)
+        A0 = ((U + U.t()) * 0.5).t().contiguous().t()
+        del U
+        A = torch.empty_like(A0)
+        for w in ws:
+            for b in range(16, w + 1, 16):
+                for la in (0, -1):
+                    o = br.make_opts(b=b, lookahead=la, precision=args.precision)
+                    tau = torch.zeros(max(n - w, 1), dtype=torch.float64, device=dev)
+                    work = torch.empty(br.bandred_sy2sb_workspace(n, w, o), dtype=torch.uint8, device=dev)
+                    st = torch.zeros(1, dtype=torch.int32, device=dev)
+                    ms = []
+                    for it in range(3):
+                        A.copy_(A0)
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        rc = br.bandred_sy2sb_ex(A, w, tau, o, work, st, stream)
+                        e1.record(stream)
+                        torch.cuda.synchronize(dev)
+                        if rc != 0 or int(st.item()) != 0:
+                            raise br.BandredError(rc or int(st.item()), f"paper_sweep n={n} w={w} b={b}")
+                        if it:
+                            ms.append(e0.elapsed_time(e1))
+                    med = statistics.median(ms)
+                    tf = nominal_flops(n) / (med / 1e3) / 1e12
+                    rows.append([n, w, b, la, round(med, 3), round(tf, 3)])
+                    key = f"n{n}/w{w}/la{'auto' if la else 'none'}"
+                    if key not in best or tf > best[key][1]:
+                        best[key] = (b, round(tf, 3))
+        del A, A0
+        torch.cuda.empty_cache()
+    clocks.mark_end()
+    return {"metric": HEADLINE_METRIC, "workload": "paper_sweep", "unit": "TFLOP/s", "precision": args.precision,
+            "data": "synthetic uniform (0,1) symmetric, drawn on the device",
+            "columns": ["n", "w", "b", "lookahead", "ms", "tflops"], "rows": rows,
+            "best_b": {k: {"b": v[0], "tflops": v[1]} for k, v in best.items()}, "clocks": clocks.stop()}
 
 
 def compact_ge2gb(args, br, dev, stream):

@@ -199,6 +199,29 @@ int bandred_ge2gb_ex(int64_t m, int64_t n, int64_t w, double* A, int64_t lda, do
                      double* taup, const bandred_opts* opts, void* work, size_t work_bytes,
                      int* dev_status, cudaStream_t stream);
 
+/* ---------------------------------------------------------------- ge2bb -------------
+ * Reduction to a band with equal lower and upper bandwidth w, Section 3.3 (the SVD band
+ * form that admits look-ahead for any b <= w): A = U B V^T, any m, n.
+ *   A     device, m x n, lda >= max(1, m).  On exit the band |i - j| <= w holds B; left
+ *         reflector c (c = 0 .. min(n, m-w)-1) has beta on A(c+w, c) and v in
+ *         A(c+w+1 : m, c); right reflector c (c = 0 .. min(m, n-w)-1) has beta on A(c, c+w)
+ *         and v in A(c, c+w+1 : n).
+ *   tauq  device, max(min(n, m-w), 0) entries: U = Hq_0 Hq_1 ..., Hq_c on rows c+w .. m-1.
+ *   taup  device, max(min(m, n-w), 0) entries: V = Hp_0 Hp_1 ..., Hp_c on columns c+w .. n-1.
+ * Per block of b columns and rows: the QR of the column panel and the LQ of the row panel
+ * (independent of each other), the one-sided updates of the blocks between the panels and
+ * the trailing block, and the trailing block D := Q_L^T D Q_R as one two-sided update
+ * D += X Y_R^T + Y_L Z_L^T (Eq. gebrd_2k), with the products in the chosen precision.
+ * opts->lookahead: 0 none; otherwise the next iteration's two panels are factored on a
+ * second stream, Variant V1 (2b <= w: they lie in B1 and C1, reached by one-sided updates)
+ * or V2 (2b > w: after the products of D, the first 2b - w columns and rows of D are
+ * updated first, the 2 x 2 partition of D); -1 picks by b and w.  work, dev_status,
+ * return codes: as for bandred_ge2gb_ex.
+ */
+size_t bandred_ge2bb_workspace(int64_t m, int64_t n, int64_t w, const bandred_opts* opts);
+int bandred_ge2bb_ex(int64_t m, int64_t n, int64_t w, double* A, int64_t lda, double* tauq, double* taup,
+                     const bandred_opts* opts, void* work, size_t work_bytes, int* dev_status, cudaStream_t stream);
+
 /* ---------------------------------------------------------------- forming Q, U, V ---
  * The orthogonal factors of a finished reduction, formed on the GPU from the packed
  * reflectors (the step that eigenvector and singular-vector solvers take after the band
@@ -220,6 +243,10 @@ int bandred_sy2sb_form_q(int64_t n, int64_t w, const double* A, int64_t lda, con
                          int64_t ldq, const bandred_opts* opts, void* work, size_t work_bytes, int* dev_status,
                          cudaStream_t stream);
 int bandred_ge2gb_form(int64_t m, int64_t n, int64_t w, const double* A, int64_t lda, const double* tau, int side,
+                       double* Q, int64_t ldq, const bandred_opts* opts, void* work, size_t work_bytes,
+                       int* dev_status, cudaStream_t stream);
+/*   bandred_ge2bb_form:   side 0: U (N = m), side 1: V (N = n) of a finished ge2bb. */
+int bandred_ge2bb_form(int64_t m, int64_t n, int64_t w, const double* A, int64_t lda, const double* tau, int side,
                        double* Q, int64_t ldq, const bandred_opts* opts, void* work, size_t work_bytes,
                        int* dev_status, cudaStream_t stream);
 

@@ -149,6 +149,12 @@ def lib():
         L.bandred_sy2sb_form_q.restype = ci
         L.bandred_ge2gb_form.argtypes = [i64, i64, i64, vp, i64, vp, ci, vp, i64, op, vp, sz, vp, vp]
         L.bandred_ge2gb_form.restype = ci
+        L.bandred_ge2bb_workspace.argtypes = [i64, i64, i64, op]
+        L.bandred_ge2bb_workspace.restype = sz
+        L.bandred_ge2bb_ex.argtypes = [i64, i64, i64, vp, i64, vp, vp, op, vp, sz, vp, vp]
+        L.bandred_ge2bb_ex.restype = ci
+        L.bandred_ge2bb_form.argtypes = [i64, i64, i64, vp, i64, vp, ci, vp, i64, op, vp, sz, vp, vp]
+        L.bandred_ge2bb_form.restype = ci
         L.bandred_newton_eval.argtypes = [i64, vp, vp, vp, vp]
         L.bandred_newton_eval.restype = ci
         L.bandred_fp64_probe.argtypes = [ci, ci, ci, vp, vp]
@@ -455,6 +461,42 @@ def ge2gb_form(A, w: int, tau, side: int, opts: bandred_opts | None = None, stre
                                   ctypes.byref(opts), _ptr(work), work.numel(), _ptr(status), _stream(stream))
     if rc != 0:
         raise BandredError(rc, "bandred_ge2gb_form")
+    return Q, status
+
+
+def ge2bb(A, w: int, opts: bandred_opts | None = None, stream=None, check: bool = True):
+    """In-place reduction of the column-major CUDA tensor A (m x n) to the band with lower
+    and upper bandwidth w (Section 3.3).  Returns (A, tauq, taup, dev_status)."""
+    import torch
+
+    m, n = A.shape
+    opts = make_opts() if opts is None else opts
+    tauq = torch.zeros(max(min(n, m - w), 0), dtype=torch.float64, device=A.device)
+    taup = torch.zeros(max(min(m, n - w), 0), dtype=torch.float64, device=A.device)
+    work = torch.empty(max(lib().bandred_ge2bb_workspace(m, n, w, ctypes.byref(opts)), 256), dtype=torch.uint8,
+                       device=A.device)
+    status = torch.zeros(1, dtype=torch.int32, device=A.device)
+    rc = lib().bandred_ge2bb_ex(m, n, w, _ptr(A), _lda(A), _ptr(tauq), _ptr(taup), ctypes.byref(opts), _ptr(work),
+                                work.numel(), _ptr(status), _stream(stream))
+    if rc != 0:
+        raise BandredError(rc, "bandred_ge2bb_ex")
+    if check:
+        st = int(status.item())
+        if st != 0:
+            raise BandredError(st, "bandred_ge2bb_ex (device)")
+    return A, tauq, taup, status
+
+
+def ge2bb_form(A, w: int, tau, side: int, opts: bandred_opts | None = None, stream=None):
+    """side 0: U (m x m), side 1: V (n x n) of a finished ge2bb."""
+    m, n = A.shape
+    N = m if side == 0 else n
+    opts = make_opts() if opts is None else opts
+    Q, work, status = _form_buffers(N, opts, A.device)
+    rc = lib().bandred_ge2bb_form(m, n, w, _ptr(A), _lda(A), _ptr(tau), side, _ptr(Q), Q.stride(1),
+                                  ctypes.byref(opts), _ptr(work), work.numel(), _ptr(status), _stream(stream))
+    if rc != 0:
+        raise BandredError(rc, "bandred_ge2bb_form")
     return Q, status
 
 

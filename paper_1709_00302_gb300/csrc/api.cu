@@ -215,4 +215,44 @@ int bandred_ge2gb_form(int64_t m, int64_t n, int64_t w, const double* A, int64_t
                    work, work_bytes, dev_status, stream);
 }
 
+size_t bandred_ge2bb_workspace(int64_t m, int64_t n, int64_t w, const bandred_opts* opts) {
+  Options o;
+  if (m < 0 || n < 0 || w < 1 || bandred::resolve_options(opts, w, &o) != 0) return 0;
+  return bandred::ge2bb_workspace_bytes(m, n, w, o);
+}
+
+int bandred_ge2bb_ex(int64_t m, int64_t n, int64_t w, double* A, int64_t lda, double* tauq, double* taup,
+                     const bandred_opts* opts, void* work, size_t work_bytes, int* dev_status, cudaStream_t stream) {
+  if (m < 0) return -1;
+  if (n < 0) return -2;
+  if (w < 1) return -3;
+  if (m > 0 && n > 0 && !A) return -4;
+  if (lda < std::max<int64_t>(1, m)) return -5;
+  const int64_t nlq = std::max<int64_t>(0, std::min(n, m - w)), nrq = std::max<int64_t>(0, std::min(m, n - w));
+  if (nlq > 0 && !tauq) return -6;
+  if (nrq > 0 && !taup) return -7;
+  if (std::max(m, n) > INT32_MAX / 2) return BANDRED_ERR_UNSUPPORTED;
+  Options o;
+  if (bandred::resolve_options(opts, w, &o) != 0) return -8;
+  if (!work || !aligned(work)) return -9;
+  if (work_bytes < bandred::ge2bb_workspace_bytes(m, n, w, o)) return -10;
+  bandred::DeviceGuard dg;
+  if (m > 0 && n > 0 && !dg.select(A)) return -4;
+  return bandred::ge2bb_run(m, n, w, A, lda, tauq, taup, o, work, dev_status, stream);
+}
+
+int bandred_ge2bb_form(int64_t m, int64_t n, int64_t w, const double* A, int64_t lda, const double* tau, int side,
+                       double* Q, int64_t ldq, const bandred_opts* opts, void* work, size_t work_bytes,
+                       int* dev_status, cudaStream_t stream) {
+  if (m < 0) return -1;
+  if (n < 0 || w < 1) return -2;
+  if (side != 0 && side != 1) return -5;
+  if (side == 0)  // U: reflector c acts on rows c+w .., v in column c below the band
+    return form_call(m, std::max<int64_t>(0, std::min(n, m - w)), w, A, lda, m, 1, lda, tau, Q, ldq, opts, work,
+                     work_bytes, dev_status, stream);
+  // V: reflector c acts on columns c+w .., v in row c right of the band
+  return form_call(n, std::max<int64_t>(0, std::min(m, n - w)), w, A, lda, m, lda, 1, tau, Q, ldq, opts, work,
+                   work_bytes, dev_status, stream);
+}
+
 }  // extern "C"

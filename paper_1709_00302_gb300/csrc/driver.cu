@@ -133,8 +133,17 @@ int resolve_options(const bandred_opts* in, int64_t w, Options* o) {
 
 // Workspace of sy2sb (layout shared by sizing and carving).  Y and W are double-buffered:
 // with look-ahead the next panel writes one pair while the current update reads the other.
+// W of an Ozaki-precision panel as one tensor-core product W = Y Tn (Tn = -T from the
+// panel's Gram coefficients), instead of the FP64 forward substitution.
+struct PanelW {
+  double* Tn;    // bk x bk
+  char* oz;      // Ozaki buffers of a j x bk x bk product
+  size_t oz_cap;
+};
+
 struct Sy2sbWs {
   double *Y[3], *W[3], *X, *X2;
+  PanelW pw;
   double *Z[2], *splitk[2];  // FP64 small products; [1] belongs to the panel stream
   double *part, *rowbuf, *gram;
   GridSync* gs;
@@ -146,6 +155,8 @@ struct Sy2sbWs {
   // packed operands of the rank-2k update
   char *ozp, *ozr;
   size_t ozp_cap;
+  int* weB;                // W's exponents and digits as the right operand of X1 = A2 W, kept
+  __nv_bfloat16* wblobz;   // for X2 = X1^T W / 2 (the same right operand)
   int64_t ld;
   size_t splitk_cap;
   int* status;
@@ -211,6 +222,11 @@ static Sy2sbWs carve_sy2sb(void* work, int64_t n, int64_t w, const Options& o, i
     ws.ozp_cap = ozaki::bytes(J, B, J, ozaki::choose_splits(J, B, J, sms));
     ws.ozp = c.take<char>(ws.ozp_cap);
     ws.ozr = c.take<char>(ozaki::bytes(J, J, 2 * B, 1, false));
+    ws.pw.Tn = c.take<double>((size_t)B * B);
+    ws.pw.oz_cap = ozaki::bytes(J, B, B, 1);
+    ws.pw.oz = c.take<char>(ws.pw.oz_cap);
+    ws.weB = c.take<int>((size_t)B);
+    ws.wblobz = c.take<__nv_bfloat16>(ozaki::packed_bytes(B, J, ozaki::kTileB) / 2);
   }
   ws.status = c.take<int>(1);  // last piece: the short forms read it at bytes - 256
   ws.bytes = c.off;
@@ -227,6 +243,9 @@ struct SplitBufs {
 
 struct Ge2gbWs {
   double *Yu[2], *Wu[2], *Yv[2], *Wv[2], *Z[2], *ZT, *MT, *P, *splitk[2], *part, *rowbuf, *gram;
+  double *ZT2, *P2;  // ge2bb: the panel stream's one-sided products (Variant V1)
+  PanelW pw;
+  int* sh;           // ge2bb: exponent balance of the two-sided update's operands
   GridSync* gs;
   SplitBufs sb[2];  // [0] caller's stream, [1] panel stream (look-ahead)
   char *ozp[2], *ozr[2];  // Ozaki-scheme buffers per stream (see Sy2sbWs)
@@ -237,7 +256,8 @@ struct Ge2gbWs {
   size_t bytes;
 };
 
-static Ge2gbWs carve_ge2gb(void* work, int64_t m, int64_t n, int64_t w, const Options& o, int sms) {
+static Ge2gbWs carve_ge2gb(void* work, int64_t m, int64_t n, int64_t w, const Options& o, int sms,
+                           bool bb = false) {
   Carver c{static_cast<char*>(work)};
   Ge2gbWs ws{};
   const int64_t b = o.b;
@@ -250,7 +270,7 @@ static Ge2gbWs carve_ge2gb(void* work, int64_t m, int64_t n, int64_t w, const Op
   }
   // row-panel Y/W: two pairs with the second look-ahead overlap (w >= 3b), which keeps the
   // previous row panel's reflectors while the next one is factored
-  const int nbv = (o.lookahead != 0 && 3 * b <= w) ? 2 : 1;
+  const int nbv = (o.lookahead != 0 && (bb || 3 * b <= w)) ? 2 : 1;
   for (int q = 0; q < 2; ++q) {
     ws.Yv[q] = q < nbv ? c.take<double>(ws.ldv * b) : ws.Yv[0];
     ws.Wv[q] = q < nbv ? c.take<double>(ws.ldv * b) : ws.Wv[0];
@@ -258,6 +278,11 @@ static Ge2gbWs carve_ge2gb(void* work, int64_t m, int64_t n, int64_t w, const Op
   ws.MT = c.take<double>((size_t)b * b);
   ws.ZT = c.take<double>(ws.ldv * b);
   ws.P = c.take<double>(ws.ldu * b);
+  if (bb) {
+    ws.ZT2 = o.lookahead != 0 ? c.take<double>(ws.ldv * b) : ws.ZT;
+    ws.P2 = o.lookahead != 0 ? c.take<double>(ws.ldu * b) : ws.P;
+    ws.sh = c.take<int>(2);
+  }
   ws.splitk_cap = (size_t)kSmallSplits * b * b * 4;
   for (int q = 0; q < 2; ++q) {
     ws.Z[q] = q < nbuf ? c.take<double>(b * ws.ldv) : ws.Z[0];
@@ -285,9 +310,12 @@ static Ge2gbWs carve_ge2gb(void* work, int64_t m, int64_t n, int64_t w, const Op
   if (o.precision == BANDRED_OZAKI) {
     const int big = (int)std::max(ws.ldu, ws.ldv), B = (int)b;
     ws.ozp_cap = ozaki::bytes(big, B, big, ozaki::choose_splits(big, B, big, sms));
+    ws.pw.Tn = c.take<double>((size_t)B * B);
+    ws.pw.oz_cap = ozaki::bytes(big, B, B, 1);
+    ws.pw.oz = c.take<char>(ws.pw.oz_cap);
     for (int q = 0; q < nbuf; ++q) {
       ws.ozp[q] = c.take<char>(ws.ozp_cap);
-      ws.ozr[q] = c.take<char>(ozaki::bytes(big, big, B, 1, false));
+      ws.ozr[q] = c.take<char>(ozaki::bytes(big, big, bb ? 2 * B : B, 1, false));  // ge2bb: rank br + bl
     }
     if (nbuf == 1) {
       ws.ozp[1] = ws.ozp[0];
@@ -313,9 +341,28 @@ static int current_sms() {
 
 // One panel factorisation: QR of the j x bk panel at `A` (rs = 1, cs = lda) or LQ of the
 // bk x j row panel (rs = lda, cs = 1).
+// W = -Y T of a panel factored in Gram mode: with the Ozaki precision Tn = -T (one small
+// kernel) and the product W = Y Tn on the tensor cores; otherwise the FP64 row-parallel
+// forward substitution.
+static int form_w(int j, int bk, const double* Y, double* W, int64_t ldy, const double* tau, const double* gram,
+                  const PanelW* pw, int* status, const Options& o, cudaStream_t s) {
+  if (pw && pw->Tn && o.precision == BANDRED_OZAKI) {
+    CK(launch_t_from_gram(bk, tau, gram, pw->Tn, s));
+    using ozaki::Operand;
+    const Operand a{Y, ldy, 0, bk, nullptr, 0, 0, 0, j}, t{pw->Tn, bk, 1, bk, nullptr, 0, 0, 0, bk};
+    const int sp = ozaki::fit_splits(j, bk, bk, 1, pw->oz_cap);
+    CK(ozaki::product(a, t, j, bk, bk, 1.0, 0.0, W, ldy, ozaki::carve(pw->oz, j, bk, bk, sp), sp, status, o.limit_ns,
+                      s));
+    return 0;
+  }
+  CK(launch_w_from_gram(j, bk, Y, tau, gram, W, ldy, s));
+  return 0;
+}
+
 static int run_panel(double* A, int64_t rs, int64_t cs, int j, int bk, double* tau, double* Y, double* W,
                      int64_t ldy, double* acc, double* rowbuf, double* gram, GridSync* gs, int* status,
-                     const Options& o, int max_ctas, unsigned int extra, cudaStream_t s) {
+                     const Options& o, int max_ctas, unsigned int extra, cudaStream_t s,
+                     const PanelW* pw = nullptr) {
   PanelParams p{};
   p.trace = prof::trace_take();
   // Short panels: one thread-block cluster (no grid-wide barrier, deterministic sums).
@@ -343,8 +390,7 @@ static int run_panel(double* A, int64_t rs, int64_t cs, int j, int bk, double* t
       if (!is_split(o) && bk <= 128) {  // FP64 W formed after the panel, as for the grid panel
         p.G = gram;
         CK(launch_panel_cluster(&p, nullptr, 1, C, p.Rp, bk, s));
-        CK(launch_w_from_gram(j, bk, Y, tau, gram, W, ldy, s));
-        return 0;
+        return form_w(j, bk, Y, W, ldy, tau, gram, pw, status, o, s);
       }
       CK(launch_panel_cluster(&p, nullptr, 1, C, p.Rp, bk, s));
       return 0;
@@ -389,8 +435,7 @@ static int run_panel(double* A, int64_t rs, int64_t cs, int j, int bk, double* t
     p.G = gram;
     p.w_in_smem = false;
     CK(launch_panel(p, G, s));
-    CK(launch_w_from_gram(j, bk, Y, tau, gram, W, ldy, s));
-    return 0;
+    return form_w(j, bk, Y, W, ldy, tau, gram, pw, status, o, s);
   }
   CK(launch_panel(p, G, s));
   return 0;
@@ -495,7 +540,7 @@ struct Sy2sb {
     prof::Scope sc(prof::kPanel, s, panel_flops(j, bk), panel_bytes(j, bk));
     prof::TraceScope tr(prof::kTracePanel, k);
     int rc = run_panel(A + r0 + k * lda, 1, lda, j, bk, tau + k, ws.Y[buf], ws.W[buf], ws.ld, ws.part, ws.rowbuf,
-                       ws.gram, ws.gs, status, o, ctas > 0 ? std::min(ctas, pmax) : pmax, extra, s);
+                       ws.gram, ws.gs, status, o, ctas > 0 ? std::min(ctas, pmax) : pmax, extra, s, &ws.pw);
     extra = 0;
     return rc;
   }
@@ -544,16 +589,24 @@ struct Sy2sb {
         // X1 = A2 W (A2 symmetric, lower stored; row (n, k) of the right operand is W(k, n))
         prof::Scope sc(prof::kSymm, s, symm_flops(j, bk), symm_bytes(j, bk));
         prof::TraceScope tr(prof::kTraceSymm, k);
+        // W's exponents and digits go to their own buffers, which X2 reads again
         const int sp = ozaki::fit_splits(j, B, j, ozaki::choose_splits(j, B, j, sms), ws.ozp_cap);
         const Operand a{A2, lda, 2, j, nullptr, 0, 0, 0, j}, w{W, ld, 1, j, nullptr, 0, 0, 0, B};
-        CK(ozaki::product(a, w, j, B, j, 1.0, 0.0, ws.X, ld, ozaki::carve(ws.ozp, j, B, j, sp), sp, status, lim, s));
+        ozaki::Bufs bx = ozaki::carve(ws.ozp, j, B, j, sp);
+        bx.eB = ws.weB;
+        bx.Bblob = ws.wblobz;
+        CK(ozaki::product(a, w, j, B, j, 1.0, 0.0, ws.X, ld, bx, sp, status, lim, s));
       }
       prof::Scope sc(prof::kGemm, s, 4.0 * j * bk * bk, 8.0 * 4.0 * j * bk);
       {
-        // X2 = X1^T W / 2
+        // X2 = X1^T W / 2, W packed by the X1 product
         const int sp = ozaki::fit_splits(B, B, j, ozaki::choose_splits(B, B, j, sms), ws.ozp_cap);
         const Operand x{ws.X, ld, 1, j, nullptr, 0, 0, 0, B}, w{W, ld, 1, j, nullptr, 0, 0, 0, B};
-        CK(ozaki::product(x, w, B, B, j, 0.5, 0.0, ws.X2, B, ozaki::carve(ws.ozp, B, B, j, sp), sp, status, lim, s));
+        ozaki::Bufs bx = ozaki::carve(ws.ozp, B, B, j, sp);
+        bx.eB = ws.weB;
+        bx.Bblob = ws.wblobz;
+        bx.b_packed = true;
+        CK(ozaki::product(x, w, B, B, j, 0.5, 0.0, ws.X2, B, bx, sp, status, lim, s));
       }
       {
         // X3 = X1 + Y X2
@@ -1019,14 +1072,15 @@ struct Ge2gb {
 
   int bk_of(int64_t k) const { return (int)std::min<int64_t>(o.b, n - k); }
 
-  // QR of B = A(k:m, k:k+bk) (Eq. updateB).
-  int left_panel(int64_t k, int buf, cudaStream_t s) {
+  // QR of B = A(k:m, k:k+bk) (Eq. updateB); ctas > 0 caps the panel's CTAs.
+  int left_panel(int64_t k, int buf, cudaStream_t s, int ctas = 0) {
     const int bk = bk_of(k);
     const int j = (int)(m - k);
     prof::Scope sc(prof::kPanel, s, panel_flops(j, bk), panel_bytes(j, bk));
     prof::TraceScope tr(prof::kTracePanel, k);
     int rc = run_panel(A + k + k * lda, 1, lda, j, bk, tauq + k, ws.Yu[buf], ws.Wu[buf], ws.ldu, ws.part,
-                       ws.rowbuf, ws.gram, ws.gs, status, o, pmax, extra, s);
+                       ws.rowbuf, ws.gram, ws.gs, status, o, ctas > 0 ? std::min(ctas, pmax) : pmax, extra, s,
+                       &ws.pw);
     extra = 0;
     return rc;
   }
@@ -1117,9 +1171,10 @@ struct Ge2gb {
     return split_product(M, N, K, As, lda, split::kModePlain, Bs, ldb, 1.0, 0.0, C, ldc, ws.sb[q], S, sms, status,
                          o.limit_ns, s);
   }
-  // C (M x N, ldc) += L R^T with L M x K (ldl) and R N x K (ldr).
+  // C (M x N, ldc) += L R^T with L M x K (ldl) and R N x K (ldr); max_ctas > 0 holds the
+  // Ozaki update to that many CTAs (SMs left to a panel on the other stream).
   int rank_k(int M, int N, int K, const double* L, int64_t ldl, const double* Rm, int64_t ldr, double* C, int64_t ldc,
-             int q, cudaStream_t s) {
+             int q, cudaStream_t s, int max_ctas = 0) {
     if (M <= 0 || N <= 0 || K <= 0) return 0;
     prof::Scope sc(prof::kRank, s, 2.0 * M * N * K, 8.0 * (2.0 * M * N + (double)(M + N) * K));
     if (o.precision == BANDRED_FP64) {
@@ -1131,14 +1186,15 @@ struct Ge2gb {
       const Operand l{L, ldl, 0, K, nullptr, 0, 0, 0, M}, r{Rm, ldr, 0, K, nullptr, 0, 0, 0, N};
       const ozaki::Bufs rb = ozaki::carve(ws.ozr[q], M, N, K, 1);
       CK(ozaki::prepare(l, r, rb, s));
-      CK(ozaki::rank_apply(M, N, K, 1.0, C, ldc, 0, N, 0, rb, status, o.limit_ns, s));
+      CK(ozaki::rank_apply(M, N, K, 1.0, C, ldc, 0, N, 0, rb, status, o.limit_ns, s, max_ctas));
       return 0;
     }
     return split_rank(M, N, K, L, ldl, Rm, ldr, C, ldc, ws.sb[q], S, status, o.limit_ns, s);
   }
 
-  // LQ of C = A(k:k+bkr, k+w:n) (Eq. updateC) into row-panel buffer bvi.
-  int right_panel(int64_t k, cudaStream_t s, int bvi = 0) {
+  // LQ of C = A(k:k+bkr, k+w:n) (Eq. updateC) into row-panel buffer bvi; ctas > 0 caps the
+  // panel's CTAs.
+  int right_panel(int64_t k, cudaStream_t s, int bvi = 0, int ctas = 0) {
     const int bk = bk_of(k);
     const int64_t bkr = std::min<int64_t>(bk, n - w - 1 - k);
     if (bkr <= 0) return 0;
@@ -1146,8 +1202,7 @@ struct Ge2gb {
     prof::Scope sc(prof::kPanel, s, panel_flops(jr, (int)bkr), panel_bytes(jr, (int)bkr));
     prof::TraceScope tr(prof::kTracePanelRow, k);
     return run_panel(A + k + (k + w) * lda, lda, 1, jr, (int)bkr, taup + k, ws.Yv[bvi], ws.Wv[bvi], ws.ldv, ws.part,
-                     ws.rowbuf,
-                     ws.gram, ws.gs, status, o, pmax, 0u, s);
+                     ws.rowbuf, ws.gram, ws.gs, status, o, ctas > 0 ? std::min(ctas, pmax) : pmax, 0u, s, &ws.pw);
   }
 
   // D = A(k+bkr:m, k+w:n) += (D W_V) Y_V^T (Eq. updateD), row panel from buffer bvi.
@@ -1206,9 +1261,9 @@ struct Ge2gb {
 // columns of E and is untouched by this iteration's right update, so the panel stream
 // updates those columns and factors the next panel while the caller's stream finishes
 // the left update; the row panel follows on the panel stream (panels never run
-// concurrently: they share their reduction scratch and each is a cooperative grid over
-// all SMs), then the right update on the caller's stream.  (The paper's second overlap,
-// which needs w >= 3b, is not used.)  With w < 2b the steps run in order.
+// concurrently: they share their reduction scratch), then the right update on the
+// caller's stream.  With w >= 3b (and lookahead -1 or 2) both overlaps of the paper's
+// third case run, below.  With w < 2b the steps run in order.
 int ge2gb_run(int64_t m, int64_t n, int64_t w, double* A, int64_t lda, double* tauq, double* taup,
               const Options& o, void* work, int* dev_status, cudaStream_t s) {
   if (n > m) {
@@ -1296,28 +1351,35 @@ int ge2gb_run(int64_t m, int64_t n, int64_t w, double* A, int64_t lda, double* t
       CK(cudaEventRecord(ev_e, s));
       CK(cudaStreamWaitEvent(sp, ev_e, 0));
       const int bkn = R.bk_of(k + b);
+      // With the Ozaki precision the panels hold P SMs and the caller's updates the others
+      // (the model of the look-ahead split, with the two rank-b updates of j rows as the
+      // update), so both streams run at once; other precisions take every SM.
+      const int P = o.precision == BANDRED_OZAKI
+                        ? lookahead_panel_ctas(std::max(jr, j - bk), b, j, 2 * b, R.sms, o.panel_ctas)
+                        : 0;
+      const int rest = P > 0 && P < R.sms ? R.sms - P : 0;
       // panel stream: row block k (rows k .. k+bk), then row panel k; the next column
       // panel's columns below the row block, then that panel
       if ((rc = R.rank_k(bk, nc, bk, R.ws.Yu[bu], R.ws.ldu, R.ws.ZT, R.ws.ldv, E, lda, 1, sp))) return rc;
       if (kprev >= 0 &&
           (rc = R.rank_k(bk, jr, b, R.ws.P, R.ws.ldu, R.ws.Yv[bvp], R.ws.ldv, A + k + (kprev + w) * lda, lda, 1, sp)))
         return rc;
-      if ((rc = R.right_panel(k, sp, bvp ^ 1))) return rc;
+      if ((rc = R.right_panel(k, sp, bvp ^ 1, P))) return rc;
       if ((rc = R.rank_k(j - bk, bkn, bk, R.ws.Yu[bu] + bk, R.ws.ldu, R.ws.ZT, R.ws.ldv, E + bk, lda, 1, sp)))
         return rc;
-      if ((rc = R.left_panel(k + b, bu ^ 1, sp))) return rc;
+      if ((rc = R.left_panel(k + b, bu ^ 1, sp, P))) return rc;
       CK(cudaEventRecord(ev_panel, sp));
       // caller's stream: the rest (rows below the row block, columns past the next panel)
       {
         prof::TraceScope tr(prof::kTraceLeft, k);
         if ((rc = R.rank_k(j - bk, nc - bkn, bk, R.ws.Yu[bu] + bk, R.ws.ldu, R.ws.ZT + bkn, R.ws.ldv,
-                           E + bk + (int64_t)bkn * lda, lda, 0, s)))
+                           E + bk + (int64_t)bkn * lda, lda, 0, s, rest)))
           return rc;
       }
       if (kprev >= 0) {
         prof::TraceScope tr(prof::kTraceRight, kprev);
         if ((rc = R.rank_k(j - bk, jr, b, R.ws.P + bk, R.ws.ldu, R.ws.Yv[bvp], R.ws.ldv,
-                           A + k + bk + (kprev + w) * lda, lda, 0, s)))
+                           A + k + bk + (kprev + w) * lda, lda, 0, s, rest)))
           return rc;
       }
       kprev = k;
@@ -1364,6 +1426,257 @@ int ge2gb_run(int64_t m, int64_t n, int64_t w, double* A, int64_t lda, double* t
   CK(cudaEventRecord(ev_fork, sp));
   CK(cudaStreamWaitEvent(s, ev_fork, 0));
   return 0;
+}
+
+// ---------------------------------------------------------------------------------
+// ge2bb: band with lower and upper bandwidth w, Section 3.3 (Eqs. updateB0 .. gebrd_2k).
+// Iteration k: QR of the column panel A(k+w:m, k:k+bl) and LQ of the row panel
+// A(k:k+br, k+w:n) (independent: the left reflectors act on rows >= k+w, the right ones on
+// columns >= k+w); the one-sided updates of B1 = A(k+w:m, k+bl:k+w) and
+// C1 = A(k+br:k+w, k+w:n); and D = A(k+w:m, k+w:n) := Q_L^T D Q_R written as one two-sided
+// update from products of D: Z_L = D^T W_L, Z_R = D W_R, X = Z_R + Y_L (Z_L^T W_R),
+// D += X Y_R^T + Y_L Z_L^T (Eq. gebrd_2k).
+//
+// Look-ahead (the panels of iteration k + b on a second stream):
+//   V1 (2b <= w): the next column panel lies in the first b columns of B1 and the next row
+//     panel in the first b rows of C1, which only one-sided updates reach.  The panel stream
+//     updates those columns and rows and factors both panels while the caller's stream
+//     updates the rest of B1 and C1 and all of D.
+//   V2 (2b > w): with t = 2b - w, the next panels lie in B1, C1 and the first t columns and
+//     first t rows of D.  After the products of D, the panel stream applies the two-sided
+//     update to D(:, 0:t) and D(0:t, t:) and factors both panels, while the caller's
+//     stream updates D(t:, t:), the 2 x 2 partition of D.
+namespace {
+
+struct Ge2bb {
+  Ge2gb R;  // precision-dispatched products and panels of the ge2gb driver
+  int64_t m, n, w, nlq, nrq;
+  int b;
+
+  int bl_of(int64_t k) const { return (int)std::max<int64_t>(0, std::min<int64_t>(b, nlq - k)); }
+  int br_of(int64_t k) const { return (int)std::max<int64_t>(0, std::min<int64_t>(b, nrq - k)); }
+  int jl_of(int64_t k) const { return (int)(m - k - w); }
+  int jr_of(int64_t k) const { return (int)(n - k - w); }
+  bool lq(int64_t k) const { return bl_of(k) > 0 && jl_of(k) >= 2; }
+  bool rq(int64_t k) const { return br_of(k) > 0 && jr_of(k) >= 2; }
+
+  // QR of the column panel and LQ of the row panel of iteration k into buffer q.
+  int panels(int64_t k, int q, cudaStream_t s) {
+    Ge2gbWs& ws = R.ws;
+    int rc;
+    if (lq(k)) {
+      const int jl = jl_of(k), bl = bl_of(k);
+      prof::Scope sc(prof::kPanel, s, panel_flops(jl, bl), panel_bytes(jl, bl));
+      prof::TraceScope tr(prof::kTracePanel, k);
+      if ((rc = run_panel(R.A + (k + w) + k * R.lda, 1, R.lda, jl, bl, R.tauq + k, ws.Yu[q], ws.Wu[q], ws.ldu, ws.part,
+                          ws.rowbuf, ws.gram, ws.gs, R.status, R.o, R.pmax, 0u, s, &ws.pw)))
+        return rc;
+    }
+    if (rq(k)) {
+      const int jr = jr_of(k), br = br_of(k);
+      prof::Scope sc(prof::kPanel, s, panel_flops(jr, br), panel_bytes(jr, br));
+      prof::TraceScope tr(prof::kTracePanelRow, k);
+      if ((rc = run_panel(R.A + k + (k + w) * R.lda, R.lda, 1, jr, br, R.taup + k, ws.Yv[q], ws.Wv[q], ws.ldv, ws.part,
+                          ws.rowbuf, ws.gram, ws.gs, R.status, R.o, R.pmax, 0u, s, &ws.pw)))
+        return rc;
+    }
+    return 0;
+  }
+
+  // B1 columns [c0, c1) += Y_L (W_L^T B1) (Eq. updateB1), products into Z (ldz = ldv).
+  int b1_update(int64_t k, int q, int c0, int c1, double* Z, int qs, cudaStream_t s) {
+    if (!lq(k)) return 0;
+    const int bl = bl_of(k), jl = jl_of(k);
+    c1 = std::min<int>(c1, (int)std::min<int64_t>(w - bl, n - k - bl));
+    if (c1 <= c0) return 0;
+    double* B1 = R.A + (k + w) + (k + bl + c0) * R.lda;
+    int rc;
+    if ((rc = R.prod_t(c1 - c0, bl, jl, B1, R.lda, R.ws.Wu[q], R.ws.ldu, Z, R.ws.ldv, qs, s))) return rc;
+    return R.rank_k(jl, c1 - c0, bl, R.ws.Yu[q], R.ws.ldu, Z, R.ws.ldv, B1, R.lda, qs, s);
+  }
+
+  // C1 rows [r0, r1) += (C1 W_R) Y_R^T (Eq. updateC1), products into P (ldp = ldu).
+  int c1_update(int64_t k, int q, int r0, int r1, double* P, int qs, cudaStream_t s) {
+    if (!rq(k)) return 0;
+    const int br = br_of(k), jr = jr_of(k);
+    r1 = std::min<int>(r1, (int)std::min<int64_t>(w - br, m - k - br));
+    if (r1 <= r0) return 0;
+    double* C1 = R.A + (k + br + r0) + (k + w) * R.lda;
+    int rc;
+    if ((rc = R.prod_n(r1 - r0, br, jr, C1, R.lda, R.ws.Wv[q], R.ws.ldv, P, R.ws.ldu, qs, s))) return rc;
+    return R.rank_k(r1 - r0, jr, br, P, R.ws.ldu, R.ws.Yv[q], R.ws.ldv, C1, R.lda, qs, s);
+  }
+
+  // Products of D for the two-sided update: Z_L = D^T W_L (ZT), X = D W_R + Y_L (Z_L^T W_R) (P).
+  int d_products(int64_t k, int q, cudaStream_t s) {
+    const int bl = bl_of(k), br = br_of(k), jl = jl_of(k), jr = jr_of(k);
+    const bool l = lq(k), r = rq(k);
+    if (jl < 1 || jr < 1 || !(l || r)) return 0;
+    Ge2gbWs& ws = R.ws;
+    const double* D = R.A + (k + w) + (k + w) * R.lda;
+    int rc;
+    if (l && (rc = R.prod_t(jr, bl, jl, D, R.lda, ws.Wu[q], ws.ldu, ws.ZT, ws.ldv, 0, s))) return rc;
+    if (r) {
+      if ((rc = R.prod_n(jl, br, jr, D, R.lda, ws.Wv[q], ws.ldv, ws.P, ws.ldu, 0, s))) return rc;
+      if (l) {
+        // S^T = W_R^T Z_L (br x bl), then X = Z_R + Y_L S
+        if ((rc = R.prod_t(br, bl, jr, ws.Wv[q], ws.ldv, ws.ZT, ws.ldv, ws.MT, br, 0, s))) return rc;
+        if ((rc = R.rank_k(jl, br, bl, ws.Yu[q], ws.ldu, ws.MT, br, ws.P, ws.ldu, 0, s))) return rc;
+      }
+    }
+    return 0;
+  }
+
+  // D(r0:r1, c0:c1) += X Y_R^T + Y_L Z_L^T on those rows and columns (Eq. gebrd_2k).  With
+  // the Ozaki precision one rank-(br + bl) update of [X | Y_L] and [Y_R | Z_L], balanced by a
+  // power of two between the halves (X and Z_L carry the matrix's scale, |Y| <= 1).
+  int d_rank(int64_t k, int q, int r0, int r1, int c0, int c1, int qs, cudaStream_t s) {
+    const int bl = bl_of(k), br = br_of(k), jl = jl_of(k), jr = jr_of(k);
+    const bool l = lq(k), r = rq(k);
+    r1 = std::min(r1, jl);
+    c1 = std::min(c1, jr);
+    if (r1 <= r0 || c1 <= c0 || !(l || r)) return 0;
+    Ge2gbWs& ws = R.ws;
+    double* D = R.A + (k + w + r0) + (k + w + c0) * R.lda;
+    const int M = r1 - r0, N = c1 - c0;
+    if (R.o.precision == BANDRED_OZAKI && l && r) {
+      using ozaki::Operand;
+      prof::Scope sc(prof::kRank, s, 2.0 * M * N * (bl + br), 8.0 * (2.0 * M * N + (double)(M + N) * (bl + br)));
+      Operand lo{ws.P + r0, ws.ldu, 0, br, ws.Yu[q] + r0, ws.ldu, 0, bl, M};
+      Operand ro{ws.Yv[q] + c0, ws.ldv, 0, br, ws.ZT + c0, ws.ldv, 0, bl, N};
+      int* sh = ws.sh + 0;
+      // one balance per iteration serves every block of D (the exponents of the full X, Y_L)
+      lo.sh = ro.sh = sh;
+      lo.shsign = 1;
+      ro.shsign = -1;
+      const ozaki::Bufs rb = ozaki::carve(ws.ozr[qs], M, N, br + bl, 1);
+      CK(ozaki::prepare(lo, ro, rb, s));
+      CK(ozaki::rank_apply(M, N, br + bl, 1.0, D, R.lda, 0, N, 0, rb, R.status, R.o.limit_ns, s));
+      return 0;
+    }
+    int rc;
+    if (r && (rc = R.rank_k(M, N, br, ws.P + r0, ws.ldu, ws.Yv[q] + c0, ws.ldv, D, R.lda, qs, s))) return rc;
+    if (l && (rc = R.rank_k(M, N, bl, ws.Yu[q] + r0, ws.ldu, ws.ZT + c0, ws.ldv, D, R.lda, qs, s))) return rc;
+    return 0;
+  }
+
+  // The balance exponents of [X | Y_L] over all of D's rows (before any block of d_rank).
+  int d_balance(int64_t k, int q, cudaStream_t s) {
+    if (R.o.precision != BANDRED_OZAKI || !lq(k) || !rq(k) || jl_of(k) < 1 || jr_of(k) < 1) return 0;
+    Ge2gbWs& ws = R.ws;
+    const ozaki::Operand lo{ws.P, ws.ldu, 0, br_of(k), ws.Yu[q], ws.ldu, 0, bl_of(k), jl_of(k)};
+    CK(ozaki::balance(lo, ws.sh, s));
+    return 0;
+  }
+};
+
+}  // namespace
+
+static int ge2bb_variant(const Options& o, int64_t w) {
+  int la = o.lookahead;
+  if (la < 0) la = (2 * o.b > w) ? 2 : 1;
+  if (la == 1 && 2 * o.b > w) la = 2;
+  if (la == 2 && 2 * o.b <= w) la = 1;
+  return la;
+}
+
+int ge2bb_run(int64_t m, int64_t n, int64_t w, double* A, int64_t lda, double* tauq, double* taup, const Options& o,
+              void* work, int* dev_status, cudaStream_t s) {
+  Ge2bb G{};
+  Ge2gb& R = G.R;
+  R.m = m;
+  R.n = n;
+  R.w = w;
+  R.A = A;
+  R.lda = lda;
+  R.tauq = tauq;
+  R.taup = taup;
+  R.o = o;
+  R.sms = current_sms();
+  R.ws = carve_ge2gb(work, std::max(m, n), std::max(m, n), w, o, R.sms, true);
+  R.status = dev_status ? dev_status : R.ws.status;
+  R.pmax = panel_max_ctas(R.sms, o);
+  R.S = is_split(o) ? split::slices_of(o.precision) : 0;
+  R.extra = 0;
+  G.m = m;
+  G.n = n;
+  G.w = w;
+  G.b = o.b;
+  G.nlq = std::max<int64_t>(0, std::min(n, m - w));
+  G.nrq = std::max<int64_t>(0, std::min(m, n - w));
+  CK(cudaMemsetAsync(R.status, 0, sizeof(int), s));
+  if (G.nlq > 0) CK(cudaMemsetAsync(tauq, 0, sizeof(double) * G.nlq, s));
+  if (G.nrq > 0) CK(cudaMemsetAsync(taup, 0, sizeof(double) * G.nrq, s));
+  const int b = o.b;
+  const int64_t kend = std::max(G.nlq, G.nrq);
+  const int la = o.lookahead == 0 ? 0 : ge2bb_variant(o, w);
+  int rc;
+  if (la == 0 || kend <= b) {
+    for (int64_t k = 0; k < kend; k += b) {
+      if ((rc = G.panels(k, 0, s))) return rc;
+      if ((rc = G.b1_update(k, 0, 0, (int)w, R.ws.ZT, 0, s))) return rc;
+      if ((rc = G.c1_update(k, 0, 0, (int)w, R.ws.P, 0, s))) return rc;
+      if ((rc = G.d_products(k, 0, s))) return rc;
+      if ((rc = G.d_balance(k, 0, s))) return rc;
+      if ((rc = G.d_rank(k, 0, 0, (int)m, 0, (int)n, 0, s))) return rc;
+    }
+    return 0;
+  }
+  AuxStreams* ax = nullptr;
+  if ((rc = aux_streams(&ax))) return rc;
+  cudaStream_t sp = ax->panel;
+  cudaEvent_t ev_fork = ax->ev[0], ev_panel = ax->ev[1];
+  CK(cudaEventRecord(ev_fork, s));
+  CK(cudaStreamWaitEvent(sp, ev_fork, 0));
+  if ((rc = G.panels(0, 0, sp))) return rc;
+  CK(cudaEventRecord(ev_panel, sp));
+  int buf = 0;
+  for (int64_t k = 0; k < kend; k += b, buf ^= 1) {
+    const int64_t kn = k + b;
+    const bool has_next = kn < kend;
+    CK(cudaStreamWaitEvent(s, ev_panel, 0));  // the panels of iteration k are factored
+    if (la == 1) {
+      if (has_next) {
+        CK(cudaEventRecord(ev_fork, s));  // iteration k - b's update is complete
+        CK(cudaStreamWaitEvent(sp, ev_fork, 0));
+        if ((rc = G.b1_update(k, buf, 0, b, R.ws.ZT2, 1, sp))) return rc;
+        if ((rc = G.c1_update(k, buf, 0, b, R.ws.P2, 1, sp))) return rc;
+        if ((rc = G.panels(kn, buf ^ 1, sp))) return rc;
+        CK(cudaEventRecord(ev_panel, sp));
+      }
+      const int rest = has_next ? b : 0;
+      if ((rc = G.b1_update(k, buf, rest, (int)w, R.ws.ZT, 0, s))) return rc;
+      if ((rc = G.c1_update(k, buf, rest, (int)w, R.ws.P, 0, s))) return rc;
+      if ((rc = G.d_products(k, buf, s))) return rc;
+      if ((rc = G.d_balance(k, buf, s))) return rc;
+      if ((rc = G.d_rank(k, buf, 0, (int)m, 0, (int)n, 0, s))) return rc;
+      continue;
+    }
+    // V2
+    if ((rc = G.b1_update(k, buf, 0, (int)w, R.ws.ZT2, 0, s))) return rc;
+    if ((rc = G.c1_update(k, buf, 0, (int)w, R.ws.P2, 0, s))) return rc;
+    if ((rc = G.d_products(k, buf, s))) return rc;
+    if ((rc = G.d_balance(k, buf, s))) return rc;
+    if (!has_next) {
+      if ((rc = G.d_rank(k, buf, 0, (int)m, 0, (int)n, 0, s))) return rc;
+      continue;
+    }
+    const int t = (int)(2 * b - w);
+    CK(cudaEventRecord(ev_fork, s));
+    CK(cudaStreamWaitEvent(sp, ev_fork, 0));
+    if ((rc = G.d_rank(k, buf, 0, (int)m, 0, t, 1, sp))) return rc;  // D(:, 0:t)
+    if ((rc = G.d_rank(k, buf, 0, t, t, (int)n, 1, sp))) return rc;  // D(0:t, t:)
+    if ((rc = G.panels(kn, buf ^ 1, sp))) return rc;
+    CK(cudaEventRecord(ev_panel, sp));
+    if ((rc = G.d_rank(k, buf, t, (int)m, t, (int)n, 0, s))) return rc;  // D(t:, t:)
+  }
+  CK(cudaEventRecord(ev_fork, sp));
+  CK(cudaStreamWaitEvent(s, ev_fork, 0));
+  return 0;
+}
+
+size_t ge2bb_workspace_bytes(int64_t m, int64_t n, int64_t w, const Options& o) {
+  return carve_ge2gb(nullptr, std::max(m, n), std::max(m, n), w, o, current_sms(), true).bytes;
 }
 
 size_t ge2gb_workspace_bytes(int64_t m, int64_t n, int64_t w, const Options& o) {

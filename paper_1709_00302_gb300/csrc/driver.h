@@ -70,6 +70,9 @@ int sy2sb_run(int64_t n, int64_t w, double* A, int64_t lda, double* tau, const O
               int* dev_status, cudaStream_t s);
 
 size_t ge2gb_workspace_bytes(int64_t m, int64_t n, int64_t w, const Options& o);
+size_t ge2bb_workspace_bytes(int64_t m, int64_t n, int64_t w, const Options& o);
+int ge2bb_run(int64_t m, int64_t n, int64_t w, double* A, int64_t lda, double* tauq, double* taup, const Options& o,
+              void* work, int* dev_status, cudaStream_t s);
 int ge2gb_run(int64_t m, int64_t n, int64_t w, double* A, int64_t lda, double* tauq, double* taup,
               const Options& o, void* work, int* dev_status, cudaStream_t s);
 

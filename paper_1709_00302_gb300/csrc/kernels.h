@@ -39,6 +39,10 @@ struct PanelParams {
 cudaError_t launch_w_from_gram(int j, int bk, const double* Y, const double* tau, const double* G, double* W,
                                int64_t ldy, cudaStream_t s);
 
+// Tn = -T (bk x bk, ld bk, zero below the diagonal) of a factored panel from the same Gram
+// coefficients and tau (bk <= 128): W = -Y T = Y Tn is then one product of Y and Tn.
+cudaError_t launch_t_from_gram(int bk, const double* tau, const double* G, double* Tn, cudaStream_t s);
+
 size_t panel_smem_bytes(int bk, int Rp, bool w_in_smem);
 size_t panel_sync_bytes(int bk);  // bytes from gs to the end of acc
 int panel_geometry(int j, int bk, int max_ctas, int min_rows, int* G, int* R, int* Rp, bool* w_in_smem);

@@ -67,6 +67,17 @@ __global__ void zero_kernel(int* e, int n) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) e[i] = 0;
 }
 
+// e1[0 .. n1) = 0 and e2[0 .. n2) = 0 in one launch (both operands' exponent arrays)
+__global__ void zero2_kernel(int* e1, int n1, int* e2, int n2) {
+  pdl_wait_and_release();
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n1 + n2; i += gridDim.x * blockDim.x) {
+    if (i < n1)
+      e1[i] = 0;
+    else
+      e2[i - n1] = 0;
+  }
+}
+
 // entries M[r + k ld]: one 32 x 32 tile per block (lanes along rows, eight warps of four
 // columns each), row maxima combined across the warps
 __global__ void rowexp_cols_kernel(const double* M, int64_t ld, int R, int K, int* e, const int* sh, int dir) {
@@ -1013,11 +1024,21 @@ __global__ void __launch_bounds__(256)
 }  // namespace
 
 // ---------------------------------------------------------------- host API
-cudaError_t row_exponents(const Operand& op, int* e, cudaStream_t s) {
-  if (op.R <= 0) return cudaSuccess;
+namespace {
+
+// both exponent arrays zeroed by one launch (n2 = 0: the first only)
+cudaError_t zero_exponents(int* e1, int n1, int* e2, int n2, cudaStream_t s) {
+  n1 = std::max(n1, 0);
+  n2 = e2 ? std::max(n2, 0) : 0;
+  if (n1 + n2 <= 0) return cudaSuccess;
   prof::count_launch();
-  cudaError_t err = launch_pdl(zero_kernel, dim3((unsigned)std::min(1024, (op.R + 255) / 256)), dim3(256), 0, s, e, op.R);
-  if (err != cudaSuccess) return err;
+  return launch_pdl(zero2_kernel, dim3((unsigned)std::min(1024, (n1 + n2 + 255) / 256)), dim3(256), 0, s, e1, n1, e2,
+                    n2);
+}
+
+// the row exponents of op into e, which the caller has zeroed
+cudaError_t row_exponents_nozero(const Operand& op, int* e, cudaStream_t s) {
+  if (op.R <= 0) return cudaSuccess;
   auto one = [&](const double* M, int64_t ld, int mode, int K, int dir) -> cudaError_t {
     if (K <= 0 || !M) return cudaSuccess;
     const int ks = std::max(1, std::min(64, K / 256));
@@ -1040,9 +1061,18 @@ cudaError_t row_exponents(const Operand& op, int* e, cudaStream_t s) {
     }
     return cudaGetLastError();
   };
-  err = one(op.M1, op.ld1, op.mode1, op.K1, op.sh ? -op.shsign : 0);
+  cudaError_t err = one(op.M1, op.ld1, op.mode1, op.K1, op.sh ? -op.shsign : 0);
   if (err != cudaSuccess) return err;
   return one(op.M2, op.ld2, op.mode2, op.K2, op.sh ? op.shsign : 0);
+}
+
+}  // namespace
+
+cudaError_t row_exponents(const Operand& op, int* e, cudaStream_t s) {
+  if (op.R <= 0) return cudaSuccess;
+  cudaError_t err = zero_exponents(e, op.R, nullptr, 0, s);
+  if (err != cudaSuccess) return err;
+  return row_exponents_nozero(op, e, s);
 }
 
 cudaError_t balance(const Operand& op, int* sh, cudaStream_t s) {
@@ -1143,10 +1173,12 @@ Bufs carve(void* base, int M, int N, int K, int splits) {
 }
 
 cudaError_t prepare(const Operand& A, const Operand& B, const Bufs& b, cudaStream_t s) {
-  cudaError_t e = row_exponents(A, b.eA, s);
-  if (e == cudaSuccess && b.eB != b.eA) e = row_exponents(B, b.eB, s);
+  const bool twoB = b.eB != b.eA && !b.b_packed;
+  cudaError_t e = zero_exponents(b.eA, A.R, twoB ? b.eB : nullptr, B.R, s);
+  if (e == cudaSuccess) e = row_exponents_nozero(A, b.eA, s);
+  if (e == cudaSuccess && twoB) e = row_exponents_nozero(B, b.eB, s);
   if (e == cudaSuccess) e = pack(A, b.eA, kTileA, b.Ablob, s);
-  if (e == cudaSuccess) e = pack(B, b.eB, kTileB, b.Bblob, s);
+  if (e == cudaSuccess && !b.b_packed) e = pack(B, b.eB, kTileB, b.Bblob, s);
   return e;
 }
 
@@ -1179,10 +1211,13 @@ bool stream_product(const Operand& A, const Operand& B, int M, int N, int K, dou
       if (e != cudaSuccess) return e;
       configured = dev;
     }
-    cudaError_t e = row_exponents(A, b.eA, s);
+    cudaError_t e = zero_exponents(b.eA, A.R, b.b_packed ? nullptr : b.eB, B.R, s);
     if (e != cudaSuccess) return e;
-    if ((e = row_exponents(B, b.eB, s)) != cudaSuccess) return e;
-    if ((e = pack(B, b.eB, kTileB, b.Bblob, s)) != cudaSuccess) return e;
+    if ((e = row_exponents_nozero(A, b.eA, s)) != cudaSuccess) return e;
+    if (!b.b_packed) {
+      if ((e = row_exponents_nozero(B, b.eB, s)) != cudaSuccess) return e;
+      if ((e = pack(B, b.eB, kTileB, b.Bblob, s)) != cudaSuccess) return e;
+    }
     StreamParams sp{};
     sp.A = A.M1;
     sp.lda = A.ld1;

@@ -86,6 +86,9 @@ struct Bufs {
   __nv_bfloat16* Ablob;
   __nv_bfloat16* Bblob;
   int64_t* P;  // 2 * splits * M * N
+  // eB and Bblob already hold the right operand's exponents and digits (an earlier product
+  // with the same right operand packed them there): not computed again
+  bool b_packed = false;
 };
 int choose_splits(int M, int N, int K, int sms);
 size_t bytes(int M, int N, int K, int splits, bool partials = true);

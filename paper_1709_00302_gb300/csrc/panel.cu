@@ -568,7 +568,72 @@ __global__ void w_from_gram_kernel(int j, int bk, const double* Y, const double*
   trace_end(trace);
 }
 
+// Tn = -T of a factored panel from its Gram coefficients: T = U^{-1} with U = strict upper
+// of Y^T Y (G) + diag(1 / tau).  Column c by back substitution T(c, c) = tau_c,
+// T(r, c) = -tau_r sum_{p = r+1..c} G(r, p) T(p, c) for r = c - 1 .. 0 (a tau_r of 0 gives a
+// zero row, the identity reflector), in right-looking order: once T(p, c) is known, every
+// lane adds G(r, p) T(p, c) into the sums of its rows r < p, so the dependent chain per
+// step is one multiply, one broadcast and one FMA.  On GB300 each FP64 warp instruction
+// holds a sub-partition's FP64 unit for tens of cycles, so the kernel runs one warp per
+// column and one column per CTA (one warp per SM), with the column's part of G in shared
+// memory.
+__global__ void t_from_gram_kernel(int bk, const double* tau, const double* G, double* Tn,
+                                   unsigned long long* trace) {
+  extern __shared__ double tg_smem[];  // G(0:c, 0:c+1), column p at p * bk; then tau
+  pdl_wait_and_release();
+  trace_start(trace);
+  const int lane = threadIdx.x, c = blockIdx.x;
+  double* sTau = tg_smem + (size_t)bk * bk;
+  for (int p = 1; p <= c; ++p)
+    for (int r = lane; r < p; r += 32) tg_smem[r + (size_t)p * bk] = G[r + (size_t)p * bk];
+  for (int r = lane; r <= c; r += 32) sTau[r] = tau[r];
+  __syncwarp();
+  double acc[4] = {0.0, 0.0, 0.0, 0.0}, t[4] = {0.0, 0.0, 0.0, 0.0};  // rows lane + 32 u (bk <= 128)
+  for (int p = c; p >= 0; --p) {
+    const int q = p >> 5;
+    const bool mine = (p & 31) == lane;
+    double accp = 0.0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (u == q) accp = acc[u];
+    double tp = 0.0;
+    if (mine) tp = p == c ? sTau[c] : -sTau[p] * accp;
+    tp = __shfl_sync(0xffffffffu, tp, p & 31);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int r = lane + 32 * u;
+      if (mine && u == q) t[u] = tp;
+      if (r < p) acc[u] = fma(tg_smem[r + (size_t)p * bk], tp, acc[u]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int r = lane + 32 * u;
+    if (r < bk) Tn[r + (size_t)c * bk] = r <= c ? -t[u] : 0.0;
+  }
+  trace_end(trace);
+}
+
 }  // namespace
+
+cudaError_t launch_t_from_gram(int bk, const double* tau, const double* G, double* Tn, cudaStream_t s) {
+  if (bk <= 0) return cudaSuccess;
+  if (bk > 128) return cudaErrorInvalidValue;
+  static int configured_device = -1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (configured_device != dev) {
+    cudaError_t e = cudaFuncSetAttribute(t_from_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)((128 * 128 + 128) * sizeof(double)));
+    if (e != cudaSuccess) return e;
+    configured_device = dev;
+  }
+  prof::TraceScope tr(prof::kTraceW, 0);
+  unsigned long long* rec = prof::trace_take();
+  prof::count_launch();
+  return launch_pdl(t_from_gram_kernel, dim3(bk), dim3(32), ((size_t)bk * bk + bk) * sizeof(double), s, bk, tau, G,
+                    Tn, rec);
+}
 
 cudaError_t launch_w_from_gram(int j, int bk, const double* Y, const double* tau, const double* G, double* W,
                                int64_t ldy, cudaStream_t s) {

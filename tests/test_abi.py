@@ -74,6 +74,14 @@ def test_invalid_arguments_are_rejected_before_any_device_work(L):
     assert L.bandred_ge2gb_ex(6, 5, 1, fake, 5, fake, fake, None, null, 0, null, null) == -5
     assert L.bandred_ge2gb_ex(6, 5, 1, fake, 6, null, fake, None, null, 0, null, null) == -6
     assert L.bandred_ge2gb_ex(6, 5, 1, fake, 6, fake, null, None, null, 0, null, null) == -7
+    # ge2bb: m < 0, n < 0, w < 1, lda < m, tauq / taup missing where reflectors exist
+    assert L.bandred_ge2bb_ex(-1, 5, 1, fake, 4, fake, fake, None, null, 0, null, null) == -1
+    assert L.bandred_ge2bb_ex(6, -5, 1, fake, 6, fake, fake, None, null, 0, null, null) == -2
+    assert L.bandred_ge2bb_ex(6, 5, 0, fake, 6, fake, fake, None, null, 0, null, null) == -3
+    assert L.bandred_ge2bb_ex(6, 5, 1, fake, 5, fake, fake, None, null, 0, null, null) == -5
+    assert L.bandred_ge2bb_ex(6, 5, 1, fake, 6, null, fake, None, null, 0, null, null) == -6
+    assert L.bandred_ge2bb_ex(6, 5, 1, fake, 6, fake, null, None, null, 0, null, null) == -7
+    assert L.bandred_ge2bb_ex(6, 5, 6, fake, 6, null, null, None, null, 0, null, null) == -9  # no reflectors
     # cost model: shape limits, missing pointers
     assert L.bandred_mlp_param_count(8, 32) == 8 * 32 + 32 + 32 * 32 + 3 * 32 + 1 - 32
     assert L.bandred_mlp_param_count(0, 4) == 0 and L.bandred_mlp_param_count(4, 65) == 0
