@@ -48,6 +48,10 @@ def _load():
         lib.oracle_ge2gb.restype = c_int
         lib.oracle_ge2bb.argtypes = [i64, i64, i64, dp, i64, dp, dp, i64]
         lib.oracle_ge2bb.restype = c_int
+        lib.oracle_sb2st.argtypes = [i64, i64, dp, i64, dp, dp]
+        lib.oracle_sb2st.restype = c_int
+        lib.oracle_tridiag_eig.argtypes = [i64, dp, dp, dp]
+        lib.oracle_tridiag_eig.restype = c_int
         lib.oracle_jacobi_eig.argtypes = [i64, dp, i64, dp]
         lib.oracle_jacobi_eig.restype = c_int
         lib.oracle_jacobi_svd.argtypes = [i64, i64, dp, i64, dp]
@@ -141,6 +145,34 @@ def ge2gb_wide(A: np.ndarray, w: int):
         raise ValueError("ge2gb_wide: m must be < n (use ge2gb for m >= n)")
     T, tq_t, tp_t = ge2gb(np.asfortranarray(A.T), w)
     return np.asfortranarray(T.T), tp_t, tq_t
+
+
+def sb2st(A: np.ndarray, w: int):
+    """Symmetric band (lower triangle, bandwidth w) -> tridiagonal by bulge chasing with
+    Householder reflectors (the second stage after the band form).  Returns (d, e)."""
+    A = np.array(A, dtype=np.float64, order="F", copy=True)
+    n = A.shape[0]
+    d = np.zeros(max(n, 1))
+    e = np.zeros(max(n - 1, 1))
+    info = _load().oracle_sb2st(n, w, _ptr(A), max(n, 1), _ptr(d), _ptr(e))
+    if info != 0:
+        raise ValueError(f"oracle_sb2st: info={info}")
+    return d[:n], e[: max(n - 1, 0)]
+
+
+def tridiag_eig(d: np.ndarray, e: np.ndarray) -> np.ndarray:
+    """Eigenvalues (ascending) of the symmetric tridiagonal (d, e) by bisection on Sturm
+    counts."""
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    e = np.ascontiguousarray(e, dtype=np.float64)
+    n = d.shape[0]
+    ee = np.zeros(max(n, 1))
+    ee[: max(n - 1, 0)] = e[: max(n - 1, 0)]
+    lam = np.zeros(max(n, 1))
+    info = _load().oracle_tridiag_eig(n, _ptr(d if n else np.zeros(1)), _ptr(ee), _ptr(lam))
+    if info != 0:
+        raise ValueError(f"oracle_tridiag_eig: info={info}")
+    return lam[:n]
 
 
 def jacobi_eig(A: np.ndarray) -> np.ndarray:

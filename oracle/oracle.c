@@ -404,3 +404,134 @@ int oracle_jacobi_svd(int64_t m, int64_t n, const double *A, int64_t lda, double
     free(U);
     return sweeps;
 }
+
+/* ---------------------------------------------------------------------------------
+ * Second stage (the step after the band form that the paper's eigenvalue experiments
+ * take with SBRDT and DSTERF): symmetric band (bandwidth w) -> tridiagonal by bulge
+ * chasing with Householder reflectors, then the eigenvalues of the tridiagonal.
+ *
+ * Band -> tridiagonal, one reflector at a time on a dense symmetric copy.  Sweep c
+ * (c = 0 .. n-3) first annihilates A(c+2 : c+w+1, c) with a reflector on the index range
+ * [c+1, c+1+w) (keeping A(c+1, c)), applied from both sides.  Its right application to
+ * the rows below that range fills a triangle below the band (the bulge); the next
+ * reflector of the sweep annihilates the bulge's first column below its in-band entry,
+ * on the range shifted by w, and so on to the end of the matrix.  The other columns of a
+ * bulge are annihilated by the sweeps that follow, whose ranges start one index later.
+ * Every reflector follows the larfg convention above.  Each application touches only
+ * the rows and columns within 2w of its range (everything else is zero there).
+ * A: n x n, lower triangle holds the band (0 <= i-j <= w; the rest of it is ignored).
+ * On return d[0..n) is the diagonal and e[0..n-1) the subdiagonal.
+ * Returns 0, -i for an invalid i-th argument, -100 when out of memory.
+ * ---------------------------------------------------------------------------------*/
+int oracle_sb2st(int64_t n, int64_t w, const double *A, int64_t lda, double *d, double *e) {
+    if (n < 0) return -1;
+    if (w < 1) return -2;
+    if (lda < (n > 1 ? n : 1)) return -4;
+    if (n == 0) return 0;
+    double *M = (double *)calloc((size_t)n * (size_t)n, sizeof(double));
+    double *v = (double *)malloc(sizeof(double) * (size_t)(w + 1));
+    double *p = (double *)malloc(sizeof(double) * (size_t)(5 * w + 2));
+    if (!M || !v || !p) { free(M); free(v); free(p); return -100; }
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t i = j; i < n && i <= j + w; ++i) AT(M, n, i, j) = AT(M, n, j, i) = AT(A, lda, i, j);
+    for (int64_t c = 0; c + 2 < n; ++c) {
+        int64_t col = c, s = c + 1;
+        while (1) {
+            int64_t end = s + w < n ? s + w : n;
+            int64_t len = end - s;
+            if (len < 2) break;
+            double t;
+            house(len, &AT(M, n, s, col), 1, &t);
+            /* the mirror of the annihilated column */
+            for (int64_t i = 0; i < len; ++i) AT(M, n, col, s + i) = AT(M, n, s + i, col);
+            if (t != 0.0) {
+                v[0] = 1.0;
+                for (int64_t i = 1; i < len; ++i) v[i] = AT(M, n, s + i, col);
+                int64_t lo = s - 2 * w > 0 ? s - 2 * w : 0, hi = end + 2 * w < n ? end + 2 * w : n;
+                /* left: rows [s, end) of columns [lo, hi) other than col, which is done */
+                for (int64_t j = lo; j < hi; ++j) {
+                    if (j == col) continue;
+                    double z = 0.0;
+                    for (int64_t i = 0; i < len; ++i) z += v[i] * AT(M, n, s + i, j);
+                    z *= t;
+                    for (int64_t i = 0; i < len; ++i) AT(M, n, s + i, j) -= z * v[i];
+                }
+                /* right: columns [s, end) of rows [lo, hi) other than col */
+                for (int64_t i = lo; i < hi; ++i) {
+                    if (i == col) continue;
+                    double z = 0.0;
+                    for (int64_t k = 0; k < len; ++k) z += AT(M, n, i, s + k) * v[k];
+                    p[i - lo] = z * t;
+                }
+                for (int64_t k = 0; k < len; ++k)
+                    for (int64_t i = lo; i < hi; ++i)
+                        if (i != col) AT(M, n, i, s + k) -= p[i - lo] * v[k];
+            }
+            /* the annihilated entries are exactly zero */
+            for (int64_t i = 1; i < len; ++i) AT(M, n, s + i, col) = AT(M, n, col, s + i) = 0.0;
+            col = s;
+            s += w;
+        }
+    }
+    for (int64_t i = 0; i < n; ++i) d[i] = AT(M, n, i, i);
+    for (int64_t i = 0; i + 1 < n; ++i) e[i] = AT(M, n, i + 1, i);
+    free(M);
+    free(v);
+    free(p);
+    return 0;
+}
+
+/* Number of eigenvalues of the symmetric tridiagonal (d, e) below x: the negative terms
+ * of the Sturm sequence q_0 = d_0 - x, q_i = d_i - x - e_{i-1}^2 / q_{i-1} (Sylvester's law
+ * of inertia for the LDL^T factorisation of T - x I).  A zero term is replaced by
+ * -pivmin, a tiny negative number (x nudged past an eigenvalue at the pole). */
+static int64_t sturm_count(int64_t n, const double *d, const double *e, double x, double pivmin) {
+    int64_t neg = 0;
+    double q = d[0] - x;
+    if (fabs(q) < pivmin) q = -pivmin;
+    if (q < 0.0) ++neg;
+    for (int64_t i = 1; i < n; ++i) {
+        q = d[i] - x - e[i - 1] * e[i - 1] / q;
+        if (fabs(q) < pivmin) q = -pivmin;
+        if (q < 0.0) ++neg;
+    }
+    return neg;
+}
+
+/* Eigenvalues of the symmetric tridiagonal T = (d, e), ascending, by bisection: lam[k]
+ * is the point where the count of eigenvalues below x passes k, bracketed in the
+ * Gershgorin interval and halved until the bracket is within a few units in the last
+ * place of max |T|.  Returns 0, -i for an invalid i-th argument. */
+int oracle_tridiag_eig(int64_t n, const double *d, const double *e, double *lam) {
+    if (n < 0) return -1;
+    if (n == 0) return 0;
+    double gl = d[0], gu = d[0], tmax = 0.0, emax2 = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < n ? fabs(e[i]) : 0.0);
+        if (d[i] - r < gl) gl = d[i] - r;
+        if (d[i] + r > gu) gu = d[i] + r;
+        if (fabs(d[i]) > tmax) tmax = fabs(d[i]);
+        if (i + 1 < n) {
+            if (fabs(e[i]) > tmax) tmax = fabs(e[i]);
+            if (e[i] * e[i] > emax2) emax2 = e[i] * e[i];
+        }
+    }
+    const double eps = 0x1p-53;
+    const double pivmin = (emax2 > 1.0 ? emax2 : 1.0) * 0x1p-1020;
+    const double tol = 4.0 * eps * (tmax > 0.0 ? tmax : 1.0);
+    gl -= tol;
+    gu += tol;
+    for (int64_t k = 0; k < n; ++k) {
+        double lo = gl, hi = gu;  /* count(lo) <= k < count(hi) */
+        for (int it = 0; it < 200 && hi - lo > tol; ++it) {
+            double mid = 0.5 * (lo + hi);
+            if (mid <= lo || mid >= hi) break;
+            if (sturm_count(n, d, e, mid, pivmin) > k)
+                hi = mid;
+            else
+                lo = mid;
+        }
+        lam[k] = 0.5 * (lo + hi);
+    }
+    return 0;
+}
