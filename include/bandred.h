@@ -222,6 +222,35 @@ size_t bandred_ge2bb_workspace(int64_t m, int64_t n, int64_t w, const bandred_op
 int bandred_ge2bb_ex(int64_t m, int64_t n, int64_t w, double* A, int64_t lda, double* tauq, double* taup,
                      const bandred_opts* opts, void* work, size_t work_bytes, int* dev_status, cudaStream_t stream);
 
+/* ---------------------------------------------------------------- second stage --------
+ * The step after the band form in the paper's eigenvalue experiments (there SBRDT, then
+ * DSTERF): band -> tridiagonal by Householder bulge chasing, then the eigenvalues of the
+ * tridiagonal.
+ *
+ * bandred_sb2st: A device, n x n, lda >= max(1, n); its lower band 0 <= i-j <= w holds the
+ *   symmetric band B (as bandred_sy2sb leaves it; nothing else of A is read, A is not
+ *   written).  Sweep c (c = 0 .. n-3) annihilates B(c+2 : c+w+1, c) by a reflector on the
+ *   index range [c+1, c+1+w) applied from both sides, then chases the bulge it creates
+ *   below the band down the matrix, one reflector per w rows (larfg convention).  On exit
+ *   d (device, n) holds the diagonal and e (device, n - 1) the subdiagonal of T = Q^T B Q.
+ *   1 <= w <= 128.  opts: only timeout_ms is used (NULL: defaults).  work: device,
+ *   16-byte aligned, >= bandred_sb2st_workspace(n, w) bytes (the band with room for the
+ *   bulge, 2 w n doubles, and per-sweep progress counters).  dev_status: as for
+ *   bandred_sy2sb_ex (BANDRED_DEV_TIMEOUT when a sweep's bounded wait for the previous
+ *   sweep gave up).  Returns 0, -i for an invalid i-th argument, BANDRED_ERR_UNSUPPORTED
+ *   for w > 128, or a CUDA error code.
+ * bandred_sterf: eigenvalues of the symmetric tridiagonal (d, e) (device, n and n - 1
+ *   entries) into lam (device, n, ascending), by bisection on Sturm counts to within a
+ *   few units in the last place of max |T|.  work: device, 16-byte aligned,
+ *   >= bandred_sterf_workspace(n) bytes.  Returns 0, -i for an invalid i-th argument.
+ */
+size_t bandred_sb2st_workspace(int64_t n, int64_t w);
+int bandred_sb2st(int64_t n, int64_t w, const double* A, int64_t lda, double* d, double* e,
+                  const bandred_opts* opts, void* work, size_t work_bytes, int* dev_status, cudaStream_t stream);
+size_t bandred_sterf_workspace(int64_t n);
+int bandred_sterf(int64_t n, const double* d, const double* e, double* lam, void* work, size_t work_bytes,
+                  cudaStream_t stream);
+
 /* ---------------------------------------------------------------- forming Q, U, V ---
  * The orthogonal factors of a finished reduction, formed on the GPU from the packed
  * reflectors (the step that eigenvector and singular-vector solvers take after the band

@@ -155,6 +155,14 @@ def lib():
         L.bandred_ge2bb_ex.restype = ci
         L.bandred_ge2bb_form.argtypes = [i64, i64, i64, vp, i64, vp, ci, vp, i64, op, vp, sz, vp, vp]
         L.bandred_ge2bb_form.restype = ci
+        L.bandred_sb2st_workspace.argtypes = [i64, i64]
+        L.bandred_sb2st_workspace.restype = sz
+        L.bandred_sb2st.argtypes = [i64, i64, vp, i64, vp, vp, op, vp, sz, vp, vp]
+        L.bandred_sb2st.restype = ci
+        L.bandred_sterf_workspace.argtypes = [i64]
+        L.bandred_sterf_workspace.restype = sz
+        L.bandred_sterf.argtypes = [i64, vp, vp, vp, vp, sz, vp]
+        L.bandred_sterf.restype = ci
         L.bandred_newton_eval.argtypes = [i64, vp, vp, vp, vp]
         L.bandred_newton_eval.restype = ci
         L.bandred_fp64_probe.argtypes = [ci, ci, ci, vp, vp]
@@ -498,6 +506,41 @@ def ge2bb_form(A, w: int, tau, side: int, opts: bandred_opts | None = None, stre
     if rc != 0:
         raise BandredError(rc, "bandred_ge2bb_form")
     return Q, status
+
+
+def sb2st(A, w: int, opts: bandred_opts | None = None, stream=None, check: bool = True):
+    """Band -> tridiagonal by bulge chasing: the lower band (bandwidth w) of the
+    column-major CUDA tensor A (n x n, read only).  Returns (d, e, dev_status)."""
+    import torch
+
+    n = A.shape[0]
+    d = torch.zeros(max(n, 1), dtype=torch.float64, device=A.device)
+    e = torch.zeros(max(n - 1, 1), dtype=torch.float64, device=A.device)
+    work = torch.empty(max(lib().bandred_sb2st_workspace(n, w), 256), dtype=torch.uint8, device=A.device)
+    status = torch.zeros(1, dtype=torch.int32, device=A.device)
+    rc = lib().bandred_sb2st(n, w, _ptr(A), _lda(A), _ptr(d), _ptr(e), None if opts is None else ctypes.byref(opts),
+                             _ptr(work), work.numel(), _ptr(status), _stream(stream))
+    if rc != 0:
+        raise BandredError(rc, "bandred_sb2st")
+    if check:
+        st = int(status.item())
+        if st != 0:
+            raise BandredError(st, "bandred_sb2st (device)")
+    return d[:n], e[: max(n - 1, 0)], status
+
+
+def sterf(d, e, stream=None):
+    """Eigenvalues (ascending) of the symmetric tridiagonal (d, e), CUDA tensors."""
+    import torch
+
+    n = d.shape[0]
+    lam = torch.zeros(max(n, 1), dtype=torch.float64, device=d.device)
+    work = torch.empty(max(lib().bandred_sterf_workspace(n), 256), dtype=torch.uint8, device=d.device)
+    ee = e if e.numel() > 0 else torch.zeros(1, dtype=torch.float64, device=d.device)
+    rc = lib().bandred_sterf(n, _ptr(d), _ptr(ee), _ptr(lam), _ptr(work), work.numel(), _stream(stream))
+    if rc != 0:
+        raise BandredError(rc, "bandred_sterf")
+    return lam[:n]
 
 
 def bandred_panel_phase_trace(buf) -> int:

@@ -255,4 +255,44 @@ int bandred_ge2bb_form(int64_t m, int64_t n, int64_t w, const double* A, int64_t
                    work_bytes, dev_status, stream);
 }
 
+size_t bandred_sb2st_workspace(int64_t n, int64_t w) {
+  if (n < 0 || w < 1 || w > 128) return 0;
+  return bandred::sb2st_workspace_bytes(n, w);
+}
+
+int bandred_sb2st(int64_t n, int64_t w, const double* A, int64_t lda, double* d, double* e,
+                  const bandred_opts* opts, void* work, size_t work_bytes, int* dev_status, cudaStream_t stream) {
+  if (n < 0) return -1;
+  if (w < 1) return -2;
+  if (w > 128) return BANDRED_ERR_UNSUPPORTED;
+  if (n > 0 && !A) return -3;
+  if (lda < std::max<int64_t>(1, n)) return -4;
+  if (n > 0 && !d) return -5;
+  if (n > 1 && !e) return -6;
+  if (n > INT32_MAX / 256) return BANDRED_ERR_UNSUPPORTED;
+  Options o;
+  if (bandred::resolve_options(opts, w, &o) != 0) return -7;
+  if (!work || !aligned(work)) return -8;
+  if (work_bytes < bandred::sb2st_workspace_bytes(n, w)) return -9;
+  bandred::DeviceGuard dg;
+  if (n > 0 && !dg.select(A)) return -3;
+  return bandred::sb2st_run(n, w, A, lda, d, e, o.limit_ns, work, dev_status, stream);
+}
+
+size_t bandred_sterf_workspace(int64_t n) { return n < 0 ? 0 : bandred::sterf_workspace_bytes(n); }
+
+int bandred_sterf(int64_t n, const double* d, const double* e, double* lam, void* work, size_t work_bytes,
+                  cudaStream_t stream) {
+  if (n < 0) return -1;
+  if (n > 0 && !d) return -2;
+  if (n > 1 && !e) return -3;
+  if (n > 0 && !lam) return -4;
+  if (n > INT32_MAX / 2) return BANDRED_ERR_UNSUPPORTED;
+  if (!work || !aligned(work)) return -5;
+  if (work_bytes < bandred::sterf_workspace_bytes(n)) return -6;
+  bandred::DeviceGuard dg;
+  if (n > 0 && !dg.select(lam)) return -4;
+  return bandred::sterf_run(n, d, e, lam, work, stream);
+}
+
 }  // extern "C"

@@ -71,6 +71,12 @@ int sy2sb_run(int64_t n, int64_t w, double* A, int64_t lda, double* tau, const O
 
 size_t ge2gb_workspace_bytes(int64_t m, int64_t n, int64_t w, const Options& o);
 size_t ge2bb_workspace_bytes(int64_t m, int64_t n, int64_t w, const Options& o);
+// Second stage: band -> tridiagonal (bulge chasing) and the tridiagonal's eigenvalues.
+size_t sb2st_workspace_bytes(int64_t n, int64_t w);
+int sb2st_run(int64_t n, int64_t w, const double* A, int64_t lda, double* d, double* e, unsigned long long limit_ns,
+              void* work, int* dev_status, cudaStream_t s);
+size_t sterf_workspace_bytes(int64_t n);
+int sterf_run(int64_t n, const double* d, const double* e, double* lam, void* work, cudaStream_t s);
 int ge2bb_run(int64_t m, int64_t n, int64_t w, double* A, int64_t lda, double* tauq, double* taup, const Options& o,
               void* work, int* dev_status, cudaStream_t s);
 int ge2gb_run(int64_t m, int64_t n, int64_t w, double* A, int64_t lda, double* tauq, double* taup,

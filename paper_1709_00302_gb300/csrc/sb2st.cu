@@ -1,0 +1,432 @@
+// Second stage after the band form (the step the paper's eigenvalue experiments take with
+// SBRDT and DSTERF): the symmetric band B (bandwidth w) is reduced to a tridiagonal T by
+// Householder bulge chasing, and the eigenvalues of T are found by bisection on Sturm
+// counts.
+//
+// Bulge chasing.  Sweep c (c = 0 .. n-3) annihilates B(c+2 : c+w+1, c) with a reflector
+// on the index range [c+1, c+1+w), applied from both sides; its right application to
+// the rows below the range fills a triangle below the band, and the sweep's next
+// reflector annihilates that bulge's first column below its in-band entry, on the range
+// shifted by w, down to the end of the matrix (the bulge's other columns are taken by
+// the sweeps that follow).  Each reflector follows the larfg convention (beta =
+// -sign(alpha) ||x||, sign(0) = +1; tau = 0 for a zero tail).
+//
+// GB300 mapping.  The band lives in a compact lower band store of 2w rows per column
+// (offsets 0 .. 2w-1 hold the band and the bulge), which stays in L2 (n = 8192, w = 64:
+// 8 MB).  One persistent cooperative kernel: CTA g runs sweeps g, g + G, ... in order.
+// A step of sweep c touches indices within [s - w, s + 2w) of its range start s, so step
+// t of sweep c waits until sweep c - 1 has finished its step t + 3 (its range then lies
+// 3w further on): every entry sees the sweeps' updates in sequential order, and the
+// result equals the one-sweep-at-a-time algorithm up to the rounding of the sums.  The
+// waits are bounded: past the time limit the kernel records BANDRED_DEV_TIMEOUT and
+// returns.  Within a step the three blocks the reflector touches (the bulge columns to
+// the left of the range, the symmetric diagonal block, the rows below the range) are
+// independent vectors, one warp each at a time.
+#include <algorithm>
+#include <cstdint>
+
+#include "common.cuh"
+#include "driver.h"
+#include "kernels.h"
+#include "launch.h"
+#include "prof.h"
+
+namespace bandred {
+namespace {
+
+constexpr int kChaseThreads = 256;
+constexpr int kMaxW = 128;  // reflector length <= w <= 128: four entries per lane
+constexpr int kDone = 1 << 30;
+
+struct ChaseParams {
+  int n, w, LB;       // LB = 2w: rows of the band store per column
+  double* Bs;         // entry (i, k), 0 <= i - k < LB, at Bs[(i - k) + k * LB]
+  int* prog;          // prog[c]: steps sweep c has finished (kDone when finished)
+  int* status;
+  unsigned long long limit_ns;
+};
+
+// Loads go to L2 (ld.cg): another CTA may have changed a line this SM read before.
+__device__ __forceinline__ double ldb(const ChaseParams& p, int i, int k) {
+  return __ldcg(&p.Bs[(int64_t)(i - k) + (int64_t)k * p.LB]);
+}
+__device__ __forceinline__ void stb(const ChaseParams& p, int i, int k, double x) {
+  p.Bs[(int64_t)(i - k) + (int64_t)k * p.LB] = x;
+}
+// symmetric read of the band store (either triangle)
+__device__ __forceinline__ double bsym(const ChaseParams& p, int i, int k) {
+  return i >= k ? ldb(p, i, k) : ldb(p, k, i);
+}
+
+__device__ __forceinline__ int ld_acquire_int(const int* q) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(q) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_int(int* q, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(q), "r"(v) : "memory");
+}
+
+__global__ void __launch_bounds__(kChaseThreads) sb2st_chase_kernel(ChaseParams p) {
+  __shared__ double v[kMaxW];       // the reflector (v[0] = 1)
+  __shared__ double pdiag[kMaxW];   // tau * B(R, R) v, then K = p - (tau/2)(p.v) v
+  __shared__ double red[kChaseThreads / 32];
+  __shared__ double s_tau, s_beta, s_scal, s_half;
+  __shared__ int s_ok;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = kChaseThreads / 32;
+  const int n = p.n, w = p.w;
+  for (int c = blockIdx.x; c + 2 < n; c += gridDim.x) {
+    int col = c, s = c + 1, t = 0;
+    while (true) {
+      const int end = min(s + w, n), len = end - s;
+      if (len < 2) break;
+      // wait for sweep c - 1 to pass step t + 3 (or to finish)
+      if (tid == 0) {
+        int ok = 1;
+        if (c > 0) {
+          unsigned long long t0 = 0;
+          unsigned int spins = 0;
+          while (ld_acquire_int(&p.prog[c - 1]) < t + 4) {
+            if ((++spins & 63u) == 0u) {
+              const unsigned long long now = global_ns();
+              if (t0 == 0) t0 = now;
+              else if (now - t0 > p.limit_ns) {
+                if (p.status) atomicCAS(p.status, 0, BANDRED_DEV_TIMEOUT);
+                ok = 0;
+                break;
+              }
+              if (p.status && ld_acquire_int(p.status) != 0) { ok = 0; break; }
+            }
+          }
+        }
+        s_ok = ok;
+      }
+      __syncthreads();
+      if (!s_ok) return;
+
+      // reflector from x = B(s : end, col): warp 0 forms max |x2| and the scaled sum
+      if (warp == 0) {
+        double xv[4], amax = 0.0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = lane + 32 * u;
+          xv[u] = (i < len) ? ldb(p, s + i, col) : 0.0;
+          if (i >= 1 && i < len) amax = fmax(amax, fabs(xv[u]));
+          if (i < len) v[i] = xv[u];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        double ss = 0.0;
+        if (amax > 0.0) {
+          const double inv = 1.0 / amax;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int i = lane + 32 * u;
+            if (i >= 1 && i < len) {
+              const double q = xv[u] * inv;
+              ss = fma(q, q, ss);
+            }
+          }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        if (lane == 0) {
+          const double alpha = xv[0];
+          double tau = 0.0, beta = alpha, scal = 1.0;
+          if (amax > 0.0) {
+            const double xnorm = amax * sqrt(ss);
+            const double h = hypot(alpha, xnorm);
+            beta = alpha >= 0.0 ? -h : h;
+            tau = (beta - alpha) / beta;
+            scal = 1.0 / (alpha - beta);
+          }
+          s_tau = tau;
+          s_beta = beta;
+          s_scal = scal;
+        }
+      }
+      __syncthreads();
+      const double tau = s_tau;
+      // v = [1; x2 scal]; the column becomes [beta; 0 ...]
+      for (int i = tid; i < len; i += kChaseThreads) {
+        stb(p, s + i, col, i == 0 ? s_beta : 0.0);
+      }
+      __syncthreads();
+      if (tid < len) v[tid] = tid == 0 ? 1.0 : v[tid] * s_scal;
+      __syncthreads();
+
+      if (tau != 0.0) {
+        // phase A, one warp per vector: the bulge columns j in (col, s) (left
+        // application), the rows i in [end, end + w) below the range (right application),
+        // and p = tau B(R, R) v over the symmetric diagonal block
+        const int nb = s - col - 1;                 // bulge columns
+        const int nl = min(end + w, n) - end;       // rows below
+        const int items = nb + nl + len;
+        for (int it = warp; it < items; it += NW) {
+          double vv[4], a[4];
+          if (it < nb) {
+            const int j = col + 1 + it;
+            double z = 0.0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int i = lane + 32 * u;
+              vv[u] = i < len ? v[i] : 0.0;
+              a[u] = i < len ? ldb(p, s + i, j) : 0.0;
+              z = fma(vv[u], a[u], z);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
+            z *= tau;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int i = lane + 32 * u;
+              if (i < len) stb(p, s + i, j, fma(-z, vv[u], a[u]));
+            }
+          } else if (it < nb + nl) {
+            const int i = end + (it - nb);
+            double y = 0.0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int k = lane + 32 * u;
+              vv[u] = k < len ? v[k] : 0.0;
+              a[u] = k < len ? ldb(p, i, s + k) : 0.0;
+              y = fma(a[u], vv[u], y);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
+            y *= tau;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int k = lane + 32 * u;
+              if (k < len) stb(p, i, s + k, fma(-y, vv[u], a[u]));
+            }
+          } else {
+            const int i = it - nb - nl;
+            double y = 0.0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int k = lane + 32 * u;
+              if (k < len) y = fma(bsym(p, s + i, s + k), v[k], y);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
+            if (lane == 0) pdiag[i] = tau * y;
+          }
+        }
+        __syncthreads();
+        // K = p - (tau/2)(p.v) v
+        double pv = 0.0;
+        if (tid < len) pv = pdiag[tid] * v[tid];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) pv += __shfl_xor_sync(0xffffffffu, pv, o);
+        if (lane == 0) red[warp] = pv;
+        __syncthreads();
+        if (tid == 0) {
+          double sum = 0.0;
+          for (int q = 0; q < NW; ++q) sum += red[q];
+          s_half = 0.5 * tau * sum;
+        }
+        __syncthreads();
+        if (tid < len) pdiag[tid] = fma(-s_half, v[tid], pdiag[tid]);
+        __syncthreads();
+        // phase B: B(R, R) -= v K^T + K v^T on the stored lower triangle
+        for (int q = tid; q < len * len; q += kChaseThreads) {
+          const int i = q % len, k = q / len;
+          if (i >= k) stb(p, s + i, s + k, fma(-v[i], pdiag[k], fma(-pdiag[i], v[k], ldb(p, s + i, s + k))));
+        }
+      }
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        st_release_int(&p.prog[c], t + 1);
+      }
+      col = s;
+      s += w;
+      ++t;
+    }
+    if (tid == 0) {
+      __threadfence();
+      st_release_int(&p.prog[c], kDone);
+    }
+  }
+}
+
+// Band store from the packed sy2sb output: offsets 0 .. w from A's lower band, zeros
+// above (the bulge rows).
+__global__ void band_in_kernel(int n, int w, int LB, const double* A, int64_t lda, double* Bs) {
+  const int64_t total = (int64_t)n * LB;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    const int off = (int)(q % LB), k = (int)(q / LB), i = k + off;
+    Bs[q] = (off <= w && i < n) ? A[i + (int64_t)k * lda] : 0.0;
+  }
+}
+
+__global__ void band_out_kernel(int n, int LB, const double* Bs, double* d, double* e) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    d[k] = Bs[(int64_t)k * LB];
+    if (k + 1 < n) e[k] = Bs[1 + (int64_t)k * LB];
+  }
+}
+
+}  // namespace
+
+namespace {
+
+// ---------------------------------------------------------------- eigenvalues
+// Gershgorin interval [gl, gu], the stopping width and the pivot guard of the bisection,
+// and e^2 (one CTA): prm = {gl, gu, tol, pivmin}.
+constexpr int kGThreads = 256;
+__global__ void sterf_setup_kernel(int n, const double* d, const double* e, double* e2, double* prm) {
+  __shared__ double s_lo[kGThreads], s_hi[kGThreads], s_mx[kGThreads], s_e2[kGThreads];
+  pdl_wait_and_release();
+  const int tid = threadIdx.x;
+  double lo = 1e300, hi = -1e300, mx = 0.0, em = 0.0;
+  for (int i = tid; i < n; i += kGThreads) {
+    const double el = i > 0 ? fabs(e[i - 1]) : 0.0, er = i + 1 < n ? fabs(e[i]) : 0.0;
+    lo = fmin(lo, d[i] - (el + er));
+    hi = fmax(hi, d[i] + (el + er));
+    mx = fmax(mx, fmax(fabs(d[i]), er));
+    if (i + 1 < n) {
+      const double q = e[i] * e[i];
+      e2[i] = q;
+      em = fmax(em, q);
+    }
+  }
+  s_lo[tid] = lo;
+  s_hi[tid] = hi;
+  s_mx[tid] = mx;
+  s_e2[tid] = em;
+  __syncthreads();
+  for (int h = kGThreads / 2; h > 0; h >>= 1) {
+    if (tid < h) {
+      s_lo[tid] = fmin(s_lo[tid], s_lo[tid + h]);
+      s_hi[tid] = fmax(s_hi[tid], s_hi[tid + h]);
+      s_mx[tid] = fmax(s_mx[tid], s_mx[tid + h]);
+      s_e2[tid] = fmax(s_e2[tid], s_e2[tid + h]);
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    const double tol = 4.0 * 0x1p-53 * (s_mx[0] > 0.0 ? s_mx[0] : 1.0);
+    prm[0] = s_lo[0] - tol;
+    prm[1] = s_hi[0] + tol;
+    prm[2] = tol;
+    prm[3] = fmax(s_e2[0], 1.0) * 0x1p-1020;
+  }
+}
+
+// Eigenvalue k of T by bisection: the Sturm sequence q_0 = d_0 - x,
+// q_i = d_i - x - e_{i-1}^2 / q_{i-1} has as many negative terms as T has eigenvalues below
+// x (a term below the pivot guard counts as -pivmin).  One thread per eigenvalue; the
+// threads of a warp read the same d_i and e_i^2 at each step.
+__global__ void sterf_bisect_kernel(int n, const double* d, const double* e2, const double* prm, double* lam) {
+  pdl_wait_and_release();
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const double tol = prm[2], pivmin = prm[3];
+  double lo = prm[0], hi = prm[1];
+  for (int it = 0; it < 200 && hi - lo > tol; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    int neg = 0;
+    double q = d[0] - mid;
+    if (fabs(q) < pivmin) q = -pivmin;
+    neg += q < 0.0;
+    for (int i = 1; i < n; ++i) {
+      q = (d[i] - mid) - e2[i - 1] / q;
+      if (fabs(q) < pivmin) q = -pivmin;
+      neg += q < 0.0;
+    }
+    if (neg > k)
+      hi = mid;
+    else
+      lo = mid;
+  }
+  lam[k] = 0.5 * (lo + hi);
+}
+
+struct Sb2stWs {
+  double* Bs;
+  int* prog;
+  int* status;
+  size_t bytes;
+};
+
+Sb2stWs carve_sb2st(void* work, int64_t n, int64_t w) {
+  char* base = static_cast<char*>(work);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    char* q = base ? base + off : nullptr;
+    off += (bytes + 255) / 256 * 256;
+    return q;
+  };
+  Sb2stWs ws{};
+  ws.Bs = reinterpret_cast<double*>(take(sizeof(double) * (size_t)std::max<int64_t>(n, 1) * 2 * w));
+  ws.prog = reinterpret_cast<int*>(take(sizeof(int) * (size_t)std::max<int64_t>(n, 1)));
+  ws.status = reinterpret_cast<int*>(take(256));
+  ws.bytes = off;
+  return ws;
+}
+
+}  // namespace
+
+size_t sb2st_workspace_bytes(int64_t n, int64_t w) { return carve_sb2st(nullptr, n, w).bytes; }
+
+size_t sterf_workspace_bytes(int64_t n) { return (sizeof(double) * (size_t)std::max<int64_t>(n, 1) + 255) / 256 * 256 + 256; }
+
+#define CKS(call)                                                 \
+  do {                                                            \
+    cudaError_t e_ = (call);                                      \
+    if (e_ != cudaSuccess) return record_cuda_error(e_, #call);   \
+  } while (0)
+
+int sb2st_run(int64_t n, int64_t w, const double* A, int64_t lda, double* d, double* e, unsigned long long limit_ns,
+              void* work, int* dev_status, cudaStream_t s) {
+  Sb2stWs ws = carve_sb2st(work, n, w);
+  int* status = dev_status ? dev_status : ws.status;
+  CKS(cudaMemsetAsync(status, 0, sizeof(int), s));
+  if (n <= 0) return 0;
+  const int LB = (int)(2 * w);
+  {
+    const int blocks = (int)std::min<int64_t>((n * LB + 255) / 256, 4096);
+    prof::count_launch();
+    band_in_kernel<<<blocks, 256, 0, s>>>((int)n, (int)w, LB, A, lda, ws.Bs);
+    CKS(cudaGetLastError());
+  }
+  if (n > 2 && w > 1) {
+    CKS(cudaMemsetAsync(ws.prog, 0, sizeof(int) * (size_t)n, s));
+    int dev = 0, sms = 0;
+    CKS(cudaGetDevice(&dev));
+    CKS(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    // one CTA per SM (each sweep's FP64 work keeps its SM's FP64 units busy), all
+    // co-resident: the cooperative launch guarantees it
+    const int G = (int)std::min<int64_t>(n - 2, sms);
+    ChaseParams p{(int)n, (int)w, LB, ws.Bs, ws.prog, status, limit_ns};
+    void* args[] = {&p};
+    prof::count_launch();
+    CKS(cudaLaunchCooperativeKernel((const void*)sb2st_chase_kernel, dim3(G), dim3(kChaseThreads), args, 0, s));
+  }
+  {
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 1024);
+    prof::count_launch();
+    band_out_kernel<<<blocks, 256, 0, s>>>((int)n, LB, ws.Bs, d, e);
+    CKS(cudaGetLastError());
+  }
+  return 0;
+}
+
+int sterf_run(int64_t n, const double* d, const double* e, double* lam, void* work, cudaStream_t s) {
+  if (n <= 0) return 0;
+  double* e2 = static_cast<double*>(work);
+  double* prm = reinterpret_cast<double*>(static_cast<char*>(work) +
+                                          (sizeof(double) * (size_t)std::max<int64_t>(n, 1) + 255) / 256 * 256);
+  prof::count_launch();
+  CKS(launch_pdl(sterf_setup_kernel, dim3(1), dim3(kGThreads), 0, s, (int)n, d, e, e2, prm));
+  prof::count_launch();
+  CKS(launch_pdl(sterf_bisect_kernel, dim3((unsigned)((n + 127) / 128)), dim3(128), 0, s, (int)n, d,
+                 static_cast<const double*>(e2), static_cast<const double*>(prm), lam));
+  return 0;
+}
+
+}  // namespace bandred
