@@ -574,20 +574,24 @@ __global__ void w_from_gram_kernel(int j, int bk, const double* Y, const double*
 // zero row, the identity reflector), in right-looking order: once T(p, c) is known, every
 // lane adds G(r, p) T(p, c) into the sums of its rows r < p, so the dependent chain per
 // step is one multiply, one broadcast and one FMA.  On GB300 each FP64 warp instruction
-// holds a sub-partition's FP64 unit for tens of cycles, so the kernel runs one warp per
-// column and one column per CTA (one warp per SM), with the column's part of G in shared
-// memory.
+// holds a sub-partition's FP64 unit for tens of cycles, so the kernel runs one column per
+// CTA, whose threads stage the column's part of G in shared memory and whose first warp
+// alone substitutes (one substituting warp per SM).
 __global__ void t_from_gram_kernel(int bk, const double* tau, const double* G, double* Tn,
                                    unsigned long long* trace) {
   extern __shared__ double tg_smem[];  // G(0:c, 0:c+1), column p at p * bk; then tau
   pdl_wait_and_release();
   trace_start(trace);
-  const int lane = threadIdx.x, c = blockIdx.x;
+  const int lane = threadIdx.x & 31, c = blockIdx.x;
   double* sTau = tg_smem + (size_t)bk * bk;
-  for (int p = 1; p <= c; ++p)
-    for (int r = lane; r < p; r += 32) tg_smem[r + (size_t)p * bk] = G[r + (size_t)p * bk];
-  for (int r = lane; r <= c; r += 32) sTau[r] = tau[r];
-  __syncwarp();
+  // every thread of the CTA stages (many loads in flight); warp 0 alone substitutes
+  for (int q = threadIdx.x; q < (c + 1) * bk; q += blockDim.x) {
+    const int r = q % bk, p = q / bk;
+    if (r < p) tg_smem[q] = G[q];
+  }
+  for (int r = threadIdx.x; r <= c; r += blockDim.x) sTau[r] = tau[r];
+  __syncthreads();
+  if (threadIdx.x >= 32) return;
   double acc[4] = {0.0, 0.0, 0.0, 0.0}, t[4] = {0.0, 0.0, 0.0, 0.0};  // rows lane + 32 u (bk <= 128)
   for (int p = c; p >= 0; --p) {
     const int q = p >> 5;
@@ -631,7 +635,7 @@ cudaError_t launch_t_from_gram(int bk, const double* tau, const double* G, doubl
   prof::TraceScope tr(prof::kTraceW, 0);
   unsigned long long* rec = prof::trace_take();
   prof::count_launch();
-  return launch_pdl(t_from_gram_kernel, dim3(bk), dim3(32), ((size_t)bk * bk + bk) * sizeof(double), s, bk, tau, G,
+  return launch_pdl(t_from_gram_kernel, dim3(bk), dim3(256), ((size_t)bk * bk + bk) * sizeof(double), s, bk, tau, G,
                     Tn, rec);
 }
 
