@@ -411,10 +411,10 @@ def make_problem(args, br, dev, stream):
             G = torch.randn((n, n), dtype=torch.float64, device=dev, generator=g)
             A0 = ((G + G.t()) * 0.5).t().contiguous().t()
             del G
-            A_host = None
+            A_host = lam_true = None
             desc = f"sy2sb n={n} w={w} b={b} N(0,1) symmetrised (drawn on the device)"
         else:
-            A_host, _ = workloads.sym_known_spectrum(n, 0, 1)
+            A_host, lam_true = workloads.sym_known_spectrum(n, 0, 1)
             A0 = torch.from_numpy(A_host).to(dev)
             desc = (f"sy2sb n={n} w={w} b={b} known-spectrum (lam log-uniform [1e-6,1], random signs)")
 
@@ -436,7 +436,7 @@ def make_problem(args, br, dev, stream):
             return sym_probe_backward(A_host, A.cpu().numpy(), outs[0].cpu().numpy(), w, probes=4)
 
         return dict(A0=A0, make_call=make_call, flops=nominal_flops(n), backward=backward, desc=desc,
-                    config={"n": n, "w": w, "b": b}, units=1)
+                    config={"n": n, "w": w, "b": b}, units=1, lam=lam_true)
     if wl == "ge2gb":
         m = n = args.n
         w, b = args.w, args.b
@@ -853,6 +853,8 @@ def main():
     if args.workload == "sy2sb" and not args.no_extras and world == 1:
         del A
         torch.cuda.empty_cache()
+        extras["eigenvalues"] = compact_eigen(args, br, dev, stream, prob)
+        torch.cuda.empty_cache()
         extras["ge2gb"] = compact_ge2gb(args, br, dev, stream)
         torch.cuda.empty_cache()
         extras["batched"] = compact_batched(args, br, dev, stream, world, rank, dist)
@@ -945,6 +947,62 @@ def paper_sweep(args, br, dev, stream):
             "data": "synthetic uniform (0,1) symmetric, drawn on the device",
             "columns": ["n", "w", "b", "lookahead", "ms", "tflops"], "rows": rows,
             "best_b": {k: {"b": v[0], "tflops": v[1]} for k, v in best.items()}, "clocks": clocks.stop()}
+
+
+def compact_eigen(args, br, dev, stream, prob):
+    """The whole eigenvalue path on the headline's matrix (the paper's two-stage solver:
+    band reduction, band -> tridiagonal, tridiagonal eigenvalues): sy2sb in the Ozaki
+    precision, then bandred_sb2st and bandred_sterf, each timed with CUDA events over one
+    run after one warm-up, with the largest eigenvalue error against the known spectrum."""
+    import ctypes
+
+    import numpy as np
+    import torch
+
+    n, w, b = args.n, args.w, args.b
+    A0 = prob["A0"]
+    A = torch.empty_like(A0)
+    o = br.make_opts(b=b, lookahead=args.lookahead, precision="ozaki")
+    tau = torch.zeros(n - w, dtype=torch.float64, device=dev)
+    work = torch.empty(br.bandred_sy2sb_workspace(n, w, o), dtype=torch.uint8, device=dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    d = torch.zeros(n, dtype=torch.float64, device=dev)
+    e = torch.zeros(max(n - 1, 1), dtype=torch.float64, device=dev)
+    lam = torch.zeros(n, dtype=torch.float64, device=dev)
+    w2 = torch.empty(max(br.lib().bandred_sb2st_workspace(n, w), 256), dtype=torch.uint8, device=dev)
+    w3 = torch.empty(max(br.lib().bandred_sterf_workspace(n), 256), dtype=torch.uint8, device=dev)
+    st2 = torch.zeros(1, dtype=torch.int32, device=dev)
+    L = br.lib()
+    P = ctypes.c_void_p
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    for _ in range(2):
+        A.copy_(A0)
+        torch.cuda.synchronize(dev)
+        ev[0].record(stream)
+        if br.bandred_sy2sb_ex(A, w, tau, o, work, st, stream) != 0:
+            raise br.BandredError(-1, "bandred_sy2sb_ex")
+        ev[1].record(stream)
+        rc = L.bandred_sb2st(n, w, P(A.data_ptr()), A.stride(1), P(d.data_ptr()), P(e.data_ptr()), None,
+                             P(w2.data_ptr()), w2.numel(), P(st2.data_ptr()), P(stream.cuda_stream))
+        if rc != 0:
+            raise br.BandredError(rc, "bandred_sb2st")
+        ev[2].record(stream)
+        rc = L.bandred_sterf(n, P(d.data_ptr()), P(e.data_ptr()), P(lam.data_ptr()), P(w3.data_ptr()), w3.numel(),
+                             P(stream.cuda_stream))
+        if rc != 0:
+            raise br.BandredError(rc, "bandred_sterf")
+        ev[3].record(stream)
+        torch.cuda.synchronize(dev)
+    if int(st.item()) != 0 or int(st2.item()) != 0:
+        raise br.BandredError(int(st.item()) or int(st2.item()), "device status (eigenvalue path)")
+    ms = [ev[q].elapsed_time(ev[q + 1]) for q in range(3)]
+    out = {"workload": prob["desc"] + " precision=ozaki, then band -> tridiagonal and bisection",
+           "sy2sb_ms": ms[0], "sb2st_ms": ms[1], "sterf_ms": ms[2], "total_ms": sum(ms)}
+    if prob.get("lam") is not None:
+        lt = np.sort(np.asarray(prob["lam"]))
+        out["max_eig_error_rel"] = float(np.max(np.abs(lam.cpu().numpy() - lt)) / np.max(np.abs(lt)))
+    del A
+    return out
 
 
 def compact_ge2gb(args, br, dev, stream):

@@ -14,10 +14,13 @@
 // GB300 mapping.  The band lives in a compact lower band store of 2w rows per column
 // (offsets 0 .. 2w-1 hold the band and the bulge), which stays in L2 (n = 8192, w = 64:
 // 8 MB).  One persistent cooperative kernel: CTA g runs sweeps g, g + G, ... in order.
-// A step of sweep c touches indices within [s - w, s + 2w) of its range start s, so step
-// t of sweep c waits until sweep c - 1 has finished its step t + 3 (its range then lies
-// 3w further on): every entry sees the sweeps' updates in sequential order, and the
-// result equals the one-sweep-at-a-time algorithm up to the rounding of the sums.  The
+// A step of sweep c with range start s writes only entries whose column index lies in
+// [s - w, s + w) (the annihilated column, the bulge columns, the range), and step t'' of
+// sweep c - 1 only entries whose column index is at least its own s'' - w = s - 1 +
+// (t'' - t - 1) w.  They share entries only for t'' <= t + 2, so step t of sweep c waits
+// until sweep c - 1 has finished its step t + 2: every entry sees the sweeps' updates in
+// sequential order, and the result equals the one-sweep-at-a-time algorithm up to the
+// rounding of the sums.  The
 // waits are bounded: past the time limit the kernel records BANDRED_DEV_TIMEOUT and
 // returns.  Within a step the three blocks the reflector touches (the bulge columns to
 // the left of the range, the symmetric diagonal block, the rows below the range) are
@@ -81,13 +84,13 @@ __global__ void __launch_bounds__(kChaseThreads) sb2st_chase_kernel(ChaseParams 
     while (true) {
       const int end = min(s + w, n), len = end - s;
       if (len < 2) break;
-      // wait for sweep c - 1 to pass step t + 3 (or to finish)
+      // wait for sweep c - 1 to pass step t + 2 (or to finish)
       if (tid == 0) {
         int ok = 1;
         if (c > 0) {
           unsigned long long t0 = 0;
           unsigned int spins = 0;
-          while (ld_acquire_int(&p.prog[c - 1]) < t + 4) {
+          while (ld_acquire_int(&p.prog[c - 1]) < t + 3) {
             if ((++spins & 63u) == 0u) {
               const unsigned long long now = global_ns();
               if (t0 == 0) t0 = now;
@@ -234,6 +237,190 @@ __global__ void __launch_bounds__(kChaseThreads) sb2st_chase_kernel(ChaseParams 
         for (int q = tid; q < len * len; q += kChaseThreads) {
           const int i = q % len, k = q / len;
           if (i >= k) stb(p, s + i, s + k, fma(-v[i], pdiag[k], fma(-pdiag[i], v[k], ldb(p, s + i, s + k))));
+        }
+      }
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        st_release_int(&p.prog[c], t + 1);
+      }
+      col = s;
+      s += w;
+      ++t;
+    }
+    if (tid == 0) {
+      __threadfence();
+      st_release_int(&p.prog[c], kDone);
+    }
+  }
+}
+
+// The same chase with each step's three blocks staged in shared memory (w <= 64): all
+// threads load the bulge columns, the symmetric diagonal block and the rows below in one
+// round of L2 loads, the step runs in shared memory with one thread per vector (no warp
+// reductions: every FP64 instruction does useful work), and the blocks go back at the
+// end.  Strides of kSLd = 65 doubles keep the per-thread vectors conflict-free.
+constexpr int kSMaxW = 64;
+constexpr int kSLd = kSMaxW + 1;
+constexpr size_t kSmemChase = sizeof(double) * (3 * (size_t)kSMaxW * kSLd + 3 * kSMaxW);
+
+__global__ void __launch_bounds__(kChaseThreads) sb2st_chase_smem_kernel(ChaseParams p) {
+  extern __shared__ double cs_smem[];
+  double* sB = cs_smem;                         // bulge column j, row i at j * kSLd + i
+  double* sD = sB + (size_t)kSMaxW * kSLd;      // diagonal block, (i, k) at k * kSLd + i (both triangles)
+  double* sL = sD + (size_t)kSMaxW * kSLd;      // row r below the range, column k at r * kSLd + k
+  double* v = sL + (size_t)kSMaxW * kSLd;       // the reflector
+  double* pd = v + kSMaxW;                      // tau B(R, R) v, then K
+  double* sx = pd + kSMaxW;                     // the column to annihilate
+  __shared__ double s_tau, s_beta, s_scal, s_half;
+  __shared__ int s_ok;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int n = p.n, w = p.w;
+  for (int c = blockIdx.x; c + 2 < n; c += gridDim.x) {
+    int col = c, s = c + 1, t = 0;
+    while (true) {
+      const int end = min(s + w, n), len = end - s;
+      if (len < 2) break;
+      if (tid == 0) {
+        int ok = 1;
+        if (c > 0) {
+          unsigned long long t0 = 0;
+          unsigned int spins = 0;
+          while (ld_acquire_int(&p.prog[c - 1]) < t + 3) {
+            if ((++spins & 63u) == 0u) {
+              const unsigned long long now = global_ns();
+              if (t0 == 0) t0 = now;
+              else if (now - t0 > p.limit_ns) {
+                if (p.status) atomicCAS(p.status, 0, BANDRED_DEV_TIMEOUT);
+                ok = 0;
+                break;
+              }
+              if (p.status && ld_acquire_int(p.status) != 0) { ok = 0; break; }
+            }
+          }
+        }
+        s_ok = ok;
+      }
+      __syncthreads();
+      if (!s_ok) return;
+      const int nb = s - col - 1, nl = min(end + w, n) - end;
+      // stage: the column, the bulge columns, the diagonal block, the rows below
+      for (int i = tid; i < len; i += kChaseThreads) sx[i] = ldb(p, s + i, col);
+      for (int q = tid; q < nb * len; q += kChaseThreads) {
+        const int j = q / len, i = q - j * len;
+        sB[j * kSLd + i] = ldb(p, s + i, col + 1 + j);
+      }
+      for (int q = tid; q < len * len; q += kChaseThreads) {
+        const int k = q / len, i = q - k * len;
+        if (i >= k) {
+          const double x = ldb(p, s + i, s + k);
+          sD[k * kSLd + i] = x;
+          sD[i * kSLd + k] = x;
+        }
+      }
+      for (int q = tid; q < nl * len; q += kChaseThreads) {
+        const int k = q / nl, r = q - k * nl;
+        sL[r * kSLd + k] = ldb(p, end + r, s + k);
+      }
+      __syncthreads();
+      // the reflector (warp 0): max-scaled norm of the tail, larfg convention
+      if (tid < 32) {
+        double amax = 0.0;
+        for (int i = 1 + lane; i < len; i += 32) amax = fmax(amax, fabs(sx[i]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        double ss = 0.0;
+        if (amax > 0.0) {
+          const double inv = 1.0 / amax;
+          for (int i = 1 + lane; i < len; i += 32) {
+            const double q = sx[i] * inv;
+            ss = fma(q, q, ss);
+          }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        if (lane == 0) {
+          const double alpha = sx[0];
+          double tau = 0.0, beta = alpha, scal = 1.0;
+          if (amax > 0.0) {
+            const double h = hypot(alpha, amax * sqrt(ss));
+            beta = alpha >= 0.0 ? -h : h;
+            tau = (beta - alpha) / beta;
+            scal = 1.0 / (alpha - beta);
+          }
+          s_tau = tau;
+          s_beta = beta;
+          s_scal = scal;
+        }
+      }
+      __syncthreads();
+      const double tau = s_tau;
+      if (tid < len) v[tid] = tid == 0 ? 1.0 : sx[tid] * s_scal;
+      for (int i = tid; i < len; i += kChaseThreads) stb(p, s + i, col, i == 0 ? s_beta : 0.0);
+      __syncthreads();
+      if (tau != 0.0) {
+        // one thread per vector: bulge column (left), row below (right), row of B(R, R) v
+        if (tid < nb) {
+          double* b = sB + tid * kSLd;
+          double z0 = 0.0, z1 = 0.0;
+          int i = 0;
+          for (; i + 1 < len; i += 2) {
+            z0 = fma(v[i], b[i], z0);
+            z1 = fma(v[i + 1], b[i + 1], z1);
+          }
+          if (i < len) z0 = fma(v[i], b[i], z0);
+          const double z = tau * (z0 + z1);
+          for (i = 0; i < len; ++i) b[i] = fma(-z, v[i], b[i]);
+        } else if (tid < nb + nl) {
+          double* b = sL + (tid - nb) * kSLd;
+          double y0 = 0.0, y1 = 0.0;
+          int k = 0;
+          for (; k + 1 < len; k += 2) {
+            y0 = fma(b[k], v[k], y0);
+            y1 = fma(b[k + 1], v[k + 1], y1);
+          }
+          if (k < len) y0 = fma(b[k], v[k], y0);
+          const double y = tau * (y0 + y1);
+          for (k = 0; k < len; ++k) b[k] = fma(-y, v[k], b[k]);
+        } else if (tid < nb + nl + len) {
+          const int i = tid - nb - nl;
+          double y0 = 0.0, y1 = 0.0;
+          int k = 0;
+          for (; k + 1 < len; k += 2) {
+            y0 = fma(sD[k * kSLd + i], v[k], y0);
+            y1 = fma(sD[(k + 1) * kSLd + i], v[k + 1], y1);
+          }
+          if (k < len) y0 = fma(sD[k * kSLd + i], v[k], y0);
+          pd[i] = tau * (y0 + y1);
+        }
+        __syncthreads();
+        if (tid < 32) {
+          double pv = 0.0;
+          for (int i = lane; i < len; i += 32) pv = fma(pd[i], v[i], pv);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) pv += __shfl_xor_sync(0xffffffffu, pv, o);
+          if (lane == 0) s_half = 0.5 * tau * pv;
+        }
+        __syncthreads();
+        if (tid < len) pd[tid] = fma(-s_half, v[tid], pd[tid]);
+        __syncthreads();
+        for (int q = tid; q < len * len; q += kChaseThreads) {
+          const int k = q / len, i = q - k * len;
+          if (i >= k) sD[k * kSLd + i] = fma(-v[i], pd[k], fma(-pd[i], v[k], sD[k * kSLd + i]));
+        }
+        __syncthreads();
+        // write back what changed
+        for (int q = tid; q < nb * len; q += kChaseThreads) {
+          const int j = q / len, i = q - j * len;
+          stb(p, s + i, col + 1 + j, sB[j * kSLd + i]);
+        }
+        for (int q = tid; q < len * len; q += kChaseThreads) {
+          const int k = q / len, i = q - k * len;
+          if (i >= k) stb(p, s + i, s + k, sD[k * kSLd + i]);
+        }
+        for (int q = tid; q < nl * len; q += kChaseThreads) {
+          const int k = q / nl, r = q - k * nl;
+          stb(p, end + r, s + k, sL[r * kSLd + k]);
         }
       }
       __syncthreads();
@@ -405,7 +592,17 @@ int sb2st_run(int64_t n, int64_t w, const double* A, int64_t lda, double* d, dou
     ChaseParams p{(int)n, (int)w, LB, ws.Bs, ws.prog, status, limit_ns};
     void* args[] = {&p};
     prof::count_launch();
-    CKS(cudaLaunchCooperativeKernel((const void*)sb2st_chase_kernel, dim3(G), dim3(kChaseThreads), args, 0, s));
+    if (w <= kSMaxW) {
+      static int configured = -1;
+      if (configured != dev) {
+        CKS(cudaFuncSetAttribute(sb2st_chase_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemChase));
+        configured = dev;
+      }
+      CKS(cudaLaunchCooperativeKernel((const void*)sb2st_chase_smem_kernel, dim3(G), dim3(kChaseThreads), args,
+                                      kSmemChase, s));
+    } else {
+      CKS(cudaLaunchCooperativeKernel((const void*)sb2st_chase_kernel, dim3(G), dim3(kChaseThreads), args, 0, s));
+    }
   }
   {
     const int blocks = (int)std::min<int64_t>((n + 255) / 256, 1024);

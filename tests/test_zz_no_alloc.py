@@ -7,8 +7,9 @@ scratch array as workspace.  These tests check, on a GPU, that two calls in a ro
 the same result as the existing entry point and as the FP64 oracle within the tolerances
 of the FP64 parity tests (the Ozaki precision included; bf16x6 by the spectrum of its
 band, at its stated tolerance), with the default options (look-ahead on) as well as
-without look-ahead, that the caller's current device is left alone, and that a problem
-too large for the scratch is refused before any device work.  The file is named so that
+without look-ahead, that a call captured into a CUDA graph replays correctly, that the
+caller's current device is left alone, and that a problem too large for the scratch is
+refused before any device work.  The file is named so that
 pytest collects it last.
 """
 import ctypes
@@ -121,6 +122,52 @@ def test_noalloc_split_precision_keeps_the_spectrum_twice(br):
         L = np.where((i - j >= 0) & (i - j <= w), Aout, 0.0)
         B = L + np.tril(L, -1).T
         assert np.max(np.abs(np.linalg.eigvalsh(B) - lam)) <= 2e-5 * np.max(np.abs(lam))
+
+
+@pytest.mark.parametrize("lookahead", [0, -1])
+def test_noalloc_captured_in_a_cuda_graph_replays(br, lookahead):
+    """The stated use case: after one call outside the capture (which creates the look-ahead
+    stream and events), a call is captured into a CUDA graph together with the copy that
+    resets A, and two replays each give the oracle's reduction."""
+    import torch
+
+    n, w = 600, 32
+    A = workloads.sym_gaussian(n, seed=n + w + 9)
+    opts = br.make_opts(precision="fp64", lookahead=lookahead)
+    dA0 = to_dev(A)
+    dA = torch.empty_like(dA0)
+    tau = torch.zeros(n - w, dtype=torch.float64, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+
+    def call():
+        s = torch.cuda.current_stream()
+        return br.lib().bandred_sy2sb_noalloc(n, w, ctypes.c_void_p(dA.data_ptr()), dA.stride(1),
+                                              ctypes.c_void_p(tau.data_ptr()), ctypes.byref(opts),
+                                              ctypes.c_void_p(status.data_ptr()), ctypes.c_void_p(s.cuda_stream))
+
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        dA.copy_(dA0)
+        assert call() == 0
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        dA.copy_(dA0)
+        rc = call()
+    assert rc == 0
+    Ao, to = oracle.sy2sb(A, w)
+    bo, vo = lower_band_and_v(Ao, w)
+    fa = np.linalg.norm(A)
+    for _ in range(2):
+        dA.zero_()
+        tau.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert int(status.item()) == 0
+        bg, vg = lower_band_and_v(to_host(dA), w)
+        assert np.max(np.abs(bg - bo)) <= B_TOL * fa
+        assert np.max(np.abs(vg - vo), initial=0.0) <= V_TOL
+        assert np.max(np.abs(tau.cpu().numpy() - to), initial=0.0) <= V_TOL
 
 
 def test_noalloc_refuses_problems_beyond_the_scratch(br):
