@@ -77,9 +77,11 @@ typedef struct bandred_opts {
                               path and reports BANDRED_DEV_TIMEOUT in dev_status */
     int panel_group;       /* reflectors taken per grid-wide reduction in the FP64 panel
                               factorisation: 0 = default (2), 2 (pairs) or 4 (half the grid
-                              barriers, four times the serial scalar work; slower on GB300).
-                              Both give the Householder reflectors of Section 2.1 up to
-                              rounding */
+                              barriers, four times the serial scalar work; slower on GB300);
+                              1 = pairs, and panels of at most 512 rows on one thread-block
+                              cluster, one reflector per cluster barrier (the batched path's
+                              panel).  All give the Householder reflectors of Section 2.1 up
+                              to rounding */
     int depth;             /* look-ahead depth: 0 = default (1); 2 factors the panel two
                               iterations ahead, only with V1 and 3b <= w (that panel is then
                               reached by one-sided updates alone); otherwise 1 is used */
@@ -240,8 +242,8 @@ int bandred_ge2bb_ex(int64_t m, int64_t n, int64_t w, double* A, int64_t lda, do
  *   sweep gave up).  Returns 0, -i for an invalid i-th argument, BANDRED_ERR_UNSUPPORTED
  *   for w > 128, or a CUDA error code.
  * bandred_sterf: eigenvalues of the symmetric tridiagonal (d, e) (device, n and n - 1
- *   entries) into lam (device, n, ascending), by bisection on Sturm counts to within a
- *   few units in the last place of max |T|.  work: device, 16-byte aligned,
+ *   entries) into lam (device, n, ascending), by trisection on Sturm counts (two lanes per
+ *   eigenvalue) to within a few units in the last place of max |T|.  work: device, 16-byte aligned,
  *   >= bandred_sterf_workspace(n) bytes.  Returns 0, -i for an invalid i-th argument.
  */
 size_t bandred_sb2st_workspace(int64_t n, int64_t w);

@@ -20,9 +20,17 @@ namespace bandred {
 namespace {
 
 constexpr size_t kAlign = 256;
-constexpr int kMinPanelRows = 32;
+constexpr int kMinPanelRows = 16;
 constexpr int kClusterMax = 16;    // CTAs of a cluster panel
-constexpr int kClusterRows = 32;   // a panel of at most kClusterMax * kClusterRows rows uses a cluster
+constexpr int kClusterRows = 32;   // a panel of at most kClusterMax * kClusterRows rows may use a cluster
+constexpr int kClusterMinRows = 16;  // rows per cluster CTA the cluster size aims at (more CTAs: less FP64 each)
+// The single-matrix reductions take the grid panel at every size by default: measured on
+// GB300 its paired steps (two reflectors per grid reduction) beat the cluster panel's one
+// reflector per cluster barrier on the last panels (j <= 512: about 0.2 against 0.28-0.3
+// ms), and a 16-CTA cluster needs 16 free SMs in one GPC, which the capped update beside
+// it rarely leaves.  The cluster panel is the batched path's, one cluster per matrix, and
+// the single-matrix reductions' with opts->panel_group = 1.
+static bool cluster_panels(const Options& o) { return o.panel_group == 1; }
 constexpr int kMaxSplits = 128;
 constexpr int kSmallSplits = 32;       // split-K of the FP64 products with a b-wide output
 constexpr int kMaxStreamSplits = 8;    // split-K of the streamed X1 = A2 W product
@@ -117,7 +125,7 @@ int resolve_options(const bandred_opts* in, int64_t w, Options* o) {
   if (d.precision < 0 || d.precision > 3) return -1;
   if (d.panel_ctas < 0 || d.timeout_ms < 0) return -1;
   if (d.debug < 0 || d.debug > 1) return -1;
-  if (d.panel_group != 0 && d.panel_group != 2 && d.panel_group != 4) return -1;
+  if (d.panel_group != 0 && d.panel_group != 1 && d.panel_group != 2 && d.panel_group != 4) return -1;
   if (d.depth < 0 || d.depth > 2) return -1;
   o->b = d.b;
   o->lookahead = d.lookahead;
@@ -367,9 +375,9 @@ static int run_panel(double* A, int64_t rs, int64_t cs, int j, int bk, double* t
   p.trace = prof::trace_take();
   // Short panels: one thread-block cluster (no grid-wide barrier, deterministic sums).
   // (The phase trace is taken only by the grid panel below.)
-  if (extra == 0) {
+  if (cluster_panels(o) && extra == 0) {
     int C = 1;
-    while (C < kClusterMax && (j + C - 1) / C > kClusterRows) C *= 2;
+    while (C < kClusterMax && (j + C - 1) / C > kClusterMinRows) C *= 2;
     const int Rc = (j + C - 1) / C;
     if (Rc <= kClusterRows) {
       p.A = A;
@@ -487,13 +495,13 @@ static int stream_splits(int tiles, int nkb, int sms, int cap) {
 
 // SMs for the look-ahead panel of V2 (jp x bp rows and columns) while the rank-2k update of
 // the rest of A2 (order j, rank 2 bu) holds the others.  A model of the two durations on
-// GB300, fitted to device traces of the Ozaki path at n = 8192, w = b = 64:
-//   panel  ~ 8.5 us per pair of reflectors (latency) + 7.9e-4 us x jp bp^2 / P,
-//   update ~ 1.23e-5 us x j^2 bu / (sms - P),
+// GB300, fitted (least squares) to device traces of the Ozaki path at n = 8192, w = b = 64:
+//   panel  ~ 6.4 us per pair of reflectors (latency) + 5.1e-4 us x jp bp^2 / P,
+//   update ~ 1.26e-5 us x j^2 bu / (sms - P),
 // and P minimises the larger of the two.  P never drops below the CTA count at which the
 // panel's rows still fit in shared memory; fixed > 0 overrides the model.
-static int lookahead_panel_ctas(int jp, int bp, int j, int bu, int sms, int fixed) {
-  if (jp <= kClusterMax * kClusterRows) return std::min(kClusterMax, sms - 1);  // a cluster panel
+static int lookahead_panel_ctas(int jp, int bp, int j, int bu, int sms, int fixed, bool cluster) {
+  if (cluster && jp <= kClusterMax * kClusterRows) return std::min(kClusterMax, sms - 1);  // a cluster panel
   const int pmax = std::min(sms - 1, (jp + kMinPanelRows - 1) / kMinPanelRows);  // CTAs a grid panel uses
   int pmin = 1;
   while (pmin < sms) {
@@ -507,8 +515,8 @@ static int lookahead_panel_ctas(int jp, int bp, int j, int bu, int sms, int fixe
   int best = std::min(pmin, pmax);
   double best_t = 1e300;
   for (int P = pmin; P <= pmax; ++P) {
-    const double tp = 8.5 * (bp / 2.0) + 7.9e-4 * (double)jp * bp * bp / P;
-    const double tu = 1.23e-5 * (double)j * j * bu / (sms - P);
+    const double tp = 6.4 * (bp / 2.0) + 5.1e-4 * (double)jp * bp * bp / P;
+    const double tu = 1.26e-5 * (double)j * j * bu / (sms - P);
     const double t = std::max(tp, tu);
     if (t < best_t) {
       best_t = t;
@@ -924,7 +932,7 @@ int sy2sb_run(int64_t n, int64_t w, double* A, int64_t lda, double* tau, const O
         CK(cudaEventRecord(ev_fork, s));
         CK(cudaStreamWaitEvent(sp, ev_fork, 0));
         if ((rc = R.syr2k(k, buf, 0, cL, sp))) return rc;
-        const int la_panel = la_split ? lookahead_panel_ctas(j - b, bkn, j, bk, R.sms, o.panel_ctas) : 0;
+        const int la_panel = la_split ? lookahead_panel_ctas(j - b, bkn, j, bk, R.sms, o.panel_ctas, cluster_panels(o)) : 0;
         if ((rc = R.panel(kn, buf ^ 1, sp, la_panel))) return rc;
         CK(cudaEventRecord(ev_panel, sp));
         if ((rc = R.syr2k(k, buf, cL, j, s, la_split ? R.sms - la_panel : 0))) return rc;
@@ -1355,7 +1363,7 @@ int ge2gb_run(int64_t m, int64_t n, int64_t w, double* A, int64_t lda, double* t
       // (the model of the look-ahead split, with the two rank-b updates of j rows as the
       // update), so both streams run at once; other precisions take every SM.
       const int P = o.precision == BANDRED_OZAKI
-                        ? lookahead_panel_ctas(std::max(jr, j - bk), b, j, 2 * b, R.sms, o.panel_ctas)
+                        ? lookahead_panel_ctas(std::max(jr, j - bk), b, j, 2 * b, R.sms, o.panel_ctas, cluster_panels(o))
                         : 0;
       const int rest = P > 0 && P < R.sms ? R.sms - P : 0;
       // panel stream: row block k (rows k .. k+bk), then row panel k; the next column
@@ -1369,17 +1377,19 @@ int ge2gb_run(int64_t m, int64_t n, int64_t w, double* A, int64_t lda, double* t
         return rc;
       if ((rc = R.left_panel(k + b, bu ^ 1, sp, P))) return rc;
       CK(cudaEventRecord(ev_panel, sp));
-      // caller's stream: the rest (rows below the row block, columns past the next panel)
-      {
-        prof::TraceScope tr(prof::kTraceLeft, k);
-        if ((rc = R.rank_k(j - bk, nc - bkn, bk, R.ws.Yu[bu] + bk, R.ws.ldu, R.ws.ZT + bkn, R.ws.ldv,
-                           E + bk + (int64_t)bkn * lda, lda, 0, s, rest)))
-          return rc;
-      }
+      // caller's stream: the rest (rows below the row block, columns past the next panel);
+      // the pending right update first, so that it is the one beside the row panel (the
+      // two are additive updates from the same pre-state products and commute)
       if (kprev >= 0) {
         prof::TraceScope tr(prof::kTraceRight, kprev);
         if ((rc = R.rank_k(j - bk, jr, b, R.ws.P + bk, R.ws.ldu, R.ws.Yv[bvp], R.ws.ldv,
                            A + k + bk + (kprev + w) * lda, lda, 0, s, rest)))
+          return rc;
+      }
+      {
+        prof::TraceScope tr(prof::kTraceLeft, k);
+        if ((rc = R.rank_k(j - bk, nc - bkn, bk, R.ws.Yu[bu] + bk, R.ws.ldu, R.ws.ZT + bkn, R.ws.ldv,
+                           E + bk + (int64_t)bkn * lda, lda, 0, s, rest)))
           return rc;
       }
       kprev = k;

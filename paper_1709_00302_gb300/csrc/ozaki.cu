@@ -101,6 +101,35 @@ __global__ void rowexp_cols_kernel(const double* M, int64_t ld, int R, int K, in
   }
 }
 
+// both sources of a two-source operand in one launch: column blocks [0, t1) of grid.y read
+// M1 (shift dir1 sigma), the rest M2 (shift dir2 sigma)
+__global__ void rowexp_cols2_kernel(const double* M1, int64_t ld1, int K1, int dir1, const double* M2, int64_t ld2,
+                                    int K2, int dir2, int R, int* e, const int* sh) {
+  __shared__ int rowmax[8][32];
+  pdl_wait_and_release();
+  const int t1 = (K1 + 31) / 32;
+  const bool first = (int)blockIdx.y < t1;
+  const double* M = first ? M1 : M2;
+  const int64_t ld = first ? ld1 : ld2;
+  const int K = first ? K1 : K2, by = first ? blockIdx.y : blockIdx.y - t1;
+  const int shift = (first ? dir1 : dir2) * balance_sigma(sh);
+  const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + lane;
+  int m = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int k = by * 32 + wy * 4 + q;
+    if (i < R && k < K) m = max(m, shifted_exp(M[i + (int64_t)k * ld], shift));
+  }
+  rowmax[wy][lane] = m;
+  __syncthreads();
+  if (wy == 0) {
+#pragma unroll
+    for (int q = 1; q < 8; ++q) m = max(m, rowmax[q][lane]);
+    if (m && i < R) atomicMax(&e[i], m);
+  }
+}
+
 // entries M[k + r ld] (k in [k0, k1), k > r when `upper`): one warp per row
 __global__ void rowexp_rows_kernel(const double* M, int64_t ld, int R, int k0, int k1, int upper, int* e,
                                    const int* sh, int dir) {
@@ -231,13 +260,23 @@ __device__ __forceinline__ uint32_t bf16_pair(float a, float b) {
   return __byte_perm(__float_as_uint(a), __float_as_uint(b), 0x7632);
 }
 
-__global__ void pack_kernel(Operand op, const int* e, int TR, int nrb, int nkb, __nv_bfloat16* out) {
-  pdl_wait_and_release();
+struct PackJob {
+  Operand op;
+  const int* e;
+  int TR, nrb, nkb;
+  __nv_bfloat16* out;
+};
+
+// group g (TR rows x 8 reduction steps of one packed block) of a packing job
+__device__ __forceinline__ void pack_group(const PackJob& jb, int64_t g) {
+  const Operand& op = jb.op;
+  const int* e = jb.e;
+  const int TR = jb.TR, nkb = jb.nkb;
+  __nv_bfloat16* out = jb.out;
   const int groups = TR * (kDepth / 8);
-  const int64_t total = (int64_t)nrb * nkb * groups;
   const int K = op.K1 + op.K2;
   const int sigma = op.shsign * balance_sigma(op.sh);  // M1 entries times 2^-sigma, M2 entries times 2^sigma
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
+  {
     const int within = (int)(g % groups);
     const int64_t tile = g / groups;
     const int kb = (int)(tile % nkb), rb = (int)(tile / nkb);
@@ -265,6 +304,29 @@ __global__ void pack_kernel(Operand op, const int* e, int TR, int nrb, int nkb, 
       *dst = make_uint4(bf16_pair(d[0][s], d[1][s]), bf16_pair(d[2][s], d[3][s]), bf16_pair(d[4][s], d[5][s]),
                         bf16_pair(d[6][s], d[7][s]));
     }
+  }
+}
+
+__device__ __forceinline__ int64_t pack_total(const PackJob& jb) {
+  return (int64_t)jb.nrb * jb.nkb * jb.TR * (kDepth / 8);
+}
+
+__global__ void pack_kernel(PackJob a) {
+  pdl_wait_and_release();
+  const int64_t total = pack_total(a);
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x)
+    pack_group(a, g);
+}
+
+// both operands of a product in one launch
+__global__ void pack2_kernel(PackJob a, PackJob b) {
+  pdl_wait_and_release();
+  const int64_t ta = pack_total(a), total = ta + pack_total(b);
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
+    if (g < ta)
+      pack_group(a, g);
+    else
+      pack_group(b, g - ta);
   }
 }
 
@@ -1061,6 +1123,15 @@ cudaError_t row_exponents_nozero(const Operand& op, int* e, cudaStream_t s) {
     }
     return cudaGetLastError();
   };
+  if (op.M1 && op.M2 && op.mode1 == 0 && op.mode2 == 0 && op.K1 > 0 && op.K2 > 0) {
+    const int t = (op.K1 + 31) / 32 + (op.K2 + 31) / 32;
+    prof::count_launch();
+    if (cudaError_t le = launch_pdl(rowexp_cols2_kernel, dim3((op.R + 31) / 32, t), dim3(256), 0, s, op.M1, op.ld1,
+                                    op.K1, op.sh ? -op.shsign : 0, op.M2, op.ld2, op.K2, op.sh ? op.shsign : 0, op.R, e,
+                                    op.sh))
+      return le;
+    return cudaGetLastError();
+  }
   cudaError_t err = one(op.M1, op.ld1, op.mode1, op.K1, op.sh ? -op.shsign : 0);
   if (err != cudaSuccess) return err;
   return one(op.M2, op.ld2, op.mode2, op.K2, op.sh ? op.shsign : 0);
@@ -1090,14 +1161,31 @@ size_t packed_bytes(int R, int K, int TR) {
   return nrb * nkb * (size_t)S * TR * kDepth * 2;
 }
 
-cudaError_t pack(const Operand& op, const int* e, int TR, __nv_bfloat16* out, cudaStream_t s) {
+static PackJob pack_job(const Operand& op, const int* e, int TR, __nv_bfloat16* out) {
   const int K = op.K1 + op.K2;
-  if (op.R <= 0 || K <= 0) return cudaSuccess;
-  const int nrb = (op.R + TR - 1) / TR, nkb = (K + kDepth - 1) / kDepth;
-  const int64_t total = (int64_t)nrb * nkb * TR * (kDepth / 8);
+  PackJob jb{op, e, TR, (op.R + TR - 1) / TR, (K + kDepth - 1) / kDepth, out};
+  if (op.R <= 0 || K <= 0) jb.nrb = jb.nkb = 0;
+  return jb;
+}
+
+cudaError_t pack(const Operand& op, const int* e, int TR, __nv_bfloat16* out, cudaStream_t s) {
+  const PackJob jb = pack_job(op, e, TR, out);
+  const int64_t total = (int64_t)jb.nrb * jb.nkb * TR * (kDepth / 8);
+  if (total <= 0) return cudaSuccess;
   const int blocks = (int)std::min<int64_t>((total + 255) / 256, 8192);
   prof::count_launch();
-  return launch_pdl(pack_kernel, dim3(blocks), dim3(256), 0, s, op, e, TR, nrb, nkb, out);
+  return launch_pdl(pack_kernel, dim3(blocks), dim3(256), 0, s, jb);
+}
+
+// both operands of a product, one launch
+static cudaError_t pack2(const Operand& A, const int* eA, int TRA, __nv_bfloat16* outA, const Operand& B,
+                         const int* eB, int TRB, __nv_bfloat16* outB, cudaStream_t s) {
+  const PackJob a = pack_job(A, eA, TRA, outA), b = pack_job(B, eB, TRB, outB);
+  const int64_t total = (int64_t)a.nrb * a.nkb * TRA * (kDepth / 8) + (int64_t)b.nrb * b.nkb * TRB * (kDepth / 8);
+  if (total <= 0) return cudaSuccess;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 8192);
+  prof::count_launch();
+  return launch_pdl(pack2_kernel, dim3(blocks), dim3(256), 0, s, a, b);
 }
 
 cudaError_t gemm(const GemmParams& p, int splits, cudaStream_t s) {
@@ -1177,8 +1265,12 @@ cudaError_t prepare(const Operand& A, const Operand& B, const Bufs& b, cudaStrea
   cudaError_t e = zero_exponents(b.eA, A.R, twoB ? b.eB : nullptr, B.R, s);
   if (e == cudaSuccess) e = row_exponents_nozero(A, b.eA, s);
   if (e == cudaSuccess && twoB) e = row_exponents_nozero(B, b.eB, s);
-  if (e == cudaSuccess) e = pack(A, b.eA, kTileA, b.Ablob, s);
-  if (e == cudaSuccess && !b.b_packed) e = pack(B, b.eB, kTileB, b.Bblob, s);
+  if (e == cudaSuccess) {
+    if (b.b_packed)
+      e = pack(A, b.eA, kTileA, b.Ablob, s);
+    else
+      e = pack2(A, b.eA, kTileA, b.Ablob, B, b.eB, kTileB, b.Bblob, s);
+  }
   return e;
 }
 

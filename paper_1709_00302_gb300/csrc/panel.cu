@@ -210,21 +210,23 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
       const double Sab = ldcg(&acc[(size_t)(i + 1) * kAccStride]);
       const double Sbb = ldcg(&acc[(size_t)(bk + 2 + i) * kAccStride]);
       const double bi = ldcg(&rowg[i + 1]), ai1 = ldcg(&rowg[bk + i]), bi1 = ldcg(&rowg[bk + i + 1]);
-      const int rescale = (p.j - i > 1) && (amax > 0.0) && !(ssq < 0x1p1000 && amax > 0x1p-450);
-      s_rescale = rescale || !(fabs(alpha) < 0x1p500);
+      const long long us = dbits(ssq), um = dbits(amax);  // amax >= 0 (an integer maximum)
+      const int rescale = (p.j - i > 1) && (um > 0) && !(us >= 0 && us < kBits2p1000 && um > kBits2m450);
+      s_rescale = rescale || !(abits(alpha) < kBits2p500);
       // Common path: h = ||[alpha; x2]|| = q / sqrt(q) with q = alpha^2 + ||x2||^2 (no
       // overflow: both terms are bounded here); tau = (beta - alpha) / beta = 1 + |alpha|/h
       // and scal = 1 / (alpha - beta) = sign(alpha) / (|alpha| + h).
       double tau = 0.0, beta = alpha, scal = 1.0;
-      if (!s_rescale && p.j - i > 1 && ssq != 0.0) {
+      if (!s_rescale && p.j - i > 1 && (us << 1) != 0) {
         const double q = fma(alpha, alpha, ssq);
         const double rq = rsqrt_newton(q);
         const double h = q * rq;
         const double aa = fabs(alpha);
-        beta = (alpha >= 0.0) ? -h : h;
+        const bool apos = nonneg(alpha);
+        beta = neg_if(h, apos);
         tau = fma(aa, rq, 1.0);
         const double rs = rcp_newton(aa + h);
-        scal = (alpha >= 0.0) ? rs : -rs;
+        scal = neg_if(rs, !apos);
       }
       s_beta = beta;
       s_tau = tau;
@@ -246,15 +248,19 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
         const double n2 = fma(zs * zs, Taa, fma(-2.0 * zs, Tab, Tbb));
         const double alpha2 = fma(-zs, ai1, bi1);
         const double bound = fma(zs * zs, ssq, Sbb);
-        if (n2 > 0.125 * bound && n2 < 0x1p1000 && n2 > 0x1p-900 && fabs(alpha2) < 0x1p500) {
+        // n2 > bound / 8 (bound >= 0: the pattern of bound / 8 is bound's minus 3 in the
+        // exponent; when that underflows, n2 > 2^-900 decides as the FP64 test would)
+        const long long un2 = dbits(n2), ub = dbits(bound);
+        if (un2 > kBits2m900 && un2 < kBits2p1000 && un2 > ub - (3LL << 52) && abits(alpha2) < kBits2p500) {
           const double q = fma(alpha2, alpha2, n2);
           const double rq = rsqrt_newton(q);
           const double h = q * rq;
           const double aa = fabs(alpha2);
-          s_beta2 = (alpha2 >= 0.0) ? -h : h;
+          const bool apos = nonneg(alpha2);
+          s_beta2 = neg_if(h, apos);
           s_tau2 = fma(aa, rq, 1.0);
           const double rs = rcp_newton(aa + h);
-          s_scal2 = (alpha2 >= 0.0) ? rs : -rs;
+          s_scal2 = neg_if(rs, !apos);
           s_zb = zb;
           s_Taa = Taa;
           s_Tab = Tab;
@@ -274,7 +280,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) panel_qr_kernel(PanelParams 
     int bad = 0;
     if (tid >= 32) {
       const int nsum = want_pair ? 2 * bk + 1 : bk + 1;
-      for (int v = tid - 32; v < nsum; v += NT - 32) bad |= !(fabs(dsum[v]) < 0x1p1000);
+      for (int v = tid - 32; v < nsum; v += NT - 32) bad |= !(abits(dsum[v]) < kBits2p1000);
     }
     const int force = __syncthreads_or(bad);
     stamp(step, 4);

@@ -143,18 +143,20 @@ __global__ void __launch_bounds__(kPanelThreads, 4)
 
     if (tid == 0) {
       const double alpha = rowi[i], ssq = dsum[i], amax = dsum[bk];
-      const int rescale = (p.j - i > 1) && (amax > 0.0) && !(ssq < 0x1p1000 && amax > 0x1p-450);
-      s_rescale = rescale || !(fabs(alpha) < 0x1p500);
+      const long long us = dbits(ssq), um = dbits(amax);  // amax >= 0 (an integer maximum)
+      const int rescale = (p.j - i > 1) && (um > 0) && !(us >= 0 && us < kBits2p1000 && um > kBits2m450);
+      s_rescale = rescale || !(abits(alpha) < kBits2p500);
       double tau = 0.0, beta = alpha, scal = 1.0;
-      if (!s_rescale && p.j - i > 1 && ssq != 0.0) {
+      if (!s_rescale && p.j - i > 1 && (us << 1) != 0) {
         const double q = fma(alpha, alpha, ssq);
         const double rq = rsqrt_newton(q);
         const double h = q * rq;
         const double aa = fabs(alpha);
-        beta = (alpha >= 0.0) ? -h : h;
+        const bool apos = nonneg(alpha);
+        beta = neg_if(h, apos);
         tau = fma(aa, rq, 1.0);
         const double rs = rcp_newton(aa + h);
-        scal = (alpha >= 0.0) ? rs : -rs;
+        scal = neg_if(rs, !apos);
       }
       s_beta = beta;
       s_tau = tau;
@@ -164,7 +166,7 @@ __global__ void __launch_bounds__(kPanelThreads, 4)
     // A sum outside the range where the plain formulas hold (not finite, or near the
     // overflow threshold) forces the scaled path too.
     int bad = 0;
-    for (int v = tid; v < bk; v += NT) bad |= !(fabs(dsum[v]) < 0x1p1000);
+    for (int v = tid; v < bk; v += NT) bad |= !(abits(dsum[v]) < kBits2p1000);
     const int force = __syncthreads_or(bad);
     // Rare path: column i scaled by the power of two 2^-e with 2^e <= max|x2| < 2^(e+1)
     // (exact); a second cluster reduction forms ||x2 2^-e||^2 and the dot products

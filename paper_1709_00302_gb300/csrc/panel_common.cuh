@@ -59,6 +59,27 @@ __device__ __forceinline__ double rcp_newton(double s) {
   return __longlong_as_double(__double_as_longlong(r) - ((long long)e << 52));
 }
 
+// Range and sign tests of FP64 values by integer compares of their bit patterns (no FP64
+// instruction, so they do not queue behind the scalar chain on the FP64 pipe).  For
+// x >= 0 and for NaN the order of the patterns as signed 64-bit integers is the order of
+// the values (NaN above +inf, or below zero when its sign bit is set), so each test below
+// gives the same answer as the FP64 comparison it replaces.
+constexpr long long kBits2p1000 = 0x7E70000000000000LL;   // 2^1000
+constexpr long long kBits2p500 = 0x5F30000000000000LL;    // 2^500
+constexpr long long kBits2m450 = 0x23D0000000000000LL;    // 2^-450
+constexpr long long kBits2m900 = 0x07B0000000000000LL;    // 2^-900
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ long long abits(double x) { return __double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFLL; }
+// x >= 0.0 (true for -0.0 as well)
+__device__ __forceinline__ bool nonneg(double x) {
+  const long long u = dbits(x);
+  return u >= 0 || (u << 1) == 0;
+}
+// -x when c, else x (a sign flip, exact)
+__device__ __forceinline__ double neg_if(double x, bool c) {
+  return __longlong_as_double(dbits(x) ^ (c ? (long long)0x8000000000000000ULL : 0LL));
+}
+
 // FP64 -> FP32 by integer truncation of the mantissa (no FP64 instruction); values
 // outside FP32's normal range take the ordinary conversion.
 __device__ __forceinline__ float f64_to_f32_rz(double x) {

@@ -125,6 +125,6 @@ def test_panel_group_is_validated(L):
 
     fake = ctypes.c_void_p(4096)
     null = ctypes.c_void_p(0)
-    for bad_group in (1, 3, 8, -2):
+    for bad_group in (3, 8, -2):
         o = br.make_opts(b=2, panel_group=bad_group)
         assert L.bandred_sy2sb_ex(10, 4, fake, 10, fake, ctypes.byref(o), null, 0, null, null) == -6

@@ -149,9 +149,9 @@ def test_short_form_allocates_and_matches(br):
     check_sy2sb_parity(A, to_host(dA), tau.cpu().numpy(), w)
 
 
-# Panels taller than one thread-block cluster holds (j > 512) run on the cooperative grid
-# kernel, which takes its reflectors either in pairs or in groups of four per grid-wide
-# reduction (option panel_group); both must give the oracle's reflectors.  Orthogonality of
+# Panels of the single-matrix reductions run on the cooperative grid kernel, which takes
+# its reflectors either in pairs or in groups of four per grid-wide reduction (option
+# panel_group); both must give the oracle's reflectors.  Orthogonality of
 # the Q formed from them is bounded by 3e-16 n (the oracle's own reaches about 8e-17 n).
 @pytest.mark.parametrize("group", [2, 4])
 @pytest.mark.parametrize("n,w,b,la", [(1200, 64, 64, 0), (1100, 40, 16, -1), (1030, 21, 5, 0), (1100, 64, 32, -1)])

@@ -39,8 +39,8 @@ def run(br, A, w, **kw):
     return to_host(dA), tq.cpu().numpy(), tp.cpu().numpy()
 
 
-# (m, n, w, b) with 3b <= w: square and tall, grid panels (m > 512) and cluster panels,
-# w a multiple of b and not, the last iterations narrower than b
+# (m, n, w, b) with 3b <= w: square and tall, tall panels and short ones (few rows per
+# CTA), w a multiple of b and not, the last iterations narrower than b
 SHAPES = [(640, 600, 24, 8), (700, 700, 96, 32), (300, 170, 10, 3), (1100, 900, 100, 33), (200, 200, 48, 16)]
 
 
@@ -85,13 +85,16 @@ def test_row_panel_overlaps_previous_right_update(br):
     rows = {r["iteration"]: r for r in recs if r["kind"] == "row_panel"}
     right = {r["iteration"]: r for r in recs if r["kind"] == "right_update"}
     ov = []
-    for kp, r in right.items():
-        rp = rows.get(kp + b)
+    for kp in sorted(right):
+        r, rp = right[kp], rows.get(kp + b)
         if rp is not None:
             o = max(0, min(rp["t1_ns"], r["t1_ns"]) - max(rp["t0_ns"], r["t0_ns"]))
             ov.append(o / min(rp["t1_ns"] - rp["t0_ns"], r["t1_ns"] - r["t0_ns"]))
     print("\nrow panel k vs right update of k - b, overlap of the shorter:", np.round(ov, 2).tolist())
-    assert len(ov) >= 10 and np.median(ov) > 0.3, ov
+    # the early iterations, where the right update is long, run the two side by side (late
+    # ones finish the short update before the panel stream's own row-block updates end)
+    early = np.array(ov[: max(10, len(ov) // 4)])
+    assert len(ov) >= 10 and np.median(early) > 0.5 and np.max(early) > 0.9, ov
     Ao, _, _ = oracle.ge2gb(A, w)
     i, j = np.indices((m, n))
     band = (j - i >= 0) & (j - i <= w)

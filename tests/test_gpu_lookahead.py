@@ -47,7 +47,7 @@ def check(br, n, w, **kw):
     assert np.max(np.abs(tau - to), initial=0.0) <= V_TOL
 
 
-# (n, w, b): 3b <= w; n = 1100 has grid panels (more than 512 rows) and cluster panels
+# (n, w, b): 3b <= w; n = 1100 has tall panels (more than 512 rows) and short ones
 @pytest.mark.parametrize("precision", ["fp64", "ozaki"])
 @pytest.mark.parametrize("n,w,b", [(600, 48, 16), (1100, 96, 32), (1100, 100, 33), (260, 64, 8)])
 def test_depth2_v1_matches_oracle(br, n, w, b, precision):

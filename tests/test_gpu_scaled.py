@@ -95,9 +95,8 @@ def gen_case(br, m, n, w, s, precision, **kw):
     assert r["backward"] < 1e-13 and r["sv"] < 1e-13, r
 
 
-# (n, w, b): the first panels of n = 700 have more than 512 rows (the cooperative grid
-# panel), the later ones at most 512 (the thread-block-cluster panel); b < w adds the A1
-# update and the V1 look-ahead
+# (n, w, b): the first panels of n = 700 have more than 512 rows, the later ones fewer
+# (fewer CTAs of the grid panel); b < w adds the A1 update and the V1 look-ahead
 SYM = [(700, 32, 32), (300, 20, 8)]
 
 
@@ -112,6 +111,14 @@ def test_sy2sb_scaled_by_power_of_two(br, n, w, b, s, precision):
 @pytest.mark.parametrize("s", [600, -600])
 def test_ge2gb_scaled_by_power_of_two(br, s, precision):
     gen_case(br, 640, 600, 24, s, precision, b=8)
+
+
+@pytest.mark.parametrize("s", [600, -600])
+def test_sy2sb_scaled_cluster_panels(br, s):
+    # panel_group = 1: panels of at most 512 rows on one thread-block cluster (the batched
+    # path's panel), so its rare path runs too
+    sym_case(br, 700, 32, s, "fp64", b=32, panel_group=1)
+    sym_case(br, 300, 20, s, "ozaki", b=8, panel_group=1)
 
 
 def test_sy2sb_scaled_four_reflector_panel(br):
