@@ -1,6 +1,6 @@
 // Second stage after the band form (the step the paper's eigenvalue experiments take with
 // SBRDT and DSTERF): the symmetric band B (bandwidth w) is reduced to a tridiagonal T by
-// Householder bulge chasing, and the eigenvalues of T are found by bisection on Sturm
+// Householder bulge chasing, and the eigenvalues of T are found by trisection on Sturm
 // counts.
 //
 // Bulge chasing.  Sweep c (c = 0 .. n-3) annihilates B(c+2 : c+w+1, c) with a reflector
@@ -30,6 +30,7 @@
 
 #include "common.cuh"
 #include "driver.h"
+#include "panel_common.cuh"
 #include "kernels.h"
 #include "launch.h"
 #include "prof.h"
@@ -304,49 +305,93 @@ __global__ void __launch_bounds__(kChaseThreads) sb2st_chase_smem_kernel(ChasePa
       __syncthreads();
       if (!s_ok) return;
       const int nb = s - col - 1, nl = min(end + w, n) - end;
-      // stage: the column, the bulge columns, the diagonal block, the rows below
-      for (int i = tid; i < len; i += kChaseThreads) sx[i] = ldb(p, s + i, col);
-      for (int q = tid; q < nb * len; q += kChaseThreads) {
-        const int j = q / len, i = q - j * len;
-        sB[j * kSLd + i] = ldb(p, s + i, col + 1 + j);
-      }
-      for (int q = tid; q < len * len; q += kChaseThreads) {
-        const int k = q / len, i = q - k * len;
-        if (i >= k) {
-          const double x = ldb(p, s + i, s + k);
-          sD[k * kSLd + i] = x;
-          sD[i * kSLd + k] = x;
+      // stage: the column, the bulge columns, the diagonal block, the rows below.  Every
+      // load of the step is issued before any is used (one round trip to L2): each block
+      // has at most kSMaxW^2 = 16 x kChaseThreads entries, sixteen per thread.
+      {
+        constexpr int kPer = kSMaxW * kSMaxW / kChaseThreads;
+        double rb[kPer], rd[kPer], rl[kPer];
+        const double xs = tid < len ? ldb(p, s + tid, col) : 0.0;
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+          const int q = tid + u * kChaseThreads;
+          const int j = q / len, i = q - j * len;
+          rb[u] = q < nb * len ? ldb(p, s + i, col + 1 + j) : 0.0;
+          const int k = q / len, i2 = q - k * len;
+          rd[u] = (q < len * len && i2 >= k) ? ldb(p, s + i2, s + k) : 0.0;
+          const int kl = nl > 0 ? q / nl : 0, r = nl > 0 ? q - kl * nl : 0;
+          rl[u] = (nl > 0 && q < nl * len) ? ldb(p, end + r, s + kl) : 0.0;
+        }
+        if (tid < len) sx[tid] = xs;
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+          const int q = tid + u * kChaseThreads;
+          if (q < nb * len) {
+            const int j = q / len, i = q - j * len;
+            sB[j * kSLd + i] = rb[u];
+          }
+          if (q < len * len) {
+            const int k = q / len, i2 = q - k * len;
+            if (i2 >= k) {
+              sD[k * kSLd + i2] = rd[u];
+              sD[i2 * kSLd + k] = rd[u];
+            }
+          }
+          if (nl > 0 && q < nl * len) {
+            const int kl = q / nl, r = q - kl * nl;
+            sL[r * kSLd + kl] = rl[u];
+          }
         }
       }
-      for (int q = tid; q < nl * len; q += kChaseThreads) {
-        const int k = q / nl, r = q - k * nl;
-        sL[r * kSLd + k] = ldb(p, end + r, s + k);
-      }
       __syncthreads();
-      // the reflector (warp 0): max-scaled norm of the tail, larfg convention
+      // the reflector (warp 0), larfg convention.  Common path: the plain sum of squares
+      // when it and |alpha| are safely in range (max |x2| from the bit patterns, integer
+      // compares), then h = ||x|| = q / sqrt(q), tau = 1 + |alpha| / h and
+      // 1 / (alpha - beta) by Newton-Raphson; otherwise the max-scaled sum and hypot.
       if (tid < 32) {
-        double amax = 0.0;
-        for (int i = 1 + lane; i < len; i += 32) amax = fmax(amax, fabs(sx[i]));
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        unsigned long long um = 0ull;
         double ss = 0.0;
-        if (amax > 0.0) {
+        for (int i = 1 + lane; i < len; i += 32) {
+          const double x = sx[i];
+          const unsigned long long u = (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+          um = u > um ? u : um;
+          ss = fma(x, x, ss);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const unsigned long long u = __shfl_xor_sync(0xffffffffu, um, o);
+          um = u > um ? u : um;
+          ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        }
+        const double amax = __longlong_as_double((long long)um), alpha = sx[0];
+        const bool plain = amax > 0x1p-450 && ss < 0x1p1000 && fabs(alpha) < 0x1p500;
+        if (amax > 0.0 && !plain) {  // rare: scaled sum (warp-uniform branch)
           const double inv = 1.0 / amax;
+          ss = 0.0;
           for (int i = 1 + lane; i < len; i += 32) {
             const double q = sx[i] * inv;
             ss = fma(q, q, ss);
           }
-        }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+          for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        }
         if (lane == 0) {
-          const double alpha = sx[0];
           double tau = 0.0, beta = alpha, scal = 1.0;
           if (amax > 0.0) {
-            const double h = hypot(alpha, amax * sqrt(ss));
-            beta = alpha >= 0.0 ? -h : h;
-            tau = (beta - alpha) / beta;
-            scal = 1.0 / (alpha - beta);
+            if (plain) {
+              const double q = fma(alpha, alpha, ss);
+              const double rq = panel_detail::rsqrt_newton(q);
+              const double h = q * rq, aa = fabs(alpha);
+              beta = alpha >= 0.0 ? -h : h;
+              tau = fma(aa, rq, 1.0);
+              const double rs = panel_detail::rcp_newton(aa + h);
+              scal = alpha >= 0.0 ? rs : -rs;
+            } else {
+              const double h = hypot(alpha, amax * sqrt(ss));
+              beta = alpha >= 0.0 ? -h : h;
+              tau = (beta - alpha) / beta;
+              scal = 1.0 / (alpha - beta);
+            }
           }
           s_tau = tau;
           s_beta = beta;
@@ -461,7 +506,7 @@ __global__ void band_out_kernel(int n, int LB, const double* Bs, double* d, doub
 namespace {
 
 // ---------------------------------------------------------------- eigenvalues
-// Gershgorin interval [gl, gu], the stopping width and the pivot guard of the bisection,
+// Gershgorin interval [gl, gu], the stopping width and the pivot guard of the trisection,
 // and e^2 (one CTA): prm = {gl, gu, tol, pivmin}.
 constexpr int kGThreads = 256;
 __global__ void sterf_setup_kernel(int n, const double* d, const double* e, double* e2, double* prm) {
@@ -503,34 +548,61 @@ __global__ void sterf_setup_kernel(int n, const double* d, const double* e, doub
   }
 }
 
-// Eigenvalue k of T by bisection: the Sturm sequence q_0 = d_0 - x,
+// Eigenvalue k of T by trisection on Sturm counts: the sequence q_0 = d_0 - x,
 // q_i = d_i - x - e_{i-1}^2 / q_{i-1} has as many negative terms as T has eigenvalues below
-// x (a term below the pivot guard counts as -pivmin).  One thread per eigenvalue; the
-// threads of a warp read the same d_i and e_i^2 at each step.
-__global__ void sterf_bisect_kernel(int n, const double* d, const double* e2, const double* prm, double* lam) {
+// x (a term below the pivot guard counts as -pivmin).  Two lanes per eigenvalue: each
+// iteration the pair counts at the two points that cut [lo, hi) into thirds, one point per
+// lane, and both lanes keep the third that holds eigenvalue k.  The bracket shrinks
+// threefold per iteration from the same Gershgorin interval for every eigenvalue, so all
+// pairs run the same number of iterations (no divergence).  On GB300 the FP64 division
+// chain is latency-bound, so two lanes per eigenvalue (twice the warps) and a third fewer
+// sequential counts than bisection beat the extra count per iteration.
+// One Sturm step costs a reciprocal and one FMA: 1/q by the panel's Newton-Raphson
+// reciprocal (FP32 seed, two FP64 steps: a few units in the last place, well inside the
+// recurrence's own backward error), the pivot guard and the sign test as integer
+// compares of the bit patterns.
+__device__ __forceinline__ int sturm_count(int n, const double* d, const double* e2, double x, double pivmin) {
+  const long long piv = panel_detail::dbits(pivmin);
+  const double npiv = -pivmin;
+  int neg = 0;
+  double q = d[0] - x;
+  if (panel_detail::abits(q) < piv) q = npiv;
+  neg += panel_detail::dbits(q) < 0;
+  for (int i = 1; i < n; ++i) {
+    const double aq = fabs(q);
+    const double r = panel_detail::neg_if(panel_detail::rcp_newton(aq), panel_detail::dbits(q) < 0);
+    q = fma(-e2[i - 1], r, d[i] - x);
+    if (panel_detail::abits(q) < piv) q = npiv;
+    neg += panel_detail::dbits(q) < 0;
+  }
+  return neg;
+}
+
+__global__ void sterf_trisect_kernel(int n, const double* d, const double* e2, const double* prm, double* lam) {
   pdl_wait_and_release();
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n) return;
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = min(g >> 1, n - 1), half = g & 1;
   const double tol = prm[2], pivmin = prm[3];
   double lo = prm[0], hi = prm[1];
-  for (int it = 0; it < 200 && hi - lo > tol; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (mid <= lo || mid >= hi) break;
-    int neg = 0;
-    double q = d[0] - mid;
-    if (fabs(q) < pivmin) q = -pivmin;
-    neg += q < 0.0;
-    for (int i = 1; i < n; ++i) {
-      q = (d[i] - mid) - e2[i - 1] / q;
-      if (fabs(q) < pivmin) q = -pivmin;
-      neg += q < 0.0;
-    }
-    if (neg > k)
-      hi = mid;
-    else
-      lo = mid;
+  // iterations until the width falls to tol: the same for every pair
+  int iters = 0;
+  for (double wd = hi - lo; wd > tol && iters < 120; wd *= (1.0 / 3.0)) ++iters;
+  for (int it = 0; it < iters; ++it) {
+    const double h = (hi - lo) * (1.0 / 3.0);
+    const double x = half ? hi - h : lo + h;
+    const int c = sturm_count(n, d, e2, x, pivmin);
+    const int c1 = __shfl_xor_sync(0xffffffffu, c, 1);
+    const double x1 = lo + h, x2 = hi - h;
+    const int ca = half ? c1 : c, cb = half ? c : c1;  // counts at x1, x2
+    if (ca > k)
+      hi = x1;
+    else if (cb > k) {
+      lo = x1;
+      hi = x2;
+    } else
+      lo = x2;
   }
-  lam[k] = 0.5 * (lo + hi);
+  if (!half && (g >> 1) < n) lam[k] = 0.5 * (lo + hi);
 }
 
 struct Sb2stWs {
@@ -621,7 +693,7 @@ int sterf_run(int64_t n, const double* d, const double* e, double* lam, void* wo
   prof::count_launch();
   CKS(launch_pdl(sterf_setup_kernel, dim3(1), dim3(kGThreads), 0, s, (int)n, d, e, e2, prm));
   prof::count_launch();
-  CKS(launch_pdl(sterf_bisect_kernel, dim3((unsigned)((n + 127) / 128)), dim3(128), 0, s, (int)n, d,
+  CKS(launch_pdl(sterf_trisect_kernel, dim3((unsigned)((2 * n + 63) / 64)), dim3(64), 0, s, (int)n, d,
                  static_cast<const double*>(e2), static_cast<const double*>(prm), lam));
   return 0;
 }
