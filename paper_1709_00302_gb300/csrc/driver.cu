@@ -931,8 +931,10 @@ int sy2sb_run(int64_t n, int64_t w, double* A, int64_t lda, double* tau, const O
       if (has_next && cL > 0) {
         CK(cudaEventRecord(ev_fork, s));
         CK(cudaStreamWaitEvent(sp, ev_fork, 0));
-        if ((rc = R.syr2k(k, buf, 0, cL, sp))) return rc;
+        // A2^L runs on the SMs the next panel will hold, so that it does not compete with
+        // A2^R for the others
         const int la_panel = la_split ? lookahead_panel_ctas(j - b, bkn, j, bk, R.sms, o.panel_ctas, cluster_panels(o)) : 0;
+        if ((rc = R.syr2k(k, buf, 0, cL, sp, la_panel))) return rc;
         if ((rc = R.panel(kn, buf ^ 1, sp, la_panel))) return rc;
         CK(cudaEventRecord(ev_panel, sp));
         if ((rc = R.syr2k(k, buf, cL, j, s, la_split ? R.sms - la_panel : 0))) return rc;
