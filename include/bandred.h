@@ -217,7 +217,8 @@ int bandred_ge2gb_ex(int64_t m, int64_t n, int64_t w, double* A, int64_t lda, do
  * opts->lookahead: 0 none; otherwise the next iteration's two panels are factored on a
  * second stream, Variant V1 (2b <= w: they lie in B1 and C1, reached by one-sided updates)
  * or V2 (2b > w: after the products of D, the first 2b - w columns and rows of D are
- * updated first, the 2 x 2 partition of D); -1 picks by b and w.  work, dev_status,
+ * updated first, the 2 x 2 partition of D); -1 takes V1 when 2b <= w and none otherwise
+ * (V2 measured slower than no look-ahead at b = w), 2 asks for V2.  work, dev_status,
  * return codes: as for bandred_ge2gb_ex.
  */
 size_t bandred_ge2bb_workspace(int64_t m, int64_t n, int64_t w, const bandred_opts* opts);

@@ -1472,16 +1472,18 @@ struct Ge2bb {
   bool lq(int64_t k) const { return bl_of(k) > 0 && jl_of(k) >= 2; }
   bool rq(int64_t k) const { return br_of(k) > 0 && jr_of(k) >= 2; }
 
-  // QR of the column panel and LQ of the row panel of iteration k into buffer q.
-  int panels(int64_t k, int q, cudaStream_t s) {
+  // QR of the column panel and LQ of the row panel of iteration k into buffer q; ctas > 0
+  // caps their CTAs.
+  int panels(int64_t k, int q, cudaStream_t s, int ctas = 0) {
     Ge2gbWs& ws = R.ws;
+    const int pm = ctas > 0 ? std::min(ctas, R.pmax) : R.pmax;
     int rc;
     if (lq(k)) {
       const int jl = jl_of(k), bl = bl_of(k);
       prof::Scope sc(prof::kPanel, s, panel_flops(jl, bl), panel_bytes(jl, bl));
       prof::TraceScope tr(prof::kTracePanel, k);
       if ((rc = run_panel(R.A + (k + w) + k * R.lda, 1, R.lda, jl, bl, R.tauq + k, ws.Yu[q], ws.Wu[q], ws.ldu, ws.part,
-                          ws.rowbuf, ws.gram, ws.gs, R.status, R.o, R.pmax, 0u, s, &ws.pw)))
+                          ws.rowbuf, ws.gram, ws.gs, R.status, R.o, pm, 0u, s, &ws.pw)))
         return rc;
     }
     if (rq(k)) {
@@ -1489,7 +1491,7 @@ struct Ge2bb {
       prof::Scope sc(prof::kPanel, s, panel_flops(jr, br), panel_bytes(jr, br));
       prof::TraceScope tr(prof::kTracePanelRow, k);
       if ((rc = run_panel(R.A + k + (k + w) * R.lda, R.lda, 1, jr, br, R.taup + k, ws.Yv[q], ws.Wv[q], ws.ldv, ws.part,
-                          ws.rowbuf, ws.gram, ws.gs, R.status, R.o, R.pmax, 0u, s, &ws.pw)))
+                          ws.rowbuf, ws.gram, ws.gs, R.status, R.o, pm, 0u, s, &ws.pw)))
         return rc;
     }
     return 0;
@@ -1542,7 +1544,7 @@ struct Ge2bb {
   // D(r0:r1, c0:c1) += X Y_R^T + Y_L Z_L^T on those rows and columns (Eq. gebrd_2k).  With
   // the Ozaki precision one rank-(br + bl) update of [X | Y_L] and [Y_R | Z_L], balanced by a
   // power of two between the halves (X and Z_L carry the matrix's scale, |Y| <= 1).
-  int d_rank(int64_t k, int q, int r0, int r1, int c0, int c1, int qs, cudaStream_t s) {
+  int d_rank(int64_t k, int q, int r0, int r1, int c0, int c1, int qs, cudaStream_t s, int max_ctas = 0) {
     const int bl = bl_of(k), br = br_of(k), jl = jl_of(k), jr = jr_of(k);
     const bool l = lq(k), r = rq(k);
     r1 = std::min(r1, jl);
@@ -1563,12 +1565,13 @@ struct Ge2bb {
       ro.shsign = -1;
       const ozaki::Bufs rb = ozaki::carve(ws.ozr[qs], M, N, br + bl, 1);
       CK(ozaki::prepare(lo, ro, rb, s));
-      CK(ozaki::rank_apply(M, N, br + bl, 1.0, D, R.lda, 0, N, 0, rb, R.status, R.o.limit_ns, s));
+      CK(ozaki::rank_apply(M, N, br + bl, 1.0, D, R.lda, 0, N, 0, rb, R.status, R.o.limit_ns, s, max_ctas));
       return 0;
     }
     int rc;
-    if (r && (rc = R.rank_k(M, N, br, ws.P + r0, ws.ldu, ws.Yv[q] + c0, ws.ldv, D, R.lda, qs, s))) return rc;
-    if (l && (rc = R.rank_k(M, N, bl, ws.Yu[q] + r0, ws.ldu, ws.ZT + c0, ws.ldv, D, R.lda, qs, s))) return rc;
+    if (r && (rc = R.rank_k(M, N, br, ws.P + r0, ws.ldu, ws.Yv[q] + c0, ws.ldv, D, R.lda, qs, s, max_ctas))) return rc;
+    if (l && (rc = R.rank_k(M, N, bl, ws.Yu[q] + r0, ws.ldu, ws.ZT + c0, ws.ldv, D, R.lda, qs, s, max_ctas)))
+      return rc;
     return 0;
   }
 
@@ -1584,9 +1587,13 @@ struct Ge2bb {
 
 }  // namespace
 
+// Auto (-1): V1 when 2b <= w; no look-ahead otherwise (at m = n = 8192, w = b = 64 the V2
+// schedule measured 174 ms against 160 ms without: its two extra block updates of D cost
+// more than the panels' overlap saves); 2 asks for V2 explicitly.
 static int ge2bb_variant(const Options& o, int64_t w) {
   int la = o.lookahead;
-  if (la < 0) la = (2 * o.b > w) ? 2 : 1;
+  if (la < 0) la = (2 * o.b > w) ? 0 : 1;
+  if (la == 0) return 0;
   if (la == 1 && 2 * o.b > w) la = 2;
   if (la == 2 && 2 * o.b <= w) la = 1;
   return la;
@@ -1674,13 +1681,20 @@ int ge2bb_run(int64_t m, int64_t n, int64_t w, double* A, int64_t lda, double* t
       continue;
     }
     const int t = (int)(2 * b - w);
+    // with the Ozaki precision the panel stream (its blocks of D, then the panels) holds P
+    // SMs and D(t:, t:) the others, by the look-ahead model with the rank-(bl + br) update
+    const int jn = std::max(G.jl_of(kn), G.jr_of(kn)), jd = std::max(G.jl_of(k), G.jr_of(k));
+    const int P = o.precision == BANDRED_OZAKI && jn > 1
+                      ? lookahead_panel_ctas(jn, b, jd, 2 * b, R.sms, o.panel_ctas, cluster_panels(o))
+                      : 0;
+    const int rest = P > 0 && P < R.sms ? R.sms - P : 0;
     CK(cudaEventRecord(ev_fork, s));
     CK(cudaStreamWaitEvent(sp, ev_fork, 0));
-    if ((rc = G.d_rank(k, buf, 0, (int)m, 0, t, 1, sp))) return rc;  // D(:, 0:t)
-    if ((rc = G.d_rank(k, buf, 0, t, t, (int)n, 1, sp))) return rc;  // D(0:t, t:)
-    if ((rc = G.panels(kn, buf ^ 1, sp))) return rc;
+    if ((rc = G.d_rank(k, buf, 0, (int)m, 0, t, 1, sp, P))) return rc;  // D(:, 0:t)
+    if ((rc = G.d_rank(k, buf, 0, t, t, (int)n, 1, sp, P))) return rc;  // D(0:t, t:)
+    if ((rc = G.panels(kn, buf ^ 1, sp, P))) return rc;
     CK(cudaEventRecord(ev_panel, sp));
-    if ((rc = G.d_rank(k, buf, t, (int)m, t, (int)n, 0, s))) return rc;  // D(t:, t:)
+    if ((rc = G.d_rank(k, buf, t, (int)m, t, (int)n, 0, s, rest))) return rc;  // D(t:, t:)
   }
   CK(cudaEventRecord(ev_fork, sp));
   CK(cudaStreamWaitEvent(s, ev_fork, 0));

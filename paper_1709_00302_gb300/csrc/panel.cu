@@ -494,11 +494,13 @@ int panel_geometry(int j, int bk, int max_ctas, int min_rows, int* G, int* R, in
   int r = (j + g - 1) / g;
   g = (j + r - 1) / r;  // every CTA owns at least one row
   int rp = r | 1;       // odd stride: conflict-free strided shared-memory access
-  if (panel_smem_bytes(bk, rp, false) > 227 * 1024) return -2;
+  // the opt-in limit (227 KB) less a kilobyte for the kernel's static shared memory
+  constexpr size_t kDynMax = 226 * 1024;
+  if (panel_smem_bytes(bk, rp, false) > kDynMax) return -2;
   *G = g;
   *R = r;
   *Rp = rp;
-  *w_in_smem = panel_smem_bytes(bk, rp, true) <= 227 * 1024;
+  *w_in_smem = panel_smem_bytes(bk, rp, true) <= kDynMax;
   return 0;
 }
 

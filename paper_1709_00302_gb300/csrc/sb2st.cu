@@ -449,9 +449,14 @@ __global__ void __launch_bounds__(kChaseThreads) sb2st_chase_smem_kernel(ChasePa
         __syncthreads();
         if (tid < len) pd[tid] = fma(-s_half, v[tid], pd[tid]);
         __syncthreads();
-        for (int q = tid; q < len * len; q += kChaseThreads) {
-          const int k = q / len, i = q - k * len;
-          if (i >= k) sD[k * kSLd + i] = fma(-v[i], pd[k], fma(-pd[i], v[k], sD[k * kSLd + i]));
+        // over the packed lower triangle only (each FP64 warp instruction costs the same
+        // whatever the number of active lanes): row-major index q = i (i + 1) / 2 + k
+        for (int q = tid; q < len * (len + 1) / 2; q += kChaseThreads) {
+          int i = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
+          while (i * (i + 1) / 2 > q) --i;
+          while ((i + 1) * (i + 2) / 2 <= q) ++i;
+          const int k = q - i * (i + 1) / 2;
+          sD[k * kSLd + i] = fma(-v[i], pd[k], fma(-pd[i], v[k], sD[k * kSLd + i]));
         }
         __syncthreads();
         // write back what changed

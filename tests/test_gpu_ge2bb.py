@@ -8,7 +8,8 @@ reflector vectors and the tau at 1e-10.  bf16x6 is checked through the singular 
 the band at its stated tolerance.  Shapes cover tall, wide and square matrices, b < w and
 b = w, ragged last blocks, and the degenerate cases where only one side (or neither) has
 reflectors, each without look-ahead and with it (Variant V1 for 2b <= w: the next panels
-inside B1 and C1; Variant V2 otherwise: inside the first t = 2b - w columns and rows of D).
+inside B1 and C1; Variant V2 otherwise, asked for with lookahead = 2: inside the first
+t = 2b - w columns and rows of D).
 """
 import numpy as np
 import pytest
@@ -46,7 +47,7 @@ def run(br, A, w, **kw):
     return dA, tq, tp
 
 
-@pytest.mark.parametrize("lookahead", [0, -1])
+@pytest.mark.parametrize("lookahead", [0, -1, 2])
 @pytest.mark.parametrize("precision", ["fp64", "ozaki"])
 @pytest.mark.parametrize("m,n,w,b", SHAPES)
 def test_ge2bb_matches_oracle(br, m, n, w, b, precision, lookahead):
