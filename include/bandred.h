@@ -394,13 +394,23 @@ int bandred_trace_begin(void* buf, size_t bytes);
 int bandred_trace_end(bandred_trace_record* out, int max_records);
 
 /* Phase timing of one panel (a diagnostic of the panel's latency).  Arms the next panel
- * factorisation that runs as a cooperative grid (a panel of more than 512 rows with the
- * default pairs of reflectors): its CTA 0 writes the SM clock (clock64) at 8 points of
+ * factorisation that runs as a cooperative grid (every panel of the single-matrix
+ * reductions with the default pairs of reflectors): its CTA 0 writes the SM clock (clock64) at 8 points of
  * each step into buf[8 step + q], for steps < max_steps: q = 0 step start, 1 dot products
  * summed, 2 arrival at the grid barrier, 3 barrier passed, 4 reflectors derived, 5 the
  * in-panel update done, 6 step end.  buf: device, 8 * max_steps int64 (slots not written
  * keep their contents).  One panel per call; returns 0 or a negative code. */
 int bandred_panel_phase_trace(void* buf, int max_steps);
+
+/* Phase timing of the bulge chase (a diagnostic of bandred_sb2st's step latency).  Arms
+ * the next bandred_sb2st with w <= 64: the CTA running sweep (n - 2) / 2 writes the SM
+ * clock (clock64) at 8 points of each of its steps into buf[8 step + q], for steps <
+ * max_steps: q = 0 step start, 1 the wait for the previous sweep passed, 2 the column
+ * staged (the blocks' loads in flight), 3 reflector formed and the blocks in shared
+ * memory, 4 one-sided blocks and the diagonal matvec done, 7 those blocks written back and
+ * K formed, 5 the diagonal block's rank-2 update written back, 6 the step released.  buf:
+ * device, 8 * max_steps int64.  One call; returns 0 or a negative code. */
+int bandred_sb2st_phase_trace(void* buf, int max_steps);
 
 /* ---------------------------------------------------------------- diagnostics -------
  * The reciprocal square root and reciprocal that the panel kernels use in place of FP64

@@ -143,6 +143,8 @@ def lib():
         L.bandred_trace_end.restype = ci
         L.bandred_panel_phase_trace.argtypes = [vp, ci]
         L.bandred_panel_phase_trace.restype = ci
+        L.bandred_sb2st_phase_trace.argtypes = [vp, ci]
+        L.bandred_sb2st_phase_trace.restype = ci
         L.bandred_form_workspace.argtypes = [i64, op]
         L.bandred_form_workspace.restype = sz
         L.bandred_sy2sb_form_q.argtypes = [i64, i64, vp, i64, vp, vp, i64, op, vp, sz, vp, vp]
@@ -546,6 +548,12 @@ def sterf(d, e, stream=None):
 def bandred_panel_phase_trace(buf) -> int:
     """Arms the phase timing of the next grid panel into the device int64 tensor buf (8 per step)."""
     return lib().bandred_panel_phase_trace(_ptr(buf), buf.numel() // 8)
+
+
+def bandred_sb2st_phase_trace(buf) -> int:
+    """Arms the phase timing of the next bulge chase (its middle sweep) into the device int64
+    tensor buf (8 per step)."""
+    return lib().bandred_sb2st_phase_trace(_ptr(buf), buf.numel() // 8)
 
 
 def bandred_newton_eval(x, rsqrt=None, rcp=None, stream=None) -> int:

@@ -111,6 +111,20 @@ long long* phase_take(int* steps) {
   return p;
 }
 
+namespace {
+long long* g_chase_buf = nullptr;
+int g_chase_steps = 0;
+}  // namespace
+
+long long* chase_phase_take(int* steps) {
+  std::lock_guard<std::mutex> lock(g_pmu);
+  long long* p = g_chase_buf;
+  *steps = g_chase_steps;
+  g_chase_buf = nullptr;
+  g_chase_steps = 0;
+  return p;
+}
+
 }  // namespace prof
 }  // namespace bandred
 
@@ -172,6 +186,14 @@ int bandred_panel_phase_trace(void* buf, int max_steps) {
   std::lock_guard<std::mutex> lock(g_pmu);
   g_phase_buf = static_cast<long long*>(buf);
   g_phase_steps = max_steps;
+  return 0;
+}
+
+int bandred_sb2st_phase_trace(void* buf, int max_steps) {
+  if (max_steps < 0 || (max_steps > 0 && !buf)) return -2;
+  std::lock_guard<std::mutex> lock(bandred::prof::g_pmu);
+  bandred::prof::g_chase_buf = static_cast<long long*>(buf);
+  bandred::prof::g_chase_steps = max_steps;
   return 0;
 }
 

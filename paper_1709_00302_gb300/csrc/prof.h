@@ -46,6 +46,8 @@ class TraceScope {
 unsigned long long* trace_take();
 // The armed phase buffer of bandred_panel_phase_trace (taken by the next grid panel), or nullptr.
 long long* phase_take(int* steps);
+// The armed buffer of bandred_sb2st_phase_trace (taken by the next bulge chase), or nullptr.
+long long* chase_phase_take(int* steps);
 
 }  // namespace prof
 }  // namespace bandred

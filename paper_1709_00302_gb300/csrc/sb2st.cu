@@ -48,6 +48,8 @@ struct ChaseParams {
   int* prog;          // prog[c]: steps sweep c has finished (kDone when finished)
   int* status;
   unsigned long long limit_ns;
+  long long* phases;  // diagnostic: clock64 at 8 points of each step of sweep phase_sweep, or nullptr
+  int phase_steps, phase_sweep;
 };
 
 // Loads go to L2 (ld.cg): another CTA may have changed a line this SM read before.
@@ -57,6 +59,16 @@ __device__ __forceinline__ double ldb(const ChaseParams& p, int i, int k) {
 __device__ __forceinline__ void stb(const ChaseParams& p, int i, int k, double x) {
   p.Bs[(int64_t)(i - k) + (int64_t)k * p.LB] = x;
 }
+// q / d for 0 <= q < 2^20, 1 <= d <= 128, from the FP32 reciprocal rd of d plus one
+// integer correction each way (the product is within one of the quotient): the staging
+// loops divide by the block's runtime row count many times a step
+__device__ __forceinline__ int fdiv(int q, int d, float rd) {
+  int j = __float2int_rz((float)q * rd);
+  j += (j + 1) * d <= q;
+  j -= j * d > q;
+  return j;
+}
+
 // symmetric read of the band store (either triangle)
 __device__ __forceinline__ double bsym(const ChaseParams& p, int i, int k) {
   return i >= k ? ldb(p, i, k) : ldb(p, k, i);
@@ -282,6 +294,10 @@ __global__ void __launch_bounds__(kChaseThreads) sb2st_chase_smem_kernel(ChasePa
     while (true) {
       const int end = min(s + w, n), len = end - s;
       if (len < 2) break;
+      auto stamp = [&](int q) {
+        if (p.phases && c == p.phase_sweep && tid == 0 && t < p.phase_steps) p.phases[t * 8 + q] = clock64();
+      };
+      stamp(0);
       if (tid == 0) {
         int ok = 1;
         if (c > 0) {
@@ -304,46 +320,48 @@ __global__ void __launch_bounds__(kChaseThreads) sb2st_chase_smem_kernel(ChasePa
       }
       __syncthreads();
       if (!s_ok) return;
+      stamp(1);
       const int nb = s - col - 1, nl = min(end + w, n) - end;
-      // stage: the column, the bulge columns, the diagonal block, the rows below.  Every
-      // load of the step is issued before any is used (one round trip to L2): each block
-      // has at most kSMaxW^2 = 16 x kChaseThreads entries, sixteen per thread.
+      const float rlen = 1.0f / (float)len, rnl = nl > 0 ? 1.0f / (float)nl : 0.0f;
+      // Stage the column, then the bulge columns, the diagonal block and the rows below:
+      // every load of the step is issued at once (each block has at most
+      // kSMaxW^2 = 16 x kChaseThreads entries, sixteen per thread) and lands in registers
+      // while warp 0 forms the reflector from the column; the other warps move theirs to
+      // shared memory meanwhile, warp 0 after the reflector.
+      constexpr int kPer = kSMaxW * kSMaxW / kChaseThreads;
+      double rb[kPer], rd[kPer], rl[kPer];
       {
-        constexpr int kPer = kSMaxW * kSMaxW / kChaseThreads;
-        double rb[kPer], rd[kPer], rl[kPer];
         const double xs = tid < len ? ldb(p, s + tid, col) : 0.0;
 #pragma unroll
         for (int u = 0; u < kPer; ++u) {
           const int q = tid + u * kChaseThreads;
-          const int j = q / len, i = q - j * len;
+          const int j = fdiv(q, len, rlen), i = q - j * len;
           rb[u] = q < nb * len ? ldb(p, s + i, col + 1 + j) : 0.0;
-          const int k = q / len, i2 = q - k * len;
-          rd[u] = (q < len * len && i2 >= k) ? ldb(p, s + i2, s + k) : 0.0;
-          const int kl = nl > 0 ? q / nl : 0, r = nl > 0 ? q - kl * nl : 0;
+          rd[u] = (q < len * len && i >= j) ? ldb(p, s + i, s + j) : 0.0;
+          const int kl = nl > 0 ? fdiv(q, nl, rnl) : 0, r = nl > 0 ? q - kl * nl : 0;
           rl[u] = (nl > 0 && q < nl * len) ? ldb(p, end + r, s + kl) : 0.0;
         }
         if (tid < len) sx[tid] = xs;
+      }
+      __syncthreads();
+      stamp(2);
+      auto park = [&]() {  // the staged blocks into shared memory
 #pragma unroll
         for (int u = 0; u < kPer; ++u) {
           const int q = tid + u * kChaseThreads;
-          if (q < nb * len) {
-            const int j = q / len, i = q - j * len;
-            sB[j * kSLd + i] = rb[u];
-          }
-          if (q < len * len) {
-            const int k = q / len, i2 = q - k * len;
-            if (i2 >= k) {
-              sD[k * kSLd + i2] = rd[u];
-              sD[i2 * kSLd + k] = rd[u];
-            }
+          const int j = fdiv(q, len, rlen), i = q - j * len;
+          if (q < nb * len) sB[j * kSLd + i] = rb[u];
+          if (q < len * len && i >= j) {
+            sD[j * kSLd + i] = rd[u];
+            sD[i * kSLd + j] = rd[u];
           }
           if (nl > 0 && q < nl * len) {
-            const int kl = q / nl, r = q - kl * nl;
+            const int kl = fdiv(q, nl, rnl), r = q - kl * nl;
             sL[r * kSLd + kl] = rl[u];
           }
         }
-      }
-      __syncthreads();
+      };
+      if (tid >= 32) park();
       // the reflector (warp 0), larfg convention.  Common path: the plain sum of squares
       // when it and |alpha| are safely in range (max |x2| from the bit patterns, integer
       // compares), then h = ||x|| = q / sqrt(q), tau = 1 + |alpha| / h and
@@ -397,9 +415,11 @@ __global__ void __launch_bounds__(kChaseThreads) sb2st_chase_smem_kernel(ChasePa
           s_beta = beta;
           s_scal = scal;
         }
+        park();
       }
       __syncthreads();
       const double tau = s_tau;
+      stamp(3);
       if (tid < len) v[tid] = tid == 0 ? 1.0 : sx[tid] * s_scal;
       for (int i = tid; i < len; i += kChaseThreads) stb(p, s + i, col, i == 0 ? s_beta : 0.0);
       __syncthreads();
@@ -439,45 +459,46 @@ __global__ void __launch_bounds__(kChaseThreads) sb2st_chase_smem_kernel(ChasePa
           pd[i] = tau * (y0 + y1);
         }
         __syncthreads();
+        stamp(4);
+        // warp 0 forms p.v while the others write the final bulge columns and rows below back
         if (tid < 32) {
           double pv = 0.0;
           for (int i = lane; i < len; i += 32) pv = fma(pd[i], v[i], pv);
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) pv += __shfl_xor_sync(0xffffffffu, pv, o);
           if (lane == 0) s_half = 0.5 * tau * pv;
+        } else {
+          for (int q = tid - 32; q < nb * len; q += kChaseThreads - 32) {
+            const int j = fdiv(q, len, rlen), i = q - j * len;
+            stb(p, s + i, col + 1 + j, sB[j * kSLd + i]);
+          }
+          for (int q = tid - 32; q < nl * len; q += kChaseThreads - 32) {
+            const int k = fdiv(q, nl, rnl), r = q - k * nl;
+            stb(p, end + r, s + k, sL[r * kSLd + k]);
+          }
         }
         __syncthreads();
         if (tid < len) pd[tid] = fma(-s_half, v[tid], pd[tid]);
         __syncthreads();
-        // over the packed lower triangle only (each FP64 warp instruction costs the same
-        // whatever the number of active lanes): row-major index q = i (i + 1) / 2 + k
+        stamp(7);
+        // the diagonal block's rank-2 update over the packed lower triangle only (each FP64
+        // warp instruction costs the same whatever the number of active lanes), row-major
+        // index q = i (i + 1) / 2 + k, written straight back
         for (int q = tid; q < len * (len + 1) / 2; q += kChaseThreads) {
           int i = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
           while (i * (i + 1) / 2 > q) --i;
           while ((i + 1) * (i + 2) / 2 <= q) ++i;
           const int k = q - i * (i + 1) / 2;
-          sD[k * kSLd + i] = fma(-v[i], pd[k], fma(-pd[i], v[k], sD[k * kSLd + i]));
+          stb(p, s + i, s + k, fma(-v[i], pd[k], fma(-pd[i], v[k], sD[k * kSLd + i])));
         }
-        __syncthreads();
-        // write back what changed
-        for (int q = tid; q < nb * len; q += kChaseThreads) {
-          const int j = q / len, i = q - j * len;
-          stb(p, s + i, col + 1 + j, sB[j * kSLd + i]);
-        }
-        for (int q = tid; q < len * len; q += kChaseThreads) {
-          const int k = q / len, i = q - k * len;
-          if (i >= k) stb(p, s + i, s + k, sD[k * kSLd + i]);
-        }
-        for (int q = tid; q < nl * len; q += kChaseThreads) {
-          const int k = q / nl, r = q - k * nl;
-          stb(p, end + r, s + k, sL[r * kSLd + k]);
-        }
+        stamp(5);
       }
       __syncthreads();
       if (tid == 0) {
         __threadfence();
         st_release_int(&p.prog[c], t + 1);
       }
+      stamp(6);
       col = s;
       s += w;
       ++t;
@@ -666,7 +687,9 @@ int sb2st_run(int64_t n, int64_t w, const double* A, int64_t lda, double* d, dou
     // one CTA per SM (each sweep's FP64 work keeps its SM's FP64 units busy), all
     // co-resident: the cooperative launch guarantees it
     const int G = (int)std::min<int64_t>(n - 2, sms);
-    ChaseParams p{(int)n, (int)w, LB, ws.Bs, ws.prog, status, limit_ns};
+    ChaseParams p{(int)n, (int)w, LB, ws.Bs, ws.prog, status, limit_ns, nullptr, 0, 0};
+    p.phases = prof::chase_phase_take(&p.phase_steps);
+    p.phase_sweep = (int)((n - 2) / 2);
     void* args[] = {&p};
     prof::count_launch();
     if (w <= kSMaxW) {
