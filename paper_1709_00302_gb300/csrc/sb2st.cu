@@ -268,29 +268,73 @@ __global__ void __launch_bounds__(kChaseThreads) sb2st_chase_kernel(ChaseParams 
   }
 }
 
-// The same chase with each step's three blocks staged in shared memory (w <= 64): all
-// threads load the bulge columns, the symmetric diagonal block and the rows below in one
-// round of L2 loads, the step runs in shared memory with one thread per vector (no warp
-// reductions: every FP64 instruction does useful work), and the blocks go back at the
-// end.  Strides of kSLd = 65 doubles keep the per-thread vectors conflict-free.
+// The same chase with the step's blocks in shared memory (w <= 64), one thread per
+// vector (no warp reductions: every FP64 instruction does useful work).
+//
+// Carry.  After step t's right application, the rows below its range, B(end : end + w,
+// s : end), are exactly the column that step t + 1 annihilates (their first column) and
+// step t + 1's bulge columns (the others), and nothing else writes them in between (the
+// sweep before has finished with them, the sweep after waits for step t + 1).  So they
+// stay in shared memory and reach global memory once, as step t + 1's bulge columns.
+//
+// Prefetch.  Step t + 1's own blocks (its diagonal block and the rows below it) have
+// column indices from end on, which step t does not write; of the sweep before, only
+// its step t + 3 writes any of them (column end + w - 1 at rows from end + 2w - 1, the
+// last column of the rows below).  So step t issues their loads into registers as soon
+// as its own wait is over, parks them in shared memory after its phase A, and step
+// t + 1 reloads the last column of its rows below after its wait.
+//
+// Buffers: two diagonal blocks (lower triangle, (i, k) at k * kSLd + i) and three
+// rows-below blocks ((r, k) at r * kSLd + k) used in turn: this step's, the carried one
+// of the step before, and the next step's.  A thread per row and a thread per carried
+// column both see stride-1 or stride-65 addresses, free of bank conflicts.
 constexpr int kSMaxW = 64;
 constexpr int kSLd = kSMaxW + 1;
-constexpr size_t kSmemChase = sizeof(double) * (3 * (size_t)kSMaxW * kSLd + 3 * kSMaxW);
+constexpr size_t kSBlk = (size_t)kSMaxW * kSLd;
+constexpr size_t kSmemChase = sizeof(double) * (5 * kSBlk + 4 * kSMaxW);
+constexpr int kSPer = kSMaxW * kSMaxW / kChaseThreads;  // block entries per thread
+static_assert(kChaseThreads == 4 * kSMaxW, "phase A gives 64 threads to each of four jobs");
 
 __global__ void __launch_bounds__(kChaseThreads) sb2st_chase_smem_kernel(ChaseParams p) {
   extern __shared__ double cs_smem[];
-  double* sB = cs_smem;                         // bulge column j, row i at j * kSLd + i
-  double* sD = sB + (size_t)kSMaxW * kSLd;      // diagonal block, (i, k) at k * kSLd + i (both triangles)
-  double* sL = sD + (size_t)kSMaxW * kSLd;      // row r below the range, column k at r * kSLd + k
-  double* v = sL + (size_t)kSMaxW * kSLd;       // the reflector
-  double* pd = v + kSMaxW;                      // tau B(R, R) v, then K
-  double* sx = pd + kSMaxW;                     // the column to annihilate
+  double* sD0 = cs_smem;                 // two diagonal blocks
+  double* sL0 = sD0 + 2 * kSBlk;         // three blocks of rows below
+  double* v = sL0 + 3 * kSBlk;           // the reflector
+  double* pd = v + kSMaxW;               // tau B(R, R) v, then K
+  double* pa = pd + kSMaxW;              // B(R, R) v over the first and second half of k
+  double* pb = pa + kSMaxW;
   __shared__ double s_tau, s_beta, s_scal, s_half;
   __shared__ int s_ok;
   const int tid = threadIdx.x, lane = tid & 31;
   const int n = p.n, w = p.w;
+  double rd[kSPer], rl[kSPer];  // one step's blocks on their way to shared memory
+  // loads of the blocks of the step with range [sx, sx + lx) and nx rows below
+  auto fetch = [&](int sx, int lx, int nx) {
+    const float rx = 1.0f / (float)lx, ry = nx > 0 ? 1.0f / (float)nx : 0.0f;
+#pragma unroll
+    for (int u = 0; u < kSPer; ++u) {
+      const int q = tid + u * kChaseThreads;
+      const int j = fdiv(q, lx, rx), i = q - j * lx;
+      rd[u] = (q < lx * lx && i >= j) ? ldb(p, sx + i, sx + j) : 0.0;
+      const int kl = nx > 0 ? fdiv(q, nx, ry) : 0, r = nx > 0 ? q - kl * nx : 0;
+      rl[u] = (nx > 0 && q < nx * lx) ? ldb(p, sx + lx + r, sx + kl) : 0.0;
+    }
+  };
+  auto park = [&](double* D, double* L, int lx, int nx) {
+    const float rx = 1.0f / (float)lx, ry = nx > 0 ? 1.0f / (float)nx : 0.0f;
+#pragma unroll
+    for (int u = 0; u < kSPer; ++u) {
+      const int q = tid + u * kChaseThreads;
+      const int j = fdiv(q, lx, rx), i = q - j * lx;
+      if (q < lx * lx && i >= j) D[j * kSLd + i] = rd[u];
+      if (nx > 0 && q < nx * lx) {
+        const int kl = fdiv(q, nx, ry), r = q - kl * nx;
+        L[r * kSLd + kl] = rl[u];
+      }
+    }
+  };
   for (int c = blockIdx.x; c + 2 < n; c += gridDim.x) {
-    int col = c, s = c + 1, t = 0;
+    int col = c, s = c + 1, t = 0, li = 0;  // li = t mod 3
     while (true) {
       const int end = min(s + w, n), len = end - s;
       if (len < 2) break;
@@ -321,47 +365,33 @@ __global__ void __launch_bounds__(kChaseThreads) sb2st_chase_smem_kernel(ChasePa
       __syncthreads();
       if (!s_ok) return;
       stamp(1);
+      // nb = s - col - 1 bulge columns (0 at t = 0, else w - 1); nl rows below, which is
+      // the next step's len: the step after this one runs iff nl >= 2
       const int nb = s - col - 1, nl = min(end + w, n) - end;
-      const float rlen = 1.0f / (float)len, rnl = nl > 0 ? 1.0f / (float)nl : 0.0f;
-      // Stage the column, then the bulge columns, the diagonal block and the rows below:
-      // every load of the step is issued at once (each block has at most
-      // kSMaxW^2 = 16 x kChaseThreads entries, sixteen per thread) and lands in registers
-      // while warp 0 forms the reflector from the column; the other warps move theirs to
-      // shared memory meanwhile, warp 0 after the reflector.
-      constexpr int kPer = kSMaxW * kSMaxW / kChaseThreads;
-      double rb[kPer], rd[kPer], rl[kPer];
-      {
+      const bool next = nl >= 2;
+      const int nl1 = next ? min(end + nl + w, n) - (end + nl) : 0;  // the next step's rows below
+      double* Dc = sD0 + (size_t)(t & 1) * kSBlk;
+      double* Dn = sD0 + (size_t)((t + 1) & 1) * kSBlk;
+      double* Lc = sL0 + (size_t)li * kSBlk;                         // this step's rows below
+      double* Ln = sL0 + (size_t)(li == 2 ? 0 : li + 1) * kSBlk;     // the next step's
+      double* Lp = sL0 + (size_t)(li == 0 ? 2 : li - 1) * kSBlk;     // carried: x at (i, 0), bulge column j at (i, 1 + j)
+      const float rlen = 1.0f / (float)len;
+      if (t == 0) {  // this step's blocks and the column, from global memory
         const double xs = tid < len ? ldb(p, s + tid, col) : 0.0;
-#pragma unroll
-        for (int u = 0; u < kPer; ++u) {
-          const int q = tid + u * kChaseThreads;
-          const int j = fdiv(q, len, rlen), i = q - j * len;
-          rb[u] = q < nb * len ? ldb(p, s + i, col + 1 + j) : 0.0;
-          rd[u] = (q < len * len && i >= j) ? ldb(p, s + i, s + j) : 0.0;
-          const int kl = nl > 0 ? fdiv(q, nl, rnl) : 0, r = nl > 0 ? q - kl * nl : 0;
-          rl[u] = (nl > 0 && q < nl * len) ? ldb(p, end + r, s + kl) : 0.0;
-        }
-        if (tid < len) sx[tid] = xs;
+        fetch(s, len, nl);
+        if (tid < len) Lp[tid * kSLd] = xs;
+        park(Dc, Lc, len, nl);
+        if (next) fetch(end, nl, nl1);
+        __syncthreads();
+      } else {
+        // the last column of the rows below, which the sweep before could write until
+        // this step's wait; then the next step's blocks
+        const int r = tid - 32;
+        const double xr = (r >= 0 && r < nl) ? ldb(p, end + r, end - 1) : 0.0;
+        if (next) fetch(end, nl, nl1);
+        if (r >= 0 && r < nl) Lc[r * kSLd + len - 1] = xr;
       }
-      __syncthreads();
       stamp(2);
-      auto park = [&]() {  // the staged blocks into shared memory
-#pragma unroll
-        for (int u = 0; u < kPer; ++u) {
-          const int q = tid + u * kChaseThreads;
-          const int j = fdiv(q, len, rlen), i = q - j * len;
-          if (q < nb * len) sB[j * kSLd + i] = rb[u];
-          if (q < len * len && i >= j) {
-            sD[j * kSLd + i] = rd[u];
-            sD[i * kSLd + j] = rd[u];
-          }
-          if (nl > 0 && q < nl * len) {
-            const int kl = fdiv(q, nl, rnl), r = q - kl * nl;
-            sL[r * kSLd + kl] = rl[u];
-          }
-        }
-      };
-      if (tid >= 32) park();
       // the reflector (warp 0), larfg convention.  Common path: the plain sum of squares
       // when it and |alpha| are safely in range (max |x2| from the bit patterns, integer
       // compares), then h = ||x|| = q / sqrt(q), tau = 1 + |alpha| / h and
@@ -370,7 +400,7 @@ __global__ void __launch_bounds__(kChaseThreads) sb2st_chase_smem_kernel(ChasePa
         unsigned long long um = 0ull;
         double ss = 0.0;
         for (int i = 1 + lane; i < len; i += 32) {
-          const double x = sx[i];
+          const double x = Lp[i * kSLd];
           const unsigned long long u = (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
           um = u > um ? u : um;
           ss = fma(x, x, ss);
@@ -381,13 +411,13 @@ __global__ void __launch_bounds__(kChaseThreads) sb2st_chase_smem_kernel(ChasePa
           um = u > um ? u : um;
           ss += __shfl_xor_sync(0xffffffffu, ss, o);
         }
-        const double amax = __longlong_as_double((long long)um), alpha = sx[0];
+        const double amax = __longlong_as_double((long long)um), alpha = Lp[0];
         const bool plain = amax > 0x1p-450 && ss < 0x1p1000 && fabs(alpha) < 0x1p500;
         if (amax > 0.0 && !plain) {  // rare: scaled sum (warp-uniform branch)
           const double inv = 1.0 / amax;
           ss = 0.0;
           for (int i = 1 + lane; i < len; i += 32) {
-            const double q = sx[i] * inv;
+            const double q = Lp[i * kSLd] * inv;
             ss = fma(q, q, ss);
           }
 #pragma unroll
@@ -415,68 +445,99 @@ __global__ void __launch_bounds__(kChaseThreads) sb2st_chase_smem_kernel(ChasePa
           s_beta = beta;
           s_scal = scal;
         }
-        park();
       }
       __syncthreads();
       const double tau = s_tau;
       stamp(3);
-      if (tid < len) v[tid] = tid == 0 ? 1.0 : sx[tid] * s_scal;
+      if (tid < len) v[tid] = tid == 0 ? 1.0 : Lp[tid * kSLd] * s_scal;
       for (int i = tid; i < len; i += kChaseThreads) stb(p, s + i, col, i == 0 ? s_beta : 0.0);
       __syncthreads();
+      // the bulge columns (their final values) and, when no step follows, the rows below
+      // go to global memory; the rows below otherwise stay for the next step
+      auto write_back = [&](int t0, int nt) {
+        for (int q = t0; q < nb * len; q += nt) {
+          const int j = fdiv(q, len, rlen), i = q - j * len;
+          stb(p, s + i, col + 1 + j, Lp[i * kSLd + 1 + j]);
+        }
+        if (nl == 1) {
+          for (int k = t0; k < len; k += nt) stb(p, end, s + k, Lc[k]);
+        }
+      };
+      // x -= z v over len entries at stride ld (a bulge column or a row below), eight at a
+      // time so that the loads are not held behind the stores
+      auto axpy = [&](double* b, int ld, double z) {
+        for (int i0 = 0; i0 < len; i0 += 8) {
+          double bb[8], vv[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int i = min(i0 + u, len - 1);
+            bb[u] = b[i * ld];
+            vv[u] = v[i];
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            if (i0 + u < len) b[(i0 + u) * ld] = fma(-z, vv[u], bb[u]);
+          }
+        }
+      };
+      auto dot = [&](const double* b, int ld) {
+        double z0 = 0.0, z1 = 0.0;
+        int i = 0;
+        for (; i + 1 < len; i += 2) {
+          z0 = fma(v[i], b[i * ld], z0);
+          z1 = fma(v[i + 1], b[(i + 1) * ld], z1);
+        }
+        if (i < len) z0 = fma(v[i], b[i * ld], z0);
+        return z0 + z1;
+      };
       if (tau != 0.0) {
-        // one thread per vector: bulge column (left), row below (right), row of B(R, R) v
-        if (tid < nb) {
-          double* b = sB + tid * kSLd;
-          double z0 = 0.0, z1 = 0.0;
-          int i = 0;
-          for (; i + 1 < len; i += 2) {
-            z0 = fma(v[i], b[i], z0);
-            z1 = fma(v[i + 1], b[i + 1], z1);
+        // phase A, one thread per vector, 64 threads per job so that each SM sub-partition
+        // (warp % 4) gets the same FP64 work: threads 0..63 the bulge columns (left
+        // application), 64..127 the rows below (right application), 128..255 the rows of
+        // B(R, R) v over the first and the second half of k (the lower triangle read
+        // across the diagonal)
+        if (tid < kSMaxW) {
+          if (tid < nb) {
+            double* b = Lp + 1 + tid;
+            axpy(b, kSLd, tau * dot(b, kSLd));
           }
-          if (i < len) z0 = fma(v[i], b[i], z0);
-          const double z = tau * (z0 + z1);
-          for (i = 0; i < len; ++i) b[i] = fma(-z, v[i], b[i]);
-        } else if (tid < nb + nl) {
-          double* b = sL + (tid - nb) * kSLd;
-          double y0 = 0.0, y1 = 0.0;
-          int k = 0;
-          for (; k + 1 < len; k += 2) {
-            y0 = fma(b[k], v[k], y0);
-            y1 = fma(b[k + 1], v[k + 1], y1);
+        } else if (tid < 2 * kSMaxW) {
+          if (tid - kSMaxW < nl) {
+            double* b = Lc + (tid - kSMaxW) * kSLd;
+            axpy(b, 1, tau * dot(b, 1));
           }
-          if (k < len) y0 = fma(b[k], v[k], y0);
-          const double y = tau * (y0 + y1);
-          for (k = 0; k < len; ++k) b[k] = fma(-y, v[k], b[k]);
-        } else if (tid < nb + nl + len) {
-          const int i = tid - nb - nl;
-          double y0 = 0.0, y1 = 0.0;
-          int k = 0;
-          for (; k + 1 < len; k += 2) {
-            y0 = fma(sD[k * kSLd + i], v[k], y0);
-            y1 = fma(sD[(k + 1) * kSLd + i], v[k + 1], y1);
+        } else {
+          const int h = tid >= 3 * kSMaxW, i = tid - 2 * kSMaxW - h * kSMaxW;
+          if (i < len) {
+            const int k1 = h ? len : len / 2;
+            double y0 = 0.0, y1 = 0.0;
+            int k = h ? len / 2 : 0;
+            for (; k + 1 < k1; k += 2) {
+              y0 = fma(Dc[k <= i ? k * kSLd + i : i * kSLd + k], v[k], y0);
+              y1 = fma(Dc[k + 1 <= i ? (k + 1) * kSLd + i : i * kSLd + k + 1], v[k + 1], y1);
+            }
+            if (k < k1) y0 = fma(Dc[k <= i ? k * kSLd + i : i * kSLd + k], v[k], y0);
+            (h ? pb : pa)[i] = y0 + y1;
           }
-          if (k < len) y0 = fma(sD[k * kSLd + i], v[k], y0);
-          pd[i] = tau * (y0 + y1);
         }
         __syncthreads();
         stamp(4);
-        // warp 0 forms p.v while the others write the final bulge columns and rows below back
+        // warp 0 forms p and p.v while the others write back; then the next step's blocks
+        // go to shared memory
         if (tid < 32) {
           double pv = 0.0;
-          for (int i = lane; i < len; i += 32) pv = fma(pd[i], v[i], pv);
+          for (int i = lane; i < len; i += 32) {
+            const double y = tau * (pa[i] + pb[i]);
+            pd[i] = y;
+            pv = fma(y, v[i], pv);
+          }
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) pv += __shfl_xor_sync(0xffffffffu, pv, o);
           if (lane == 0) s_half = 0.5 * tau * pv;
         } else {
-          for (int q = tid - 32; q < nb * len; q += kChaseThreads - 32) {
-            const int j = fdiv(q, len, rlen), i = q - j * len;
-            stb(p, s + i, col + 1 + j, sB[j * kSLd + i]);
-          }
-          for (int q = tid - 32; q < nl * len; q += kChaseThreads - 32) {
-            const int k = fdiv(q, nl, rnl), r = q - k * nl;
-            stb(p, end + r, s + k, sL[r * kSLd + k]);
-          }
+          write_back(tid - 32, kChaseThreads - 32);
         }
+        if (next) park(Dn, Ln, nl, nl1);
         __syncthreads();
         if (tid < len) pd[tid] = fma(-s_half, v[tid], pd[tid]);
         __syncthreads();
@@ -489,9 +550,12 @@ __global__ void __launch_bounds__(kChaseThreads) sb2st_chase_smem_kernel(ChasePa
           while (i * (i + 1) / 2 > q) --i;
           while ((i + 1) * (i + 2) / 2 <= q) ++i;
           const int k = q - i * (i + 1) / 2;
-          stb(p, s + i, s + k, fma(-v[i], pd[k], fma(-pd[i], v[k], sD[k * kSLd + i])));
+          stb(p, s + i, s + k, fma(-v[i], pd[k], fma(-pd[i], v[k], Dc[k * kSLd + i])));
         }
         stamp(5);
+      } else {
+        write_back(tid, kChaseThreads);
+        if (next) park(Dn, Ln, nl, nl1);
       }
       __syncthreads();
       if (tid == 0) {
@@ -502,6 +566,7 @@ __global__ void __launch_bounds__(kChaseThreads) sb2st_chase_smem_kernel(ChasePa
       col = s;
       s += w;
       ++t;
+      li = li == 2 ? 0 : li + 1;
     }
     if (tid == 0) {
       __threadfence();
