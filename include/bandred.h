@@ -404,12 +404,14 @@ int bandred_panel_phase_trace(void* buf, int max_steps);
 
 /* Phase timing of the bulge chase (a diagnostic of bandred_sb2st's step latency).  Arms
  * the next bandred_sb2st with w <= 64: the CTA running sweep (n - 2) / 2 writes the SM
- * clock (clock64) at 8 points of each of its steps into buf[8 step + q], for steps <
- * max_steps: q = 0 step start, 1 the wait for the previous sweep passed, 2 the column
- * staged (the blocks' loads in flight), 3 reflector formed and the blocks in shared
- * memory, 4 one-sided blocks and the diagonal matvec done, 7 those blocks written back and
- * K formed, 5 the diagonal block's rank-2 update written back, 6 the step released.  buf:
- * device, 8 * max_steps int64.  One call; returns 0 or a negative code. */
+ * clock (clock64) at up to 16 points of each of its steps into buf[16 step + q], for
+ * steps < max_steps: q = 0 step start, 1 the wait for the previous sweep passed, 2 the
+ * step's blocks in shared memory, 3 the rows below's last column reloaded (thread 32),
+ * 4 the reflector's scalars formed, 5 the reflector applied to the column, 6 the
+ * one-sided blocks and the diagonal matvec done, 7 the bulge written back and K formed,
+ * 8 the diagonal block's rank-2 update written back, 9 the step released (slots 10-15 are
+ * not written).  buf: device, 16 * max_steps int64.  One call; returns 0 or a negative
+ * code. */
 int bandred_sb2st_phase_trace(void* buf, int max_steps);
 
 /* ---------------------------------------------------------------- diagnostics -------

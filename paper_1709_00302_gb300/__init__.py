@@ -552,8 +552,8 @@ def bandred_panel_phase_trace(buf) -> int:
 
 def bandred_sb2st_phase_trace(buf) -> int:
     """Arms the phase timing of the next bulge chase (its middle sweep) into the device int64
-    tensor buf (8 per step)."""
-    return lib().bandred_sb2st_phase_trace(_ptr(buf), buf.numel() // 8)
+    tensor buf (16 per step)."""
+    return lib().bandred_sb2st_phase_trace(_ptr(buf), buf.numel() // 16)
 
 
 def bandred_newton_eval(x, rsqrt=None, rcp=None, stream=None) -> int:

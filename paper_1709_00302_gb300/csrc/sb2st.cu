@@ -34,13 +34,23 @@
 #include "kernels.h"
 #include "launch.h"
 #include "prof.h"
+#include "tc.cuh"
 
 namespace bandred {
 namespace {
 
+using panel_detail::abits;
+using panel_detail::dbits;
+using panel_detail::kBits2m450;
+using panel_detail::kBits2p1000;
+using panel_detail::kBits2p500;
+using panel_detail::neg_if;
+using panel_detail::nonneg;
+
 constexpr int kChaseThreads = 256;
 constexpr int kMaxW = 128;  // reflector length <= w <= 128: four entries per lane
 constexpr int kDone = 1 << 30;
+constexpr int kPhaseSlots = 16;
 
 struct ChaseParams {
   int n, w, LB;       // LB = 2w: rows of the band store per column
@@ -48,7 +58,7 @@ struct ChaseParams {
   int* prog;          // prog[c]: steps sweep c has finished (kDone when finished)
   int* status;
   unsigned long long limit_ns;
-  long long* phases;  // diagnostic: clock64 at 8 points of each step of sweep phase_sweep, or nullptr
+  long long* phases;  // diagnostic: clock64 at kPhaseSlots points of each step of sweep phase_sweep, or nullptr
   int phase_steps, phase_sweep;
 };
 
@@ -280,66 +290,167 @@ __global__ void __launch_bounds__(kChaseThreads) sb2st_chase_kernel(ChaseParams 
 // Prefetch.  Step t + 1's own blocks (its diagonal block and the rows below it) have
 // column indices from end on, which step t does not write; of the sweep before, only
 // its step t + 3 writes any of them (column end + w - 1 at rows from end + 2w - 1, the
-// last column of the rows below).  So step t issues their loads into registers as soon
-// as its own wait is over, parks them in shared memory after its phase A, and step
-// t + 1 reloads the last column of its rows below after its wait.
+// last column of the rows below).  So as soon as step t's wait is over, four warps issue
+// their copies on the TMA engine, completing on an mbarrier, and step t + 1 reloads the
+// last column of its rows below after its own wait.  In the band store, column j of a
+// step's range holds its diagonal-block part (offsets 0 .. len - j) and its rows-below
+// part (offsets len - j .. len - j + nl) back to back, so one bulk copy per column brings
+// both (rounded up to whole 16-byte pairs), into a column block with a stride of kCLd
+// doubles: (i, j) of the diagonal block (i >= j) at kC j + i, and row r of the rows
+// below in column k at kC k + len + r, kC = kCLd - 1 = 129.  A thread per row and a thread
+// per column both step by 1 or by 129 = 1 (mod 16) words, and across the diagonal (k > i)
+// the word kC i + k has the bank of kC k + i: no access pattern here has bank conflicts.
 //
-// Buffers: two diagonal blocks (lower triangle, (i, k) at k * kSLd + i) and three
-// rows-below blocks ((r, k) at r * kSLd + k) used in turn: this step's, the carried one
-// of the step before, and the next step's.  A thread per row and a thread per carried
-// column both see stride-1 or stride-65 addresses, free of bank conflicts.
+// Buffers: three column blocks used in turn: this step's, the one of the step before
+// (whose rows below are this step's column and bulge), and the next step's.
 constexpr int kSMaxW = 64;
-constexpr int kSLd = kSMaxW + 1;
-constexpr size_t kSBlk = (size_t)kSMaxW * kSLd;
-constexpr size_t kSmemChase = sizeof(double) * (5 * kSBlk + 4 * kSMaxW);
-constexpr int kSPer = kSMaxW * kSMaxW / kChaseThreads;  // block entries per thread
-static_assert(kChaseThreads == 4 * kSMaxW, "phase A gives 64 threads to each of four jobs");
+constexpr int kCLd = 2 * kSMaxW + 2;  // even: every column starts on 16 bytes
+constexpr int kC = kCLd - 1;
+constexpr size_t kCBlk = (size_t)kSMaxW * kCLd;
+constexpr int kChaseWarps = kChaseThreads / 32;
+constexpr size_t kSmemChase = sizeof(double) * (3 * kCBlk + 10 * kSMaxW);
+static_assert(kChaseThreads == 4 * kSMaxW && kChaseWarps == 8, "phase A's split over eight warps");
+static_assert((kCBlk * sizeof(double)) % 16 == 0, "blocks on 16-byte boundaries");
+static_assert(kSmemChase <= 227 * 1024, "shared memory of one CTA");
 
-__global__ void __launch_bounds__(kChaseThreads) sb2st_chase_smem_kernel(ChaseParams p) {
-  extern __shared__ double cs_smem[];
-  double* sD0 = cs_smem;                 // two diagonal blocks
-  double* sL0 = sD0 + 2 * kSBlk;         // three blocks of rows below
-  double* v = sL0 + 3 * kSBlk;           // the reflector
-  double* pd = v + kSMaxW;               // tau B(R, R) v, then K
-  double* pa = pd + kSMaxW;              // B(R, R) v over the first and second half of k
-  double* pb = pa + kSMaxW;
-  __shared__ double s_tau, s_beta, s_scal, s_half;
-  __shared__ int s_ok;
-  const int tid = threadIdx.x, lane = tid & 31;
-  const int n = p.n, w = p.w;
-  double rd[kSPer], rl[kSPer];  // one step's blocks on their way to shared memory
-  // loads of the blocks of the step with range [sx, sx + lx) and nx rows below
-  auto fetch = [&](int sx, int lx, int nx) {
-    const float rx = 1.0f / (float)lx, ry = nx > 0 ? 1.0f / (float)nx : 0.0f;
+// The copy of column j of the step with range length lx and nx rows below: offsets
+// 0 .. lx - j + nx of the band store's column, rounded up to whole pairs.
+__device__ __forceinline__ uint32_t chase_col_bytes(int lx, int nx, int j) {
+  const int m = lx - j + nx;
+  return 8u * (uint32_t)(m + (m & 1));
+}
+
+// Issues the copies of the step with range [sx, sx + lx) and nx rows below into C,
+// completing on bar (expected arrivals: one per warp).  Called by every warp: warp g
+// takes columns g, g + 8, ...
+__device__ __forceinline__ void chase_issue(const ChaseParams& p, int sx, int lx, int nx, double* C, uint64_t* bar,
+                                            int g, int lane) {
+  uint32_t bytes = 0;
+  const int j = g + kChaseWarps * lane;
+  if (j < lx) bytes = chase_col_bytes(lx, nx, j);
+  bytes = __reduce_add_sync(0xffffffffu, bytes);
+  tc::fence_proxy_async();
+  if (lane == 0) tc::mbar_arrive_expect_tx(bar, bytes);
+  __syncwarp();
+  if (j < lx) tc::bulk_g2s(C + (size_t)j * kCLd, p.Bs + (int64_t)(sx + j) * p.LB, chase_col_bytes(lx, nx, j), bar);
+}
+
+// One warp's half of a vector of phase A (k in [k0, k0 + 32)): y[kk] = b[kk st] for
+// k0 + kk < len, in registers; returns sum v[k0 + kk] y[kk] (four chains).
+__device__ __forceinline__ double half_load_dot(const double* b, int st, const double* v, int k0, int len,
+                                                double (&y)[32]) {
 #pragma unroll
-    for (int u = 0; u < kSPer; ++u) {
-      const int q = tid + u * kChaseThreads;
-      const int j = fdiv(q, lx, rx), i = q - j * lx;
-      rd[u] = (q < lx * lx && i >= j) ? ldb(p, sx + i, sx + j) : 0.0;
-      const int kl = nx > 0 ? fdiv(q, nx, ry) : 0, r = nx > 0 ? q - kl * nx : 0;
-      rl[u] = (nx > 0 && q < nx * lx) ? ldb(p, sx + lx + r, sx + kl) : 0.0;
+  for (int kk = 0; kk < 32; ++kk) y[kk] = k0 + kk < len ? b[kk * st] : 0.0;
+  double z0 = 0.0, z1 = 0.0, z2 = 0.0, z3 = 0.0;
+#pragma unroll
+  for (int kk = 0; kk < 32; kk += 4) {
+    if (k0 + kk < len) z0 = fma(v[k0 + kk], y[kk], z0);
+    if (k0 + kk + 1 < len) z1 = fma(v[k0 + kk + 1], y[kk + 1], z1);
+    if (k0 + kk + 2 < len) z2 = fma(v[k0 + kk + 2], y[kk + 2], z2);
+    if (k0 + kk + 3 < len) z3 = fma(v[k0 + kk + 3], y[kk + 3], z3);
+  }
+  return (z0 + z1) + (z2 + z3);
+}
+// b[kk st] = y[kk] - z v[k0 + kk] for k0 + kk < len
+__device__ __forceinline__ void half_update(double* b, int st, const double* v, int k0, int len, double z,
+                                            const double (&y)[32]) {
+#pragma unroll
+  for (int kk = 0; kk < 32; ++kk) {
+    if (k0 + kk < len) b[kk * st] = fma(-z, v[k0 + kk], y[kk]);
+  }
+}
+
+// The reflector of x[0 .. len) (one whole warp; lane 0 writes tau, beta and the scale of
+// the tail), larfg convention.  Common path: the plain sum of squares when it and |alpha|
+// are safely in range (max |x2| from the bit patterns, integer compares off the FP64
+// pipe), then h = ||x|| = q / sqrt(q), tau = 1 + |alpha| / h and 1 / (alpha - beta) by
+// Newton-Raphson; otherwise the max-scaled sum and hypot.
+__device__ __forceinline__ void chase_reflector(const double* x, int len, int lane, double* o_tau, double* o_beta,
+                                                double* o_scal) {
+  unsigned long long um = 0ull;
+  double ss = 0.0;
+  for (int i = 1 + lane; i < len; i += 32) {
+    const double xi = x[i];
+    const unsigned long long u = (unsigned long long)__double_as_longlong(xi) & 0x7FFFFFFFFFFFFFFFull;
+    um = u > um ? u : um;
+    ss = fma(xi, xi, ss);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long u = __shfl_xor_sync(0xffffffffu, um, o);
+    um = u > um ? u : um;
+    ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  }
+  const double amax = __longlong_as_double((long long)um), alpha = x[0];
+  const bool plain = (long long)um > kBits2m450 && dbits(ss) < kBits2p1000 && abits(alpha) < kBits2p500;
+  if (um != 0ull && !plain) {  // rare: scaled sum (warp-uniform branch)
+    const double inv = 1.0 / amax;
+    ss = 0.0;
+    for (int i = 1 + lane; i < len; i += 32) {
+      const double q = x[i] * inv;
+      ss = fma(q, q, ss);
     }
-  };
-  auto park = [&](double* D, double* L, int lx, int nx) {
-    const float rx = 1.0f / (float)lx, ry = nx > 0 ? 1.0f / (float)nx : 0.0f;
 #pragma unroll
-    for (int u = 0; u < kSPer; ++u) {
-      const int q = tid + u * kChaseThreads;
-      const int j = fdiv(q, lx, rx), i = q - j * lx;
-      if (q < lx * lx && i >= j) D[j * kSLd + i] = rd[u];
-      if (nx > 0 && q < nx * lx) {
-        const int kl = fdiv(q, nx, ry), r = q - kl * nx;
-        L[r * kSLd + kl] = rl[u];
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  }
+  if (lane == 0) {
+    double tau = 0.0, beta = alpha, scal = 1.0;
+    if (um != 0ull) {
+      if (plain) {
+        const double q = fma(alpha, alpha, ss);
+        const double rq = panel_detail::rsqrt_newton(q);
+        const double h = q * rq, aa = __longlong_as_double(abits(alpha));
+        const bool apos = nonneg(alpha);
+        beta = neg_if(h, apos);
+        tau = fma(aa, rq, 1.0);
+        scal = neg_if(panel_detail::rcp_newton(aa + h), !apos);
+      } else {
+        const double h = hypot(alpha, amax * sqrt(ss));
+        beta = alpha >= 0.0 ? -h : h;
+        tau = (beta - alpha) / beta;
+        scal = 1.0 / (alpha - beta);
       }
     }
+    *o_tau = tau;
+    *o_beta = beta;
+    *o_scal = scal;
+  }
+}
+
+__global__ void __launch_bounds__(kChaseThreads, 1) sb2st_chase_smem_kernel(ChaseParams p) {
+  extern __shared__ __align__(16) double cs_smem[];
+  __shared__ __align__(8) uint64_t s_bar[2];  // the copies of the steps with t even, odd
+  double* sC0 = cs_smem;                 // three column blocks
+  double* v = sC0 + 3 * kCBlk;           // the reflector
+  double* pd = v + kSMaxW;               // tau B(R, R) v, then K
+  double* zb = pd + kSMaxW;              // the bulge columns' dot products, k < 32 and k >= 32
+  double* zl = zb + 2 * kSMaxW;          // the rows below's
+  double* pq = zl + 2 * kSMaxW;          // B(R, R) v over the four quarters of k
+  __shared__ double s_tau, s_beta, s_scal;
+  __shared__ int s_ok;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int n = p.n, w = p.w;
+  if (tid == 0) {
+    tc::mbar_init(&s_bar[0], kChaseWarps);
+    tc::mbar_init(&s_bar[1], kChaseWarps);
+    tc::fence_mbar_init();
+  }
+  __syncthreads();
+  uint32_t ph0 = 0, ph1 = 0;  // parity of the next completion of s_bar[0], s_bar[1]
+  // waits for the copies of step t (all threads); false past the time limit
+  auto copies_wait = [&](int t) {
+    uint32_t& ph = (t & 1) ? ph1 : ph0;
+    const bool ok = tc::mbar_wait(&s_bar[t & 1], ph, global_ns() + p.limit_ns);
+    ph ^= 1u;
+    return ok;
   };
   for (int c = blockIdx.x; c + 2 < n; c += gridDim.x) {
     int col = c, s = c + 1, t = 0, li = 0;  // li = t mod 3
     while (true) {
       const int end = min(s + w, n), len = end - s;
       if (len < 2) break;
-      auto stamp = [&](int q) {
-        if (p.phases && c == p.phase_sweep && tid == 0 && t < p.phase_steps) p.phases[t * 8 + q] = clock64();
+      auto stamp = [&](int q, int who = 0) {
+        if (p.phases && c == p.phase_sweep && tid == who && t < p.phase_steps) p.phases[t * kPhaseSlots + q] = clock64();
       };
       stamp(0);
       if (tid == 0) {
@@ -363,206 +474,169 @@ __global__ void __launch_bounds__(kChaseThreads) sb2st_chase_smem_kernel(ChasePa
         s_ok = ok;
       }
       __syncthreads();
-      if (!s_ok) return;
+      if (!s_ok) {
+        if (t > 0) copies_wait(t);  // the prefetch of this step is still in flight
+        return;
+      }
       stamp(1);
       // nb = s - col - 1 bulge columns (0 at t = 0, else w - 1); nl rows below, which is
       // the next step's len: the step after this one runs iff nl >= 2
       const int nb = s - col - 1, nl = min(end + w, n) - end;
       const bool next = nl >= 2;
       const int nl1 = next ? min(end + nl + w, n) - (end + nl) : 0;  // the next step's rows below
-      double* Dc = sD0 + (size_t)(t & 1) * kSBlk;
-      double* Dn = sD0 + (size_t)((t + 1) & 1) * kSBlk;
-      double* Lc = sL0 + (size_t)li * kSBlk;                         // this step's rows below
-      double* Ln = sL0 + (size_t)(li == 2 ? 0 : li + 1) * kSBlk;     // the next step's
-      double* Lp = sL0 + (size_t)(li == 0 ? 2 : li - 1) * kSBlk;     // carried: x at (i, 0), bulge column j at (i, 1 + j)
+      double* Cc = sC0 + (size_t)li * kCBlk;                      // this step's blocks
+      double* Cn = sC0 + (size_t)(li == 2 ? 0 : li + 1) * kCBlk;  // the next step's
+      // the step before's: its rows below (laid out for len = w) hold x in column 0 and
+      // bulge column j in column 1 + j, row i at kC k + w + i
+      double* Cp = sC0 + (size_t)(li == 0 ? 2 : li - 1) * kCBlk;
       const float rlen = 1.0f / (float)len;
       if (t == 0) {  // this step's blocks and the column, from global memory
-        const double xs = tid < len ? ldb(p, s + tid, col) : 0.0;
-        fetch(s, len, nl);
-        if (tid < len) Lp[tid * kSLd] = xs;
-        park(Dc, Lc, len, nl);
-        if (next) fetch(end, nl, nl1);
+        const double x = tid < len ? ldb(p, s + tid, col) : 0.0;
+        chase_issue(p, s, len, nl, Cc, &s_bar[0], warp, lane);
+        if (tid < len) Cp[w + tid] = x;
+      }
+      if (!__syncthreads_and(copies_wait(t))) {
+        if (tid == 0 && p.status) atomicCAS(p.status, 0, BANDRED_DEV_TIMEOUT);
+        tc::mbar_wait(&s_bar[t & 1], ((t & 1) ? ph1 : ph0) ^ 1u, global_ns() + p.limit_ns);  // still in flight
+        return;
+      }
+      stamp(2);
+      if (t == 0) {
+        // the reflector of a sweep's first step; the later ones are formed by the step
+        // before, as soon as its right application has finished their column
+        if (warp == 0) chase_reflector(Cp + w, len, lane, &s_tau, &s_beta, &s_scal);
         __syncthreads();
       } else {
         // the last column of the rows below, which the sweep before could write until
-        // this step's wait; then the next step's blocks
+        // this step's wait
         const int r = tid - 32;
-        const double xr = (r >= 0 && r < nl) ? ldb(p, end + r, end - 1) : 0.0;
-        if (next) fetch(end, nl, nl1);
-        if (r >= 0 && r < nl) Lc[r * kSLd + len - 1] = xr;
+        if (r >= 0 && r < nl) Cc[(size_t)kC * (len - 1) + len + r] = ldb(p, end + r, end - 1);
+        stamp(3, 32);
       }
-      stamp(2);
-      // the reflector (warp 0), larfg convention.  Common path: the plain sum of squares
-      // when it and |alpha| are safely in range (max |x2| from the bit patterns, integer
-      // compares), then h = ||x|| = q / sqrt(q), tau = 1 + |alpha| / h and
-      // 1 / (alpha - beta) by Newton-Raphson; otherwise the max-scaled sum and hypot.
-      if (tid < 32) {
-        unsigned long long um = 0ull;
-        double ss = 0.0;
-        for (int i = 1 + lane; i < len; i += 32) {
-          const double x = Lp[i * kSLd];
-          const unsigned long long u = (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
-          um = u > um ? u : um;
-          ss = fma(x, x, ss);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          const unsigned long long u = __shfl_xor_sync(0xffffffffu, um, o);
-          um = u > um ? u : um;
-          ss += __shfl_xor_sync(0xffffffffu, ss, o);
-        }
-        const double amax = __longlong_as_double((long long)um), alpha = Lp[0];
-        const bool plain = amax > 0x1p-450 && ss < 0x1p1000 && fabs(alpha) < 0x1p500;
-        if (amax > 0.0 && !plain) {  // rare: scaled sum (warp-uniform branch)
-          const double inv = 1.0 / amax;
-          ss = 0.0;
-          for (int i = 1 + lane; i < len; i += 32) {
-            const double q = Lp[i * kSLd] * inv;
-            ss = fma(q, q, ss);
-          }
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-        }
-        if (lane == 0) {
-          double tau = 0.0, beta = alpha, scal = 1.0;
-          if (amax > 0.0) {
-            if (plain) {
-              const double q = fma(alpha, alpha, ss);
-              const double rq = panel_detail::rsqrt_newton(q);
-              const double h = q * rq, aa = fabs(alpha);
-              beta = alpha >= 0.0 ? -h : h;
-              tau = fma(aa, rq, 1.0);
-              const double rs = panel_detail::rcp_newton(aa + h);
-              scal = alpha >= 0.0 ? rs : -rs;
-            } else {
-              const double h = hypot(alpha, amax * sqrt(ss));
-              beta = alpha >= 0.0 ? -h : h;
-              tau = (beta - alpha) / beta;
-              scal = 1.0 / (alpha - beta);
-            }
-          }
-          s_tau = tau;
-          s_beta = beta;
-          s_scal = scal;
-        }
-      }
-      __syncthreads();
       const double tau = s_tau;
-      stamp(3);
-      if (tid < len) v[tid] = tid == 0 ? 1.0 : Lp[tid * kSLd] * s_scal;
+      if (tid < len) v[tid] = tid == 0 ? 1.0 : Cp[w + tid] * s_scal;
       for (int i = tid; i < len; i += kChaseThreads) stb(p, s + i, col, i == 0 ? s_beta : 0.0);
       __syncthreads();
+      stamp(5);
       // the bulge columns (their final values) and, when no step follows, the rows below
       // go to global memory; the rows below otherwise stay for the next step
       auto write_back = [&](int t0, int nt) {
         for (int q = t0; q < nb * len; q += nt) {
           const int j = fdiv(q, len, rlen), i = q - j * len;
-          stb(p, s + i, col + 1 + j, Lp[i * kSLd + 1 + j]);
+          stb(p, s + i, col + 1 + j, Cp[(size_t)kC * (1 + j) + w + i]);
         }
         if (nl == 1) {
-          for (int k = t0; k < len; k += nt) stb(p, end, s + k, Lc[k]);
+          for (int k = t0; k < len; k += nt) stb(p, end, s + k, Cc[(size_t)kC * k + len]);
         }
       };
-      // x -= z v over len entries at stride ld (a bulge column or a row below), eight at a
-      // time so that the loads are not held behind the stores
-      auto axpy = [&](double* b, int ld, double z) {
-        for (int i0 = 0; i0 < len; i0 += 8) {
-          double bb[8], vv[8];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const int i = min(i0 + u, len - 1);
-            bb[u] = b[i * ld];
-            vv[u] = v[i];
-          }
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            if (i0 + u < len) b[(i0 + u) * ld] = fma(-z, vv[u], bb[u]);
-          }
-        }
-      };
-      auto dot = [&](const double* b, int ld) {
-        double z0 = 0.0, z1 = 0.0;
-        int i = 0;
-        for (; i + 1 < len; i += 2) {
-          z0 = fma(v[i], b[i * ld], z0);
-          z1 = fma(v[i + 1], b[(i + 1) * ld], z1);
-        }
-        if (i < len) z0 = fma(v[i], b[i * ld], z0);
-        return z0 + z1;
-      };
+      // the next step's copies, issued by every warp (eight columns each)
+      if (next) chase_issue(p, end, nl, nl1, Cn, &s_bar[(t + 1) & 1], warp, lane);
       if (tau != 0.0) {
-        // phase A, one thread per vector, 64 threads per job so that each SM sub-partition
-        // (warp % 4) gets the same FP64 work: threads 0..63 the bulge columns (left
-        // application), 64..127 the rows below (right application), 128..255 the rows of
-        // B(R, R) v over the first and the second half of k (the lower triangle read
-        // across the diagonal)
-        if (tid < kSMaxW) {
-          if (tid < nb) {
-            double* b = Lp + 1 + tid;
-            axpy(b, kSLd, tau * dot(b, kSLd));
-          }
-        } else if (tid < 2 * kSMaxW) {
-          if (tid - kSMaxW < nl) {
-            double* b = Lc + (tid - kSMaxW) * kSLd;
-            axpy(b, 1, tau * dot(b, 1));
-          }
-        } else {
-          const int h = tid >= 3 * kSMaxW, i = tid - 2 * kSMaxW - h * kSMaxW;
+        // phase A in two halves around a barrier, with the same FP64 work for every warp
+        // (some 86 instructions at len = 64), whichever warps share an SM sub-partition.
+        // Warp g takes the vector job g & 3 (bulge columns 0..31, 32..63, rows below
+        // 0..31, 32..63) over k in [32 (g >> 2), 32 (g >> 2) + 32), and rows 32 (g & 1) +
+        // lane of B(R, R) v over k in [16 (g >> 1), 16 (g >> 1) + 16) (the lower triangle
+        // read across the diagonal).  First the partial dot products; then, with the two
+        // halves summed, the updates of the same entries, held in registers in between.
+        const int job = warp & 3, kh = warp >> 2, k0 = 32 * kh;
+        const bool bulge = job < 2;
+        const int q = 32 * (job & 1) + lane;  // the bulge column or the row below
+        const bool have = bulge ? q < nb : q < nl;
+        double* b = bulge ? Cp + (size_t)kC * (1 + q) + w + k0 : Cc + len + q + (size_t)kC * k0;
+        const int st = bulge ? 1 : kC;
+        double* zs = bulge ? zb : zl;
+        double y[32];
+        if (have) zs[kSMaxW * kh + q] = half_load_dot(b, st, v, k0, len, y);
+        {
+          const int i = 32 * (warp & 1) + lane, kq = warp >> 1;
           if (i < len) {
-            const int k1 = h ? len : len / 2;
             double y0 = 0.0, y1 = 0.0;
-            int k = h ? len / 2 : 0;
-            for (; k + 1 < k1; k += 2) {
-              y0 = fma(Dc[k <= i ? k * kSLd + i : i * kSLd + k], v[k], y0);
-              y1 = fma(Dc[k + 1 <= i ? (k + 1) * kSLd + i : i * kSLd + k + 1], v[k + 1], y1);
+#pragma unroll
+            for (int kk = 0; kk < 16; kk += 2) {
+              const int k = 16 * kq + kk;
+              if (k < len) y0 = fma(Cc[k <= i ? kC * k + i : kC * i + k], v[k], y0);
+              if (k + 1 < len) y1 = fma(Cc[k + 1 <= i ? kC * (k + 1) + i : kC * i + k + 1], v[k + 1], y1);
             }
-            if (k < k1) y0 = fma(Dc[k <= i ? k * kSLd + i : i * kSLd + k], v[k], y0);
-            (h ? pb : pa)[i] = y0 + y1;
+            pq[kSMaxW * kq + i] = y0 + y1;
           }
         }
         __syncthreads();
-        stamp(4);
-        // warp 0 forms p and p.v while the others write back; then the next step's blocks
-        // go to shared memory
+        stamp(10);
+        if (have) half_update(b, st, v, k0, len, tau * (zs[q] + zs[kSMaxW + q]), y);
+        __syncthreads();
+        stamp(6);
+        // warp 0 forms p = tau B(R, R) v and K = p - (tau/2)(p.v) v, warp 1 the next step's
+        // reflector, and the others write back
         if (tid < 32) {
-          double pv = 0.0;
-          for (int i = lane; i < len; i += 32) {
-            const double y = tau * (pa[i] + pb[i]);
-            pd[i] = y;
-            pv = fma(y, v[i], pv);
+          double y[kSMaxW / 32], pv = 0.0;
+#pragma unroll
+          for (int u = 0; u < kSMaxW / 32; ++u) {
+            const int i = lane + 32 * u;
+            y[u] = i < len ? tau * ((pq[i] + pq[kSMaxW + i]) + (pq[2 * kSMaxW + i] + pq[3 * kSMaxW + i])) : 0.0;
+            pv = fma(y[u], i < len ? v[i] : 0.0, pv);
           }
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) pv += __shfl_xor_sync(0xffffffffu, pv, o);
-          if (lane == 0) s_half = 0.5 * tau * pv;
+          const double half = 0.5 * tau * pv;
+#pragma unroll
+          for (int u = 0; u < kSMaxW / 32; ++u) {
+            const int i = lane + 32 * u;
+            if (i < len) pd[i] = fma(-half, v[i], y[u]);
+          }
+        } else if (next && warp == 1) {
+          // the next step's reflector: its column (the first of the rows below) is final
+          chase_reflector(Cc + len, nl, lane, &s_tau, &s_beta, &s_scal);
         } else {
-          write_back(tid - 32, kChaseThreads - 32);
+          const int w0 = next ? 64 : 32;
+          write_back(tid - w0, kChaseThreads - w0);
         }
-        if (next) park(Dn, Ln, nl, nl1);
-        __syncthreads();
-        if (tid < len) pd[tid] = fma(-s_half, v[tid], pd[tid]);
         __syncthreads();
         stamp(7);
         // the diagonal block's rank-2 update over the packed lower triangle only (each FP64
-        // warp instruction costs the same whatever the number of active lanes), row-major
-        // index q = i (i + 1) / 2 + k, written straight back
-        for (int q = tid; q < len * (len + 1) / 2; q += kChaseThreads) {
-          int i = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
-          while (i * (i + 1) / 2 > q) --i;
-          while ((i + 1) * (i + 2) / 2 <= q) ++i;
-          const int k = q - i * (i + 1) / 2;
-          stb(p, s + i, s + k, fma(-v[i], pd[k], fma(-pd[i], v[k], Dc[k * kSLd + i])));
+        // warp instruction costs the same whatever the number of active lanes), column by
+        // column (index q = off(k) + i - k, off(k) = k len - k (k - 1) / 2, so that a warp's
+        // stores are contiguous); a thread forms all its entries before it stores any, so
+        // that their FP64 chains overlap
+        {
+          constexpr int kPer = (kSMaxW * (kSMaxW + 1) / 2 + kChaseThreads - 1) / kChaseThreads;
+          const int nq = len * (len + 1) / 2;
+          double r[kPer];
+          int ri[kPer], rk[kPer];
+#pragma unroll
+          for (int u = 0; u < kPer; ++u) {
+            const int q = tid + u * kChaseThreads < nq ? tid + u * kChaseThreads : 0;
+            const float a = 2.0f * (float)len + 1.0f;
+            int k = (int)((a - sqrtf(a * a - 8.0f * (float)q)) * 0.5f);
+            k = max(0, min(k, len - 1));
+            while (k > 0 && k * len - k * (k - 1) / 2 > q) --k;
+            while (k + 1 < len && (k + 1) * len - (k + 1) * k / 2 <= q) ++k;
+            const int i = k + q - (k * len - k * (k - 1) / 2);
+            ri[u] = i;
+            rk[u] = k;
+            r[u] = fma(-v[i], pd[k], fma(-pd[i], v[k], Cc[kC * k + i]));
+          }
+#pragma unroll
+          for (int u = 0; u < kPer; ++u) {
+            if (tid + u * kChaseThreads < nq) stb(p, s + ri[u], s + rk[u], r[u]);
+          }
         }
-        stamp(5);
+        stamp(8);
       } else {
-        write_back(tid, kChaseThreads);
-        if (next) park(Dn, Ln, nl, nl1);
+        if (next && warp == 1) {
+          chase_reflector(Cc + len, nl, lane, &s_tau, &s_beta, &s_scal);
+        } else {
+          const int w0 = next ? 32 : 0;
+          write_back(tid - (warp > 1 ? w0 : 0), kChaseThreads - w0);
+        }
       }
+      tc::fence_proxy_async();  // this step's shared-memory accesses before the copies that reuse the buffers
       __syncthreads();
       if (tid == 0) {
         __threadfence();
         st_release_int(&p.prog[c], t + 1);
       }
-      stamp(6);
+      stamp(9);
       col = s;
       s += w;
       ++t;
