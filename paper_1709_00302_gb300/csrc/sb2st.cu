@@ -308,7 +308,8 @@ constexpr int kCLd = 2 * kSMaxW + 2;  // even: every column starts on 16 bytes
 constexpr int kC = kCLd - 1;
 constexpr size_t kCBlk = (size_t)kSMaxW * kCLd;
 constexpr int kChaseWarps = kChaseThreads / 32;
-constexpr size_t kSmemChase = sizeof(double) * (3 * kCBlk + 10 * kSMaxW);
+constexpr int kTri = kSMaxW * (kSMaxW + 1) / 2;  // entries of a diagonal block's lower triangle
+constexpr size_t kSmemChase = sizeof(double) * (3 * kCBlk + 10 * kSMaxW) + sizeof(uint16_t) * kTri;
 static_assert(kChaseThreads == 4 * kSMaxW && kChaseWarps == 8, "phase A's split over eight warps");
 static_assert((kCBlk * sizeof(double)) % 16 == 0, "blocks on 16-byte boundaries");
 static_assert(kSmemChase <= 227 * 1024, "shared memory of one CTA");
@@ -417,6 +418,17 @@ __device__ __forceinline__ void chase_reflector(const double* x, int len, int la
   }
 }
 
+// (i, k), k <= i < len, of entry q of a lower triangle packed column by column:
+// q = off(k) + i - k, off(k) = k len - k (k - 1) / 2
+__device__ __forceinline__ void tri_entry(int q, int len, int& i, int& k) {
+  const float a = 2.0f * (float)len + 1.0f;
+  k = (int)((a - sqrtf(a * a - 8.0f * (float)q)) * 0.5f);
+  k = max(0, min(k, len - 1));
+  while (k > 0 && k * len - k * (k - 1) / 2 > q) --k;
+  while (k + 1 < len && (k + 1) * len - (k + 1) * k / 2 <= q) ++k;
+  i = k + q - (k * len - k * (k - 1) / 2);
+}
+
 __global__ void __launch_bounds__(kChaseThreads, 1) sb2st_chase_smem_kernel(ChaseParams p) {
   extern __shared__ __align__(16) double cs_smem[];
   __shared__ __align__(8) uint64_t s_bar[2];  // the copies of the steps with t even, odd
@@ -426,10 +438,16 @@ __global__ void __launch_bounds__(kChaseThreads, 1) sb2st_chase_smem_kernel(Chas
   double* zb = pd + kSMaxW;              // the bulge columns' dot products, k < 32 and k >= 32
   double* zl = zb + 2 * kSMaxW;          // the rows below's
   double* pq = zl + 2 * kSMaxW;          // B(R, R) v over the four quarters of k
+  uint16_t* tri = reinterpret_cast<uint16_t*>(pq + 4 * kSMaxW);  // (i, k) of the packed index q at len = w
   __shared__ double s_tau, s_beta, s_scal;
   __shared__ int s_ok;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = p.n, w = p.w;
+  for (int q = tid; q < w * (w + 1) / 2; q += kChaseThreads) {
+    int i, k;
+    tri_entry(q, w, i, k);
+    tri[q] = (uint16_t)(i | (k << 8));
+  }
   if (tid == 0) {
     tc::mbar_init(&s_bar[0], kChaseWarps);
     tc::mbar_init(&s_bar[1], kChaseWarps);
@@ -606,16 +624,18 @@ __global__ void __launch_bounds__(kChaseThreads, 1) sb2st_chase_smem_kernel(Chas
 #pragma unroll
           for (int u = 0; u < kPer; ++u) {
             const int q = tid + u * kChaseThreads < nq ? tid + u * kChaseThreads : 0;
-            const float a = 2.0f * (float)len + 1.0f;
-            int k = (int)((a - sqrtf(a * a - 8.0f * (float)q)) * 0.5f);
-            k = max(0, min(k, len - 1));
-            while (k > 0 && k * len - k * (k - 1) / 2 > q) --k;
-            while (k + 1 < len && (k + 1) * len - (k + 1) * k / 2 <= q) ++k;
-            const int i = k + q - (k * len - k * (k - 1) / 2);
+            int i, k;
+            if (len == w) {  // every step but a sweep's last: the table
+              i = tri[q] & 255;
+              k = tri[q] >> 8;
+            } else {
+              tri_entry(q, len, i, k);
+            }
             ri[u] = i;
             rk[u] = k;
             r[u] = fma(-v[i], pd[k], fma(-pd[i], v[k], Cc[kC * k + i]));
           }
+          stamp(11);
 #pragma unroll
           for (int u = 0; u < kPer; ++u) {
             if (tid + u * kChaseThreads < nq) stb(p, s + ri[u], s + rk[u], r[u]);
@@ -713,59 +733,72 @@ __global__ void sterf_setup_kernel(int n, const double* d, const double* e, doub
   }
 }
 
-// Eigenvalue k of T by trisection on Sturm counts: the sequence q_0 = d_0 - x,
-// q_i = d_i - x - e_{i-1}^2 / q_{i-1} has as many negative terms as T has eigenvalues below
-// x (a term below the pivot guard counts as -pivmin).  Two lanes per eigenvalue: each
-// iteration the pair counts at the two points that cut [lo, hi) into thirds, one point per
-// lane, and both lanes keep the third that holds eigenvalue k.  The bracket shrinks
-// threefold per iteration from the same Gershgorin interval for every eigenvalue, so all
-// pairs run the same number of iterations (no divergence).  On GB300 the FP64 division
-// chain is latency-bound, so two lanes per eigenvalue (twice the warps) and a third fewer
-// sequential counts than bisection beat the extra count per iteration.
-// One Sturm step costs a reciprocal and one FMA: 1/q by the panel's Newton-Raphson
-// reciprocal (FP32 seed, two FP64 steps: a few units in the last place, well inside the
-// recurrence's own backward error), the pivot guard and the sign test as integer
-// compares of the bit patterns.
+// 1/s for a normal s > 0: an FP32 seed r0 of the mantissa m, then one cubic Newton step
+// r = r0 (1 + d + d^2), d = 1 - m r0 (|d| < 2^-22, so the dropped d^3 term is below
+// 2^-66): three dependent FP64 operations, a unit or so in the last place
+__device__ __forceinline__ double rcp_cubic(double s) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(s);
+  const int e = (int)((u >> 52) & 0x7FF) - 1023;
+  const double m = __longlong_as_double((long long)((u & 0x000FFFFFFFFFFFFFull) | (1023ull << 52)));
+  const float mf = __uint_as_float((127u << 23) | (uint32_t)((u >> 29) & 0x7FFFFFu));
+  const double r0 = tc::f32_to_f64(__frcp_rn(mf));
+  const double dd = fma(-m, r0, 1.0);
+  const double r = fma(r0, fma(dd, dd, dd), r0);
+  return __longlong_as_double(__double_as_longlong(r) - ((long long)e << 52));
+}
+
+// Sturm count of T at x: the sequence q_0 = d_0 - x, q_i = d_i - x - e_{i-1}^2 / q_{i-1}
+// has as many negative terms as T has eigenvalues below x (a term below the pivot guard
+// counts as -pivmin).  One step costs five FP64 operations (rcp_cubic's three, d_i - x,
+// and the FMA), well inside the recurrence's own backward error; the pivot guard and the
+// sign test are integer compares of the bit patterns.
 __device__ __forceinline__ int sturm_count(int n, const double* d, const double* e2, double x, double pivmin) {
-  const long long piv = panel_detail::dbits(pivmin);
+  const long long piv = dbits(pivmin);
   const double npiv = -pivmin;
-  int neg = 0;
   double q = d[0] - x;
-  if (panel_detail::abits(q) < piv) q = npiv;
-  neg += panel_detail::dbits(q) < 0;
+  if (abits(q) < piv) q = npiv;
+  int neg = dbits(q) < 0;
   for (int i = 1; i < n; ++i) {
-    const double aq = fabs(q);
-    const double r = panel_detail::neg_if(panel_detail::rcp_newton(aq), panel_detail::dbits(q) < 0);
+    const double r = neg_if(rcp_cubic(__longlong_as_double(abits(q))), dbits(q) < 0);
     q = fma(-e2[i - 1], r, d[i] - x);
-    if (panel_detail::abits(q) < piv) q = npiv;
-    neg += panel_detail::dbits(q) < 0;
+    if (abits(q) < piv) q = npiv;
+    neg += dbits(q) < 0;
   }
   return neg;
 }
 
+// Eigenvalue k of T by trisection on Sturm counts.  Two lanes per eigenvalue: each round
+// the pair counts at the two points that cut [lo, hi) into thirds, one point per lane, and
+// both lanes keep the third that holds eigenvalue k.  The bracket shrinks threefold per
+// round from the same Gershgorin interval for every eigenvalue, so all pairs run the same
+// number of rounds (no divergence).  The Sturm chain is bound by GB300's FP64 throughput
+// (a single chain already keeps a sub-partition's FP64 pipe busy; four points per
+// eigenvalue and round, two chains per lane, were measured slower): two lanes per
+// eigenvalue give twice the warps of bisection (512 at n = 8192, for 608 sub-partitions)
+// at a third fewer sequential rounds.
 __global__ void sterf_trisect_kernel(int n, const double* d, const double* e2, const double* prm, double* lam) {
   pdl_wait_and_release();
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   const int k = min(g >> 1, n - 1), half = g & 1;
   const double tol = prm[2], pivmin = prm[3];
   double lo = prm[0], hi = prm[1];
-  // iterations until the width falls to tol: the same for every pair
-  int iters = 0;
-  for (double wd = hi - lo; wd > tol && iters < 120; wd *= (1.0 / 3.0)) ++iters;
-  for (int it = 0; it < iters; ++it) {
+  // rounds until the width falls to tol: the same for every pair
+  int rounds = 0;
+  for (double wd = hi - lo; wd > tol && rounds < 120; wd *= (1.0 / 3.0)) ++rounds;
+  for (int it = 0; it < rounds; ++it) {
     const double h = (hi - lo) * (1.0 / 3.0);
-    const double x = half ? hi - h : lo + h;
-    const int c = sturm_count(n, d, e2, x, pivmin);
-    const int c1 = __shfl_xor_sync(0xffffffffu, c, 1);
     const double x1 = lo + h, x2 = hi - h;
+    const int c = sturm_count(n, d, e2, half ? x2 : x1, pivmin);
+    const int c1 = __shfl_xor_sync(0xffffffffu, c, 1);
     const int ca = half ? c1 : c, cb = half ? c : c1;  // counts at x1, x2
-    if (ca > k)
+    if (ca > k) {
       hi = x1;
-    else if (cb > k) {
+    } else if (cb > k) {
       lo = x1;
       hi = x2;
-    } else
+    } else {
       lo = x2;
+    }
   }
   if (!half && (g >> 1) < n) lam[k] = 0.5 * (lo + hi);
 }
