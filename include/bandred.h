@@ -237,15 +237,15 @@ int bandred_ge2bb_ex(int64_t m, int64_t n, int64_t w, double* A, int64_t lda, do
  *   below the band down the matrix, one reflector per w rows (larfg convention).  On exit
  *   d (device, n) holds the diagonal and e (device, n - 1) the subdiagonal of T = Q^T B Q.
  *   1 <= w <= 128.  opts: only timeout_ms is used (NULL: defaults).  work: device,
- *   16-byte aligned, >= bandred_sb2st_workspace(n, w) bytes (the band with room for the
+ *   256-byte aligned, >= bandred_sb2st_workspace(n, w) bytes (the band with room for the
  *   bulge, 2 w n doubles, and per-sweep progress counters).  dev_status: as for
  *   bandred_sy2sb_ex (BANDRED_DEV_TIMEOUT when a sweep's bounded wait for the previous
  *   sweep gave up).  Returns 0, -i for an invalid i-th argument, BANDRED_ERR_UNSUPPORTED
  *   for w > 128, or a CUDA error code.
  * bandred_sterf: eigenvalues of the symmetric tridiagonal (d, e) (device, n and n - 1
  *   entries) into lam (device, n, ascending), by trisection on Sturm counts (two lanes per
- *   eigenvalue) to within a few units in the last place of max |T|.  work: device, 16-byte aligned,
- *   >= bandred_sterf_workspace(n) bytes.  Returns 0, -i for an invalid i-th argument.
+ *   eigenvalue) to within a few units in the last place of max |T|.  work: device,
+ *   256-byte aligned, >= bandred_sterf_workspace(n) bytes.  Returns 0, -i for an invalid i-th argument.
  */
 size_t bandred_sb2st_workspace(int64_t n, int64_t w);
 int bandred_sb2st(int64_t n, int64_t w, const double* A, int64_t lda, double* d, double* e,
@@ -407,11 +407,12 @@ int bandred_panel_phase_trace(void* buf, int max_steps);
  * clock (clock64) at up to 16 points of each of its steps into buf[16 step + q], for
  * steps < max_steps: q = 0 step start, 1 the wait for the previous sweep passed, 2 the
  * step's blocks in shared memory, 3 the rows below's last column reloaded (thread 32),
- * 4 the reflector's scalars formed, 5 the reflector applied to the column, 6 the
- * one-sided blocks and the diagonal matvec done, 7 the bulge written back and K formed,
- * 8 the diagonal block's rank-2 update written back, 9 the step released (slots 10-15 are
- * not written).  buf: device, 16 * max_steps int64.  One call; returns 0 or a negative
- * code. */
+ * 5 the reflector's vector formed and the column written, 6 the
+ * one-sided blocks and the diagonal matvec done, 7 the bulge written back, K and the
+ * next step's reflector formed, 8 the diagonal block's rank-2 update written back, 9 the
+ * step released, 10 the first half of the one-sided blocks (the dot products) done, 11 the
+ * diagonal block's entries formed (slots 4 and 12-15 are not written).  buf: device,
+ * 16 * max_steps int64.  One call; returns 0 or a negative code. */
 int bandred_sb2st_phase_trace(void* buf, int max_steps);
 
 /* ---------------------------------------------------------------- diagnostics -------
