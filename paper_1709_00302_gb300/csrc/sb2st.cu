@@ -13,18 +13,24 @@
 //
 // GB300 mapping.  The band lives in a compact lower band store of 2w rows per column
 // (offsets 0 .. 2w-1 hold the band and the bulge), which stays in L2 (n = 8192, w = 64:
-// 8 MB).  One persistent cooperative kernel: CTA g runs sweeps g, g + G, ... in order.
-// A step of sweep c with range start s writes only entries whose column index lies in
-// [s - w, s + w) (the annihilated column, the bulge columns, the range), and step t'' of
-// sweep c - 1 only entries whose column index is at least its own s'' - w = s - 1 +
-// (t'' - t - 1) w.  They share entries only for t'' <= t + 2, so step t of sweep c waits
-// until sweep c - 1 has finished its step t + 2: every entry sees the sweeps' updates in
-// sequential order, and the result equals the one-sweep-at-a-time algorithm up to the
-// rounding of the sums.  The
-// waits are bounded: past the time limit the kernel records BANDRED_DEV_TIMEOUT and
-// returns.  Within a step the three blocks the reflector touches (the bulge columns to
+// 8 MB).  One persistent cooperative kernel: CTA g runs sweeps g, g + G, ... in order, and
+// each sweep publishes its progress in a counter that the next sweep waits on (bounded:
+// past the time limit the kernel records BANDRED_DEV_TIMEOUT and returns).  Step t of
+// sweep c, range start s, touches entries whose column lies in [s - w, s + w) and whose
+// row lies in [s, s + 2w); step t'' of sweep c - 1 those with columns from s - 1 +
+// (t'' - t - 1) w and rows from s - 1 + (t'' - t) w.  Every entry must see the sweeps'
+// updates in sequential order, so step t of sweep c needs step t + 1 of sweep c - 1
+// finished; of step t + 2 it shares a single entry, (s + 2w - 1, s + w - 1), the first
+// entry of that step's column.
+//   * The L2 kernel (w <= 128) waits for step t + 2 of the sweep before.
+//   * The shared-memory kernel (w <= 64) writes each step's column (beta, 0, ..) during
+//     the step before, as soon as that step's right application has made it final, and a
+//     sweep's counter at t + 1 means "steps <= t done and step t + 1's column written":
+//     step t waits for t + 2 on the counter of the sweep before, a lag of two steps.
+// Either way the result equals the one-sweep-at-a-time algorithm up to the rounding of
+// the sums.  Within a step the three blocks the reflector touches (the bulge columns to
 // the left of the range, the symmetric diagonal block, the rows below the range) are
-// independent vectors, one warp each at a time.
+// independent vectors.
 #include <algorithm>
 #include <cstdint>
 
@@ -284,15 +290,15 @@ __global__ void __launch_bounds__(kChaseThreads) sb2st_chase_kernel(ChaseParams 
 // Carry.  After step t's right application, the rows below its range, B(end : end + w,
 // s : end), are exactly the column that step t + 1 annihilates (their first column) and
 // step t + 1's bulge columns (the others), and nothing else writes them in between (the
-// sweep before has finished with them, the sweep after waits for step t + 1).  So they
-// stay in shared memory and reach global memory once, as step t + 1's bulge columns.
+// sweep before has finished with them; of the sweep after, step t - 1 reads only their
+// first entry, the next step's column, written to global memory early, and step t waits
+// for step t + 1).  So they stay in shared memory and reach global memory once, as step
+// t + 1's bulge columns.
 //
-// Prefetch.  Step t + 1's own blocks (its diagonal block and the rows below it) have
-// column indices from end on, which step t does not write; of the sweep before, only
-// its step t + 3 writes any of them (column end + w - 1 at rows from end + 2w - 1, the
-// last column of the rows below).  So as soon as step t's wait is over, four warps issue
-// their copies on the TMA engine, completing on an mbarrier, and step t + 1 reloads the
-// last column of its rows below after its own wait.  In the band store, column j of a
+// Copies.  A step's own blocks (its diagonal block and the rows below it) are final once
+// its wait is over (the sweep before has finished its step t + 1 and written the column of
+// its step t + 2); they go to shared memory on the TMA engine, each warp issuing the bulk
+// copies of eight columns, completing on an mbarrier.  In the band store, column j of a
 // step's range holds its diagonal-block part (offsets 0 .. len - j) and its rows-below
 // part (offsets len - j .. len - j + nl) back to back, so one bulk copy per column brings
 // both (rounded up to whole 16-byte pairs), into a column block with a stride of kCLd
@@ -300,16 +306,18 @@ __global__ void __launch_bounds__(kChaseThreads) sb2st_chase_kernel(ChaseParams 
 // below in column k at kC k + len + r, kC = kCLd - 1 = 129.  A thread per row and a thread
 // per column both step by 1 or by 129 = 1 (mod 16) words, and across the diagonal (k > i)
 // the word kC i + k has the bank of kC k + i: no access pattern here has bank conflicts.
+// While the copies are in flight the step forms its reflector's vector from the carried
+// column.
 //
-// Buffers: three column blocks used in turn: this step's, the one of the step before
-// (whose rows below are this step's column and bulge), and the next step's.
+// Buffers: two column blocks used in turn: this step's, and the one of the step before
+// (whose rows below are this step's column and bulge).
 constexpr int kSMaxW = 64;
 constexpr int kCLd = 2 * kSMaxW + 2;  // even: every column starts on 16 bytes
 constexpr int kC = kCLd - 1;
 constexpr size_t kCBlk = (size_t)kSMaxW * kCLd;
 constexpr int kChaseWarps = kChaseThreads / 32;
 constexpr int kTri = kSMaxW * (kSMaxW + 1) / 2;  // entries of a diagonal block's lower triangle
-constexpr size_t kSmemChase = sizeof(double) * (3 * kCBlk + 10 * kSMaxW) + sizeof(uint16_t) * kTri;
+constexpr size_t kSmemChase = sizeof(double) * (2 * kCBlk + 10 * kSMaxW) + sizeof(uint16_t) * kTri;
 static_assert(kChaseThreads == 4 * kSMaxW && kChaseWarps == 8, "phase A's split over eight warps");
 static_assert((kCBlk * sizeof(double)) % 16 == 0, "blocks on 16-byte boundaries");
 static_assert(kSmemChase <= 227 * 1024, "shared memory of one CTA");
@@ -432,8 +440,8 @@ __device__ __forceinline__ void tri_entry(int q, int len, int& i, int& k) {
 __global__ void __launch_bounds__(kChaseThreads, 1) sb2st_chase_smem_kernel(ChaseParams p) {
   extern __shared__ __align__(16) double cs_smem[];
   __shared__ __align__(8) uint64_t s_bar[2];  // the copies of the steps with t even, odd
-  double* sC0 = cs_smem;                 // three column blocks
-  double* v = sC0 + 3 * kCBlk;           // the reflector
+  double* sC0 = cs_smem;                 // two column blocks
+  double* v = sC0 + 2 * kCBlk;           // the reflector
   double* pd = v + kSMaxW;               // tau B(R, R) v, then K
   double* zb = pd + kSMaxW;              // the bulge columns' dot products, k < 32 and k >= 32
   double* zl = zb + 2 * kSMaxW;          // the rows below's
@@ -463,7 +471,7 @@ __global__ void __launch_bounds__(kChaseThreads, 1) sb2st_chase_smem_kernel(Chas
     return ok;
   };
   for (int c = blockIdx.x; c + 2 < n; c += gridDim.x) {
-    int col = c, s = c + 1, t = 0, li = 0;  // li = t mod 3
+    int col = c, s = c + 1, t = 0;
     while (true) {
       const int end = min(s + w, n), len = end - s;
       if (len < 2) break;
@@ -476,7 +484,7 @@ __global__ void __launch_bounds__(kChaseThreads, 1) sb2st_chase_smem_kernel(Chas
         if (c > 0) {
           unsigned long long t0 = 0;
           unsigned int spins = 0;
-          while (ld_acquire_int(&p.prog[c - 1]) < t + 3) {
+          while (ld_acquire_int(&p.prog[c - 1]) < t + 2) {
             if ((++spins & 63u) == 0u) {
               const unsigned long long now = global_ns();
               if (t0 == 0) t0 = now;
@@ -492,52 +500,50 @@ __global__ void __launch_bounds__(kChaseThreads, 1) sb2st_chase_smem_kernel(Chas
         s_ok = ok;
       }
       __syncthreads();
-      if (!s_ok) {
-        if (t > 0) copies_wait(t);  // the prefetch of this step is still in flight
-        return;
-      }
+      if (!s_ok) return;  // (no copies are in flight between steps)
       stamp(1);
       // nb = s - col - 1 bulge columns (0 at t = 0, else w - 1); nl rows below, which is
       // the next step's len: the step after this one runs iff nl >= 2
       const int nb = s - col - 1, nl = min(end + w, n) - end;
       const bool next = nl >= 2;
-      const int nl1 = next ? min(end + nl + w, n) - (end + nl) : 0;  // the next step's rows below
-      double* Cc = sC0 + (size_t)li * kCBlk;                      // this step's blocks
-      double* Cn = sC0 + (size_t)(li == 2 ? 0 : li + 1) * kCBlk;  // the next step's
+      double* Cc = sC0 + (size_t)(t & 1) * kCBlk;  // this step's blocks
       // the step before's: its rows below (laid out for len = w) hold x in column 0 and
       // bulge column j in column 1 + j, row i at kC k + w + i
-      double* Cp = sC0 + (size_t)(li == 0 ? 2 : li - 1) * kCBlk;
+      double* Cp = sC0 + (size_t)((t + 1) & 1) * kCBlk;
       const float rlen = 1.0f / (float)len;
-      if (t == 0) {  // this step's blocks and the column, from global memory
-        const double x = tid < len ? ldb(p, s + tid, col) : 0.0;
-        chase_issue(p, s, len, nl, Cc, &s_bar[0], warp, lane);
-        if (tid < len) Cp[w + tid] = x;
+      // this step's blocks, all final now: the sweep before has finished its step t + 1
+      // and written its step t + 2's column
+      const double x0 = (t == 0 && tid < len) ? ldb(p, s + tid, col) : 0.0;
+      chase_issue(p, s, len, nl, Cc, &s_bar[t & 1], warp, lane);
+      if (t == 0) {
+        // a sweep's first column and reflector; each later one is formed, and its column
+        // written, by the step before as soon as that step's right application is done
+        if (tid < len) Cp[w + tid] = x0;
+        __syncthreads();
+        if (warp == 0) chase_reflector(Cp + w, len, lane, &s_tau, &s_beta, &s_scal);
+        __syncthreads();
+        for (int i = tid; i < len; i += kChaseThreads) stb(p, s + i, col, i == 0 ? s_beta : 0.0);
       }
+      const double tau = s_tau;
+      if (tid < len) v[tid] = tid == 0 ? 1.0 : Cp[w + tid] * s_scal;
       if (!__syncthreads_and(copies_wait(t))) {
         if (tid == 0 && p.status) atomicCAS(p.status, 0, BANDRED_DEV_TIMEOUT);
         tc::mbar_wait(&s_bar[t & 1], ((t & 1) ? ph1 : ph0) ^ 1u, global_ns() + p.limit_ns);  // still in flight
         return;
       }
       stamp(2);
-      if (t == 0) {
-        // the reflector of a sweep's first step; the later ones are formed by the step
-        // before, as soon as its right application has finished their column
-        if (warp == 0) chase_reflector(Cp + w, len, lane, &s_tau, &s_beta, &s_scal);
-        __syncthreads();
-      } else {
-        // the last column of the rows below, which the sweep before could write until
-        // this step's wait
-        const int r = tid - 32;
-        if (r >= 0 && r < nl) Cc[(size_t)kC * (len - 1) + len + r] = ldb(p, end + r, end - 1);
-        stamp(3, 32);
-      }
-      const double tau = s_tau;
-      if (tid < len) v[tid] = tid == 0 ? 1.0 : Cp[w + tid] * s_scal;
-      for (int i = tid; i < len; i += kChaseThreads) stb(p, s + i, col, i == 0 ? s_beta : 0.0);
-      __syncthreads();
       stamp(5);
       // the bulge columns (their final values) and, when no step follows, the rows below
       // go to global memory; the rows below otherwise stay for the next step
+      // the next step's reflector, from its column (the first of the rows below, final
+      // once this step's right application is done), and that column written as
+      // (beta, 0, ..): the one entry of the next step that the sweep after needs before it
+      // may start its step t - 1 (warp 1)
+      auto next_column = [&]() {
+        chase_reflector(Cc + len, nl, lane, &s_tau, &s_beta, &s_scal);
+        __syncwarp();
+        for (int i = lane; i < nl; i += 32) stb(p, end + i, s, i == 0 ? s_beta : 0.0);
+      };
       auto write_back = [&](int t0, int nt) {
         for (int q = t0; q < nb * len; q += nt) {
           const int j = fdiv(q, len, rlen), i = q - j * len;
@@ -547,8 +553,6 @@ __global__ void __launch_bounds__(kChaseThreads, 1) sb2st_chase_smem_kernel(Chas
           for (int k = t0; k < len; k += nt) stb(p, end, s + k, Cc[(size_t)kC * k + len]);
         }
       };
-      // the next step's copies, issued by every warp (eight columns each)
-      if (next) chase_issue(p, end, nl, nl1, Cn, &s_bar[(t + 1) & 1], warp, lane);
       if (tau != 0.0) {
         // phase A in two halves around a barrier, with the same FP64 work for every warp
         // (some 86 instructions at len = 64), whichever warps share an SM sub-partition.
@@ -603,8 +607,7 @@ __global__ void __launch_bounds__(kChaseThreads, 1) sb2st_chase_smem_kernel(Chas
             if (i < len) pd[i] = fma(-half, v[i], y[u]);
           }
         } else if (next && warp == 1) {
-          // the next step's reflector: its column (the first of the rows below) is final
-          chase_reflector(Cc + len, nl, lane, &s_tau, &s_beta, &s_scal);
+          next_column();
         } else {
           const int w0 = next ? 64 : 32;
           write_back(tid - w0, kChaseThreads - w0);
@@ -644,7 +647,7 @@ __global__ void __launch_bounds__(kChaseThreads, 1) sb2st_chase_smem_kernel(Chas
         stamp(8);
       } else {
         if (next && warp == 1) {
-          chase_reflector(Cc + len, nl, lane, &s_tau, &s_beta, &s_scal);
+          next_column();
         } else {
           const int w0 = next ? 32 : 0;
           write_back(tid - (warp > 1 ? w0 : 0), kChaseThreads - w0);
@@ -660,7 +663,6 @@ __global__ void __launch_bounds__(kChaseThreads, 1) sb2st_chase_smem_kernel(Chas
       col = s;
       s += w;
       ++t;
-      li = li == 2 ? 0 : li + 1;
     }
     if (tid == 0) {
       __threadfence();

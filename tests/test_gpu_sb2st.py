@@ -61,6 +61,37 @@ def test_sb2st_matches_oracle(br, n, w):
     assert np.array_equal(to_host(dA), np.tril(A))
 
 
+@pytest.mark.parametrize("n,w", [(3000, 64), (3001, 17), (1200, 2)])
+def test_sb2st_repeatable_and_matches_oracle(br, n, w):
+    """Sweeps run concurrently, each waiting on the one before through a progress counter:
+    the same input must give the same bits on every run (a missed dependency shows up as
+    run-to-run differences), the eigenvalues of the band (an orthogonal similarity: also
+    its trace and Frobenius norm), and for w >= 16 the oracle's d and e elementwise.  For
+    small w and long chases the tridiagonal itself is ill-conditioned: the oracle moves by
+    7e-12 ||A||_F at n = 1200, w = 2 when each input entry moves by one ulp, so rounding
+    in another order is not held to 1e-11 there."""
+    A = band_of(n, w, 5 * n + w)
+    dA = to_dev(np.tril(A))
+    runs = []
+    for _ in range(4):
+        d, e, st = br.sb2st(dA, w)
+        assert int(st.item()) == 0
+        runs.append((d.cpu().numpy(), e.cpu().numpy()))
+    for d, e in runs[1:]:
+        assert np.array_equal(d, runs[0][0]) and np.array_equal(e, runs[0][1])
+    d, e = runs[0]
+    fa = np.linalg.norm(A)
+    la = np.linalg.eigvalsh(A)
+    lt = sl.eigvalsh_tridiagonal(d, e)
+    assert np.max(np.abs(lt - la)) <= 1e-13 * n * np.abs(la).max()
+    assert abs(d.sum() - np.trace(A)) <= 1e-13 * n * fa
+    assert abs((d @ d + 2 * e @ e) - fa * fa) <= 1e-13 * n * fa * fa
+    if w >= 16:
+        do, eo = oracle.sb2st(np.tril(A), w)
+        assert np.max(np.abs(d - do)) <= 1e-11 * fa
+        assert np.max(np.abs(e - eo)) <= 1e-11 * fa
+
+
 def test_sb2st_on_sy2sb_output(br):
     """The packed sy2sb output (reflectors below the band) goes in unchanged."""
     n, w = 600, 24
