@@ -52,6 +52,10 @@ def _load():
         lib.oracle_sb2st.restype = c_int
         lib.oracle_tridiag_eig.argtypes = [i64, dp, dp, dp]
         lib.oracle_tridiag_eig.restype = c_int
+        lib.oracle_gb2bd.argtypes = [i64, i64, dp, i64, dp, dp]
+        lib.oracle_gb2bd.restype = c_int
+        lib.oracle_bd_singular_values.argtypes = [i64, dp, dp, dp]
+        lib.oracle_bd_singular_values.restype = c_int
         lib.oracle_jacobi_eig.argtypes = [i64, dp, i64, dp]
         lib.oracle_jacobi_eig.restype = c_int
         lib.oracle_jacobi_svd.argtypes = [i64, i64, dp, i64, dp]
@@ -173,6 +177,34 @@ def tridiag_eig(d: np.ndarray, e: np.ndarray) -> np.ndarray:
     if info != 0:
         raise ValueError(f"oracle_tridiag_eig: info={info}")
     return lam[:n]
+
+
+def gb2bd(A: np.ndarray, w: int):
+    """Upper band (upper triangle, upper bandwidth w) -> upper bidiagonal by bulge chasing
+    with Householder reflectors (the SVD's second stage).  Returns (d, e): the diagonal
+    and the superdiagonal."""
+    A = np.array(A, dtype=np.float64, order="F", copy=True)
+    n = A.shape[0]
+    d = np.zeros(max(n, 1))
+    e = np.zeros(max(n - 1, 1))
+    info = _load().oracle_gb2bd(n, w, _ptr(A), max(n, 1), _ptr(d), _ptr(e))
+    if info != 0:
+        raise ValueError(f"oracle_gb2bd: info={info}")
+    return d[:n], e[: max(n - 1, 0)]
+
+
+def bd_singular_values(d: np.ndarray, e: np.ndarray) -> np.ndarray:
+    """Singular values (descending) of the upper bidiagonal (d, e), by bisection on its
+    Golub-Kahan tridiagonal."""
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    n = d.shape[0]
+    ee = np.zeros(max(n, 1))
+    ee[: max(n - 1, 0)] = np.asarray(e, dtype=np.float64)[: max(n - 1, 0)]
+    sig = np.zeros(max(n, 1))
+    info = _load().oracle_bd_singular_values(n, _ptr(d if n else np.zeros(1)), _ptr(ee), _ptr(sig))
+    if info != 0:
+        raise ValueError(f"oracle_bd_singular_values: info={info}")
+    return sig[:n]
 
 
 def jacobi_eig(A: np.ndarray) -> np.ndarray:

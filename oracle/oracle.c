@@ -535,3 +535,107 @@ int oracle_tridiag_eig(int64_t n, const double *d, const double *e, double *lam)
     }
     return 0;
 }
+
+/* ---------------------------------------------------------------------------------
+ * Second stage for the SVD (the paper's introduction: the SVD's compact form is upper
+ * triangular-band with upper bandwidth w, reduced to bidiagonal form in a second stage,
+ * whose singular values follow): upper band -> upper bidiagonal by bulge chasing with
+ * Householder reflectors, then the singular values of the bidiagonal.
+ *
+ * Band -> bidiagonal, one reflector at a time on a dense copy.  Sweep c (c = 0 .. n-2)
+ * alternates right and left reflectors on index ranges that move down by w.  The right
+ * reflector on columns [a, a+w) (a = c+1 first) annihilates row r's entries past its
+ * first (r = c first) and is applied to every other row; on rows [a, a+w) it fills the
+ * triangle below their diagonal (the lower bulge).  The left reflector on rows [a, a+w)
+ * annihilates column a below its diagonal and is applied to every other column; on rows
+ * [a, a+w) it fills the entries past the band (the upper bulge).  Then r = a and a moves
+ * on by w: the next right reflector annihilates the upper bulge's first row past its
+ * in-band entry, and so on to the end of the matrix.  The other rows and columns of each
+ * bulge are annihilated by the sweeps that follow.  Every reflector follows the larfg
+ * convention above.  Nonzeros never sit more than 2w - 1 above or w - 2 below the
+ * diagonal, so a right reflector touches only the rows within 2w before and w after its
+ * range, and a left one only the columns within w before and 2w after it.
+ * A: n x n, its upper triangle holds the band (0 <= j-i <= w; the rest is ignored).
+ * On return d[0..n) is the diagonal and e[0..n-1) the superdiagonal.
+ * Returns 0, -i for an invalid i-th argument, -100 when out of memory.
+ * ---------------------------------------------------------------------------------*/
+int oracle_gb2bd(int64_t n, int64_t w, const double *A, int64_t lda, double *d, double *e) {
+    if (n < 0) return -1;
+    if (w < 1) return -2;
+    if (lda < (n > 1 ? n : 1)) return -4;
+    if (n == 0) return 0;
+    double *M = (double *)calloc((size_t)n * (size_t)n, sizeof(double));
+    double *v = (double *)malloc(sizeof(double) * (size_t)(w + 1));
+    if (!M || !v) { free(M); free(v); return -100; }
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t i = (j - w > 0 ? j - w : 0); i <= j; ++i) AT(M, n, i, j) = AT(A, lda, i, j);
+    for (int64_t c = 0; c + 1 < n; ++c) {
+        int64_t r = c, a = c + 1;
+        while (a < n) {
+            int64_t end = a + w < n ? a + w : n;
+            int64_t len = end - a;
+            if (len < 2) break;
+            double t;
+            /* right: from row r, columns [a, end), applied to rows [a - 2w, end + w) */
+            house(len, &AT(M, n, r, a), n, &t);
+            if (t != 0.0) {
+                v[0] = 1.0;
+                for (int64_t k = 1; k < len; ++k) v[k] = AT(M, n, r, a + k);
+                int64_t lo = a - 2 * w > 0 ? a - 2 * w : 0, hi = end + w < n ? end + w : n;
+                for (int64_t i = lo; i < hi; ++i) {
+                    if (i == r) continue;
+                    double z = 0.0;
+                    for (int64_t k = 0; k < len; ++k) z += AT(M, n, i, a + k) * v[k];
+                    z *= t;
+                    for (int64_t k = 0; k < len; ++k) AT(M, n, i, a + k) -= z * v[k];
+                }
+            }
+            for (int64_t k = 1; k < len; ++k) AT(M, n, r, a + k) = 0.0;
+            /* left: from column a, rows [a, end), applied to columns [a - w, end + 2w) */
+            house(len, &AT(M, n, a, a), 1, &t);
+            if (t != 0.0) {
+                v[0] = 1.0;
+                for (int64_t i = 1; i < len; ++i) v[i] = AT(M, n, a + i, a);
+                int64_t lo = a - w > 0 ? a - w : 0, hi = end + 2 * w < n ? end + 2 * w : n;
+                for (int64_t j = lo; j < hi; ++j) {
+                    if (j == a) continue;
+                    double z = 0.0;
+                    for (int64_t i = 0; i < len; ++i) z += v[i] * AT(M, n, a + i, j);
+                    z *= t;
+                    for (int64_t i = 0; i < len; ++i) AT(M, n, a + i, j) -= z * v[i];
+                }
+            }
+            for (int64_t i = 1; i < len; ++i) AT(M, n, a + i, a) = 0.0;
+            r = a;
+            a += w;
+        }
+    }
+    for (int64_t i = 0; i < n; ++i) d[i] = AT(M, n, i, i);
+    for (int64_t i = 0; i + 1 < n; ++i) e[i] = AT(M, n, i, i + 1);
+    free(M);
+    free(v);
+    return 0;
+}
+
+/* Singular values of the upper bidiagonal B = (d, e), descending: the eigenvalues of the
+ * Golub-Kahan tridiagonal of order 2n (zero diagonal, off-diagonal d_0, e_0, d_1, e_1,
+ * ..., d_{n-1}) are +-sigma_k, so its n largest, by the bisection above, are the singular
+ * values.  Returns 0, -i for an invalid i-th argument, -100 when out of memory. */
+int oracle_bd_singular_values(int64_t n, const double *d, const double *e, double *sig) {
+    if (n < 0) return -1;
+    if (n == 0) return 0;
+    double *z = (double *)calloc((size_t)(2 * n), sizeof(double));
+    double *o = (double *)calloc((size_t)(2 * n), sizeof(double));
+    double *lam = (double *)malloc(sizeof(double) * (size_t)(2 * n));
+    if (!z || !o || !lam) { free(z); free(o); free(lam); return -100; }
+    for (int64_t i = 0; i < n; ++i) {
+        o[2 * i] = d[i];
+        if (i + 1 < n) o[2 * i + 1] = e[i];
+    }
+    int info = oracle_tridiag_eig(2 * n, z, o, lam);
+    for (int64_t k = 0; k < n && info == 0; ++k) sig[k] = lam[2 * n - 1 - k];
+    free(z);
+    free(o);
+    free(lam);
+    return info;
+}
