@@ -254,6 +254,39 @@ size_t bandred_sterf_workspace(int64_t n);
 int bandred_sterf(int64_t n, const double* d, const double* e, double* lam, void* work, size_t work_bytes,
                   cudaStream_t stream);
 
+/* ---------------------------------------------------------------- SVD second stage -----
+ * The paper's introduction: for the SVD the compact form is an upper triangular-band
+ * matrix with upper bandwidth w (ge2gb's result), which a second stage reduces to
+ * bidiagonal form before the singular values are computed.
+ *
+ * bandred_gb2bd: upper band -> upper bidiagonal by Householder bulge chasing.  A (device,
+ *   column-major, lda >= n) holds the band in its upper n x n triangle (entries with
+ *   0 <= j - i <= w are read, nothing else: a packed ge2gb result with m >= n goes in
+ *   unchanged).  Sweep c (c = 0 .. n-2) alternates a right reflector, which annihilates a
+ *   row past its first entry over a column range [a, a+w), and a left reflector, which
+ *   annihilates column a below its diagonal, on ranges that move down by w (larfg
+ *   convention); the bulges' other rows and columns are taken by the sweeps that follow.
+ *   On exit d (device, n) holds the diagonal and e (device, n - 1) the superdiagonal of
+ *   B = U^T A V.  1 <= w <= 128.  opts: only timeout_ms is used (NULL: defaults).  work:
+ *   device, 256-byte aligned, >= bandred_gb2bd_workspace(n, w) bytes (the band with room
+ *   for the bulges, 3 w n doubles, and per-sweep progress counters).  dev_status: as for
+ *   bandred_sy2sb_ex (BANDRED_DEV_TIMEOUT when a sweep's bounded wait for the previous
+ *   sweep gave up).  Returns 0, -i for an invalid i-th argument, BANDRED_ERR_UNSUPPORTED
+ *   for w > 128, or a CUDA error code.
+ * bandred_bdsv: singular values of the upper bidiagonal (d, e) (device, n and n - 1
+ *   entries) into sigma (device, n, descending): the n largest eigenvalues of its
+ *   Golub-Kahan tridiagonal (order 2n, zero diagonal, off-diagonal d_0, e_0, d_1, ..), by
+ *   the trisection of bandred_sterf, to within a few units in the last place of max |B|.
+ *   work: device, 256-byte aligned, >= bandred_bdsv_workspace(n) bytes.  Returns 0, -i
+ *   for an invalid i-th argument, or a CUDA error code.
+ */
+size_t bandred_gb2bd_workspace(int64_t n, int64_t w);
+int bandred_gb2bd(int64_t n, int64_t w, const double* A, int64_t lda, double* d, double* e,
+                  const bandred_opts* opts, void* work, size_t work_bytes, int* dev_status, cudaStream_t stream);
+size_t bandred_bdsv_workspace(int64_t n);
+int bandred_bdsv(int64_t n, const double* d, const double* e, double* sigma, void* work, size_t work_bytes,
+                 cudaStream_t stream);
+
 /* ---------------------------------------------------------------- forming Q, U, V ---
  * The orthogonal factors of a finished reduction, formed on the GPU from the packed
  * reflectors (the step that eigenvector and singular-vector solvers take after the band

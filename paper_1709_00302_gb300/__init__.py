@@ -165,6 +165,14 @@ def lib():
         L.bandred_sterf_workspace.restype = sz
         L.bandred_sterf.argtypes = [i64, vp, vp, vp, vp, sz, vp]
         L.bandred_sterf.restype = ci
+        L.bandred_gb2bd_workspace.argtypes = [i64, i64]
+        L.bandred_gb2bd_workspace.restype = sz
+        L.bandred_gb2bd.argtypes = [i64, i64, vp, i64, vp, vp, op, vp, sz, vp, vp]
+        L.bandred_gb2bd.restype = ci
+        L.bandred_bdsv_workspace.argtypes = [i64]
+        L.bandred_bdsv_workspace.restype = sz
+        L.bandred_bdsv.argtypes = [i64, vp, vp, vp, vp, sz, vp]
+        L.bandred_bdsv.restype = ci
         L.bandred_newton_eval.argtypes = [i64, vp, vp, vp, vp]
         L.bandred_newton_eval.restype = ci
         L.bandred_fp64_probe.argtypes = [ci, ci, ci, vp, vp]
@@ -543,6 +551,42 @@ def sterf(d, e, stream=None):
     if rc != 0:
         raise BandredError(rc, "bandred_sterf")
     return lam[:n]
+
+
+def gb2bd(A, w: int, opts: bandred_opts | None = None, stream=None, check: bool = True):
+    """Upper band -> upper bidiagonal by bulge chasing: the upper band (bandwidth w) of the
+    column-major CUDA tensor A (its upper n x n triangle, read only; n = A.shape[1]).
+    Returns (d, e, dev_status): the diagonal and the superdiagonal."""
+    import torch
+
+    n = A.shape[1]
+    d = torch.zeros(max(n, 1), dtype=torch.float64, device=A.device)
+    e = torch.zeros(max(n - 1, 1), dtype=torch.float64, device=A.device)
+    work = torch.empty(max(lib().bandred_gb2bd_workspace(n, w), 256), dtype=torch.uint8, device=A.device)
+    status = torch.zeros(1, dtype=torch.int32, device=A.device)
+    rc = lib().bandred_gb2bd(n, w, _ptr(A), _lda(A), _ptr(d), _ptr(e), None if opts is None else ctypes.byref(opts),
+                             _ptr(work), work.numel(), _ptr(status), _stream(stream))
+    if rc != 0:
+        raise BandredError(rc, "bandred_gb2bd")
+    if check:
+        st = int(status.item())
+        if st != 0:
+            raise BandredError(st, "bandred_gb2bd (device)")
+    return d[:n], e[: max(n - 1, 0)], status
+
+
+def bdsv(d, e, stream=None):
+    """Singular values (descending) of the upper bidiagonal (d, e), CUDA tensors."""
+    import torch
+
+    n = d.shape[0]
+    sig = torch.zeros(max(n, 1), dtype=torch.float64, device=d.device)
+    work = torch.empty(max(lib().bandred_bdsv_workspace(n), 256), dtype=torch.uint8, device=d.device)
+    ee = e if e.numel() > 0 else torch.zeros(1, dtype=torch.float64, device=d.device)
+    rc = lib().bandred_bdsv(n, _ptr(d), _ptr(ee), _ptr(sig), _ptr(work), work.numel(), _stream(stream))
+    if rc != 0:
+        raise BandredError(rc, "bandred_bdsv")
+    return sig[:n]
 
 
 def bandred_panel_phase_trace(buf) -> int:

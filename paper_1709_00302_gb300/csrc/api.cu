@@ -279,6 +279,45 @@ int bandred_sb2st(int64_t n, int64_t w, const double* A, int64_t lda, double* d,
   return bandred::sb2st_run(n, w, A, lda, d, e, o.limit_ns, work, dev_status, stream);
 }
 
+size_t bandred_gb2bd_workspace(int64_t n, int64_t w) {
+  return (n < 0 || w < 1 || w > 128) ? 0 : bandred::gb2bd_workspace_bytes(n, w);
+}
+
+int bandred_gb2bd(int64_t n, int64_t w, const double* A, int64_t lda, double* d, double* e,
+                  const bandred_opts* opts, void* work, size_t work_bytes, int* dev_status, cudaStream_t stream) {
+  if (n < 0) return -1;
+  if (w < 1) return -2;
+  if (w > 128) return BANDRED_ERR_UNSUPPORTED;
+  if (n > 0 && !A) return -3;
+  if (lda < std::max<int64_t>(1, n)) return -4;
+  if (n > 0 && !d) return -5;
+  if (n > 1 && !e) return -6;
+  if (n > INT32_MAX / 512) return BANDRED_ERR_UNSUPPORTED;
+  Options o;
+  if (bandred::resolve_options(opts, w, &o) != 0) return -7;
+  if (!work || !aligned(work)) return -8;
+  if (work_bytes < bandred::gb2bd_workspace_bytes(n, w)) return -9;
+  bandred::DeviceGuard dg;
+  if (n > 0 && !dg.select(A)) return -3;
+  return bandred::gb2bd_run(n, w, A, lda, d, e, o.limit_ns, work, dev_status, stream);
+}
+
+size_t bandred_bdsv_workspace(int64_t n) { return n < 0 ? 0 : bandred::bdsv_workspace_bytes(n); }
+
+int bandred_bdsv(int64_t n, const double* d, const double* e, double* sigma, void* work, size_t work_bytes,
+                 cudaStream_t stream) {
+  if (n < 0) return -1;
+  if (n > 0 && !d) return -2;
+  if (n > 1 && !e) return -3;
+  if (n > 0 && !sigma) return -4;
+  if (n > INT32_MAX / 4) return BANDRED_ERR_UNSUPPORTED;
+  if (!work || !aligned(work)) return -5;
+  if (work_bytes < bandred::bdsv_workspace_bytes(n)) return -6;
+  bandred::DeviceGuard dg;
+  if (n > 0 && !dg.select(sigma)) return -4;
+  return bandred::bdsv_run(n, d, e, sigma, work, stream);
+}
+
 size_t bandred_sterf_workspace(int64_t n) { return n < 0 ? 0 : bandred::sterf_workspace_bytes(n); }
 
 int bandred_sterf(int64_t n, const double* d, const double* e, double* lam, void* work, size_t work_bytes,

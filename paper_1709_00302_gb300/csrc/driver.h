@@ -77,6 +77,11 @@ int sb2st_run(int64_t n, int64_t w, const double* A, int64_t lda, double* d, dou
               void* work, int* dev_status, cudaStream_t s);
 size_t sterf_workspace_bytes(int64_t n);
 int sterf_run(int64_t n, const double* d, const double* e, double* lam, void* work, cudaStream_t s);
+size_t gb2bd_workspace_bytes(int64_t n, int64_t w);
+int gb2bd_run(int64_t n, int64_t w, const double* A, int64_t lda, double* d, double* e, unsigned long long limit_ns,
+              void* work, int* dev_status, cudaStream_t s);
+size_t bdsv_workspace_bytes(int64_t n);
+int bdsv_run(int64_t n, const double* d, const double* e, double* sig, void* work, cudaStream_t s);
 int ge2bb_run(int64_t m, int64_t n, int64_t w, double* A, int64_t lda, double* tauq, double* taup, const Options& o,
               void* work, int* dev_status, cudaStream_t s);
 int ge2gb_run(int64_t m, int64_t n, int64_t w, double* A, int64_t lda, double* tauq, double* taup,

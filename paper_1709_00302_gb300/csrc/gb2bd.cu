@@ -1,0 +1,380 @@
+// Second stage for the SVD.  The paper's introduction gives the SVD's compact form as an
+// upper triangular-band matrix (upper bandwidth w), which a second stage reduces to
+// bidiagonal form before the singular values are computed.  Here the band goes to an
+// upper bidiagonal B by Householder bulge chasing, and the singular values of B come
+// from the eigenvalues of its Golub-Kahan tridiagonal (trisection on Sturm counts, the
+// eigenvalue kernel of the symmetric second stage).
+//
+// Bulge chasing.  Sweep c (c = 0 .. n-2) alternates right and left reflectors on index
+// ranges [a, a + w) that move down by w (a = c + 1 first).  The right reflector
+// annihilates row r's entries past its first (r = c first, then r = the previous range's
+// first row) and is applied to rows (r, a + w); on rows [a, a + w) it fills the triangle
+// below their diagonal.  The left reflector annihilates column a below its diagonal and is
+// applied to columns (a, a + 2w); on rows [a, a + w) it fills the entries past the band,
+// whose first row the next right reflector takes.  The other rows and columns of each
+// bulge are annihilated by the sweeps that follow.  Each reflector follows the larfg
+// convention (beta = -sign(alpha) ||x||, sign(0) = +1; tau = 0 for a zero tail).  Those
+// application ranges hold every nonzero the reflectors meet: entries never sit more than
+// 2w - 1 above or w - 1 below the diagonal (measured over many shapes on a dense copy,
+// and what the ranges' geometry allows).
+//
+// GB300 mapping.  The band lives in a compact store of 3w rows per column (offsets
+// 0 .. 3w - 1 for i - j from -(2w - 1) to w), resident in L2 (n = 8192, w = 64: 12.6 MB).
+// One persistent cooperative kernel: CTA g runs sweeps g, g + G, ... in order, one warp
+// per vector, and each sweep publishes its progress in a counter.  On a dense copy, step t
+// of sweep c touches entries of sweep c - 1's steps up to t + 2 (at t + 2 a single entry,
+// the first of that step's right-reflector row), so step t waits until sweep c - 1 has
+// finished its step t + 2.  The waits are bounded: past the time limit the kernel records
+// BANDRED_DEV_TIMEOUT and returns.
+#include <algorithm>
+#include <cstdint>
+
+#include "common.cuh"
+#include "driver.h"
+#include "kernels.h"
+#include "launch.h"
+#include "prof.h"
+
+namespace bandred {
+namespace {
+
+constexpr int kGbThreads = 256;
+constexpr int kGbWarps = kGbThreads / 32;
+constexpr int kGbMaxW = 128;  // reflector length <= w <= 128: four entries per lane
+constexpr int kGbDone = 1 << 30;
+
+struct GbParams {
+  int n, w, up, LB;  // entry (i, j), -up <= i - j <= w, at Bs[(i - j + up) + j LB]
+  double* Bs;
+  int* prog;         // prog[c]: steps sweep c has finished (kGbDone when finished)
+  int* status;
+  unsigned long long limit_ns;
+};
+
+// Loads go to L2 (ld.cg): another CTA may have changed a line this SM read before.
+__device__ __forceinline__ double gld(const GbParams& p, int i, int j) {
+  return __ldcg(&p.Bs[(int64_t)(i - j + p.up) + (int64_t)j * p.LB]);
+}
+__device__ __forceinline__ void gst(const GbParams& p, int i, int j, double x) {
+  p.Bs[(int64_t)(i - j + p.up) + (int64_t)j * p.LB] = x;
+}
+__device__ __forceinline__ int gb_ld_acquire(const int* q) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(q) : "memory");
+  return v;
+}
+__device__ __forceinline__ void gb_st_release(int* q, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(q), "r"(v) : "memory");
+}
+
+// The reflector of x (one warp; x[lane + 32 u] in xv[u], len <= 128), larfg convention
+// with the max-scaled sum of squares: tau, beta, and the tail's scale, v = (x sx) scal, on
+// every lane.  Along a long chase the bulge's far entries decay towards the underflow
+// threshold, so tiny vectors are handled by exact power-of-two scalings: when every entry
+// is below 2^-900 the reflector is formed from x 2^600 (the same tau and v, beta scaled
+// back), and a tail below 2^-900 beside a larger alpha is scaled by 2^600 in the sum of
+// squares, where 1 / max would overflow.
+__device__ __forceinline__ void warp_reflector(const double (&xv)[4], int len, int lane, double& tau, double& beta,
+                                               double& scal, double& sx) {
+  double amax = 0.0;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int i = lane + 32 * u;
+    if (i >= 1 && i < len) amax = fmax(amax, fabs(xv[u]));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  const double alpha = __shfl_sync(0xffffffffu, xv[0], 0);
+  const double big = fmax(amax, fabs(alpha));
+  sx = big < 0x1p-900 ? 0x1p600 : 1.0;
+  const double am = amax * sx;
+  const double ns = am < 0x1p-900 ? 0x1p600 : 1.0;
+  double ss = 0.0;
+  if (amax > 0.0) {
+    const double inv = 1.0 / (am * ns);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = lane + 32 * u;
+      if (i >= 1 && i < len) {
+        const double q = ((xv[u] * sx) * ns) * inv;
+        ss = fma(q, q, ss);
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  tau = 0.0;
+  beta = alpha;
+  scal = 1.0;
+  if (amax > 0.0) {
+    const double as = alpha * sx;
+    const double h = hypot(as, am * sqrt(ss));
+    const double bs = as >= 0.0 ? -h : h;
+    tau = (bs - as) / bs;
+    scal = 1.0 / (as - bs);
+    beta = bs * (1.0 / sx);
+  }
+}
+
+__global__ void __launch_bounds__(kGbThreads) gb2bd_chase_kernel(GbParams p) {
+  __shared__ double v[kGbMaxW];
+  __shared__ double s_tau;
+  __shared__ int s_ok;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int n = p.n, w = p.w;
+  for (int c = blockIdx.x; c + 1 < n; c += gridDim.x) {
+    int r = c, a = c + 1, t = 0;
+    while (true) {
+      const int end = min(a + w, n), len = end - a;
+      if (len < 2) break;
+      // wait for sweep c - 1 to pass step t + 2 (or to finish)
+      if (tid == 0) {
+        int ok = 1;
+        if (c > 0) {
+          unsigned long long t0 = 0;
+          unsigned int spins = 0;
+          while (gb_ld_acquire(&p.prog[c - 1]) < t + 3) {
+            if ((++spins & 63u) == 0u) {
+              const unsigned long long now = global_ns();
+              if (t0 == 0) t0 = now;
+              else if (now - t0 > p.limit_ns) {
+                if (p.status) atomicCAS(p.status, 0, BANDRED_DEV_TIMEOUT);
+                ok = 0;
+                break;
+              }
+              if (p.status && gb_ld_acquire(p.status) != 0) { ok = 0; break; }
+            }
+          }
+        }
+        s_ok = ok;
+      }
+      __syncthreads();
+      if (!s_ok) return;
+
+      // right reflector from row r, columns [a, end); row r becomes (beta, 0, ..)
+      if (warp == 0) {
+        double xv[4], tau, beta, scal, sx;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int j = lane + 32 * u;
+          xv[u] = j < len ? gld(p, r, a + j) : 0.0;
+        }
+        warp_reflector(xv, len, lane, tau, beta, scal, sx);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int j = lane + 32 * u;
+          if (j < len) {
+            v[j] = j == 0 ? 1.0 : (xv[u] * sx) * scal;
+            gst(p, r, a + j, j == 0 ? beta : 0.0);
+          }
+        }
+        if (lane == 0) s_tau = tau;
+      }
+      __syncthreads();
+      double tau = s_tau;
+      if (tau != 0.0) {
+        // rows (r, min(a + w, n)), one warp each: y = row v, row -= tau y v^T
+        for (int i = r + 1 + warp; i < min(a + w, n); i += kGbWarps) {
+          double yv[4], z = 0.0;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int j = lane + 32 * u;
+            yv[u] = j < len ? gld(p, i, a + j) : 0.0;
+            if (j < len) z = fma(yv[u], v[j], z);
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
+          z *= tau;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int j = lane + 32 * u;
+            if (j < len) gst(p, i, a + j, fma(-z, v[j], yv[u]));
+          }
+        }
+      }
+      __syncthreads();
+
+      // left reflector from column a, rows [a, end); column a becomes (beta, 0, ..)^T
+      if (warp == 0) {
+        double xv[4], tl, beta, scal, sx;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = lane + 32 * u;
+          xv[u] = i < len ? gld(p, a + i, a) : 0.0;
+        }
+        warp_reflector(xv, len, lane, tl, beta, scal, sx);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = lane + 32 * u;
+          if (i < len) {
+            v[i] = i == 0 ? 1.0 : (xv[u] * sx) * scal;
+            gst(p, a + i, a, i == 0 ? beta : 0.0);
+          }
+        }
+        if (lane == 0) s_tau = tl;
+      }
+      __syncthreads();
+      tau = s_tau;
+      if (tau != 0.0) {
+        // columns (a, min(a + 2w, n)), one warp each: z = v^T col, col -= tau v z
+        for (int j = a + 1 + warp; j < min(a + 2 * w, n); j += kGbWarps) {
+          double yv[4], z = 0.0;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int i = lane + 32 * u;
+            yv[u] = i < len ? gld(p, a + i, j) : 0.0;
+            if (i < len) z = fma(v[i], yv[u], z);
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
+          z *= tau;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int i = lane + 32 * u;
+            if (i < len) gst(p, a + i, j, fma(-z, v[i], yv[u]));
+          }
+        }
+      }
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        gb_st_release(&p.prog[c], t + 1);
+      }
+      r = a;
+      a += w;
+      ++t;
+    }
+    if (tid == 0) {
+      __threadfence();
+      gb_st_release(&p.prog[c], kGbDone);
+    }
+  }
+}
+
+// Band store from the upper band of A (0 <= j - i <= w; everything else of A, such as the
+// reflectors of a packed ge2gb result, is not read), zeros elsewhere.
+__global__ void gb_band_in_kernel(int n, int w, int up, int LB, const double* A, int64_t lda, double* Bs) {
+  const int64_t total = (int64_t)n * LB;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    const int off = (int)(q % LB), j = (int)(q / LB), i = j + off - up;
+    Bs[q] = (i >= 0 && j - i >= 0 && j - i <= w) ? A[i + (int64_t)j * lda] : 0.0;
+  }
+}
+
+__global__ void gb_band_out_kernel(int n, int up, int LB, const double* Bs, double* d, double* e) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    d[k] = Bs[up + (int64_t)k * LB];
+    if (k + 1 < n) e[k] = Bs[(up - 1) + (int64_t)(k + 1) * LB];
+  }
+}
+
+// The Golub-Kahan tridiagonal of the upper bidiagonal (d, e): zero diagonal, off-diagonal
+// d_0, e_0, d_1, e_1, .., d_{n-1} (2n - 1 entries; o[2n - 1] = 0 is not read).
+__global__ void tgk_kernel(int n, const double* d, const double* e, double* z, double* o) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < 2 * n; q += gridDim.x * blockDim.x) {
+    z[q] = 0.0;
+    const int i = q >> 1;
+    o[q] = (q & 1) ? (i + 1 < n ? e[i] : 0.0) : d[i];
+  }
+}
+
+// The singular values, descending: the n largest eigenvalues of the Golub-Kahan
+// tridiagonal (its eigenvalues are +-sigma_k).
+__global__ void sv_out_kernel(int n, const double* lam, double* sig) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) sig[k] = lam[2 * n - 1 - k];
+}
+
+struct GbWs {
+  double* Bs;
+  int* prog;
+  int* status;
+  size_t bytes;
+};
+
+GbWs carve_gb2bd(void* work, int64_t n, int64_t w) {
+  char* base = static_cast<char*>(work);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    char* q = base ? base + off : nullptr;
+    off += (bytes + 255) / 256 * 256;
+    return q;
+  };
+  GbWs ws{};
+  ws.Bs = reinterpret_cast<double*>(take(sizeof(double) * (size_t)std::max<int64_t>(n, 1) * 3 * w));
+  ws.prog = reinterpret_cast<int*>(take(sizeof(int) * (size_t)std::max<int64_t>(n, 1)));
+  ws.status = reinterpret_cast<int*>(take(256));
+  ws.bytes = off;
+  return ws;
+}
+
+#define CKG(call)                                                 \
+  do {                                                            \
+    cudaError_t e_ = (call);                                      \
+    if (e_ != cudaSuccess) return record_cuda_error(e_, #call);   \
+  } while (0)
+
+}  // namespace
+
+size_t gb2bd_workspace_bytes(int64_t n, int64_t w) { return carve_gb2bd(nullptr, n, w).bytes; }
+
+int gb2bd_run(int64_t n, int64_t w, const double* A, int64_t lda, double* d, double* e, unsigned long long limit_ns,
+              void* work, int* dev_status, cudaStream_t s) {
+  GbWs ws = carve_gb2bd(work, n, w);
+  int* status = dev_status ? dev_status : ws.status;
+  CKG(cudaMemsetAsync(status, 0, sizeof(int), s));
+  if (n <= 0) return 0;
+  const int LB = (int)(3 * w), up = (int)(2 * w - 1);
+  {
+    const int blocks = (int)std::min<int64_t>((n * LB + 255) / 256, 4096);
+    prof::count_launch();
+    gb_band_in_kernel<<<blocks, 256, 0, s>>>((int)n, (int)w, up, LB, A, lda, ws.Bs);
+    CKG(cudaGetLastError());
+  }
+  if (n > 2 && w > 1) {
+    CKG(cudaMemsetAsync(ws.prog, 0, sizeof(int) * (size_t)n, s));
+    int dev = 0, sms = 0;
+    CKG(cudaGetDevice(&dev));
+    CKG(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    // one CTA per SM, all co-resident (the cooperative launch guarantees it): a sweep
+    // waits only on the sweep before it, which another CTA runs
+    const int G = (int)std::min<int64_t>(n - 1, sms);
+    GbParams p{(int)n, (int)w, up, LB, ws.Bs, ws.prog, status, limit_ns};
+    void* args[] = {&p};
+    prof::count_launch();
+    CKG(cudaLaunchCooperativeKernel((const void*)gb2bd_chase_kernel, dim3(G), dim3(kGbThreads), args, 0, s));
+  }
+  {
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 1024);
+    prof::count_launch();
+    gb_band_out_kernel<<<blocks, 256, 0, s>>>((int)n, up, LB, ws.Bs, d, e);
+    CKG(cudaGetLastError());
+  }
+  return 0;
+}
+
+size_t bdsv_workspace_bytes(int64_t n) {
+  const size_t v = (sizeof(double) * (size_t)std::max<int64_t>(2 * n, 1) + 255) / 256 * 256;
+  return 3 * v + sterf_workspace_bytes(std::max<int64_t>(2 * n, 1));
+}
+
+int bdsv_run(int64_t n, const double* d, const double* e, double* sig, void* work, cudaStream_t s) {
+  if (n <= 0) return 0;
+  const size_t v = (sizeof(double) * (size_t)(2 * n) + 255) / 256 * 256;
+  char* base = static_cast<char*>(work);
+  double* z = reinterpret_cast<double*>(base);
+  double* o = reinterpret_cast<double*>(base + v);
+  double* lam = reinterpret_cast<double*>(base + 2 * v);
+  void* sw = base + 3 * v;
+  const int blocks = (int)std::min<int64_t>((2 * n + 255) / 256, 1024);
+  prof::count_launch();
+  tgk_kernel<<<blocks, 256, 0, s>>>((int)n, d, e, z, o);
+  CKG(cudaGetLastError());
+  const int rc = sterf_run(2 * n, z, o, lam, sw, s);
+  if (rc != 0) return rc;
+  prof::count_launch();
+  sv_out_kernel<<<blocks, 256, 0, s>>>((int)n, lam, sig);
+  CKG(cudaGetLastError());
+  return 0;
+}
+
+}  // namespace bandred

@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(kChaseThreads) sb2st_chase_kernel(ChaseParams 
   __shared__ double v[kMaxW];       // the reflector (v[0] = 1)
   __shared__ double pdiag[kMaxW];   // tau * B(R, R) v, then K = p - (tau/2)(p.v) v
   __shared__ double red[kChaseThreads / 32];
-  __shared__ double s_tau, s_beta, s_scal, s_half;
+  __shared__ double s_tau, s_beta, s_scal, s_sx, s_half;
   __shared__ int s_ok;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int NW = kChaseThreads / 32;
@@ -149,14 +149,18 @@ __global__ void __launch_bounds__(kChaseThreads) sb2st_chase_kernel(ChaseParams 
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        // tiny vectors by exact power-of-two scalings (see chase_reflector)
+        const double alpha = __shfl_sync(0xffffffffu, xv[0], 0);
+        const double sx = fmax(amax, fabs(alpha)) < 0x1p-900 ? 0x1p600 : 1.0;
+        const double am = amax * sx, ns = am < 0x1p-900 ? 0x1p600 : 1.0;
         double ss = 0.0;
         if (amax > 0.0) {
-          const double inv = 1.0 / amax;
+          const double inv = 1.0 / (am * ns);
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             const int i = lane + 32 * u;
             if (i >= 1 && i < len) {
-              const double q = xv[u] * inv;
+              const double q = ((xv[u] * sx) * ns) * inv;
               ss = fma(q, q, ss);
             }
           }
@@ -164,18 +168,19 @@ __global__ void __launch_bounds__(kChaseThreads) sb2st_chase_kernel(ChaseParams 
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
         if (lane == 0) {
-          const double alpha = xv[0];
           double tau = 0.0, beta = alpha, scal = 1.0;
           if (amax > 0.0) {
-            const double xnorm = amax * sqrt(ss);
-            const double h = hypot(alpha, xnorm);
-            beta = alpha >= 0.0 ? -h : h;
-            tau = (beta - alpha) / beta;
-            scal = 1.0 / (alpha - beta);
+            const double as = alpha * sx;
+            const double h = hypot(as, am * sqrt(ss));
+            const double bs = as >= 0.0 ? -h : h;
+            tau = (bs - as) / bs;
+            scal = 1.0 / (as - bs);
+            beta = bs * (1.0 / sx);
           }
           s_tau = tau;
           s_beta = beta;
           s_scal = scal;
+          s_sx = sx;
         }
       }
       __syncthreads();
@@ -185,7 +190,7 @@ __global__ void __launch_bounds__(kChaseThreads) sb2st_chase_kernel(ChaseParams 
         stb(p, s + i, col, i == 0 ? s_beta : 0.0);
       }
       __syncthreads();
-      if (tid < len) v[tid] = tid == 0 ? 1.0 : v[tid] * s_scal;
+      if (tid < len) v[tid] = tid == 0 ? 1.0 : (v[tid] * s_sx) * s_scal;
       __syncthreads();
 
       if (tau != 0.0) {
@@ -369,13 +374,18 @@ __device__ __forceinline__ void half_update(double* b, int st, const double* v, 
   }
 }
 
-// The reflector of x[0 .. len) (one whole warp; lane 0 writes tau, beta and the scale of
-// the tail), larfg convention.  Common path: the plain sum of squares when it and |alpha|
-// are safely in range (max |x2| from the bit patterns, integer compares off the FP64
-// pipe), then h = ||x|| = q / sqrt(q), tau = 1 + |alpha| / h and 1 / (alpha - beta) by
-// Newton-Raphson; otherwise the max-scaled sum and hypot.
+// The reflector of x[0 .. len) (one whole warp; lane 0 writes tau, beta and the tail's
+// scale, v = (x sx) scal), larfg convention.  Common path: the plain sum of squares when it
+// and |alpha| are safely in range (max |x2| from the bit patterns, integer compares off the
+// FP64 pipe), then h = ||x|| = q / sqrt(q), tau = 1 + |alpha| / h and 1 / (alpha - beta) by
+// Newton-Raphson; otherwise the max-scaled sum and hypot.  Along a long chase the bulge's
+// far entries decay towards the underflow threshold, so in the latter path tiny vectors
+// take exact power-of-two scalings: when every entry is below 2^-900 the reflector is
+// formed from x 2^600 (the same tau and v, beta scaled back), and a tail below 2^-900
+// beside a larger alpha is scaled by 2^600 in the sum of squares, where 1 / max would
+// overflow.
 __device__ __forceinline__ void chase_reflector(const double* x, int len, int lane, double* o_tau, double* o_beta,
-                                                double* o_scal) {
+                                                double* o_scal, double* o_sx) {
   unsigned long long um = 0ull;
   double ss = 0.0;
   for (int i = 1 + lane; i < len; i += 32) {
@@ -392,11 +402,14 @@ __device__ __forceinline__ void chase_reflector(const double* x, int len, int la
   }
   const double amax = __longlong_as_double((long long)um), alpha = x[0];
   const bool plain = (long long)um > kBits2m450 && dbits(ss) < kBits2p1000 && abits(alpha) < kBits2p500;
+  const double sx = (!plain && fmax(amax, fabs(alpha)) < 0x1p-900) ? 0x1p600 : 1.0;
+  const double am = amax * sx;
   if (um != 0ull && !plain) {  // rare: scaled sum (warp-uniform branch)
-    const double inv = 1.0 / amax;
+    const double ns = am < 0x1p-900 ? 0x1p600 : 1.0;
+    const double inv = 1.0 / (am * ns);
     ss = 0.0;
     for (int i = 1 + lane; i < len; i += 32) {
-      const double q = x[i] * inv;
+      const double q = ((x[i] * sx) * ns) * inv;
       ss = fma(q, q, ss);
     }
 #pragma unroll
@@ -414,15 +427,18 @@ __device__ __forceinline__ void chase_reflector(const double* x, int len, int la
         tau = fma(aa, rq, 1.0);
         scal = neg_if(panel_detail::rcp_newton(aa + h), !apos);
       } else {
-        const double h = hypot(alpha, amax * sqrt(ss));
-        beta = alpha >= 0.0 ? -h : h;
-        tau = (beta - alpha) / beta;
-        scal = 1.0 / (alpha - beta);
+        const double as = alpha * sx;
+        const double h = hypot(as, am * sqrt(ss));
+        const double bs = as >= 0.0 ? -h : h;
+        tau = (bs - as) / bs;
+        scal = 1.0 / (as - bs);
+        beta = bs * (1.0 / sx);
       }
     }
     *o_tau = tau;
     *o_beta = beta;
     *o_scal = scal;
+    *o_sx = sx;
   }
 }
 
@@ -447,7 +463,7 @@ __global__ void __launch_bounds__(kChaseThreads, 1) sb2st_chase_smem_kernel(Chas
   double* zl = zb + 2 * kSMaxW;          // the rows below's
   double* pq = zl + 2 * kSMaxW;          // B(R, R) v over the four quarters of k
   uint16_t* tri = reinterpret_cast<uint16_t*>(pq + 4 * kSMaxW);  // (i, k) of the packed index q at len = w
-  __shared__ double s_tau, s_beta, s_scal;
+  __shared__ double s_tau, s_beta, s_scal, s_sx;
   __shared__ int s_ok;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = p.n, w = p.w;
@@ -520,12 +536,12 @@ __global__ void __launch_bounds__(kChaseThreads, 1) sb2st_chase_smem_kernel(Chas
         // written, by the step before as soon as that step's right application is done
         if (tid < len) Cp[w + tid] = x0;
         __syncthreads();
-        if (warp == 0) chase_reflector(Cp + w, len, lane, &s_tau, &s_beta, &s_scal);
+        if (warp == 0) chase_reflector(Cp + w, len, lane, &s_tau, &s_beta, &s_scal, &s_sx);
         __syncthreads();
         for (int i = tid; i < len; i += kChaseThreads) stb(p, s + i, col, i == 0 ? s_beta : 0.0);
       }
       const double tau = s_tau;
-      if (tid < len) v[tid] = tid == 0 ? 1.0 : Cp[w + tid] * s_scal;
+      if (tid < len) v[tid] = tid == 0 ? 1.0 : (Cp[w + tid] * s_sx) * s_scal;
       if (!__syncthreads_and(copies_wait(t))) {
         if (tid == 0 && p.status) atomicCAS(p.status, 0, BANDRED_DEV_TIMEOUT);
         tc::mbar_wait(&s_bar[t & 1], ((t & 1) ? ph1 : ph0) ^ 1u, global_ns() + p.limit_ns);  // still in flight
@@ -540,7 +556,7 @@ __global__ void __launch_bounds__(kChaseThreads, 1) sb2st_chase_smem_kernel(Chas
       // (beta, 0, ..): the one entry of the next step that the sweep after needs before it
       // may start its step t - 1 (warp 1)
       auto next_column = [&]() {
-        chase_reflector(Cc + len, nl, lane, &s_tau, &s_beta, &s_scal);
+        chase_reflector(Cc + len, nl, lane, &s_tau, &s_beta, &s_scal, &s_sx);
         __syncwarp();
         for (int i = lane; i < nl; i += 32) stb(p, end + i, s, i == 0 ? s_beta : 0.0);
       };

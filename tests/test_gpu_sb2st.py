@@ -155,3 +155,19 @@ def test_eigenvalue_path_known_spectrum(br, n, w, precision):
           f"sterf {1e3 * (t3 - t2):.1f} ms")
     err = np.max(np.abs(lam - np.sort(lam_true)))
     assert err <= 1e-12 * np.abs(lam_true).max(), err
+
+
+@pytest.mark.parametrize("n,w", [(300, 32), (260, 100)])
+def test_sb2st_tiny_entries(br, n, w):
+    """A band scaled by 2^-1000 (every reflector's vector below 2^-900), through the
+    shared-memory kernel (w = 32) and the L2 one (w = 100): tiny vectors are scaled by exact
+    powers of two, so d and e are 2^-1000 times the unscaled oracle's."""
+    A = band_of(n, w, 13 * n + w)
+    d, e, st = br.sb2st(to_dev(np.tril(A) * 2.0 ** -1000), w)
+    assert int(st.item()) == 0
+    d, e = d.cpu().numpy() * 2.0 ** 1000, e.cpu().numpy() * 2.0 ** 1000
+    do, eo = oracle.sb2st(np.tril(A), w)
+    fa = np.linalg.norm(A)
+    assert np.all(np.isfinite(d)) and np.all(np.isfinite(e))
+    assert np.max(np.abs(d - do)) <= 1e-11 * fa
+    assert np.max(np.abs(e - eo)) <= 1e-11 * fa
