@@ -855,6 +855,8 @@ def main():
         torch.cuda.empty_cache()
         extras["eigenvalues"] = compact_eigen(args, br, dev, stream, prob)
         torch.cuda.empty_cache()
+        extras["singular_values"] = compact_svd(args, br, dev, stream, prob)
+        torch.cuda.empty_cache()
         extras["ge2gb"] = compact_ge2gb(args, br, dev, stream)
         torch.cuda.empty_cache()
         extras["batched"] = compact_batched(args, br, dev, stream, world, rank, dist)
@@ -1001,6 +1003,64 @@ def compact_eigen(args, br, dev, stream, prob):
     if prob.get("lam") is not None:
         lt = np.sort(np.asarray(prob["lam"]))
         out["max_eig_error_rel"] = float(np.max(np.abs(lam.cpu().numpy() - lt)) / np.max(np.abs(lt)))
+    del A
+    return out
+
+
+def compact_svd(args, br, dev, stream, prob):
+    """The whole singular-value path on the headline's matrix (its singular values are
+    the absolute values of its known eigenvalues): ge2gb in the Ozaki precision (the
+    general reduction to upper band form), then bandred_gb2bd and bandred_bdsv, each timed
+    with CUDA events over one run after one warm-up."""
+    import ctypes
+
+    import numpy as np
+    import torch
+
+    n, w, b = args.n, args.w, args.b
+    A0 = prob["A0"]
+    A = torch.empty_like(A0)
+    o = br.make_opts(b=b, lookahead=args.lookahead, precision="ozaki")
+    tauq = torch.zeros(n, dtype=torch.float64, device=dev)
+    taup = torch.zeros(max(n - w, 1), dtype=torch.float64, device=dev)
+    work = torch.empty(max(br.bandred_ge2gb_workspace(n, n, w, o), 256), dtype=torch.uint8, device=dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    d = torch.zeros(n, dtype=torch.float64, device=dev)
+    e = torch.zeros(max(n - 1, 1), dtype=torch.float64, device=dev)
+    sig = torch.zeros(n, dtype=torch.float64, device=dev)
+    L = br.lib()
+    w2 = torch.empty(max(L.bandred_gb2bd_workspace(n, w), 256), dtype=torch.uint8, device=dev)
+    w3 = torch.empty(max(L.bandred_bdsv_workspace(n), 256), dtype=torch.uint8, device=dev)
+    st2 = torch.zeros(1, dtype=torch.int32, device=dev)
+    P = ctypes.c_void_p
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    for _ in range(2):
+        A.copy_(A0)
+        torch.cuda.synchronize(dev)
+        ev[0].record(stream)
+        if br.bandred_ge2gb_ex(A, w, tauq, taup, o, work, st, stream) != 0:
+            raise br.BandredError(-1, "bandred_ge2gb_ex")
+        ev[1].record(stream)
+        rc = L.bandred_gb2bd(n, w, P(A.data_ptr()), A.stride(1), P(d.data_ptr()), P(e.data_ptr()), None,
+                             P(w2.data_ptr()), w2.numel(), P(st2.data_ptr()), P(stream.cuda_stream))
+        if rc != 0:
+            raise br.BandredError(rc, "bandred_gb2bd")
+        ev[2].record(stream)
+        rc = L.bandred_bdsv(n, P(d.data_ptr()), P(e.data_ptr()), P(sig.data_ptr()), P(w3.data_ptr()), w3.numel(),
+                            P(stream.cuda_stream))
+        if rc != 0:
+            raise br.BandredError(rc, "bandred_bdsv")
+        ev[3].record(stream)
+        torch.cuda.synchronize(dev)
+    if int(st.item()) != 0 or int(st2.item()) != 0:
+        raise br.BandredError(int(st.item()) or int(st2.item()), "device status (singular-value path)")
+    ms = [ev[q].elapsed_time(ev[q + 1]) for q in range(3)]
+    out = {"workload": prob["desc"].replace("sy2sb", "ge2gb") + " precision=ozaki, then band -> bidiagonal and "
+           "trisection on the Golub-Kahan tridiagonal",
+           "ge2gb_ms": ms[0], "gb2bd_ms": ms[1], "bdsv_ms": ms[2], "total_ms": sum(ms)}
+    if prob.get("lam") is not None:
+        st_ = np.sort(np.abs(np.asarray(prob["lam"])))[::-1]
+        out["max_sv_error_rel"] = float(np.max(np.abs(sig.cpu().numpy() - st_)) / st_[0])
     del A
     return out
 

@@ -77,6 +77,9 @@ int sb2st_run(int64_t n, int64_t w, const double* A, int64_t lda, double* d, dou
               void* work, int* dev_status, cudaStream_t s);
 size_t sterf_workspace_bytes(int64_t n);
 int sterf_run(int64_t n, const double* d, const double* e, double* lam, void* work, cudaStream_t s);
+// eigenvalues k0 .. k0 + count - 1 (ascending) of (d, e) into lam[0 .. count)
+int sterf_range_run(int64_t n, const double* d, const double* e, double* lam, int64_t k0, int64_t count, void* work,
+                    cudaStream_t s);
 size_t gb2bd_workspace_bytes(int64_t n, int64_t w);
 int gb2bd_run(int64_t n, int64_t w, const double* A, int64_t lda, double* d, double* e, unsigned long long limit_ns,
               void* work, int* dev_status, cudaStream_t s);

@@ -278,10 +278,10 @@ __global__ void tgk_kernel(int n, const double* d, const double* e, double* z, d
   }
 }
 
-// The singular values, descending: the n largest eigenvalues of the Golub-Kahan
-// tridiagonal (its eigenvalues are +-sigma_k).
+// The singular values, descending, from the n largest eigenvalues of the Golub-Kahan
+// tridiagonal (its eigenvalues are +-sigma_k), ascending in lam[0 .. n).
 __global__ void sv_out_kernel(int n, const double* lam, double* sig) {
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) sig[k] = lam[2 * n - 1 - k];
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) sig[k] = lam[n - 1 - k];
 }
 
 struct GbWs {
@@ -369,7 +369,8 @@ int bdsv_run(int64_t n, const double* d, const double* e, double* sig, void* wor
   prof::count_launch();
   tgk_kernel<<<blocks, 256, 0, s>>>((int)n, d, e, z, o);
   CKG(cudaGetLastError());
-  const int rc = sterf_run(2 * n, z, o, lam, sw, s);
+  // only the upper half of the Golub-Kahan spectrum: eigenvalues n .. 2n - 1
+  const int rc = sterf_range_run(2 * n, z, o, lam, n, n, sw, s);
   if (rc != 0) return rc;
   prof::count_launch();
   sv_out_kernel<<<blocks, 256, 0, s>>>((int)n, lam, sig);

@@ -794,10 +794,12 @@ __device__ __forceinline__ int sturm_count(int n, const double* d, const double*
 // eigenvalue and round, two chains per lane, were measured slower): two lanes per
 // eigenvalue give twice the warps of bisection (512 at n = 8192, for 608 sub-partitions)
 // at a third fewer sequential rounds.
-__global__ void sterf_trisect_kernel(int n, const double* d, const double* e2, const double* prm, double* lam) {
+// Eigenvalues k0 .. k0 + count - 1 (ascending) into lam[0 .. count).
+__global__ void sterf_trisect_kernel(int n, const double* d, const double* e2, const double* prm, double* lam,
+                                     int k0, int count) {
   pdl_wait_and_release();
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  const int k = min(g >> 1, n - 1), half = g & 1;
+  const int k = k0 + min(g >> 1, count - 1), half = g & 1;
   const double tol = prm[2], pivmin = prm[3];
   double lo = prm[0], hi = prm[1];
   // rounds until the width falls to tol: the same for every pair
@@ -818,7 +820,7 @@ __global__ void sterf_trisect_kernel(int n, const double* d, const double* e2, c
       lo = x2;
     }
   }
-  if (!half && (g >> 1) < n) lam[k] = 0.5 * (lo + hi);
+  if (!half && (g >> 1) < count) lam[k - k0] = 0.5 * (lo + hi);
 }
 
 struct Sb2stWs {
@@ -904,15 +906,20 @@ int sb2st_run(int64_t n, int64_t w, const double* A, int64_t lda, double* d, dou
 }
 
 int sterf_run(int64_t n, const double* d, const double* e, double* lam, void* work, cudaStream_t s) {
-  if (n <= 0) return 0;
+  return sterf_range_run(n, d, e, lam, 0, n, work, s);
+}
+
+int sterf_range_run(int64_t n, const double* d, const double* e, double* lam, int64_t k0, int64_t count, void* work,
+                    cudaStream_t s) {
+  if (n <= 0 || count <= 0) return 0;
   double* e2 = static_cast<double*>(work);
   double* prm = reinterpret_cast<double*>(static_cast<char*>(work) +
                                           (sizeof(double) * (size_t)std::max<int64_t>(n, 1) + 255) / 256 * 256);
   prof::count_launch();
   CKS(launch_pdl(sterf_setup_kernel, dim3(1), dim3(kGThreads), 0, s, (int)n, d, e, e2, prm));
   prof::count_launch();
-  CKS(launch_pdl(sterf_trisect_kernel, dim3((unsigned)((2 * n + 63) / 64)), dim3(64), 0, s, (int)n, d,
-                 static_cast<const double*>(e2), static_cast<const double*>(prm), lam));
+  CKS(launch_pdl(sterf_trisect_kernel, dim3((unsigned)((2 * count + 63) / 64)), dim3(64), 0, s, (int)n, d,
+                 static_cast<const double*>(e2), static_cast<const double*>(prm), lam, (int)k0, (int)count));
   return 0;
 }
 
