@@ -251,6 +251,160 @@ __global__ void __launch_bounds__(kGbThreads) gb2bd_chase_kernel(GbParams p) {
   }
 }
 
+// The same chase with the step's entries in shared memory (w <= 64), one thread per
+// vector.  A step touches the rows (r, a + w) of columns [a, a + w) (right reflector) and
+// the rows [a, a + w) of columns (a, a + 2w) (left reflector); both sit in the tile of rows
+// (r, a + w) by columns [a, a + 2w), staged once (its top-right corner, rows (r, a) by
+// columns [a + w, a + 2w), lies outside the band store and is neither read nor written),
+// with a row stride of kGTLd = 129 doubles: a thread per row steps by 1 and a thread per
+// column by 129 = 1 (mod 16) words, free of bank conflicts.  The reflectors' own row r and
+// column a go to global memory directly.
+constexpr int kGTMaxW = 64;
+constexpr int kGTLd = 2 * kGTMaxW + 1;
+constexpr size_t kSmemGbTile = sizeof(double) * ((size_t)(2 * kGTMaxW - 1) * kGTLd + 2 * kGTMaxW);
+
+__global__ void __launch_bounds__(kGbThreads) gb2bd_chase_smem_kernel(GbParams p) {
+  extern __shared__ double gt_smem[];
+  double* U = gt_smem;                                       // (i, j) at (i - r - 1) kGTLd + (j - a)
+  double* v = U + (size_t)(2 * kGTMaxW - 1) * kGTLd;         // the reflector
+  double* xr = v + kGTMaxW;                                  // row r's entries [a, end)
+  __shared__ double s_tau;
+  __shared__ int s_ok;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int n = p.n, w = p.w;
+  for (int c = blockIdx.x; c + 1 < n; c += gridDim.x) {
+    int r = c, a = c + 1, t = 0;
+    while (true) {
+      const int end = min(a + w, n), len = end - a;
+      if (len < 2) break;
+      if (tid == 0) {
+        int ok = 1;
+        if (c > 0) {
+          unsigned long long t0 = 0;
+          unsigned int spins = 0;
+          while (gb_ld_acquire(&p.prog[c - 1]) < t + 3) {
+            if ((++spins & 63u) == 0u) {
+              const unsigned long long now = global_ns();
+              if (t0 == 0) t0 = now;
+              else if (now - t0 > p.limit_ns) {
+                if (p.status) atomicCAS(p.status, 0, BANDRED_DEV_TIMEOUT);
+                ok = 0;
+                break;
+              }
+              if (p.status && gb_ld_acquire(p.status) != 0) { ok = 0; break; }
+            }
+          }
+        }
+        s_ok = ok;
+      }
+      __syncthreads();
+      if (!s_ok) return;
+      // the tile: rows (r, rend), columns [a, cend); entry (i, j) belongs to the step when
+      // j < end (right reflector) or a <= i < end (left reflector)
+      const int rend = min(a + w, n), cend = min(a + 2 * w, n);
+      const int nr = rend - r - 1, nc = cend - a;
+      for (int q = tid; q < nr * nc; q += kGbThreads) {
+        const int jj = q / nr, ii = q - jj * nr;
+        const int i = r + 1 + ii, j = a + jj;
+        const bool mine = j < end || (i >= a && i < end);
+        U[(size_t)ii * kGTLd + jj] = mine ? gld(p, i, j) : 0.0;
+      }
+      if (tid < len) xr[tid] = gld(p, r, a + tid);
+      __syncthreads();
+
+      // right reflector from row r (warp 0); row r becomes (beta, 0, ..)
+      if (warp == 0) {
+        double xv[4], tau, beta, scal, sx;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int j = lane + 32 * u;
+          xv[u] = j < len ? xr[j] : 0.0;
+        }
+        warp_reflector(xv, len, lane, tau, beta, scal, sx);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int j = lane + 32 * u;
+          if (j < len) {
+            v[j] = j == 0 ? 1.0 : (xv[u] * sx) * scal;
+            gst(p, r, a + j, j == 0 ? beta : 0.0);
+          }
+        }
+        if (lane == 0) s_tau = tau;
+      }
+      __syncthreads();
+      double tau = s_tau;
+      if (tau != 0.0 && tid < nr) {  // one thread per row of the tile, columns [a, end)
+        double* b = U + (size_t)tid * kGTLd;
+        double z0 = 0.0, z1 = 0.0;
+        int k = 0;
+        for (; k + 1 < len; k += 2) {
+          z0 = fma(b[k], v[k], z0);
+          z1 = fma(b[k + 1], v[k + 1], z1);
+        }
+        if (k < len) z0 = fma(b[k], v[k], z0);
+        const double z = tau * (z0 + z1);
+        for (k = 0; k < len; ++k) b[k] = fma(-z, v[k], b[k]);
+      }
+      __syncthreads();
+
+      // left reflector from column a, rows [a, end) (tile rows a - r - 1 ..); the column
+      // becomes (beta, 0, ..)^T, in the tile and in global memory
+      const int ia = a - r - 1;
+      if (warp == 0) {
+        double xv[4], tl, beta, scal, sx;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = lane + 32 * u;
+          xv[u] = i < len ? U[(size_t)(ia + i) * kGTLd] : 0.0;
+        }
+        warp_reflector(xv, len, lane, tl, beta, scal, sx);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = lane + 32 * u;
+          if (i < len) {
+            v[i] = i == 0 ? 1.0 : (xv[u] * sx) * scal;
+            U[(size_t)(ia + i) * kGTLd] = i == 0 ? beta : 0.0;
+          }
+        }
+        if (lane == 0) s_tau = tl;
+      }
+      __syncthreads();
+      tau = s_tau;
+      if (tau != 0.0 && tid >= 1 && tid < nc) {  // one thread per column (a, cend), rows [a, end)
+        double* b = U + (size_t)ia * kGTLd + tid;
+        double z0 = 0.0, z1 = 0.0;
+        int i = 0;
+        for (; i + 1 < len; i += 2) {
+          z0 = fma(v[i], b[(size_t)i * kGTLd], z0);
+          z1 = fma(v[i + 1], b[(size_t)(i + 1) * kGTLd], z1);
+        }
+        if (i < len) z0 = fma(v[i], b[(size_t)i * kGTLd], z0);
+        const double z = tau * (z0 + z1);
+        for (i = 0; i < len; ++i) b[(size_t)i * kGTLd] = fma(-z, v[i], b[(size_t)i * kGTLd]);
+      }
+      __syncthreads();
+      // the step's entries back to the band store, column by column
+      for (int q = tid; q < nr * nc; q += kGbThreads) {
+        const int jj = q / nr, ii = q - jj * nr;
+        const int i = r + 1 + ii, j = a + jj;
+        if (j < end || (i >= a && i < end)) gst(p, i, j, U[(size_t)ii * kGTLd + jj]);
+      }
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        gb_st_release(&p.prog[c], t + 1);
+      }
+      r = a;
+      a += w;
+      ++t;
+    }
+    if (tid == 0) {
+      __threadfence();
+      gb_st_release(&p.prog[c], kGbDone);
+    }
+  }
+}
+
 // Band store from the upper band of A (0 <= j - i <= w; everything else of A, such as the
 // reflectors of a packed ge2gb result, is not read), zeros elsewhere.
 __global__ void gb_band_in_kernel(int n, int w, int up, int LB, const double* A, int64_t lda, double* Bs) {
@@ -341,7 +495,18 @@ int gb2bd_run(int64_t n, int64_t w, const double* A, int64_t lda, double* d, dou
     GbParams p{(int)n, (int)w, up, LB, ws.Bs, ws.prog, status, limit_ns};
     void* args[] = {&p};
     prof::count_launch();
-    CKG(cudaLaunchCooperativeKernel((const void*)gb2bd_chase_kernel, dim3(G), dim3(kGbThreads), args, 0, s));
+    if (w <= kGTMaxW) {
+      static int configured = -1;
+      if (configured != dev) {
+        CKG(cudaFuncSetAttribute(gb2bd_chase_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kSmemGbTile));
+        configured = dev;
+      }
+      CKG(cudaLaunchCooperativeKernel((const void*)gb2bd_chase_smem_kernel, dim3(G), dim3(kGbThreads), args,
+                                      kSmemGbTile, s));
+    } else {
+      CKG(cudaLaunchCooperativeKernel((const void*)gb2bd_chase_kernel, dim3(G), dim3(kGbThreads), args, 0, s));
+    }
   }
   {
     const int blocks = (int)std::min<int64_t>((n + 255) / 256, 1024);
