@@ -22,10 +22,15 @@
 // 0 .. 3w - 1 for i - j from -(2w - 1) to w), resident in L2 (n = 8192, w = 64: 12.6 MB).
 // One persistent cooperative kernel: CTA g runs sweeps g, g + G, ... in order, one warp
 // per vector, and each sweep publishes its progress in a counter.  On a dense copy, step t
-// of sweep c touches entries of sweep c - 1's steps up to t + 2 (at t + 2 a single entry,
-// the first of that step's right-reflector row), so step t waits until sweep c - 1 has
-// finished its step t + 2.  The waits are bounded: past the time limit the kernel records
-// BANDRED_DEV_TIMEOUT and returns.
+// of sweep c touches entries of sweep c - 1's steps up to t + 2, at t + 2 a single entry:
+// the first of that step's right-reflector row.  The L2 kernel (w <= 128) waits until
+// sweep c - 1 has finished its step t + 2.  The shared-memory kernel (w <= 64) forms each
+// step's right reflector during the step before, as soon as that row is final, and
+// writes the row then; a counter value of t + 1 means "steps <= t done and step t + 1's
+// row written", and step t waits for t + 2 (a CPU simulation that interleaves concurrent
+// sweeps phase by phase under either rule reproduces the sequential result bit for bit).
+// The waits are bounded: past the time limit the kernel records BANDRED_DEV_TIMEOUT and
+// returns.
 #include <algorithm>
 #include <cstdint>
 
@@ -257,18 +262,19 @@ __global__ void __launch_bounds__(kGbThreads) gb2bd_chase_kernel(GbParams p) {
 // (r, a + w) by columns [a, a + 2w), staged once (its top-right corner, rows (r, a) by
 // columns [a + w, a + 2w), lies outside the band store and is neither read nor written),
 // with a row stride of kGTLd = 129 doubles: a thread per row steps by 1 and a thread per
-// column by 129 = 1 (mod 16) words, free of bank conflicts.  The reflectors' own row r and
-// column a go to global memory directly.
+// column by 129 = 1 (mod 16) words, free of bank conflicts.  The left reflector's column a
+// and the next step's right-reflector row a are set to (beta, 0, ..) in the tile and go
+// out with its write-back; a sweep's first right-reflector row goes out directly.
 constexpr int kGTMaxW = 64;
 constexpr int kGTLd = 2 * kGTMaxW + 1;
-constexpr size_t kSmemGbTile = sizeof(double) * ((size_t)(2 * kGTMaxW - 1) * kGTLd + 2 * kGTMaxW);
+constexpr size_t kSmemGbTile = sizeof(double) * ((size_t)(2 * kGTMaxW - 1) * kGTLd + 2 * kGTMaxW);  // tile, v, vr
 
 __global__ void __launch_bounds__(kGbThreads) gb2bd_chase_smem_kernel(GbParams p) {
   extern __shared__ double gt_smem[];
   double* U = gt_smem;                                       // (i, j) at (i - r - 1) kGTLd + (j - a)
-  double* v = U + (size_t)(2 * kGTMaxW - 1) * kGTLd;         // the reflector
-  double* xr = v + kGTMaxW;                                  // row r's entries [a, end)
-  __shared__ double s_tau;
+  double* v = U + (size_t)(2 * kGTMaxW - 1) * kGTLd;         // the left reflector
+  double* vr = v + kGTMaxW;                                  // the right reflector (formed a step early)
+  __shared__ double s_tau, s_taur;
   __shared__ int s_ok;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = p.n, w = p.w;
@@ -282,7 +288,7 @@ __global__ void __launch_bounds__(kGbThreads) gb2bd_chase_smem_kernel(GbParams p
         if (c > 0) {
           unsigned long long t0 = 0;
           unsigned int spins = 0;
-          while (gb_ld_acquire(&p.prog[c - 1]) < t + 3) {
+          while (gb_ld_acquire(&p.prog[c - 1]) < t + 2) {
             if ((++spins & 63u) == 0u) {
               const unsigned long long now = global_ns();
               if (t0 == 0) t0 = now;
@@ -309,41 +315,39 @@ __global__ void __launch_bounds__(kGbThreads) gb2bd_chase_smem_kernel(GbParams p
         const bool mine = j < end || (i >= a && i < end);
         U[(size_t)ii * kGTLd + jj] = mine ? gld(p, i, j) : 0.0;
       }
-      if (tid < len) xr[tid] = gld(p, r, a + tid);
-      __syncthreads();
-
-      // right reflector from row r (warp 0); row r becomes (beta, 0, ..)
-      if (warp == 0) {
+      if (t == 0 && warp == 0) {
+        // a sweep's first right reflector, from row r; row r becomes (beta, 0, ..).  The
+        // later ones are formed by the step before (below), from its final row a
         double xv[4], tau, beta, scal, sx;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int j = lane + 32 * u;
-          xv[u] = j < len ? xr[j] : 0.0;
+          xv[u] = j < len ? gld(p, r, a + j) : 0.0;
         }
         warp_reflector(xv, len, lane, tau, beta, scal, sx);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int j = lane + 32 * u;
           if (j < len) {
-            v[j] = j == 0 ? 1.0 : (xv[u] * sx) * scal;
+            vr[j] = j == 0 ? 1.0 : (xv[u] * sx) * scal;
             gst(p, r, a + j, j == 0 ? beta : 0.0);
           }
         }
-        if (lane == 0) s_tau = tau;
+        if (lane == 0) s_taur = tau;
       }
       __syncthreads();
-      double tau = s_tau;
+      double tau = s_taur;
       if (tau != 0.0 && tid < nr) {  // one thread per row of the tile, columns [a, end)
         double* b = U + (size_t)tid * kGTLd;
         double z0 = 0.0, z1 = 0.0;
         int k = 0;
         for (; k + 1 < len; k += 2) {
-          z0 = fma(b[k], v[k], z0);
-          z1 = fma(b[k + 1], v[k + 1], z1);
+          z0 = fma(b[k], vr[k], z0);
+          z1 = fma(b[k + 1], vr[k + 1], z1);
         }
-        if (k < len) z0 = fma(b[k], v[k], z0);
+        if (k < len) z0 = fma(b[k], vr[k], z0);
         const double z = tau * (z0 + z1);
-        for (k = 0; k < len; ++k) b[k] = fma(-z, v[k], b[k]);
+        for (k = 0; k < len; ++k) b[k] = fma(-z, vr[k], b[k]);
       }
       __syncthreads();
 
@@ -381,6 +385,32 @@ __global__ void __launch_bounds__(kGbThreads) gb2bd_chase_smem_kernel(GbParams p
         if (i < len) z0 = fma(v[i], b[(size_t)i * kGTLd], z0);
         const double z = tau * (z0 + z1);
         for (i = 0; i < len; ++i) b[(size_t)i * kGTLd] = fma(-z, v[i], b[(size_t)i * kGTLd]);
+      }
+      __syncthreads();
+      // the next step's right reflector, from row a (tile row ia) over columns
+      // [a + w, a + w + nl), final now; the row becomes (beta, 0, ..) in the tile and goes
+      // out with the write-back below.  This row's first entry is the one entry the sweep
+      // after shares with the next step, so with it written at this step's release the
+      // sweep after may run two steps behind instead of three.
+      const int nl = min(a + 2 * w, n) - (a + w);
+      if (nl >= 2 && warp == 0) {
+        double xv[4], tn, beta, scal, sx;
+        double* row = U + (size_t)ia * kGTLd + w;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int j = lane + 32 * u;
+          xv[u] = j < nl ? row[j] : 0.0;
+        }
+        warp_reflector(xv, nl, lane, tn, beta, scal, sx);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int j = lane + 32 * u;
+          if (j < nl) {
+            vr[j] = j == 0 ? 1.0 : (xv[u] * sx) * scal;
+            row[j] = j == 0 ? beta : 0.0;
+          }
+        }
+        if (lane == 0) s_taur = tn;
       }
       __syncthreads();
       // the step's entries back to the band store, column by column
