@@ -267,13 +267,39 @@ __global__ void __launch_bounds__(kGbThreads) gb2bd_chase_kernel(GbParams p) {
 // out with its write-back; a sweep's first right-reflector row goes out directly.
 constexpr int kGTMaxW = 64;
 constexpr int kGTLd = 2 * kGTMaxW + 1;
-constexpr size_t kSmemGbTile = sizeof(double) * ((size_t)(2 * kGTMaxW - 1) * kGTLd + 2 * kGTMaxW);  // tile, v, vr
+constexpr size_t kSmemGbTile = sizeof(double) * ((size_t)(2 * kGTMaxW - 1) * kGTLd + 2 * kGTMaxW + 4 * kGTMaxW);  // tile, v, vr, zp
+static_assert(kGTMaxW == 64 && kGbThreads == 256, "two threads per vector, 32 entries each");
+
+// Half of a vector (entries k0 .. k0 + 31 below len): y[kk] = b[kk st] in registers, and
+// sum v[k0 + kk] y[kk] (four chains); then b[kk st] = y[kk] - z v[k0 + kk].
+__device__ __forceinline__ double gb_half_load_dot(const double* b, int st, const double* v, int k0, int len,
+                                                   double (&y)[32]) {
+#pragma unroll
+  for (int kk = 0; kk < 32; ++kk) y[kk] = k0 + kk < len ? b[kk * st] : 0.0;
+  double z0 = 0.0, z1 = 0.0, z2 = 0.0, z3 = 0.0;
+#pragma unroll
+  for (int kk = 0; kk < 32; kk += 4) {
+    if (k0 + kk < len) z0 = fma(v[k0 + kk], y[kk], z0);
+    if (k0 + kk + 1 < len) z1 = fma(v[k0 + kk + 1], y[kk + 1], z1);
+    if (k0 + kk + 2 < len) z2 = fma(v[k0 + kk + 2], y[kk + 2], z2);
+    if (k0 + kk + 3 < len) z3 = fma(v[k0 + kk + 3], y[kk + 3], z3);
+  }
+  return (z0 + z1) + (z2 + z3);
+}
+__device__ __forceinline__ void gb_half_update(double* b, int st, const double* v, int k0, int len, double z,
+                                               const double (&y)[32]) {
+#pragma unroll
+  for (int kk = 0; kk < 32; ++kk) {
+    if (k0 + kk < len) b[kk * st] = fma(-z, v[k0 + kk], y[kk]);
+  }
+}
 
 __global__ void __launch_bounds__(kGbThreads) gb2bd_chase_smem_kernel(GbParams p) {
   extern __shared__ double gt_smem[];
   double* U = gt_smem;                                       // (i, j) at (i - r - 1) kGTLd + (j - a)
   double* v = U + (size_t)(2 * kGTMaxW - 1) * kGTLd;         // the left reflector
   double* vr = v + kGTMaxW;                                  // the right reflector (formed a step early)
+  double* zp = vr + kGTMaxW;                                 // the two halves' dot products, per vector
   __shared__ double s_tau, s_taur;
   __shared__ int s_ok;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -337,17 +363,16 @@ __global__ void __launch_bounds__(kGbThreads) gb2bd_chase_smem_kernel(GbParams p
       }
       __syncthreads();
       double tau = s_taur;
-      if (tau != 0.0 && tid < nr) {  // one thread per row of the tile, columns [a, end)
-        double* b = U + (size_t)tid * kGTLd;
-        double z0 = 0.0, z1 = 0.0;
-        int k = 0;
-        for (; k + 1 < len; k += 2) {
-          z0 = fma(b[k], vr[k], z0);
-          z1 = fma(b[k + 1], vr[k + 1], z1);
-        }
-        if (k < len) z0 = fma(b[k], vr[k], z0);
-        const double z = tau * (z0 + z1);
-        for (k = 0; k < len; ++k) b[k] = fma(-z, vr[k], b[k]);
+      // the right reflector on the tile's rows (columns [a, end)): two threads per row,
+      // thread q + 128 h taking columns a + 32 h .. a + 32 h + 31, so all eight warps work
+      {
+        const int q = tid & 127, h = tid >> 7, k0 = 32 * h;
+        const bool have = tau != 0.0 && q < nr;
+        double* b = U + (size_t)q * kGTLd + k0;
+        double y[32];
+        if (have) zp[h * 128 + q] = gb_half_load_dot(b, 1, vr, k0, len, y);
+        __syncthreads();
+        if (have) gb_half_update(b, 1, vr, k0, len, tau * (zp[q] + zp[128 + q]), y);
       }
       __syncthreads();
 
@@ -374,17 +399,16 @@ __global__ void __launch_bounds__(kGbThreads) gb2bd_chase_smem_kernel(GbParams p
       }
       __syncthreads();
       tau = s_tau;
-      if (tau != 0.0 && tid >= 1 && tid < nc) {  // one thread per column (a, cend), rows [a, end)
-        double* b = U + (size_t)ia * kGTLd + tid;
-        double z0 = 0.0, z1 = 0.0;
-        int i = 0;
-        for (; i + 1 < len; i += 2) {
-          z0 = fma(v[i], b[(size_t)i * kGTLd], z0);
-          z1 = fma(v[i + 1], b[(size_t)(i + 1) * kGTLd], z1);
-        }
-        if (i < len) z0 = fma(v[i], b[(size_t)i * kGTLd], z0);
-        const double z = tau * (z0 + z1);
-        for (i = 0; i < len; ++i) b[(size_t)i * kGTLd] = fma(-z, v[i], b[(size_t)i * kGTLd]);
+      // the left reflector on columns (a, cend) (rows [a, end)): two threads per column,
+      // thread q + 128 h taking rows a + 32 h .. a + 32 h + 31
+      {
+        const int q = tid & 127, h = tid >> 7, i0 = 32 * h;
+        const bool have = tau != 0.0 && q >= 1 && q < nc;
+        double* b = U + (size_t)(ia + i0) * kGTLd + q;
+        double y[32];
+        if (have) zp[h * 128 + q] = gb_half_load_dot(b, kGTLd, v, i0, len, y);
+        __syncthreads();
+        if (have) gb_half_update(b, kGTLd, v, i0, len, tau * (zp[q] + zp[128 + q]), y);
       }
       __syncthreads();
       // the next step's right reflector, from row a (tile row ia) over columns
