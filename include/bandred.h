@@ -244,7 +244,9 @@ int bandred_ge2bb_ex(int64_t m, int64_t n, int64_t w, double* A, int64_t lda, do
  *   for w > 128, or a CUDA error code.
  * bandred_sterf: eigenvalues of the symmetric tridiagonal (d, e) (device, n and n - 1
  *   entries) into lam (device, n, ascending), by trisection on Sturm counts (two lanes per
- *   eigenvalue) to within a few units in the last place of max |T|.  work: device,
+ *   eigenvalue; a first pass on an FP32 copy of T narrows each bracket, widened well past
+ *   its roundoff before the FP64 rounds) to within a few units in the last place of
+ *   max |T|.  work: device,
  *   256-byte aligned, >= bandred_sterf_workspace(n) bytes.  Returns 0, -i for an invalid i-th argument.
  */
 size_t bandred_sb2st_workspace(int64_t n, int64_t w);

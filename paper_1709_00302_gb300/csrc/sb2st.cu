@@ -712,7 +712,10 @@ namespace {
 // Gershgorin interval [gl, gu], the stopping width and the pivot guard of the trisection,
 // and e^2 (one CTA): prm = {gl, gu, tol, pivmin}.
 constexpr int kGThreads = 256;
-__global__ void sterf_setup_kernel(int n, const double* d, const double* e, double* e2, double* prm) {
+// Also the scale sc = 2^-k with max |T| sc in [1/2, 1) (prm[4]) and the scaled copy of T in
+// FP32 for the first pass: d32 = d sc, e32 = e^2 sc^2.
+__global__ void sterf_setup_kernel(int n, const double* d, const double* e, double* e2, double* prm, float* d32,
+                                   float* e32) {
   __shared__ double s_lo[kGThreads], s_hi[kGThreads], s_mx[kGThreads], s_e2[kGThreads];
   pdl_wait_and_release();
   const int tid = threadIdx.x;
@@ -748,7 +751,33 @@ __global__ void sterf_setup_kernel(int n, const double* d, const double* e, doub
     prm[1] = s_hi[0] + tol;
     prm[2] = tol;
     prm[3] = fmax(s_e2[0], 1.0) * 0x1p-1020;
+    int k = 0;
+    if (s_mx[0] > 0.0) frexp(s_mx[0], &k);
+    prm[4] = ldexp(1.0, -k);
   }
+  __syncthreads();
+  const double sc = prm[4];
+  for (int i = tid; i < n; i += kGThreads) {
+    d32[i] = (float)(d[i] * sc);
+    if (i + 1 < n) e32[i] = (float)((e2[i] * sc) * sc);
+  }
+}
+
+// Sturm count of the scaled FP32 copy of T at x (entries below 1 in magnitude; the pivot
+// guard 2^-100), FP32 arithmetic throughout: a quick first pass, whose counts are exact
+// for a matrix within about 7 units of FP32 roundoff of max |T| (the recurrence's backward
+// error, with the rounding of the copy itself).
+__device__ __forceinline__ int sturm_count32(int n, const float* d, const float* e2, float x) {
+  constexpr float kPiv = 0x1p-100f;
+  float q = d[0] - x;
+  if (fabsf(q) < kPiv) q = -kPiv;
+  int neg = q < 0.0f;
+  for (int i = 1; i < n; ++i) {
+    q = (d[i] - x) - e2[i - 1] * __frcp_rn(q);
+    if (fabsf(q) < kPiv) q = -kPiv;
+    neg += q < 0.0f;
+  }
+  return neg;
 }
 
 // 1/s for a normal s > 0: an FP32 seed r0 of the mantissa m, then one cubic Newton step
@@ -796,15 +825,43 @@ __device__ __forceinline__ int sturm_count(int n, const double* d, const double*
 // at a third fewer sequential rounds.
 // Eigenvalues k0 .. k0 + count - 1 (ascending) into lam[0 .. count).
 __global__ void sterf_trisect_kernel(int n, const double* d, const double* e2, const double* prm, double* lam,
-                                     int k0, int count) {
+                                     int k0, int count, const float* d32, const float* e32) {
   pdl_wait_and_release();
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   const int k = k0 + min(g >> 1, count - 1), half = g & 1;
-  const double tol = prm[2], pivmin = prm[3];
+  const double tol = prm[2], pivmin = prm[3], sc = prm[4];
   double lo = prm[0], hi = prm[1];
-  // rounds until the width falls to tol: the same for every pair
+  // First pass in FP32 on T sc (max |T sc| in [1/2, 1)), by the same trisection, down to a
+  // width of 2^-14; the bracket then widens by 2^-16 on each side, far beyond the FP32
+  // pass's error (about 7 x 2^-24), and the FP64 rounds start from there.
+  {
+    float lo32 = (float)(lo * sc), hi32 = (float)(hi * sc);
+    int r32 = 0;
+    for (double wd = (double)hi32 - (double)lo32; wd > 0x1p-14 && r32 < 60; wd *= (1.0 / 3.0)) ++r32;
+    for (int it = 0; it < r32; ++it) {
+      const float h = (hi32 - lo32) * (1.0f / 3.0f);
+      const float x1 = lo32 + h, x2 = hi32 - h;
+      const int c = sturm_count32(n, d32, e32, half ? x2 : x1);
+      const int c1 = __shfl_xor_sync(0xffffffffu, c, 1);
+      const int ca = half ? c1 : c, cb = half ? c : c1;
+      if (ca > k) {
+        hi32 = x1;
+      } else if (cb > k) {
+        lo32 = x1;
+        hi32 = x2;
+      } else {
+        lo32 = x2;
+      }
+    }
+    const double m = 0x1p-16 / sc;
+    lo = fmax(prm[0], (double)lo32 / sc - m);
+    hi = fmin(prm[1], (double)hi32 / sc + m);
+  }
+  // FP64 rounds until the width falls to tol, from the widest bracket the first pass can
+  // leave: the same for every pair
   int rounds = 0;
-  for (double wd = hi - lo; wd > tol && rounds < 120; wd *= (1.0 / 3.0)) ++rounds;
+  const double w0 = fmin(prm[1] - prm[0], (0x1p-14 * 1.001 + 0x1p-15) / sc);
+  for (double wd = w0; wd > tol && rounds < 120; wd *= (1.0 / 3.0)) ++rounds;
   for (int it = 0; it < rounds; ++it) {
     const double h = (hi - lo) * (1.0 / 3.0);
     const double x1 = lo + h, x2 = hi - h;
@@ -850,7 +907,10 @@ Sb2stWs carve_sb2st(void* work, int64_t n, int64_t w) {
 
 size_t sb2st_workspace_bytes(int64_t n, int64_t w) { return carve_sb2st(nullptr, n, w).bytes; }
 
-size_t sterf_workspace_bytes(int64_t n) { return (sizeof(double) * (size_t)std::max<int64_t>(n, 1) + 255) / 256 * 256 + 256; }
+size_t sterf_workspace_bytes(int64_t n) {
+  const size_t nn = (size_t)std::max<int64_t>(n, 1);
+  return (sizeof(double) * nn + 255) / 256 * 256 + 256 + 2 * ((sizeof(float) * nn + 255) / 256 * 256);
+}
 
 #define CKS(call)                                                 \
   do {                                                            \
@@ -912,14 +972,18 @@ int sterf_run(int64_t n, const double* d, const double* e, double* lam, void* wo
 int sterf_range_run(int64_t n, const double* d, const double* e, double* lam, int64_t k0, int64_t count, void* work,
                     cudaStream_t s) {
   if (n <= 0 || count <= 0) return 0;
-  double* e2 = static_cast<double*>(work);
-  double* prm = reinterpret_cast<double*>(static_cast<char*>(work) +
-                                          (sizeof(double) * (size_t)std::max<int64_t>(n, 1) + 255) / 256 * 256);
+  const size_t nn = (size_t)std::max<int64_t>(n, 1);
+  char* base = static_cast<char*>(work);
+  double* e2 = reinterpret_cast<double*>(base);
+  double* prm = reinterpret_cast<double*>(base + (sizeof(double) * nn + 255) / 256 * 256);
+  float* d32 = reinterpret_cast<float*>(reinterpret_cast<char*>(prm) + 256);
+  float* e32 = reinterpret_cast<float*>(reinterpret_cast<char*>(d32) + (sizeof(float) * nn + 255) / 256 * 256);
   prof::count_launch();
-  CKS(launch_pdl(sterf_setup_kernel, dim3(1), dim3(kGThreads), 0, s, (int)n, d, e, e2, prm));
+  CKS(launch_pdl(sterf_setup_kernel, dim3(1), dim3(kGThreads), 0, s, (int)n, d, e, e2, prm, d32, e32));
   prof::count_launch();
   CKS(launch_pdl(sterf_trisect_kernel, dim3((unsigned)((2 * count + 63) / 64)), dim3(64), 0, s, (int)n, d,
-                 static_cast<const double*>(e2), static_cast<const double*>(prm), lam, (int)k0, (int)count));
+                 static_cast<const double*>(e2), static_cast<const double*>(prm), lam, (int)k0, (int)count,
+                 static_cast<const float*>(d32), static_cast<const float*>(e32)));
   return 0;
 }
 
