@@ -20,8 +20,8 @@
 //
 // GB300 mapping.  The band lives in a compact store of 3w rows per column (offsets
 // 0 .. 3w - 1 for i - j from -(2w - 1) to w), resident in L2 (n = 8192, w = 64: 12.6 MB).
-// One persistent cooperative kernel: CTA g runs sweeps g, g + G, ... in order, one warp
-// per vector, and each sweep publishes its progress in a counter.  On a dense copy, step t
+// One persistent cooperative kernel: CTA g runs sweeps g, g + G, ... in order, and each
+// sweep publishes its progress in a counter.  On a dense copy, step t
 // of sweep c touches entries of sweep c - 1's steps up to t + 2, at t + 2 a single entry:
 // the first of that step's right-reflector row.  The L2 kernel (w <= 128) waits until
 // sweep c - 1 has finished its step t + 2.  The shared-memory kernel (w <= 64) forms each
@@ -256,18 +256,20 @@ __global__ void __launch_bounds__(kGbThreads) gb2bd_chase_kernel(GbParams p) {
   }
 }
 
-// The same chase with the step's entries in shared memory (w <= 64), one thread per
-// vector.  A step touches the rows (r, a + w) of columns [a, a + w) (right reflector) and
+// The same chase with the step's entries in shared memory (w <= 64), two threads per
+// vector (each half of its entries, so all eight warps apply each reflector; the halves'
+// dot products meet in shared memory).  A step touches the rows (r, a + w) of columns [a, a + w) (right reflector) and
 // the rows [a, a + w) of columns (a, a + 2w) (left reflector); both sit in the tile of rows
 // (r, a + w) by columns [a, a + 2w), staged once (its top-right corner, rows (r, a) by
 // columns [a + w, a + 2w), lies outside the band store and is neither read nor written),
-// with a row stride of kGTLd = 129 doubles: a thread per row steps by 1 and a thread per
-// column by 129 = 1 (mod 16) words, free of bank conflicts.  The left reflector's column a
+// with a row stride of kGTLd = 129 doubles: threads along a row step by 1 and threads
+// along a column by 129 = 1 (mod 16) words, free of bank conflicts.  The left reflector's column a
 // and the next step's right-reflector row a are set to (beta, 0, ..) in the tile and go
 // out with its write-back; a sweep's first right-reflector row goes out directly.
 constexpr int kGTMaxW = 64;
 constexpr int kGTLd = 2 * kGTMaxW + 1;
-constexpr size_t kSmemGbTile = sizeof(double) * ((size_t)(2 * kGTMaxW - 1) * kGTLd + 2 * kGTMaxW + 4 * kGTMaxW);  // tile, v, vr, zp
+// the tile, the two reflectors, the two halves' dot products
+constexpr size_t kSmemGbTile = sizeof(double) * ((size_t)(2 * kGTMaxW - 1) * kGTLd + 2 * kGTMaxW + 4 * kGTMaxW);
 static_assert(kGTMaxW == 64 && kGbThreads == 256, "two threads per vector, 32 entries each");
 
 // Half of a vector (entries k0 .. k0 + 31 below len): y[kk] = b[kk st] in registers, and
