@@ -82,6 +82,42 @@ def test_invalid_arguments_are_rejected_before_any_device_work(L):
     assert L.bandred_ge2bb_ex(6, 5, 1, fake, 6, null, fake, None, null, 0, null, null) == -6
     assert L.bandred_ge2bb_ex(6, 5, 1, fake, 6, fake, null, None, null, 0, null, null) == -7
     assert L.bandred_ge2bb_ex(6, 5, 6, fake, 6, null, null, None, null, 0, null, null) == -9  # no reflectors
+    # second stage: sb2st, sterf, gb2bd, bdsv (argument order, bandwidth limit, workspace)
+    unsupported = -1003  # BANDRED_ERR_UNSUPPORTED
+    assert L.bandred_sb2st(-1, 4, fake, 1, fake, fake, None, fake, 1 << 20, null, null) == -1
+    assert L.bandred_sb2st(10, 0, fake, 10, fake, fake, None, fake, 1 << 20, null, null) == -2
+    assert L.bandred_sb2st(10, 129, fake, 10, fake, fake, None, fake, 1 << 20, null, null) == unsupported
+    assert L.bandred_sb2st(10, 4, null, 10, fake, fake, None, fake, 1 << 20, null, null) == -3
+    assert L.bandred_sb2st(10, 4, fake, 9, fake, fake, None, fake, 1 << 20, null, null) == -4
+    assert L.bandred_sb2st(10, 4, fake, 10, null, fake, None, fake, 1 << 20, null, null) == -5
+    assert L.bandred_sb2st(10, 4, fake, 10, fake, null, None, fake, 1 << 20, null, null) == -6
+    assert L.bandred_sb2st(10, 4, fake, 10, fake, fake, None, null, 1 << 20, null, null) == -8
+    assert L.bandred_sb2st(10, 4, fake, 10, fake, fake, None, ctypes.c_void_p(4096 + 16), 1 << 20, null, null) == -8
+    assert L.bandred_sb2st(10, 4, fake, 10, fake, fake, None, fake, 8, null, null) == -9
+    assert L.bandred_sterf(-1, fake, fake, fake, fake, 1 << 20, null) == -1
+    assert L.bandred_sterf(10, null, fake, fake, fake, 1 << 20, null) == -2
+    assert L.bandred_sterf(10, fake, null, fake, fake, 1 << 20, null) == -3
+    assert L.bandred_sterf(10, fake, fake, null, fake, 1 << 20, null) == -4
+    assert L.bandred_sterf(10, fake, fake, fake, null, 1 << 20, null) == -5
+    assert L.bandred_sterf(10, fake, fake, fake, fake, 8, null) == -6
+    assert L.bandred_gb2bd(-1, 4, fake, 1, fake, fake, None, fake, 1 << 20, null, null) == -1
+    assert L.bandred_gb2bd(10, 0, fake, 10, fake, fake, None, fake, 1 << 20, null, null) == -2
+    assert L.bandred_gb2bd(10, 129, fake, 10, fake, fake, None, fake, 1 << 20, null, null) == unsupported
+    assert L.bandred_gb2bd(10, 4, null, 10, fake, fake, None, fake, 1 << 20, null, null) == -3
+    assert L.bandred_gb2bd(10, 4, fake, 9, fake, fake, None, fake, 1 << 20, null, null) == -4
+    assert L.bandred_gb2bd(10, 4, fake, 10, null, fake, None, fake, 1 << 20, null, null) == -5
+    assert L.bandred_gb2bd(10, 4, fake, 10, fake, null, None, fake, 1 << 20, null, null) == -6
+    assert L.bandred_gb2bd(10, 4, fake, 10, fake, fake, None, null, 1 << 20, null, null) == -8
+    assert L.bandred_gb2bd(10, 4, fake, 10, fake, fake, None, ctypes.c_void_p(4096 + 16), 1 << 20, null, null) == -8
+    assert L.bandred_gb2bd(10, 4, fake, 10, fake, fake, None, fake, 8, null, null) == -9
+    assert L.bandred_gb2bd_workspace(10, 129) == 0 and L.bandred_gb2bd_workspace(10, 4) >= 3 * 4 * 10 * 8
+    assert L.bandred_bdsv(-1, fake, fake, fake, fake, 1 << 20, null) == -1
+    assert L.bandred_bdsv(10, null, fake, fake, fake, 1 << 20, null) == -2
+    assert L.bandred_bdsv(10, fake, null, fake, fake, 1 << 20, null) == -3
+    assert L.bandred_bdsv(10, fake, fake, null, fake, 1 << 20, null) == -4
+    assert L.bandred_bdsv(10, fake, fake, fake, null, 1 << 20, null) == -5
+    assert L.bandred_bdsv(10, fake, fake, fake, fake, 8, null) == -6
+    assert L.bandred_bdsv_workspace(10) >= L.bandred_sterf_workspace(20)
     # cost model: shape limits, missing pointers
     assert L.bandred_mlp_param_count(8, 32) == 8 * 32 + 32 + 32 * 32 + 3 * 32 + 1 - 32
     assert L.bandred_mlp_param_count(0, 4) == 0 and L.bandred_mlp_param_count(4, 65) == 0
