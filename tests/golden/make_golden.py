@@ -27,6 +27,16 @@ def main():
     G = workloads.gen_gaussian(10, 8, seed=6)
     Gout, tq, tp = oracle.ge2gb(G, 2)
     write("ge2gb_m10_n8_w2.txt", {"A": G, "Aout": Gout, "tauq": tq, "taup": tp})
+    # the second stage: a symmetric band -> tridiagonal, an upper band -> bidiagonal
+    S = workloads.sym_gaussian(14, seed=7)
+    i, j = np.indices(S.shape)
+    S[np.abs(i - j) > 3] = 0.0
+    d, e = oracle.sb2st(np.tril(S), 3)
+    write("sb2st_n14_w3.txt", {"A_lower": np.tril(S), "d": d, "e": e})
+    U = np.triu(workloads.gen_gaussian(14, 14, seed=8))
+    U = U - np.triu(U, 4)
+    d, e = oracle.gb2bd(U, 3)
+    write("gb2bd_n14_w3.txt", {"A_upper": U, "d": d, "e": e})
 
 
 if __name__ == "__main__":

@@ -301,6 +301,14 @@ def test_oracle_matches_its_frozen_outputs():
     np.testing.assert_allclose(Gout, h["Aout"], rtol=0, atol=1e-14)
     np.testing.assert_allclose(tq, h["tauq"].ravel(), rtol=0, atol=1e-15)
     np.testing.assert_allclose(tp, h["taup"].ravel(), rtol=0, atol=1e-15)
+    s = _read_golden("sb2st_n14_w3.txt")
+    d, e = oracle.sb2st(s["A_lower"], 3)
+    np.testing.assert_allclose(d, s["d"].ravel(), rtol=0, atol=1e-14)
+    np.testing.assert_allclose(e, s["e"].ravel(), rtol=0, atol=1e-14)
+    u = _read_golden("gb2bd_n14_w3.txt")
+    d, e = oracle.gb2bd(u["A_upper"], 3)
+    np.testing.assert_allclose(d, u["d"].ravel(), rtol=0, atol=1e-14)
+    np.testing.assert_allclose(e, u["e"].ravel(), rtol=0, atol=1e-14)
 
 
 # --------------------------------------------------------------------------- wide (m < n)
