@@ -343,6 +343,9 @@ __device__ __forceinline__ void chase_issue(const ChaseParams& p, int sx, int lx
   const int j = g + kChaseWarps * lane;
   if (j < lx) bytes = chase_col_bytes(lx, nx, j);
   bytes = __reduce_add_sync(0xffffffffu, bytes);
+  // the band columns were written by other CTAs (generic stores, seen through this
+  // sweep's acquire of the counter) and are read here by the TMA engine (async proxy)
+  tc::fence_proxy_async_global();
   tc::fence_proxy_async();
   if (lane == 0) tc::mbar_arrive_expect_tx(bar, bytes);
   __syncwarp();

@@ -82,6 +82,10 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 // Generic-proxy shared-memory writes -> visible to the async proxy (tcgen05.mma operands).
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// Orders this thread's view of global memory (including writes by other CTAs that an
+// acquire has made visible) before its later bulk copies, which read through the async
+// proxy.
+__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 
 // ---------------------------------------------------------------- TMEM
 // Whole warp: allocates ncols (power of two, >= 32) columns; the address lands in *dst.
