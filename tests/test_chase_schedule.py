@@ -3,10 +3,12 @@
 Both second-stage kernels run every sweep of the chase at once, one CTA per sweep, and
 each sweep waits on a progress counter of the sweep before.  Correctness rests on a rule:
 a sweep's step t may start once the sweep before has published a given count, and every
-value a step reads is then final.  This file models each shared-memory kernel at the
-granularity at which it touches the band store, in NumPy:
+value a step reads is then final.  This file models each of the four chase kernels (the
+shared-memory and the L2 kernel of each second stage) at the granularity at which it
+touches the band store, in NumPy:
 
-* what a step reads, it reads at its start (the blocks it stages, after its wait);
+* what a step reads, it reads at its start (the blocks the shared-memory kernels stage
+  after their wait), or, in the L2 kernels, at the moment one warp updates one vector;
 * what it writes, it writes at the phase where the kernel writes it (the early column or
   row of the next step, the write-back, the diagonal block), and its counter goes up last;
 * what it carries between steps stays private to the sweep.
@@ -145,6 +147,77 @@ def bd_sweep(M, n, w, c):
         r, a, t = a, a + w, t + 1
 
 
+# --------------------------------------------------------------------------- L2 kernels
+def sym_sweep_l2(M, n, w, c):
+    """Sweep c of the symmetric chase as the L2 kernel (w <= 128) runs it: every vector
+    (a bulge column, a row below, a row of the diagonal block) is read and written back at
+    its own moment, one warp at a time."""
+    col, s, t = c, c + 1, 0
+    while True:
+        end = min(s + w, n)
+        ln = end - s
+        if ln < 2:
+            return
+        yield ("start", t)
+        v, tau, beta = larfg(M[s:end, col].copy())
+        M[s:end, col] = 0.0
+        M[s, col] = beta
+        M[col, s:end] = M[s:end, col]
+        yield ("column", t)
+        nl = min(end + w, n) - end
+        if tau != 0.0:
+            for j in range(col + 1, s):  # bulge columns: left application
+                y = M[s:end, j].copy()
+                M[s:end, j] = y - tau * (v @ y) * v
+                M[j, s:end] = M[s:end, j]
+                yield ("vector", t)
+            for i in range(end, end + nl):  # rows below: right application
+                y = M[i, s:end].copy()
+                M[i, s:end] = y - tau * (y @ v) * v
+                M[s:end, i] = M[i, s:end]
+                yield ("vector", t)
+            p = tau * (M[s:end, s:end] @ v)  # the diagonal block's matvec (reads)
+            yield ("matvec", t)
+            K = p - 0.5 * tau * (p @ v) * v
+            D = M[s:end, s:end] - np.outer(v, K) - np.outer(K, v)
+            M[s:end, s:end] = D
+            yield ("diagonal", t)
+        yield ("done", t)
+        col, s, t = s, s + w, t + 1
+
+
+def bd_sweep_l2(M, n, w, c):
+    """Sweep c of the bidiagonal chase as the L2 kernel runs it: each row (right
+    reflector) and column (left reflector) updated at its own moment."""
+    r, a, t = c, c + 1, 0
+    while True:
+        end = min(a + w, n)
+        ln = end - a
+        if ln < 2:
+            return
+        yield ("start", t)
+        v, tau, beta = larfg(M[r, a:end].copy())
+        M[r, a:end] = 0.0
+        M[r, a] = beta
+        yield ("row", t)
+        if tau != 0.0:
+            for i in range(r + 1, min(a + w, n)):
+                y = M[i, a:end].copy()
+                M[i, a:end] = y - tau * (y @ v) * v
+                yield ("vector", t)
+        v, tau, beta = larfg(M[a:end, a].copy())
+        M[a:end, a] = 0.0
+        M[a, a] = beta
+        yield ("column", t)
+        if tau != 0.0:
+            for j in range(a + 1, min(a + 2 * w, n)):
+                y = M[a:end, j].copy()
+                M[a:end, j] = y - tau * (v @ y) * v
+                yield ("vector", t)
+        yield ("done", t)
+        r, a, t = a, a + w, t + 1
+
+
 # --------------------------------------------------------------------------- scheduler
 def run(M0, w, sweep, lag, seed=None):
     """All sweeps of the chase.  seed None: one sweep after the other.  Otherwise random
@@ -228,3 +301,23 @@ def test_a_shorter_lag_shows_a_race(sweep, band):
     A = band(n, w, 5)
     S = run(A, w, sweep, 2)
     assert any(not np.array_equal(run(A, w, sweep, 1, seed), S) for seed in range(12))
+
+
+@pytest.mark.parametrize("sweep,band,ref", [(sym_sweep_l2, sym_band, "sb2st"), (bd_sweep_l2, upper_band, "gb2bd")])
+def test_l2_kernels_three_step_lag_is_exact(sweep, band, ref):
+    """The L2 kernels (w up to 128) wait for step t + 2 of the sweep before; each vector's
+    update touches the band store at its own moment."""
+    for n, w in [(30, 3), (37, 5)]:
+        A = band(n, w, 3 * n + w)
+        S = run(A, w, sweep, 3)
+        if ref == "sb2st":
+            d, e = oracle.sb2st(np.tril(A), w)
+            off = np.diag(S, -1)
+        else:
+            d, e = oracle.gb2bd(A, w)
+            off = np.diag(S, 1)
+        assert np.max(np.abs(np.diag(S) - d)) <= 1e-12 and np.max(np.abs(off - e)) <= 1e-12
+        for seed in range(12):
+            assert np.array_equal(run(A, w, sweep, 3, seed), S), (n, w, seed)
+        # one step less, and the single shared entry can be read too early
+        assert any(not np.array_equal(run(A, w, sweep, 2, seed), S) for seed in range(24))
